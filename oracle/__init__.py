@@ -1,0 +1,27 @@
+"""CPU oracle of the detect pipeline (test infrastructure, not product code).
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and ``bench.py`` (its cpu_baseline
+and reference arm) may import this package. It shares no code with the CUDA
+path in ``paper_1607_00908_gb300/``; the two meet only on the seeded input
+fields of ``paper_1607_00908_gb300.inputs``.
+"""
+from .detect import (  # noqa: F401
+    Q,
+    Detector,
+    centroids_q10,
+    component_sums,
+    delaunay_edges,
+    flips,
+    foreground,
+    incircle,
+    label_components,
+    make_keys,
+    match_overlap,
+    orient2d,
+    owners,
+    owners_bruteforce,
+    plaquette_diagonal,
+    rdiv,
+    split_keys,
+    wrap,
+)

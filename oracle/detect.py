@@ -1,0 +1,496 @@
+"""CPU oracle for the detect pipeline: plain, slow, and written to be checked by eye.
+
+TEST INFRASTRUCTURE ONLY. Nothing on the product path imports this module: only
+``tests/``, ``__graft_entry__.smoke()`` and the ``cpu_baseline`` / reference arm
+of ``bench.py`` may call it. It shares no code with the CUDA path.
+
+Every function states the passage of the paper it follows (M. Bernaschi,
+M. Lulli, M. Sbragaglia, "GPU Based Detection of Topological Changes in Voronoi
+Diagrams", arXiv:1607.00908). Where the paper is silent or ambiguous the
+reading taken is stated in the docstring. All arithmetic on the path is
+integer (int64, or Python integers for the incircle determinant), so results
+are exact and the GPU must match them bit for bit.
+
+Library primitives used as single steps: ``scipy.ndimage.label`` (connected
+components on the open rectangle), ``numpy.unique`` / sorting, and
+``scipy.spatial.cKDTree`` (exact k-nearest-neighbour search; its float64
+arithmetic is exact for the integer fixed-point coordinates used here, and
+ties are resolved in integers afterwards). ``owners_bruteforce`` is the
+literal definition and pins ``owners``.
+"""
+from __future__ import annotations
+
+import numpy as np
+from scipy import ndimage
+from scipy.spatial import cKDTree
+
+#: Fixed-point scale of centroids: 1/1024 site.
+Q = 1024
+
+
+# ----------------------------------------------------------------------------
+# Small integer helpers
+# ----------------------------------------------------------------------------
+
+def wrap(d, L):
+    """Minimum-image displacement on a ring of length L: ((d + L//2) mod L) - L//2.
+
+    Result lies in [-(L//2), L - L//2). Works elementwise on int64 arrays and on
+    Python ints (both use floor modulo).
+    """
+    h = L // 2
+    return ((d + h) % L) - h
+
+
+def rdiv(p, q):
+    """Round-half-up integer division p/q for q > 0: floor((2p + q) / (2q))."""
+    return (2 * p + q) // (2 * q)
+
+
+# ----------------------------------------------------------------------------
+# Section 3.1: threshold and cluster labelling
+# ----------------------------------------------------------------------------
+
+def foreground(F, theta: float = 0.5, polarity: int = 1) -> np.ndarray:
+    """Spin variable of Section 3.1 as a boolean: site belongs to a bubble.
+
+    The paper calls a site part of a bubble when the field is *below* the
+    threshold; the workloads here mark droplets by values *above* it. Reading:
+    ``polarity=+1`` means F > theta (strict), ``polarity=-1`` means F < theta.
+    Comparisons are done in float32, and NaN is never foreground.
+    """
+    F = np.asarray(F, dtype=np.float32)
+    t = np.float32(theta)
+    return (F > t) if polarity > 0 else (F < t)
+
+
+def _neighbour_offsets(connectivity: int):
+    if connectivity == 4:
+        return [(1, 0), (0, 1)]
+    if connectivity == 8:
+        return [(1, 0), (0, 1), (1, 1), (1, -1)]
+    raise ValueError("connectivity must be 4 or 8")
+
+
+def label_components(fg: np.ndarray, connectivity: int = 4):
+    """Periodic connected-component labels with canonical ids (Section 3.1).
+
+    Bubbles are maximal sets of foreground sites connected through lattice
+    neighbours; the domain is a torus (both axes periodic). Reading: 4-neighbour
+    connectivity by default (the Ising cluster-labelling analogy of Section 3.1),
+    8 as an option. The paper fixes no label values; here a component's id is
+    the rank of its smallest linear index y*Lx + x among all components, so ids
+    run 0..K-1 in raster order of first sites. Background is -1.
+
+    Returns (labels int32 [Ly, Lx], K).
+    """
+    fg = np.asarray(fg, dtype=bool)
+    Ly, Lx = fg.shape
+    struct = ndimage.generate_binary_structure(2, 1 if connectivity == 4 else 2)
+    raw, npieces = ndimage.label(fg, structure=struct)
+    if npieces == 0:
+        return np.full((Ly, Lx), -1, dtype=np.int32), 0
+    # Pieces of the open rectangle that touch across a periodic seam are the
+    # same component: collect every neighbour pair (with wrap) whose raw labels
+    # differ and join them with a union-find.
+    parent = list(range(npieces + 1))
+
+    def find(a):
+        while parent[a] != a:
+            parent[a] = parent[parent[a]]
+            a = parent[a]
+        return a
+
+    pairs = set()
+    for dx, dy in _neighbour_offsets(connectivity):
+        nb = np.roll(np.roll(raw, -dy, axis=0), -dx, axis=1)   # raw at (x+dx, y+dy)
+        m = (raw > 0) & (nb > 0) & (raw != nb)
+        if m.any():
+            a = raw[m].astype(np.int64)
+            b = nb[m].astype(np.int64)
+            pairs.update(zip(np.minimum(a, b).tolist(), np.maximum(a, b).tolist()))
+    for a, b in pairs:
+        ra, rb = find(a), find(b)
+        if ra != rb:
+            parent[max(ra, rb)] = min(ra, rb)
+    roots = np.array([find(a) for a in range(npieces + 1)], dtype=np.int64)
+    # smallest linear index of each piece, then of each merged component
+    flat = raw.ravel()
+    ids, first = np.unique(flat, return_index=True)
+    first_of_piece = np.full(npieces + 1, np.iinfo(np.int64).max, dtype=np.int64)
+    first_of_piece[ids] = first
+    first_of_root = np.full(npieces + 1, np.iinfo(np.int64).max, dtype=np.int64)
+    np.minimum.at(first_of_root, roots[1:], first_of_piece[1:])
+    comp_roots = np.unique(roots[1:])
+    order = np.argsort(first_of_root[comp_roots], kind="stable")
+    canon = np.full(npieces + 1, -1, dtype=np.int64)
+    rank_of_root = np.empty(npieces + 1, dtype=np.int64)
+    rank_of_root[comp_roots[order]] = np.arange(comp_roots.size)
+    canon[1:] = rank_of_root[roots[1:]]
+    labels = canon[raw].astype(np.int32)
+    return labels, int(comp_roots.size)
+
+
+# ----------------------------------------------------------------------------
+# Section 3.1: size and centre of mass
+# ----------------------------------------------------------------------------
+
+def component_sums(labels: np.ndarray, K: int):
+    """Per component: root site r, size n, and Sx, Sy = sums of wrap(x - x_r), wrap(y - y_r).
+
+    Section 3.1 counts the sites of each bubble and sums their x and y
+    coordinates separately. On the torus the coordinates are taken as
+    minimum-image displacements from the component's first site r (smallest
+    linear index), which is this implementation's reading of a periodic centre
+    of mass. Returns int64 arrays (xr, yr, n, Sx, Sy), each of length K.
+    """
+    Ly, Lx = labels.shape
+    flat = labels.ravel().astype(np.int64)
+    idx = np.flatnonzero(flat >= 0)
+    lab = flat[idx]
+    first = np.full(K, Lx * Ly, dtype=np.int64)
+    np.minimum.at(first, lab, idx)
+    xr = first % Lx
+    yr = first // Lx
+    x = idx % Lx
+    y = idx // Lx
+    dx = wrap(x - xr[lab], Lx)
+    dy = wrap(y - yr[lab], Ly)
+    n = np.bincount(lab, minlength=K).astype(np.int64)
+    Sx = np.zeros(K, dtype=np.int64)
+    Sy = np.zeros(K, dtype=np.int64)
+    np.add.at(Sx, lab, dx)
+    np.add.at(Sy, lab, dy)
+    return xr, yr, n, Sx, Sy
+
+
+def centroids_q10(labels: np.ndarray, K: int) -> np.ndarray:
+    """Centre of mass of each bubble in 1/1024-site fixed point (Section 3.1).
+
+    c = x_r + Sx / n per axis, with the division rounded half up in units of
+    1/1024 site and the result taken modulo the lattice:
+    cx = (1024*x_r + rdiv(1024*Sx, n)) mod (1024*Lx), likewise cy.
+    Returns int64 array [K, 2] of (cx, cy).
+    """
+    Ly, Lx = labels.shape
+    if K == 0:
+        return np.zeros((0, 2), dtype=np.int64)
+    xr, yr, n, Sx, Sy = component_sums(labels, K)
+    cx = np.mod(Q * xr + rdiv(Q * Sx, n), Q * Lx)
+    cy = np.mod(Q * yr + rdiv(Q * Sy, n), Q * Ly)
+    return np.stack([cx, cy], axis=1).astype(np.int64)
+
+
+# ----------------------------------------------------------------------------
+# Section 3.2.1: digital Voronoi tessellation
+# ----------------------------------------------------------------------------
+
+def _site_grid(Lx: int, Ly: int):
+    y, x = np.divmod(np.arange(Lx * Ly, dtype=np.int64), Lx)
+    return x, y
+
+
+def sq_dist_q10(sx, sy, cx, cy, Lx: int, Ly: int):
+    """Exact squared minimum-image distance between Q10 points (int64)."""
+    dx = wrap(sx - cx, Q * Lx)
+    dy = wrap(sy - cy, Q * Ly)
+    return dx * dx + dy * dy
+
+
+def owners_bruteforce(cq: np.ndarray, Lx: int, Ly: int, sites=None) -> np.ndarray:
+    """Digital Voronoi colouring, literally as in Section 3.2.1.
+
+    Every site (foreground or not) takes the label of the nearest centre of
+    mass by squared Euclidean distance (no square root). Distances are exact
+    int64 in 1/1024-site units with minimum image on the torus; the site (x, y)
+    sits at (1024x, 1024y). The paper leaves ties open; here a tie goes to the
+    smallest label (np.argmin returns the first minimum). With no centres every
+    owner is -1. ``sites`` optionally restricts the evaluation to an int64 array
+    of linear indices.
+    """
+    K = cq.shape[0]
+    if sites is None:
+        x, y = _site_grid(Lx, Ly)
+    else:
+        sites = np.asarray(sites, dtype=np.int64)
+        y, x = np.divmod(sites, Lx)
+    out = np.full(x.shape[0], -1, dtype=np.int32)
+    if K == 0:
+        return out if sites is not None else out.reshape(Ly, Lx)
+    sx = Q * x
+    sy = Q * y
+    cx = cq[:, 0].astype(np.int64)
+    cy = cq[:, 1].astype(np.int64)
+    chunk = max(1, 4_000_000 // K)
+    for s in range(0, x.shape[0], chunk):
+        d2 = sq_dist_q10(sx[s:s + chunk, None], sy[s:s + chunk, None],
+                         cx[None, :], cy[None, :], Lx, Ly)
+        out[s:s + chunk] = np.argmin(d2, axis=1)
+    return out if sites is not None else out.reshape(Ly, Lx)
+
+
+def owners(cq: np.ndarray, Lx: int, Ly: int, workers: int = 1) -> np.ndarray:
+    """Same result as ``owners_bruteforce``, with a k-d tree as the search step.
+
+    The tree (periodic box of 1024*Lx by 1024*Ly) returns the k = 4 nearest
+    centres of every site. Its float64 distances are exact here: coordinates are
+    integers below 2**23 and squared distances below 2**45. The exact int64
+    squared distances of those k candidates are then recomputed, and the owner
+    is the smallest label among the candidates at the minimum. Where the k-th
+    candidate also sits at the minimum (a tie that may extend past k), the site
+    is resolved by the brute-force definition.
+    """
+    K = cq.shape[0]
+    if K == 0:
+        return np.full((Ly, Lx), -1, dtype=np.int32)
+    x, y = _site_grid(Lx, Ly)
+    sx = Q * x
+    sy = Q * y
+    k = min(4, K)
+    tree = cKDTree(cq.astype(np.float64), boxsize=[float(Q * Lx), float(Q * Ly)])
+    pts = np.stack([sx, sy], axis=1).astype(np.float64)
+    _, ind = tree.query(pts, k=k, workers=workers)
+    ind = ind.reshape(-1, k).astype(np.int64)
+    cx = cq[:, 0].astype(np.int64)
+    cy = cq[:, 1].astype(np.int64)
+    d2 = sq_dist_q10(sx[:, None], sy[:, None], cx[ind], cy[ind], Lx, Ly)
+    best = d2.min(axis=1)
+    at_best = d2 == best[:, None]
+    cand = np.where(at_best, ind, np.iinfo(np.int64).max)
+    out = cand.min(axis=1).astype(np.int32)
+    if k < K:
+        unsure = np.flatnonzero(at_best[:, k - 1])
+        if unsure.size:
+            out[unsure] = owners_bruteforce(cq, Lx, Ly, sites=unsure)
+    return out.reshape(Ly, Lx)
+
+
+# ----------------------------------------------------------------------------
+# Section 3.2.2: Delaunay edges from the digital Voronoi colouring
+# ----------------------------------------------------------------------------
+
+def orient2d(a, b, c) -> int:
+    """Twice the signed area of triangle abc (Python ints, exact)."""
+    return (b[0] - a[0]) * (c[1] - a[1]) - (b[1] - a[1]) * (c[0] - a[0])
+
+
+def incircle(a, b, c, d) -> int:
+    """In-circle determinant (Python ints, exact): > 0 iff d lies inside the
+    circle through a, b, c when a, b, c are counter-clockwise."""
+    adx, ady = a[0] - d[0], a[1] - d[1]
+    bdx, bdy = b[0] - d[0], b[1] - d[1]
+    cdx, cdy = c[0] - d[0], c[1] - d[1]
+    return ((adx * adx + ady * ady) * (bdx * cdy - cdx * bdy)
+            + (bdx * bdx + bdy * bdy) * (cdx * ady - adx * cdy)
+            + (cdx * cdx + cdy * cdy) * (adx * bdy - bdx * ady))
+
+
+def _sign(v: int) -> int:
+    return (v > 0) - (v < 0)
+
+
+def plaquette_diagonal(A: int, B: int, C: int, D: int, cq: np.ndarray,
+                       Lx: int, Ly: int):
+    """Diagonal link of a 2x2 plaquette whose four owners are pairwise distinct.
+
+    The plaquette's sites (x,y), (x+1,y), (x+1,y+1), (x,y+1) carry owners A, B,
+    C, D in cyclic order, so four Voronoi cells meet inside it and one of the
+    diagonals A-C or B-D is a Delaunay edge (Section 3.2.2, the second-nearest-
+    neighbour case, whose fifth condition decides which diagonal to keep). The
+    figure that fixes the paper's inner-frame point is lost, so the decision is
+    taken here by the exact Delaunay criterion on the four centres, unwrapped by
+    minimum image around A: s = sign(incircle(a,b,c,d)) * sign(orient(a,b,c)).
+    s > 0 (d inside the circle of a, b, c) keeps B-D, s < 0 keeps A-C, and an
+    exact tie (s = 0) keeps the diagonal whose smaller label is smaller.
+    Returns the kept pair (lo, hi).
+    """
+    ax, ay = int(cq[A, 0]), int(cq[A, 1])
+
+    def unwrapped(i):
+        return (ax + int(wrap(int(cq[i, 0]) - ax, Q * Lx)),
+                ay + int(wrap(int(cq[i, 1]) - ay, Q * Ly)))
+
+    a = (ax, ay)
+    b, c, d = unwrapped(B), unwrapped(C), unwrapped(D)
+    s = _sign(incircle(a, b, c, d)) * _sign(orient2d(a, b, c))
+    if s > 0 or (s == 0 and min(B, D) < min(A, C)):
+        return (min(B, D), max(B, D))
+    return (min(A, C), max(A, C))
+
+
+def delaunay_edges(owner: np.ndarray, cq: np.ndarray) -> np.ndarray:
+    """Delaunay edge set of the digital Voronoi diagram, as sorted uint64 keys.
+
+    Section 3.2.2 reads the adjacency of Voronoi cells off the colours of
+    neighbouring sites. Reading taken here (the paper's vertex/inner-frame rule
+    depends on a lost figure): two labels are linked when
+
+    (i)  a site and its +x or +y neighbour (periodic) have different owners, or
+    (ii) a 2x2 plaquette carries four pairwise distinct owners; then the
+         diagonal chosen by ``plaquette_diagonal`` is linked.
+
+    A link {a, b} is stored once as the key (min << 32) | max; the result is
+    sorted and unique (the "compressed adjacency" of Section 3.2.2).
+    """
+    Ly, Lx = owner.shape
+    A = owner.astype(np.int64)
+    B = np.roll(A, -1, axis=1)                    # owner at (x+1, y)
+    D = np.roll(A, -1, axis=0)                    # owner at (x, y+1)
+    C = np.roll(B, -1, axis=0)                    # owner at (x+1, y+1)
+    keys = []
+    for P, R in ((A, B), (A, D)):
+        m = P != R
+        lo = np.minimum(P[m], R[m])
+        hi = np.maximum(P[m], R[m])
+        keys.append((lo << 32) | hi)
+    four = (A != B) & (A != C) & (A != D) & (B != C) & (B != D) & (C != D)
+    diag = []
+    for ia, ib, ic, id_ in zip(A[four].tolist(), B[four].tolist(),
+                               C[four].tolist(), D[four].tolist()):
+        lo, hi = plaquette_diagonal(ia, ib, ic, id_, cq, Lx, Ly)
+        diag.append((lo << 32) | hi)
+    keys.append(np.array(diag, dtype=np.int64))
+    allk = np.concatenate(keys) if keys else np.zeros(0, dtype=np.int64)
+    return np.unique(allk).astype(np.uint64)
+
+
+# ----------------------------------------------------------------------------
+# Section 3.2.3: isomorphism between past and now labels
+# ----------------------------------------------------------------------------
+
+def match_overlap(lab_prev: np.ndarray, lab_now: np.ndarray, K_prev: int, K_now: int):
+    """Label isomorphism Phi_{P->N} by mutual best overlap (Section 3.2.3).
+
+    The paper obtains Phi by comparing the two sets of centres of mass of
+    frames a short time apart, and excludes labels where the map is not
+    injective (a bubble vanished) or a now-label has no partner (a bubble
+    appeared). Reading used here: H(p, n) counts sites labelled p in the past
+    frame and n now. best_n(p) = argmax_n H(p, n) (ties to the smallest n),
+    best_p(n) likewise, and Phi(p) = n exactly when the choice is mutual;
+    every other label is unmatched (-1). Returns (phi [K_prev], inv [K_now]).
+    """
+    phi = np.full(K_prev, -1, dtype=np.int32)
+    inv = np.full(K_now, -1, dtype=np.int32)
+    m = (lab_prev >= 0) & (lab_now >= 0)
+    if K_prev == 0 or K_now == 0 or not m.any():
+        return phi, inv
+    keys = lab_prev[m].astype(np.int64) * K_now + lab_now[m].astype(np.int64)
+    uk, cnt = np.unique(keys, return_counts=True)
+    p = uk // K_now
+    n = uk % K_now
+    # best n for each p: largest count, then smallest n
+    o = np.lexsort((n, -cnt, p))
+    first = np.ones(o.size, dtype=bool)
+    first[1:] = p[o][1:] != p[o][:-1]
+    best_n = np.full(K_prev, -1, dtype=np.int64)
+    best_n[p[o][first]] = n[o][first]
+    # best p for each n: largest count, then smallest p
+    o = np.lexsort((p, -cnt, n))
+    first = np.ones(o.size, dtype=bool)
+    first[1:] = n[o][1:] != n[o][:-1]
+    best_p = np.full(K_now, -1, dtype=np.int64)
+    best_p[n[o][first]] = p[o][first]
+    pp = np.flatnonzero(best_n >= 0)
+    mutual = best_p[best_n[pp]] == pp
+    phi[pp[mutual]] = best_n[pp[mutual]]
+    inv[best_n[pp[mutual]]] = pp[mutual]
+    return phi, inv
+
+
+# ----------------------------------------------------------------------------
+# Sections 3.2.3-3.2.4: translation, comparison, breaking and arising links
+# ----------------------------------------------------------------------------
+
+def split_keys(E: np.ndarray):
+    E = np.asarray(E, dtype=np.uint64)
+    return (E >> np.uint64(32)).astype(np.int64), (E & np.uint64(0xFFFFFFFF)).astype(np.int64)
+
+
+def make_keys(a, b) -> np.ndarray:
+    a = np.asarray(a, dtype=np.int64)
+    b = np.asarray(b, dtype=np.int64)
+    lo = np.minimum(a, b)
+    hi = np.maximum(a, b)
+    return ((lo << 32) | hi).astype(np.uint64)
+
+
+def flips(E_prev: np.ndarray, E_now: np.ndarray, phi: np.ndarray, inv: np.ndarray):
+    """Breaking and arising links between two triangulations (Sections 3.2.3-3.2.4).
+
+    Translation: every past link {a, b} with both ends matched becomes
+    {Phi(a), Phi(b)} in now-labels. Links with an unmatched end, and now-links
+    touching a label outside Phi's image, are excluded (appearing or vanishing
+    bubbles). A link present only in the translated past set is *breaking*,
+    one present only in the now set is *arising*. Both lists are sorted by
+    now-key; each breaking link also carries its past-label key. ``active`` is
+    the local trigger: 1 for every now-label at an end of a flip.
+
+    Returns dict(breaking, breaking_prev, arising, active, global_trigger).
+    """
+    K_now = inv.shape[0]
+    a, b = split_keys(E_prev)
+    keep = (phi[a] >= 0) & (phi[b] >= 0) if a.size else np.zeros(0, dtype=bool)
+    EPt = np.unique(make_keys(phi[a[keep]], phi[b[keep]])) if keep.any() else np.zeros(0, np.uint64)
+    na, nb = split_keys(E_now)
+    keepn = (inv[na] >= 0) & (inv[nb] >= 0) if na.size else np.zeros(0, dtype=bool)
+    ENt = np.asarray(E_now, dtype=np.uint64)[keepn]
+    breaking = np.setdiff1d(EPt, ENt).astype(np.uint64)
+    arising = np.setdiff1d(ENt, EPt).astype(np.uint64)
+    ba, bb = split_keys(breaking)
+    breaking_prev = make_keys(inv[ba], inv[bb]) if breaking.size else np.zeros(0, np.uint64)
+    active = np.zeros(K_now, dtype=np.uint8)
+    for E in (breaking, arising):
+        x, y = split_keys(E)
+        active[x] = 1
+        active[y] = 1
+    return dict(breaking=breaking, breaking_prev=breaking_prev, arising=arising,
+                active=active, global_trigger=int(breaking.size + arising.size > 0))
+
+
+# ----------------------------------------------------------------------------
+# Whole pipeline, one frame after another
+# ----------------------------------------------------------------------------
+
+class Detector:
+    """Frame-to-frame detector: push fields in order, get every intermediate.
+
+    ``push(F)`` runs threshold -> labels -> Q10 centroids -> Voronoi owners ->
+    edge keys on F, then (from the second frame on) the match against the
+    previous frame and the flip lists. The first frame reports no changes.
+    """
+
+    def __init__(self, Lx: int, Ly: int, theta: float = 0.5, polarity: int = 1,
+                 connectivity: int = 4, workers: int = 1, voronoi: str = "kdtree"):
+        self.Lx, self.Ly = Lx, Ly
+        self.theta, self.polarity = theta, polarity
+        self.connectivity = connectivity
+        self.workers = workers
+        self.voronoi = voronoi
+        self.prev = None
+        self.frame = 0
+
+    def push(self, F: np.ndarray) -> dict:
+        F = np.asarray(F, dtype=np.float32)
+        assert F.shape == (self.Ly, self.Lx)
+        fg = foreground(F, self.theta, self.polarity)
+        labels, K = label_components(fg, self.connectivity)
+        cq = centroids_q10(labels, K)
+        if self.voronoi == "brute":
+            own = owners_bruteforce(cq, self.Lx, self.Ly)
+        else:
+            own = owners(cq, self.Lx, self.Ly, workers=self.workers)
+        E = delaunay_edges(own, cq)
+        out = dict(frame=self.frame, labels=labels, K=K, centroids=cq, owners=own, edges=E)
+        if self.prev is None:
+            out.update(phi=np.zeros(0, np.int32), inv=np.full(K, -1, np.int32),
+                       breaking=np.zeros(0, np.uint64), breaking_prev=np.zeros(0, np.uint64),
+                       arising=np.zeros(0, np.uint64), active=np.zeros(K, np.uint8),
+                       global_trigger=0, K_prev=0, n_matched=0)
+        else:
+            p = self.prev
+            phi, inv = match_overlap(p["labels"], labels, p["K"], K)
+            fl = flips(p["edges"], E, phi, inv)
+            out.update(phi=phi, inv=inv, K_prev=p["K"], n_matched=int((phi >= 0).sum()), **fl)
+        self.prev = dict(labels=labels, K=K, edges=E)
+        self.frame += 1
+        return out

@@ -1,0 +1,619 @@
+"""Pins of the CPU oracle against facts fixed by the paper and by mathematics.
+
+Each test checks the oracle against something other than itself: hand-derived
+fixtures under tests/golden/, brute force on tiny inputs (BFS flood fill,
+all-centres argmin, an O(n^4) empty-circle Delaunay), closed forms (centroids
+of symmetric shapes), invariants (translation covariance, the torus Euler
+relation E = 3V of a triangulation) and constructed events (identity frames,
+translations, births, deaths, merges, a single T1 flip).
+"""
+from __future__ import annotations
+
+import os
+import random
+from collections import deque
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1607_00908_gb300 import inputs as I
+from tests.delaunay_bruteforce import periodic_delaunay
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+Q = 1024
+
+
+# ----------------------------------------------------------------------------
+# helpers independent of the oracle
+# ----------------------------------------------------------------------------
+
+def bfs_labels(fg: np.ndarray, connectivity: int = 4) -> np.ndarray:
+    """Flood fill in raster order on the torus: ids come out canonical directly."""
+    Ly, Lx = fg.shape
+    lab = -np.ones((Ly, Lx), dtype=np.int64)
+    if connectivity == 4:
+        steps = [(1, 0), (-1, 0), (0, 1), (0, -1)]
+    else:
+        steps = [(a, b) for a in (-1, 0, 1) for b in (-1, 0, 1) if (a, b) != (0, 0)]
+    nxt = 0
+    for y in range(Ly):
+        for x in range(Lx):
+            if fg[y, x] and lab[y, x] < 0:
+                lab[y, x] = nxt
+                dq = deque([(x, y)])
+                while dq:
+                    cx, cy = dq.popleft()
+                    for dx, dy in steps:
+                        nx, ny = (cx + dx) % Lx, (cy + dy) % Ly
+                        if fg[ny, nx] and lab[ny, nx] < 0:
+                            lab[ny, nx] = nxt
+                            dq.append((nx, ny))
+                nxt += 1
+    return lab
+
+
+def renumber_canonical(lab: np.ndarray) -> np.ndarray:
+    """Relabel so ids are ranks of each label's first raster-order site."""
+    flat = lab.ravel()
+    out = -np.ones_like(flat)
+    seen = {}
+    for i, v in enumerate(flat.tolist()):
+        if v >= 0:
+            if v not in seen:
+                seen[v] = len(seen)
+            out[i] = seen[v]
+    return out.reshape(lab.shape)
+
+
+def read_golden(name):
+    sections = {}
+    cur = None
+    with open(os.path.join(GOLDEN, name)) as f:
+        for line in f:
+            line = line.strip()
+            if not line or line.startswith("#"):
+                continue
+            parts = line.split()
+            if parts[0] in ("Lx", "Ly", "K"):
+                sections[parts[0]] = int(parts[1])
+            elif len(parts) == 1 and not parts[0].lstrip("-").isdigit():
+                cur = parts[0]
+                sections[cur] = []
+            else:
+                sections.setdefault(cur, []).append([int(float(p)) for p in parts])
+    return sections
+
+
+# ----------------------------------------------------------------------------
+# Section 3.1: labelling
+# ----------------------------------------------------------------------------
+
+def test_golden_ccl_centroids():
+    g = read_golden("ccl_centroid_6x5.txt")
+    F = np.array(g["field"], dtype=np.float32)
+    lab, K = O.label_components(O.foreground(F, 0.5))
+    assert K == g["K"]
+    assert np.array_equal(lab, np.array(g["labels"]))
+    cq = O.centroids_q10(lab, K)
+    assert np.array_equal(cq, np.array(g["centroids"]))
+
+
+@pytest.mark.parametrize("conn", [4, 8])
+def test_ccl_matches_bfs_on_random_tiny_tori(conn):
+    rng = np.random.default_rng(11 + conn)
+    for trial in range(300):
+        Lx = int(rng.integers(1, 13))
+        Ly = int(rng.integers(1, 13))
+        p = float(rng.uniform(0.05, 0.95))
+        fg = rng.random((Ly, Lx)) < p
+        lab, K = O.label_components(fg, conn)
+        ref = bfs_labels(fg, conn)
+        assert np.array_equal(lab, ref), (trial, Lx, Ly)
+        assert K == (ref.max() + 1 if (ref >= 0).any() else 0)
+
+
+def test_threshold_polarity_and_nan():
+    F = np.array([[0.5, 0.50001, np.nan, -1.0, 2.0]], dtype=np.float32)
+    assert O.foreground(F, 0.5, +1).tolist() == [[False, True, False, False, True]]
+    assert O.foreground(F, 0.5, -1).tolist() == [[False, False, False, True, False]]
+
+
+def test_ccl_roll_covariance():
+    F = I.smoothed_noise(96, 80, 3.0, seed=4)
+    lab, K = O.label_components(O.foreground(F))
+    for sx, sy in [(1, 0), (0, 1), (17, 33), (79, 95)]:
+        Fr = np.roll(np.roll(F, sy, axis=0), sx, axis=1)
+        labr, Kr = O.label_components(O.foreground(Fr))
+        assert Kr == K
+        expect = renumber_canonical(np.roll(np.roll(lab, sy, axis=0), sx, axis=1))
+        assert np.array_equal(labr, expect)
+
+
+def test_ccl_discs_are_components():
+    st = I.rsa_discs(192, seed=2, max_consecutive_rejections=20000)
+    F = I.raster_discs(st)
+    lab, K = O.label_components(O.foreground(F))
+    assert K == st.n
+    # every disc's raster is exactly one component
+    for i in range(st.n):
+        one = I.raster_discs(I.DiscState(st.L, st.cx[i:i + 1], st.cy[i:i + 1], st.r[i:i + 1]))
+        sites = one > 0.5
+        vals = np.unique(lab[sites])
+        assert vals.size == 1 and vals[0] >= 0
+        assert int((lab == vals[0]).sum()) == int(sites.sum())
+
+
+# ----------------------------------------------------------------------------
+# Section 3.1: centre of mass
+# ----------------------------------------------------------------------------
+
+@pytest.mark.parametrize("w,h", [(1, 1), (3, 5), (4, 4), (6, 3), (7, 8)])
+def test_centroid_closed_form_rectangles_across_seams(w, h):
+    """A w x h block has its centre at x0 + (w-1)/2, y0 + (h-1)/2 exactly."""
+    Lx, Ly = 23, 19
+    for x0 in (0, 5, Lx - 2, Lx - 1):
+        for y0 in (0, 7, Ly - 3):
+            F = np.zeros((Ly, Lx), np.float32)
+            for dy in range(h):
+                for dx in range(w):
+                    F[(y0 + dy) % Ly, (x0 + dx) % Lx] = 1.0
+            lab, K = O.label_components(O.foreground(F))
+            assert K == 1
+            cq = O.centroids_q10(lab, K)
+            ex = (Q * (2 * x0 + w - 1)) // 2 % (Q * Lx)
+            ey = (Q * (2 * y0 + h - 1)) // 2 % (Q * Ly)
+            assert tuple(cq[0]) == (ex, ey)
+
+
+@pytest.mark.parametrize("L", [5, 7, 23])
+def test_centroid_closed_form_half_ring_bars(L):
+    """A bar of w = ceil(L/2) sites starting at its own first site: every
+    displacement 0..w-1 lies inside the minimum-image window, so the centroid
+    is the bar's midpoint, in both axes and on odd rings too."""
+    w = (L + 1) // 2
+    for y0 in range(L):
+        F = np.zeros((L, L), np.float32)
+        F[y0, 0:w] = 1.0
+        lab, K = O.label_components(O.foreground(F))
+        cq = O.centroids_q10(lab, K)
+        assert tuple(cq[0]) == ((Q * (w - 1)) // 2, Q * y0)
+        lab, K = O.label_components(O.foreground(F.T.copy()))
+        cq = O.centroids_q10(lab, K)
+        assert tuple(cq[0]) == (Q * y0, (Q * (w - 1)) // 2)
+
+
+def test_centroid_closed_form_discs_on_grid_points():
+    """A disc raster centred on an integer or half-integer point is symmetric."""
+    L = 40
+    for cx, cy in [(10.0, 10.0), (0.0, 0.0), (39.5, 20.5), (0.5, 39.0), (20.5, 0.5)]:
+        for r in (2.3, 3.7, 5.0):
+            st = I.DiscState(L, np.array([cx]), np.array([cy]), np.array([r]))
+            F = I.raster_discs(st)
+            lab, K = O.label_components(O.foreground(F))
+            assert K == 1
+            cq = O.centroids_q10(lab, K)
+            assert tuple(cq[0]) == (int(round(Q * cx)) % (Q * L), int(round(Q * cy)) % (Q * L))
+
+
+def test_centroid_within_half_unit_of_plain_mean():
+    """Away from the seams the centroid is the plain mean of coordinates; near a
+    seam, rolling the lattice to move the bubble away gives the same answer."""
+    F = I.smoothed_noise(64, 72, 2.5, seed=9)
+    lab, K = O.label_components(O.foreground(F))
+    cq = O.centroids_q10(lab, K)
+    Ly, Lx = lab.shape
+    for k in range(K):
+        ys, xs = np.nonzero(lab == k)
+        # roll so that the bubble's first site sits at the lattice centre
+        first = int(np.flatnonzero(lab.ravel() == k)[0])
+        fy, fx = divmod(first, Lx)
+        sx, sy = Lx // 2 - fx, Ly // 2 - fy
+        xr = (xs + sx) % Lx
+        yr = (ys + sy) % Ly
+        if xr.max() - xr.min() >= Lx // 2 or yr.max() - yr.min() >= Ly // 2:
+            continue  # too wide for a seam-free view
+        mx = Q * (xr.mean() - sx)
+        my = Q * (yr.mean() - sy)
+        dx = (cq[k, 0] - mx + Q * Lx / 2) % (Q * Lx) - Q * Lx / 2
+        dy = (cq[k, 1] - my + Q * Ly / 2) % (Q * Ly) - Q * Ly / 2
+        assert abs(dx) <= 0.5 + 1e-9 and abs(dy) <= 0.5 + 1e-9
+
+
+def _narrow(lab, k):
+    """True when bubble k fits in a half-lattice window around its first site."""
+    Ly, Lx = lab.shape
+    first = int(np.flatnonzero(lab.ravel() == k)[0])
+    fy, fx = divmod(first, Lx)
+    ys, xs = np.nonzero(lab == k)
+    dx = (xs - fx + Lx // 2) % Lx - Lx // 2
+    dy = (ys - fy + Ly // 2) % Ly - Ly // 2
+    return dx.max() - dx.min() < Lx // 2 - 1 and dy.max() - dy.min() < Ly // 2 - 1 \
+        and abs(dx).max() < Lx // 2 - 1 and abs(dy).max() < Ly // 2 - 1
+
+
+def test_centroid_translation_covariance():
+    """Shifting the field by whole sites shifts every narrow bubble's centroid
+    by exactly 1024 units per site (bubbles spanning half the lattice or more
+    have a root-dependent minimum image and are excluded)."""
+    F = I.smoothed_noise(48, 56, 2.0, seed=5)
+    lab, K = O.label_components(O.foreground(F))
+    cq = O.centroids_q10(lab, K)
+    narrow = [k for k in range(K) if _narrow(lab, k)]
+    assert len(narrow) >= 5
+    for sx, sy in [(3, 0), (0, 11), (29, 47)]:
+        labr, Kr = O.label_components(O.foreground(np.roll(np.roll(F, sy, 0), sx, 1)))
+        cqr = O.centroids_q10(labr, Kr)
+        for k in narrow:
+            first = int(np.flatnonzero(lab.ravel() == k)[0])
+            y, x = divmod(first, 56)
+            kr = labr[(y + sy) % 48, (x + sx) % 56]
+            assert tuple(cqr[kr]) == ((cq[k, 0] + Q * sx) % (Q * 56), (cq[k, 1] + Q * sy) % (Q * 48))
+
+
+# ----------------------------------------------------------------------------
+# Section 3.2.1: Voronoi colouring
+# ----------------------------------------------------------------------------
+
+def test_golden_voronoi_ring():
+    g = read_golden("voronoi_ring_8x1.txt")
+    cq = np.array(g["centroids"], dtype=np.int64)
+    own = O.owners(cq, g["Lx"], g["Ly"])
+    assert own.ravel().tolist() == g["owners"][0]
+    E = O.delaunay_edges(own, cq)
+    assert [tuple(p) for p in zip(*O.split_keys(E))] == [tuple(g["edges"][0])]
+
+
+def test_owners_kdtree_matches_bruteforce():
+    rng = np.random.default_rng(3)
+    for trial in range(60):
+        Lx = int(rng.integers(1, 40))
+        Ly = int(rng.integers(1, 40))
+        K = int(rng.integers(1, 25))
+        if trial % 3 == 0:
+            # centres on lattice points and half points: many exact ties
+            cq = np.stack([rng.integers(0, 2 * Lx, K) * (Q // 2),
+                           rng.integers(0, 2 * Ly, K) * (Q // 2)], 1).astype(np.int64)
+        else:
+            cq = np.stack([rng.integers(0, Q * Lx, K), rng.integers(0, Q * Ly, K)], 1).astype(np.int64)
+        a = O.owners(cq, Lx, Ly)
+        b = O.owners_bruteforce(cq, Lx, Ly)
+        assert np.array_equal(a, b), trial
+
+
+def test_owner_tie_goes_to_smallest_label():
+    # site (4, 4) at (4096, 4096); ids 3 and 7 both at squared distance 2*1024^2
+    Lx = Ly = 16
+    cq = np.array([[12000, 12000 + 7 * j] for j in range(10)], dtype=np.int64)
+    cq[3] = (3072, 3072)
+    cq[7] = (5120, 5120)
+    own = O.owners(cq, Lx, Ly)
+    assert own[4, 4] == 3
+    own_b = O.owners_bruteforce(cq, Lx, Ly)
+    assert own_b[4, 4] == 3
+    # same with the labels swapped: still the smaller one wins
+    cq[[3, 7]] = cq[[7, 3]]
+    assert O.owners(cq, Lx, Ly)[4, 4] == 3
+
+
+def test_owners_translation_covariance():
+    rng = np.random.default_rng(8)
+    Lx, Ly, K = 37, 29, 15
+    cq = np.stack([rng.integers(0, Q * Lx, K), rng.integers(0, Q * Ly, K)], 1).astype(np.int64)
+    own = O.owners(cq, Lx, Ly)
+    for sx, sy in [(1, 0), (5, 9), (36, 28)]:
+        cs = np.stack([(cq[:, 0] + Q * sx) % (Q * Lx), (cq[:, 1] + Q * sy) % (Q * Ly)], 1)
+        assert np.array_equal(O.owners(cs, Lx, Ly), np.roll(np.roll(own, sy, 0), sx, 1))
+
+
+def test_owners_empty_and_single():
+    assert (O.owners(np.zeros((0, 2), np.int64), 5, 4) == -1).all()
+    assert (O.owners(np.array([[100, 200]]), 5, 4) == 0).all()
+    assert O.delaunay_edges(O.owners(np.zeros((0, 2), np.int64), 5, 4), np.zeros((0, 2))).size == 0
+
+
+# ----------------------------------------------------------------------------
+# Section 3.2.2: edges
+# ----------------------------------------------------------------------------
+
+def test_golden_plaquette_incircle():
+    rows = read_golden("plaquette_incircle.txt")[None]
+    for ax, ay, bx, by, cx, cy, dx, dy, lo, hi in rows:
+        cq = np.array([[ax, ay], [bx, by], [cx, cy], [dx, dy]], dtype=np.int64)
+        assert O.plaquette_diagonal(0, 1, 2, 3, cq, 64, 64) == (lo, hi)
+
+
+def test_golden_plaquette_owners():
+    g = read_golden("plaquette_owners_10x10.txt")
+    own = np.array(g["owners"], dtype=np.int32)
+    cq = np.array(g["centroids"], dtype=np.int64)
+    E = O.delaunay_edges(own, cq)
+    assert [list(p) for p in zip(*[v.tolist() for v in O.split_keys(E)])] == g["edges"]
+
+
+def _generic_points(rng, L, K, min_sep):
+    pts = []
+    tries = 0
+    while len(pts) < K and tries < 10000:
+        tries += 1
+        p = (int(rng.integers(0, Q * L)), int(rng.integers(0, Q * L)))
+        ok = True
+        for q in pts:
+            dx = O.wrap(p[0] - q[0], Q * L)
+            dy = O.wrap(p[1] - q[1], Q * L)
+            if dx * dx + dy * dy < (min_sep * Q) ** 2:
+                ok = False
+                break
+        if ok:
+            pts.append(p)
+    return pts
+
+
+def _jittered_triangular(rng, a, m, n, Lx, Ly, jitter):
+    pts = []
+    for j in range(n):
+        for i in range(m):
+            x = (i * a + (j % 2) * a / 2 + rng.uniform(-jitter, jitter)) % Lx
+            y = (j * Ly / n + rng.uniform(-jitter, jitter)) % Ly
+            pts.append((int(x * Q), int(y * Q)))
+    return pts
+
+
+def test_edges_equal_bruteforce_delaunay_on_generic_configurations():
+    """Jittered triangular lattices have every dual Voronoi edge several sites
+    long. For those (no cocircular quadruple, every dual edge longer than 3
+    sites) the digital edge set is exactly the periodic Delaunay
+    triangulation, and it satisfies the torus Euler relation E = 3K."""
+    rng = np.random.default_rng(21)
+    a, m, n = 12, 6, 4
+    Lx, Ly = a * m, 42
+    K = m * n
+    checked = 0
+    for trial in range(12):
+        pts = _jittered_triangular(rng, a, m, n, Lx, Ly, jitter=1.5)
+        edges, tris, margin, dual, _ = periodic_delaunay(pts, Q * Lx, Q * Ly, radius=int(2.5 * a * Q))
+        assert len(tris) == 3 * 2 * K          # each of the 2K triangles seen from its 3 vertices
+        if margin == 0 or dual < 3 * Q or len(edges) != 3 * K:
+            continue
+        cq = np.array(pts, dtype=np.int64)
+        own = O.owners_bruteforce(cq, Lx, Ly)
+        E = O.delaunay_edges(own, cq)
+        got = set(zip(*[a_.tolist() for a_ in O.split_keys(E)]))
+        assert got == edges, trial
+        assert len(E) == 3 * K
+        checked += 1
+    assert checked >= 5
+
+
+def test_edges_differ_from_delaunay_only_near_degenerate_quads():
+    """On random point sets every Delaunay edge whose dual Voronoi edge is at
+    least 2*sqrt(2) sites long is found, and every extra digital link is the
+    other diagonal of a quad whose Delaunay diagonal has a short dual edge."""
+    rng = np.random.default_rng(22)
+    L, K = 48, 14
+    for trial in range(8):
+        pts = _generic_points(rng, L, K, min_sep=7)
+        edges, tris, margin, dual, dual_of = periodic_delaunay(pts, Q * L, Q * L, radius=int(0.8 * L * Q))
+        assert len(tris) == 3 * 2 * K
+        cq = np.array(pts, dtype=np.int64)
+        E = O.delaunay_edges(O.owners_bruteforce(cq, L, L), cq)
+        got = set(zip(*[a_.tolist() for a_ in O.split_keys(E)]))
+        for e in edges - got:
+            assert dual_of[e] < 2 * np.sqrt(2) * Q, (trial, e, dual_of[e] / Q)
+        short = [e for e in edges if dual_of[e] < 2 * np.sqrt(2) * Q]
+        short_ends = set(x for e in short for x in e)
+        for e in got - edges:
+            assert e[0] in short_ends and e[1] in short_ends, (trial, e)
+        # the digital links still form a triangulation: a missing Delaunay
+        # edge is replaced by the other diagonal of its quad
+        nb = {}
+        for x, y in edges:
+            nb.setdefault(x, set()).add(y)
+            nb.setdefault(y, set()).add(x)
+        for e in edges - got:
+            opp = sorted(nb[e[0]] & nb[e[1]])
+            if len(opp) == 2:
+                assert (opp[0], opp[1]) in got, (trial, e, opp)
+        if len(edges) == 3 * K:
+            assert len(got) == 3 * K, trial
+
+
+def test_every_cell_connected_on_generic_configurations():
+    rng = np.random.default_rng(5)
+    L, K = 40, 12
+    for _ in range(10):
+        pts = _generic_points(rng, L, K, min_sep=8)
+        cq = np.array(pts, dtype=np.int64)
+        own = O.owners_bruteforce(cq, L, L)
+        for k in range(len(pts)):
+            lab, n = O.label_components(own == k, connectivity=8)
+            assert n == 1
+
+
+# ----------------------------------------------------------------------------
+# Sections 3.2.3-3.2.4: match and flips
+# ----------------------------------------------------------------------------
+
+def _disc_field(L, pts, r):
+    st = I.DiscState(L, np.array([p[0] for p in pts], float), np.array([p[1] for p in pts], float),
+                     np.full(len(pts), r, float))
+    return I.raster_discs(st)
+
+
+def test_identity_frame_has_identity_match_and_no_flips():
+    F = I.smoothed_noise(64, 64, 3.0, seed=1)
+    d = O.Detector(64, 64, voronoi="brute")
+    d.push(F)
+    r = d.push(F.copy())
+    assert np.array_equal(r["phi"], np.arange(r["K"]))
+    assert r["breaking"].size == 0 and r["arising"].size == 0 and r["global_trigger"] == 0
+
+
+def test_integer_translation_is_a_bijection_with_no_flips():
+    """Droplets (radius >= 4) moved by a whole-site shift smaller than their size
+    overlap their own past selves most: Phi is a bijection, and the Voronoi
+    diagram moves rigidly, so no link breaks or arises."""
+    st = I.rsa_discs(96, seed=6, rmin=4.0, rmax=6.0, max_consecutive_rejections=5000)
+    F = I.raster_discs(st)
+    Ly, Lx = F.shape
+    d = O.Detector(Lx, Ly, voronoi="brute")
+    r0 = d.push(F)
+    sx, sy = 2, 1
+    r1 = d.push(np.roll(np.roll(F, sy, 0), sx, 1))
+    assert r0["K"] == st.n
+    assert r1["n_matched"] == r0["K"] == r1["K"]
+    # Phi(p) is the now-label found at p's first site shifted by (sx, sy)
+    lab0 = r0["labels"]
+    for p in range(r0["K"]):
+        first = int(np.flatnonzero(lab0.ravel() == p)[0])
+        y, x = divmod(first, Lx)
+        assert r1["phi"][p] == r1["labels"][(y + sy) % Ly, (x + sx) % Lx]
+    assert r1["breaking"].size == 0 and r1["arising"].size == 0
+
+
+def _disc_label_map(lab, pts):
+    """label -> disc index, by the label at each disc's centre site."""
+    m = {}
+    for i, (x, y) in enumerate(pts):
+        m[int(lab[int(y), int(x)])] = i
+    return m
+
+
+def test_single_t1_flip_matches_bruteforce_delaunay_difference():
+    """A T1 event built by hand: in a jittered triangular packing pick a
+    Delaunay edge (i, k), and squeeze its two opposite droplets j, l toward each
+    other past the cocircular point. Where the brute-force triangulation of the
+    centroids of both frames changes by exactly that one flip (and the digital
+    edge sets equal it in both frames), the oracle must report exactly one
+    breaking link {i, k}, one arising link {j, l}, and four active labels (a
+    bulk T1 conserves coordination)."""
+    rng = np.random.default_rng(7)
+    a, m, n = 12, 6, 4
+    Lx, Ly = a * m, 42
+    K = m * n
+    r = 3.0
+    found = 0
+    for trial in range(40):
+        base = _jittered_triangular(rng, a, m, n, Lx, Ly, jitter=0.8)
+        pts0 = [(p[0] // Q + 0.5, p[1] // Q + 0.5) for p in base]
+        cq0 = [(int(Q * x), int(Q * y)) for x, y in pts0]
+        e_base, _, _, _, _ = periodic_delaunay(cq0, Q * Lx, Q * Ly, 2 * a * Q)
+        i, k = sorted(e_base)[int(rng.integers(len(e_base)))]
+        nb = {}
+        for x, y in e_base:
+            nb.setdefault(x, set()).add(y)
+            nb.setdefault(y, set()).add(x)
+        opp = sorted(nb[i] & nb[k])
+        if len(opp) != 2:
+            continue
+        j, l = opp
+        vx = float(O.wrap(int(Q * (pts0[l][0] - pts0[j][0])), Q * Lx)) / Q
+        vy = float(O.wrap(int(Q * (pts0[l][1] - pts0[j][1])), Q * Ly)) / Q
+        dist = np.hypot(vx, vy)
+        s = rng.uniform(4.5, 5.5)
+        pts1 = list(pts0)
+        pts1[j] = ((int(np.floor(pts0[j][0] + s * vx / dist)) % Lx) + 0.5,
+                   (int(np.floor(pts0[j][1] + s * vy / dist)) % Ly) + 0.5)
+        pts1[l] = ((int(np.floor(pts0[l][0] - s * vx / dist)) % Lx) + 0.5,
+                   (int(np.floor(pts0[l][1] - s * vy / dist)) % Ly) + 0.5)
+        st0 = I.DiscState(Lx, np.array([p[0] for p in pts0]), np.array([p[1] for p in pts0]), np.full(K, r))
+        st1 = I.DiscState(Lx, np.array([p[0] for p in pts1]), np.array([p[1] for p in pts1]), np.full(K, r))
+        d = O.Detector(Lx, Ly, voronoi="brute")
+        ra = d.push(_raster_rect(st0, Lx, Ly))
+        rb = d.push(_raster_rect(st1, Lx, Ly))
+        if ra["K"] != K or rb["K"] != K or rb["n_matched"] != K:
+            continue
+        m0 = _disc_label_map(ra["labels"], pts0)
+        m1 = _disc_label_map(rb["labels"], pts1)
+        if len(m0) != K or len(m1) != K:
+            continue
+        e0, t0, g0, _, _ = periodic_delaunay([tuple(c) for c in ra["centroids"].tolist()], Q * Lx, Q * Ly, 2 * a * Q)
+        e1, t1, g1, _, _ = periodic_delaunay([tuple(c) for c in rb["centroids"].tolist()], Q * Lx, Q * Ly, 2 * a * Q)
+        if len(t0) != 6 * K or len(t1) != 6 * K or min(g0, g1) == 0:
+            continue
+        got0 = set(zip(*[v.tolist() for v in O.split_keys(ra["edges"])]))
+        got1 = set(zip(*[v.tolist() for v in O.split_keys(rb["edges"])]))
+        if got0 != e0 or got1 != e1:
+            continue
+        s0 = {tuple(sorted((m0[x], m0[y]))) for x, y in e0}
+        s1 = {tuple(sorted((m1[x], m1[y]))) for x, y in e1}
+        if s0 - s1 != {(min(i, k), max(i, k))} or s1 - s0 != {(min(j, l), max(j, l))}:
+            continue
+        brk = {tuple(sorted((m1[x], m1[y]))) for x, y in zip(*[v.tolist() for v in O.split_keys(rb["breaking"])])}
+        ari = {tuple(sorted((m1[x], m1[y]))) for x, y in zip(*[v.tolist() for v in O.split_keys(rb["arising"])])}
+        assert brk == s0 - s1 and ari == s1 - s0
+        assert int(rb["active"].sum()) == 4
+        prev = {tuple(sorted((m0[x], m0[y]))) for x, y in zip(*[v.tolist() for v in O.split_keys(rb["breaking_prev"])])}
+        assert prev == s0 - s1
+        found += 1
+        if found >= 2:
+            break
+    assert found >= 1
+
+
+def _raster_rect(st, Lx, Ly):
+    """Disc raster on an Lx x Ly torus (the generator's raster is square-only)."""
+    F = np.zeros((Ly, Lx), np.float32)
+    for cx, cy, r in zip(st.cx, st.cy, st.r):
+        R = int(np.ceil(r)) + 1
+        for dy in range(-R, R + 1):
+            for dx in range(-R, R + 1):
+                x = int(np.floor(cx)) + dx
+                y = int(np.floor(cy)) + dy
+                if (x - cx) ** 2 + (y - cy) ** 2 < r * r:
+                    F[y % Ly, x % Lx] = 1.0
+    return F
+
+
+def test_birth_and_death_are_excluded():
+    L = 64
+    rng = np.random.default_rng(4)
+    pts = [(p[0] // Q + 0.5, p[1] // Q + 0.5) for p in _generic_points(rng, L, 12, min_sep=12)]
+    extra = ((pts[0][0] + 6.0) % L, (pts[0][1] + 6.0) % L)
+    F0 = _disc_field(L, pts, 2.2)
+    F1 = _disc_field(L, pts + [extra], 2.2)
+    for frames, kind in (((F0, F1), "birth"), ((F1, F0), "death")):
+        d = O.Detector(L, L, voronoi="brute")
+        a = d.push(frames[0])
+        b = d.push(frames[1])
+        if kind == "birth":
+            new = int(b["labels"][int(extra[1]), int(extra[0])])
+            assert b["inv"][new] == -1
+            ends = set(O.split_keys(b["breaking"])[0].tolist() + O.split_keys(b["breaking"])[1].tolist()
+                       + O.split_keys(b["arising"])[0].tolist() + O.split_keys(b["arising"])[1].tolist())
+            assert new not in ends
+            assert b["n_matched"] == a["K"]
+        else:
+            gone = int(a["labels"][int(extra[1]), int(extra[0])])
+            assert b["inv"].tolist().count(-1) == 0
+            assert a["K"] - b["n_matched"] == 1
+            assert gone not in [p for p in range(a["K"]) if b["phi"][p] >= 0]
+
+
+def test_merge_keeps_only_the_mutual_best():
+    L = 48
+    F0 = np.zeros((L, L), np.float32)
+    F0[10:14, 10:16] = 1.0      # p0: 24 sites
+    F0[10:14, 17:20] = 1.0      # p1: 12 sites
+    F1 = F0.copy()
+    F1[10:14, 16] = 1.0          # bridge: one bubble
+    d = O.Detector(L, L, voronoi="brute")
+    d.push(F0)
+    b = d.push(F1)
+    assert b["K"] == 1 and b["K_prev"] == 2
+    assert b["phi"].tolist() == [0, -1]
+
+
+def test_overlap_tie_goes_to_smallest_label():
+    # two past labels tie for one now label: the smaller past label wins
+    lab_prev = np.array([[0, 0, 1, 1]], dtype=np.int32)
+    lab_now = np.array([[0, 0, 0, 0]], dtype=np.int32)
+    phi, inv = O.match_overlap(lab_prev, lab_now, 2, 1)
+    assert phi.tolist() == [0, -1] and inv.tolist() == [0]
+    # one past label splits evenly into two now labels: the smaller now label wins
+    phi, inv = O.match_overlap(lab_now, lab_prev, 1, 2)
+    assert phi.tolist() == [0] and inv.tolist() == [0, -1]
+    # a strictly larger overlap beats a smaller label
+    phi, inv = O.match_overlap(np.array([[0, 0, 0, 0, 0]], np.int32),
+                               np.array([[0, 1, 1, 1, -1]], np.int32), 1, 2)
+    assert phi.tolist() == [1] and inv.tolist() == [-1, 0]
