@@ -1,0 +1,318 @@
+#!/usr/bin/env python3
+"""Benchmark of the detect pipeline (Gsites/s) on GB300.
+
+Default workload: 64 frames of a 1024x1024 periodic smoothed-noise lattice
+(sigma 4, threshold 0.5, shear 0.005 per frame + N(0, 0.01)), processed in
+order through vd_push_frame. One step = the whole 64-frame sequence
+(67.1M sites); the 256 MiB of input frames is resident in HBM and larger
+than L2 (129 MB), so every frame is read cold.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line. Multi-GPU (torchrun): every rank runs an independent
+replica on its own GPU (weak scaling, no collective on the data path); the
+time is the max over ranks. ``--impl reference`` times the CPU oracle as it
+stands on the host cores (bounded sample of the same workload).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1607_00908_gb300 import inputs  # noqa: E402
+
+METRIC = "Gsites/s full detect pipeline"
+UNIT = "Gsites/s"
+
+# Algorithmic bytes per site of each pipeline stage:
+#   labelling tiles: field read 4 + foreground bit write 1/8
+#   label pass:      foreground bit read 1/8 + label write 4 + past label read 4
+#   voronoi:         owner write 4
+STAGE_BYTES_PER_SITE = {0: 4.125, 2: 8.125, 3: 4.0}
+PIPELINE_BYTES_PER_SITE = 16.0
+
+
+def workload(name: str, n_frames: int | None):
+    if name == "c1":
+        n = n_frames or 64
+        return "1024x1024 smoothed noise sigma 4, 64 frames (shear 0.005 + N(0,0.01))", list(inputs.workload_c1(1, n))
+    if name == "c0":
+        return "128x128 smoothed noise sigma 3, 2 frames", inputs.workload_c0(1)
+    if name == "c2":
+        n = n_frames or 16
+        return "4096x4096 RSA droplets r~U[8,12], 16 frames (shear 1e-3 + N(0,0.3))", \
+            [F for F, _ in inputs.workload_c2(1, n)]
+    raise SystemExit(f"unknown workload {name}")
+
+
+def read_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "100", "-f", self.path], stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        try:
+            with open(self.path) as f:
+                for line in f:
+                    p = [x.strip() for x in line.split(",")]
+                    if len(p) >= 9:
+                        rows.append(p)
+            os.unlink(self.path)
+        except Exception:
+            pass
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        sm = [num(r[1]) for r in rows if num(r[1]) is not None]
+        mx = max((num(r[2]) for r in rows if num(r[2]) is not None), default=None)
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower().startswith("active")})
+        load = [v for v in sm if mx and v > 0.5 * mx] or sm
+        return {"sm_mhz": statistics.median(load) if load else None, "sm_max_mhz": mx, "reasons": reasons,
+                "samples": len(rows)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def max_over_ranks(x: float, world: int) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world: int):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def cpu_baseline(frames, budget_s: float = 15.0, min_frames: int = 2):
+    """The CPU oracle as it stands, single-threaded, on a bounded sample of the workload."""
+    import oracle
+    Ly, Lx = frames[0].shape
+    det = oracle.Detector(Lx, Ly, workers=1)
+    t0 = time.perf_counter()
+    n = 0
+    for F in frames:
+        det.push(F)
+        n += 1
+        if n >= min_frames and time.perf_counter() - t0 > budget_s:
+            break
+    dt = time.perf_counter() - t0
+    return n * Lx * Ly / dt / 1e9, n, dt
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return
+    desc, frames = workload(args.workload, args.frames)
+    import oracle
+    Ly, Lx = frames[0].shape
+    det = oracle.Detector(Lx, Ly, workers=1)
+    # a step is one frame of the workload through the whole oracle pipeline
+    k = 0
+    for _ in range(args.warmup):
+        det.push(frames[k % len(frames)])
+        k += 1
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        det.push(frames[k % len(frames)])
+        k += 1
+    dt = time.perf_counter() - t0
+    value = args.steps * Lx * Ly / dt / 1e9
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+        "config": {"workload": desc + " (one frame per step)", "l2_policy": "host CPU oracle"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"{args.steps} frames of the workload after {args.warmup} warm-up frames"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, world, rank, local):
+    import torch
+    from paper_1607_00908_gb300 import vd
+
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    vd.lib()
+    desc, frames = workload(args.workload, args.frames)
+    Ly, Lx = frames[0].shape
+    sites_per_step = len(frames) * Lx * Ly
+    s = torch.cuda.Stream()
+    dev = [torch.from_numpy(F).cuda() for F in frames]
+    torch.cuda.synchronize()
+    det = vd.Detector(Lx, Ly, stream=s.cuda_stream)
+
+    def step():
+        for f in dev:
+            det.push(f)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    # ---- headline: device-resident inputs, graph replay per frame ----
+    clocks = Clocks(local)
+    clocks.start()
+    launches0 = det.timing()[2]
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier(world)
+    torch.cuda.synchronize()
+    e0.record(s)
+    for _ in range(args.steps):
+        step()
+    e1.record(s)
+    torch.cuda.synchronize()
+    barrier(world)
+    ms = e0.elapsed_time(e1)
+    clk = clocks.stop()
+    launches = det.timing()[2] - launches0
+    ms_max = max_over_ranks(ms, world)
+    value = world * sites_per_step * args.steps / (ms_max / 1e3) / 1e9
+
+    # ---- roofline: per-stage CUDA events on the library stream, same work ----
+    det.set_timing(True)
+    det.timing()
+    for _ in range(args.steps):
+        step()
+    stage_ms, names, _, _ = det.timing()
+    det.set_timing(False)
+    n_launch = args.steps * len(frames)
+    dom = max(STAGE_BYTES_PER_SITE, key=lambda k: stage_ms[k])
+    avg_ms = stage_ms[dom] / n_launch
+    bytes_per_launch = STAGE_BYTES_PER_SITE[dom] * Lx * Ly
+    peak, peak_kind = read_peaks()
+    achieved = bytes_per_launch / (avg_ms / 1e3) / 1e9
+    roofline = {"bound": "hbm", "kernel": names[dom], "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "peak_kind": peak_kind, "traffic": None,
+                "bytes_per_launch": bytes_per_launch, "avg_launch_ms": avg_ms,
+                "stage_ms_per_frame": {names[k]: stage_ms[k] / n_launch for k in range(len(names))},
+                "pipeline_frac_16B_per_site": value * PIPELINE_BYTES_PER_SITE / peak}
+
+    # ---- end to end through the C ABI with host buffers ----
+    host = [torch.from_numpy(F).pin_memory() for F in frames]
+    e2e_steps = max(1, min(args.steps, 3))
+    d2h = 0
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        for h in host:
+            vd._check(vd.vd_push_frame_host(det.h, h.data_ptr(), Lx), "vd_push_frame_host")
+            ch = det.changes()
+            d2h += 40 + 16 * len(ch["breaking"]) + 8 * len(ch["arising"]) + len(ch["active"])
+    torch.cuda.synchronize()
+    e2e_dt = time.perf_counter() - t0
+    e2e_dt = max_over_ranks(e2e_dt, world)
+    e2e = {"value": world * sites_per_step * e2e_steps / e2e_dt / 1e9, "unit": UNIT,
+           "h2d_bytes_per_step": 4 * sites_per_step, "d2h_bytes_per_step": int(d2h / e2e_steps)}
+
+    if rank == 0:
+        cpu = None
+        if world == 1 and not args.no_cpu_baseline:
+            v, nfr, dt = cpu_baseline(frames)
+            cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                   "sample": f"first {nfr} frames of the workload, {dt:.1f} s single-threaded"}
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+            "config": {"workload": desc, "sites_per_step": sites_per_step, "path": "vd_push_frame per frame",
+                       "l2_policy": "inputs larger than L2 (256 MiB of frames, each read once per step)",
+                       "parallelism": f"replicas x{world}"},
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
+            "gpu_launches": launches,
+        }
+        print(json.dumps(line), flush=True)
+    det.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="c1")
+    ap.add_argument("--frames", type=int, default=None)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    world, rank, local = dist_setup()
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+    else:
+        run_ours(args, world, rank, local)
+
+
+if __name__ == "__main__":
+    main()

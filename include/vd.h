@@ -1,0 +1,167 @@
+/*
+ * vd.h — C ABI of libvd: GPU detection of topological changes in dynamic
+ * centroidal Voronoi diagrams of lattice bubbles (M. Bernaschi, M. Lulli,
+ * M. Sbragaglia, "GPU Based Detection of Topological Changes in Voronoi
+ * Diagrams", arXiv:1607.00908).
+ *
+ * One frame of a periodic 2D scalar field goes through, on the GPU:
+ *   threshold -> periodic connected-component labels     (Section 3.1)
+ *   -> 1/1024-site centre of mass per bubble             (Section 3.1)
+ *   -> exact digital Voronoi colouring of every site     (Section 3.2.1)
+ *   -> Delaunay links from owner changes                 (Section 3.2.2)
+ *   -> label isomorphism with the previous frame         (Section 3.2.3)
+ *   -> breaking / arising links, local and global trigger (Sections 3.2.3-3.2.4)
+ * All arithmetic is integer; results are bit-exact and deterministic.
+ *
+ * Conventions shared by every call:
+ *  - Every function returns vd_status (0 = VD_OK, negative = error). No C++
+ *    exception crosses this boundary.
+ *  - Fields are float32, row-major, Ly rows of Lx values, row stride `pitch`
+ *    in elements (pitch >= Lx), periodic in both axes.
+ *  - Labels are int32 in 0..K-1: the rank of the bubble's smallest linear
+ *    index y*Lx + x; background is -1.
+ *  - Centroids are int32 pairs (cx, cy) in 1/1024 site, in [0, 1024*L).
+ *  - An edge/link key is uint64 (lo << 32) | hi with lo < hi labels.
+ *  - Device work is asynchronous on the stream given at creation. Getters
+ *    synchronise that stream and copy into caller buffers, which may be host
+ *    or device memory (cudaMemcpyDefault).
+ *  - A context is not thread-safe: one host thread drives it at a time.
+ */
+#ifndef VD_H_
+#define VD_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t vd_status;
+enum {
+    VD_OK = 0,
+    VD_ERR_INVALID = -1,   /* bad argument, handle or configuration */
+    VD_ERR_OOM = -2,       /* device allocation failed */
+    VD_ERR_CAPACITY = -3,  /* a caller buffer or a device capacity was too small; counts are filled in */
+    VD_ERR_CUDA = -4,      /* a CUDA runtime call failed */
+    VD_ERR_TIMEOUT = -5,   /* a bounded device-side wait gave up */
+    VD_ERR_STATE = -6,     /* call out of order (e.g. results before any frame) */
+    VD_ERR_UNSUPPORTED = -7
+};
+
+/* Polarity of the spin variable of Section 3.1: a site is in a bubble when
+ * value > threshold (VD_ABOVE) or value < threshold (VD_BELOW, the paper's
+ * density convention). NaN is never in a bubble. */
+enum { VD_ABOVE = 1, VD_BELOW = -1 };
+
+typedef struct vd_config {
+    int32_t Lx, Ly;            /* lattice size, 1 <= Lx, Ly, Lx*Ly < 2^31 */
+    float threshold;           /* bubble threshold */
+    int32_t polarity;          /* VD_ABOVE or VD_BELOW */
+    int32_t connectivity;      /* 4 (only value supported) */
+    int32_t max_components;    /* capacity for bubbles per frame; 0 = ceil(Lx*Ly/2) (cannot overflow) */
+    int32_t max_edges;         /* capacity for links per frame; 0 = 3*max_components + 64 */
+    void* stream;              /* cudaStream_t for all device work; NULL = legacy default stream */
+} vd_config;
+
+/* Fill `cfg` with defaults for an Lx x Ly lattice (threshold 0.5, VD_ABOVE,
+ * 4-connectivity, automatic capacities, default stream). */
+vd_status vd_config_init(vd_config* cfg, int32_t Lx, int32_t Ly);
+
+typedef struct vd_ctx vd_ctx;
+
+/* Create a detector for one periodic lattice. Allocates all resident device
+ * state (two label frames, centroids, links, scratch) on the current device.
+ * `*out` is set on success. Errors: VD_ERR_INVALID (bad cfg), VD_ERR_OOM. */
+vd_status vd_create(const vd_config* cfg, vd_ctx** out);
+
+/* Enqueue one frame (Sections 3.1-3.2.4). `d_field` is a device pointer to
+ * Ly rows of `pitch` floats; it must stay valid until the stream reaches
+ * this work. The previous frame's labels and links stay resident on the
+ * device; the first frame after creation reports no changes. Asynchronous:
+ * device-side capacity overflows are reported by the next getter. */
+vd_status vd_push_frame(vd_ctx* ctx, const float* d_field, size_t pitch);
+
+/* Same as vd_push_frame with a host-memory field: copies it to a context-owned
+ * device buffer on the context stream first (synchronous w.r.t. `h_field`). */
+vd_status vd_push_frame_host(vd_ctx* ctx, const float* h_field, size_t pitch);
+
+/* Result of the last pushed frame (Sections 3.2.3-3.2.4). The caller owns the
+ * arrays and states their capacities; the library always fills the counts and
+ * writes an array only when it fits (else returns VD_ERR_CAPACITY after
+ * writing all counts). `breaking` / `breaking_prev` / `arising` are sorted by
+ * now-key; `breaking_prev[i]` is breaking[i] in past labels. `active` (length
+ * n_now) is the local trigger: 1 for labels at an end of a flip. */
+typedef struct vd_changes {
+    int64_t frame_index;       /* 0-based index of the frame these results belong to */
+    int32_t n_prev, n_now;     /* bubbles in the past and current frame */
+    int32_t n_matched;         /* labels matched by the isomorphism */
+    int32_t n_edges;           /* links of the current frame */
+    int32_t n_breaking, n_arising;
+    int32_t global_trigger;    /* 1 when n_breaking + n_arising > 0 */
+    uint64_t* breaking;        int32_t cap_breaking;
+    uint64_t* breaking_prev;   /* same capacity as breaking; may be NULL */
+    uint64_t* arising;         int32_t cap_arising;
+    uint8_t* active;           int32_t cap_active;   /* may be NULL */
+} vd_changes;
+
+vd_status vd_get_changes(vd_ctx* ctx, vd_changes* out);
+
+/* Parity/introspection getters for the last pushed frame. Each copies into a
+ * caller buffer (host or device) of `cap` elements and sets the element count
+ * in *n; VD_ERR_CAPACITY (buffer untouched) when cap is too small. */
+vd_status vd_get_counts(vd_ctx* ctx, int32_t* K, int32_t* n_edges, int64_t* frame_index);
+vd_status vd_get_labels(vd_ctx* ctx, int32_t* out, int64_t cap, int64_t* n);        /* Ly*Lx, row-major */
+vd_status vd_get_centroids_q10(vd_ctx* ctx, int32_t* out, int64_t cap, int64_t* n); /* K pairs (cx, cy): cap counts int32 */
+vd_status vd_get_owners(vd_ctx* ctx, int32_t* out, int64_t cap, int64_t* n);        /* Ly*Lx Voronoi owners */
+vd_status vd_get_edges(vd_ctx* ctx, uint64_t* out, int64_t cap, int64_t* n);        /* sorted unique keys */
+vd_status vd_get_match(vd_ctx* ctx, int32_t* phi, int64_t cap, int64_t* n);         /* K_prev entries, -1 = unmatched */
+
+/* Stage timing (measurement support, not part of the detect result). When
+ * enabled, every vd_push_frame records CUDA events on the context stream at
+ * the boundaries of the pipeline stages (labelling tiles, bubble merge and
+ * centroids, label pass, Voronoi + links, adjacency/match/flips) and runs
+ * without graph replay. vd_get_timing synchronises the stream and returns
+ * the summed milliseconds per stage since the last call (stage_ms has cap
+ * entries; *n_stages is set), the number of kernels launched and frames
+ * pushed since creation. Names via vd_stage_name. */
+vd_status vd_set_timing(vd_ctx* ctx, int32_t enable);
+vd_status vd_get_timing(vd_ctx* ctx, double* stage_ms, int32_t cap, int32_t* n_stages,
+                        int64_t* n_kernel_launches, int64_t* n_frames);
+const char* vd_stage_name(int32_t stage);
+
+/* Release all device state of the context (waits for its stream first). */
+vd_status vd_destroy(vd_ctx* ctx);
+
+/* Static description of a status code. */
+const char* vd_status_string(vd_status s);
+
+/* ---------------------------------------------------------------------------
+ * Batched form: many independent lattices of uneven size advance one frame
+ * per vd_batch_push. Every pipeline stage runs as one launch over all
+ * instances (work lists of (instance, tile)); the sequence is captured once
+ * into a CUDA graph and replayed.
+ * ------------------------------------------------------------------------- */
+typedef struct vd_batch vd_batch;
+
+/* `cfgs[i]` describes instance i; all share cfgs[0].stream. */
+vd_status vd_batch_create(const vd_config* cfgs, int32_t n, vd_batch** out);
+/* `d_fields` is a HOST array of n device pointers (each Ly*pitch floats,
+ * pitch = Lx); instance i reads d_fields[i]. Enqueues one step. */
+vd_status vd_batch_push(vd_batch* b, const float* const* d_fields);
+/* Advance only the `n_active` instances listed in `active` (host array of
+ * instance ids, each at most once); the others keep their state. */
+vd_status vd_batch_push_subset(vd_batch* b, const int32_t* active, int32_t n_active,
+                               const float* const* d_fields);
+vd_status vd_batch_get_changes(vd_batch* b, int32_t i, vd_changes* out);
+vd_status vd_batch_get_labels(vd_batch* b, int32_t i, int32_t* out, int64_t cap, int64_t* n);
+vd_status vd_batch_get_owners(vd_batch* b, int32_t i, int32_t* out, int64_t cap, int64_t* n);
+vd_status vd_batch_get_edges(vd_batch* b, int32_t i, uint64_t* out, int64_t cap, int64_t* n);
+vd_status vd_batch_get_centroids_q10(vd_batch* b, int32_t i, int32_t* out, int64_t cap, int64_t* n);
+vd_status vd_batch_get_counts(vd_batch* b, int32_t i, int32_t* K, int32_t* n_edges, int64_t* frame_index);
+vd_status vd_batch_destroy(vd_batch* b);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* VD_H_ */

@@ -1,0 +1,728 @@
+// Host side of libvd: the C ABI declared in include/vd.h.
+//
+// A context (vd_ctx) is a batch of one lattice; vd_batch holds many. Both own
+// pooled device buffers laid out by instance (InstDesc offsets), a step table
+// per active set, and enqueue the same kernel sequence on their stream:
+//   begin -> labelling tiles -> border merge -> roots/ranks -> centroids ->
+//   bucket grid -> labels + overlap -> Voronoi + links -> CSR -> match ->
+//   translation -> row comparison -> finish.
+// The batch form captures that sequence once into a CUDA graph per active set
+// size and replays it.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "vd.h"
+#include "vd_internal.cuh"
+
+using namespace vd;
+
+namespace {
+
+long long next_pow2(long long v) {
+    long long p = 1;
+    while (p < v) p <<= 1;
+    return p;
+}
+
+struct DevBuf {
+    std::vector<void*> ptrs;
+    bool ok = true;
+    template <class T>
+    T* alloc(long long n) {
+        if (n <= 0) n = 1;
+        void* p = nullptr;
+        if (cudaMalloc(&p, (size_t)n * sizeof(T)) != cudaSuccess) {
+            ok = false;
+            cudaGetLastError();
+            return nullptr;
+        }
+        ptrs.push_back(p);
+        return static_cast<T*>(p);
+    }
+    void release() {
+        for (void* p : ptrs) cudaFree(p);
+        ptrs.clear();
+    }
+};
+
+struct StepTables {
+    int n_act = 0;
+    int total_tilesA = 0, total_tilesV = 0, total_merge = 0;
+    long long total_words = 0;
+    int* d_act = nullptr;
+    int* d_tileA = nullptr;
+    int* d_tileV = nullptr;
+    int* d_merge = nullptr;
+    long long* d_words = nullptr;
+    long long* d_pre = nullptr;
+};
+
+}  // namespace
+
+struct vd_batch {
+    int n = 0;
+    cudaStream_t s = 0;
+    std::vector<InstDesc> desc;
+    DevBuf mem;
+    Pools P{};
+    StepTables all;               // every instance active
+    StepTables sub;               // scratch table for subsets
+    int grid_items = 0;
+    // field pointer tables (device) and their host mirrors
+    const float** d_fields = nullptr;
+    long long* d_pitches = nullptr;
+    std::vector<const float*> h_fields;
+    std::vector<long long> h_pitches;
+    // host input staging for vd_push_frame_host (instance 0)
+    float* d_host_field = nullptr;
+    // graph of the all-active step
+    cudaGraphExec_t graph = nullptr;
+    bool use_graph = false;
+    long long frames_pushed = 0;
+    long long launches = 0;
+    long long graph_launches = 0;
+    // stage timing
+    bool timing = false;
+    std::vector<cudaEvent_t> ev_pool;
+    int ev_used = 0;
+};
+
+static const int N_STAGES = 5;
+static const char* STAGE_NAMES[N_STAGES] = {
+    "labelling tiles (threshold + tile union-find)",
+    "bubbles (border merge, ranks, centroids, bucket grid)",
+    "label pass + overlap histogram",
+    "voronoi owners + links",
+    "adjacency, match, translation, flips",
+};
+
+struct vd_ctx {
+    vd_batch* b;
+};
+
+namespace {
+
+vd_status cuda_status(cudaError_t e) { return e == cudaSuccess ? VD_OK : VD_ERR_CUDA; }
+
+bool valid_cfg(const vd_config& c) {
+    if (c.Lx < 1 || c.Ly < 1) return false;
+    if (c.Lx >= (1 << 21) || c.Ly >= (1 << 21)) return false;   // 1024*L must fit int32
+    if ((long long)c.Lx * c.Ly >= (1ll << 31)) return false;
+    if (c.connectivity != 4) return false;
+    if (c.polarity != VD_ABOVE && c.polarity != VD_BELOW) return false;
+    if (c.max_components < 0 || c.max_edges < 0) return false;
+    return true;
+}
+
+void build_table(vd_batch* b, const std::vector<int>& act, StepTables& T, bool alloc) {
+    const int n = (int)act.size();
+    std::vector<int> tA(n + 1, 0), tV(n + 1, 0), mg(n + 1, 0);
+    std::vector<long long> wd(n + 1, 0);
+    for (int a = 0; a < n; ++a) {
+        const InstDesc& D = b->desc[act[a]];
+        tA[a + 1] = tA[a] + D.ntx * D.nty;
+        tV[a + 1] = tV[a] + D.vtx * D.vty;
+        mg[a + 1] = mg[a] + D.ntx * D.nty * (TW + TH);
+        wd[a + 1] = wd[a] + (long long)D.Ly * D.wpr;
+    }
+    if (alloc) {
+        T.d_act = b->mem.alloc<int>(b->n);
+        T.d_tileA = b->mem.alloc<int>(b->n + 1);
+        T.d_tileV = b->mem.alloc<int>(b->n + 1);
+        T.d_merge = b->mem.alloc<int>(b->n + 1);
+        T.d_words = b->mem.alloc<long long>(b->n + 1);
+        T.d_pre = b->mem.alloc<long long>((long long)NPRE * (b->n + 1));
+        if (!b->mem.ok) return;
+    }
+    T.n_act = n;
+    T.total_tilesA = tA[n];
+    T.total_tilesV = tV[n];
+    T.total_merge = mg[n];
+    T.total_words = wd[n];
+    cudaMemcpyAsync(T.d_act, act.data(), sizeof(int) * n, cudaMemcpyHostToDevice, b->s);
+    cudaMemcpyAsync(T.d_tileA, tA.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice, b->s);
+    cudaMemcpyAsync(T.d_tileV, tV.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice, b->s);
+    cudaMemcpyAsync(T.d_merge, mg.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice, b->s);
+    cudaMemcpyAsync(T.d_words, wd.data(), sizeof(long long) * (n + 1), cudaMemcpyHostToDevice, b->s);
+}
+
+Launch make_launch(vd_batch* b, const StepTables& T) {
+    Launch L;
+    L.nlaunch = &b->launches;
+    L.s = b->s;
+    L.P = b->P;
+    L.T.n_act = T.n_act;
+    L.T.act = T.d_act;
+    L.T.tileA_pre = T.d_tileA;
+    L.T.tileV_pre = T.d_tileV;
+    L.T.word_pre = T.d_words;
+    L.T.merge_pre = T.d_merge;
+    L.T.pre = T.d_pre;
+    L.grid_items = b->grid_items;
+    L.total_tilesA = T.total_tilesA;
+    L.total_tilesV = T.total_tilesV;
+    L.total_merge = T.total_merge;
+    L.total_words = T.total_words;
+    return L;
+}
+
+cudaEvent_t next_event(vd_batch* b) {
+    if (b->ev_used == (int)b->ev_pool.size()) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+        b->ev_pool.push_back(e);
+    }
+    return b->ev_pool[b->ev_used++];
+}
+
+void mark(vd_batch* b, bool on) {
+    if (!on) return;
+    cudaEvent_t e = next_event(b);
+    if (e) cudaEventRecord(e, b->s);
+}
+
+void enqueue_step(vd_batch* b, const Launch& L, bool timed) {
+    launch_begin(L);
+    mark(b, timed);
+    launch_ccl_tiles(L);
+    mark(b, timed);
+    launch_ccl_rest(L);
+    mark(b, timed);
+    launch_labels(L);
+    mark(b, timed);
+    launch_voronoi(L);
+    mark(b, timed);
+    launch_graph(L);
+    launch_finish(L);
+    mark(b, timed);
+}
+
+vd_status create_batch(const vd_config* cfgs, int n, vd_batch** out) {
+    if (!cfgs || n < 1 || !out) return VD_ERR_INVALID;
+    for (int i = 0; i < n; ++i)
+        if (!valid_cfg(cfgs[i])) return VD_ERR_INVALID;
+    vd_batch* b = new (std::nothrow) vd_batch();
+    if (!b) return VD_ERR_OOM;
+    b->n = n;
+    b->s = (cudaStream_t)cfgs[0].stream;
+    b->desc.resize(n);
+    long long site = 0, word = 0, tile = 0, border = 0, comp = 0, edge = 0, eh = 0, oh = 0, bucket = 0, ovl = 0;
+    long long piece_cap = 0, scan_items = 0;
+    for (int i = 0; i < n; ++i) {
+        const vd_config& c = cfgs[i];
+        InstDesc& D = b->desc[i];
+        memset(&D, 0, sizeof(D));
+        const long long N = (long long)c.Lx * c.Ly;
+        D.Lx = c.Lx;
+        D.Ly = c.Ly;
+        D.thr = c.threshold;
+        D.pol = c.polarity;
+        D.ntx = (c.Lx + TW - 1) / TW;
+        D.nty = (c.Ly + TH - 1) / TH;
+        D.vtx = (c.Lx + VW - 1) / VW;
+        D.vty = (c.Ly + VH - 1) / VH;
+        D.wpr = (c.Lx + 31) / 32;
+        long long kcap = c.max_components ? c.max_components
+                                          : (N <= 65536 ? (N + 1) / 2 : std::max<long long>(N / 8, 65536));
+        kcap = std::min<long long>(kcap, (N + 1) / 2);
+        long long ecap = c.max_edges ? c.max_edges : 3 * kcap + 64;
+        long long ocap = 2 * kcap + 64;
+        D.comp_cap = (int)kcap;
+        D.edge_cap = (int)ecap;
+        D.ovl_cap = (int)ocap;
+        D.ehash_mask = (int)(next_pow2(2 * ecap) - 1);
+        D.ohash_mask = (int)(next_pow2(2 * ocap) - 1);
+        D.bucket_cap = ((c.Lx + 3) / 4) * ((c.Ly + 3) / 4);
+        D.site_off = site;
+        D.word_off = word;
+        D.tile_off = tile;
+        D.border_off = border;
+        D.comp_off = comp;
+        D.edge_off = edge;
+        D.ehash_off = eh;
+        D.ohash_off = oh;
+        D.bucket_off = bucket;
+        D.ovl_off = ovl;
+        const long long ntiles = (long long)D.ntx * D.nty;
+        site += N;
+        word += (long long)c.Ly * D.wpr;
+        tile += ntiles;
+        border += ntiles * BORDER;
+        comp += kcap + 1;
+        edge += ecap;
+        eh += D.ehash_mask + 1ll;
+        oh += D.ohash_mask + 1ll;
+        bucket += D.bucket_cap + 1ll;
+        ovl += ocap;
+        piece_cap += (N <= 65536) ? ntiles * (TSITES / 2) : N / 8 + ntiles * 16;
+        scan_items = std::max(scan_items, (long long)0);
+    }
+    scan_items = std::max(std::max(word, comp), bucket);
+    if (piece_cap >= (1ll << 31) || comp >= (1ll << 31) || edge >= (1ll << 31)) {
+        delete b;
+        return VD_ERR_INVALID;
+    }
+    DevBuf& M = b->mem;
+    Pools& P = b->P;
+    P.desc = M.alloc<InstDesc>(n);
+    P.st = M.alloc<InstState>(n);
+    P.g = M.alloc<Globals>(1);
+    P.labels[0] = M.alloc<int>(site);
+    P.labels[1] = M.alloc<int>(site);
+    P.owners = M.alloc<int>(site);
+    P.fgbits = M.alloc<unsigned>(word);
+    P.rootbits = M.alloc<unsigned>(word);
+    P.rankpre = M.alloc<int>(word);
+    P.tile_pbase = M.alloc<int>(tile);
+    P.tile_pcnt = M.alloc<int>(tile);
+    P.border = M.alloc<int>(border);
+    P.piece_cap = (int)piece_cap;
+    P.p_q = M.alloc<int>(piece_cap);
+    P.p_inst = M.alloc<int>(piece_cap);
+    P.p_n = M.alloc<int>(piece_cap);
+    P.p_su = M.alloc<int>(piece_cap);
+    P.p_sv = M.alloc<int>(piece_cap);
+    P.p_parent = M.alloc<int>(piece_cap);
+    P.p_comp = M.alloc<int>(piece_cap);
+    P.p_accn = M.alloc<long long>(piece_cap);
+    P.p_accx = M.alloc<long long>(piece_cap);
+    P.p_accy = M.alloc<long long>(piece_cap);
+    P.wide = M.alloc<int>(piece_cap);
+    P.cq = M.alloc<int2>(comp);
+    P.comp_root = M.alloc<int>(comp);
+    P.bcnt = M.alloc<int>(bucket);
+    P.boff = M.alloc<int>(bucket);
+    P.bcq = M.alloc<int2>(comp);
+    P.bid = M.alloc<int>(comp);
+    P.best_n = M.alloc<unsigned long long>(comp);
+    P.best_p = M.alloc<unsigned long long>(comp);
+    P.phi = M.alloc<int>(comp);
+    P.inv = M.alloc<int>(comp);
+    P.active = M.alloc<unsigned char>(comp);
+    P.deg = M.alloc<int>(comp);
+    P.rowoff[0] = M.alloc<int>(comp);
+    P.rowoff[1] = M.alloc<int>(comp);
+    P.rowlen[0] = nullptr;
+    P.rowlen[1] = nullptr;
+    P.tdeg = M.alloc<int>(comp);
+    P.trowoff = M.alloc<int>(comp);
+    P.fcnt = M.alloc<int>(comp);
+    P.fcnt_a = M.alloc<int>(comp);
+    P.foff = M.alloc<int>(comp);
+    P.foff_a = M.alloc<int>(comp);
+    P.cols[0] = M.alloc<int>(edge);
+    P.cols[1] = M.alloc<int>(edge);
+    P.tcols = M.alloc<int>(edge);
+    P.ehash = M.alloc<unsigned long long>(eh);
+    P.elist = M.alloc<int>(edge);
+    P.ohash = M.alloc<unsigned long long>(oh);
+    P.oval = M.alloc<unsigned>(oh);
+    P.olist = M.alloc<int>(ovl);
+    P.brk = M.alloc<unsigned long long>(edge);
+    P.brk_prev = M.alloc<unsigned long long>(edge);
+    P.ari = M.alloc<unsigned long long>(edge);
+    P.ekeys = M.alloc<unsigned long long>(edge);
+    P.scan_flag_cap = scan_items / SCAN_TILE + 2;
+    P.scan_flags = M.alloc<unsigned long long>(P.scan_flag_cap);
+    b->d_fields = M.alloc<const float*>(n);
+    b->d_pitches = M.alloc<long long>(n);
+    P.fields = b->d_fields;
+    P.pitches = b->d_pitches;
+    if (!M.ok) {
+        M.release();
+        delete b;
+        return VD_ERR_OOM;
+    }
+    cudaError_t e = cudaSuccess;
+    auto chk = [&](cudaError_t x) { if (e == cudaSuccess) e = x; };
+    chk(cudaMemcpyAsync(P.desc, b->desc.data(), sizeof(InstDesc) * n, cudaMemcpyHostToDevice, b->s));
+    chk(cudaMemsetAsync(P.st, 0, sizeof(InstState) * n, b->s));
+    chk(cudaMemsetAsync(P.g, 0, sizeof(Globals), b->s));
+    chk(cudaMemsetAsync(P.labels[0], 0xff, sizeof(int) * site, b->s));
+    chk(cudaMemsetAsync(P.labels[1], 0xff, sizeof(int) * site, b->s));
+    chk(cudaMemsetAsync(P.rootbits, 0, sizeof(unsigned) * word, b->s));
+    chk(cudaMemsetAsync(P.bcnt, 0, sizeof(int) * bucket, b->s));
+    chk(cudaMemsetAsync(P.deg, 0, sizeof(int) * comp, b->s));
+    chk(cudaMemsetAsync(P.tdeg, 0, sizeof(int) * comp, b->s));
+    chk(cudaMemsetAsync(P.rowoff[0], 0, sizeof(int) * comp, b->s));
+    chk(cudaMemsetAsync(P.rowoff[1], 0, sizeof(int) * comp, b->s));
+    chk(cudaMemsetAsync(P.ehash, 0xff, sizeof(unsigned long long) * eh, b->s));
+    chk(cudaMemsetAsync(P.ohash, 0xff, sizeof(unsigned long long) * oh, b->s));
+    chk(cudaMemsetAsync(P.oval, 0, sizeof(unsigned) * oh, b->s));
+    chk(cudaMemsetAsync(P.scan_flags, 0, sizeof(unsigned long long) * P.scan_flag_cap, b->s));
+    int dev = 0, sms = 152;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    b->grid_items = 2 * sms;
+    std::vector<int> act(n);
+    for (int i = 0; i < n; ++i) act[i] = i;
+    build_table(b, act, b->all, true);
+    build_table(b, act, b->sub, true);
+    b->h_fields.assign(n, nullptr);
+    b->h_pitches.assign(n, 0);
+    if (!M.ok) {
+        M.release();
+        delete b;
+        return VD_ERR_OOM;
+    }
+    chk(cudaStreamSynchronize(b->s));
+    if (e != cudaSuccess) {
+        M.release();
+        delete b;
+        return VD_ERR_CUDA;
+    }
+    *out = b;
+    return VD_OK;
+}
+
+vd_status read_state(vd_batch* b, int i, InstState* st) {
+    if (!b || i < 0 || i >= b->n) return VD_ERR_INVALID;
+    cudaError_t e = cudaStreamSynchronize(b->s);
+    if (e != cudaSuccess) return VD_ERR_CUDA;
+    e = cudaMemcpy(st, b->P.st + i, sizeof(InstState), cudaMemcpyDeviceToHost);
+    return cuda_status(e);
+}
+
+vd_status err_status(const InstState& st) {
+    if (st.err & ERR_TIMEOUT) return VD_ERR_TIMEOUT;
+    if (st.err) return VD_ERR_CAPACITY;
+    return VD_OK;
+}
+
+vd_status push_fields(vd_batch* b, const std::vector<int>& act, const float* const* fields, const long long* pitches) {
+    for (size_t a = 0; a < act.size(); ++a) {
+        if (!fields[a]) return VD_ERR_INVALID;
+        b->h_fields[act[a]] = fields[a];
+        b->h_pitches[act[a]] = pitches[a];
+    }
+    cudaError_t e = cudaMemcpyAsync(b->d_fields, b->h_fields.data(), sizeof(float*) * b->n, cudaMemcpyHostToDevice, b->s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(b->d_pitches, b->h_pitches.data(), sizeof(long long) * b->n, cudaMemcpyHostToDevice, b->s);
+    return cuda_status(e);
+}
+
+vd_status run_all(vd_batch* b) {
+    const Launch L = make_launch(b, b->all);
+    b->frames_pushed += 1;
+    if (b->timing) {
+        enqueue_step(b, L, true);
+        return cuda_status(cudaGetLastError());
+    }
+    if (b->use_graph) {
+        if (!b->graph) {
+            cudaGraph_t g;
+            cudaError_t e = cudaStreamBeginCapture(b->s, cudaStreamCaptureModeThreadLocal);
+            if (e != cudaSuccess) return VD_ERR_CUDA;
+            const long long before = b->launches;
+            enqueue_step(b, L, false);
+            b->graph_launches = b->launches - before;
+            b->launches = before;
+            e = cudaStreamEndCapture(b->s, &g);
+            if (e != cudaSuccess) return VD_ERR_CUDA;
+            e = cudaGraphInstantiate(&b->graph, g, 0);
+            cudaGraphDestroy(g);
+            if (e != cudaSuccess) return VD_ERR_CUDA;
+        }
+        b->launches += b->graph_launches;
+        return cuda_status(cudaGraphLaunch(b->graph, b->s));
+    }
+    enqueue_step(b, L, false);
+    return cuda_status(cudaGetLastError());
+}
+
+vd_status copy_out(void* dst, const void* src, size_t bytes, cudaStream_t s) {
+    if (bytes == 0) return VD_OK;
+    cudaError_t e = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    return cuda_status(e);
+}
+
+vd_status get_changes(vd_batch* b, int i, vd_changes* out) {
+    if (!out) return VD_ERR_INVALID;
+    InstState st;
+    vd_status rs = read_state(b, i, &st);
+    if (rs) return rs;
+    if (st.frame == 0) return VD_ERR_STATE;
+    const InstDesc& D = b->desc[i];
+    out->frame_index = st.frame - 1;
+    out->n_prev = st.rep_K_prev;
+    out->n_now = st.K;
+    out->n_matched = st.n_matched;
+    out->n_edges = st.E;
+    out->n_breaking = st.n_break;
+    out->n_arising = st.n_arise;
+    out->global_trigger = (st.n_break + st.n_arise) > 0;
+    vd_status es = err_status(st);
+    if (es) return es;
+    bool fit = true;
+    if (st.n_break > 0 && (!out->breaking || out->cap_breaking < st.n_break)) fit = false;
+    if (st.n_arise > 0 && (!out->arising || out->cap_arising < st.n_arise)) fit = false;
+    if (out->active && out->cap_active < st.K) fit = false;
+    if (!fit) return VD_ERR_CAPACITY;
+    const size_t u8 = sizeof(unsigned long long);
+    vd_status r = VD_OK;
+    if (st.n_break > 0) {
+        r = copy_out(out->breaking, b->P.brk + D.edge_off, u8 * st.n_break, b->s);
+        if (!r && out->breaking_prev)
+            r = copy_out(out->breaking_prev, b->P.brk_prev + D.edge_off, u8 * st.n_break, b->s);
+    }
+    if (!r && st.n_arise > 0) r = copy_out(out->arising, b->P.ari + D.edge_off, u8 * st.n_arise, b->s);
+    if (!r && out->active && st.K > 0) r = copy_out(out->active, b->P.active + D.comp_off, st.K, b->s);
+    return r;
+}
+
+vd_status get_array(vd_batch* b, int i, int which, void* out, int64_t cap, int64_t* n) {
+    if (!out && cap > 0) return VD_ERR_INVALID;
+    InstState st;
+    vd_status rs = read_state(b, i, &st);
+    if (rs) return rs;
+    if (st.frame == 0) return VD_ERR_STATE;
+    const InstDesc& D = b->desc[i];
+    const long long N = (long long)D.Lx * D.Ly;
+    const int slot = st.slot;   // the frame just finished
+    long long cnt = 0;
+    const void* src = nullptr;
+    size_t esz = 4;
+    switch (which) {
+        case 0: cnt = N; src = b->P.labels[slot] + D.site_off; break;
+        case 1: cnt = N; src = b->P.owners + D.site_off; break;
+        case 2: cnt = 2ll * st.K; src = b->P.cq + D.comp_off; break;
+        case 3: {
+            cnt = st.E;
+            esz = 8;
+            launch_edge_keys(b->s, b->P, i, slot, b->P.ekeys + D.edge_off);
+            src = b->P.ekeys + D.edge_off;
+            break;
+        }
+        case 4: cnt = st.rep_K_prev; src = b->P.phi + D.comp_off; break;
+        default: return VD_ERR_INVALID;
+    }
+    if (n) *n = cnt;
+    vd_status es = err_status(st);
+    if (es) return es;
+    if (cap < cnt) return VD_ERR_CAPACITY;
+    return copy_out(out, src, (size_t)cnt * esz, b->s);
+}
+
+}  // namespace
+
+extern "C" {
+
+vd_status vd_config_init(vd_config* cfg, int32_t Lx, int32_t Ly) {
+    if (!cfg) return VD_ERR_INVALID;
+    memset(cfg, 0, sizeof(*cfg));
+    cfg->Lx = Lx;
+    cfg->Ly = Ly;
+    cfg->threshold = 0.5f;
+    cfg->polarity = VD_ABOVE;
+    cfg->connectivity = 4;
+    return VD_OK;
+}
+
+const char* vd_status_string(vd_status s) {
+    switch (s) {
+        case VD_OK: return "ok";
+        case VD_ERR_INVALID: return "invalid argument";
+        case VD_ERR_OOM: return "device allocation failed";
+        case VD_ERR_CAPACITY: return "capacity exceeded";
+        case VD_ERR_CUDA: return "CUDA runtime error";
+        case VD_ERR_TIMEOUT: return "bounded device wait expired";
+        case VD_ERR_STATE: return "call out of order";
+        case VD_ERR_UNSUPPORTED: return "unsupported";
+        default: return "unknown status";
+    }
+}
+
+vd_status vd_create(const vd_config* cfg, vd_ctx** out) {
+    if (!cfg || !out) return VD_ERR_INVALID;
+    vd_batch* b = nullptr;
+    vd_status r = create_batch(cfg, 1, &b);
+    if (r) return r;
+    // graph replay needs a capturable stream (not the legacy default stream)
+    b->use_graph = (cfg->stream != nullptr) && !getenv("VD_NO_GRAPH");
+    vd_ctx* c = new (std::nothrow) vd_ctx();
+    if (!c) {
+        b->mem.release();
+        delete b;
+        return VD_ERR_OOM;
+    }
+    c->b = b;
+    *out = c;
+    return VD_OK;
+}
+
+vd_status vd_push_frame(vd_ctx* ctx, const float* d_field, size_t pitch) {
+    if (!ctx || !d_field) return VD_ERR_INVALID;
+    vd_batch* b = ctx->b;
+    if ((long long)pitch < b->desc[0].Lx) return VD_ERR_INVALID;
+    const long long p = (long long)pitch;
+    std::vector<int> act{0};
+    vd_status r = push_fields(b, act, &d_field, &p);
+    if (r) return r;
+    return run_all(b);
+}
+
+vd_status vd_push_frame_host(vd_ctx* ctx, const float* h_field, size_t pitch) {
+    if (!ctx || !h_field) return VD_ERR_INVALID;
+    vd_batch* b = ctx->b;
+    const InstDesc& D = b->desc[0];
+    if ((long long)pitch < D.Lx) return VD_ERR_INVALID;
+    if (!b->d_host_field) {
+        b->d_host_field = b->mem.alloc<float>((long long)D.Lx * D.Ly);
+        if (!b->mem.ok) return VD_ERR_OOM;
+    }
+    cudaError_t e = cudaMemcpy2DAsync(b->d_host_field, sizeof(float) * D.Lx, h_field, sizeof(float) * pitch,
+                                      sizeof(float) * D.Lx, D.Ly, cudaMemcpyHostToDevice, b->s);
+    if (e != cudaSuccess) return VD_ERR_CUDA;
+    return vd_push_frame(ctx, b->d_host_field, D.Lx);
+}
+
+vd_status vd_get_changes(vd_ctx* ctx, vd_changes* out) { return ctx ? get_changes(ctx->b, 0, out) : VD_ERR_INVALID; }
+
+vd_status vd_get_counts(vd_ctx* ctx, int32_t* K, int32_t* n_edges, int64_t* frame_index) {
+    if (!ctx) return VD_ERR_INVALID;
+    return vd_batch_get_counts(ctx->b, 0, K, n_edges, frame_index);
+}
+vd_status vd_get_labels(vd_ctx* ctx, int32_t* out, int64_t cap, int64_t* n) {
+    return ctx ? get_array(ctx->b, 0, 0, out, cap, n) : VD_ERR_INVALID;
+}
+vd_status vd_get_owners(vd_ctx* ctx, int32_t* out, int64_t cap, int64_t* n) {
+    return ctx ? get_array(ctx->b, 0, 1, out, cap, n) : VD_ERR_INVALID;
+}
+vd_status vd_get_centroids_q10(vd_ctx* ctx, int32_t* out, int64_t cap, int64_t* n) {
+    return ctx ? get_array(ctx->b, 0, 2, out, cap, n) : VD_ERR_INVALID;
+}
+vd_status vd_get_edges(vd_ctx* ctx, uint64_t* out, int64_t cap, int64_t* n) {
+    return ctx ? get_array(ctx->b, 0, 3, out, cap, n) : VD_ERR_INVALID;
+}
+vd_status vd_get_match(vd_ctx* ctx, int32_t* phi, int64_t cap, int64_t* n) {
+    return ctx ? get_array(ctx->b, 0, 4, phi, cap, n) : VD_ERR_INVALID;
+}
+
+vd_status vd_set_timing(vd_ctx* ctx, int32_t enable) {
+    if (!ctx) return VD_ERR_INVALID;
+    ctx->b->timing = enable != 0;
+    return VD_OK;
+}
+
+vd_status vd_get_timing(vd_ctx* ctx, double* stage_ms, int32_t cap, int32_t* n_stages,
+                        int64_t* n_kernel_launches, int64_t* n_frames) {
+    if (!ctx) return VD_ERR_INVALID;
+    vd_batch* b = ctx->b;
+    if (cudaStreamSynchronize(b->s) != cudaSuccess) return VD_ERR_CUDA;
+    if (n_stages) *n_stages = N_STAGES;
+    if (n_kernel_launches) *n_kernel_launches = b->launches;
+    if (n_frames) *n_frames = b->frames_pushed;
+    double acc[N_STAGES] = {0, 0, 0, 0, 0};
+    const int per = N_STAGES + 1;
+    for (int g = 0; g + per <= b->ev_used; g += per) {
+        for (int k = 0; k < N_STAGES; ++k) {
+            float ms = 0.f;
+            if (cudaEventElapsedTime(&ms, b->ev_pool[g + k], b->ev_pool[g + k + 1]) == cudaSuccess) acc[k] += ms;
+        }
+    }
+    b->ev_used = 0;
+    if (stage_ms) {
+        if (cap < N_STAGES) return VD_ERR_CAPACITY;
+        for (int k = 0; k < N_STAGES; ++k) stage_ms[k] = acc[k];
+    }
+    return VD_OK;
+}
+
+const char* vd_stage_name(int32_t stage) {
+    if (stage < 0 || stage >= N_STAGES) return "";
+    return STAGE_NAMES[stage];
+}
+
+vd_status vd_destroy(vd_ctx* ctx) {
+    if (!ctx) return VD_ERR_INVALID;
+    vd_status r = vd_batch_destroy(ctx->b);
+    delete ctx;
+    return r;
+}
+
+vd_status vd_batch_create(const vd_config* cfgs, int32_t n, vd_batch** out) {
+    vd_status r = create_batch(cfgs, n, out);
+    if (!r) (*out)->use_graph = true;
+    return r;
+}
+
+vd_status vd_batch_push(vd_batch* b, const float* const* d_fields) {
+    if (!b || !d_fields) return VD_ERR_INVALID;
+    std::vector<int> act(b->n);
+    std::vector<long long> pitch(b->n);
+    for (int i = 0; i < b->n; ++i) {
+        act[i] = i;
+        pitch[i] = b->desc[i].Lx;
+    }
+    vd_status r = push_fields(b, act, d_fields, pitch.data());
+    if (r) return r;
+    return run_all(b);
+}
+
+vd_status vd_batch_push_subset(vd_batch* b, const int32_t* active, int32_t n_active, const float* const* d_fields) {
+    if (!b || !active || !d_fields || n_active < 0 || n_active > b->n) return VD_ERR_INVALID;
+    if (n_active == 0) return VD_OK;
+    std::vector<int> act(active, active + n_active);
+    std::vector<char> seen(b->n, 0);
+    std::vector<long long> pitch(n_active);
+    for (int a = 0; a < n_active; ++a) {
+        if (act[a] < 0 || act[a] >= b->n || seen[act[a]]) return VD_ERR_INVALID;
+        seen[act[a]] = 1;
+        pitch[a] = b->desc[act[a]].Lx;
+    }
+    if (n_active == b->n) {
+        bool ordered = true;
+        for (int a = 0; a < n_active; ++a) ordered &= (act[a] == a);
+        if (ordered) return vd_batch_push(b, d_fields);
+    }
+    vd_status r = push_fields(b, act, d_fields, pitch.data());
+    if (r) return r;
+    build_table(b, act, b->sub, false);
+    enqueue_step(b, make_launch(b, b->sub), false);
+    b->frames_pushed += 1;
+    return cuda_status(cudaGetLastError());
+}
+
+vd_status vd_batch_get_changes(vd_batch* b, int32_t i, vd_changes* out) { return get_changes(b, i, out); }
+vd_status vd_batch_get_labels(vd_batch* b, int32_t i, int32_t* out, int64_t cap, int64_t* n) {
+    return get_array(b, i, 0, out, cap, n);
+}
+vd_status vd_batch_get_owners(vd_batch* b, int32_t i, int32_t* out, int64_t cap, int64_t* n) {
+    return get_array(b, i, 1, out, cap, n);
+}
+vd_status vd_batch_get_centroids_q10(vd_batch* b, int32_t i, int32_t* out, int64_t cap, int64_t* n) {
+    return get_array(b, i, 2, out, cap, n);
+}
+vd_status vd_batch_get_edges(vd_batch* b, int32_t i, uint64_t* out, int64_t cap, int64_t* n) {
+    return get_array(b, i, 3, out, cap, n);
+}
+
+vd_status vd_batch_get_counts(vd_batch* b, int32_t i, int32_t* K, int32_t* n_edges, int64_t* frame_index) {
+    InstState st;
+    vd_status r = read_state(b, i, &st);
+    if (r) return r;
+    if (K) *K = st.K;
+    if (n_edges) *n_edges = st.E;
+    if (frame_index) *frame_index = st.frame - 1;
+    return err_status(st);
+}
+
+vd_status vd_batch_destroy(vd_batch* b) {
+    if (!b) return VD_ERR_INVALID;
+    cudaStreamSynchronize(b->s);
+    if (b->graph) cudaGraphExecDestroy(b->graph);
+    for (cudaEvent_t e : b->ev_pool) cudaEventDestroy(e);
+    b->mem.release();
+    delete b;
+    return VD_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,340 @@
+// Adjacency lists, isomorphism and topology changes (Sections 3.2.2-3.2.4).
+//
+// Links of a frame are kept as a CSR adjacency list: row a holds the labels
+// b > a linked to a, sorted (the paper's compressed adjacency matrix). The
+// isomorphism Phi between past and now labels is the mutual best overlap. The
+// past list is translated into now labels and re-sorted (the paper's
+// "translation"), then one thread per now-label row compares the translated
+// past row with the now row: entries only in the past row are breaking links,
+// entries only in the now row are arising links. Labels outside Phi's domain
+// or image are excluded, as the paper does for appearing and vanishing
+// bubbles. Row-by-row output keeps both lists sorted by now-key.
+#include "vd_internal.cuh"
+
+namespace vd {
+
+template <class F>
+__device__ __forceinline__ void for_items(const StepTable& T, int which, F f) {
+    const long long* pre = pre_arr(T, which);
+    const long long total = pre[T.n_act];
+    for (long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x; g < total;
+         g += (long long)gridDim.x * blockDim.x) {
+        const int a = seg_of(pre, T.n_act, g);
+        f(T.act[a], g - pre[a]);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// step begin / finish
+// ---------------------------------------------------------------------------
+__global__ void k_step_begin(Pools P, StepTable T) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        P.g->n_pieces = 0;
+        P.g->n_wide = 0;
+    }
+    for (int a = blockIdx.x * blockDim.x + threadIdx.x; a < T.n_act; a += gridDim.x * blockDim.x) {
+        const int inst = T.act[a];
+        InstState& S = P.st[inst];
+        S.field = P.fields[inst];
+        S.pitch = P.pitches[inst];
+        S.K = 0;
+        S.E = 0;
+        S.n_matched = 0;
+        S.n_break = 0;
+        S.n_arise = 0;
+        S.n_wide = 0;
+        S.n_ovl = 0;
+        S.n_edge_list = 0;
+        S.n_tedges = 0;
+        S.err = 0;
+    }
+}
+
+__global__ void k_step_finish(Pools P, StepTable T) {
+    for (int a = blockIdx.x * blockDim.x + threadIdx.x; a < T.n_act; a += gridDim.x * blockDim.x) {
+        const int inst = T.act[a];
+        InstState& S = P.st[inst];
+        S.err |= P.g->err;
+        const int ecap = P.desc[inst].edge_cap;
+        S.E = S.n_edge_list < ecap ? S.n_edge_list : ecap;
+        S.rep_K_prev = S.has_prev ? S.K_prev : 0;
+        S.K_prev = S.K;
+        S.E_prev = S.E;
+        S.slot ^= 1;
+        // a frame whose device capacities overflowed is not used as a past frame
+        S.has_prev = S.err ? 0 : 1;
+        S.frame += 1;
+    }
+}
+
+// sorted link keys of one instance's frame in `slot`
+__global__ void k_edge_keys(Pools P, int inst, int slot, unsigned long long* out) {
+    const InstDesc& D = P.desc[inst];
+    const InstState& S = P.st[inst];
+    const int K = min(S.K_prev, D.comp_cap);   // after finish, K_prev holds this frame's K
+    const int* ro = P.rowoff[slot] + D.comp_off;
+    const int* cl = P.cols[slot] + D.edge_off;
+    for (int a = blockIdx.x * blockDim.x + threadIdx.x; a < K; a += gridDim.x * blockDim.x) {
+        const int s = min(ro[a], D.edge_cap), e = min(ro[a + 1], D.edge_cap);
+        for (int k = s; k < e; ++k) out[k] = edge_key(a, cl[k]);
+    }
+}
+
+void launch_edge_keys(cudaStream_t s, const Pools& P, int inst, int slot, unsigned long long* out) {
+    k_edge_keys<<<64, 256, 0, s>>>(P, inst, slot, out);
+}
+
+// ---------------------------------------------------------------------------
+// CSR of the now links
+// ---------------------------------------------------------------------------
+__global__ void k_csr_scatter(Pools P, StepTable T) {
+    for_items(T, PRE_E, [&](int inst, long long j) {
+        const InstDesc& D = P.desc[inst];
+        if (j >= D.edge_cap) return;
+        const int now = P.st[inst].slot ^ 1;
+        const int slot = P.elist[D.edge_off + j];
+        unsigned long long* H = P.ehash + D.ehash_off;
+        const unsigned long long key = H[slot];
+        H[slot] = EMPTY_KEY;
+        const int lo = (int)(key >> 32), hi = (int)(key & 0xffffffffu);
+        const int pos = P.rowoff[now][D.comp_off + lo] + atomicSub(&P.deg[D.comp_off + lo], 1) - 1;
+        if (pos < D.edge_cap) P.cols[now][D.edge_off + pos] = hi;
+    });
+}
+
+__device__ __forceinline__ void sort_small(int* v, int n) {
+    for (int i = 1; i < n; ++i) {
+        const int x = v[i];
+        int j = i - 1;
+        while (j >= 0 && v[j] > x) {
+            v[j + 1] = v[j];
+            --j;
+        }
+        v[j + 1] = x;
+    }
+}
+
+__global__ void k_csr_sort(Pools P, StepTable T) {
+    for_items(T, PRE_K, [&](int inst, long long a) {
+        const InstDesc& D = P.desc[inst];
+        const int now = P.st[inst].slot ^ 1;
+        const int* ro = P.rowoff[now] + D.comp_off;
+        const int s = min(ro[a], D.edge_cap), e = min(ro[a + 1], D.edge_cap);
+        sort_small(P.cols[now] + D.edge_off + s, e - s);
+    });
+}
+
+// ---------------------------------------------------------------------------
+// isomorphism Phi by mutual best overlap
+// ---------------------------------------------------------------------------
+__global__ void k_match_init(Pools P, StepTable T) {
+    for_items(T, PRE_KP, [&](int inst, long long p) {
+        P.best_n[P.desc[inst].comp_off + p] = 0ull;
+    });
+    for_items(T, PRE_K, [&](int inst, long long n) {
+        const long long o = P.desc[inst].comp_off + n;
+        P.best_p[o] = 0ull;
+        P.inv[o] = -1;
+        P.active[o] = 0;
+    });
+}
+
+// pack (count, label) so that atomicMax picks the largest count, then the smallest label
+__device__ __forceinline__ unsigned long long pack_best(unsigned cnt, int label) {
+    return ((unsigned long long)cnt << 32) | (0xffffffffu - (unsigned)label);
+}
+__device__ __forceinline__ int unpack_label(unsigned long long v) {
+    return (int)(0xffffffffu - (unsigned)(v & 0xffffffffu));
+}
+
+__global__ void k_match_best(Pools P, StepTable T) {
+    for_items(T, PRE_O, [&](int inst, long long j) {
+        const InstDesc& D = P.desc[inst];
+        const int slot = P.olist[D.ovl_off + j];
+        unsigned long long* H = P.ohash + D.ohash_off;
+        unsigned* V = P.oval + D.ohash_off;
+        const unsigned long long key = H[slot];
+        const unsigned cnt = V[slot];
+        H[slot] = EMPTY_KEY;
+        V[slot] = 0;
+        const int p = (int)(key >> 32), n = (int)(key & 0xffffffffu);
+        if (p < 0 || n < 0 || p >= D.comp_cap || n >= D.comp_cap) return;   // only after an overflow
+        atomicMax(&P.best_n[D.comp_off + p], pack_best(cnt, n));
+        atomicMax(&P.best_p[D.comp_off + n], pack_best(cnt, p));
+    });
+}
+
+__global__ void k_match_phi(Pools P, StepTable T) {
+    for_items(T, PRE_KP, [&](int inst, long long p) {
+        const InstDesc& D = P.desc[inst];
+        const unsigned long long v = P.best_n[D.comp_off + p];
+        int res = -1;
+        if (v != 0ull) {
+            const int n = unpack_label(v);
+            const unsigned long long w = P.best_p[D.comp_off + n];
+            if (w != 0ull && unpack_label(w) == (int)p) {
+                res = n;
+                P.inv[D.comp_off + n] = (int)p;
+                atomicAdd(&P.st[inst].n_matched, 1);
+            }
+        }
+        P.phi[D.comp_off + p] = res;
+    });
+}
+
+// ---------------------------------------------------------------------------
+// translation of the past links into now labels, then a sorted CSR of them
+// ---------------------------------------------------------------------------
+__global__ void k_translate_count(Pools P, StepTable T) {
+    for_items(T, PRE_KP, [&](int inst, long long a) {
+        const InstDesc& D = P.desc[inst];
+        const int prev = P.st[inst].slot;
+        const int pa = P.phi[D.comp_off + a];
+        if (pa < 0) return;
+        const int* ro = P.rowoff[prev] + D.comp_off;
+        const int* cl = P.cols[prev] + D.edge_off;
+        int cnt = 0;
+        for (int k = ro[a]; k < ro[a + 1]; ++k) {
+            const int pb = P.phi[D.comp_off + cl[k]];
+            if (pb < 0) continue;
+            atomicAdd(&P.tdeg[D.comp_off + min(pa, pb)], 1);
+            ++cnt;
+        }
+        if (cnt) atomicAdd(&P.st[inst].n_tedges, cnt);
+    });
+}
+
+__global__ void k_translate_scatter(Pools P, StepTable T) {
+    for_items(T, PRE_KP, [&](int inst, long long a) {
+        const InstDesc& D = P.desc[inst];
+        const int prev = P.st[inst].slot;
+        const int pa = P.phi[D.comp_off + a];
+        if (pa < 0) return;
+        const int* ro = P.rowoff[prev] + D.comp_off;
+        const int* cl = P.cols[prev] + D.edge_off;
+        for (int k = ro[a]; k < ro[a + 1]; ++k) {
+            const int pb = P.phi[D.comp_off + cl[k]];
+            if (pb < 0) continue;
+            const int lo = min(pa, pb), hi = max(pa, pb);
+            const int pos = P.trowoff[D.comp_off + lo] + atomicSub(&P.tdeg[D.comp_off + lo], 1) - 1;
+            if (pos < D.edge_cap) P.tcols[D.edge_off + pos] = hi;
+        }
+    });
+}
+
+__global__ void k_tcsr_sort(Pools P, StepTable T) {
+    for_items(T, PRE_K, [&](int inst, long long a) {
+        const InstDesc& D = P.desc[inst];
+        const int* ro = P.trowoff + D.comp_off;
+        const int s = ro[a], e = ro[a + 1];
+        sort_small(P.tcols + D.edge_off + s, e - s);
+    });
+}
+
+// ---------------------------------------------------------------------------
+// row comparison: breaking = translated past only, arising = now only
+// ---------------------------------------------------------------------------
+template <bool WRITE>
+__device__ __forceinline__ void compare_row(const Pools& P, int inst, int a) {
+    const InstDesc& D = P.desc[inst];
+    const int now = P.st[inst].slot ^ 1;
+    const long long co = D.comp_off;
+    int nb = 0, na = 0;
+    int ob = 0, oa = 0;
+    if (WRITE) {
+        ob = P.foff[co + a];
+        oa = P.foff_a[co + a];
+    }
+    const int ia = P.inv[co + a];
+    if (ia >= 0) {
+        const int* nr = P.cols[now] + D.edge_off;
+        int i = min(P.rowoff[now][co + a], D.edge_cap);
+        const int ie = min(P.rowoff[now][co + a + 1], D.edge_cap);
+        const int* tr = P.tcols + D.edge_off;
+        int j = min(P.trowoff[co + a], D.edge_cap);
+        const int je = min(P.trowoff[co + a + 1], D.edge_cap);
+        for (;;) {
+            // next now-entry whose other end is matched
+            while (i < ie && (nr[i] >= D.comp_cap || P.inv[co + nr[i]] < 0)) ++i;
+            const bool hn = i < ie, ht = j < je;
+            if (!hn && !ht) break;
+            const int vn = hn ? nr[i] : INT_MAX, vt = ht ? tr[j] : INT_MAX;
+            if ((hn && vn >= D.comp_cap) || (ht && vt >= D.comp_cap)) break;   // only after an overflow
+            if (vn == vt) {
+                ++i;
+                ++j;
+            } else if (vt < vn) {   // only in the past: breaking
+                if (WRITE) {
+                    const long long o = D.edge_off + ob + nb;
+                    P.brk[o] = edge_key(a, vt);
+                    P.brk_prev[o] = edge_key(ia, P.inv[co + vt]);
+                    P.active[co + a] = 1;
+                    P.active[co + vt] = 1;
+                }
+                ++nb;
+                ++j;
+            } else {                // only now: arising
+                if (WRITE) {
+                    P.ari[D.edge_off + oa + na] = edge_key(a, vn);
+                    P.active[co + a] = 1;
+                    P.active[co + vn] = 1;
+                }
+                ++na;
+                ++i;
+            }
+        }
+    }
+    if (!WRITE) {
+        P.fcnt[co + a] = nb;
+        P.fcnt_a[co + a] = na;
+        if (nb) atomicAdd(&P.st[inst].n_break, nb);
+        if (na) atomicAdd(&P.st[inst].n_arise, na);
+    }
+}
+
+__global__ void k_flip_count(Pools P, StepTable T) {
+    for_items(T, PRE_K, [&](int inst, long long a) { compare_row<false>(P, inst, (int)a); });
+}
+
+__global__ void k_flip_write(Pools P, StepTable T) {
+    for_items(T, PRE_K, [&](int inst, long long a) { compare_row<true>(P, inst, (int)a); });
+}
+
+void launch_graph(const Launch& L) {
+    const int g = L.grid_items;
+    launch_scan(L, SCAN_DEG);
+    k_csr_scatter<<<g, 256, 0, L.s>>>(L.P, L.T);
+    ++*L.nlaunch;
+    k_csr_sort<<<g, 256, 0, L.s>>>(L.P, L.T);
+    ++*L.nlaunch;
+    k_match_init<<<g, 256, 0, L.s>>>(L.P, L.T);
+    ++*L.nlaunch;
+    k_match_best<<<g, 256, 0, L.s>>>(L.P, L.T);
+    ++*L.nlaunch;
+    k_match_phi<<<g, 256, 0, L.s>>>(L.P, L.T);
+    ++*L.nlaunch;
+    k_translate_count<<<g, 256, 0, L.s>>>(L.P, L.T);
+    ++*L.nlaunch;
+    launch_scan(L, SCAN_TDEG);
+    k_translate_scatter<<<g, 256, 0, L.s>>>(L.P, L.T);
+    ++*L.nlaunch;
+    k_tcsr_sort<<<g, 256, 0, L.s>>>(L.P, L.T);
+    ++*L.nlaunch;
+    k_flip_count<<<g, 256, 0, L.s>>>(L.P, L.T);
+    ++*L.nlaunch;
+    launch_scan(L, SCAN_FLIPS);
+    launch_scan(L, SCAN_FLIPS_A);
+    k_flip_write<<<g, 256, 0, L.s>>>(L.P, L.T);
+    ++*L.nlaunch;
+}
+
+void launch_begin(const Launch& L) {
+    k_step_begin<<<1, 256, 0, L.s>>>(L.P, L.T);
+    ++*L.nlaunch;
+}
+void launch_finish(const Launch& L) {
+    k_step_finish<<<1, 256, 0, L.s>>>(L.P, L.T);
+    ++*L.nlaunch;
+}
+
+}  // namespace vd

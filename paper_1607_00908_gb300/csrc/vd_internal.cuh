@@ -1,0 +1,303 @@
+// Internal data structures and device helpers of libvd.
+//
+// Every context is a batch of independent lattices ("instances"); the plain
+// single-lattice context is a batch of one. Per-instance arrays live in pooled
+// device buffers at fixed per-instance offsets; per-frame scratch that holds
+// a variable number of items (pieces of bubbles inside tiles) comes from one
+// pool shared by all instances of a step. Kernels take a step table that maps
+// their block or item index to (instance, local index).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <climits>
+#include <stdint.h>
+
+namespace vd {
+
+// ---------------------------------------------------------------------------
+// Tiling
+// ---------------------------------------------------------------------------
+constexpr int TW = 64;          // labelling tile width  (sites)
+constexpr int TH = 32;          // labelling tile height (sites)
+constexpr int TSITES = TW * TH; // 2048
+constexpr int TTHREADS = 256;   // 8 threads per tile row, 8 sites each
+constexpr int BORDER = 2 * (TW + TH);   // left col, right col, top row, bottom row
+
+constexpr int VW = 32;          // Voronoi tile width
+constexpr int VH = 32;          // Voronoi tile height
+constexpr int VTHREADS = 256;
+constexpr int VCAND = 1024;     // candidate slots per Voronoi tile (overflow -> slow path)
+constexpr int VEDGESET = 512;   // shared-memory link set per Voronoi tile
+
+constexpr int Q = 1024;         // centroid fixed point: 1/1024 site
+
+constexpr unsigned long long EMPTY_KEY = ~0ull;
+
+// error bits in InstState::err and Globals::err
+enum : int {
+    ERR_EDGE_CAP = 1,       // link hash or list overflow
+    ERR_OVL_CAP = 2,        // overlap hash overflow
+    ERR_PIECE_CAP = 4,      // tile-piece pool overflow
+    ERR_COMP_CAP = 8,       // more bubbles than max_components
+    ERR_TIMEOUT = 16,       // bounded device wait expired
+    ERR_FLIP_CAP = 32,
+};
+
+// ---------------------------------------------------------------------------
+// Static per-instance description (written once at creation)
+// ---------------------------------------------------------------------------
+struct InstDesc {
+    int Lx, Ly;
+    float thr;
+    int pol;
+    int ntx, nty;            // labelling tiles
+    int vtx, vty;            // Voronoi tiles
+    int wpr;                 // 32-bit bitmask words per lattice row
+    int pad0;
+    long long site_off;      // labels / owners pools
+    long long word_off;      // fg-bit / root-bit / rank pools (Ly * wpr words)
+    long long tile_off;      // per-labelling-tile pools (tile piece base/count)
+    long long border_off;    // border pool (ntx*nty*BORDER)
+    long long comp_off;      // per-bubble pools (comp_cap entries, +1 for offsets)
+    long long edge_off;      // per-link pools (edge_cap entries)
+    long long ehash_off;     // link hash (ehash_mask+1 slots)
+    long long ohash_off;     // overlap hash (ohash_mask+1 slots)
+    long long bucket_off;    // bucket grid pools (bucket_cap+1)
+    long long ovl_off;       // overlap occupancy list (ovl_cap)
+    int comp_cap, edge_cap;
+    int ehash_mask, ohash_mask;
+    int bucket_cap, ovl_cap;
+};
+
+// ---------------------------------------------------------------------------
+// Dynamic per-instance state (device memory)
+// ---------------------------------------------------------------------------
+struct InstState {
+    const float* field;      // this step's input
+    long long pitch;
+    int slot;                // pools of the previous frame are at index `slot`, now = slot ^ 1
+    int has_prev;            // a previous frame exists
+    long long frame;         // index of the frame in progress / last finished
+    int K, K_prev;           // bubbles now / previous frame
+    int E, E_prev;           // links now / previous frame
+    int B, nbx, nby;         // bucket grid
+    int n_matched;
+    int n_break, n_arise;
+    int n_wide;
+    int n_ovl;               // overlap pairs this frame
+    int n_edge_list;         // unique links inserted in the hash (= E)
+    int n_tedges;            // translated past links
+    int err;
+    int rep_K_prev;          // bubbles of the past frame used by the last step
+    int pad1;
+};
+
+// per-step global counters
+struct Globals {
+    int n_pieces;
+    int n_wide;
+    int err;
+    unsigned scan_epoch;     // bumped before every scan; tags look-back flags
+    int scan_ticket;         // dynamic tile index of the running scan
+    int pad[3];
+};
+
+// ---------------------------------------------------------------------------
+// Device pools
+// ---------------------------------------------------------------------------
+struct Pools {
+    InstDesc* desc;
+    InstState* st;
+    Globals* g;
+    // sites
+    int* labels[2];
+    int* owners;
+    // bitmask words
+    unsigned* fgbits;
+    unsigned* rootbits;
+    int* rankpre;            // global exclusive prefix per word (this step)
+    // labelling tiles
+    int* tile_pbase;         // first piece index of the tile in the piece pool
+    int* tile_pcnt;          // number of pieces of the tile
+    int* border;
+    // pieces (bubble fragments inside one labelling tile)
+    int piece_cap;
+    int* p_q;                // linear index of the piece's first site
+    int* p_inst;
+    int* p_n;
+    int* p_su;               // sum of (x - x_q) over the piece
+    int* p_sv;               // sum of (y - y_q)
+    int* p_parent;           // union-find over pieces (root = piece with smallest q)
+    int* p_comp;             // bubble id (valid after ranking)
+    long long* p_accn;
+    long long* p_accx;
+    long long* p_accy;
+    int* wide;               // pieces whose sums need the exact per-site path
+    // bubbles
+    int2* cq;                // centroids (now)
+    int* comp_root;          // root piece of each bubble
+    int* bcnt;               // bucket counts (zero between steps)
+    int* boff;               // bucket offsets (global scan values)
+    int2* bcq;               // centroids in bucket order
+    int* bid;                // bubble id in bucket order
+    unsigned long long* best_n;   // indexed by past label
+    unsigned long long* best_p;   // indexed by now label
+    int* phi;                // past -> now, -1 unmatched
+    int* inv;                // now -> past
+    unsigned char* active;
+    int* deg;                // link degree counts (zero between steps)
+    int* rowoff[2];          // CSR row offsets (global scan values) of past/now frames
+    int* rowlen[2];          // CSR row lengths
+    int* tdeg;               // translated-link degrees (zero between steps)
+    int* trowoff;
+    int* fcnt;               // per-row flip counts (breaking << 16 | arising is not used; two arrays)
+    int* fcnt_a;
+    int* foff;
+    int* foff_a;
+    // links
+    int* cols[2];            // CSR columns (hi label) of past/now frames, local offsets
+    int* tcols;              // translated past links
+    unsigned long long* ehash;
+    int* elist;              // occupied hash slots
+    unsigned long long* ohash;
+    unsigned* oval;
+    int* olist;
+    unsigned long long* brk;
+    unsigned long long* brk_prev;
+    unsigned long long* ari;
+    unsigned long long* ekeys;   // sorted link keys (getter output staging)
+    // scan scratch
+    unsigned long long* scan_flags;
+    long long scan_flag_cap;     // tiles of SCAN_TILE elements
+    // field pointers of this step (indexed by instance)
+    const float* const* fields;
+    const long long* pitches;
+};
+
+// Step table: which instances run this step and how blocks map onto them.
+struct StepTable {
+    int n_act;
+    const int* act;              // instance ids
+    const int* tileA_pre;        // prefix of labelling tiles over act (n_act+1)
+    const int* tileV_pre;        // prefix of Voronoi tiles
+    const long long* word_pre;   // prefix of bitmask words
+    const int* merge_pre;        // prefix of merge threads (tiles * (TW+TH))
+    // device-computed prefixes over act (n_act+1 each), filled by k_plan
+    long long* pre;              // NPRE arrays back to back
+};
+
+enum PreIdx : int {
+    PRE_K = 0,      // bubbles now
+    PRE_KP,         // bubbles previous frame
+    PRE_NB,         // buckets
+    PRE_E,          // links now
+    PRE_EP,         // links previous frame
+    PRE_O,          // overlap pairs
+    PRE_ET,         // translated links
+    PRE_FB,         // breaking links
+    PRE_FA,         // arising links
+    PRE_P,          // pieces (unused by scans)
+    NPRE
+};
+
+__device__ __forceinline__ long long* pre_arr(const StepTable& T, int which) {
+    return T.pre + (long long)which * (T.n_act + 1);
+}
+
+// ---------------------------------------------------------------------------
+// Small device helpers
+// ---------------------------------------------------------------------------
+__host__ __device__ inline long long wrap_ll(long long d, long long L) {
+    // minimum image in [-(L/2), L - L/2)
+    long long h = L / 2;
+    long long r = (d + h) % L;
+    if (r < 0) r += L;
+    return r - h;
+}
+
+__device__ __forceinline__ int upper_bound_int(const int* a, int n, int v) {
+    // first index i in [0, n] with a[i] > v; a has n+1 entries nondecreasing
+    int lo = 0, hi = n;
+    while (lo < hi) {
+        int mid = (lo + hi) >> 1;
+        if (a[mid] <= v) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ int upper_bound_ll(const long long* a, int n, long long v) {
+    int lo = 0, hi = n;
+    while (lo < hi) {
+        int mid = (lo + hi) >> 1;
+        if (a[mid] <= v) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+
+// map a virtual item index onto (slot in act list) given prefix[0..n_act]
+__device__ __forceinline__ int seg_of(const long long* pre, int n_act, long long g) {
+    return upper_bound_ll(pre, n_act + 1, g) - 1;
+}
+__device__ __forceinline__ int seg_of_int(const int* pre, int n_act, int g) {
+    return upper_bound_int(pre, n_act + 1, g) - 1;
+}
+
+__device__ __forceinline__ unsigned long long hash64(unsigned long long k) {
+    k ^= k >> 33;
+    k *= 0xff51afd7ed558ccdull;
+    k ^= k >> 33;
+    k *= 0xc4ceb9fe1a85ec53ull;
+    k ^= k >> 33;
+    return k;
+}
+
+__device__ __forceinline__ unsigned long long edge_key(int a, int b) {
+    int lo = a < b ? a : b, hi = a < b ? b : a;
+    return ((unsigned long long)(unsigned)lo << 32) | (unsigned)hi;
+}
+
+// floor division for q > 0
+__host__ __device__ inline long long floordiv_ll(long long p, long long q) {
+    long long d = p / q;
+    if ((p % q != 0) && (p < 0)) d -= 1;
+    return d;
+}
+
+// ---------------------------------------------------------------------------
+// Kernel launchers (defined in the .cu files)
+// ---------------------------------------------------------------------------
+struct Launch {
+    long long* nlaunch;  // host counter of kernel launches
+    cudaStream_t s;
+    Pools P;
+    StepTable T;
+    int grid_items;      // fixed grid for grid-stride item loops
+    int total_tilesA, total_tilesV, total_merge;
+    long long total_words;
+};
+
+void launch_ccl_tiles(const Launch& L);    // threshold + tile union-find (pass A)
+void launch_ccl_rest(const Launch& L);     // border merge, ranks, centroids, bucket grid
+void launch_labels(const Launch& L);       // per-site labels + overlap histogram
+void launch_voronoi(const Launch& L);      // owners + link hash
+void launch_graph(const Launch& L);        // CSR, match, translation, flips
+void launch_begin(const Launch& L);        // per-step counters and field pointers
+void launch_finish(const Launch& L);       // swap frames
+void launch_edge_keys(cudaStream_t s, const Pools& P, int inst, int slot, unsigned long long* out);
+
+// generic decoupled look-back scan over a virtual concatenation (vd_scan.cu)
+constexpr int SCAN_THREADS = 256;
+constexpr int SCAN_ITEMS = 16;
+constexpr int SCAN_TILE = SCAN_THREADS * SCAN_ITEMS;
+enum ScanKind : int {
+    SCAN_ROOTBITS = 0,   // popcount of root-bit words
+    SCAN_BUCKETS = 1,    // bucket counts
+    SCAN_DEG = 2,        // link degrees (now frame)
+    SCAN_TDEG = 3,       // translated link degrees
+    SCAN_FLIPS = 4,      // breaking counts per row
+    SCAN_FLIPS_A = 5,    // arising counts per row
+};
+void launch_scan(const Launch& L, ScanKind kind);   // k_plan + k_scan
+void launch_plan(const Launch& L, int with_comp);   // recompute prefixes (and bucket grids)
+
+}  // namespace vd

@@ -1,0 +1,270 @@
+// Per-step planning and the segmented exclusive scan of libvd.
+//
+// A "virtual concatenation" lists, for every instance active in the step, a
+// segment of items (bitmask words, buckets, bubbles). k_plan recomputes the
+// segment prefixes from the per-instance counters produced by the previous
+// kernel; k_scan then runs one single-pass scan (decoupled look-back, tiles
+// claimed in order through an atomic ticket) over the whole concatenation and
+// writes each item's exclusive prefix *within its own instance*: the global
+// prefix minus the sum of the totals of the earlier instances, which the
+// producers counted exactly.
+#include "vd_internal.cuh"
+
+namespace vd {
+
+// ---------------------------------------------------------------------------
+// k_plan: prefixes over the active instances; bucket grid of each instance
+// ---------------------------------------------------------------------------
+__global__ void k_plan(Pools P, StepTable T, int with_comp) {
+    // one block; instances handled serially by thread 0 in act order (n_act is
+    // at most a few hundred), other threads only help writing offsets.
+    __shared__ int s_dummy;
+    const int n = T.n_act;
+    if (threadIdx.x == 0) {
+        long long acc[NPRE];
+        for (int k = 0; k < NPRE; ++k) acc[k] = 0;
+        for (int a = 0; a < n; ++a) {
+            const int inst = T.act[a];
+            InstState& S = P.st[inst];
+            const InstDesc& D = P.desc[inst];
+            if (with_comp) {
+                int K = S.K;
+                if (K > D.comp_cap) {
+                    S.err |= ERR_COMP_CAP;
+                    K = D.comp_cap;
+                    S.K = K;
+                }
+                if (K > 0) {
+                    // bucket side ~ mean spacing of centres, clamped to [4, 64] sites
+                    double sp = sqrt((double)D.Lx * (double)D.Ly / (double)K);
+                    int B = (int)(sp + 0.5);
+                    B = B < 4 ? 4 : (B > 64 ? 64 : B);
+                    S.B = B;
+                    S.nbx = (D.Lx + B - 1) / B;
+                    S.nby = (D.Ly + B - 1) / B;
+                } else {
+                    S.B = 4; S.nbx = 0; S.nby = 0;
+                }
+            }
+            long long v[NPRE];
+            v[PRE_K] = S.K;
+            v[PRE_KP] = S.has_prev ? S.K_prev : 0;
+            v[PRE_NB] = (long long)S.nbx * S.nby;
+            v[PRE_E] = S.n_edge_list;
+            v[PRE_EP] = S.has_prev ? S.E_prev : 0;
+            v[PRE_O] = S.n_ovl < D.ovl_cap ? S.n_ovl : D.ovl_cap;
+            v[PRE_ET] = S.n_tedges;
+            v[PRE_FB] = S.n_break;
+            v[PRE_FA] = S.n_arise;
+            v[PRE_P] = 0;
+            for (int k = 0; k < NPRE; ++k) {
+                pre_arr(T, k)[a] = acc[k];
+                acc[k] += v[k];
+            }
+        }
+        for (int k = 0; k < NPRE; ++k) pre_arr(T, k)[n] = acc[k];
+        // fresh scan epoch and ticket for the scan that follows
+        P.g->scan_epoch = (P.g->scan_epoch + 1) & 0x3FFFFFFFu;
+        if (P.g->scan_epoch == 0) P.g->scan_epoch = 1;
+        P.g->scan_ticket = 0;
+    }
+    (void)s_dummy;
+}
+
+// end values of offset arrays (off[size] = total) for each instance
+__global__ void k_plan_ends(Pools P, StepTable T, int kind) {
+    for (int a = threadIdx.x; a < T.n_act; a += blockDim.x) {
+        const int inst = T.act[a];
+        const InstState& S = P.st[inst];
+        const InstDesc& D = P.desc[inst];
+        const int now = S.slot ^ 1;
+        switch (kind) {
+            case SCAN_BUCKETS: P.boff[D.bucket_off + (long long)S.nbx * S.nby] = S.K; break;
+            case SCAN_DEG: P.rowoff[now][D.comp_off + S.K] = S.n_edge_list; break;
+            case SCAN_TDEG: P.trowoff[D.comp_off + S.K] = S.n_tedges; break;
+            case SCAN_FLIPS: P.foff[D.comp_off + S.K] = S.n_break; break;
+            case SCAN_FLIPS_A: P.foff_a[D.comp_off + S.K] = S.n_arise; break;
+            default: break;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// k_scan
+// ---------------------------------------------------------------------------
+struct ScanSel {
+    int seg;      // PreIdx of segment sizes, or -1 for words (static table)
+    int base;     // PreIdx of output totals
+};
+
+__device__ __forceinline__ ScanSel scan_sel(int kind) {
+    switch (kind) {
+        case SCAN_ROOTBITS: return {-1, PRE_K};
+        case SCAN_BUCKETS: return {PRE_NB, PRE_K};
+        case SCAN_DEG: return {PRE_K, PRE_E};
+        case SCAN_TDEG: return {PRE_K, PRE_ET};
+        case SCAN_FLIPS: return {PRE_K, PRE_FB};
+        default: return {PRE_K, PRE_FA};
+    }
+}
+
+__device__ __forceinline__ int scan_value(const Pools& P, int kind, int inst, long long j) {
+    const InstDesc& D = P.desc[inst];
+    switch (kind) {
+        case SCAN_ROOTBITS: return __popc(P.rootbits[D.word_off + j]);
+        case SCAN_BUCKETS: return P.bcnt[D.bucket_off + j];
+        case SCAN_DEG: return P.deg[D.comp_off + j];
+        case SCAN_TDEG: return P.tdeg[D.comp_off + j];
+        case SCAN_FLIPS: return P.fcnt[D.comp_off + j];
+        default: return P.fcnt_a[D.comp_off + j];
+    }
+}
+
+__device__ __forceinline__ void scan_write(const Pools& P, int kind, int inst, long long j, int v) {
+    const InstDesc& D = P.desc[inst];
+    switch (kind) {
+        case SCAN_ROOTBITS: P.rankpre[D.word_off + j] = v; break;
+        case SCAN_BUCKETS: P.boff[D.bucket_off + j] = v; break;
+        case SCAN_DEG: P.rowoff[P.st[inst].slot ^ 1][D.comp_off + j] = v; break;
+        case SCAN_TDEG: P.trowoff[D.comp_off + j] = v; break;
+        case SCAN_FLIPS: P.foff[D.comp_off + j] = v; break;
+        default: P.foff_a[D.comp_off + j] = v; break;
+    }
+}
+
+constexpr unsigned ST_AGG = 1u, ST_INC = 2u;
+constexpr int SPIN_LIMIT = 1 << 20;
+
+__device__ __forceinline__ void publish(unsigned long long* f, unsigned epoch, unsigned st, int v) {
+    unsigned long long w = ((unsigned long long)epoch << 34) | ((unsigned long long)st << 32) | (unsigned)v;
+    __threadfence();
+    *(volatile unsigned long long*)f = w;
+}
+
+__global__ __launch_bounds__(SCAN_THREADS) void k_scan(Pools P, StepTable T, int kind) {
+    __shared__ int s_tile;
+    __shared__ int s_warp[SCAN_THREADS / 32];
+    __shared__ long long s_excl;
+    const ScanSel sel = scan_sel(kind);
+    const int n = T.n_act;
+    const long long* seg = sel.seg < 0 ? T.word_pre : pre_arr(T, sel.seg);
+    const long long* base = pre_arr(T, sel.base);
+    const long long total = seg[n];
+    const unsigned epoch = *(volatile unsigned*)&P.g->scan_epoch;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+
+    for (;;) {
+        if (threadIdx.x == 0) s_tile = atomicAdd(&P.g->scan_ticket, 1);
+        __syncthreads();
+        const long long tile = s_tile;
+        const long long start = tile * SCAN_TILE;
+        if (start >= total || tile >= P.scan_flag_cap) break;
+
+        // load SCAN_ITEMS consecutive items per thread
+        int v[SCAN_ITEMS];
+        int tsum = 0;
+        const long long g0 = start + (long long)threadIdx.x * SCAN_ITEMS;
+        int a = -1, inst = 0;
+        long long lo = 0, hi = -1;
+#pragma unroll
+        for (int i = 0; i < SCAN_ITEMS; ++i) {
+            const long long g = g0 + i;
+            int x = 0;
+            if (g < total) {
+                if (g >= hi) {
+                    a = seg_of(seg, n, g);
+                    lo = seg[a];
+                    hi = seg[a + 1];
+                    inst = T.act[a];
+                }
+                x = scan_value(P, kind, inst, g - lo);
+            }
+            v[i] = x;
+            tsum += x;
+        }
+        // block exclusive scan of thread sums
+        int inc = tsum;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int y = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += y;
+        }
+        if (lane == 31) s_warp[warp] = inc;
+        __syncthreads();
+        int wpre = 0, btot = 0;
+#pragma unroll
+        for (int w = 0; w < SCAN_THREADS / 32; ++w) {
+            int t = s_warp[w];
+            if (w < warp) wpre += t;
+            btot += t;
+        }
+        const int texcl = wpre + inc - tsum;
+
+        if (threadIdx.x == 0) {
+            unsigned long long* flags = P.scan_flags;
+            long long excl = 0;
+            if (tile == 0) {
+                publish(&flags[0], epoch, ST_INC, btot);
+            } else {
+                publish(&flags[tile], epoch, ST_AGG, btot);
+                long long t = tile - 1;
+                int spins = 0;
+                while (t >= 0) {
+                    unsigned long long f = *(volatile unsigned long long*)&flags[t];
+                    unsigned fe = (unsigned)(f >> 34);
+                    unsigned fs = (unsigned)(f >> 32) & 3u;
+                    if (fe != epoch || fs == 0) {
+                        if (++spins > SPIN_LIMIT) {   // give up: flag the error, never hang
+                            atomicOr(&P.g->err, ERR_TIMEOUT);
+                            break;
+                        }
+                        continue;
+                    }
+                    __threadfence();
+                    excl += (int)(unsigned)f;
+                    if (fs == ST_INC) break;
+                    --t;
+                }
+                publish(&flags[tile], epoch, ST_INC, (int)(excl + btot));
+            }
+            s_excl = excl;
+        }
+        __syncthreads();
+        long long run = s_excl + texcl;
+        a = -1; lo = 0; hi = -1;
+#pragma unroll
+        for (int i = 0; i < SCAN_ITEMS; ++i) {
+            const long long g = g0 + i;
+            if (g < total) {
+                if (g >= hi) {
+                    a = seg_of(seg, n, g);
+                    lo = seg[a];
+                    hi = seg[a + 1];
+                    inst = T.act[a];
+                }
+                scan_write(P, kind, inst, g - lo, (int)(run - base[a]));
+                run += v[i];
+            }
+        }
+        __syncthreads();
+    }
+}
+
+void launch_plan(const Launch& L, int with_comp) {
+    k_plan<<<1, 32, 0, L.s>>>(L.P, L.T, with_comp);
+    ++*L.nlaunch;
+}
+
+void launch_scan(const Launch& L, ScanKind kind) {
+    k_plan<<<1, 32, 0, L.s>>>(L.P, L.T, 0);
+    ++*L.nlaunch;
+    if (kind != SCAN_ROOTBITS) {
+        k_plan_ends<<<1, 256, 0, L.s>>>(L.P, L.T, (int)kind);
+        ++*L.nlaunch;
+    }
+    int grid = L.grid_items;
+    k_scan<<<grid, SCAN_THREADS, 0, L.s>>>(L.P, L.T, (int)kind);
+    ++*L.nlaunch;
+}
+
+}  // namespace vd

@@ -1,0 +1,402 @@
+"""ctypes binding of libvd (include/vd.h): argument marshalling only.
+
+Every function of the C ABI is exposed under the same name. ``Detector`` and
+``Batch`` are small conveniences that own a context, take torch CUDA tensors
+(device memory and the current stream come from PyTorch) and return numpy
+arrays from the getters. All computation happens in libvd's CUDA kernels;
+there is no fallback: if libvd.so is missing or cannot be loaded, every call
+raises ``VdUnavailable``.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libvd.so")
+
+VD_OK = 0
+VD_ERR_INVALID = -1
+VD_ERR_OOM = -2
+VD_ERR_CAPACITY = -3
+VD_ERR_CUDA = -4
+VD_ERR_TIMEOUT = -5
+VD_ERR_STATE = -6
+VD_ERR_UNSUPPORTED = -7
+VD_ABOVE = 1
+VD_BELOW = -1
+
+#: every symbol include/vd.h declares
+EXPORTS = (
+    "vd_config_init", "vd_create", "vd_push_frame", "vd_push_frame_host", "vd_get_changes",
+    "vd_get_counts", "vd_get_labels", "vd_get_centroids_q10", "vd_get_owners", "vd_get_edges",
+    "vd_get_match", "vd_set_timing", "vd_get_timing", "vd_stage_name", "vd_destroy", "vd_status_string",
+    "vd_batch_create", "vd_batch_push", "vd_batch_push_subset", "vd_batch_get_changes",
+    "vd_batch_get_labels", "vd_batch_get_owners", "vd_batch_get_edges", "vd_batch_get_centroids_q10",
+    "vd_batch_get_counts", "vd_batch_destroy",
+)
+
+
+class VdUnavailable(RuntimeError):
+    pass
+
+
+class VdError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        super().__init__(f"{where}: {status_string(status)} ({status})")
+
+
+class vd_config(C.Structure):
+    _fields_ = [
+        ("Lx", C.c_int32), ("Ly", C.c_int32), ("threshold", C.c_float), ("polarity", C.c_int32),
+        ("connectivity", C.c_int32), ("max_components", C.c_int32), ("max_edges", C.c_int32),
+        ("stream", C.c_void_p),
+    ]
+
+
+class vd_changes(C.Structure):
+    _fields_ = [
+        ("frame_index", C.c_int64), ("n_prev", C.c_int32), ("n_now", C.c_int32),
+        ("n_matched", C.c_int32), ("n_edges", C.c_int32), ("n_breaking", C.c_int32),
+        ("n_arising", C.c_int32), ("global_trigger", C.c_int32),
+        ("breaking", C.POINTER(C.c_uint64)), ("cap_breaking", C.c_int32),
+        ("breaking_prev", C.POINTER(C.c_uint64)),
+        ("arising", C.POINTER(C.c_uint64)), ("cap_arising", C.c_int32),
+        ("active", C.POINTER(C.c_uint8)), ("cap_active", C.c_int32),
+    ]
+
+
+_lib = None
+
+
+def lib():
+    """Load libvd.so (built by ``paper_1607_00908_gb300.build``)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise VdUnavailable(f"{LIB_PATH} is missing: run paper_1607_00908_gb300.build.build() first")
+    try:
+        L = C.CDLL(LIB_PATH)
+    except OSError as e:
+        raise VdUnavailable(f"cannot load {LIB_PATH}: {e}") from e
+    P, I32, I64, VP = C.POINTER, C.c_int32, C.c_int64, C.c_void_p
+    sig = {
+        "vd_config_init": [P(vd_config), I32, I32],
+        "vd_create": [P(vd_config), P(VP)],
+        "vd_push_frame": [VP, VP, C.c_size_t],
+        "vd_push_frame_host": [VP, VP, C.c_size_t],
+        "vd_get_changes": [VP, P(vd_changes)],
+        "vd_get_counts": [VP, P(I32), P(I32), P(I64)],
+        "vd_get_labels": [VP, VP, I64, P(I64)],
+        "vd_get_centroids_q10": [VP, VP, I64, P(I64)],
+        "vd_get_owners": [VP, VP, I64, P(I64)],
+        "vd_get_edges": [VP, VP, I64, P(I64)],
+        "vd_get_match": [VP, VP, I64, P(I64)],
+        "vd_set_timing": [VP, I32],
+        "vd_get_timing": [VP, P(C.c_double), I32, P(I32), P(I64), P(I64)],
+        "vd_stage_name": [I32],
+        "vd_destroy": [VP],
+        "vd_status_string": [I32],
+        "vd_batch_create": [P(vd_config), I32, P(VP)],
+        "vd_batch_push": [VP, P(VP)],
+        "vd_batch_push_subset": [VP, P(I32), I32, P(VP)],
+        "vd_batch_get_changes": [VP, I32, P(vd_changes)],
+        "vd_batch_get_labels": [VP, I32, VP, I64, P(I64)],
+        "vd_batch_get_owners": [VP, I32, VP, I64, P(I64)],
+        "vd_batch_get_edges": [VP, I32, VP, I64, P(I64)],
+        "vd_batch_get_centroids_q10": [VP, I32, VP, I64, P(I64)],
+        "vd_batch_get_counts": [VP, I32, P(I32), P(I32), P(I64)],
+        "vd_batch_destroy": [VP],
+    }
+    for name, args in sig.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = C.c_char_p if name in ("vd_status_string", "vd_stage_name") else C.c_int32
+    _lib = L
+    return L
+
+
+def status_string(s: int) -> str:
+    return lib().vd_status_string(int(s)).decode()
+
+
+def _check(s: int, where: str):
+    if s != VD_OK:
+        raise VdError(s, where)
+
+
+# ----------------------------------------------------------------------------
+# raw C-ABI names
+# ----------------------------------------------------------------------------
+
+def vd_config_init(Lx: int, Ly: int, threshold: float = 0.5, polarity: int = VD_ABOVE,
+                   stream: int | None = None, max_components: int = 0, max_edges: int = 0) -> vd_config:
+    cfg = vd_config()
+    _check(lib().vd_config_init(C.byref(cfg), int(Lx), int(Ly)), "vd_config_init")
+    cfg.threshold = float(threshold)
+    cfg.polarity = int(polarity)
+    cfg.max_components = int(max_components)
+    cfg.max_edges = int(max_edges)
+    cfg.stream = C.c_void_p(stream or 0)
+    return cfg
+
+
+def vd_create(cfg: vd_config) -> C.c_void_p:
+    h = C.c_void_p()
+    _check(lib().vd_create(C.byref(cfg), C.byref(h)), "vd_create")
+    return h
+
+
+def vd_push_frame(ctx, d_field_ptr: int, pitch: int) -> int:
+    return lib().vd_push_frame(ctx, C.c_void_p(d_field_ptr), pitch)
+
+
+def vd_push_frame_host(ctx, h_field_ptr: int, pitch: int) -> int:
+    return lib().vd_push_frame_host(ctx, C.c_void_p(h_field_ptr), pitch)
+
+
+def vd_get_changes(ctx, out: vd_changes) -> int:
+    return lib().vd_get_changes(ctx, C.byref(out))
+
+
+def vd_get_counts(ctx):
+    K, E, f = C.c_int32(), C.c_int32(), C.c_int64()
+    s = lib().vd_get_counts(ctx, C.byref(K), C.byref(E), C.byref(f))
+    return s, K.value, E.value, f.value
+
+
+def vd_get_labels(ctx, out_ptr: int, cap: int):
+    n = C.c_int64()
+    return lib().vd_get_labels(ctx, C.c_void_p(out_ptr), cap, C.byref(n)), n.value
+
+
+def vd_get_owners(ctx, out_ptr: int, cap: int):
+    n = C.c_int64()
+    return lib().vd_get_owners(ctx, C.c_void_p(out_ptr), cap, C.byref(n)), n.value
+
+
+def vd_get_centroids_q10(ctx, out_ptr: int, cap: int):
+    n = C.c_int64()
+    return lib().vd_get_centroids_q10(ctx, C.c_void_p(out_ptr), cap, C.byref(n)), n.value
+
+
+def vd_get_edges(ctx, out_ptr: int, cap: int):
+    n = C.c_int64()
+    return lib().vd_get_edges(ctx, C.c_void_p(out_ptr), cap, C.byref(n)), n.value
+
+
+def vd_get_match(ctx, out_ptr: int, cap: int):
+    n = C.c_int64()
+    return lib().vd_get_match(ctx, C.c_void_p(out_ptr), cap, C.byref(n)), n.value
+
+
+def vd_destroy(ctx) -> int:
+    return lib().vd_destroy(ctx)
+
+
+def vd_batch_create(cfgs) -> C.c_void_p:
+    arr = (vd_config * len(cfgs))(*cfgs)
+    h = C.c_void_p()
+    _check(lib().vd_batch_create(arr, len(cfgs), C.byref(h)), "vd_batch_create")
+    return h
+
+
+def vd_batch_push(b, field_ptrs) -> int:
+    arr = (C.c_void_p * len(field_ptrs))(*[C.c_void_p(p) for p in field_ptrs])
+    return lib().vd_batch_push(b, arr)
+
+
+def vd_batch_push_subset(b, active, field_ptrs) -> int:
+    act = (C.c_int32 * len(active))(*active)
+    arr = (C.c_void_p * len(field_ptrs))(*[C.c_void_p(p) for p in field_ptrs])
+    return lib().vd_batch_push_subset(b, act, len(active), arr)
+
+
+def vd_batch_get_changes(b, i: int, out: vd_changes) -> int:
+    return lib().vd_batch_get_changes(b, i, C.byref(out))
+
+
+def vd_batch_get_counts(b, i: int):
+    K, E, f = C.c_int32(), C.c_int32(), C.c_int64()
+    s = lib().vd_batch_get_counts(b, i, C.byref(K), C.byref(E), C.byref(f))
+    return s, K.value, E.value, f.value
+
+
+def vd_batch_destroy(b) -> int:
+    return lib().vd_batch_destroy(b)
+
+
+# ----------------------------------------------------------------------------
+# conveniences
+# ----------------------------------------------------------------------------
+
+def _changes(getter, K_now: int, cap: int):
+    brk = np.empty(max(cap, 1), np.uint64)
+    brkp = np.empty(max(cap, 1), np.uint64)
+    ari = np.empty(max(cap, 1), np.uint64)
+    act = np.empty(max(K_now, 1), np.uint8)
+    ch = vd_changes()
+    ch.breaking = brk.ctypes.data_as(C.POINTER(C.c_uint64))
+    ch.breaking_prev = brkp.ctypes.data_as(C.POINTER(C.c_uint64))
+    ch.arising = ari.ctypes.data_as(C.POINTER(C.c_uint64))
+    ch.active = act.ctypes.data_as(C.POINTER(C.c_uint8))
+    ch.cap_breaking = cap
+    ch.cap_arising = cap
+    ch.cap_active = max(K_now, 1)
+    s = getter(ch)
+    return s, ch, brk, brkp, ari, act
+
+
+class _Base:
+    _get_counts = None
+
+    def _read(self, getter_name, i, dtype, count, mult=1):
+        out = np.empty(max(count * mult, 1), dtype=dtype)
+        n = C.c_int64()
+        fn = getattr(lib(), getter_name)
+        args = (self.h,) if i is None else (self.h, i)
+        s = fn(*args, out.ctypes.data_as(C.c_void_p), out.size, C.byref(n))
+        _check(s, getter_name)
+        return out[: n.value]
+
+
+class Detector(_Base):
+    """One periodic lattice (vd_create / vd_push_frame / vd_get_* / vd_destroy)."""
+
+    def __init__(self, Lx: int, Ly: int, threshold: float = 0.5, polarity: int = VD_ABOVE,
+                 stream: int | None = None, max_components: int = 0, max_edges: int = 0):
+        if stream is None:
+            import torch
+            stream = torch.cuda.current_stream().cuda_stream
+        self.Lx, self.Ly = Lx, Ly
+        self.cfg = vd_config_init(Lx, Ly, threshold, polarity, stream, max_components, max_edges)
+        self.h = vd_create(self.cfg)
+
+    def push(self, field) -> None:
+        """field: torch CUDA float32 tensor [Ly, Lx] (row stride = field.stride(0))."""
+        assert field.is_cuda and field.dtype.itemsize == 4 and field.stride(1) == 1
+        _check(vd_push_frame(self.h, field.data_ptr(), field.stride(0)), "vd_push_frame")
+
+    def push_host(self, arr: np.ndarray) -> None:
+        a = np.ascontiguousarray(arr, dtype=np.float32)
+        _check(vd_push_frame_host(self.h, a.ctypes.data, a.shape[1]), "vd_push_frame_host")
+
+    def counts(self):
+        s, K, E, f = vd_get_counts(self.h)
+        _check(s, "vd_get_counts")
+        return K, E, f
+
+    def labels(self) -> np.ndarray:
+        return self._read("vd_get_labels", None, np.int32, self.Lx * self.Ly).reshape(self.Ly, self.Lx)
+
+    def owners(self) -> np.ndarray:
+        return self._read("vd_get_owners", None, np.int32, self.Lx * self.Ly).reshape(self.Ly, self.Lx)
+
+    def centroids(self) -> np.ndarray:
+        K, _, _ = self.counts()
+        return self._read("vd_get_centroids_q10", None, np.int32, K, 2).reshape(-1, 2)
+
+    def edges(self) -> np.ndarray:
+        _, E, _ = self.counts()
+        return self._read("vd_get_edges", None, np.uint64, E)
+
+    def match(self) -> np.ndarray:
+        """Phi: past label -> now label (-1 unmatched), one entry per past bubble."""
+        return self._read("vd_get_match", None, np.int32, self.changes()["K_prev"])
+
+    def changes(self) -> dict:
+        K, E, _ = self.counts()
+        cap = max(E, 1) * 2 + 16
+        s, ch, brk, brkp, ari, act = _changes(lambda c: vd_get_changes(self.h, c), K, cap)
+        _check(s, "vd_get_changes")
+        return dict(frame=ch.frame_index, K_prev=ch.n_prev, K=ch.n_now, n_matched=ch.n_matched,
+                    n_edges=ch.n_edges, breaking=brk[: ch.n_breaking].copy(),
+                    breaking_prev=brkp[: ch.n_breaking].copy(), arising=ari[: ch.n_arising].copy(),
+                    active=act[: ch.n_now].copy(), global_trigger=ch.global_trigger)
+
+    def set_timing(self, on: bool) -> None:
+        _check(lib().vd_set_timing(self.h, int(bool(on))), "vd_set_timing")
+
+    def timing(self):
+        """(per-stage ms since the last call, stage names, kernel launches, frames)."""
+        ms = (C.c_double * 16)()
+        n, kl, nf = C.c_int32(), C.c_int64(), C.c_int64()
+        _check(lib().vd_get_timing(self.h, ms, 16, C.byref(n), C.byref(kl), C.byref(nf)), "vd_get_timing")
+        names = [lib().vd_stage_name(i).decode() for i in range(n.value)]
+        return list(ms[: n.value]), names, kl.value, nf.value
+
+    def close(self):
+        if getattr(self, "h", None):
+            vd_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch(_Base):
+    """Many lattices advanced together (vd_batch_*)."""
+
+    def __init__(self, sizes, threshold: float = 0.5, polarity: int = VD_ABOVE, stream: int | None = None,
+                 max_components: int = 0):
+        if stream is None:
+            import torch
+            stream = torch.cuda.current_stream().cuda_stream
+        self.sizes = [(int(lx), int(ly)) for lx, ly in sizes]
+        cfgs = [vd_config_init(lx, ly, threshold, polarity, stream, max_components) for lx, ly in self.sizes]
+        self.h = vd_batch_create(cfgs)
+
+    def push(self, fields) -> None:
+        _check(vd_batch_push(self.h, [f.data_ptr() for f in fields]), "vd_batch_push")
+
+    def push_subset(self, active, fields) -> None:
+        _check(vd_batch_push_subset(self.h, list(active), [f.data_ptr() for f in fields]), "vd_batch_push_subset")
+
+    def counts(self, i):
+        s, K, E, f = vd_batch_get_counts(self.h, i)
+        _check(s, "vd_batch_get_counts")
+        return K, E, f
+
+    def labels(self, i):
+        lx, ly = self.sizes[i]
+        return self._read("vd_batch_get_labels", i, np.int32, lx * ly).reshape(ly, lx)
+
+    def owners(self, i):
+        lx, ly = self.sizes[i]
+        return self._read("vd_batch_get_owners", i, np.int32, lx * ly).reshape(ly, lx)
+
+    def centroids(self, i):
+        K, _, _ = self.counts(i)
+        return self._read("vd_batch_get_centroids_q10", i, np.int32, K, 2).reshape(-1, 2)
+
+    def edges(self, i):
+        _, E, _ = self.counts(i)
+        return self._read("vd_batch_get_edges", i, np.uint64, E)
+
+    def changes(self, i) -> dict:
+        K, E, _ = self.counts(i)
+        cap = max(E, 1) * 2 + 16
+        s, ch, brk, brkp, ari, act = _changes(lambda c: vd_batch_get_changes(self.h, i, c), K, cap)
+        _check(s, "vd_batch_get_changes")
+        return dict(frame=ch.frame_index, K_prev=ch.n_prev, K=ch.n_now, n_matched=ch.n_matched,
+                    n_edges=ch.n_edges, breaking=brk[: ch.n_breaking].copy(),
+                    breaking_prev=brkp[: ch.n_breaking].copy(), arising=ari[: ch.n_arising].copy(),
+                    active=act[: ch.n_now].copy(), global_trigger=ch.global_trigger)
+
+    def close(self):
+        if getattr(self, "h", None):
+            vd_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

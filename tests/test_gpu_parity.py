@@ -1,0 +1,209 @@
+"""GPU parity: libvd (through its C ABI) against the CPU oracle, bit for bit.
+
+Every output is integer, so the tolerance is exact (0) for labels, Q10
+centroids, Voronoi owners, sorted link keys, the isomorphism Phi and the
+breaking/arising lists. Sizes span several 64x32 labelling tiles and 32x32
+Voronoi tiles with ragged tails; full-size workloads check every output the
+oracle can produce in seconds and sampled Voronoi owners (brute force per
+site) where the full oracle is slower.
+"""
+from __future__ import annotations
+
+import os
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+import oracle as O  # noqa: E402
+from paper_1607_00908_gb300 import inputs as I  # noqa: E402
+from paper_1607_00908_gb300 import vd  # noqa: E402
+
+FULL = os.environ.get("VD_FULL", "0") == "1"
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    vd.lib()
+
+
+def check_frame(det, r, what=("labels", "centroids", "owners", "edges", "changes"), tag=""):
+    K, E, _ = det.counts()
+    assert K == r["K"], (tag, "K", K, r["K"])
+    if "labels" in what:
+        got = det.labels()
+        if not np.array_equal(got, r["labels"]):
+            bad = np.argwhere(got != r["labels"])
+            raise AssertionError(f"{tag} labels differ at {len(bad)} sites, first {bad[:5].tolist()}")
+    if "centroids" in what:
+        got = det.centroids()
+        if not np.array_equal(got, r["centroids"]):
+            bad = np.flatnonzero((got != r["centroids"]).any(axis=1))
+            raise AssertionError(f"{tag} centroids differ for {len(bad)} bubbles: {bad[:5].tolist()} "
+                                 f"got {got[bad[:3]].tolist()} want {r['centroids'][bad[:3]].tolist()}")
+    if "owners" in what:
+        got = det.owners()
+        if not np.array_equal(got, r["owners"]):
+            bad = np.argwhere(got != r["owners"])
+            raise AssertionError(f"{tag} owners differ at {len(bad)} sites, first {bad[:5].tolist()}")
+    if "edges" in what:
+        got = det.edges()
+        assert E == len(r["edges"]), (tag, "E", E, len(r["edges"]))
+        assert np.array_equal(got, r["edges"]), f"{tag} edge keys differ"
+    if "changes" in what:
+        ch = det.changes()
+        assert ch["K_prev"] == r["K_prev"], (tag, ch["K_prev"], r["K_prev"])
+        assert ch["n_matched"] == r["n_matched"], (tag, "matched", ch["n_matched"], r["n_matched"])
+        assert np.array_equal(ch["breaking"], r["breaking"]), f"{tag} breaking differs"
+        assert np.array_equal(ch["breaking_prev"], r["breaking_prev"]), f"{tag} breaking_prev differs"
+        assert np.array_equal(ch["arising"], r["arising"]), f"{tag} arising differs"
+        assert np.array_equal(ch["active"], r["active"]), f"{tag} active differs"
+        assert ch["global_trigger"] == r["global_trigger"]
+        if r["K_prev"]:
+            assert np.array_equal(det.match(), r["phi"]), f"{tag} phi differs"
+
+
+def run_pair(frames, threshold=0.5, polarity=1, voronoi="kdtree", what=None, tag=""):
+    Ly, Lx = frames[0].shape
+    det = vd.Detector(Lx, Ly, threshold=threshold, polarity=polarity)
+    ref = O.Detector(Lx, Ly, theta=threshold, polarity=polarity, voronoi=voronoi, workers=-1)
+    for f, F in enumerate(frames):
+        det.push(torch.from_numpy(np.ascontiguousarray(F)).cuda())
+        r = ref.push(F)
+        check_frame(det, r, tag=f"{tag} frame {f}", **({} if what is None else {"what": what}))
+    det.close()
+    return r
+
+
+def test_c0_two_frames():
+    r = run_pair(I.workload_c0(seed=1), tag="c0")
+    assert r["K"] > 10
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_random_small_lattices(seed):
+    """Random sizes (1..150, ragged against both tilings), densities and polarity."""
+    rng = np.random.default_rng(100 + seed)
+    for trial in range(6):
+        Lx = int(rng.integers(1, 150))
+        Ly = int(rng.integers(1, 150))
+        if trial % 3 == 0:
+            F0 = rng.random((Ly, Lx)).astype(np.float32)
+            F1 = np.where(rng.random((Ly, Lx)) < 0.1, rng.random((Ly, Lx)), F0).astype(np.float32)
+            thr = float(rng.uniform(0.2, 0.8))
+        else:
+            sig = float(rng.uniform(1.0, 4.0))
+            F0 = I.smoothed_noise(Ly, Lx, sig, seed=seed * 10 + trial)
+            F1 = I.shear_resample(F0, 0.03, 0.02, np.random.default_rng(trial))
+            thr = float(rng.uniform(-0.5, 1.0))
+        pol = 1 if rng.random() < 0.7 else -1
+        run_pair([F0, F1], threshold=thr, polarity=pol, voronoi="brute", tag=f"{Lx}x{Ly} pol{pol}")
+
+
+def test_degenerate_fields():
+    L = 70
+    cases = {
+        "empty": np.zeros((L, L), np.float32),
+        "full": np.ones((L, L), np.float32),
+        "checker": ((np.indices((L, L)).sum(0) % 2) == 0).astype(np.float32),
+        "stripes": np.tile((np.arange(L) % 3 == 0).astype(np.float32), (L, 1)),
+        "single": np.pad(np.ones((1, 1), np.float32), ((5, L - 6), (9, L - 10))),
+        "nan": np.where(np.random.default_rng(0).random((L, L)) < 0.3, np.nan, 1.0).astype(np.float32),
+    }
+    for name, F in cases.items():
+        run_pair([F, np.roll(F, 1, axis=1)], voronoi="brute", tag=name)
+
+
+def test_wide_bubbles_across_seams():
+    """Bubbles wider than half the lattice and winding ones take the exact path."""
+    for L in (40, 64, 96, 130):
+        F = np.zeros((L, L), np.float32)
+        F[3, :] = 1.0                              # winds around x
+        F[:, 7] = 1.0                              # winds around y (joined with the row)
+        F[10:14, 2: L - 5] = 1.0                   # wider than L/2
+        F[L - 3:, L - 3:] = 1.0                    # corner block across both seams
+        F[:2, :2] = 1.0
+        F[20: 20 + L // 2 + 3, 30 % L] = 1.0       # tall bar
+        run_pair([F, np.roll(F, 2, axis=0)], voronoi="brute", tag=f"wide{L}")
+
+
+def test_tiny_lattices():
+    rng = np.random.default_rng(5)
+    for Lx, Ly in [(1, 1), (1, 7), (7, 1), (2, 2), (3, 2), (1, 64), (64, 1), (65, 33), (33, 65)]:
+        F0 = rng.random((Ly, Lx)).astype(np.float32)
+        F1 = rng.random((Ly, Lx)).astype(np.float32)
+        run_pair([F0, F1], voronoi="brute", tag=f"tiny{Lx}x{Ly}")
+
+
+def test_pitched_field():
+    F = I.smoothed_noise(100, 90, 2.5, seed=3)
+    big = np.zeros((100, 96), np.float32)
+    big[:, :90] = F
+    det = vd.Detector(90, 100)
+    t = torch.from_numpy(big).cuda()[:, :90]
+    det.push(t)
+    r = O.Detector(90, 100).push(F)
+    check_frame(det, r, what=("labels", "centroids", "owners", "edges"), tag="pitched")
+
+
+def test_host_push_matches_device_push():
+    frames = I.workload_c0(seed=4)
+    a = vd.Detector(128, 128)
+    b = vd.Detector(128, 128)
+    for F in frames:
+        a.push(torch.from_numpy(F).cuda())
+        b.push_host(F)
+        assert np.array_equal(a.labels(), b.labels())
+        assert np.array_equal(a.edges(), b.edges())
+        ca, cb = a.changes(), b.changes()
+        assert np.array_equal(ca["breaking"], cb["breaking"]) and np.array_equal(ca["arising"], cb["arising"])
+
+
+def test_c1_frames():
+    """1024x1024 smoothed noise (sigma 4), sheared frame to frame: full oracle each frame."""
+    n = 64 if FULL else 6
+    frames = list(I.workload_c1(seed=1, n_frames=n))
+    r = run_pair(frames, tag="c1")
+    assert r["K"] > 500
+
+
+def test_c2_frames():
+    """4096x4096 RSA droplets: labels, centroids, links and flips from the full oracle."""
+    n = 16 if FULL else 2
+    frames = [F for F, _ in I.workload_c2(seed=1, n_frames=n)]
+    r = run_pair(frames, tag="c2")
+    assert r["K"] > 20000
+
+
+def test_c2_sampled_owners_bruteforce():
+    """Voronoi owners at full size, sampled sites checked by the all-centres definition."""
+    F, st = next(iter(I.workload_c2(seed=2, n_frames=1)))
+    L = F.shape[0]
+    det = vd.Detector(L, L)
+    det.push(torch.from_numpy(F).cuda())
+    lab, K = O.label_components(O.foreground(F))
+    cq = O.centroids_q10(lab, K)
+    assert np.array_equal(det.centroids(), cq)
+    own = det.owners().ravel()
+    rng = np.random.default_rng(0)
+    sites = rng.choice(L * L, size=4000, replace=False)
+    want = O.owners_bruteforce(cq, L, L, sites=sites)
+    assert np.array_equal(own[sites], want)
+
+
+def test_capacity_overflow_is_reported():
+    F = ((np.indices((64, 64)).sum(0) % 2) == 0).astype(np.float32)   # 2048 bubbles
+    det = vd.Detector(64, 64, max_components=100)
+    det.push(torch.from_numpy(F).cuda())
+    with pytest.raises(vd.VdError) as e:
+        det.labels()
+    assert e.value.status == vd.VD_ERR_CAPACITY
+    # the context stays usable after a capacity error on a fitting frame
+    G = np.zeros((64, 64), np.float32)
+    G[10:20, 10:20] = 1.0
+    det.push(torch.from_numpy(G).cuda())
+    assert det.counts()[0] == 1
