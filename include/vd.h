@@ -133,6 +133,29 @@ const char* vd_stage_name(int32_t stage);
 /* Release all device state of the context (waits for its stream first). */
 vd_status vd_destroy(vd_ctx* ctx);
 
+/* Voronoi owners without any device allocation. The paper has no
+ * counterpart: this exists for callers that cannot call cudaMalloc (code
+ * inside stream capture with allocation forbidden, processes whose device
+ * memory belongs to another allocator, hosts that allocate everything at
+ * start-up). It computes the same exact colouring as the pipeline's owner
+ * step: owner(x,y) = the label i minimising |1024*(x,y) - c_i|^2 (minimum
+ * image, ties to the smallest i), or -1 when K == 0.
+ *   d_centroids_q10  device, K pairs (cx, cy) in 1/1024 site, in [0, 1024*L);
+ *                    pairs outside that range are ignored
+ *   d_owners         device, Ly*Lx int32, row-major (written)
+ *   stream           cudaStream_t (NULL = legacy default stream)
+ * Its scratch is one static __device__ array of about 1.5 MB per GPU, held
+ * until the process exits: at most 65536 centroids and 65536 bucket cells
+ * per call (larger K returns VD_ERR_CAPACITY without launching anything).
+ * Every call shares that array: calls whose device work may overlap (other
+ * streams, other host threads) race and must be serialised by the caller.
+ * The first call on a device resolves the array's device address (a runtime
+ * query, no allocation); make that first call before any stream capture.
+ * Asynchronous on `stream`; errors: VD_ERR_INVALID, VD_ERR_CAPACITY,
+ * VD_ERR_CUDA. */
+vd_status vd_voronoi_owners_static(const int32_t* d_centroids_q10, int32_t K, int32_t Lx, int32_t Ly,
+                                   int32_t* d_owners, void* stream);
+
 /* Static description of a status code. */
 const char* vd_status_string(vd_status s);
 

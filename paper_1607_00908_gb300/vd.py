@@ -35,7 +35,7 @@ EXPORTS = (
     "vd_get_match", "vd_set_timing", "vd_get_timing", "vd_stage_name", "vd_destroy", "vd_status_string",
     "vd_batch_create", "vd_batch_push", "vd_batch_push_subset", "vd_batch_get_changes",
     "vd_batch_get_labels", "vd_batch_get_owners", "vd_batch_get_edges", "vd_batch_get_centroids_q10",
-    "vd_batch_get_counts", "vd_batch_destroy",
+    "vd_batch_get_counts", "vd_batch_destroy", "vd_voronoi_owners_static",
 )
 
 
@@ -111,6 +111,7 @@ def lib():
         "vd_batch_get_centroids_q10": [VP, I32, VP, I64, P(I64)],
         "vd_batch_get_counts": [VP, I32, P(I32), P(I32), P(I64)],
         "vd_batch_destroy": [VP],
+        "vd_voronoi_owners_static": [VP, I32, I32, I32, VP, VP],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -228,6 +229,12 @@ def vd_batch_get_counts(b, i: int):
 
 def vd_batch_destroy(b) -> int:
     return lib().vd_batch_destroy(b)
+
+
+def vd_voronoi_owners_static(d_centroids_ptr: int, K: int, Lx: int, Ly: int, d_owners_ptr: int,
+                             stream: int = 0) -> int:
+    return lib().vd_voronoi_owners_static(C.c_void_p(d_centroids_ptr), K, Lx, Ly, C.c_void_p(d_owners_ptr),
+                                          C.c_void_p(stream))
 
 
 # ----------------------------------------------------------------------------
