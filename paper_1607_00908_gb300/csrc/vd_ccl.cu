@@ -49,220 +49,228 @@ __device__ __forceinline__ void uf_union(int* p, int a, int b) {
     } while (!done);
 }
 
-__device__ __forceinline__ unsigned long long row_bits(const unsigned (*s_bits)[2], int r) {
-    return (unsigned long long)s_bits[r][0] | ((unsigned long long)s_bits[r][1] << 32);
+// ---------------------------------------------------------------------------
+// Warp-per-tile labelling. A 64 x 32 tile is handled by one warp: lane r owns
+// tile row r, whose 64 foreground bits live in one 64-bit mask. Runs of a row
+// are numbered left to right; run j of row r has id r*32 + j, so ids follow
+// raster order and the smallest id of a component is its first site.
+// ---------------------------------------------------------------------------
+constexpr int RUNS = TH * 32;   // run ids per tile
+
+__device__ __forceinline__ unsigned long long run_starts(unsigned long long m) { return m & ~(m << 1); }
+__device__ __forceinline__ unsigned long long upto(int c) { return c == 63 ? ~0ull : ((2ull << c) - 1ull); }
+// index of the run of row mask m (starts S) that contains column c (bit c set)
+__device__ __forceinline__ int run_index(unsigned long long S, int c) { return __popcll(S & upto(c)) - 1; }
+// column of the j-th run start (0-based)
+__device__ __forceinline__ int run_column(unsigned long long S, int j) {
+    const unsigned lo = (unsigned)S, hi = (unsigned)(S >> 32);
+    const int nlo = __popc(lo);
+    return j < nlo ? (int)__fns(lo, 0, j + 1) : 32 + (int)__fns(hi, 0, j - nlo + 1);
+}
+__device__ __forceinline__ int run_length(unsigned long long m, int c) {
+    const unsigned long long inv = ~(m >> c);
+    return inv ? __ffsll(inv) - 1 : 64;   // all ones only when c == 0
 }
 
-// Called by all TTHREADS threads. Thread t owns row t/8, sites 8*(t%8) .. +7.
-// On return s_par[i] is the smallest tile-local index of site i's component
-// (i itself for a root) for foreground sites, -1 for background sites.
-__device__ void tile_union_find(const unsigned (*s_bits)[2], int* s_par) {
-    const int r = threadIdx.x >> 3, sg = threadIdx.x & 7;
-    const unsigned long long row = row_bits(s_bits, r);
-    const unsigned seg = (unsigned)(row >> (sg * 8)) & 0xFFu;
-    const int base = r * TW + sg * 8;
-    int rs = -1;
-#pragma unroll
-    for (int i = 0; i < 8; ++i) {
-        if ((seg >> i) & 1u) {
-            if (rs < 0) rs = base + i;
-            s_par[base + i] = rs;
-        } else {
-            rs = -1;
-            s_par[base + i] = -1;
-        }
-    }
-    __syncthreads();
-    if (sg > 0 && (seg & 1u) && ((row >> (sg * 8 - 1)) & 1ull)) uf_union(s_par, base, base - 1);
+struct UfSmem {                  // one warp's tile: row masks and union-find over runs
+    unsigned long long m[TH];
+    int par[RUNS];
+};
+struct LabelSmem : UfSmem {
+    int aux[RUNS];     // per root run: (n << 16) | sum(y - y_root), then piece id / bubble id
+};
+struct TileSmem : LabelSmem {
+    int su[RUNS];      // per root run: sum(x - x_root)
+};
+
+// union-find over runs; lane r owns row r; m = this lane's row mask, mu = row r-1
+__device__ void warp_runs_uf(UfSmem& T, unsigned long long m) {
+    const int r = threadIdx.x & 31;
+    const unsigned long long S = run_starts(m);
+    const int nr = __popcll(S);
+    for (int j = 0; j < nr; ++j) T.par[r * 32 + j] = r * 32 + j;
+    const unsigned long long mu = __shfl_up_sync(0xffffffffu, m, 1);
+    __syncwarp();
     if (r > 0) {
-        const unsigned long long up = row_bits(s_bits, r - 1);
-        const unsigned vm = seg & ((unsigned)(up >> (sg * 8)) & 0xFFu);
-        unsigned starts = vm & ~(vm << 1);
-        while (starts) {
-            const int i = __ffs(starts) - 1;
-            starts &= starts - 1;
-            uf_union(s_par, base + i, base + i - TW);
+        const unsigned long long Su = run_starts(mu);
+        unsigned long long os = run_starts(m & mu);
+        while (os) {
+            const int c = __ffsll(os) - 1;
+            os &= os - 1;
+            uf_union(T.par, r * 32 + run_index(S, c), (r - 1) * 32 + run_index(Su, c));
         }
     }
-    __syncthreads();
-#pragma unroll
-    for (int i = 0; i < 8; ++i)
-        if ((seg >> i) & 1u) s_par[base + i] = uf_find(s_par, base + i);
-    __syncthreads();
+    __syncwarp();
+    for (int j = 0; j < nr; ++j) T.par[r * 32 + j] = uf_find(T.par, r * 32 + j);
+    __syncwarp();
 }
 
-// block exclusive scan of one int per thread (TTHREADS threads); returns the
-// thread's exclusive prefix and writes the block total to *total
-__device__ __forceinline__ int block_excl_scan(int x, int* s_tmp, int* total) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    int inc = x;
+// mask (over run indices) of this lane's root runs, and the exclusive count of
+// roots in rows above (raster order); *total = roots in the tile
+__device__ __forceinline__ unsigned warp_roots(const UfSmem& T, unsigned long long m, int* base, int* total) {
+    const int r = threadIdx.x & 31;
+    const int nr = __popcll(run_starts(m));
+    unsigned R = 0;
+    for (int j = 0; j < nr; ++j)
+        if (T.par[r * 32 + j] == r * 32 + j) R |= 1u << j;
+    const int cnt = __popc(R);
+    int inc = cnt;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-        int y = __shfl_up_sync(0xffffffffu, inc, o);
-        if (lane >= o) inc += y;
+        const int y = __shfl_up_sync(0xffffffffu, inc, o);
+        if (r >= o) inc += y;
     }
-    if (lane == 31) s_tmp[warp] = inc;
-    __syncthreads();
-    int pre = 0, tot = 0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
-        int t = s_tmp[w];
-        if (w < warp) pre += t;
-        tot += t;
-    }
-    *total = tot;
-    __syncthreads();
-    return pre + inc - x;
+    *base = inc - cnt;
+    *total = __shfl_sync(0xffffffffu, inc, 31);
+    return R;
 }
 
-// load the tile's foreground bits from the global bitmask
-__device__ __forceinline__ void load_tile_bits(const Pools& P, const InstDesc& D, int x0, int y0,
-                                               unsigned (*s_bits)[2]) {
-    for (int k = threadIdx.x; k < TH * 2; k += blockDim.x) {
-        const int r = k >> 1, h = k & 1;
-        const int y = y0 + r;
-        const int wx = (x0 >> 5) + h;
-        unsigned w = 0;
-        if (y < D.Ly && wx < D.wpr) w = P.fgbits[D.word_off + (long long)y * D.wpr + wx];
-        s_bits[r][h] = w;
+// row masks of a tile from the stored foreground bits (lane r -> row r)
+__device__ __forceinline__ unsigned long long load_row_mask(const Pools& P, const InstDesc& D, int x0, int y0) {
+    const int y = y0 + (threadIdx.x & 31);
+    unsigned long long m = 0;
+    if (y < D.Ly) {
+        const unsigned* row = P.fgbits + D.word_off + (long long)y * D.wpr;
+        const int wx = x0 >> 5;
+        m = row[wx];
+        if (wx + 1 < D.wpr) m |= (unsigned long long)row[wx + 1] << 32;
     }
-    __syncthreads();
+    return m;
 }
 
 __device__ __forceinline__ bool is_fg(float v, float thr, int pol) {
     return pol > 0 ? (v > thr) : (v < thr);
 }
 
-// ---------------------------------------------------------------------------
-// Pass A: threshold + tile union-find + pieces + borders
-// ---------------------------------------------------------------------------
-__global__ __launch_bounds__(TTHREADS) void k_ccl_tiles(Pools P, StepTable T) {
-    __shared__ unsigned s_bits[TH][2];
-    __shared__ int s_par[TSITES];
-    __shared__ int s_nsv[TSITES];   // (n << 16) | sum of (y - y_root), later piece id
-    __shared__ int s_su[TSITES];    // sum of (x - x_root)
-    __shared__ int s_tmp[TTHREADS / 32];
-    __shared__ int s_base;
+constexpr int CCL_WARPS = 2;    // tiles per block in pass A
 
-    const int b = blockIdx.x;
+// ---------------------------------------------------------------------------
+// Pass A: threshold + union-find over runs + pieces + borders (one warp per tile)
+// ---------------------------------------------------------------------------
+__global__ __launch_bounds__(32 * CCL_WARPS) void k_ccl_tiles(Pools P, StepTable T) {
+    __shared__ TileSmem s_tile[CCL_WARPS];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int b = blockIdx.x * CCL_WARPS + w;
+    if (b >= T.tileA_pre[T.n_act]) return;
+    TileSmem& TS = s_tile[w];
     const int a = seg_of_int(T.tileA_pre, T.n_act, b);
     const int inst = T.act[a];
-    const InstDesc D = P.desc[inst];
+    const InstDesc& D = P.desc[inst];
     const InstState& S = P.st[inst];
     const int t = b - T.tileA_pre[a];
     const int tx = t % D.ntx, ty = t / D.ntx;
     const int x0 = tx * TW, y0 = ty * TH;
-    const int r = threadIdx.x >> 3, sg = threadIdx.x & 7;
-    const int y = y0 + r, xs = x0 + sg * 8;
+    const int Lx = D.Lx, Ly = D.Ly;
+    const float thr = D.thr;
+    const int pol = D.pol;
+    const float* field = S.field;
+    const long long pitch = S.pitch;
+    const bool in0 = x0 + lane < Lx, in1 = x0 + 32 + lane < Lx;
 
-    // 1. threshold 8 sites per thread
-    unsigned bits8 = 0;
-    if (y < D.Ly && xs < D.Lx) {
-        const float* f = S.field + (long long)y * S.pitch + xs;
-        if (xs + 8 <= D.Lx && ((reinterpret_cast<uintptr_t>(f) & 15u) == 0)) {
-            const float4 u = __ldcs(reinterpret_cast<const float4*>(f));
-            const float4 w = __ldcs(reinterpret_cast<const float4*>(f) + 1);
-            bits8 = (unsigned)is_fg(u.x, D.thr, D.pol) | ((unsigned)is_fg(u.y, D.thr, D.pol) << 1) |
-                    ((unsigned)is_fg(u.z, D.thr, D.pol) << 2) | ((unsigned)is_fg(u.w, D.thr, D.pol) << 3) |
-                    ((unsigned)is_fg(w.x, D.thr, D.pol) << 4) | ((unsigned)is_fg(w.y, D.thr, D.pol) << 5) |
-                    ((unsigned)is_fg(w.z, D.thr, D.pol) << 6) | ((unsigned)is_fg(w.w, D.thr, D.pol) << 7);
-        } else {
-            for (int i = 0; i < 8; ++i)
-                if (xs + i < D.Lx && is_fg(__ldcs(f + i), D.thr, D.pol)) bits8 |= 1u << i;
+    // 1. threshold: lane l reads columns l and l+32 of every row (coalesced)
+    unsigned long long my_m = 0;
+#pragma unroll 4
+    for (int rb = 0; rb < TH; rb += 8) {
+        float v0[8], v1[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const int y = y0 + rb + k;
+            const float* f = field + (long long)y * pitch + x0 + lane;
+            v0[k] = (y < Ly && in0) ? __ldcs(f) : NAN;
+            v1[k] = (y < Ly && in1) ? __ldcs(f + 32) : NAN;
+        }
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const unsigned lo = __ballot_sync(0xffffffffu, is_fg(v0[k], thr, pol));
+            const unsigned hi = __ballot_sync(0xffffffffu, is_fg(v1[k], thr, pol));
+            if (lane == rb + k) my_m = (unsigned long long)lo | ((unsigned long long)hi << 32);
         }
     }
-    // gather the row's two 32-bit words (lanes 8r..8r+3 and 8r+4..8r+7)
-    unsigned wv = bits8 << (8 * (sg & 3));
-    wv |= __shfl_xor_sync(0xffffffffu, wv, 1);
-    wv |= __shfl_xor_sync(0xffffffffu, wv, 2);
-    if ((sg & 3) == 0) {
-        s_bits[r][sg >> 2] = wv;
-        const int wx = (x0 >> 5) + (sg >> 2);
-        if (y < D.Ly && wx < D.wpr) P.fgbits[D.word_off + (long long)y * D.wpr + wx] = wv;
-    }
-    for (int k = threadIdx.x; k < TSITES; k += TTHREADS) {
-        s_nsv[k] = 0;
-        s_su[k] = 0;
-    }
-    __syncthreads();
-
-    // 2. tile union-find
-    tile_union_find(s_bits, s_par);
-
-    // 3. piece sums, aggregated over runs of equal root within the thread
-    const int base = r * TW + sg * 8;
     {
-        int cur = -1, cnt = 0, su = 0;
-        int nroots = 0;
-        for (int i = 0; i < 8; ++i) {
-            const int p = s_par[base + i];
-            if (p == base + i) ++nroots;
-            if (p != cur) {
-                if (cur >= 0) {
-                    const int dv = r - (cur / TW);
-                    atomicAdd(&s_nsv[cur], (cnt << 16) + cnt * dv);
-                    atomicAdd(&s_su[cur], su);
-                }
-                cur = p;
-                cnt = 0;
-                su = 0;
-            }
-            if (p >= 0) {
-                ++cnt;
-                su += (sg * 8 + i) - (p % TW);
-            }
-        }
-        if (cur >= 0) {
-            const int dv = r - (cur / TW);
-            atomicAdd(&s_nsv[cur], (cnt << 16) + cnt * dv);
-            atomicAdd(&s_su[cur], su);
-        }
-        __syncthreads();
-
-        // 4. roots in raster order -> piece ids
-        int m;
-        const int rank0 = block_excl_scan(nroots, s_tmp, &m);
-        if (threadIdx.x == 0) {
-            int bse = atomicAdd(&P.g->n_pieces, m);
-            if (bse + m > P.piece_cap) {
-                atomicOr(&P.g->err, ERR_PIECE_CAP);
-                atomicOr(&P.st[inst].err, ERR_PIECE_CAP);
-                bse = -1;
-            }
-            s_base = bse;
-            P.tile_pbase[D.tile_off + t] = bse;
-            P.tile_pcnt[D.tile_off + t] = m;
-        }
-        __syncthreads();
-        const int pbase = s_base;
-        int rk = rank0;
-        for (int i = 0; i < 8; ++i) {
-            const int li = base + i;
-            if (s_par[li] == li) {
-                const int nsv = s_nsv[li];
-                int pid = -1;
-                if (pbase >= 0) {
-                    pid = pbase + rk;
-                    P.p_q[pid] = (y0 + r) * D.Lx + x0 + sg * 8 + i;
-                    P.p_inst[pid] = inst;
-                    P.p_n[pid] = nsv >> 16;
-                    P.p_sv[pid] = nsv & 0xFFFF;
-                    P.p_su[pid] = s_su[li];
-                    P.p_parent[pid] = pid;
-                    P.p_accn[pid] = 0;
-                    P.p_accx[pid] = 0;
-                    P.p_accy[pid] = 0;
-                }
-                ++rk;
-                s_nsv[li] = pid;   // only this thread touches a root's slot
-            }
+        const int y = y0 + lane;
+        const int wx = x0 >> 5;
+        if (y < Ly) {
+            unsigned* row = P.fgbits + D.word_off + (long long)y * D.wpr;
+            row[wx] = (unsigned)my_m;
+            if (wx + 1 < D.wpr) row[wx + 1] = (unsigned)(my_m >> 32);
         }
     }
-    __syncthreads();
+    TS.m[lane] = my_m;
+
+    // 2. union-find over runs
+    warp_runs_uf(TS, my_m);
+
+    // 3. sums per root run
+    const unsigned long long S0 = run_starts(my_m);
+    const int nr = __popcll(S0);
+    for (int j = 0; j < nr; ++j) {
+        TS.aux[lane * 32 + j] = 0;
+        TS.su[lane * 32 + j] = 0;
+    }
+    __syncwarp();
+    {
+        unsigned long long q = S0;
+        int j = 0;
+        while (q) {
+            const int c = __ffsll(q) - 1;
+            q &= q - 1;
+            const int len = run_length(my_m, c);
+            const int root = TS.par[lane * 32 + j];
+            const int rr = root >> 5;
+            const int cr = run_column(run_starts(TS.m[rr]), root & 31);
+            atomicAdd(&TS.aux[root], (len << 16) + len * (lane - rr));
+            atomicAdd(&TS.su[root], len * (c - cr) + (len * (len - 1)) / 2);
+            ++j;
+        }
+    }
+    __syncwarp();
+
+    // 4. roots in raster order -> piece ids
+    int rbase, m_tot;
+    const unsigned R = warp_roots(TS, my_m, &rbase, &m_tot);
+    int pbase = 0;
+    if (lane == 0) {
+        pbase = atomicAdd(&P.g->n_pieces, m_tot);
+        if (pbase + m_tot > P.piece_cap) {
+            atomicOr(&P.g->err, ERR_PIECE_CAP);
+            atomicOr(&P.st[inst].err, ERR_PIECE_CAP);
+            pbase = -1;
+        }
+        P.tile_pbase[D.tile_off + t] = pbase;
+        P.tile_pcnt[D.tile_off + t] = m_tot;
+    }
+    pbase = __shfl_sync(0xffffffffu, pbase, 0);
+    {
+        unsigned rq = R;
+        int k = rbase;
+        while (rq) {
+            const int j = __ffs(rq) - 1;
+            rq &= rq - 1;
+            const int id = lane * 32 + j;
+            int pid = -1;
+            if (pbase >= 0) {
+                pid = pbase + k;
+                const int nsv = TS.aux[id];
+                P.p_q[pid] = (y0 + lane) * Lx + x0 + run_column(S0, j);
+                P.p_inst[pid] = inst;
+                P.p_n[pid] = nsv >> 16;
+                P.p_sv[pid] = nsv & 0xFFFF;
+                P.p_su[pid] = TS.su[id];
+                P.p_parent[pid] = pid;
+                P.p_accn[pid] = 0;
+                P.p_accx[pid] = 0;
+                P.p_accy[pid] = 0;
+            }
+            ++k;
+            TS.aux[id] = pid;   // root slot now holds the piece id
+        }
+    }
+    __syncwarp();
 
     // 5. borders: [0,TH) left col, [TH,2TH) right col, [2TH,2TH+TW) top row, [.., +TW) bottom row
-    const int ncols = min(TW, D.Lx - x0), nrows = min(TH, D.Ly - y0);
+    const int ncols = min(TW, Lx - x0), nrows = min(TH, Ly - y0);
     int* bd = P.border + D.border_off + (long long)t * BORDER;
-    for (int k = threadIdx.x; k < BORDER; k += TTHREADS) {
+    for (int k = lane; k < BORDER; k += 32) {
         int lx, ly;
         if (k < TH) { ly = k; lx = 0; }
         else if (k < 2 * TH) { ly = k - TH; lx = ncols - 1; }
@@ -270,8 +278,8 @@ __global__ __launch_bounds__(TTHREADS) void k_ccl_tiles(Pools P, StepTable T) {
         else { lx = k - 2 * TH - TW; ly = nrows - 1; }
         int v = -1;
         if (lx < ncols && ly < nrows) {
-            const int p = s_par[ly * TW + lx];
-            if (p >= 0) v = s_nsv[p];
+            const unsigned long long m = TS.m[ly];
+            if ((m >> lx) & 1ull) v = TS.aux[TS.par[ly * 32 + run_index(run_starts(m), lx)]];
         }
         bd[k] = v;
     }
@@ -337,7 +345,7 @@ __global__ void k_ccl_flatten(Pools P) {
             const int q = P.p_q[pid];
             const int y = q / D.Lx, x = q - y * D.Lx;
             atomicOr(&P.rootbits[D.word_off + (long long)y * D.wpr + (x >> 5)], 1u << (x & 31));
-            atomicAdd(&P.st[inst].K, 1);
+            warp_add(&P.st[inst].K, 1);
         }
     }
 }
@@ -372,57 +380,62 @@ __global__ void k_comp_accum(Pools P) {
             atomicAdd((unsigned long long*)&P.p_accx[r], (unsigned long long)(nn * dx + P.p_su[pid]));
             atomicAdd((unsigned long long*)&P.p_accy[r], (unsigned long long)(nn * dy + P.p_sv[pid]));
         } else {
-            const int w = atomicAdd(&P.g->n_wide, 1);
+            const int w = warp_fetch_inc(&P.g->n_wide);
             P.wide[w] = pid;
         }
     }
 }
 
 // exact per-site sums for pieces whose minimum image is not a single shift
-__global__ __launch_bounds__(TTHREADS) void k_comp_wide(Pools P) {
-    __shared__ unsigned s_bits[TH][2];
-    __shared__ int s_par[TSITES];
-    __shared__ long long s_red[3][TTHREADS / 32];
+// (one warp per piece; warps of a block work on different pieces)
+constexpr int WIDE_WARPS = 4;
+__global__ __launch_bounds__(32 * WIDE_WARPS) void k_comp_wide(Pools P) {
+    __shared__ UfSmem s_tile[WIDE_WARPS];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    UfSmem& TS = s_tile[w];
     const int nw = P.g->n_wide;
-    for (int w = blockIdx.x; w < nw; w += gridDim.x) {
-        const int pid = P.wide[w];
+    for (int k = blockIdx.x * WIDE_WARPS + w; k < nw; k += gridDim.x * WIDE_WARPS) {
+        const int pid = P.wide[k];
         const int inst = P.p_inst[pid];
-        const InstDesc D = P.desc[inst];
+        const InstDesc& D = P.desc[inst];
         const int q = P.p_q[pid];
         const int yq = q / D.Lx, xq = q - yq * D.Lx;
         const int x0 = (xq / TW) * TW, y0 = (yq / TH) * TH;
         const int r = P.p_parent[pid];
         const int qr = P.p_q[r];
         const int yr = qr / D.Lx, xr = qr - yr * D.Lx;
-        load_tile_bits(P, D, x0, y0, s_bits);
-        tile_union_find(s_bits, s_par);
-        const int lq = (yq - y0) * TW + (xq - x0);
+        const unsigned long long m = load_row_mask(P, D, x0, y0);
+        TS.m[lane] = m;
+        warp_runs_uf(TS, m);
+        const unsigned long long Sq = run_starts(TS.m[yq - y0]);
+        const int lq = (yq - y0) * 32 + run_index(Sq, xq - x0);
+        const unsigned long long S = run_starts(m);
         long long n = 0, sx = 0, sy = 0;
-        const int rr = threadIdx.x >> 3, sg = threadIdx.x & 7;
-        for (int i = 0; i < 8; ++i) {
-            const int li = rr * TW + sg * 8 + i;
-            if (s_par[li] == lq) {
-                ++n;
-                sx += wrap_ll((x0 + sg * 8 + i) - xr, D.Lx);
-                sy += wrap_ll((y0 + rr) - yr, D.Ly);
+        unsigned long long t = S;
+        int j = 0;
+        const long long dy = wrap_ll((y0 + lane) - yr, D.Ly);
+        while (t) {
+            const int c = __ffsll(t) - 1;
+            t &= t - 1;
+            if (TS.par[lane * 32 + j] == lq) {
+                const int len = run_length(m, c);
+                for (int i = 0; i < len; ++i) sx += wrap_ll((x0 + c + i) - xr, D.Lx);
+                n += len;
+                sy += len * dy;
             }
+            ++j;
         }
         for (int o = 16; o > 0; o >>= 1) {
             n += __shfl_xor_sync(0xffffffffu, n, o);
             sx += __shfl_xor_sync(0xffffffffu, sx, o);
             sy += __shfl_xor_sync(0xffffffffu, sy, o);
         }
-        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-        if (lane == 0) { s_red[0][warp] = n; s_red[1][warp] = sx; s_red[2][warp] = sy; }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            long long a0 = 0, a1 = 0, a2 = 0;
-            for (int k = 0; k < TTHREADS / 32; ++k) { a0 += s_red[0][k]; a1 += s_red[1][k]; a2 += s_red[2][k]; }
-            atomicAdd((unsigned long long*)&P.p_accn[r], (unsigned long long)a0);
-            atomicAdd((unsigned long long*)&P.p_accx[r], (unsigned long long)a1);
-            atomicAdd((unsigned long long*)&P.p_accy[r], (unsigned long long)a2);
+        if (lane == 0) {
+            atomicAdd((unsigned long long*)&P.p_accn[r], (unsigned long long)n);
+            atomicAdd((unsigned long long*)&P.p_accx[r], (unsigned long long)sx);
+            atomicAdd((unsigned long long*)&P.p_accy[r], (unsigned long long)sy);
         }
-        __syncthreads();
+        __syncwarp();
     }
 }
 
@@ -474,145 +487,146 @@ __global__ void k_bucket_scatter(Pools P) {
 // Label pass: final labels from the stored bits; overlap histogram with the
 // previous frame's labels (Section 3.2.3)
 // ---------------------------------------------------------------------------
-constexpr int OSET = 256;
-
 __device__ __forceinline__ void ovl_global_insert(const Pools& P, const InstDesc& D, int inst,
                                                   unsigned long long key, unsigned cnt) {
     unsigned long long* H = P.ohash + D.ohash_off;
     unsigned* V = P.oval + D.ohash_off;
-    unsigned h = (unsigned)hash64(key) & (unsigned)D.ohash_mask;
-    for (int probe = 0; probe <= D.ohash_mask; ++probe) {
+    const InstState& S = P.st[inst];
+    const unsigned mask = dyn_mask(D.ohash_mask, 8ll * ((long long)S.K + S.K_prev) + 64);
+    unsigned h = (unsigned)hash64(key) & mask;
+    for (unsigned probe = 0; probe <= mask; ++probe) {
         const unsigned long long k = atomicCAS(&H[h], EMPTY_KEY, key);
         if (k == EMPTY_KEY || k == key) {
             atomicAdd(&V[h], cnt);
             if (k == EMPTY_KEY) {
-                const int idx = atomicAdd(&P.st[inst].n_ovl, 1);
+                const int idx = warp_fetch_inc(&P.st[inst].n_ovl);
                 if (idx < D.ovl_cap) P.olist[D.ovl_off + idx] = (int)h;
                 else atomicOr(&P.st[inst].err, ERR_OVL_CAP);
             }
             return;
         }
-        h = (h + 1) & (unsigned)D.ohash_mask;
+        h = (h + 1) & mask;
     }
     atomicOr(&P.st[inst].err, ERR_OVL_CAP);
 }
 
-__device__ __forceinline__ void ovl_add(unsigned long long* s_key, unsigned* s_cnt, const Pools& P,
-                                        const InstDesc& D, int inst, unsigned long long key, unsigned cnt) {
-    unsigned h = (unsigned)hash64(key) & (OSET - 1);
-    for (int probe = 0; probe < OSET; ++probe) {
-        const unsigned long long k = atomicCAS(&s_key[h], EMPTY_KEY, key);
-        if (k == EMPTY_KEY || k == key) {
-            atomicAdd(&s_cnt[h], cnt);
+constexpr int LBL_WARPS = 4;    // tiles per block in the label pass
+constexpr int WSET = 128;       // per-warp overlap set
+
+__device__ __forceinline__ void ovl_add_w(unsigned long long* key, unsigned* cnt, const Pools& P, const InstDesc& D,
+                                          int inst, unsigned long long k, unsigned c) {
+    unsigned h = (unsigned)hash64(k) & (WSET - 1);
+    for (int probe = 0; probe < WSET; ++probe) {
+        const unsigned long long o = atomicCAS(&key[h], EMPTY_KEY, k);
+        if (o == EMPTY_KEY || o == k) {
+            atomicAdd(&cnt[h], c);
             return;
         }
-        h = (h + 1) & (OSET - 1);
+        h = (h + 1) & (WSET - 1);
     }
-    ovl_global_insert(P, D, inst, key, cnt);   // shared set full
+    ovl_global_insert(P, D, inst, k, c);   // set full
 }
 
-__global__ __launch_bounds__(TTHREADS) void k_labels(Pools P, StepTable T) {
-    __shared__ unsigned s_bits[TH][2];
-    __shared__ int s_par[TSITES];
-    __shared__ int s_comp[TSITES];
-    __shared__ int s_tmp[TTHREADS / 32];
-    __shared__ unsigned long long s_key[OSET];
-    __shared__ unsigned s_cnt[OSET];
-
-    const int b = blockIdx.x;
+__global__ __launch_bounds__(32 * LBL_WARPS) void k_labels(Pools P, StepTable T) {
+    __shared__ LabelSmem s_tile[LBL_WARPS];
+    __shared__ unsigned long long s_key[LBL_WARPS][WSET];
+    __shared__ unsigned s_cnt[LBL_WARPS][WSET];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int b = blockIdx.x * LBL_WARPS + w;
+    if (b >= T.tileA_pre[T.n_act]) return;
+    LabelSmem& TS = s_tile[w];
+    unsigned long long* skey = s_key[w];
+    unsigned* scnt = s_cnt[w];
     const int a = seg_of_int(T.tileA_pre, T.n_act, b);
     const int inst = T.act[a];
-    const InstDesc D = P.desc[inst];
+    const InstDesc& D = P.desc[inst];
     const InstState& S = P.st[inst];
     const int t = b - T.tileA_pre[a];
     const int tx = t % D.ntx, ty = t / D.ntx;
     const int x0 = tx * TW, y0 = ty * TH;
     const int now = S.slot ^ 1;
     const bool with_prev = S.has_prev != 0;
+    const int Lx = D.Lx;
 
-    for (int k = threadIdx.x; k < OSET; k += TTHREADS) {
-        s_key[k] = EMPTY_KEY;
-        s_cnt[k] = 0;
+    for (int k = lane; k < WSET; k += 32) {
+        skey[k] = EMPTY_KEY;
+        scnt[k] = 0;
     }
-    load_tile_bits(P, D, x0, y0, s_bits);
-    tile_union_find(s_bits, s_par);
-
-    const int r = threadIdx.x >> 3, sg = threadIdx.x & 7;
-    const int base = r * TW + sg * 8;
-    int nroots = 0;
-    for (int i = 0; i < 8; ++i) nroots += (s_par[base + i] == base + i);
-    int m;
-    int rk = block_excl_scan(nroots, s_tmp, &m);
-    const int pbase = P.tile_pbase[D.tile_off + t];
-    for (int i = 0; i < 8; ++i) {
-        const int li = base + i;
-        if (s_par[li] == li) {
-            int c = -1;
-            if (pbase >= 0) c = P.p_comp[P.p_parent[pbase + rk]];
-            s_comp[li] = c;
-            ++rk;
+    const unsigned long long my_m = load_row_mask(P, D, x0, y0);
+    TS.m[lane] = my_m;
+    warp_runs_uf(TS, my_m);
+    {
+        int rbase, m_tot;
+        const unsigned R = warp_roots(TS, my_m, &rbase, &m_tot);
+        const int pbase = P.tile_pbase[D.tile_off + t];
+        unsigned rq = R;
+        int k = rbase;
+        while (rq) {
+            const int j = __ffs(rq) - 1;
+            rq &= rq - 1;
+            TS.aux[lane * 32 + j] = pbase >= 0 ? P.p_comp[P.p_parent[pbase + k]] : -1;
+            ++k;
         }
     }
-    __syncthreads();
+    __syncwarp();
 
-    const int y = y0 + r, xs = x0 + sg * 8;
-    if (y < D.Ly && xs < D.Lx) {
-        int lab[8];
+    // labels, row by row: lane l writes columns l and l+32 (coalesced)
+    const bool in0 = x0 + lane < Lx, in1 = x0 + 32 + lane < Lx;
+    const int nrows = min(TH, D.Ly - y0);
+    int* out = P.labels[now] + D.site_off + (long long)y0 * Lx + x0 + lane;
+    const int* prv = P.labels[now ^ 1] + D.site_off + (long long)y0 * Lx + x0 + lane;
+    unsigned long long cur0 = EMPTY_KEY, cur1 = EMPTY_KEY;
+    unsigned c0 = 0, c1 = 0;
+    for (int rb = 0; rb < nrows; rb += 8) {
+        // past labels of 8 rows in flight at once
+        int p0[8], p1[8];
 #pragma unroll
-        for (int i = 0; i < 8; ++i) {
-            const int p = s_par[base + i];
-            lab[i] = p >= 0 ? s_comp[p] : -1;
+        for (int k = 0; k < 8; ++k) {
+            const int r = rb + k;
+            const bool ok = with_prev && r < nrows;
+            p0[k] = (ok && in0) ? __ldcs(prv + (long long)r * Lx) : -1;
+            p1[k] = (ok && in1) ? __ldcs(prv + (long long)r * Lx + 32) : -1;
         }
-        int* out = P.labels[now] + D.site_off + (long long)y * D.Lx + xs;
-        const int* prv = P.labels[now ^ 1] + D.site_off + (long long)y * D.Lx + xs;
-        int pl[8];
-        const bool vec = (xs + 8 <= D.Lx) && ((reinterpret_cast<uintptr_t>(out) & 15u) == 0);
-        if (vec) {
-            reinterpret_cast<int4*>(out)[0] = make_int4(lab[0], lab[1], lab[2], lab[3]);
-            reinterpret_cast<int4*>(out)[1] = make_int4(lab[4], lab[5], lab[6], lab[7]);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const int r = rb + k;
+            if (r >= nrows) break;
+            const unsigned long long m = TS.m[r];
+            const unsigned long long Sr = run_starts(m);
+            const int l0 = ((m >> lane) & 1ull) ? TS.aux[TS.par[r * 32 + run_index(Sr, lane)]] : -1;
+            const int l1 = ((m >> (lane + 32)) & 1ull) ? TS.aux[TS.par[r * 32 + run_index(Sr, lane + 32)]] : -1;
+            if (in0) out[(long long)r * Lx] = l0;
+            if (in1) out[(long long)r * Lx + 32] = l1;
             if (with_prev) {
-                const int4 u = __ldcs(reinterpret_cast<const int4*>(prv));
-                const int4 w = __ldcs(reinterpret_cast<const int4*>(prv) + 1);
-                pl[0] = u.x; pl[1] = u.y; pl[2] = u.z; pl[3] = u.w;
-                pl[4] = w.x; pl[5] = w.y; pl[6] = w.z; pl[7] = w.w;
-            }
-        } else {
-            for (int i = 0; i < 8; ++i) {
-                if (xs + i < D.Lx) {
-                    out[i] = lab[i];
-                    pl[i] = with_prev ? prv[i] : -1;
-                } else {
-                    pl[i] = -1;
+                // aggregate equal (past, now) pairs down each column
+                const unsigned long long k0 = (l0 >= 0 && p0[k] >= 0) ? (((unsigned long long)(unsigned)p0[k] << 32) | (unsigned)l0) : EMPTY_KEY;
+                const unsigned long long k1 = (l1 >= 0 && p1[k] >= 0) ? (((unsigned long long)(unsigned)p1[k] << 32) | (unsigned)l1) : EMPTY_KEY;
+                if (k0 != cur0) {
+                    if (cur0 != EMPTY_KEY) ovl_add_w(skey, scnt, P, D, inst, cur0, c0);
+                    cur0 = k0;
+                    c0 = 0;
                 }
-            }
-        }
-        if (with_prev) {
-            unsigned long long cur = EMPTY_KEY;
-            unsigned cnt = 0;
-            for (int i = 0; i < 8; ++i) {
-                const bool inb = (xs + i < D.Lx);
-                const bool both = inb && lab[i] >= 0 && pl[i] >= 0;
-                const unsigned long long key =
-                    both ? (((unsigned long long)(unsigned)pl[i] << 32) | (unsigned)lab[i]) : EMPTY_KEY;
-                if (key != cur) {
-                    if (cur != EMPTY_KEY) ovl_add(s_key, s_cnt, P, D, inst, cur, cnt);
-                    cur = key;
-                    cnt = 0;
+                if (k0 != EMPTY_KEY) ++c0;
+                if (k1 != cur1) {
+                    if (cur1 != EMPTY_KEY) ovl_add_w(skey, scnt, P, D, inst, cur1, c1);
+                    cur1 = k1;
+                    c1 = 0;
                 }
-                if (both) ++cnt;
+                if (k1 != EMPTY_KEY) ++c1;
             }
-            if (cur != EMPTY_KEY) ovl_add(s_key, s_cnt, P, D, inst, cur, cnt);
         }
     }
     if (with_prev) {
-        __syncthreads();
-        for (int k = threadIdx.x; k < OSET; k += TTHREADS)
-            if (s_key[k] != EMPTY_KEY) ovl_global_insert(P, D, inst, s_key[k], s_cnt[k]);
+        if (cur0 != EMPTY_KEY) ovl_add_w(skey, scnt, P, D, inst, cur0, c0);
+        if (cur1 != EMPTY_KEY) ovl_add_w(skey, scnt, P, D, inst, cur1, c1);
+        __syncwarp();
+        for (int k = lane; k < WSET; k += 32)
+            if (skey[k] != EMPTY_KEY) ovl_global_insert(P, D, inst, skey[k], scnt[k]);
     }
 }
 
 void launch_ccl_tiles(const Launch& L) {
-    k_ccl_tiles<<<L.total_tilesA, TTHREADS, 0, L.s>>>(L.P, L.T);
+    k_ccl_tiles<<<(L.total_tilesA + CCL_WARPS - 1) / CCL_WARPS, 32 * CCL_WARPS, 0, L.s>>>(L.P, L.T);
     ++*L.nlaunch;
 }
 
@@ -627,7 +641,7 @@ void launch_ccl_rest(const Launch& L) {
     launch_scan(L, SCAN_ROOTBITS);
     k_comp_accum<<<L.grid_items, 256, 0, L.s>>>(L.P);
     ++*L.nlaunch;
-    k_comp_wide<<<L.grid_items, TTHREADS, 0, L.s>>>(L.P);
+    k_comp_wide<<<L.grid_items, 32 * WIDE_WARPS, 0, L.s>>>(L.P);
     ++*L.nlaunch;
     k_comp_final<<<L.grid_items, 256, 0, L.s>>>(L.P);
     ++*L.nlaunch;
@@ -637,7 +651,7 @@ void launch_ccl_rest(const Launch& L) {
 }
 
 void launch_labels(const Launch& L) {
-    k_labels<<<L.total_tilesA, TTHREADS, 0, L.s>>>(L.P, L.T);
+    k_labels<<<(L.total_tilesA + LBL_WARPS - 1) / LBL_WARPS, 32 * LBL_WARPS, 0, L.s>>>(L.P, L.T);
     ++*L.nlaunch;
 }
 

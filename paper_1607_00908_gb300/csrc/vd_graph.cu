@@ -175,7 +175,7 @@ __global__ void k_match_phi(Pools P, StepTable T) {
             if (w != 0ull && unpack_label(w) == (int)p) {
                 res = n;
                 P.inv[D.comp_off + n] = (int)p;
-                atomicAdd(&P.st[inst].n_matched, 1);
+                warp_add(&P.st[inst].n_matched, 1);
             }
         }
         P.phi[D.comp_off + p] = res;
@@ -200,7 +200,7 @@ __global__ void k_translate_count(Pools P, StepTable T) {
             atomicAdd(&P.tdeg[D.comp_off + min(pa, pb)], 1);
             ++cnt;
         }
-        if (cnt) atomicAdd(&P.st[inst].n_tedges, cnt);
+        warp_add(&P.st[inst].n_tedges, cnt);
     });
 }
 
@@ -287,8 +287,8 @@ __device__ __forceinline__ void compare_row(const Pools& P, int inst, int a) {
     if (!WRITE) {
         P.fcnt[co + a] = nb;
         P.fcnt_a[co + a] = na;
-        if (nb) atomicAdd(&P.st[inst].n_break, nb);
-        if (na) atomicAdd(&P.st[inst].n_arise, na);
+        warp_add(&P.st[inst].n_break, nb);
+        warp_add(&P.st[inst].n_arise, na);
     }
 }
 

@@ -251,6 +251,36 @@ __device__ __forceinline__ unsigned long long hash64(unsigned long long k) {
     return k;
 }
 
+// Warp-aggregated atomic add: lanes that target the same counter are grouped,
+// one lane adds the group's sum (far fewer same-address atomics).
+__device__ __forceinline__ void warp_add(int* p, int v) {
+    const unsigned act = __activemask();
+    const unsigned grp = __match_any_sync(act, (unsigned long long)p);
+    const int sum = __reduce_add_sync(grp, (unsigned)v);
+    if ((int)(threadIdx.x & 31) == __ffs(grp) - 1) atomicAdd(p, sum);
+}
+
+// Warp-aggregated fetch-and-increment: returns a unique old value per lane.
+__device__ __forceinline__ int warp_fetch_inc(int* p) {
+    const unsigned act = __activemask();
+    const unsigned grp = __match_any_sync(act, (unsigned long long)p);
+    const int lane = threadIdx.x & 31;
+    const int leader = __ffs(grp) - 1;
+    int base = 0;
+    if (lane == leader) base = atomicAdd(p, __popc(grp));
+    base = __shfl_sync(grp, base, leader);
+    return base + __popc(grp & ((1u << lane) - 1u));
+}
+
+// Hash tables are allocated for the worst case but used per frame with a
+// power-of-two size proportional to the bubble count (small enough to stay in
+// L2): returns (2^k - 1) with 2^k >= want, capped by the allocated mask.
+__device__ __forceinline__ unsigned dyn_mask(int alloc_mask, long long want) {
+    unsigned p = 63u;
+    while ((long long)p + 1 < want && p < (unsigned)alloc_mask) p = (p << 1) | 1u;
+    return p < (unsigned)alloc_mask ? p : (unsigned)alloc_mask;
+}
+
 __device__ __forceinline__ unsigned long long edge_key(int a, int b) {
     int lo = a < b ? a : b, hi = a < b ? b : a;
     return ((unsigned long long)(unsigned)lo << 32) | (unsigned)hi;

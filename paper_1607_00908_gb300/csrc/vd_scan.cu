@@ -152,6 +152,8 @@ __global__ __launch_bounds__(SCAN_THREADS) void k_scan(Pools P, StepTable T, int
     const long long total = seg[n];
     const unsigned epoch = *(volatile unsigned*)&P.g->scan_epoch;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    // blocks beyond the number of tiles never take a ticket
+    if ((long long)blockIdx.x * SCAN_TILE >= total) return;
 
     for (;;) {
         if (threadIdx.x == 0) s_tile = atomicAdd(&P.g->scan_ticket, 1);
@@ -200,34 +202,47 @@ __global__ __launch_bounds__(SCAN_THREADS) void k_scan(Pools P, StepTable T, int
         }
         const int texcl = wpre + inc - tsum;
 
-        if (threadIdx.x == 0) {
+        if (warp == 0) {
+            // warp-parallel decoupled look-back over windows of 32 predecessors
             unsigned long long* flags = P.scan_flags;
             long long excl = 0;
             if (tile == 0) {
-                publish(&flags[0], epoch, ST_INC, btot);
+                if (lane == 0) publish(&flags[0], epoch, ST_INC, btot);
             } else {
-                publish(&flags[tile], epoch, ST_AGG, btot);
-                long long t = tile - 1;
+                if (lane == 0) publish(&flags[tile], epoch, ST_AGG, btot);
+                long long top = tile - 1;
                 int spins = 0;
-                while (t >= 0) {
-                    unsigned long long f = *(volatile unsigned long long*)&flags[t];
-                    unsigned fe = (unsigned)(f >> 34);
-                    unsigned fs = (unsigned)(f >> 32) & 3u;
-                    if (fe != epoch || fs == 0) {
+                for (;;) {
+                    const long long idx = top - lane;
+                    bool ready = true, inc = true;
+                    int val = 0;
+                    if (idx >= 0) {
+                        const unsigned long long f = *(volatile unsigned long long*)&flags[idx];
+                        const unsigned fe = (unsigned)(f >> 34), fs = (unsigned)(f >> 32) & 3u;
+                        ready = (fe == epoch) && fs != 0u;
+                        inc = ready && fs == ST_INC;
+                        val = (int)(unsigned)f;
+                    }
+                    const unsigned incm = __ballot_sync(0xffffffffu, inc);
+                    const unsigned nrdy = __ballot_sync(0xffffffffu, !ready);
+                    const int first = incm ? __ffs(incm) - 1 : 31;
+                    const unsigned need = (first >= 31) ? 0xffffffffu : ((2u << first) - 1u);
+                    if (nrdy & need) {
                         if (++spins > SPIN_LIMIT) {   // give up: flag the error, never hang
-                            atomicOr(&P.g->err, ERR_TIMEOUT);
+                            if (lane == 0) atomicOr(&P.g->err, ERR_TIMEOUT);
                             break;
                         }
                         continue;
                     }
                     __threadfence();
-                    excl += (int)(unsigned)f;
-                    if (fs == ST_INC) break;
-                    --t;
+                    const int part = __reduce_add_sync(0xffffffffu, (unsigned)((lane <= first) ? val : 0));
+                    excl += part;
+                    if (incm) break;
+                    top -= 32;
                 }
-                publish(&flags[tile], epoch, ST_INC, (int)(excl + btot));
+                if (lane == 0) publish(&flags[tile], epoch, ST_INC, (int)(excl + btot));
             }
-            s_excl = excl;
+            if (lane == 0) s_excl = excl;
         }
         __syncthreads();
         long long run = s_excl + texcl;

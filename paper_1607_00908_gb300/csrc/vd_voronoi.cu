@@ -19,30 +19,6 @@
 
 namespace vd {
 
-__device__ __forceinline__ long long floordiv_i(long long a, long long b) {
-    long long d = a / b;
-    if ((a % b != 0) && ((a < 0) != (b < 0))) --d;
-    return d;
-}
-
-// unwrapped bucket geometry along one axis (L sites, bucket side B, nb buckets)
-__device__ __forceinline__ long long bucket_start(long long j, int L, int B, int nb) {
-    const long long per = floordiv_i(j, nb);
-    const long long jm = j - per * nb;
-    return per * L + jm * B;
-}
-__device__ __forceinline__ long long bucket_end(long long j, int L, int B, int nb) {
-    const long long per = floordiv_i(j, nb);
-    const long long jm = j - per * nb;
-    const long long e = (jm + 1) * B;
-    return per * L + (e < L ? e : L);
-}
-__device__ __forceinline__ long long bucket_of_pos(long long p, int L, int B, int nb) {
-    const long long per = floordiv_i(p, L);
-    const long long pm = p - per * L;
-    return per * nb + pm / B;
-}
-
 // distance from a point (offset d of the point from the interval start, already
 // reduced to [-M/2, M/2)) to an interval [0, W] on a ring of length M
 __device__ __forceinline__ long long ring_mindist(long long d, long long W, long long M) {
@@ -90,18 +66,19 @@ __device__ unsigned long long plaquette_key(int A, int B, int C, int D, const in
 __device__ __forceinline__ void edge_global_insert(const Pools& P, const InstDesc& D, int inst,
                                                    unsigned long long key) {
     unsigned long long* H = P.ehash + D.ehash_off;
-    unsigned h = (unsigned)hash64(key) & (unsigned)D.ehash_mask;
-    for (int probe = 0; probe <= D.ehash_mask; ++probe) {
+    const unsigned mask = dyn_mask(D.ehash_mask, 16ll * P.st[inst].K + 64);
+    unsigned h = (unsigned)hash64(key) & mask;
+    for (unsigned probe = 0; probe <= mask; ++probe) {
         const unsigned long long k = atomicCAS(&H[h], EMPTY_KEY, key);
         if (k == EMPTY_KEY) {
-            const int idx = atomicAdd(&P.st[inst].n_edge_list, 1);
+            const int idx = warp_fetch_inc(&P.st[inst].n_edge_list);
             if (idx < D.edge_cap) P.elist[D.edge_off + idx] = (int)h;
             else atomicOr(&P.st[inst].err, ERR_EDGE_CAP);
             atomicAdd(&P.deg[D.comp_off + (int)(key >> 32)], 1);
             return;
         }
         if (k == key) return;
-        h = (h + 1) & (unsigned)D.ehash_mask;
+        h = (h + 1) & mask;
     }
     atomicOr(&P.st[inst].err, ERR_EDGE_CAP);
 }
@@ -117,14 +94,32 @@ __device__ __forceinline__ void edge_add(unsigned long long* s_set, const Pools&
     edge_global_insert(P, D, inst, key);
 }
 
+constexpr int WCAND = 64;   // per-warp candidate list
+
+// Exact owner over a candidate list with int64 distances (rel. coordinates,
+// no wrap needed), ties to the smallest label.
+__device__ __forceinline__ int owner_exact(long long sx, long long sy, const int* cx, const int* cy, const int* id,
+                                           int n) {
+    long long best = LLONG_MAX;
+    int bi = -1;
+    for (int j = 0; j < n; ++j) {
+        const long long dx = sx - cx[j], dy = sy - cy[j];
+        const long long d2 = dx * dx + dy * dy;
+        if (d2 < best || (d2 == best && id[j] < bi)) { best = d2; bi = id[j]; }
+    }
+    return bi;
+}
+
 __global__ __launch_bounds__(VTHREADS) void k_voronoi(Pools P, StepTable T) {
+    // centres scanned by the ring search, relative to the tile origin (minimum image)
     __shared__ int s_cx[VCAND], s_cy[VCAND], s_id[VCAND];
-    __shared__ long long s_md[VCAND];
+    // per-warp candidate lists of each warp's 16 x 8 patch
+    __shared__ float s_wfx[8][WCAND], s_wfy[8][WCAND];
+    __shared__ int s_wix[8][WCAND], s_wiy[8][WCAND], s_wid[8][WCAND];
     __shared__ int s_own[VH + 1][VW + 1];
     __shared__ unsigned long long s_set[VEDGESET];
-    __shared__ int s_n;
-    __shared__ int s_overflow;
-    __shared__ long long s_U;
+    __shared__ int s_n, s_over;
+    __shared__ unsigned long long s_U;
 
     const int b = blockIdx.x;
     const int a = seg_of_int(T.tileV_pre, T.n_act, b);
@@ -135,152 +130,281 @@ __global__ __launch_bounds__(VTHREADS) void k_voronoi(Pools P, StepTable T) {
     const int tx = t % D.vtx, ty = t / D.vtx;
     const int x0 = tx * VW, y0 = ty * VH;
     const int ncols = min(VW, D.Lx - x0), nrows = min(VH, D.Ly - y0);
-    const int now = S.slot ^ 1;
     const int K = min(S.K, D.comp_cap);
     const long long MX = (long long)Q * D.Lx, MY = (long long)Q * D.Ly;
+    const long long X0 = (long long)Q * x0, Y0 = (long long)Q * y0;
+    const long long WR = (long long)Q * ncols, HR = (long long)Q * nrows;   // region incl. halo
     const int2* cq = P.cq + D.comp_off;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
     for (int k = threadIdx.x; k < VEDGESET; k += VTHREADS) s_set[k] = EMPTY_KEY;
-    if (threadIdx.x == 0) { s_n = 0; s_overflow = 0; }
+    if (threadIdx.x == 0) {
+        s_n = 0;
+        s_over = 0;
+        s_U = ULLONG_MAX;
+    }
     __syncthreads();
 
-    if (K > 0 && threadIdx.x < 32) {
-        // ---- candidate search (one warp) ----
-        const int lane = threadIdx.x;
+    if (K > 0) {
+        // ---- ring search over the bucket grid (all threads) ----
+        // Bucket indices are unwrapped (they may run below 0 or past nb-1 by
+        // less than one period); all arithmetic is 32-bit here.
         const int Bk = S.B, nbx = S.nbx, nby = S.nby;
-        const long long X0 = (long long)Q * x0, Y0 = (long long)Q * y0;
-        const long long WR = (long long)Q * ncols, HR = (long long)Q * nrows;   // region incl. halo
-        const long long bx0 = bucket_of_pos(x0, D.Lx, Bk, nbx), bx1 = bucket_of_pos(x0 + ncols, D.Lx, Bk, nbx);
-        const long long by0 = bucket_of_pos(y0, D.Ly, Bk, nby), by1 = bucket_of_pos(y0 + nrows, D.Ly, Bk, nby);
+        const int bx0 = x0 / Bk, bx1 = (x0 + ncols) >= D.Lx ? nbx : (x0 + ncols) / Bk;
+        const int by0 = y0 / Bk, by1 = (y0 + nrows) >= D.Ly ? nby : (y0 + nrows) / Bk;
         const int* boff = P.boff + D.bucket_off;
         const int2* bcq = P.bcq + D.comp_off;
         const int* bid = P.bid + D.comp_off;
-        long long U = LLONG_MAX;
-        long long px0 = 0, px1 = -1, py0 = 0, py1 = -1;
+        int px0 = 0, px1 = -1, py0 = 0, py1 = -1;
         bool pfx = false, pfy = false, have_prev = false;
+        unsigned long long myU = ULLONG_MAX;
         for (int r = 0;; ++r) {
-            long long rx0 = bx0 - r, rx1 = bx1 + r, ry0 = by0 - r, ry1 = by1 + r;
+            int rx0 = bx0 - r, rx1 = bx1 + r, ry0 = by0 - r, ry1 = by1 + r;
             const bool fx = (rx1 - rx0 + 1) >= nbx, fy = (ry1 - ry0 + 1) >= nby;
             if (fx) { rx0 = 0; rx1 = nbx - 1; }
             if (fy) { ry0 = 0; ry1 = nby - 1; }
-            const long long wx = rx1 - rx0 + 1, wy = ry1 - ry0 + 1;
-            const long long ncell = wx * wy;
-            for (long long k = lane; k < ncell; k += 32) {
-                const long long cu = rx0 + k % wx, rv = ry0 + k / wx;
-                if (have_prev) {
-                    const bool inx = pfx || ((((cu - px0) % nbx) + nbx) % nbx) <= (px1 - px0);
-                    const bool iny = pfy || ((((rv - py0) % nby) + nby) % nby) <= (py1 - py0);
-                    if (inx && iny) continue;
+            const int wx = rx1 - rx0 + 1, wy = ry1 - ry0 + 1;
+            const int ncell = wx * wy;
+            for (int kb = warp * 32; kb < ncell; kb += VTHREADS) {   // warp-uniform loop
+                const int k = kb + lane;
+                int jb = 0, je = 0;
+                if (k < ncell) {
+                    const int kr = k / wx;
+                    const int cu = rx0 + (k - kr * wx), rv = ry0 + kr;
+                    bool skip = false;
+                    if (have_prev) {
+                        int dxp = cu - px0, dyp = rv - py0;
+                        if (dxp < 0) dxp += nbx; else if (dxp >= nbx) dxp -= nbx;
+                        if (dyp < 0) dyp += nby; else if (dyp >= nby) dyp -= nby;
+                        skip = (pfx || dxp <= px1 - px0) && (pfy || dyp <= py1 - py0);
+                    }
+                    if (!skip) {
+                        const int cm = cu < 0 ? cu + nbx : (cu >= nbx ? cu - nbx : cu);
+                        const int rm = rv < 0 ? rv + nby : (rv >= nby ? rv - nby : rv);
+                        const int bk = rm * nbx + cm;
+                        jb = boff[bk];
+                        je = boff[bk + 1];
+                    }
                 }
-                const long long cm = ((cu % nbx) + nbx) % nbx, rm = ((rv % nby) + nby) % nby;
-                const int bk = (int)(rm * nbx + cm);
-                const int e = boff[bk + 1];
-                for (int j = boff[bk]; j < e; ++j) {
+                // one shared-memory reservation per warp
+                const int cnt = je - jb;
+                int inc = cnt;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int y = __shfl_up_sync(0xffffffffu, inc, o);
+                    if (lane >= o) inc += y;
+                }
+                const int tot = __shfl_sync(0xffffffffu, inc, 31);
+                int base = 0;
+                if (lane == 31 && tot > 0) base = atomicAdd(&s_n, tot);
+                base = __shfl_sync(0xffffffffu, base, 31) + inc - cnt;
+                for (int j = jb; j < je; ++j, ++base) {
                     const int2 c = bcq[j];
                     const long long ddx = wrapM((long long)c.x - X0, MX);
                     const long long ddy = wrapM((long long)c.y - Y0, MY);
-                    const long long mnx = ring_mindist(ddx, WR, MX), mny = ring_mindist(ddy, HR, MY);
                     long long mxx = max(ddx < 0 ? -ddx : ddx, (ddx - WR) < 0 ? WR - ddx : ddx - WR);
                     long long mxy = max(ddy < 0 ? -ddy : ddy, (ddy - HR) < 0 ? HR - ddy : ddy - HR);
                     mxx = min(mxx, MX >> 1);
                     mxy = min(mxy, MY >> 1);
-                    const long long mind = mnx * mnx + mny * mny;
-                    const long long maxd = mxx * mxx + mxy * mxy;
-                    if (maxd < U) U = maxd;
-                    if (mind <= U) {
-                        const int pos = atomicAdd(&s_n, 1);
-                        if (pos < VCAND) {
-                            s_cx[pos] = c.x;
-                            s_cy[pos] = c.y;
-                            s_id[pos] = bid[j];
-                            s_md[pos] = mind;
-                        } else {
-                            s_overflow = 1;
-                        }
+                    const unsigned long long u = (unsigned long long)(mxx * mxx + mxy * mxy);
+                    myU = u < myU ? u : myU;
+                    if (base < VCAND) {
+                        s_cx[base] = (int)ddx;
+                        s_cy[base] = (int)ddy;
+                        s_id[base] = bid[j];
+                    } else {
+                        s_over = 1;
                     }
                 }
             }
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) {
-                const long long v = __shfl_xor_sync(0xffffffffu, U, o);
-                U = v < U ? v : U;
+                const unsigned long long v = __shfl_xor_sync(0xffffffffu, myU, o);
+                myU = v < myU ? v : myU;
             }
+            if (lane == 0 && myU != ULLONG_MAX) atomicMin(&s_U, myU);
+            __syncthreads();
             if (fx && fy) break;
-            long long gx = LLONG_MAX, gy = LLONG_MAX;
+            // gap between the region and the unscanned buckets (periods handled by
+            // one conditional shift: the ranges are narrower than a period here)
+            long long g = LLONG_MAX;
             if (!fx) {
-                const long long l = X0 - (long long)Q * bucket_start(rx0, D.Lx, Bk, nbx);
-                const long long rr = (long long)Q * bucket_end(rx1, D.Lx, Bk, nbx) - (X0 + WR);
-                gx = min(l, rr);
+                const int lx = rx0 < 0 ? (rx0 + nbx) * Bk - D.Lx : rx0 * Bk;            // start of bucket rx0
+                const int ex = rx1 >= nbx ? min((rx1 - nbx + 1) * Bk, D.Lx) + D.Lx      // end of bucket rx1
+                                          : min((rx1 + 1) * Bk, D.Lx);
+                g = min((long long)Q * (x0 - lx), (long long)Q * (ex - (x0 + ncols)));
             }
             if (!fy) {
-                const long long l = Y0 - (long long)Q * bucket_start(ry0, D.Ly, Bk, nby);
-                const long long rr = (long long)Q * bucket_end(ry1, D.Ly, Bk, nby) - (Y0 + HR);
-                gy = min(l, rr);
+                const int ly = ry0 < 0 ? (ry0 + nby) * Bk - D.Ly : ry0 * Bk;
+                const int ey = ry1 >= nby ? min((ry1 - nby + 1) * Bk, D.Ly) + D.Ly : min((ry1 + 1) * Bk, D.Ly);
+                g = min(g, min((long long)Q * (y0 - ly), (long long)Q * (ey - (y0 + nrows))));
             }
-            const long long g = min(gx, gy);
+            const unsigned long long U = s_U;
+            __syncthreads();
             // every unscanned centre is at least g away from the region
-            if (g > 0 && g < (1ll << 31) && g * g > U) break;
-            if (g >= (1ll << 31)) break;
+            if (g > 0 && (g >= (1ll << 31) || (unsigned long long)(g * g) > U)) break;
             px0 = rx0; px1 = rx1; py0 = ry0; py1 = ry1; pfx = fx; pfy = fy; have_prev = true;
         }
-        if (lane == 0) s_U = U;
     }
-    __syncthreads();
 
-    // ---- compact candidates to those within U ----
-    const bool slow = (s_overflow != 0);
-    int nc = min(s_n, VCAND);
-    if (!slow && K > 0 && threadIdx.x < 32) {
-        const long long U = s_U;
-        int w = 0;
-        for (int base = 0; base < nc; base += 32) {
-            const int k = base + threadIdx.x;
+    // Each warp filters the scanned centres for its own patch; a scanned set
+    // holds every centre within U of the tile, so it holds every patch owner.
+    const int px0 = (warp & 1) * 16, py0 = (warp >> 1) * 8;
+    const bool hx = (px0 < ncols) && (ncols <= px0 + 16), hy = (py0 < nrows) && (nrows <= py0 + 8);
+    const int cbx = hx ? ncols : min(px0 + 15, ncols - 1);
+    const int rbx = hy ? nrows : min(py0 + 7, nrows - 1);
+    const bool has_patch = (px0 < ncols) && (py0 < nrows);
+    int wn = 0;
+    bool wover = false, wbad = false;
+    const int nscan = min(s_n, VCAND);
+    if (K > 0 && !s_over && has_patch) {
+        const long long PX0 = (long long)Q * px0, PY0 = (long long)Q * py0;
+        const long long PW = (long long)Q * (cbx - px0), PH = (long long)Q * (rbx - py0);
+        long long Uw = LLONG_MAX;
+        for (int k = lane; k < nscan; k += 32) {
+            const long long dx = s_cx[k] - PX0, dy = s_cy[k] - PY0;
+            const long long mxx = max(dx < 0 ? -dx : dx, dx > PW ? dx - PW : PW - dx);
+            const long long mxy = max(dy < 0 ? -dy : dy, dy > PH ? dy - PH : PH - dy);
+            Uw = min(Uw, mxx * mxx + mxy * mxy);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) Uw = min(Uw, __shfl_xor_sync(0xffffffffu, Uw, o));
+        for (int base = 0; base < nscan; base += 32) {
+            const int k = base + lane;
             bool keep = false;
-            int cx = 0, cy = 0, id = 0;
-            long long md = 0;
-            if (k < nc) {
-                cx = s_cx[k]; cy = s_cy[k]; id = s_id[k]; md = s_md[k];
-                keep = md <= U;
+            if (k < nscan) {
+                const int cx = s_cx[k], cy = s_cy[k];
+                const long long dx = cx - PX0, dy = cy - PY0;
+                const long long ex = dx < 0 ? -dx : (dx > PW ? dx - PW : 0);
+                const long long ey = dy < 0 ? -dy : (dy > PH ? dy - PH : 0);
+                keep = ex * ex + ey * ey <= Uw;
+                // The fast path needs every scanned centre's tile-relative position to
+                // be its minimum image for every site of the region (otherwise the
+                // distances above are not the torus distances) and exact in float32
+                // (|v| < 2^23). Any exception sends the warp to the exact general path.
+                if (!((long long)cx > WR - (MX >> 1) && (long long)cy > HR - (MY >> 1) &&
+                      cx < (1 << 23) && cx > -(1 << 23) && cy < (1 << 23) && cy > -(1 << 23)))
+                    wbad = true;
             }
             const unsigned m = __ballot_sync(0xffffffffu, keep);
-            __syncwarp();
             if (keep) {
-                const int pos = w + __popc(m & ((1u << threadIdx.x) - 1u));
-                s_cx[pos] = cx; s_cy[pos] = cy; s_id[pos] = id; s_md[pos] = md;
+                const int pos = wn + __popc(m & ((1u << lane) - 1u));
+                if (pos < WCAND) {
+                    s_wix[warp][pos] = s_cx[k];
+                    s_wiy[warp][pos] = s_cy[k];
+                    s_wfx[warp][pos] = (float)s_cx[k];
+                    s_wfy[warp][pos] = (float)s_cy[k];
+                    s_wid[warp][pos] = s_id[k];
+                }
             }
-            w += __popc(m);
-            __syncwarp();
+            wn += __popc(m);
         }
-        if (threadIdx.x == 0) s_n = w;
+        wbad = __any_sync(0xffffffffu, wbad);
+        wover = wn > WCAND;
+        __syncwarp();
     }
-    __syncthreads();
-    nc = slow ? K : s_n;
 
-    // ---- owners of the tile plus halo ----
-    const int ew = ncols + 1, eh = nrows + 1;
-    for (int k = threadIdx.x; k < ew * eh; k += VTHREADS) {
-        const int lx = k % ew, ly = k / ew;
-        const long long sx = (long long)Q * (x0 + lx), sy = (long long)Q * (y0 + ly);
-        long long best = LLONG_MAX;
-        int bi = -1;
-        if (!slow) {
+    const bool fast = (K > 0) && !s_over && !wbad;
+    if (fast && has_patch) {
+        const float* wfx = s_wfx[warp];
+        const int n = wover ? nscan : wn;
+        // sites: lane -> column px0 + (lane & 15), rows py0 + 4*(lane >> 4) .. +3;
+        // then the halo column/row sites outside that 16 x 8 block
+        const int c = px0 + (lane & 15);
+        const int rb = py0 + 4 * (lane >> 4);
+        if (c <= cbx && rb <= rbx) {
+            const float sxf = (float)(Q * c);
+            float syf[4];
+            float f1[4], f2[4];
+            int i1[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                f1[k] = INFINITY; f2[k] = INFINITY; i1[k] = -1;
+                syf[k] = (float)(Q * (rb + k));
+            }
+            if (!wover) {
+                for (int j = 0; j < n; ++j) {
+                    const float dx = sxf - wfx[j];
+                    const float dx2 = dx * dx;
+                    const float fy = s_wfy[warp][j];
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        const float dy = syf[k] - fy;
+                        const float d = fmaf(dy, dy, dx2);
+                        if (d < f1[k]) { f2[k] = f1[k]; f1[k] = d; i1[k] = j; }
+                        else f2[k] = fminf(f2[k], d);
+                    }
+                }
+            } else {
+                for (int j = 0; j < n; ++j) {
+                    const float dx = sxf - (float)s_cx[j];
+                    const float dx2 = dx * dx;
+                    const float fy = (float)s_cy[j];
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        const float dy = syf[k] - fy;
+                        const float d = fmaf(dy, dy, dx2);
+                        if (d < f1[k]) { f2[k] = f1[k]; f1[k] = d; i1[k] = j; }
+                        else f2[k] = fminf(f2[k], d);
+                    }
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const int rr = rb + k;
+                if (rr > rbx) break;
+                int o;
+                // a gap above 2^-20 relative means the float32 order is the exact order
+                // (the float32 distance is within 2^-23 relative of the exact one)
+                if (f2[k] == INFINITY || f2[k] - f1[k] > f2[k] * 9.5367431640625e-07f) {
+                    o = wover ? s_id[i1[k]] : s_wid[warp][i1[k]];
+                } else {
+                    o = wover ? owner_exact((long long)Q * c, (long long)Q * rr, s_cx, s_cy, s_id, n)
+                              : owner_exact((long long)Q * c, (long long)Q * rr, s_wix[warp], s_wiy[warp],
+                                            s_wid[warp], n);
+                }
+                s_own[rr][c] = o;
+            }
+        }
+        // halo sites beyond the 16 x 8 lane block
+        const int ex = (cbx == px0 + 16) ? (rbx - py0 + 1) : 0;       // column px0+16, rows py0..rbx
+        const int ey = (rbx == py0 + 8) ? (cbx - px0 + 1) : 0;       // row py0+8, columns px0..cbx
+        for (int k = lane; k < ex + ey; k += 32) {
+            int cc, rr;
+            if (k < ex) { cc = px0 + 16; rr = py0 + k; }
+            else { cc = px0 + (k - ex); rr = py0 + 8; }
+            if (k >= ex && cc == px0 + 16 && ex > 0) continue;        // corner counted once
+            s_own[rr][cc] = wover ? owner_exact((long long)Q * cc, (long long)Q * rr, s_cx, s_cy, s_id, n)
+                                  : owner_exact((long long)Q * cc, (long long)Q * rr, s_wix[warp], s_wiy[warp],
+                                                s_wid[warp], n);
+        }
+    } else if (has_patch) {
+        // ---- general path for this warp's sites: per-site minimum image over
+        // the scanned centres (or over all centres when the scan overflowed) ----
+        const bool all = (K > 0) && s_over;
+        const int nc = all ? K : (K > 0 ? nscan : 0);
+        const int ew = cbx - px0 + 1, eh = rbx - py0 + 1;
+        for (int k = lane; k < ew * eh; k += 32) {
+            const int lx = px0 + k % ew, ly = py0 + k / ew;
+            const long long sx = (long long)Q * lx, sy = (long long)Q * ly;   // relative to the tile origin
+            long long best = LLONG_MAX;
+            int bi = -1;
             for (int j = 0; j < nc; ++j) {
-                const long long dx = wrapM(sx - s_cx[j], MX);
-                const long long dy = wrapM(sy - s_cy[j], MY);
+                long long cx, cy;
+                int id;
+                if (all) {
+                    cx = wrapM((long long)cq[j].x - X0, MX);
+                    cy = wrapM((long long)cq[j].y - Y0, MY);
+                    id = j;
+                } else {
+                    cx = s_cx[j]; cy = s_cy[j]; id = s_id[j];
+                }
+                const long long dx = wrapM(sx - cx, MX), dy = wrapM(sy - cy, MY);
                 const long long d2 = dx * dx + dy * dy;
-                const int id = s_id[j];
                 if (d2 < best || (d2 == best && id < bi)) { best = d2; bi = id; }
             }
-        } else {
-            for (int j = 0; j < K; ++j) {
-                const int2 c = cq[j];
-                const long long dx = wrapM(sx - c.x, MX);
-                const long long dy = wrapM(sy - c.y, MY);
-                const long long d2 = dx * dx + dy * dy;
-                if (d2 < best) { best = d2; bi = j; }
-            }
+            s_own[ly][lx] = bi;
         }
-        s_own[ly][lx] = bi;
     }
     __syncthreads();
 
@@ -326,7 +450,6 @@ __global__ __launch_bounds__(VTHREADS) void k_voronoi(Pools P, StepTable T) {
         for (int k = threadIdx.x; k < VEDGESET; k += VTHREADS)
             if (s_set[k] != EMPTY_KEY) edge_global_insert(P, D, inst, s_set[k]);
     }
-    (void)now;
 }
 
 void launch_voronoi(const Launch& L) {
