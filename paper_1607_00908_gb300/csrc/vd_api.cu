@@ -198,6 +198,7 @@ void enqueue_step(vd_batch* b, const Launch& L, bool timed) {
     launch_labels(L);
     mark(b, timed);
     launch_voronoi(L);
+    launch_merge_lists(L);
     mark(b, timed);
     launch_graph(L);
     launch_finish(L);
@@ -329,6 +330,8 @@ vd_status create_batch(const vd_config* cfgs, int n, vd_batch** out) {
     P.brk_prev = M.alloc<unsigned long long>(edge);
     P.ari = M.alloc<unsigned long long>(edge);
     P.ekeys = M.alloc<unsigned long long>(edge);
+    P.oapp_key = M.alloc<unsigned long long>(ovl);
+    P.oapp_cnt = M.alloc<unsigned>(ovl);
     P.scan_flag_cap = scan_items / SCAN_TILE + 2;
     P.scan_flags = M.alloc<unsigned long long>(P.scan_flag_cap);
     b->d_fields = M.alloc<const float*>(n);

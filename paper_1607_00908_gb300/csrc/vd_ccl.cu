@@ -72,9 +72,43 @@ __device__ __forceinline__ int run_length(unsigned long long m, int c) {
     return inv ? __ffsll(inv) - 1 : 64;   // all ones only when c == 0
 }
 
+// Run id r*32 + j is stored at r*32 + (j ^ r): lanes that own different rows
+// touch different shared-memory banks.
+__device__ __forceinline__ int SW(int id) { return id ^ ((id >> 5) & 31); }
+
+__device__ __forceinline__ int rfind(volatile int* p, int x) {
+    int y = p[SW(x)];
+    while (y != x) {
+        x = y;
+        y = p[SW(x)];
+    }
+    return x;
+}
+
+// lock-free union by smaller run id on the swizzled parent array
+__device__ __forceinline__ void runion(int* p, int a, int b) {
+    bool done;
+    do {
+        a = rfind(p, a);
+        b = rfind(p, b);
+        if (a < b) {
+            const int old = atomicMin(&p[SW(b)], a);
+            done = (old == b);
+            b = old;
+        } else if (b < a) {
+            const int old = atomicMin(&p[SW(a)], b);
+            done = (old == a);
+            a = old;
+        } else {
+            done = true;
+        }
+    } while (!done);
+}
+
 struct UfSmem {                  // one warp's tile: row masks and union-find over runs
     unsigned long long m[TH];
-    int par[RUNS];
+    int par[RUNS];               // swizzled: parent of run id k at par[SW(k)]
+    unsigned char col[RUNS];     // swizzled: start column of each run
 };
 struct LabelSmem : UfSmem {
     int aux[RUNS];     // per root run: (n << 16) | sum(y - y_root), then piece id / bubble id
@@ -87,8 +121,17 @@ struct TileSmem : LabelSmem {
 __device__ void warp_runs_uf(UfSmem& T, unsigned long long m) {
     const int r = threadIdx.x & 31;
     const unsigned long long S = run_starts(m);
-    const int nr = __popcll(S);
-    for (int j = 0; j < nr; ++j) T.par[r * 32 + j] = r * 32 + j;
+    {
+        unsigned long long t = S;
+        int j = 0;
+        while (t) {
+            const int c = __ffsll(t) - 1;
+            t &= t - 1;
+            T.par[SW(r * 32 + j)] = r * 32 + j;
+            T.col[SW(r * 32 + j)] = (unsigned char)c;
+            ++j;
+        }
+    }
     const unsigned long long mu = __shfl_up_sync(0xffffffffu, m, 1);
     __syncwarp();
     if (r > 0) {
@@ -97,11 +140,12 @@ __device__ void warp_runs_uf(UfSmem& T, unsigned long long m) {
         while (os) {
             const int c = __ffsll(os) - 1;
             os &= os - 1;
-            uf_union(T.par, r * 32 + run_index(S, c), (r - 1) * 32 + run_index(Su, c));
+            runion(T.par, r * 32 + run_index(S, c), (r - 1) * 32 + run_index(Su, c));
         }
     }
     __syncwarp();
-    for (int j = 0; j < nr; ++j) T.par[r * 32 + j] = uf_find(T.par, r * 32 + j);
+    const int nr = __popcll(S);
+    for (int j = 0; j < nr; ++j) T.par[SW(r * 32 + j)] = rfind(T.par, r * 32 + j);
     __syncwarp();
 }
 
@@ -112,7 +156,7 @@ __device__ __forceinline__ unsigned warp_roots(const UfSmem& T, unsigned long lo
     const int nr = __popcll(run_starts(m));
     unsigned R = 0;
     for (int j = 0; j < nr; ++j)
-        if (T.par[r * 32 + j] == r * 32 + j) R |= 1u << j;
+        if (T.par[SW(r * 32 + j)] == r * 32 + j) R |= 1u << j;
     const int cnt = __popc(R);
     int inc = cnt;
 #pragma unroll
@@ -145,7 +189,44 @@ __device__ __forceinline__ bool is_fg(float v, float thr, int pol) {
 constexpr int CCL_WARPS = 2;    // tiles per block in pass A
 
 // ---------------------------------------------------------------------------
-// Pass A: threshold + union-find over runs + pieces + borders (one warp per tile)
+// Threshold (Section 3.1): one 32-bit foreground word per thread, streamed
+// from the field with 16-byte loads; bit i of word w of row y is site
+// (32w + i, y). Items are the words of all active instances.
+// ---------------------------------------------------------------------------
+__global__ __launch_bounds__(256) void k_threshold(Pools P, StepTable T) {
+    const long long total = T.word_pre[T.n_act];
+    for (long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x; g < total;
+         g += (long long)gridDim.x * blockDim.x) {
+        const int a = seg_of(T.word_pre, T.n_act, g);
+        const int inst = T.act[a];
+        const InstDesc& D = P.desc[inst];
+        const InstState& S = P.st[inst];
+        const long long w = g - T.word_pre[a];
+        const int y = (int)(w / D.wpr), wx = (int)(w - (long long)y * D.wpr);
+        const int x = wx * 32;
+        const float* f = S.field + (long long)y * S.pitch + x;
+        const float thr = D.thr;
+        const int pol = D.pol;
+        unsigned bits = 0;
+        if (x + 32 <= D.Lx && ((reinterpret_cast<uintptr_t>(f) & 15u) == 0)) {
+            const float4* f4 = reinterpret_cast<const float4*>(f);
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                const float4 v = __ldcs(f4 + i);
+                bits |= ((unsigned)is_fg(v.x, thr, pol) | ((unsigned)is_fg(v.y, thr, pol) << 1) |
+                         ((unsigned)is_fg(v.z, thr, pol) << 2) | ((unsigned)is_fg(v.w, thr, pol) << 3)) << (4 * i);
+            }
+        } else {
+            const int n = min(32, D.Lx - x);
+            for (int i = 0; i < n; ++i)
+                if (is_fg(__ldcs(f + i), thr, pol)) bits |= 1u << i;
+        }
+        P.fgbits[D.word_off + w] = bits;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Pass A: union-find over runs + pieces + borders (one warp per tile)
 // ---------------------------------------------------------------------------
 __global__ __launch_bounds__(32 * CCL_WARPS) void k_ccl_tiles(Pools P, StepTable T) {
     __shared__ TileSmem s_tile[CCL_WARPS];
@@ -161,40 +242,9 @@ __global__ __launch_bounds__(32 * CCL_WARPS) void k_ccl_tiles(Pools P, StepTable
     const int tx = t % D.ntx, ty = t / D.ntx;
     const int x0 = tx * TW, y0 = ty * TH;
     const int Lx = D.Lx, Ly = D.Ly;
-    const float thr = D.thr;
-    const int pol = D.pol;
-    const float* field = S.field;
-    const long long pitch = S.pitch;
-    const bool in0 = x0 + lane < Lx, in1 = x0 + 32 + lane < Lx;
 
-    // 1. threshold: lane l reads columns l and l+32 of every row (coalesced)
-    unsigned long long my_m = 0;
-#pragma unroll 4
-    for (int rb = 0; rb < TH; rb += 8) {
-        float v0[8], v1[8];
-#pragma unroll
-        for (int k = 0; k < 8; ++k) {
-            const int y = y0 + rb + k;
-            const float* f = field + (long long)y * pitch + x0 + lane;
-            v0[k] = (y < Ly && in0) ? __ldcs(f) : NAN;
-            v1[k] = (y < Ly && in1) ? __ldcs(f + 32) : NAN;
-        }
-#pragma unroll
-        for (int k = 0; k < 8; ++k) {
-            const unsigned lo = __ballot_sync(0xffffffffu, is_fg(v0[k], thr, pol));
-            const unsigned hi = __ballot_sync(0xffffffffu, is_fg(v1[k], thr, pol));
-            if (lane == rb + k) my_m = (unsigned long long)lo | ((unsigned long long)hi << 32);
-        }
-    }
-    {
-        const int y = y0 + lane;
-        const int wx = x0 >> 5;
-        if (y < Ly) {
-            unsigned* row = P.fgbits + D.word_off + (long long)y * D.wpr;
-            row[wx] = (unsigned)my_m;
-            if (wx + 1 < D.wpr) row[wx + 1] = (unsigned)(my_m >> 32);
-        }
-    }
+    // 1. foreground masks of the tile rows (written by k_threshold; L2-resident)
+    const unsigned long long my_m = load_row_mask(P, D, x0, y0);
     TS.m[lane] = my_m;
 
     // 2. union-find over runs
@@ -204,8 +254,8 @@ __global__ __launch_bounds__(32 * CCL_WARPS) void k_ccl_tiles(Pools P, StepTable
     const unsigned long long S0 = run_starts(my_m);
     const int nr = __popcll(S0);
     for (int j = 0; j < nr; ++j) {
-        TS.aux[lane * 32 + j] = 0;
-        TS.su[lane * 32 + j] = 0;
+        TS.aux[SW(lane * 32 + j)] = 0;
+        TS.su[SW(lane * 32 + j)] = 0;
     }
     __syncwarp();
     {
@@ -215,11 +265,11 @@ __global__ __launch_bounds__(32 * CCL_WARPS) void k_ccl_tiles(Pools P, StepTable
             const int c = __ffsll(q) - 1;
             q &= q - 1;
             const int len = run_length(my_m, c);
-            const int root = TS.par[lane * 32 + j];
+            const int root = TS.par[SW(lane * 32 + j)];
             const int rr = root >> 5;
-            const int cr = run_column(run_starts(TS.m[rr]), root & 31);
-            atomicAdd(&TS.aux[root], (len << 16) + len * (lane - rr));
-            atomicAdd(&TS.su[root], len * (c - cr) + (len * (len - 1)) / 2);
+            const int cr = TS.col[SW(root)];
+            atomicAdd(&TS.aux[SW(root)], (len << 16) + len * (lane - rr));
+            atomicAdd(&TS.su[SW(root)], len * (c - cr) + (len * (len - 1)) / 2);
             ++j;
         }
     }
@@ -246,12 +296,12 @@ __global__ __launch_bounds__(32 * CCL_WARPS) void k_ccl_tiles(Pools P, StepTable
         while (rq) {
             const int j = __ffs(rq) - 1;
             rq &= rq - 1;
-            const int id = lane * 32 + j;
+            const int id = SW(lane * 32 + j);
             int pid = -1;
             if (pbase >= 0) {
                 pid = pbase + k;
                 const int nsv = TS.aux[id];
-                P.p_q[pid] = (y0 + lane) * Lx + x0 + run_column(S0, j);
+                P.p_q[pid] = (y0 + lane) * Lx + x0 + TS.col[id];
                 P.p_inst[pid] = inst;
                 P.p_n[pid] = nsv >> 16;
                 P.p_sv[pid] = nsv & 0xFFFF;
@@ -279,7 +329,7 @@ __global__ __launch_bounds__(32 * CCL_WARPS) void k_ccl_tiles(Pools P, StepTable
         int v = -1;
         if (lx < ncols && ly < nrows) {
             const unsigned long long m = TS.m[ly];
-            if ((m >> lx) & 1ull) v = TS.aux[TS.par[ly * 32 + run_index(run_starts(m), lx)]];
+            if ((m >> lx) & 1ull) v = TS.aux[SW(TS.par[SW(ly * 32 + run_index(run_starts(m), lx))])];
         }
         bd[k] = v;
     }
@@ -417,7 +467,7 @@ __global__ __launch_bounds__(32 * WIDE_WARPS) void k_comp_wide(Pools P) {
         while (t) {
             const int c = __ffsll(t) - 1;
             t &= t - 1;
-            if (TS.par[lane * 32 + j] == lq) {
+            if (TS.par[SW(lane * 32 + j)] == lq) {
                 const int len = run_length(m, c);
                 for (int i = 0; i < len; ++i) sx += wrap_ll((x0 + c + i) - xr, D.Lx);
                 n += len;
@@ -487,37 +537,15 @@ __global__ void k_bucket_scatter(Pools P) {
 // Label pass: final labels from the stored bits; overlap histogram with the
 // previous frame's labels (Section 3.2.3)
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void ovl_global_insert(const Pools& P, const InstDesc& D, int inst,
-                                                  unsigned long long key, unsigned cnt) {
-    unsigned long long* H = P.ohash + D.ohash_off;
-    unsigned* V = P.oval + D.ohash_off;
-    const InstState& S = P.st[inst];
-    const unsigned mask = dyn_mask(D.ohash_mask, 8ll * ((long long)S.K + S.K_prev) + 64);
-    unsigned h = (unsigned)hash64(key) & mask;
-    for (unsigned probe = 0; probe <= mask; ++probe) {
-        const unsigned long long k = atomicCAS(&H[h], EMPTY_KEY, key);
-        if (k == EMPTY_KEY || k == key) {
-            atomicAdd(&V[h], cnt);
-            if (k == EMPTY_KEY) {
-                const int idx = warp_fetch_inc(&P.st[inst].n_ovl);
-                if (idx < D.ovl_cap) P.olist[D.ovl_off + idx] = (int)h;
-                else atomicOr(&P.st[inst].err, ERR_OVL_CAP);
-            }
-            return;
-        }
-        h = (h + 1) & mask;
-    }
-    atomicOr(&P.st[inst].err, ERR_OVL_CAP);
-}
-
 constexpr int LBL_WARPS = 4;    // tiles per block in the label pass
 constexpr int WSET = 128;       // per-warp overlap set
 
+// add (key, count) to the warp's shared set (read-first probe, 32-bit hash)
 __device__ __forceinline__ void ovl_add_w(unsigned long long* key, unsigned* cnt, const Pools& P, const InstDesc& D,
                                           int inst, unsigned long long k, unsigned c) {
-    unsigned h = (unsigned)hash64(k) & (WSET - 1);
+    unsigned h = hash_small(k) & (WSET - 1);
     for (int probe = 0; probe < WSET; ++probe) {
-        const unsigned long long o = atomicCAS(&key[h], EMPTY_KEY, k);
+        const unsigned long long o = key[h] == k ? k : atomicCAS(&key[h], EMPTY_KEY, k);
         if (o == EMPTY_KEY || o == k) {
             atomicAdd(&cnt[h], c);
             return;
@@ -564,7 +592,7 @@ __global__ __launch_bounds__(32 * LBL_WARPS) void k_labels(Pools P, StepTable T)
         while (rq) {
             const int j = __ffs(rq) - 1;
             rq &= rq - 1;
-            TS.aux[lane * 32 + j] = pbase >= 0 ? P.p_comp[P.p_parent[pbase + k]] : -1;
+            TS.aux[SW(lane * 32 + j)] = pbase >= 0 ? P.p_comp[P.p_parent[pbase + k]] : -1;
             ++k;
         }
     }
@@ -593,8 +621,8 @@ __global__ __launch_bounds__(32 * LBL_WARPS) void k_labels(Pools P, StepTable T)
             if (r >= nrows) break;
             const unsigned long long m = TS.m[r];
             const unsigned long long Sr = run_starts(m);
-            const int l0 = ((m >> lane) & 1ull) ? TS.aux[TS.par[r * 32 + run_index(Sr, lane)]] : -1;
-            const int l1 = ((m >> (lane + 32)) & 1ull) ? TS.aux[TS.par[r * 32 + run_index(Sr, lane + 32)]] : -1;
+            const int l0 = ((m >> lane) & 1ull) ? TS.aux[SW(TS.par[SW(r * 32 + run_index(Sr, lane))])] : -1;
+            const int l1 = ((m >> (lane + 32)) & 1ull) ? TS.aux[SW(TS.par[SW(r * 32 + run_index(Sr, lane + 32))])] : -1;
             if (in0) out[(long long)r * Lx] = l0;
             if (in1) out[(long long)r * Lx + 32] = l1;
             if (with_prev) {
@@ -620,12 +648,36 @@ __global__ __launch_bounds__(32 * LBL_WARPS) void k_labels(Pools P, StepTable T)
         if (cur0 != EMPTY_KEY) ovl_add_w(skey, scnt, P, D, inst, cur0, c0);
         if (cur1 != EMPTY_KEY) ovl_add_w(skey, scnt, P, D, inst, cur1, c1);
         __syncwarp();
-        for (int k = lane; k < WSET; k += 32)
-            if (skey[k] != EMPTY_KEY) ovl_global_insert(P, D, inst, skey[k], scnt[k]);
+        // append the tile's (past, now, count) triples (one reservation per
+        // round); k_merge_lists adds them into the overlap hash
+        for (int kb = 0; kb < WSET; kb += 32) {
+            const unsigned long long key = skey[kb + lane];
+            const bool has = key != EMPTY_KEY;
+            const unsigned m = __ballot_sync(0xffffffffu, has);
+            if (!m) continue;
+            int base = 0;
+            if (lane == 0) base = atomicAdd(&P.st[inst].n_oapp, __popc(m));
+            base = __shfl_sync(0xffffffffu, base, 0);
+            if (has) {
+                const int pos = base + __popc(m & ((1u << lane) - 1u));
+                if (pos < D.ovl_cap) {
+                    P.oapp_key[D.ovl_off + pos] = key;
+                    P.oapp_cnt[D.ovl_off + pos] = scnt[kb + lane];
+                } else {
+                    ovl_global_insert(P, D, inst, key, scnt[kb + lane]);   // list full: insert directly
+                }
+            }
+        }
     }
 }
 
 void launch_ccl_tiles(const Launch& L) {
+    {
+        const long long need = (L.total_words + 255) / 256;
+        const int grid = (int)(need < 8LL * L.grid_items ? need : 8LL * L.grid_items);
+        k_threshold<<<grid > 0 ? grid : 1, 256, 0, L.s>>>(L.P, L.T);
+        ++*L.nlaunch;
+    }
     k_ccl_tiles<<<(L.total_tilesA + CCL_WARPS - 1) / CCL_WARPS, 32 * CCL_WARPS, 0, L.s>>>(L.P, L.T);
     ++*L.nlaunch;
 }

@@ -46,6 +46,8 @@ __global__ void k_step_begin(Pools P, StepTable T) {
         S.n_ovl = 0;
         S.n_edge_list = 0;
         S.n_tedges = 0;
+        S.n_eapp = 0;
+        S.n_oapp = 0;
         S.err = 0;
     }
 }

@@ -87,6 +87,8 @@ struct InstState {
     int n_ovl;               // overlap pairs this frame
     int n_edge_list;         // unique links inserted in the hash (= E)
     int n_tedges;            // translated past links
+    int n_eapp;              // links appended by Voronoi tiles (before dedup)
+    int n_oapp;              // overlap pairs appended by label tiles (before merge)
     int err;
     int rep_K_prev;          // bubbles of the past frame used by the last step
     int pad1;
@@ -165,7 +167,9 @@ struct Pools {
     unsigned long long* brk;
     unsigned long long* brk_prev;
     unsigned long long* ari;
-    unsigned long long* ekeys;   // sorted link keys (getter output staging)
+    unsigned long long* ekeys;   // per-tile unique links appended by the Voronoi pass; getter staging
+    unsigned long long* oapp_key;   // per-tile (past, now) pairs appended by the label pass
+    unsigned* oapp_cnt;
     // scan scratch
     unsigned long long* scan_flags;
     long long scan_flag_cap;     // tiles of SCAN_TILE elements
@@ -196,7 +200,8 @@ enum PreIdx : int {
     PRE_ET,         // translated links
     PRE_FB,         // breaking links
     PRE_FA,         // arising links
-    PRE_P,          // pieces (unused by scans)
+    PRE_EA,         // appended links
+    PRE_OA,         // appended overlap pairs
     NPRE
 };
 
@@ -251,6 +256,60 @@ __device__ __forceinline__ unsigned long long hash64(unsigned long long k) {
     return k;
 }
 
+// cheap 32-bit hash of a (lo, hi) key for small shared-memory sets
+__device__ __forceinline__ unsigned hash_small(unsigned long long k) {
+    return ((unsigned)k * 0x9E3779B1u) ^ ((unsigned)(k >> 32) * 0x85EBCA77u);
+}
+
+// Warp-cooperative insert of per-lane keys (EMPTY_KEY = none) into a shared
+// open-addressing set of `cap` slots (power of two). All lanes first probe
+// read-only (almost every key is already present); keys not found are merged
+// across the warp and inserted by one lane each. Returns false for a lane
+// whose key could not be placed (set full).
+__device__ __forceinline__ bool warp_set_insert(unsigned long long* set, int cap, unsigned long long key) {
+    const int lane = threadIdx.x & 31;
+    unsigned h = hash_small(key) & (cap - 1);
+    const bool pending = key != EMPTY_KEY && set[h] != key;
+    if (!__any_sync(0xffffffffu, pending)) return true;
+    const unsigned grp = __match_any_sync(0xffffffffu, pending ? key : EMPTY_KEY);
+    bool ok = true;
+    if (pending && lane == __ffs(grp) - 1) {
+        ok = false;
+        for (int probe = 0; probe < cap; ++probe) {
+            const unsigned long long o = atomicCAS(&set[h], EMPTY_KEY, key);
+            if (o == EMPTY_KEY || o == key) { ok = true; break; }
+            h = (h + 1) & (cap - 1);
+        }
+    }
+    return ok;
+}
+
+// Warp-cooperative add of per-lane (key, count) pairs into a shared counted
+// set: equal keys are merged across the warp first, then one lane per key
+// probes and adds the group's count. Returns false for the lane holding a
+// merged group that could not be placed (set full); that lane's `*csum_out`
+// carries the group's count.
+__device__ __forceinline__ bool warp_set_add(unsigned long long* set, unsigned* cnt, int cap,
+                                             unsigned long long key, unsigned c, unsigned* csum_out) {
+    const int lane = threadIdx.x & 31;
+    const bool has = key != EMPTY_KEY;
+    if (!__any_sync(0xffffffffu, has)) return true;
+    const unsigned grp = __match_any_sync(0xffffffffu, key);
+    const unsigned csum = __reduce_add_sync(grp, has ? c : 0u);
+    *csum_out = csum;
+    if (!has || lane != __ffs(grp) - 1) return true;
+    unsigned h = hash_small(key) & (cap - 1);
+    for (int probe = 0; probe < cap; ++probe) {
+        const unsigned long long o = set[h] == key ? key : atomicCAS(&set[h], EMPTY_KEY, key);
+        if (o == EMPTY_KEY || o == key) {
+            atomicAdd(&cnt[h], csum);
+            return true;
+        }
+        h = (h + 1) & (cap - 1);
+    }
+    return false;
+}
+
 // Warp-aggregated atomic add: lanes that target the same counter are grouped,
 // one lane adds the group's sum (far fewer same-address atomics).
 __device__ __forceinline__ void warp_add(int* p, int v) {
@@ -293,6 +352,31 @@ __host__ __device__ inline long long floordiv_ll(long long p, long long q) {
     return d;
 }
 
+// insert or add into the (past, now) overlap hash; new keys are listed in olist
+__device__ __forceinline__ void ovl_global_insert(const Pools& P, const InstDesc& D, int inst,
+                                                  unsigned long long key, unsigned cnt) {
+    unsigned long long* H = P.ohash + D.ohash_off;
+    unsigned* V = P.oval + D.ohash_off;
+    const InstState& S = P.st[inst];
+    const unsigned mask = dyn_mask(D.ohash_mask, 8ll * ((long long)S.K + S.K_prev) + 64);
+    unsigned h = (unsigned)hash64(key) & mask;
+    for (unsigned probe = 0; probe <= mask; ++probe) {
+        const unsigned long long k = atomicCAS(&H[h], EMPTY_KEY, key);
+        if (k == EMPTY_KEY || k == key) {
+            atomicAdd(&V[h], cnt);
+            if (k == EMPTY_KEY) {
+                const int idx = warp_fetch_inc(&P.st[inst].n_ovl);
+                if (idx < D.ovl_cap) P.olist[D.ovl_off + idx] = (int)h;
+                else atomicOr(&P.st[inst].err, ERR_OVL_CAP);
+            }
+            return;
+        }
+        h = (h + 1) & mask;
+    }
+    atomicOr(&P.st[inst].err, ERR_OVL_CAP);
+}
+
+
 // ---------------------------------------------------------------------------
 // Kernel launchers (defined in the .cu files)
 // ---------------------------------------------------------------------------
@@ -309,7 +393,8 @@ struct Launch {
 void launch_ccl_tiles(const Launch& L);    // threshold + tile union-find (pass A)
 void launch_ccl_rest(const Launch& L);     // border merge, ranks, centroids, bucket grid
 void launch_labels(const Launch& L);       // per-site labels + overlap histogram
-void launch_voronoi(const Launch& L);      // owners + link hash
+void launch_voronoi(const Launch& L);      // owners + per-tile links
+void launch_merge_lists(const Launch& L);  // appended links/pairs -> hash tables
 void launch_graph(const Launch& L);        // CSR, match, translation, flips
 void launch_begin(const Launch& L);        // per-step counters and field pointers
 void launch_finish(const Launch& L);       // swap frames

@@ -56,7 +56,8 @@ __global__ void k_plan(Pools P, StepTable T, int with_comp) {
             v[PRE_ET] = S.n_tedges;
             v[PRE_FB] = S.n_break;
             v[PRE_FA] = S.n_arise;
-            v[PRE_P] = 0;
+            v[PRE_EA] = S.n_eapp < D.edge_cap ? S.n_eapp : D.edge_cap;
+            v[PRE_OA] = S.n_oapp < D.ovl_cap ? S.n_oapp : D.ovl_cap;
             for (int k = 0; k < NPRE; ++k) {
                 pre_arr(T, k)[a] = acc[k];
                 acc[k] += v[k];

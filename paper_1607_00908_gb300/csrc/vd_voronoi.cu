@@ -116,8 +116,7 @@ __global__ __launch_bounds__(VTHREADS) void k_voronoi(Pools P, StepTable T) {
     // per-warp candidate lists of each warp's 16 x 8 patch
     __shared__ float s_wfx[8][WCAND], s_wfy[8][WCAND];
     __shared__ int s_wix[8][WCAND], s_wiy[8][WCAND], s_wid[8][WCAND];
-    __shared__ int s_own[VH + 1][VW + 1];
-    __shared__ unsigned long long s_set[VEDGESET];
+    __shared__ int s_own[VH][VW + 1];
     __shared__ int s_n, s_over;
     __shared__ unsigned long long s_U;
 
@@ -133,11 +132,10 @@ __global__ __launch_bounds__(VTHREADS) void k_voronoi(Pools P, StepTable T) {
     const int K = min(S.K, D.comp_cap);
     const long long MX = (long long)Q * D.Lx, MY = (long long)Q * D.Ly;
     const long long X0 = (long long)Q * x0, Y0 = (long long)Q * y0;
-    const long long WR = (long long)Q * ncols, HR = (long long)Q * nrows;   // region incl. halo
+    const long long WR = (long long)Q * (ncols - 1), HR = (long long)Q * (nrows - 1);   // core sites only
     const int2* cq = P.cq + D.comp_off;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
-    for (int k = threadIdx.x; k < VEDGESET; k += VTHREADS) s_set[k] = EMPTY_KEY;
     if (threadIdx.x == 0) {
         s_n = 0;
         s_over = 0;
@@ -150,15 +148,16 @@ __global__ __launch_bounds__(VTHREADS) void k_voronoi(Pools P, StepTable T) {
         // Bucket indices are unwrapped (they may run below 0 or past nb-1 by
         // less than one period); all arithmetic is 32-bit here.
         const int Bk = S.B, nbx = S.nbx, nby = S.nby;
-        const int bx0 = x0 / Bk, bx1 = (x0 + ncols) >= D.Lx ? nbx : (x0 + ncols) / Bk;
-        const int by0 = y0 / Bk, by1 = (y0 + nrows) >= D.Ly ? nby : (y0 + nrows) / Bk;
+        const int bx0 = x0 / Bk, bx1 = (x0 + ncols - 1) / Bk;
+        const int by0 = y0 / Bk, by1 = (y0 + nrows - 1) / Bk;
         const int* boff = P.boff + D.bucket_off;
         const int2* bcq = P.bcq + D.comp_off;
         const int* bid = P.bid + D.comp_off;
         int px0 = 0, px1 = -1, py0 = 0, py1 = -1;
         bool pfx = false, pfy = false, have_prev = false;
         unsigned long long myU = ULLONG_MAX;
-        for (int r = 0;; ++r) {
+        // the first round takes rings 0..2 at once (one latency round instead of three)
+        for (int r = 2;; ++r) {
             int rx0 = bx0 - r, rx1 = bx1 + r, ry0 = by0 - r, ry1 = by1 + r;
             const bool fx = (rx1 - rx0 + 1) >= nbx, fy = (ry1 - ry0 + 1) >= nby;
             if (fx) { rx0 = 0; rx1 = nbx - 1; }
@@ -232,12 +231,12 @@ __global__ __launch_bounds__(VTHREADS) void k_voronoi(Pools P, StepTable T) {
                 const int lx = rx0 < 0 ? (rx0 + nbx) * Bk - D.Lx : rx0 * Bk;            // start of bucket rx0
                 const int ex = rx1 >= nbx ? min((rx1 - nbx + 1) * Bk, D.Lx) + D.Lx      // end of bucket rx1
                                           : min((rx1 + 1) * Bk, D.Lx);
-                g = min((long long)Q * (x0 - lx), (long long)Q * (ex - (x0 + ncols)));
+                g = min((long long)Q * (x0 - lx), (long long)Q * (ex - (x0 + ncols - 1)));
             }
             if (!fy) {
                 const int ly = ry0 < 0 ? (ry0 + nby) * Bk - D.Ly : ry0 * Bk;
                 const int ey = ry1 >= nby ? min((ry1 - nby + 1) * Bk, D.Ly) + D.Ly : min((ry1 + 1) * Bk, D.Ly);
-                g = min(g, min((long long)Q * (y0 - ly), (long long)Q * (ey - (y0 + nrows))));
+                g = min(g, min((long long)Q * (y0 - ly), (long long)Q * (ey - (y0 + nrows - 1))));
             }
             const unsigned long long U = s_U;
             __syncthreads();
@@ -250,9 +249,8 @@ __global__ __launch_bounds__(VTHREADS) void k_voronoi(Pools P, StepTable T) {
     // Each warp filters the scanned centres for its own patch; a scanned set
     // holds every centre within U of the tile, so it holds every patch owner.
     const int px0 = (warp & 1) * 16, py0 = (warp >> 1) * 8;
-    const bool hx = (px0 < ncols) && (ncols <= px0 + 16), hy = (py0 < nrows) && (nrows <= py0 + 8);
-    const int cbx = hx ? ncols : min(px0 + 15, ncols - 1);
-    const int rbx = hy ? nrows : min(py0 + 7, nrows - 1);
+    const int cbx = min(px0 + 15, ncols - 1);
+    const int rbx = min(py0 + 7, nrows - 1);
     const bool has_patch = (px0 < ncols) && (py0 < nrows);
     int wn = 0;
     bool wover = false, wbad = false;
@@ -366,18 +364,6 @@ __global__ __launch_bounds__(VTHREADS) void k_voronoi(Pools P, StepTable T) {
                 s_own[rr][c] = o;
             }
         }
-        // halo sites beyond the 16 x 8 lane block
-        const int ex = (cbx == px0 + 16) ? (rbx - py0 + 1) : 0;       // column px0+16, rows py0..rbx
-        const int ey = (rbx == py0 + 8) ? (cbx - px0 + 1) : 0;       // row py0+8, columns px0..cbx
-        for (int k = lane; k < ex + ey; k += 32) {
-            int cc, rr;
-            if (k < ex) { cc = px0 + 16; rr = py0 + k; }
-            else { cc = px0 + (k - ex); rr = py0 + 8; }
-            if (k >= ex && cc == px0 + 16 && ex > 0) continue;        // corner counted once
-            s_own[rr][cc] = wover ? owner_exact((long long)Q * cc, (long long)Q * rr, s_cx, s_cy, s_id, n)
-                                  : owner_exact((long long)Q * cc, (long long)Q * rr, s_wix[warp], s_wiy[warp],
-                                                s_wid[warp], n);
-        }
     } else if (has_patch) {
         // ---- general path for this warp's sites: per-site minimum image over
         // the scanned centres (or over all centres when the scan overflowed) ----
@@ -421,39 +407,120 @@ __global__ __launch_bounds__(VTHREADS) void k_voronoi(Pools P, StepTable T) {
         }
     }
 
-    // ---- links ----
-    if (K > 1) {
-        for (int k = threadIdx.x; k < VW * VH / 4; k += VTHREADS) {
-            const int ly = k / (VW / 4), lx0 = (k % (VW / 4)) * 4;
-            if (ly >= nrows) continue;
-            unsigned long long last = EMPTY_KEY;
-            for (int i = 0; i < 4; ++i) {
-                const int lx = lx0 + i;
-                if (lx >= ncols) break;
-                const int o = s_own[ly][lx], rt = s_own[ly][lx + 1];
-                const int dn = s_own[ly + 1][lx], dg = s_own[ly + 1][lx + 1];
-                if (o != rt) {
-                    const unsigned long long kk = edge_key(o, rt);
-                    if (kk != last) { edge_add(s_set, P, D, inst, kk); last = kk; }
-                }
-                if (o != dn) {
-                    const unsigned long long kk = edge_key(o, dn);
-                    if (kk != last) { edge_add(s_set, P, D, inst, kk); last = kk; }
-                }
-                if (o != rt && o != dn && o != dg && rt != dn && rt != dg && dn != dg) {
-                    const unsigned long long kk = plaquette_key(o, rt, dg, dn, cq, MX, MY);
-                    edge_add(s_set, P, D, inst, kk);
-                }
-            }
+}
+
+// ---------------------------------------------------------------------------
+// Links from the owner array (Section 3.2.2), one block per 32 x 32 tile: one
+// warp per row, lane l looks at site (x0+l, y), its +x and +y neighbours
+// (periodic) and the plaquette they span. Equal keys inside a warp are merged
+// with __match_any_sync, then in a shared set; the tile's unique links are
+// appended to the instance's link list.
+// ---------------------------------------------------------------------------
+__global__ __launch_bounds__(VTHREADS) void k_links(Pools P, StepTable T) {
+    __shared__ unsigned long long s_set[VEDGESET];
+    const int b = blockIdx.x;
+    const int a = seg_of_int(T.tileV_pre, T.n_act, b);
+    const int inst = T.act[a];
+    const InstDesc& D = P.desc[inst];
+    const int K = min(P.st[inst].K, D.comp_cap);
+    if (K < 2) return;
+    const int t = b - T.tileV_pre[a];
+    const int tx = t % D.vtx, ty = t / D.vtx;
+    const int x0 = tx * VW, y0 = ty * VH;
+    const int ncols = min(VW, D.Lx - x0), nrows = min(VH, D.Ly - y0);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const long long MX = (long long)Q * D.Lx, MY = (long long)Q * D.Ly;
+    const int2* cq = P.cq + D.comp_off;
+    const int* own = P.owners + D.site_off;
+    for (int k = threadIdx.x; k < VEDGESET; k += VTHREADS) s_set[k] = EMPTY_KEY;
+    __syncthreads();
+    const int x = x0 + lane;
+    const int xr = (x + 1 == D.Lx) ? 0 : x + 1;
+    constexpr int RPW = VH / (VTHREADS / 32);   // rows per warp
+    // all of this warp's owner loads in flight at once
+    int o[RPW], rt[RPW], dn[RPW], dg[RPW];
+#pragma unroll
+    for (int i = 0; i < RPW; ++i) {
+        const int ly = warp + i * (VTHREADS / 32);
+        o[i] = rt[i] = dn[i] = dg[i] = -1;
+        if (ly < nrows && lane < ncols) {
+            const int y = y0 + ly;
+            const int yd = (y + 1 == D.Ly) ? 0 : y + 1;
+            const int* row = own + (long long)y * D.Lx;
+            const int* rowd = own + (long long)yd * D.Lx;
+            o[i] = __ldcs(row + x);
+            rt[i] = row[xr];
+            dn[i] = rowd[x];
+            dg[i] = rowd[xr];
         }
-        __syncthreads();
-        for (int k = threadIdx.x; k < VEDGESET; k += VTHREADS)
-            if (s_set[k] != EMPTY_KEY) edge_global_insert(P, D, inst, s_set[k]);
     }
+#pragma unroll
+    for (int i = 0; i < RPW; ++i) {
+        unsigned long long kh = EMPTY_KEY, kv = EMPTY_KEY, kp = EMPTY_KEY;
+        if (o[i] >= 0) {
+            if (o[i] != rt[i]) kh = edge_key(o[i], rt[i]);
+            if (o[i] != dn[i]) kv = edge_key(o[i], dn[i]);
+            if (o[i] != rt[i] && o[i] != dn[i] && o[i] != dg[i] && rt[i] != dn[i] && rt[i] != dg[i] && dn[i] != dg[i])
+                kp = plaquette_key(o[i], rt[i], dg[i], dn[i], cq, MX, MY);
+        }
+        if (!warp_set_insert(s_set, VEDGESET, kh)) edge_global_insert(P, D, inst, kh);
+        if (!warp_set_insert(s_set, VEDGESET, kv)) edge_global_insert(P, D, inst, kv);
+        if (__any_sync(0xffffffffu, kp != EMPTY_KEY) && !warp_set_insert(s_set, VEDGESET, kp))
+            edge_global_insert(P, D, inst, kp);
+    }
+    __syncthreads();
+    // append the tile's unique links (one reservation per warp); the hash
+    // insertion happens in k_merge_lists, off this block's critical path
+    for (int kb = warp * 32; kb < VEDGESET; kb += VTHREADS) {
+        const unsigned long long key = s_set[kb + lane];
+        const bool has = key != EMPTY_KEY;
+        const unsigned m = __ballot_sync(0xffffffffu, has);
+        if (!m) continue;
+        int base = 0;
+        if (lane == 0) base = atomicAdd(&P.st[inst].n_eapp, __popc(m));
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (has) {
+            const int pos = base + __popc(m & ((1u << lane) - 1u));
+            if (pos < D.edge_cap) P.ekeys[D.edge_off + pos] = key;
+            else edge_global_insert(P, D, inst, key);   // list full: insert directly
+        }
+    }
+}
+
+// appended links -> link hash (+ degrees); appended pairs -> overlap hash
+
+__global__ void k_merge_lists(Pools P, StepTable T) {
+    const long long* pe = pre_arr(T, PRE_EA);
+    const long long* po = pre_arr(T, PRE_OA);
+    const long long ne = pe[T.n_act], no = po[T.n_act];
+    for (long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x; g < ne + no;
+         g += (long long)gridDim.x * blockDim.x) {
+        if (g < ne) {
+            const int a = seg_of(pe, T.n_act, g);
+            const int inst = T.act[a];
+            const InstDesc& D = P.desc[inst];
+            edge_global_insert(P, D, inst, P.ekeys[D.edge_off + (g - pe[a])]);
+        } else {
+            const long long h = g - ne;
+            const int a = seg_of(po, T.n_act, h);
+            const int inst = T.act[a];
+            const InstDesc& D = P.desc[inst];
+            const long long j = D.ovl_off + (h - po[a]);
+            ovl_global_insert(P, D, inst, P.oapp_key[j], P.oapp_cnt[j]);
+        }
+    }
+}
+
+void launch_merge_lists(const Launch& L) {
+    launch_plan(L, 0);
+    k_merge_lists<<<L.grid_items, 256, 0, L.s>>>(L.P, L.T);
+    ++*L.nlaunch;
 }
 
 void launch_voronoi(const Launch& L) {
     k_voronoi<<<L.total_tilesV, VTHREADS, 0, L.s>>>(L.P, L.T);
+    ++*L.nlaunch;
+    k_links<<<L.total_tilesV, VTHREADS, 0, L.s>>>(L.P, L.T);
     ++*L.nlaunch;
 }
 
