@@ -3,9 +3,11 @@
 
 Default workload: 64 frames of a 1024x1024 periodic smoothed-noise lattice
 (sigma 4, threshold 0.5, shear 0.005 per frame + N(0, 0.01)), processed in
-order through vd_push_frame. One step = the whole 64-frame sequence
-(67.1M sites); the 256 MiB of input frames is resident in HBM and larger
-than L2 (129 MB), so every frame is read cold.
+order. One step = the whole 64-frame sequence (67.1M sites) pushed through
+a frame-sequence batch (every stage launched once for all 64 frames); the
+plain one-frame-per-call path is timed too and reported beside it. The
+256 MiB of input frames is resident in HBM and larger than L2 (129 MB), so
+every frame is read cold.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -35,11 +37,8 @@ from paper_1607_00908_gb300 import inputs  # noqa: E402
 METRIC = "Gsites/s full detect pipeline"
 UNIT = "Gsites/s"
 
-# Algorithmic bytes per site of each pipeline stage:
-#   labelling tiles: field read 4 + foreground bit write 1/8
-#   label pass:      foreground bit read 1/8 + label write 4 + past label read 4
-#   voronoi:         owner write 4
-STAGE_BYTES_PER_SITE = {0: 4.125, 2: 8.125, 3: 4.0}
+# The pipeline's algorithmic traffic per site: field read 4, past label read
+# 4, label write 4, owner write 4.
 PIPELINE_BYTES_PER_SITE = 16.0
 
 
@@ -192,6 +191,32 @@ def run_reference(args, world, rank):
     print(json.dumps(line), flush=True)
 
 
+def stage_bytes(sequence: bool):
+    """Algorithmic bytes per site of the stages that touch every site.
+
+    stage 0 threshold + tile union-find: field read 4, foreground bit write and
+            read 1/8 + 1/8
+    stage 2 label pass: foreground bits 1/8, label write 4, plus the past
+            labels: read 4 in the label pass (frame from an earlier push), or
+            read 4 + 4 (labels now and past) by the overlap pass (frame
+            sequence, past frame written in the same push)
+    stage 3 Voronoi owners + links: owner write 4, owner read 4
+    """
+    return {0: 4.25, 2: 12.125 if sequence else 8.125, 3: 8.0}
+
+
+def roofline_of(stage_ms, names, launches_per_stage, sites_per_launch, sequence, peak, peak_kind):
+    sb = stage_bytes(sequence)
+    dom = max(sb, key=lambda k: stage_ms[k])
+    avg_ms = stage_ms[dom] / launches_per_stage
+    bytes_per_launch = sb[dom] * sites_per_launch
+    achieved = bytes_per_launch / (avg_ms / 1e3) / 1e9
+    return {"bound": "hbm", "kernel": names[dom], "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "peak_kind": peak_kind, "traffic": None,
+            "bytes_per_site": sb[dom], "bytes_per_launch": bytes_per_launch, "avg_launch_ms": avg_ms,
+            "stage_ms_per_launch": {names[k]: stage_ms[k] / launches_per_stage for k in range(len(names))}}
+
+
 def run_ours(args, world, rank, local):
     import torch
     from paper_1607_00908_gb300 import vd
@@ -204,58 +229,46 @@ def run_ours(args, world, rank, local):
         torch.cuda.set_device(0)
     vd.lib()
     desc, frames = workload(args.workload, args.frames)
+    n = len(frames)
     Ly, Lx = frames[0].shape
-    sites_per_step = len(frames) * Lx * Ly
+    sites_per_step = n * Lx * Ly
     s = torch.cuda.Stream()
     dev = [torch.from_numpy(F).cuda() for F in frames]
     torch.cuda.synchronize()
-    det = vd.Detector(Lx, Ly, stream=s.cuda_stream)
+    peak, peak_kind = read_peaks()
 
-    def step():
-        for f in dev:
-            det.push(f)
-
+    # ---- headline: the whole frame sequence per push (one launch per stage) ----
+    seq = vd.Batch([(Lx, Ly)], sequence=n, stream=s.cuda_stream)
     for _ in range(args.warmup):
-        step()
+        seq.push(dev)
     torch.cuda.synchronize()
-
-    # ---- headline: device-resident inputs, graph replay per frame ----
     clocks = Clocks(local)
     clocks.start()
-    launches0 = det.timing()[2]
+    launches0 = seq.timing()[2]
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     barrier(world)
     torch.cuda.synchronize()
     e0.record(s)
     for _ in range(args.steps):
-        step()
+        seq.push(dev)
     e1.record(s)
     torch.cuda.synchronize()
     barrier(world)
     ms = e0.elapsed_time(e1)
     clk = clocks.stop()
-    launches = det.timing()[2] - launches0
+    launches = seq.timing()[2] - launches0
     ms_max = max_over_ranks(ms, world)
     value = world * sites_per_step * args.steps / (ms_max / 1e3) / 1e9
 
     # ---- roofline: per-stage CUDA events on the library stream, same work ----
-    det.set_timing(True)
-    det.timing()
+    seq.set_timing(True)
+    seq.timing()
     for _ in range(args.steps):
-        step()
-    stage_ms, names, _, _ = det.timing()
-    det.set_timing(False)
-    n_launch = args.steps * len(frames)
-    dom = max(STAGE_BYTES_PER_SITE, key=lambda k: stage_ms[k])
-    avg_ms = stage_ms[dom] / n_launch
-    bytes_per_launch = STAGE_BYTES_PER_SITE[dom] * Lx * Ly
-    peak, peak_kind = read_peaks()
-    achieved = bytes_per_launch / (avg_ms / 1e3) / 1e9
-    roofline = {"bound": "hbm", "kernel": names[dom], "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "peak_kind": peak_kind, "traffic": None,
-                "bytes_per_launch": bytes_per_launch, "avg_launch_ms": avg_ms,
-                "stage_ms_per_frame": {names[k]: stage_ms[k] / n_launch for k in range(len(names))},
-                "pipeline_frac_16B_per_site": value * PIPELINE_BYTES_PER_SITE / peak}
+        seq.push(dev)
+    stage_ms, names, _, _ = seq.timing()
+    seq.set_timing(False)
+    roofline = roofline_of(stage_ms, names, args.steps, sites_per_step, n > 1, peak, peak_kind)
+    roofline["pipeline_frac_16B_per_site"] = value * PIPELINE_BYTES_PER_SITE / peak
 
     # ---- end to end through the C ABI with host buffers ----
     host = [torch.from_numpy(F).pin_memory() for F in frames]
@@ -264,15 +277,33 @@ def run_ours(args, world, rank, local):
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
-        for h in host:
-            vd._check(vd.vd_push_frame_host(det.h, h.data_ptr(), Lx), "vd_push_frame_host")
-            ch = det.changes()
+        seq.push_host_ptrs([h.data_ptr() for h in host])
+        for i in range(n):
+            ch = seq.changes(i)
             d2h += 40 + 16 * len(ch["breaking"]) + 8 * len(ch["arising"]) + len(ch["active"])
     torch.cuda.synchronize()
-    e2e_dt = time.perf_counter() - t0
-    e2e_dt = max_over_ranks(e2e_dt, world)
+    e2e_dt = max_over_ranks(time.perf_counter() - t0, world)
     e2e = {"value": world * sites_per_step * e2e_steps / e2e_dt / 1e9, "unit": UNIT,
-           "h2d_bytes_per_step": 4 * sites_per_step, "d2h_bytes_per_step": int(d2h / e2e_steps)}
+           "h2d_bytes_per_step": 4 * sites_per_step, "d2h_bytes_per_step": int(d2h / e2e_steps),
+           "path": "vd_batch_push_host + vd_batch_get_changes for every frame"}
+    seq.close()
+
+    # ---- the plain per-frame path (vd_push_frame, one frame per call) ----
+    det = vd.Detector(Lx, Ly, stream=s.cuda_stream)
+    for F in dev[: min(n, 4)]:
+        det.push(F)
+    torch.cuda.synchronize()
+    plain_steps = max(1, min(args.steps, 3))
+    e0.record(s)
+    for _ in range(plain_steps):
+        for F in dev:
+            det.push(F)
+    e1.record(s)
+    torch.cuda.synchronize()
+    plain_ms = max_over_ranks(e0.elapsed_time(e1), world)
+    plain = {"value": world * sites_per_step * plain_steps / (plain_ms / 1e3) / 1e9, "unit": UNIT,
+             "path": "vd_push_frame per frame (graph replay)", "ms_per_frame": plain_ms / plain_steps / n}
+    det.close()
 
     if rank == 0:
         cpu = None
@@ -284,14 +315,14 @@ def run_ours(args, world, rank, local):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
-            "config": {"workload": desc, "sites_per_step": sites_per_step, "path": "vd_push_frame per frame",
-                       "l2_policy": "inputs larger than L2 (256 MiB of frames, each read once per step)",
+            "config": {"workload": desc, "sites_per_step": sites_per_step,
+                       "path": f"vd_batch_create_sequence: {n} frames per push, one launch per stage",
+                       "l2_policy": "inputs larger than L2 (each step reads all frames once)",
                        "parallelism": f"replicas x{world}"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
-            "gpu_launches": launches,
+            "gpu_launches": launches, "plain_per_frame": plain,
         }
         print(json.dumps(line), flush=True)
-    det.close()
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()

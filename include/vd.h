@@ -169,9 +169,22 @@ typedef struct vd_batch vd_batch;
 
 /* `cfgs[i]` describes instance i; all share cfgs[0].stream. */
 vd_status vd_batch_create(const vd_config* cfgs, int32_t n, vd_batch** out);
+/* Frame sequence of one lattice as a batch: the n instances are n
+ * consecutive frames of the same field. Instance i's past frame is instance
+ * i-1 of the same vd_batch_push (instance 0's is instance n-1 of the
+ * previous push), so each push advances the sequence by n frames with every
+ * stage launched once for all of them (Sections 3.1-3.2.4 per frame, as in
+ * vd_push_frame). Getters take the frame's position 0..n-1 in the last push;
+ * vd_changes.frame_index counts frames since creation. */
+vd_status vd_batch_create_sequence(const vd_config* cfg, int32_t n_frames, vd_batch** out);
 /* `d_fields` is a HOST array of n device pointers (each Ly*pitch floats,
  * pitch = Lx); instance i reads d_fields[i]. Enqueues one step. */
 vd_status vd_batch_push(vd_batch* b, const float* const* d_fields);
+/* Same with HOST fields (h_fields[i]: Ly*Lx floats, row-major): each is
+ * copied into a batch-owned device buffer on the batch stream, then the step
+ * is enqueued. Pinned host memory makes the copies asynchronous; the caller
+ * keeps the host arrays unchanged until the stream has consumed them. */
+vd_status vd_batch_push_host(vd_batch* b, const float* const* h_fields);
 /* Advance only the `n_active` instances listed in `active` (host array of
  * instance ids, each at most once); the others keep their state. */
 vd_status vd_batch_push_subset(vd_batch* b, const int32_t* active, int32_t n_active,
@@ -182,6 +195,11 @@ vd_status vd_batch_get_owners(vd_batch* b, int32_t i, int32_t* out, int64_t cap,
 vd_status vd_batch_get_edges(vd_batch* b, int32_t i, uint64_t* out, int64_t cap, int64_t* n);
 vd_status vd_batch_get_centroids_q10(vd_batch* b, int32_t i, int32_t* out, int64_t cap, int64_t* n);
 vd_status vd_batch_get_counts(vd_batch* b, int32_t i, int32_t* K, int32_t* n_edges, int64_t* frame_index);
+/* Stage timing of a batch (as vd_set_timing / vd_get_timing; *n_steps
+ * counts pushes). */
+vd_status vd_batch_set_timing(vd_batch* b, int32_t enable);
+vd_status vd_batch_get_timing(vd_batch* b, double* stage_ms, int32_t cap, int32_t* n_stages,
+                              int64_t* n_kernel_launches, int64_t* n_steps);
 vd_status vd_batch_destroy(vd_batch* b);
 
 #ifdef __cplusplus

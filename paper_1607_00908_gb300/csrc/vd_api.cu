@@ -80,14 +80,16 @@ struct vd_batch {
     long long* d_pitches = nullptr;
     std::vector<const float*> h_fields;
     std::vector<long long> h_pitches;
-    // host input staging for vd_push_frame_host (instance 0)
+    // host input staging for vd_push_frame_host (instance 0) and vd_batch_push_host
     float* d_host_field = nullptr;
+    std::vector<float*> d_inputs;
     // graph of the all-active step
     cudaGraphExec_t graph = nullptr;
     bool use_graph = false;
     long long frames_pushed = 0;
     long long launches = 0;
     long long graph_launches = 0;
+    bool sequence = false;
     // stage timing
     bool timing = false;
     std::vector<cudaEvent_t> ev_pool;
@@ -156,6 +158,7 @@ void build_table(vd_batch* b, const std::vector<int>& act, StepTables& T, bool a
 Launch make_launch(vd_batch* b, const StepTables& T) {
     Launch L;
     L.nlaunch = &b->launches;
+    L.sequence = b->sequence;
     L.s = b->s;
     L.P = b->P;
     L.T.n_act = T.n_act;
@@ -205,13 +208,14 @@ void enqueue_step(vd_batch* b, const Launch& L, bool timed) {
     mark(b, timed);
 }
 
-vd_status create_batch(const vd_config* cfgs, int n, vd_batch** out) {
+vd_status create_batch(const vd_config* cfgs, int n, vd_batch** out, bool sequence = false) {
     if (!cfgs || n < 1 || !out) return VD_ERR_INVALID;
     for (int i = 0; i < n; ++i)
         if (!valid_cfg(cfgs[i])) return VD_ERR_INVALID;
     vd_batch* b = new (std::nothrow) vd_batch();
     if (!b) return VD_ERR_OOM;
     b->n = n;
+    b->sequence = sequence && n > 1;
     b->s = (cudaStream_t)cfgs[0].stream;
     b->desc.resize(n);
     long long site = 0, word = 0, tile = 0, border = 0, comp = 0, edge = 0, eh = 0, oh = 0, bucket = 0, ovl = 0;
@@ -230,6 +234,10 @@ vd_status create_batch(const vd_config* cfgs, int n, vd_batch** out) {
         D.vtx = (c.Lx + VW - 1) / VW;
         D.vty = (c.Ly + VH - 1) / VH;
         D.wpr = (c.Lx + 31) / 32;
+        // frame sequence: instance i's past frame is instance i-1 of the same
+        // step, instance 0's is instance n-1 of the previous step
+        D.seq_prev = sequence ? (i == 0 ? n - 1 : i - 1) : i;
+        D.seq_same = (sequence && i > 0) ? 1 : 0;
         long long kcap = c.max_components ? c.max_components
                                           : (N <= 65536 ? (N + 1) / 2 : std::max<long long>(N / 8, 65536));
         kcap = std::min<long long>(kcap, (N + 1) / 2);
@@ -454,7 +462,7 @@ vd_status get_changes(vd_batch* b, int i, vd_changes* out) {
     if (rs) return rs;
     if (st.frame == 0) return VD_ERR_STATE;
     const InstDesc& D = b->desc[i];
-    out->frame_index = st.frame - 1;
+    out->frame_index = b->sequence ? (st.frame - 1) * b->n + i : st.frame - 1;
     out->n_prev = st.rep_K_prev;
     out->n_now = st.K;
     out->n_matched = st.n_matched;
@@ -505,6 +513,7 @@ vd_status get_array(vd_batch* b, int i, int which, void* out, int64_t cap, int64
             break;
         }
         case 4: cnt = st.rep_K_prev; src = b->P.phi + D.comp_off; break;
+        case 5: cnt = st.K; esz = 1; src = b->P.active + D.comp_off; break;
         default: return VD_ERR_INVALID;
     }
     if (n) *n = cnt;
@@ -609,20 +618,19 @@ vd_status vd_get_match(vd_ctx* ctx, int32_t* phi, int64_t cap, int64_t* n) {
     return ctx ? get_array(ctx->b, 0, 4, phi, cap, n) : VD_ERR_INVALID;
 }
 
-vd_status vd_set_timing(vd_ctx* ctx, int32_t enable) {
-    if (!ctx) return VD_ERR_INVALID;
-    ctx->b->timing = enable != 0;
+vd_status vd_batch_set_timing(vd_batch* b, int32_t enable) {
+    if (!b) return VD_ERR_INVALID;
+    b->timing = enable != 0;
     return VD_OK;
 }
 
-vd_status vd_get_timing(vd_ctx* ctx, double* stage_ms, int32_t cap, int32_t* n_stages,
-                        int64_t* n_kernel_launches, int64_t* n_frames) {
-    if (!ctx) return VD_ERR_INVALID;
-    vd_batch* b = ctx->b;
+vd_status vd_batch_get_timing(vd_batch* b, double* stage_ms, int32_t cap, int32_t* n_stages,
+                              int64_t* n_kernel_launches, int64_t* n_steps) {
+    if (!b) return VD_ERR_INVALID;
     if (cudaStreamSynchronize(b->s) != cudaSuccess) return VD_ERR_CUDA;
     if (n_stages) *n_stages = N_STAGES;
     if (n_kernel_launches) *n_kernel_launches = b->launches;
-    if (n_frames) *n_frames = b->frames_pushed;
+    if (n_steps) *n_steps = b->frames_pushed;
     double acc[N_STAGES] = {0, 0, 0, 0, 0};
     const int per = N_STAGES + 1;
     for (int g = 0; g + per <= b->ev_used; g += per) {
@@ -639,6 +647,15 @@ vd_status vd_get_timing(vd_ctx* ctx, double* stage_ms, int32_t cap, int32_t* n_s
     return VD_OK;
 }
 
+vd_status vd_set_timing(vd_ctx* ctx, int32_t enable) {
+    return ctx ? vd_batch_set_timing(ctx->b, enable) : VD_ERR_INVALID;
+}
+
+vd_status vd_get_timing(vd_ctx* ctx, double* stage_ms, int32_t cap, int32_t* n_stages,
+                        int64_t* n_kernel_launches, int64_t* n_frames) {
+    return ctx ? vd_batch_get_timing(ctx->b, stage_ms, cap, n_stages, n_kernel_launches, n_frames) : VD_ERR_INVALID;
+}
+
 const char* vd_stage_name(int32_t stage) {
     if (stage < 0 || stage >= N_STAGES) return "";
     return STAGE_NAMES[stage];
@@ -653,7 +670,15 @@ vd_status vd_destroy(vd_ctx* ctx) {
 
 vd_status vd_batch_create(const vd_config* cfgs, int32_t n, vd_batch** out) {
     vd_status r = create_batch(cfgs, n, out);
-    if (!r) (*out)->use_graph = true;
+    if (!r) (*out)->use_graph = (cfgs[0].stream != nullptr) && !getenv("VD_NO_GRAPH");
+    return r;
+}
+
+vd_status vd_batch_create_sequence(const vd_config* cfg, int32_t n_frames, vd_batch** out) {
+    if (!cfg || n_frames < 1 || !out) return VD_ERR_INVALID;
+    std::vector<vd_config> cfgs(n_frames, *cfg);
+    vd_status r = create_batch(cfgs.data(), n_frames, out, true);
+    if (!r) (*out)->use_graph = (cfg->stream != nullptr) && !getenv("VD_NO_GRAPH");
     return r;
 }
 
@@ -670,8 +695,27 @@ vd_status vd_batch_push(vd_batch* b, const float* const* d_fields) {
     return run_all(b);
 }
 
+vd_status vd_batch_push_host(vd_batch* b, const float* const* h_fields) {
+    if (!b || !h_fields) return VD_ERR_INVALID;
+    if (b->d_inputs.empty()) {
+        b->d_inputs.resize(b->n);
+        for (int i = 0; i < b->n; ++i) {
+            b->d_inputs[i] = b->mem.alloc<float>((long long)b->desc[i].Lx * b->desc[i].Ly);
+            if (!b->mem.ok) return VD_ERR_OOM;
+        }
+    }
+    for (int i = 0; i < b->n; ++i) {
+        if (!h_fields[i]) return VD_ERR_INVALID;
+        const size_t bytes = sizeof(float) * (size_t)b->desc[i].Lx * b->desc[i].Ly;
+        if (cudaMemcpyAsync(b->d_inputs[i], h_fields[i], bytes, cudaMemcpyHostToDevice, b->s) != cudaSuccess)
+            return VD_ERR_CUDA;
+    }
+    return vd_batch_push(b, b->d_inputs.data());
+}
+
 vd_status vd_batch_push_subset(vd_batch* b, const int32_t* active, int32_t n_active, const float* const* d_fields) {
     if (!b || !active || !d_fields || n_active < 0 || n_active > b->n) return VD_ERR_INVALID;
+    if (b->sequence) return VD_ERR_INVALID;   // a frame sequence always advances as a whole
     if (n_active == 0) return VD_OK;
     std::vector<int> act(active, active + n_active);
     std::vector<char> seen(b->n, 0);

@@ -573,7 +573,9 @@ __global__ __launch_bounds__(32 * LBL_WARPS) void k_labels(Pools P, StepTable T)
     const int tx = t % D.ntx, ty = t / D.ntx;
     const int x0 = tx * TW, y0 = ty * TH;
     const int now = S.slot ^ 1;
-    const bool with_prev = S.has_prev != 0;
+    // past labels are read here only when they come from an earlier step; a
+    // past frame written in this step is compared by k_overlap afterwards
+    const bool with_prev = S.has_prev != 0 && !S.prev_same;
     const int Lx = D.Lx;
 
     for (int k = lane; k < WSET; k += 32) {
@@ -602,7 +604,7 @@ __global__ __launch_bounds__(32 * LBL_WARPS) void k_labels(Pools P, StepTable T)
     const bool in0 = x0 + lane < Lx, in1 = x0 + 32 + lane < Lx;
     const int nrows = min(TH, D.Ly - y0);
     int* out = P.labels[now] + D.site_off + (long long)y0 * Lx + x0 + lane;
-    const int* prv = P.labels[now ^ 1] + D.site_off + (long long)y0 * Lx + x0 + lane;
+    const int* prv = P.labels[S.prev_buf] + P.desc[S.prev_inst].site_off + (long long)y0 * Lx + x0 + lane;
     unsigned long long cur0 = EMPTY_KEY, cur1 = EMPTY_KEY;
     unsigned c0 = 0, c1 = 0;
     for (int rb = 0; rb < nrows; rb += 8) {
@@ -671,6 +673,88 @@ __global__ __launch_bounds__(32 * LBL_WARPS) void k_labels(Pools P, StepTable T)
     }
 }
 
+// Overlap histogram for frames whose past frame was labelled in the same step
+// (frame sequences): reads both label arrays, one warp per 64 x 32 tile.
+__global__ __launch_bounds__(32 * LBL_WARPS) void k_overlap(Pools P, StepTable T) {
+    __shared__ unsigned long long s_key[LBL_WARPS][WSET];
+    __shared__ unsigned s_cnt[LBL_WARPS][WSET];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int b = blockIdx.x * LBL_WARPS + w;
+    if (b >= T.tileA_pre[T.n_act]) return;
+    const int a = seg_of_int(T.tileA_pre, T.n_act, b);
+    const int inst = T.act[a];
+    const InstState& S = P.st[inst];
+    if (!(S.has_prev && S.prev_same)) return;
+    const InstDesc& D = P.desc[inst];
+    unsigned long long* skey = s_key[w];
+    unsigned* scnt = s_cnt[w];
+    const int t = b - T.tileA_pre[a];
+    const int tx = t % D.ntx, ty = t / D.ntx;
+    const int x0 = tx * TW, y0 = ty * TH;
+    const int Lx = D.Lx;
+    for (int k = lane; k < WSET; k += 32) {
+        skey[k] = EMPTY_KEY;
+        scnt[k] = 0;
+    }
+    __syncwarp();
+    const bool in0 = x0 + lane < Lx, in1 = x0 + 32 + lane < Lx;
+    const int nrows = min(TH, D.Ly - y0);
+    const int* cur = P.labels[S.slot ^ 1] + D.site_off + (long long)y0 * Lx + x0 + lane;
+    const int* prv = P.labels[S.prev_buf] + P.desc[S.prev_inst].site_off + (long long)y0 * Lx + x0 + lane;
+    unsigned long long cur0 = EMPTY_KEY, cur1 = EMPTY_KEY;
+    unsigned c0 = 0, c1 = 0;
+    for (int rb = 0; rb < nrows; rb += 8) {
+        int l0[8], l1[8], p0[8], p1[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const bool ok = rb + k < nrows;
+            const long long o = (long long)(rb + k) * Lx;
+            l0[k] = (ok && in0) ? __ldcs(cur + o) : -1;
+            l1[k] = (ok && in1) ? __ldcs(cur + o + 32) : -1;
+            p0[k] = (ok && in0) ? __ldcs(prv + o) : -1;
+            p1[k] = (ok && in1) ? __ldcs(prv + o + 32) : -1;
+        }
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const unsigned long long k0 = (l0[k] >= 0 && p0[k] >= 0) ? (((unsigned long long)(unsigned)p0[k] << 32) | (unsigned)l0[k]) : EMPTY_KEY;
+            const unsigned long long k1 = (l1[k] >= 0 && p1[k] >= 0) ? (((unsigned long long)(unsigned)p1[k] << 32) | (unsigned)l1[k]) : EMPTY_KEY;
+            if (k0 != cur0) {
+                if (cur0 != EMPTY_KEY) ovl_add_w(skey, scnt, P, D, inst, cur0, c0);
+                cur0 = k0;
+                c0 = 0;
+            }
+            if (k0 != EMPTY_KEY) ++c0;
+            if (k1 != cur1) {
+                if (cur1 != EMPTY_KEY) ovl_add_w(skey, scnt, P, D, inst, cur1, c1);
+                cur1 = k1;
+                c1 = 0;
+            }
+            if (k1 != EMPTY_KEY) ++c1;
+        }
+    }
+    if (cur0 != EMPTY_KEY) ovl_add_w(skey, scnt, P, D, inst, cur0, c0);
+    if (cur1 != EMPTY_KEY) ovl_add_w(skey, scnt, P, D, inst, cur1, c1);
+    __syncwarp();
+    for (int kb = 0; kb < WSET; kb += 32) {
+        const unsigned long long key = skey[kb + lane];
+        const bool has = key != EMPTY_KEY;
+        const unsigned m = __ballot_sync(0xffffffffu, has);
+        if (!m) continue;
+        int base = 0;
+        if (lane == 0) base = atomicAdd(&P.st[inst].n_oapp, __popc(m));
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (has) {
+            const int pos = base + __popc(m & ((1u << lane) - 1u));
+            if (pos < D.ovl_cap) {
+                P.oapp_key[D.ovl_off + pos] = key;
+                P.oapp_cnt[D.ovl_off + pos] = scnt[kb + lane];
+            } else {
+                ovl_global_insert(P, D, inst, key, scnt[kb + lane]);
+            }
+        }
+    }
+}
+
 void launch_ccl_tiles(const Launch& L) {
     {
         const long long need = (L.total_words + 255) / 256;
@@ -705,6 +789,10 @@ void launch_ccl_rest(const Launch& L) {
 void launch_labels(const Launch& L) {
     k_labels<<<(L.total_tilesA + LBL_WARPS - 1) / LBL_WARPS, 32 * LBL_WARPS, 0, L.s>>>(L.P, L.T);
     ++*L.nlaunch;
+    if (L.sequence) {
+        k_overlap<<<(L.total_tilesA + LBL_WARPS - 1) / LBL_WARPS, 32 * LBL_WARPS, 0, L.s>>>(L.P, L.T);
+        ++*L.nlaunch;
+    }
 }
 
 }  // namespace vd

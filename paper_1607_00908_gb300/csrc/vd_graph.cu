@@ -35,8 +35,23 @@ __global__ void k_step_begin(Pools P, StepTable T) {
     for (int a = blockIdx.x * blockDim.x + threadIdx.x; a < T.n_act; a += gridDim.x * blockDim.x) {
         const int inst = T.act[a];
         InstState& S = P.st[inst];
+        const InstDesc& D = P.desc[inst];
         S.field = P.fields[inst];
         S.pitch = P.pitches[inst];
+        // where this step's past frame lives
+        const int pi = D.seq_prev;
+        const InstState& SP = P.st[pi];
+        S.prev_inst = pi;
+        S.prev_same = D.seq_same;
+        if (D.seq_same) {
+            S.prev_buf = SP.slot ^ 1;     // written by instance pi in this step
+            S.has_prev = 1;
+            S.K_prev = 0;                 // known after labelling (k_plan)
+        } else {
+            S.prev_buf = SP.slot;         // written by instance pi in an earlier step
+            S.has_prev = (SP.frame > 0 && SP.last_ok) ? 1 : 0;
+            S.K_prev = S.has_prev ? SP.Kb[SP.slot] : 0;
+        }
         S.K = 0;
         S.E = 0;
         S.n_matched = 0;
@@ -57,14 +72,17 @@ __global__ void k_step_finish(Pools P, StepTable T) {
         const int inst = T.act[a];
         InstState& S = P.st[inst];
         S.err |= P.g->err;
+        // a past frame from this step that overflowed makes this frame's changes unreliable
+        if (S.has_prev && S.prev_same && P.st[S.prev_inst].err) S.err |= ERR_PREV;
         const int ecap = P.desc[inst].edge_cap;
         S.E = S.n_edge_list < ecap ? S.n_edge_list : ecap;
         S.rep_K_prev = S.has_prev ? S.K_prev : 0;
-        S.K_prev = S.K;
+        const int now = S.slot ^ 1;
+        S.Kb[now] = S.K;
+        S.Eb[now] = S.E;
         S.E_prev = S.E;
-        S.slot ^= 1;
-        // a frame whose device capacities overflowed is not used as a past frame
-        S.has_prev = S.err ? 0 : 1;
+        S.slot = now;
+        S.last_ok = S.err ? 0 : 1;
         S.frame += 1;
     }
 }
@@ -73,7 +91,7 @@ __global__ void k_step_finish(Pools P, StepTable T) {
 __global__ void k_edge_keys(Pools P, int inst, int slot, unsigned long long* out) {
     const InstDesc& D = P.desc[inst];
     const InstState& S = P.st[inst];
-    const int K = min(S.K_prev, D.comp_cap);   // after finish, K_prev holds this frame's K
+    const int K = min(S.Kb[slot], D.comp_cap);
     const int* ro = P.rowoff[slot] + D.comp_off;
     const int* cl = P.cols[slot] + D.edge_off;
     for (int a = blockIdx.x * blockDim.x + threadIdx.x; a < K; a += gridDim.x * blockDim.x) {
@@ -190,11 +208,12 @@ __global__ void k_match_phi(Pools P, StepTable T) {
 __global__ void k_translate_count(Pools P, StepTable T) {
     for_items(T, PRE_KP, [&](int inst, long long a) {
         const InstDesc& D = P.desc[inst];
-        const int prev = P.st[inst].slot;
+        const InstState& S = P.st[inst];
+        const InstDesc& DP = P.desc[S.prev_inst];
         const int pa = P.phi[D.comp_off + a];
         if (pa < 0) return;
-        const int* ro = P.rowoff[prev] + D.comp_off;
-        const int* cl = P.cols[prev] + D.edge_off;
+        const int* ro = P.rowoff[S.prev_buf] + DP.comp_off;
+        const int* cl = P.cols[S.prev_buf] + DP.edge_off;
         int cnt = 0;
         for (int k = ro[a]; k < ro[a + 1]; ++k) {
             const int pb = P.phi[D.comp_off + cl[k]];
@@ -209,11 +228,12 @@ __global__ void k_translate_count(Pools P, StepTable T) {
 __global__ void k_translate_scatter(Pools P, StepTable T) {
     for_items(T, PRE_KP, [&](int inst, long long a) {
         const InstDesc& D = P.desc[inst];
-        const int prev = P.st[inst].slot;
+        const InstState& S = P.st[inst];
+        const InstDesc& DP = P.desc[S.prev_inst];
         const int pa = P.phi[D.comp_off + a];
         if (pa < 0) return;
-        const int* ro = P.rowoff[prev] + D.comp_off;
-        const int* cl = P.cols[prev] + D.edge_off;
+        const int* ro = P.rowoff[S.prev_buf] + DP.comp_off;
+        const int* cl = P.cols[S.prev_buf] + DP.edge_off;
         for (int k = ro[a]; k < ro[a + 1]; ++k) {
             const int pb = P.phi[D.comp_off + cl[k]];
             if (pb < 0) continue;

@@ -41,6 +41,7 @@ enum : int {
     ERR_COMP_CAP = 8,       // more bubbles than max_components
     ERR_TIMEOUT = 16,       // bounded device wait expired
     ERR_FLIP_CAP = 32,
+    ERR_PREV = 64,          // the past frame (same step) had an error
 };
 
 // ---------------------------------------------------------------------------
@@ -53,6 +54,8 @@ struct InstDesc {
     int ntx, nty;            // labelling tiles
     int vtx, vty;            // Voronoi tiles
     int wpr;                 // 32-bit bitmask words per lattice row
+    int seq_prev;            // instance holding this instance's past frame (itself when independent)
+    int seq_same;            // 1: that past frame is produced in the same step (frame sequence)
     int pad0;
     long long site_off;      // labels / owners pools
     long long word_off;      // fg-bit / root-bit / rank pools (Ly * wpr words)
@@ -75,8 +78,14 @@ struct InstDesc {
 struct InstState {
     const float* field;      // this step's input
     long long pitch;
-    int slot;                // pools of the previous frame are at index `slot`, now = slot ^ 1
-    int has_prev;            // a previous frame exists
+    int slot;                // buffer of this instance's last finished frame; this step writes slot ^ 1
+    int has_prev;            // a past frame exists for this step
+    int prev_inst;           // instance and buffer holding the past frame (set at step begin)
+    int prev_buf;
+    int prev_same;           // the past frame is written in this step (by another instance)
+    int last_ok;             // the last finished frame had no device error
+    int Kb[2];               // bubbles of the frame stored in each buffer
+    int Eb[2];               // links of the frame stored in each buffer
     long long frame;         // index of the frame in progress / last finished
     int K, K_prev;           // bubbles now / previous frame
     int E, E_prev;           // links now / previous frame
@@ -382,6 +391,7 @@ __device__ __forceinline__ void ovl_global_insert(const Pools& P, const InstDesc
 // ---------------------------------------------------------------------------
 struct Launch {
     long long* nlaunch;  // host counter of kernel launches
+    bool sequence;       // some instance's past frame is produced in the same step
     cudaStream_t s;
     Pools P;
     StepTable T;

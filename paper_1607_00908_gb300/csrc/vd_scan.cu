@@ -46,6 +46,12 @@ __global__ void k_plan(Pools P, StepTable T, int with_comp) {
                     S.B = 4; S.nbx = 0; S.nby = 0;
                 }
             }
+            if (with_comp && S.prev_same) {
+                // the past frame was labelled in this step by instance prev_inst
+                const InstState& SP = P.st[S.prev_inst];
+                const int kp = SP.K < P.desc[S.prev_inst].comp_cap ? SP.K : P.desc[S.prev_inst].comp_cap;
+                S.K_prev = kp;
+            }
             long long v[NPRE];
             v[PRE_K] = S.K;
             v[PRE_KP] = S.has_prev ? S.K_prev : 0;

@@ -33,9 +33,10 @@ EXPORTS = (
     "vd_config_init", "vd_create", "vd_push_frame", "vd_push_frame_host", "vd_get_changes",
     "vd_get_counts", "vd_get_labels", "vd_get_centroids_q10", "vd_get_owners", "vd_get_edges",
     "vd_get_match", "vd_set_timing", "vd_get_timing", "vd_stage_name", "vd_destroy", "vd_status_string",
-    "vd_batch_create", "vd_batch_push", "vd_batch_push_subset", "vd_batch_get_changes",
+    "vd_batch_create", "vd_batch_create_sequence", "vd_batch_push", "vd_batch_push_host", "vd_batch_push_subset", "vd_batch_get_changes",
     "vd_batch_get_labels", "vd_batch_get_owners", "vd_batch_get_edges", "vd_batch_get_centroids_q10",
-    "vd_batch_get_counts", "vd_batch_destroy", "vd_voronoi_owners_static",
+    "vd_batch_get_counts", "vd_batch_set_timing", "vd_batch_get_timing", "vd_batch_destroy",
+    "vd_voronoi_owners_static",
 )
 
 
@@ -102,7 +103,9 @@ def lib():
         "vd_destroy": [VP],
         "vd_status_string": [I32],
         "vd_batch_create": [P(vd_config), I32, P(VP)],
+        "vd_batch_create_sequence": [P(vd_config), I32, P(VP)],
         "vd_batch_push": [VP, P(VP)],
+        "vd_batch_push_host": [VP, P(VP)],
         "vd_batch_push_subset": [VP, P(I32), I32, P(VP)],
         "vd_batch_get_changes": [VP, I32, P(vd_changes)],
         "vd_batch_get_labels": [VP, I32, VP, I64, P(I64)],
@@ -110,6 +113,8 @@ def lib():
         "vd_batch_get_edges": [VP, I32, VP, I64, P(I64)],
         "vd_batch_get_centroids_q10": [VP, I32, VP, I64, P(I64)],
         "vd_batch_get_counts": [VP, I32, P(I32), P(I32), P(I64)],
+        "vd_batch_set_timing": [VP, I32],
+        "vd_batch_get_timing": [VP, P(C.c_double), I32, P(I32), P(I64), P(I64)],
         "vd_batch_destroy": [VP],
         "vd_voronoi_owners_static": [VP, I32, I32, I32, VP, VP],
     }
@@ -349,19 +354,43 @@ class Detector(_Base):
 
 
 class Batch(_Base):
-    """Many lattices advanced together (vd_batch_*)."""
+    """Many lattices advanced together (vd_batch_*); with ``sequence=n`` one
+    lattice whose push takes n consecutive frames (vd_batch_create_sequence)."""
 
     def __init__(self, sizes, threshold: float = 0.5, polarity: int = VD_ABOVE, stream: int | None = None,
-                 max_components: int = 0):
+                 max_components: int = 0, sequence: int = 0):
         if stream is None:
             import torch
             stream = torch.cuda.current_stream().cuda_stream
         self.sizes = [(int(lx), int(ly)) for lx, ly in sizes]
-        cfgs = [vd_config_init(lx, ly, threshold, polarity, stream, max_components) for lx, ly in self.sizes]
-        self.h = vd_batch_create(cfgs)
+        if sequence:
+            lx, ly = self.sizes[0]
+            self.sizes = [(lx, ly)] * int(sequence)
+            cfg = vd_config_init(lx, ly, threshold, polarity, stream, max_components)
+            h = C.c_void_p()
+            _check(lib().vd_batch_create_sequence(C.byref(cfg), int(sequence), C.byref(h)), "vd_batch_create_sequence")
+            self.h = h
+        else:
+            cfgs = [vd_config_init(lx, ly, threshold, polarity, stream, max_components) for lx, ly in self.sizes]
+            self.h = vd_batch_create(cfgs)
 
     def push(self, fields) -> None:
         _check(vd_batch_push(self.h, [f.data_ptr() for f in fields]), "vd_batch_push")
+
+    def push_host_ptrs(self, host_ptrs) -> None:
+        arr = (C.c_void_p * len(host_ptrs))(*[C.c_void_p(p) for p in host_ptrs])
+        _check(lib().vd_batch_push_host(self.h, arr), "vd_batch_push_host")
+
+    def set_timing(self, on: bool) -> None:
+        _check(lib().vd_batch_set_timing(self.h, int(bool(on))), "vd_batch_set_timing")
+
+    def timing(self):
+        """(per-stage ms since the last call, stage names, kernel launches, pushes)."""
+        ms = (C.c_double * 16)()
+        n, kl, nf = C.c_int32(), C.c_int64(), C.c_int64()
+        _check(lib().vd_batch_get_timing(self.h, ms, 16, C.byref(n), C.byref(kl), C.byref(nf)), "vd_batch_get_timing")
+        names = [lib().vd_stage_name(i).decode() for i in range(n.value)]
+        return list(ms[: n.value]), names, kl.value, nf.value
 
     def push_subset(self, active, fields) -> None:
         _check(vd_batch_push_subset(self.h, list(active), [f.data_ptr() for f in fields]), "vd_batch_push_subset")

@@ -1,0 +1,98 @@
+"""GPU parity of the batched forms against the CPU oracle (exact).
+
+* Batch of lattices of uneven sizes advanced together (vd_batch_push).
+* Frame sequence (vd_batch_create_sequence): n consecutive frames per push,
+  instance i's past frame is instance i-1 of the same push.
+* Subsets of a batch advancing at different times (vd_batch_push_subset),
+  the mechanism the served form uses, and equality of every result with the
+  same lattice run alone.
+"""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+import oracle as O  # noqa: E402
+from paper_1607_00908_gb300 import inputs as I  # noqa: E402
+from paper_1607_00908_gb300 import vd  # noqa: E402
+
+
+def check(b, i, r, tag):
+    K, E, _ = b.counts(i)
+    assert K == r["K"], (tag, K, r["K"])
+    assert np.array_equal(b.labels(i), r["labels"]), f"{tag} labels"
+    assert np.array_equal(b.centroids(i), r["centroids"]), f"{tag} centroids"
+    assert np.array_equal(b.owners(i), r["owners"]), f"{tag} owners"
+    assert np.array_equal(b.edges(i), r["edges"]), f"{tag} edges"
+    ch = b.changes(i)
+    assert ch["K_prev"] == r["K_prev"], (tag, ch["K_prev"], r["K_prev"])
+    assert ch["n_matched"] == r["n_matched"], (tag, ch["n_matched"], r["n_matched"])
+    assert np.array_equal(ch["breaking"], r["breaking"]), f"{tag} breaking"
+    assert np.array_equal(ch["breaking_prev"], r["breaking_prev"]), f"{tag} breaking_prev"
+    assert np.array_equal(ch["arising"], r["arising"]), f"{tag} arising"
+    assert np.array_equal(ch["active"], r["active"]), f"{tag} active"
+
+
+def frames_for(L, sigma, seed, n, Lx=None):
+    return list(I.noise_frames(L, sigma, n, 0.03, seed, Lx=Lx))
+
+
+def test_uneven_batch_matches_per_instance_oracle():
+    specs = [(64, 64, 2.0), (96, 70, 3.0), (130, 130, 2.5), (200, 150, 4.0), (257, 257, 3.0), (33, 200, 2.0)]
+    n_frames = 3
+    seqs = [frames_for(ly, s, 10 + k, n_frames, Lx=lx) for k, (lx, ly, s) in enumerate(specs)]
+    b = vd.Batch([(lx, ly) for lx, ly, _ in specs])
+    refs = [O.Detector(lx, ly, voronoi="brute") for lx, ly, _ in specs]
+    for f in range(n_frames):
+        dev = [torch.from_numpy(seq[f]).cuda() for seq in seqs]
+        b.push(dev)
+        for i, ref in enumerate(refs):
+            check(b, i, ref.push(seqs[i][f]), f"inst {i} frame {f}")
+    b.close()
+
+
+@pytest.mark.parametrize("n_seq,pushes", [(4, 3), (1, 3), (7, 2)])
+def test_frame_sequence_matches_oracle(n_seq, pushes):
+    L = 150
+    frames = frames_for(L, 3.0, 77, n_seq * pushes)
+    b = vd.Batch([(L, L)], sequence=n_seq)
+    ref = O.Detector(L, L, voronoi="brute")
+    for p in range(pushes):
+        chunk = frames[p * n_seq:(p + 1) * n_seq]
+        b.push([torch.from_numpy(F).cuda() for F in chunk])
+        for i, F in enumerate(chunk):
+            r = ref.push(F)
+            check(b, i, r, f"push {p} frame {i}")
+            assert b.changes(i)["frame"] == p * n_seq + i
+    b.close()
+
+
+def test_subsets_and_alone_vs_mix():
+    """Instances advanced at different times give exactly the results each
+    lattice gets when run alone with vd_push_frame."""
+    specs = [(80, 80), (120, 90), (64, 130)]
+    seqs = [frames_for(ly, 3.0, 200 + k, 4, Lx=lx) for k, (lx, ly) in enumerate(specs)]
+    b = vd.Batch(specs)
+    alone = [vd.Detector(lx, ly) for lx, ly in specs]
+    refs = [O.Detector(lx, ly, voronoi="brute") for lx, ly in specs]
+    pos = [0, 0, 0]
+    schedule = [[0, 2], [1], [0, 1, 2], [2, 0], [1, 0], [1], [2]]
+    for act in schedule:
+        dev = [torch.from_numpy(seqs[i][pos[i]]).cuda() for i in act]
+        b.push_subset(act, dev)
+        for i, d in zip(act, dev):
+            alone[i].push(d)
+            r = refs[i].push(seqs[i][pos[i]])
+            check(b, i, r, f"subset inst {i} frame {pos[i]}")
+            assert np.array_equal(b.labels(i), alone[i].labels())
+            assert np.array_equal(b.owners(i), alone[i].owners())
+            ca, cb = b.changes(i), alone[i].changes()
+            assert np.array_equal(ca["breaking"], cb["breaking"]) and np.array_equal(ca["arising"], cb["arising"])
+            pos[i] += 1
+    b.close()
+    for d in alone:
+        d.close()
