@@ -202,6 +202,44 @@ vd_status vd_batch_get_timing(vd_batch* b, double* stage_ms, int32_t cap, int32_
                               int64_t* n_kernel_launches, int64_t* n_steps);
 vd_status vd_batch_destroy(vd_batch* b);
 
+/* ---------------------------------------------------------------------------
+ * Served form: frames of many simulations arrive over time; continuous
+ * batching. The server keeps every simulation's state resident (one batch
+ * instance per simulation) and runs steps over the simulations that have a
+ * waiting frame: at most one frame per simulation per step, at most
+ * max_batch simulations, admitted only while the resident state plus the
+ * frames in flight fit hbm_budget_bytes. Two steps are kept queued on the
+ * device, so frames that arrive while a step runs join the next one.
+ * ------------------------------------------------------------------------- */
+typedef struct vd_server vd_server;
+typedef struct vd_server_done {
+    int64_t ticket;             /* from vd_server_submit */
+    int32_t sim;
+    int32_t status;             /* VD_OK or the frame's device error */
+    int64_t t_submit_ns;        /* host steady-clock times */
+    int64_t t_done_ns;          /* when vd_server_poll saw the step finish */
+    int32_t n_bubbles, n_edges, n_breaking, n_arising;
+} vd_server_done;
+
+/* One config per simulation (all on sims[0].stream). Allocates all resident
+ * state; VD_ERR_CAPACITY when it alone exceeds the budget. */
+vd_status vd_server_create(const vd_config* sims, int32_t n_sims, int64_t hbm_budget_bytes, int32_t max_batch,
+                           vd_server** out);
+/* Queue one frame (device pointer, Ly*Lx floats) of simulation `sim`; the
+ * caller keeps it valid until the frame is reported done. */
+vd_status vd_server_submit(vd_server* sv, int32_t sim, const float* d_field, int64_t* ticket);
+/* Run the scheduler: retire finished steps (filling `done`, up to cap
+ * entries) and launch new steps. wait != 0 blocks until at least one frame
+ * finishes or nothing is in flight. */
+vd_status vd_server_poll(vd_server* sv, int32_t wait, vd_server_done* done, int32_t cap, int32_t* n_done);
+/* Results of a simulation's last finished frame; VD_ERR_STATE while one of
+ * its frames is in flight. */
+vd_status vd_server_get_changes(vd_server* sv, int32_t sim, vd_changes* out);
+vd_status vd_server_get_labels(vd_server* sv, int32_t sim, int32_t* out, int64_t cap, int64_t* n);
+vd_status vd_server_stats(vd_server* sv, int64_t* steps, int64_t* frames_done, int64_t* resident_bytes,
+                          int64_t* queued);
+vd_status vd_server_destroy(vd_server* sv);
+
 #ifdef __cplusplus
 }
 #endif

@@ -34,6 +34,7 @@ long long next_pow2(long long v) {
 struct DevBuf {
     std::vector<void*> ptrs;
     bool ok = true;
+    long long bytes = 0;
     template <class T>
     T* alloc(long long n) {
         if (n <= 0) n = 1;
@@ -43,6 +44,7 @@ struct DevBuf {
             cudaGetLastError();
             return nullptr;
         }
+        bytes += n * (long long)sizeof(T);
         ptrs.push_back(p);
         return static_cast<T*>(p);
     }
@@ -524,6 +526,37 @@ vd_status get_array(vd_batch* b, int i, int which, void* out, int64_t cap, int64
 }
 
 }  // namespace
+
+namespace vd {
+// per-step results of some instances, gathered on the device and copied
+// asynchronously into pinned host memory: 6 ints per instance
+// (K, E, n_breaking, n_arising, n_matched, err)
+__global__ void k_gather_counts(Pools P, const int* sims, int n, int* out) {
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+        const InstState& S = P.st[sims[k]];
+        out[6 * k + 0] = S.K;
+        out[6 * k + 1] = S.E;
+        out[6 * k + 2] = S.n_break;
+        out[6 * k + 3] = S.n_arise;
+        out[6 * k + 4] = S.n_matched;
+        out[6 * k + 5] = S.err;
+    }
+}
+}  // namespace vd
+
+long long vd_batch_resident_bytes(const vd_batch* b) { return b ? b->mem.bytes : 0; }
+
+vd_status vd_batch_gather_counts_async(vd_batch* b, const int* h_sims, int n, int* d_scratch, int* h_pinned_out) {
+    if (!b || n <= 0) return VD_ERR_INVALID;
+    int* d_sims = d_scratch;
+    int* d_out = d_scratch + n;
+    if (cudaMemcpyAsync(d_sims, h_sims, sizeof(int) * n, cudaMemcpyHostToDevice, b->s) != cudaSuccess) return VD_ERR_CUDA;
+    vd::k_gather_counts<<<1, 256, 0, b->s>>>(b->P, d_sims, n, d_out);
+    b->launches += 1;
+    if (cudaMemcpyAsync(h_pinned_out, d_out, sizeof(int) * 6 * n, cudaMemcpyDeviceToHost, b->s) != cudaSuccess)
+        return VD_ERR_CUDA;
+    return VD_OK;
+}
 
 extern "C" {
 

@@ -36,7 +36,8 @@ EXPORTS = (
     "vd_batch_create", "vd_batch_create_sequence", "vd_batch_push", "vd_batch_push_host", "vd_batch_push_subset", "vd_batch_get_changes",
     "vd_batch_get_labels", "vd_batch_get_owners", "vd_batch_get_edges", "vd_batch_get_centroids_q10",
     "vd_batch_get_counts", "vd_batch_set_timing", "vd_batch_get_timing", "vd_batch_destroy",
-    "vd_voronoi_owners_static",
+    "vd_voronoi_owners_static", "vd_server_create", "vd_server_submit", "vd_server_poll",
+    "vd_server_get_changes", "vd_server_get_labels", "vd_server_stats", "vd_server_destroy",
 )
 
 
@@ -67,6 +68,14 @@ class vd_changes(C.Structure):
         ("breaking_prev", C.POINTER(C.c_uint64)),
         ("arising", C.POINTER(C.c_uint64)), ("cap_arising", C.c_int32),
         ("active", C.POINTER(C.c_uint8)), ("cap_active", C.c_int32),
+    ]
+
+
+class vd_server_done(C.Structure):
+    _fields_ = [
+        ("ticket", C.c_int64), ("sim", C.c_int32), ("status", C.c_int32),
+        ("t_submit_ns", C.c_int64), ("t_done_ns", C.c_int64),
+        ("n_bubbles", C.c_int32), ("n_edges", C.c_int32), ("n_breaking", C.c_int32), ("n_arising", C.c_int32),
     ]
 
 
@@ -117,6 +126,13 @@ def lib():
         "vd_batch_get_timing": [VP, P(C.c_double), I32, P(I32), P(I64), P(I64)],
         "vd_batch_destroy": [VP],
         "vd_voronoi_owners_static": [VP, I32, I32, I32, VP, VP],
+        "vd_server_create": [P(vd_config), I32, I64, I32, P(VP)],
+        "vd_server_submit": [VP, I32, VP, P(I64)],
+        "vd_server_poll": [VP, I32, P(vd_server_done), I32, P(I32)],
+        "vd_server_get_changes": [VP, I32, P(vd_changes)],
+        "vd_server_get_labels": [VP, I32, VP, I64, P(I64)],
+        "vd_server_stats": [VP, P(I64), P(I64), P(I64), P(I64)],
+        "vd_server_destroy": [VP],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -429,6 +445,67 @@ class Batch(_Base):
     def close(self):
         if getattr(self, "h", None):
             vd_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """Served form (vd_server_*): frames of many simulations, continuous batching."""
+
+    def __init__(self, sizes, budget_bytes: int, max_batch: int = 64, threshold: float = 0.5,
+                 polarity: int = VD_ABOVE, stream: int | None = None, max_components: int = 0):
+        if stream is None:
+            import torch
+            stream = torch.cuda.current_stream().cuda_stream
+        self.sizes = [(int(lx), int(ly)) for lx, ly in sizes]
+        cfgs = (vd_config * len(sizes))(*[vd_config_init(lx, ly, threshold, polarity, stream, max_components)
+                                          for lx, ly in self.sizes])
+        h = C.c_void_p()
+        _check(lib().vd_server_create(cfgs, len(sizes), int(budget_bytes), int(max_batch), C.byref(h)),
+               "vd_server_create")
+        self.h = h
+        self._done = (vd_server_done * 1024)()
+
+    def submit(self, sim: int, field) -> int:
+        t = C.c_int64()
+        _check(lib().vd_server_submit(self.h, int(sim), C.c_void_p(field.data_ptr()), C.byref(t)), "vd_server_submit")
+        return t.value
+
+    def poll(self, wait: bool = False):
+        n = C.c_int32()
+        _check(lib().vd_server_poll(self.h, int(bool(wait)), self._done, 1024, C.byref(n)), "vd_server_poll")
+        return [(d.ticket, d.sim, d.status, d.t_submit_ns, d.t_done_ns, d.n_bubbles, d.n_edges, d.n_breaking,
+                 d.n_arising) for d in self._done[: n.value]]
+
+    def stats(self):
+        a, b, c, d = C.c_int64(), C.c_int64(), C.c_int64(), C.c_int64()
+        _check(lib().vd_server_stats(self.h, C.byref(a), C.byref(b), C.byref(c), C.byref(d)), "vd_server_stats")
+        return dict(steps=a.value, frames_done=b.value, resident_bytes=c.value, queued=d.value)
+
+    def labels(self, sim: int) -> np.ndarray:
+        lx, ly = self.sizes[sim]
+        out = np.empty(lx * ly, np.int32)
+        n = C.c_int64()
+        _check(lib().vd_server_get_labels(self.h, int(sim), out.ctypes.data_as(C.c_void_p), out.size, C.byref(n)),
+               "vd_server_get_labels")
+        return out.reshape(ly, lx)
+
+    def changes(self, sim: int) -> dict:
+        cap = 1 << 16
+        s, ch, brk, brkp, ari, act = _changes(lambda c: lib().vd_server_get_changes(self.h, int(sim), C.byref(c)),
+                                              1 << 22, cap)
+        _check(s, "vd_server_get_changes")
+        return dict(frame=ch.frame_index, K=ch.n_now, breaking=brk[: ch.n_breaking].copy(),
+                    arising=ari[: ch.n_arising].copy())
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().vd_server_destroy(self.h)
             self.h = None
 
     def __del__(self):

@@ -1,0 +1,106 @@
+"""Served form (vd_server_*): continuous batching gives each simulation
+exactly the results it gets alone.
+
+Frames of several simulations are submitted in an interleaved, seeded order
+while earlier steps are still on the device; every finished frame's counts
+(bubbles, links, breaking, arising) and every simulation's final labels and
+flip lists must equal those of the same frame sequence pushed through its
+own vd_push_frame context.
+"""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+from paper_1607_00908_gb300 import inputs as I  # noqa: E402
+from paper_1607_00908_gb300 import serve  # noqa: E402
+from paper_1607_00908_gb300 import vd  # noqa: E402
+
+
+def _setup(seed=3):
+    sizes = [(96, 96), (128, 80), (200, 200), (64, 64), (160, 120)]
+    n_frames = 5
+    frames = []
+    for k, (lx, ly) in enumerate(sizes):
+        seq = list(I.noise_frames(ly, 2.5 + 0.5 * k, n_frames, 0.03, seed + k, Lx=lx))
+        frames.append([torch.from_numpy(F).cuda() for F in seq])
+    rng = np.random.default_rng(seed)
+    order = []
+    for f in range(n_frames):
+        sims = list(rng.permutation(len(sizes)))
+        order += [(s, f) for s in sims]
+    return sizes, frames, order
+
+
+def _alone_counts(sizes, frames):
+    out = {}
+    finals = {}
+    for s, (lx, ly) in enumerate(sizes):
+        det = vd.Detector(lx, ly)
+        for f, F in enumerate(frames[s]):
+            det.push(F)
+            ch = det.changes()
+            out[(s, f)] = (ch["K"], ch["n_edges"], len(ch["breaking"]), len(ch["arising"]))
+        finals[s] = (det.labels(), det.changes())
+        det.close()
+    return out, finals
+
+
+@pytest.mark.parametrize("max_batch,budget_extra", [(5, 1 << 30), (3, 1 << 30), (5, 300_000)])
+def test_served_results_equal_alone(max_batch, budget_extra):
+    sizes, frames, order = _setup()
+    want, finals = _alone_counts(sizes, frames)
+    # resident state measured by a first server; the budget leaves room for
+    # `budget_extra` bytes of frames in flight
+    probe = vd.Server(sizes, budget_bytes=1 << 40, max_batch=max_batch)
+    resident = probe.stats()["resident_bytes"]
+    probe.close()
+    sv = vd.Server(sizes, budget_bytes=resident + budget_extra, max_batch=max_batch)
+    seen = {}
+    pos = [0] * len(sizes)
+    tickets = {}
+    for s, f in order:
+        tickets[sv.submit(s, frames[s][f])] = (s, f)
+        for d in sv.poll(wait=False):
+            seen[tickets[d[0]]] = d
+    while len(seen) < len(order):
+        for d in sv.poll(wait=True):
+            seen[tickets[d[0]]] = d
+    st = sv.stats()
+    assert st["frames_done"] == len(order)
+    for key, d in seen.items():
+        ticket, s, status, ts, td, K, E, nb, na = d
+        assert status == 0
+        assert (K, E, nb, na) == want[key], (key, (K, E, nb, na), want[key])
+        assert td >= ts
+    for s in range(len(sizes)):
+        lab, ch = finals[s]
+        assert np.array_equal(sv.labels(s), lab)
+        got = sv.changes(s)
+        assert np.array_equal(got["breaking"], ch["breaking"]) and np.array_equal(got["arising"], ch["arising"])
+    if max_batch > 1 and budget_extra > 1 << 20:
+        assert st["steps"] < len(order)     # frames were batched
+    sv.close()
+
+
+def test_budget_below_resident_state_is_refused():
+    with pytest.raises(vd.VdError) as e:
+        vd.Server([(256, 256)], budget_bytes=1 << 20, max_batch=4)
+    assert e.value.status == vd.VD_ERR_CAPACITY
+
+
+def test_small_served_workload_runs():
+    """The served driver on a reduced trace: batched and one-at-a-time both
+    finish every frame; batching takes fewer steps."""
+    sims = [(256, "noise"), (256, "discs"), (512, "noise"), (512, "discs")]
+    pools = serve.make_pools([256, 512], 3, rsa_cap=2000)
+    dev = {k: [torch.from_numpy(F).cuda() for F in v] for k, v in pools.items()}
+    trace = serve.poisson_trace(len(sims), rate=400.0, duration=0.5, seed=2)
+    a = serve.run(sims, dev, trace, max_batch=4, budget_bytes=8 << 30)
+    b = serve.run(sims, dev, trace, max_batch=1, budget_bytes=8 << 30)
+    assert a["frames"] == b["frames"] == len(trace)
+    assert a["steps"] <= b["steps"]
