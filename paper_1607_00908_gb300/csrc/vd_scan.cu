@@ -15,15 +15,21 @@ namespace vd {
 // ---------------------------------------------------------------------------
 // k_plan: prefixes over the active instances; bucket grid of each instance
 // ---------------------------------------------------------------------------
-__global__ void k_plan(Pools P, StepTable T, int with_comp) {
-    // one block; instances handled serially by thread 0 in act order (n_act is
-    // at most a few hundred), other threads only help writing offsets.
-    __shared__ int s_dummy;
+constexpr int PLAN_THREADS = 256;
+
+__global__ __launch_bounds__(PLAN_THREADS) void k_plan(Pools P, StepTable T, int with_comp) {
+    // one block: thread per instance, block scans for the prefixes
+    __shared__ long long s_v[NPRE][PLAN_THREADS];
+    __shared__ long long s_carry[NPRE];
     const int n = T.n_act;
-    if (threadIdx.x == 0) {
-        long long acc[NPRE];
-        for (int k = 0; k < NPRE; ++k) acc[k] = 0;
-        for (int a = 0; a < n; ++a) {
+    const int tid = threadIdx.x;
+    if (tid < NPRE) s_carry[tid] = 0;
+    __syncthreads();
+    for (int base = 0; base < n; base += PLAN_THREADS) {
+        const int a = base + tid;
+        long long v[NPRE];
+        for (int k = 0; k < NPRE; ++k) v[k] = 0;
+        if (a < n) {
             const int inst = T.act[a];
             InstState& S = P.st[inst];
             const InstDesc& D = P.desc[inst];
@@ -36,7 +42,7 @@ __global__ void k_plan(Pools P, StepTable T, int with_comp) {
                 }
                 if (K > 0) {
                     // bucket side ~ mean spacing of centres, clamped to [4, 64] sites
-                    double sp = sqrt((double)D.Lx * (double)D.Ly / (double)K);
+                    const double sp = sqrt((double)D.Lx * (double)D.Ly / (double)K);
                     int B = (int)(sp + 0.5);
                     B = B < 4 ? 4 : (B > 64 ? 64 : B);
                     S.B = B;
@@ -45,17 +51,17 @@ __global__ void k_plan(Pools P, StepTable T, int with_comp) {
                 } else {
                     S.B = 4; S.nbx = 0; S.nby = 0;
                 }
+                if (S.prev_same) {
+                    // the past frame was labelled in this step by instance prev_inst
+                    const int kp = P.st[S.prev_inst].K;
+                    const int cap = P.desc[S.prev_inst].comp_cap;
+                    S.K_prev = kp < cap ? kp : cap;
+                }
             }
-            if (with_comp && S.prev_same) {
-                // the past frame was labelled in this step by instance prev_inst
-                const InstState& SP = P.st[S.prev_inst];
-                const int kp = SP.K < P.desc[S.prev_inst].comp_cap ? SP.K : P.desc[S.prev_inst].comp_cap;
-                S.K_prev = kp;
-            }
-            long long v[NPRE];
-            v[PRE_K] = S.K;
+            const int K = S.K < D.comp_cap ? S.K : D.comp_cap;
+            v[PRE_K] = K;
             v[PRE_KP] = S.has_prev ? S.K_prev : 0;
-            v[PRE_NB] = (long long)S.nbx * S.nby;
+            v[PRE_NB] = K > 0 ? (long long)S.nbx * S.nby : 0;
             v[PRE_E] = S.n_edge_list;
             v[PRE_EP] = S.has_prev ? S.E_prev : 0;
             v[PRE_O] = S.n_ovl < D.ovl_cap ? S.n_ovl : D.ovl_cap;
@@ -64,18 +70,30 @@ __global__ void k_plan(Pools P, StepTable T, int with_comp) {
             v[PRE_FA] = S.n_arise;
             v[PRE_EA] = S.n_eapp < D.edge_cap ? S.n_eapp : D.edge_cap;
             v[PRE_OA] = S.n_oapp < D.ovl_cap ? S.n_oapp : D.ovl_cap;
-            for (int k = 0; k < NPRE; ++k) {
-                pre_arr(T, k)[a] = acc[k];
-                acc[k] += v[k];
-            }
         }
-        for (int k = 0; k < NPRE; ++k) pre_arr(T, k)[n] = acc[k];
+        for (int k = 0; k < NPRE; ++k) s_v[k][tid] = v[k];
+        __syncthreads();
+        // inclusive scans (Hillis-Steele) of every array
+        for (int o = 1; o < PLAN_THREADS; o <<= 1) {
+            long long add[NPRE];
+            for (int k = 0; k < NPRE; ++k) add[k] = tid >= o ? s_v[k][tid - o] : 0;
+            __syncthreads();
+            for (int k = 0; k < NPRE; ++k) s_v[k][tid] += add[k];
+            __syncthreads();
+        }
+        if (a < n)
+            for (int k = 0; k < NPRE; ++k) pre_arr(T, k)[a] = s_carry[k] + s_v[k][tid] - v[k];
+        __syncthreads();
+        if (tid < NPRE) s_carry[tid] += s_v[tid][PLAN_THREADS - 1];
+        __syncthreads();
+    }
+    if (tid < NPRE) pre_arr(T, tid)[n] = s_carry[tid];
+    if (tid == 0) {
         // fresh scan epoch and ticket for the scan that follows
         P.g->scan_epoch = (P.g->scan_epoch + 1) & 0x3FFFFFFFu;
         if (P.g->scan_epoch == 0) P.g->scan_epoch = 1;
         P.g->scan_ticket = 0;
     }
-    (void)s_dummy;
 }
 
 // end values of offset arrays (off[size] = total) for each instance
@@ -273,12 +291,12 @@ __global__ __launch_bounds__(SCAN_THREADS) void k_scan(Pools P, StepTable T, int
 }
 
 void launch_plan(const Launch& L, int with_comp) {
-    k_plan<<<1, 32, 0, L.s>>>(L.P, L.T, with_comp);
+    k_plan<<<1, PLAN_THREADS, 0, L.s>>>(L.P, L.T, with_comp);
     ++*L.nlaunch;
 }
 
 void launch_scan(const Launch& L, ScanKind kind) {
-    k_plan<<<1, 32, 0, L.s>>>(L.P, L.T, 0);
+    k_plan<<<1, PLAN_THREADS, 0, L.s>>>(L.P, L.T, 0);
     ++*L.nlaunch;
     if (kind != SCAN_ROOTBITS) {
         k_plan_ends<<<1, 256, 0, L.s>>>(L.P, L.T, (int)kind);
