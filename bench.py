@@ -41,6 +41,11 @@ UNIT = "Gsites/s"
 # 4, label write 4, owner write 4.
 PIPELINE_BYTES_PER_SITE = 16.0
 
+# Measured DRAM bytes (read + write) per site of a stage, from one ncu
+# capture of the current kernels (profiles/voronoi_links_c2.txt); scaled to
+# the bench launch for roofline.traffic. Stages not captured report null.
+TRAFFIC_BYTES_PER_SITE = {3: 6.374}
+
 
 def workload(name: str, n_frames: int | None):
     if name == "c1":
@@ -211,8 +216,10 @@ def roofline_of(stage_ms, names, launches_per_stage, sites_per_launch, sequence,
     avg_ms = stage_ms[dom] / launches_per_stage
     bytes_per_launch = sb[dom] * sites_per_launch
     achieved = bytes_per_launch / (avg_ms / 1e3) / 1e9
+    traffic = TRAFFIC_BYTES_PER_SITE.get(dom)
     return {"bound": "hbm", "kernel": names[dom], "achieved": achieved, "peak": peak, "unit": "GB/s",
-            "frac": achieved / peak, "peak_kind": peak_kind, "traffic": None,
+            "frac": achieved / peak, "peak_kind": peak_kind,
+            "traffic": traffic * sites_per_launch if traffic is not None else None,
             "bytes_per_site": sb[dom], "bytes_per_launch": bytes_per_launch, "avg_launch_ms": avg_ms,
             "stage_ms_per_launch": {names[k]: stage_ms[k] / launches_per_stage for k in range(len(names))}}
 
