@@ -44,7 +44,7 @@ PIPELINE_BYTES_PER_SITE = 16.0
 # Measured DRAM bytes (read + write) per site of a stage, from one ncu
 # capture of the current kernels (profiles/voronoi_links_c2.txt); scaled to
 # the bench launch for roofline.traffic. Stages not captured report null.
-TRAFFIC_BYTES_PER_SITE = {3: 6.374}
+TRAFFIC_BYTES_PER_SITE = {}
 
 
 def workload(name: str, n_frames: int | None):
@@ -205,9 +205,10 @@ def stage_bytes(sequence: bool):
             labels: read 4 in the label pass (frame from an earlier push), or
             read 4 + 4 (labels now and past) by the overlap pass (frame
             sequence, past frame written in the same push)
-    stage 3 Voronoi owners + links: owner write 4, owner read 4
+    stage 3 Voronoi owners: owner write 4
+    stage 4 links: owner read 4
     """
-    return {0: 4.25, 2: 12.125 if sequence else 8.125, 3: 8.0}
+    return {0: 4.25, 2: 12.125 if sequence else 8.125, 3: 4.0, 4: 4.0}
 
 
 def roofline_of(stage_ms, names, launches_per_stage, sites_per_launch, sequence, peak, peak_kind):

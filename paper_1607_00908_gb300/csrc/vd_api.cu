@@ -98,12 +98,13 @@ struct vd_batch {
     int ev_used = 0;
 };
 
-static const int N_STAGES = 5;
+static const int N_STAGES = 6;
 static const char* STAGE_NAMES[N_STAGES] = {
     "labelling tiles (threshold + tile union-find)",
     "bubbles (border merge, ranks, centroids, bucket grid)",
     "label pass + overlap histogram",
-    "voronoi owners + links",
+    "voronoi owners",
+    "links (owner boundaries, plaquettes, merge into hashes)",
     "adjacency, match, translation, flips",
 };
 
@@ -203,6 +204,8 @@ void enqueue_step(vd_batch* b, const Launch& L, bool timed) {
     launch_labels(L);
     mark(b, timed);
     launch_voronoi(L);
+    mark(b, timed);
+    launch_links(L);
     launch_merge_lists(L);
     mark(b, timed);
     launch_graph(L);
@@ -664,7 +667,7 @@ vd_status vd_batch_get_timing(vd_batch* b, double* stage_ms, int32_t cap, int32_
     if (n_stages) *n_stages = N_STAGES;
     if (n_kernel_launches) *n_kernel_launches = b->launches;
     if (n_steps) *n_steps = b->frames_pushed;
-    double acc[N_STAGES] = {0, 0, 0, 0, 0};
+    double acc[N_STAGES] = {};
     const int per = N_STAGES + 1;
     for (int g = 0; g + per <= b->ev_used; g += per) {
         for (int k = 0; k < N_STAGES; ++k) {

@@ -27,7 +27,6 @@ constexpr int VW = 32;          // Voronoi tile width
 constexpr int VH = 32;          // Voronoi tile height
 constexpr int VTHREADS = 256;
 constexpr int VCAND = 1024;     // candidate slots per Voronoi tile (overflow -> slow path)
-constexpr int VEDGESET = 512;   // shared-memory link set per Voronoi tile
 
 constexpr int Q = 1024;         // centroid fixed point: 1/1024 site
 
@@ -277,6 +276,7 @@ __device__ __forceinline__ unsigned hash_small(unsigned long long k) {
 // whose key could not be placed (set full).
 __device__ __forceinline__ bool warp_set_insert(unsigned long long* set, int cap, unsigned long long key) {
     const int lane = threadIdx.x & 31;
+    if (!__any_sync(0xffffffffu, key != EMPTY_KEY)) return true;
     unsigned h = hash_small(key) & (cap - 1);
     const bool pending = key != EMPTY_KEY && set[h] != key;
     if (!__any_sync(0xffffffffu, pending)) return true;
@@ -403,7 +403,8 @@ struct Launch {
 void launch_ccl_tiles(const Launch& L);    // threshold + tile union-find (pass A)
 void launch_ccl_rest(const Launch& L);     // border merge, ranks, centroids, bucket grid
 void launch_labels(const Launch& L);       // per-site labels + overlap histogram
-void launch_voronoi(const Launch& L);      // owners + per-tile links
+void launch_voronoi(const Launch& L);      // exact owner of every site
+void launch_links(const Launch& L);        // per-tile links from the owners
 void launch_merge_lists(const Launch& L);  // appended links/pairs -> hash tables
 void launch_graph(const Launch& L);        // CSR, match, translation, flips
 void launch_begin(const Launch& L);        // per-step counters and field pointers

@@ -10,11 +10,12 @@
 // scanning rings of buckets around the tile until the unscanned region is
 // farther than sqrt(U). Each site then scans only the kept candidates.
 //
-// Links: owners are computed for the tile plus one halo column and row, and
-// a link {a, b} is emitted where a site and its +x or +y neighbour differ, and
-// for a 2x2 plaquette with four distinct owners the diagonal chosen by the
-// exact incircle test (int128). Links are deduplicated in a shared-memory set,
-// then inserted into a global hash that also counts each label's degree.
+// Links: a link {a, b} joins owners that meet where a site and its +x or +y
+// neighbour differ, and for a 2x2 plaquette with four distinct owners the
+// diagonal chosen by the exact incircle test (int128). Each tile emits every
+// owner pair that meets in it at least once (one key per boundary piece, not
+// per site); the keys are then inserted into a global hash that also counts
+// each label's degree.
 #include "vd_internal.cuh"
 
 namespace vd {
@@ -83,16 +84,6 @@ __device__ __forceinline__ void edge_global_insert(const Pools& P, const InstDes
     atomicOr(&P.st[inst].err, ERR_EDGE_CAP);
 }
 
-__device__ __forceinline__ void edge_add(unsigned long long* s_set, const Pools& P, const InstDesc& D, int inst,
-                                         unsigned long long key) {
-    unsigned h = (unsigned)hash64(key) & (VEDGESET - 1);
-    for (int probe = 0; probe < VEDGESET; ++probe) {
-        const unsigned long long k = atomicCAS(&s_set[h], EMPTY_KEY, key);
-        if (k == EMPTY_KEY || k == key) return;
-        h = (h + 1) & (VEDGESET - 1);
-    }
-    edge_global_insert(P, D, inst, key);
-}
 
 constexpr int WCAND = 64;   // per-warp candidate list
 
@@ -410,15 +401,53 @@ __global__ __launch_bounds__(VTHREADS) void k_voronoi(Pools P, StepTable T) {
 }
 
 // ---------------------------------------------------------------------------
-// Links from the owner array (Section 3.2.2), one block per 32 x 32 tile: one
-// warp per row, lane l looks at site (x0+l, y), its +x and +y neighbours
-// (periodic) and the plaquette they span. Equal keys inside a warp are merged
-// with __match_any_sync, then in a shared set; the tile's unique links are
-// appended to the instance's link list.
+// Links from the owner array (Section 3.2.2). One warp per 32 x 32 tile. The
+// tile's owners plus one row below and one column right (periodic) are
+// staged in shared memory with cp.async; the warp then walks the rows, lane l
+// at column l.
+//
+// The tile answers for the adjacencies anchored in it: H(l,r) between sites
+// (l,r),(l+1,r) and V(l,r) between (l,r),(l,r+1). Ordering anchors by (row,
+// column) with H before V at the same anchor, an adjacency is emitted only if
+// none of the earlier adjacencies that share a dual corner with it joins the
+// same two owners:
+//   H(l,r): H(l,r-1), V(l,r-1), V(l+1,r-1)   (r > 0)
+//   V(l,r): H(l-1,r), V(l-1,r) (l > 0), H(l,r)
+// Every suppressed adjacency points to a strictly earlier one with the same
+// owner pair, which is emitted or suppressed in turn, so by induction over
+// the order every pair that meets somewhere is emitted at least once (the
+// tiles of the referenced anchors process them). A straight boundary crossing
+// the tile is emitted once instead of once per row. Four-owner plaquettes add
+// their incircle link. Emitted keys are collected in a per-warp list and
+// appended to the instance's link list after merging equal keys.
 // ---------------------------------------------------------------------------
-__global__ __launch_bounds__(VTHREADS) void k_links(Pools P, StepTable T) {
-    __shared__ unsigned long long s_set[VEDGESET];
-    const int b = blockIdx.x;
+constexpr int LINK_WARPS = 4;
+constexpr int LSET = 256;       // per-warp key list
+constexpr int LS = VW + 4;      // staged row stride (rows start on 16 bytes)
+
+// slot `pos` of a warp's key list; past its end the key goes to the hash
+__device__ __forceinline__ void link_list_put(unsigned long long* list, int pos, unsigned long long key,
+                                              const Pools& P, const InstDesc& D, int inst) {
+    if (pos < LSET) list[pos] = key;
+    else edge_global_insert(P, D, inst, key);
+}
+
+__device__ __forceinline__ void cp_async4(int* smem, const int* gmem) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+
+__device__ __forceinline__ void cp_async16(int* smem, const int* gmem) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+
+__global__ __launch_bounds__(32 * LINK_WARPS) void k_links(Pools P, StepTable T) {
+    __shared__ __align__(16) int s_own[LINK_WARPS][(VH + 1) * LS];
+    __shared__ unsigned long long s_list[LINK_WARPS][LSET];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int b = blockIdx.x * LINK_WARPS + warp;
+    if (b >= T.tileV_pre[T.n_act]) return;
     const int a = seg_of_int(T.tileV_pre, T.n_act, b);
     const int inst = T.act[a];
     const InstDesc& D = P.desc[inst];
@@ -428,59 +457,88 @@ __global__ __launch_bounds__(VTHREADS) void k_links(Pools P, StepTable T) {
     const int tx = t % D.vtx, ty = t / D.vtx;
     const int x0 = tx * VW, y0 = ty * VH;
     const int ncols = min(VW, D.Lx - x0), nrows = min(VH, D.Ly - y0);
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const long long MX = (long long)Q * D.Lx, MY = (long long)Q * D.Ly;
     const int2* cq = P.cq + D.comp_off;
     const int* own = P.owners + D.site_off;
-    for (int k = threadIdx.x; k < VEDGESET; k += VTHREADS) s_set[k] = EMPTY_KEY;
-    __syncthreads();
-    const int x = x0 + lane;
-    const int xr = (x + 1 == D.Lx) ? 0 : x + 1;
-    constexpr int RPW = VH / (VTHREADS / 32);   // rows per warp
-    // all of this warp's owner loads in flight at once
-    int o[RPW], rt[RPW], dn[RPW], dg[RPW];
-#pragma unroll
-    for (int i = 0; i < RPW; ++i) {
-        const int ly = warp + i * (VTHREADS / 32);
-        o[i] = rt[i] = dn[i] = dg[i] = -1;
-        if (ly < nrows && lane < ncols) {
-            const int y = y0 + ly;
-            const int yd = (y + 1 == D.Ly) ? 0 : y + 1;
+    int* S = s_own[warp];
+    unsigned long long* list = s_list[warp];
+
+    // stage rows y0..y0+nrows and columns x0..x0+ncols (both periodic); a
+    // full-width tile whose rows start on 16-byte boundaries copies 16 bytes
+    // per lane (8 lanes per row), the extra column and other tiles 4 bytes
+    const bool vec = ncols == VW && ((D.site_off | D.Lx) & 3) == 0;
+    if (vec) {
+        const int c4 = (lane & 7) * 4;
+        for (int r = lane >> 3; r <= nrows; r += 4) {
+            const int y = (y0 + r == D.Ly) ? 0 : y0 + r;
+            cp_async16(S + r * LS + c4, own + (long long)y * D.Lx + x0 + c4);
+        }
+        const int xe = (x0 + VW == D.Lx) ? 0 : x0 + VW;
+        for (int r = lane; r <= nrows; r += 32) {
+            const int y = (y0 + r == D.Ly) ? 0 : y0 + r;
+            cp_async4(S + r * LS + VW, own + (long long)y * D.Lx + xe);
+        }
+    } else {
+        for (int r = 0; r <= nrows; ++r) {
+            const int y = (y0 + r == D.Ly) ? 0 : y0 + r;
             const int* row = own + (long long)y * D.Lx;
-            const int* rowd = own + (long long)yd * D.Lx;
-            o[i] = __ldcs(row + x);
-            rt[i] = row[xr];
-            dn[i] = rowd[x];
-            dg[i] = rowd[xr];
+            for (int c = lane; c <= ncols; c += 32) {
+                const int x = (x0 + c == D.Lx) ? 0 : x0 + c;
+                cp_async4(S + r * LS + c, row + x);
+            }
         }
     }
-#pragma unroll
-    for (int i = 0; i < RPW; ++i) {
-        unsigned long long kh = EMPTY_KEY, kv = EMPTY_KEY, kp = EMPTY_KEY;
-        if (o[i] >= 0) {
-            if (o[i] != rt[i]) kh = edge_key(o[i], rt[i]);
-            if (o[i] != dn[i]) kv = edge_key(o[i], dn[i]);
-            if (o[i] != rt[i] && o[i] != dn[i] && o[i] != dg[i] && rt[i] != dn[i] && rt[i] != dg[i] && dn[i] != dg[i])
-                kp = plaquette_key(o[i], rt[i], dg[i], dn[i], cq, MX, MY);
+    asm volatile("cp.async.wait_all;\n" ::: "memory");
+    __syncwarp();
+
+    const bool valid = lane < ncols;
+    const int l = min(lane, ncols - 1);
+    const unsigned lt = (1u << lane) - 1u;
+    int o = S[l], rt = S[l + 1];
+    int up = 0, upr = 0;
+    int lf = __shfl_up_sync(0xffffffffu, o, 1);
+    int n = 0;   // keys in the warp's list (warp-uniform)
+    for (int r = 0; r < nrows; ++r) {
+        const int dn = S[(r + 1) * LS + l];
+        const int dg = S[(r + 1) * LS + l + 1];
+        const int dlf = __shfl_up_sync(0xffffffffu, dn, 1);
+        const bool eh = valid && o != rt && !(r > 0 && (up == rt || upr == o || (up == o && upr == rt)));
+        const bool ev = valid && o != dn && rt != dn && !(lane > 0 && (lf == dn || (lf == o && dlf == dn)));
+        const bool ep = valid && o != rt && o != dn && o != dg && rt != dn && rt != dg && dn != dg;
+        const unsigned mh = __ballot_sync(0xffffffffu, eh);
+        const unsigned mv = __ballot_sync(0xffffffffu, ev);
+        const unsigned mp = __ballot_sync(0xffffffffu, ep);
+        if (mh | mv | mp) {
+            // append this row's keys: horizontal, vertical, then plaquettes
+            const int nh = __popc(mh), nv = __popc(mv);
+            if (eh) link_list_put(list, n + __popc(mh & lt), edge_key(o, rt), P, D, inst);
+            if (ev) link_list_put(list, n + nh + __popc(mv & lt), edge_key(o, dn), P, D, inst);
+            if (ep) link_list_put(list, n + nh + nv + __popc(mp & lt), plaquette_key(o, rt, dg, dn, cq, MX, MY), P, D,
+                                  inst);
+            n += nh + nv + __popc(mp);
         }
-        if (!warp_set_insert(s_set, VEDGESET, kh)) edge_global_insert(P, D, inst, kh);
-        if (!warp_set_insert(s_set, VEDGESET, kv)) edge_global_insert(P, D, inst, kv);
-        if (__any_sync(0xffffffffu, kp != EMPTY_KEY) && !warp_set_insert(s_set, VEDGESET, kp))
-            edge_global_insert(P, D, inst, kp);
+        up = o;
+        upr = rt;
+        o = dn;
+        rt = dg;
+        lf = dlf;
     }
-    __syncthreads();
-    // append the tile's unique links (one reservation per warp); the hash
-    // insertion happens in k_merge_lists, off this block's critical path
-    for (int kb = warp * 32; kb < VEDGESET; kb += VTHREADS) {
-        const unsigned long long key = s_set[kb + lane];
-        const bool has = key != EMPTY_KEY;
+    __syncwarp();
+    // equal keys within a round of 32 are merged; the tile's keys are
+    // appended to the instance's link list (the link hash removes the rest)
+    n = min(n, LSET);
+    for (int kb = 0; kb < n; kb += 32) {
+        const bool in = kb + lane < n;
+        const unsigned long long key = in ? list[kb + lane] : EMPTY_KEY;
+        const unsigned grp = __match_any_sync(0xffffffffu, key);
+        const bool has = in && lane == __ffs(grp) - 1;
         const unsigned m = __ballot_sync(0xffffffffu, has);
         if (!m) continue;
         int base = 0;
         if (lane == 0) base = atomicAdd(&P.st[inst].n_eapp, __popc(m));
         base = __shfl_sync(0xffffffffu, base, 0);
         if (has) {
-            const int pos = base + __popc(m & ((1u << lane) - 1u));
+            const int pos = base + __popc(m & lt);
             if (pos < D.edge_cap) P.ekeys[D.edge_off + pos] = key;
             else edge_global_insert(P, D, inst, key);   // list full: insert directly
         }
@@ -520,7 +578,10 @@ void launch_merge_lists(const Launch& L) {
 void launch_voronoi(const Launch& L) {
     k_voronoi<<<L.total_tilesV, VTHREADS, 0, L.s>>>(L.P, L.T);
     ++*L.nlaunch;
-    k_links<<<L.total_tilesV, VTHREADS, 0, L.s>>>(L.P, L.T);
+}
+
+void launch_links(const Launch& L) {
+    k_links<<<(L.total_tilesV + LINK_WARPS - 1) / LINK_WARPS, 32 * LINK_WARPS, 0, L.s>>>(L.P, L.T);
     ++*L.nlaunch;
 }
 
