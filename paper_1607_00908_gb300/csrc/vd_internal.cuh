@@ -26,7 +26,6 @@ constexpr int BORDER = 2 * (TW + TH);   // left col, right col, top row, bottom 
 constexpr int VW = 32;          // Voronoi tile width
 constexpr int VH = 32;          // Voronoi tile height
 constexpr int VTHREADS = 256;
-constexpr int VCAND = 1024;     // candidate slots per Voronoi tile (overflow -> slow path)
 
 constexpr int Q = 1024;         // centroid fixed point: 1/1024 site
 

@@ -85,319 +85,321 @@ __device__ __forceinline__ void edge_global_insert(const Pools& P, const InstDes
 }
 
 
-constexpr int WCAND = 64;   // per-warp candidate list
+constexpr int VWARPS = 4;        // tiles per block, one warp each
+constexpr int PW = 16, PH = 8;   // patch: a 32 x 32 tile holds 2 x 4 patches
+constexpr int WSCAN = 256;       // per-warp list of scanned centres
+constexpr int WCAND = 64;        // per-patch list of kept candidates (index fits 6 bits)
 
-// Exact owner over a candidate list with int64 distances (rel. coordinates,
-// no wrap needed), ties to the smallest label.
+// Exact owner over a candidate list with int64 distances (coordinates
+// relative to the tile origin, no wrap needed), ties to the smallest label.
+// `kk` (may be null) maps list positions to entries of cx/cy/id.
 __device__ __forceinline__ int owner_exact(long long sx, long long sy, const int* cx, const int* cy, const int* id,
-                                           int n) {
+                                           const int* kk, int n) {
     long long best = LLONG_MAX;
     int bi = -1;
     for (int j = 0; j < n; ++j) {
-        const long long dx = sx - cx[j], dy = sy - cy[j];
+        const int e = kk ? kk[j] : j;
+        const long long dx = sx - cx[e], dy = sy - cy[e];
         const long long d2 = dx * dx + dy * dy;
-        if (d2 < best || (d2 == best && id[j] < bi)) { best = d2; bi = id[j]; }
+        if (d2 < best || (d2 == best && id[e] < bi)) { best = d2; bi = id[e]; }
     }
     return bi;
 }
 
-__global__ __launch_bounds__(VTHREADS) void k_voronoi(Pools P, StepTable T) {
-    // centres scanned by the ring search, relative to the tile origin (minimum image)
-    __shared__ int s_cx[VCAND], s_cy[VCAND], s_id[VCAND];
-    // per-warp candidate lists of each warp's 16 x 8 patch
-    __shared__ float s_wfx[8][WCAND], s_wfy[8][WCAND];
-    __shared__ int s_wix[8][WCAND], s_wiy[8][WCAND], s_wid[8][WCAND];
-    __shared__ int s_own[VH][VW + 1];
-    __shared__ int s_n, s_over;
-    __shared__ unsigned long long s_U;
+// squared largest distance from a coordinate to [lo, hi] on a ring (<= M/2),
+// rounded up in float32
+__device__ __forceinline__ float far2_ru(int d, int lo, int hi, int halfM) {
+    const int a = abs(d - lo), b = abs(d - hi);
+    const float f = __int2float_ru(min(max(a, b), halfM));
+    return __fmul_ru(f, f);
+}
 
-    const int b = blockIdx.x;
+// One warp per 32 x 32 tile, no block-level synchronisation.
+//  1. Ring search over the bucket grid around the tile. For each of the
+//     tile's eight 16 x 8 patches, U_p = min over scanned centres of an upper
+//     bound of their largest squared distance to the patch (float32 rounded
+//     up), so every site of patch p has a centre within sqrt(U_p). The search
+//     stops when the unscanned region is farther than sqrt(max_p U_p) from
+//     the tile; the first round already takes the rings that usually satisfy
+//     this (about the patch half-diagonal plus one bucket).
+//  2. Per patch: the owners of its sites are among the scanned centres whose
+//     smallest squared distance to the patch (rounded down) is <= U_p; every
+//     site scans only those kept centres. float32 distances with the kept
+//     index in the low 6 bits give the nearest and second-nearest; when they
+//     are within 2^-15 relative of each other the site is decided exactly in
+//     int64 (ties to the smallest label).
+__global__ __launch_bounds__(32 * VWARPS) void k_voronoi(Pools P, StepTable T) {
+    __shared__ int s_cx[VWARPS][WSCAN], s_cy[VWARPS][WSCAN], s_id[VWARPS][WSCAN];
+    __shared__ float2 s_fc[VWARPS][WCAND];
+    __shared__ int s_kk[VWARPS][WCAND];
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int b = blockIdx.x * VWARPS + warp;
+    if (b >= T.tileV_pre[T.n_act]) return;
     const int a = seg_of_int(T.tileV_pre, T.n_act, b);
     const int inst = T.act[a];
-    const InstDesc D = P.desc[inst];
+    const InstDesc& D = P.desc[inst];
     const InstState& S = P.st[inst];
     const int t = b - T.tileV_pre[a];
     const int tx = t % D.vtx, ty = t / D.vtx;
+    const int Lx = D.Lx, Ly = D.Ly;
     const int x0 = tx * VW, y0 = ty * VH;
-    const int ncols = min(VW, D.Lx - x0), nrows = min(VH, D.Ly - y0);
+    const int ncols = min(VW, Lx - x0), nrows = min(VH, Ly - y0);
     const int K = min(S.K, D.comp_cap);
-    const long long MX = (long long)Q * D.Lx, MY = (long long)Q * D.Ly;
+    int* own = P.owners + D.site_off;
+    if (K <= 0) {
+        for (int k = lane; k < ncols * nrows; k += 32)
+            own[(long long)(y0 + k / ncols) * Lx + x0 + k % ncols] = -1;
+        return;
+    }
+
+    // ---- 1. ring search over the bucket grid ----
+    // Bucket indices are unwrapped (they may run below 0 or past nb-1 by
+    // less than one period). Centre positions are stored relative to the
+    // tile origin (minimum image, |v| <= M/2 < 2^31).
+    const long long MX = (long long)Q * Lx, MY = (long long)Q * Ly;
     const long long X0 = (long long)Q * x0, Y0 = (long long)Q * y0;
-    const long long WR = (long long)Q * (ncols - 1), HR = (long long)Q * (nrows - 1);   // core sites only
-    const int2* cq = P.cq + D.comp_off;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-
-    if (threadIdx.x == 0) {
-        s_n = 0;
-        s_over = 0;
-        s_U = ULLONG_MAX;
+    const int hMX = (int)(MX >> 1), hMY = (int)(MY >> 1);
+    // patch extents relative to the tile origin (Q units); patch p = 2 * pyi + pxi
+    const int xlo0 = 0, xhi0 = Q * (min(PW, ncols) - 1);
+    const int xlo1 = Q * PW, xhi1 = Q * (ncols - 1);
+    const int Bk = S.B, nbx = S.nbx, nby = S.nby;
+    const int bx0 = x0 / Bk, bx1 = (x0 + ncols - 1) / Bk;
+    const int by0 = y0 / Bk, by1 = (y0 + nrows - 1) / Bk;
+    const int* boff = P.boff + D.bucket_off;
+    const int2* bcq = P.bcq + D.comp_off;
+    const int* bid = P.bid + D.comp_off;
+    int* cxs = s_cx[warp];
+    int* cys = s_cy[warp];
+    int* ids = s_id[warp];
+    float Up[8];
+#pragma unroll
+    for (int p = 0; p < 8; ++p) Up[p] = INFINITY;
+    int qx0 = 0, qx1 = -1, qy0 = 0, qy1 = -1;   // previous round's region
+    bool qfx = false, qfy = false, have_prev = false;
+    int rx0, rx1, ry0, ry1;
+    int n = 0;   // centres scanned so far (warp-uniform)
+    for (int r = (9 + Bk - 1) / Bk + 1;; ++r) {
+        rx0 = bx0 - r; rx1 = bx1 + r; ry0 = by0 - r; ry1 = by1 + r;
+        const bool fx = (rx1 - rx0 + 1) >= nbx, fy = (ry1 - ry0 + 1) >= nby;
+        if (fx) { rx0 = 0; rx1 = nbx - 1; }
+        if (fy) { ry0 = 0; ry1 = nby - 1; }
+        const int wx = rx1 - rx0 + 1, ncell = wx * (ry1 - ry0 + 1);
+        for (int kb = 0; kb < ncell; kb += 32) {   // warp-uniform loop
+            const int k = kb + lane;
+            int jb = 0, je = 0;
+            if (k < ncell) {
+                const int kr = k / wx;
+                const int cu = rx0 + (k - kr * wx), rv = ry0 + kr;
+                bool skip = false;
+                if (have_prev) {
+                    int dxp = cu - qx0, dyp = rv - qy0;
+                    if (dxp < 0) dxp += nbx; else if (dxp >= nbx) dxp -= nbx;
+                    if (dyp < 0) dyp += nby; else if (dyp >= nby) dyp -= nby;
+                    skip = (qfx || dxp <= qx1 - qx0) && (qfy || dyp <= qy1 - qy0);
+                }
+                if (!skip) {
+                    const int cm = cu < 0 ? cu + nbx : (cu >= nbx ? cu - nbx : cu);
+                    const int rm = rv < 0 ? rv + nby : (rv >= nby ? rv - nby : rv);
+                    const int bk = rm * nbx + cm;
+                    jb = boff[bk];
+                    je = boff[bk + 1];
+                }
+            }
+            const int cnt = je - jb;
+            int inc = cnt;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, inc, o);
+                if (lane >= o) inc += y;
+            }
+            int pos = n + inc - cnt;
+            n += __shfl_sync(0xffffffffu, inc, 31);
+            for (int j = jb; j < je; ++j, ++pos) {
+                const int2 cc = bcq[j];
+                const int ddx = (int)wrapM((long long)cc.x - X0, MX);
+                const int ddy = (int)wrapM((long long)cc.y - Y0, MY);
+                const float fx0 = far2_ru(ddx, xlo0, xhi0, hMX), fx1 = far2_ru(ddx, xlo1, xhi1, hMX);
+#pragma unroll
+                for (int pyi = 0; pyi < 4; ++pyi) {
+                    const int ylo = Q * PH * pyi, yhi = Q * (min(PH * (pyi + 1), nrows) - 1);
+                    const float fy = far2_ru(ddy, ylo, yhi, hMY);
+                    Up[2 * pyi] = fminf(Up[2 * pyi], __fadd_ru(fx0, fy));
+                    Up[2 * pyi + 1] = fminf(Up[2 * pyi + 1], __fadd_ru(fx1, fy));
+                }
+                if (pos < WSCAN) {
+                    cxs[pos] = ddx;
+                    cys[pos] = ddy;
+                    ids[pos] = bid[j];
+                }
+            }
+        }
+        float Umax = 0.f;
+#pragma unroll
+        for (int p = 0; p < 8; ++p) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) Up[p] = fminf(Up[p], __shfl_xor_sync(0xffffffffu, Up[p], o));
+            const bool valid = PW * (p & 1) < ncols && PH * (p >> 1) < nrows;
+            if (valid) Umax = fmaxf(Umax, Up[p]);
+        }
+        if (fx && fy) break;
+        // gap between the region and the unscanned buckets (periods handled by
+        // one conditional shift: the ranges are narrower than a period here)
+        long long g = LLONG_MAX;
+        if (!fx) {
+            const int lx = rx0 < 0 ? (rx0 + nbx) * Bk - Lx : rx0 * Bk;                    // start of bucket rx0
+            const int ex = rx1 >= nbx ? min((rx1 - nbx + 1) * Bk, Lx) + Lx : min((rx1 + 1) * Bk, Lx);   // end of rx1
+            g = min((long long)Q * (x0 - lx), (long long)Q * (ex - (x0 + ncols - 1)));
+        }
+        if (!fy) {
+            const int ly = ry0 < 0 ? (ry0 + nby) * Bk - Ly : ry0 * Bk;
+            const int ey = ry1 >= nby ? min((ry1 - nby + 1) * Bk, Ly) + Ly : min((ry1 + 1) * Bk, Ly);
+            g = min(g, min((long long)Q * (y0 - ly), (long long)Q * (ey - (y0 + nrows - 1))));
+        }
+        // every unscanned centre is at least g away from every patch; the
+        // double product is within 2^-53 of g^2, so the margin makes it exact
+        if (g > 0 && (double)g * (double)g > (double)Umax * (1.0 + 1.0 / (1ll << 50))) break;
+        qx0 = rx0; qx1 = rx1; qy0 = ry0; qy1 = ry1; qfx = fx; qfy = fy; have_prev = true;
     }
-    __syncthreads();
+    __syncwarp();
 
-    if (K > 0) {
-        // ---- ring search over the bucket grid (all threads) ----
-        // Bucket indices are unwrapped (they may run below 0 or past nb-1 by
-        // less than one period); all arithmetic is 32-bit here.
-        const int Bk = S.B, nbx = S.nbx, nby = S.nby;
-        const int bx0 = x0 / Bk, bx1 = (x0 + ncols - 1) / Bk;
-        const int by0 = y0 / Bk, by1 = (y0 + nrows - 1) / Bk;
-        const int* boff = P.boff + D.bucket_off;
-        const int2* bcq = P.bcq + D.comp_off;
-        const int* bid = P.bid + D.comp_off;
-        int px0 = 0, px1 = -1, py0 = 0, py1 = -1;
-        bool pfx = false, pfy = false, have_prev = false;
-        unsigned long long myU = ULLONG_MAX;
-        // the first round takes rings 0..2 at once (one latency round instead of three)
-        for (int r = 2;; ++r) {
-            int rx0 = bx0 - r, rx1 = bx1 + r, ry0 = by0 - r, ry1 = by1 + r;
-            const bool fx = (rx1 - rx0 + 1) >= nbx, fy = (ry1 - ry0 + 1) >= nby;
-            if (fx) { rx0 = 0; rx1 = nbx - 1; }
-            if (fy) { ry0 = 0; ry1 = nby - 1; }
-            const int wx = rx1 - rx0 + 1, wy = ry1 - ry0 + 1;
-            const int ncell = wx * wy;
-            for (int kb = warp * 32; kb < ncell; kb += VTHREADS) {   // warp-uniform loop
-                const int k = kb + lane;
-                int jb = 0, je = 0;
-                if (k < ncell) {
-                    const int kr = k / wx;
-                    const int cu = rx0 + (k - kr * wx), rv = ry0 + kr;
-                    bool skip = false;
-                    if (have_prev) {
-                        int dxp = cu - px0, dyp = rv - py0;
-                        if (dxp < 0) dxp += nbx; else if (dxp >= nbx) dxp -= nbx;
-                        if (dyp < 0) dyp += nby; else if (dyp >= nby) dyp -= nby;
-                        skip = (pfx || dxp <= px1 - px0) && (pfy || dyp <= py1 - py0);
-                    }
-                    if (!skip) {
-                        const int cm = cu < 0 ? cu + nbx : (cu >= nbx ? cu - nbx : cu);
-                        const int rm = rv < 0 ? rv + nby : (rv >= nby ? rv - nby : rv);
-                        const int bk = rm * nbx + cm;
-                        jb = boff[bk];
-                        je = boff[bk + 1];
-                    }
-                }
-                // one shared-memory reservation per warp
-                const int cnt = je - jb;
-                int inc = cnt;
-#pragma unroll
-                for (int o = 1; o < 32; o <<= 1) {
-                    const int y = __shfl_up_sync(0xffffffffu, inc, o);
-                    if (lane >= o) inc += y;
-                }
-                const int tot = __shfl_sync(0xffffffffu, inc, 31);
-                int base = 0;
-                if (lane == 31 && tot > 0) base = atomicAdd(&s_n, tot);
-                base = __shfl_sync(0xffffffffu, base, 31) + inc - cnt;
-                for (int j = jb; j < je; ++j, ++base) {
-                    const int2 c = bcq[j];
-                    const long long ddx = wrapM((long long)c.x - X0, MX);
-                    const long long ddy = wrapM((long long)c.y - Y0, MY);
-                    long long mxx = max(ddx < 0 ? -ddx : ddx, (ddx - WR) < 0 ? WR - ddx : ddx - WR);
-                    long long mxy = max(ddy < 0 ? -ddy : ddy, (ddy - HR) < 0 ? HR - ddy : ddy - HR);
-                    mxx = min(mxx, MX >> 1);
-                    mxy = min(mxy, MY >> 1);
-                    const unsigned long long u = (unsigned long long)(mxx * mxx + mxy * mxy);
-                    myU = u < myU ? u : myU;
-                    if (base < VCAND) {
-                        s_cx[base] = (int)ddx;
-                        s_cy[base] = (int)ddy;
-                        s_id[base] = bid[j];
-                    } else {
-                        s_over = 1;
-                    }
-                }
-            }
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                const unsigned long long v = __shfl_xor_sync(0xffffffffu, myU, o);
-                myU = v < myU ? v : myU;
-            }
-            if (lane == 0 && myU != ULLONG_MAX) atomicMin(&s_U, myU);
-            __syncthreads();
-            if (fx && fy) break;
-            // gap between the region and the unscanned buckets (periods handled by
-            // one conditional shift: the ranges are narrower than a period here)
-            long long g = LLONG_MAX;
-            if (!fx) {
-                const int lx = rx0 < 0 ? (rx0 + nbx) * Bk - D.Lx : rx0 * Bk;            // start of bucket rx0
-                const int ex = rx1 >= nbx ? min((rx1 - nbx + 1) * Bk, D.Lx) + D.Lx      // end of bucket rx1
-                                          : min((rx1 + 1) * Bk, D.Lx);
-                g = min((long long)Q * (x0 - lx), (long long)Q * (ex - (x0 + ncols - 1)));
-            }
-            if (!fy) {
-                const int ly = ry0 < 0 ? (ry0 + nby) * Bk - D.Ly : ry0 * Bk;
-                const int ey = ry1 >= nby ? min((ry1 - nby + 1) * Bk, D.Ly) + D.Ly : min((ry1 + 1) * Bk, D.Ly);
-                g = min(g, min((long long)Q * (y0 - ly), (long long)Q * (ey - (y0 + nrows - 1))));
-            }
-            const unsigned long long U = s_U;
-            __syncthreads();
-            // every unscanned centre is at least g away from the region
-            if (g > 0 && (g >= (1ll << 31) || (unsigned long long)(g * g) > U)) break;
-            px0 = rx0; px1 = rx1; py0 = ry0; py1 = ry1; pfx = fx; pfy = fy; have_prev = true;
+    // The fast path needs every scanned centre's tile-relative position to be
+    // its minimum image for every site of the tile (otherwise the distances
+    // are not the torus distances) and exact in float32 (|v| < 2^23).
+    const bool over = n > WSCAN;
+    bool bad = over;
+    if (!over) {
+        const int WRt = Q * (ncols - 1), HRt = Q * (nrows - 1);
+        for (int k = lane; k < n; k += 32) {
+            const int cx = cxs[k], cy = cys[k];
+            if (!(cx > WRt - hMX && cy > HRt - hMY && cx < (1 << 23) && cx > -(1 << 23) && cy < (1 << 23) &&
+                  cy > -(1 << 23)))
+                bad = true;
         }
-    }
-
-    // Each warp filters the scanned centres for its own patch; a scanned set
-    // holds every centre within U of the tile, so it holds every patch owner.
-    const int px0 = (warp & 1) * 16, py0 = (warp >> 1) * 8;
-    const int cbx = min(px0 + 15, ncols - 1);
-    const int rbx = min(py0 + 7, nrows - 1);
-    const bool has_patch = (px0 < ncols) && (py0 < nrows);
-    int wn = 0;
-    bool wover = false, wbad = false;
-    const int nscan = min(s_n, VCAND);
-    if (K > 0 && !s_over && has_patch) {
-        const long long PX0 = (long long)Q * px0, PY0 = (long long)Q * py0;
-        const long long PW = (long long)Q * (cbx - px0), PH = (long long)Q * (rbx - py0);
-        long long Uw = LLONG_MAX;
-        for (int k = lane; k < nscan; k += 32) {
-            const long long dx = s_cx[k] - PX0, dy = s_cy[k] - PY0;
-            const long long mxx = max(dx < 0 ? -dx : dx, dx > PW ? dx - PW : PW - dx);
-            const long long mxy = max(dy < 0 ? -dy : dy, dy > PH ? dy - PH : PH - dy);
-            Uw = min(Uw, mxx * mxx + mxy * mxy);
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) Uw = min(Uw, __shfl_xor_sync(0xffffffffu, Uw, o));
-        for (int base = 0; base < nscan; base += 32) {
-            const int k = base + lane;
-            bool keep = false;
-            if (k < nscan) {
-                const int cx = s_cx[k], cy = s_cy[k];
-                const long long dx = cx - PX0, dy = cy - PY0;
-                const long long ex = dx < 0 ? -dx : (dx > PW ? dx - PW : 0);
-                const long long ey = dy < 0 ? -dy : (dy > PH ? dy - PH : 0);
-                keep = ex * ex + ey * ey <= Uw;
-                // The fast path needs every scanned centre's tile-relative position to
-                // be its minimum image for every site of the region (otherwise the
-                // distances above are not the torus distances) and exact in float32
-                // (|v| < 2^23). Any exception sends the warp to the exact general path.
-                if (!((long long)cx > WR - (MX >> 1) && (long long)cy > HR - (MY >> 1) &&
-                      cx < (1 << 23) && cx > -(1 << 23) && cy < (1 << 23) && cy > -(1 << 23)))
-                    wbad = true;
-            }
-            const unsigned m = __ballot_sync(0xffffffffu, keep);
-            if (keep) {
-                const int pos = wn + __popc(m & ((1u << lane) - 1u));
-                if (pos < WCAND) {
-                    s_wix[warp][pos] = s_cx[k];
-                    s_wiy[warp][pos] = s_cy[k];
-                    s_wfx[warp][pos] = (float)s_cx[k];
-                    s_wfy[warp][pos] = (float)s_cy[k];
-                    s_wid[warp][pos] = s_id[k];
-                }
-            }
-            wn += __popc(m);
-        }
-        wbad = __any_sync(0xffffffffu, wbad);
-        wover = wn > WCAND;
-        __syncwarp();
+        bad = __any_sync(0xffffffffu, bad);
     }
 
-    const bool fast = (K > 0) && !s_over && !wbad;
-    if (fast && has_patch) {
-        const float* wfx = s_wfx[warp];
-        const int n = wover ? nscan : wn;
-        // sites: lane -> column px0 + (lane & 15), rows py0 + 4*(lane >> 4) .. +3;
-        // then the halo column/row sites outside that 16 x 8 block
-        const int c = px0 + (lane & 15);
-        const int rb = py0 + 4 * (lane >> 4);
-        if (c <= cbx && rb <= rbx) {
-            const float sxf = (float)(Q * c);
-            float syf[4];
-            float f1[4], f2[4];
-            int i1[4];
+    if (!bad) {
+        float2* fc = s_fc[warp];
+        int* kk = s_kk[warp];
+        const int c = lane & 15, rb = 4 * (lane >> 4);   // this lane: column c, rows rb..rb+3 of the patch
+#pragma unroll 1
+        for (int p = 0; p < 8; ++p) {
+            const int pxo = PW * (p & 1), pyo = PH * (p >> 1);
+            if (pxo >= ncols || pyo >= nrows) continue;   // warp-uniform
+            const int pw = min(PW, ncols - pxo), ph = min(PH, nrows - pyo);
+            const int xlo = Q * pxo, xhi = Q * (pxo + pw - 1);
+            const int ylo = Q * pyo, yhi = Q * (pyo + ph - 1);
+            float Uq = Up[0];
 #pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                f1[k] = INFINITY; f2[k] = INFINITY; i1[k] = -1;
-                syf[k] = (float)(Q * (rb + k));
+            for (int q = 1; q < 8; ++q) Uq = (q == p) ? Up[q] : Uq;
+            // ---- 2a. keep the scanned centres within sqrt(U_p) of the patch ----
+            int nk = 0;
+            __syncwarp();
+            for (int base = 0; base < n; base += 32) {
+                const int k = base + lane;
+                bool keep = false;
+                int cx = 0, cy = 0;
+                if (k < n) {
+                    cx = cxs[k];
+                    cy = cys[k];
+                    const int ex = max(0, max(xlo - cx, cx - xhi)), ey = max(0, max(ylo - cy, cy - yhi));
+                    const float exf = __int2float_rd(ex), eyf = __int2float_rd(ey);
+                    keep = __fmaf_rd(exf, exf, __fmul_rd(eyf, eyf)) <= Uq;
+                }
+                const unsigned m = __ballot_sync(0xffffffffu, keep);
+                if (keep) {
+                    const int q = nk + __popc(m & ((1u << lane) - 1u));
+                    if (q < WCAND) {
+                        fc[q] = make_float2((float)cx, (float)cy);
+                        kk[q] = k;
+                    }
+                }
+                nk += __popc(m);
             }
-            if (!wover) {
-                for (int j = 0; j < n; ++j) {
-                    const float dx = sxf - wfx[j];
-                    const float dx2 = dx * dx;
-                    const float fy = s_wfy[warp][j];
+            __syncwarp();
+            // ---- 2b. nearest kept centre for every site of the patch ----
+            if (c < pw && rb < ph) {
+                const int sx = pxo + c;
+                const float sxf = (float)(Q * sx);
+                int o[4];
+                if (nk <= WCAND) {
+                    float syf[4];
+                    unsigned f1[4], f2[4];
 #pragma unroll
                     for (int k = 0; k < 4; ++k) {
-                        const float dy = syf[k] - fy;
-                        const float d = fmaf(dy, dy, dx2);
-                        if (d < f1[k]) { f2[k] = f1[k]; f1[k] = d; i1[k] = j; }
-                        else f2[k] = fminf(f2[k], d);
+                        f1[k] = 0x7f800000u;
+                        f2[k] = 0x7f800000u;
+                        syf[k] = (float)(Q * (pyo + rb + k));
                     }
-                }
-            } else {
-                for (int j = 0; j < n; ++j) {
-                    const float dx = sxf - (float)s_cx[j];
-                    const float dx2 = dx * dx;
-                    const float fy = (float)s_cy[j];
+                    for (int j = 0; j < nk; ++j) {
+                        const float2 cf = fc[j];
+                        const float dx = sxf - cf.x;
+                        const float dx2 = dx * dx;
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) {
+                            const float dy = syf[k] - cf.y;
+                            const unsigned pk = (__float_as_uint(fmaf(dy, dy, dx2)) & ~63u) | (unsigned)j;
+                            const unsigned hi = max(f1[k], pk);
+                            f1[k] = min(f1[k], pk);
+                            f2[k] = min(f2[k], hi);
+                        }
+                    }
 #pragma unroll
                     for (int k = 0; k < 4; ++k) {
-                        const float dy = syf[k] - fy;
-                        const float d = fmaf(dy, dy, dx2);
-                        if (d < f1[k]) { f2[k] = f1[k]; f1[k] = d; i1[k] = j; }
-                        else f2[k] = fminf(f2[k], d);
+                        const float a1 = __uint_as_float(f1[k] & ~63u), a2 = __uint_as_float(f2[k] & ~63u);
+                        // distances carry 2^-23 rounding and 2^-17 truncation: a gap
+                        // above 2^-15 relative means the order is the exact order
+                        if (f2[k] == 0x7f800000u || a2 - a1 > a2 * 3.0517578125e-05f)
+                            o[k] = ids[kk[f1[k] & 63u]];
+                        else
+                            o[k] = owner_exact((long long)Q * sx, (long long)Q * (pyo + rb + k), cxs, cys, ids, kk, nk);
                     }
-                }
-            }
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                const int rr = rb + k;
-                if (rr > rbx) break;
-                int o;
-                // a gap above 2^-20 relative means the float32 order is the exact order
-                // (the float32 distance is within 2^-23 relative of the exact one)
-                if (f2[k] == INFINITY || f2[k] - f1[k] > f2[k] * 9.5367431640625e-07f) {
-                    o = wover ? s_id[i1[k]] : s_wid[warp][i1[k]];
                 } else {
-                    o = wover ? owner_exact((long long)Q * c, (long long)Q * rr, s_cx, s_cy, s_id, n)
-                              : owner_exact((long long)Q * c, (long long)Q * rr, s_wix[warp], s_wiy[warp],
-                                            s_wid[warp], n);
+                    // more kept centres than the list holds: exact over all scanned
+#pragma unroll
+                    for (int k = 0; k < 4; ++k)
+                        o[k] = owner_exact((long long)Q * sx, (long long)Q * (pyo + rb + k), cxs, cys, ids, nullptr, n);
                 }
-                s_own[rr][c] = o;
+#pragma unroll
+                for (int k = 0; k < 4; ++k)
+                    if (rb + k < ph) own[(long long)(y0 + pyo + rb + k) * Lx + x0 + sx] = o[k];
             }
         }
-    } else if (has_patch) {
-        // ---- general path for this warp's sites: per-site minimum image over
-        // the scanned centres (or over all centres when the scan overflowed) ----
-        const bool all = (K > 0) && s_over;
-        const int nc = all ? K : (K > 0 ? nscan : 0);
-        const int ew = cbx - px0 + 1, eh = rbx - py0 + 1;
-        for (int k = lane; k < ew * eh; k += 32) {
-            const int lx = px0 + k % ew, ly = py0 + k / ew;
-            const long long sx = (long long)Q * lx, sy = (long long)Q * ly;   // relative to the tile origin
+    } else {
+        // ---- general path: per-site minimum image, exact int64, over the
+        // scanned list, or over the scanned buckets when the list overflowed ----
+        for (int k = lane; k < ncols * nrows; k += 32) {
+            const int lx = k % ncols, ly = k / ncols;
             long long best = LLONG_MAX;
             int bi = -1;
-            for (int j = 0; j < nc; ++j) {
-                long long cx, cy;
-                int id;
-                if (all) {
-                    cx = wrapM((long long)cq[j].x - X0, MX);
-                    cy = wrapM((long long)cq[j].y - Y0, MY);
-                    id = j;
-                } else {
-                    cx = s_cx[j]; cy = s_cy[j]; id = s_id[j];
+            if (!over) {
+                const long long sx = (long long)Q * lx, sy = (long long)Q * ly;   // relative to the tile origin
+                for (int j = 0; j < n; ++j) {
+                    const long long dx = wrapM(sx - cxs[j], MX), dy = wrapM(sy - cys[j], MY);
+                    const long long d2 = dx * dx + dy * dy;
+                    if (d2 < best || (d2 == best && ids[j] < bi)) { best = d2; bi = ids[j]; }
                 }
-                const long long dx = wrapM(sx - cx, MX), dy = wrapM(sy - cy, MY);
-                const long long d2 = dx * dx + dy * dy;
-                if (d2 < best || (d2 == best && id < bi)) { best = d2; bi = id; }
+            } else {
+                const long long sx = (long long)Q * (x0 + lx), sy = (long long)Q * (y0 + ly);
+                for (int rv = ry0; rv <= ry1; ++rv) {
+                    const int rm = rv < 0 ? rv + nby : (rv >= nby ? rv - nby : rv);
+                    for (int cu = rx0; cu <= rx1; ++cu) {
+                        const int cm = cu < 0 ? cu + nbx : (cu >= nbx ? cu - nbx : cu);
+                        const int bk = rm * nbx + cm;
+                        for (int j = boff[bk]; j < boff[bk + 1]; ++j) {
+                            const int2 cc = bcq[j];
+                            const long long dx = wrapM(sx - cc.x, MX), dy = wrapM(sy - cc.y, MY);
+                            const long long d2 = dx * dx + dy * dy;
+                            const int id = bid[j];
+                            if (d2 < best || (d2 == best && id < bi)) { best = d2; bi = id; }
+                        }
+                    }
+                }
             }
-            s_own[ly][lx] = bi;
+            own[(long long)(y0 + ly) * Lx + x0 + lx] = bi;
         }
     }
-    __syncthreads();
-
-    // ---- write owners of the core tile ----
-    int* own = P.owners + D.site_off;
-    for (int k = threadIdx.x; k < VW * VH / 4; k += VTHREADS) {
-        const int ly = k / (VW / 4), lx = (k % (VW / 4)) * 4;
-        if (ly >= nrows || lx >= ncols) continue;
-        int* o = own + (long long)(y0 + ly) * D.Lx + x0 + lx;
-        if (lx + 4 <= ncols && ((reinterpret_cast<uintptr_t>(o) & 15u) == 0)) {
-            *reinterpret_cast<int4*>(o) = make_int4(s_own[ly][lx], s_own[ly][lx + 1], s_own[ly][lx + 2], s_own[ly][lx + 3]);
-        } else {
-            for (int i = 0; i < 4 && lx + i < ncols; ++i) o[i] = s_own[ly][lx + i];
-        }
-    }
-
 }
 
 // ---------------------------------------------------------------------------
@@ -576,7 +578,7 @@ void launch_merge_lists(const Launch& L) {
 }
 
 void launch_voronoi(const Launch& L) {
-    k_voronoi<<<L.total_tilesV, VTHREADS, 0, L.s>>>(L.P, L.T);
+    k_voronoi<<<(L.total_tilesV + VWARPS - 1) / VWARPS, 32 * VWARPS, 0, L.s>>>(L.P, L.T);
     ++*L.nlaunch;
 }
 
