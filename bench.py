@@ -201,14 +201,12 @@ def stage_bytes(sequence: bool):
 
     stage 0 threshold + tile union-find: field read 4, foreground bit write and
             read 1/8 + 1/8
-    stage 2 label pass: foreground bits 1/8, label write 4, plus the past
-            labels: read 4 in the label pass (frame from an earlier push), or
-            read 4 + 4 (labels now and past) by the overlap pass (frame
-            sequence, past frame written in the same push)
+    stage 2 run labels + overlaps: foreground bits of the frame and of its
+            past frame, 1/8 + 1/8 (run tables are per run, not per site)
     stage 3 Voronoi owners: owner write 4
     stage 4 links: owner read 4
     """
-    return {0: 4.25, 2: 12.125 if sequence else 8.125, 3: 4.0, 4: 4.0}
+    return {0: 4.25, 2: 0.25, 3: 4.0, 4: 4.0}
 
 
 def roofline_of(stage_ms, names, launches_per_stage, sites_per_launch, sequence, peak, peak_kind):

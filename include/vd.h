@@ -120,7 +120,8 @@ vd_status vd_get_match(vd_ctx* ctx, int32_t* phi, int64_t cap, int64_t* n);     
 /* Stage timing (measurement support, not part of the detect result). When
  * enabled, every vd_push_frame records CUDA events on the context stream at
  * the boundaries of the pipeline stages (labelling tiles, bubble merge and
- * centroids, label pass, Voronoi owners, links, adjacency/match/flips) and runs
+ * centroids, run labels and overlaps, Voronoi owners, links,
+ * adjacency/match/flips) and runs
  * without graph replay. vd_get_timing synchronises the stream and returns
  * the summed milliseconds per stage since the last call (stage_ms has cap
  * entries; *n_stages is set), the number of kernels launched and frames

@@ -102,7 +102,7 @@ static const int N_STAGES = 6;
 static const char* STAGE_NAMES[N_STAGES] = {
     "labelling tiles (threshold + tile union-find)",
     "bubbles (border merge, ranks, centroids, bucket grid)",
-    "label pass + overlap histogram",
+    "run labels + overlap histogram",
     "voronoi owners",
     "links (owner boundaries, plaquettes, merge into hashes)",
     "adjacency, match, translation, flips",
@@ -224,7 +224,7 @@ vd_status create_batch(const vd_config* cfgs, int n, vd_batch** out, bool sequen
     b->s = (cudaStream_t)cfgs[0].stream;
     b->desc.resize(n);
     long long site = 0, word = 0, tile = 0, border = 0, comp = 0, edge = 0, eh = 0, oh = 0, bucket = 0, ovl = 0;
-    long long piece_cap = 0, scan_items = 0;
+    long long piece_cap = 0, scan_items = 0, max_sites = 0;
     for (int i = 0; i < n; ++i) {
         const vd_config& c = cfgs[i];
         InstDesc& D = b->desc[i];
@@ -266,6 +266,7 @@ vd_status create_batch(const vd_config* cfgs, int n, vd_batch** out, bool sequen
         D.ovl_off = ovl;
         const long long ntiles = (long long)D.ntx * D.nty;
         site += N;
+        max_sites = std::max(max_sites, N);
         word += (long long)c.Ly * D.wpr;
         tile += ntiles;
         border += ntiles * BORDER;
@@ -288,10 +289,13 @@ vd_status create_batch(const vd_config* cfgs, int n, vd_batch** out, bool sequen
     P.desc = M.alloc<InstDesc>(n);
     P.st = M.alloc<InstState>(n);
     P.g = M.alloc<Globals>(1);
-    P.labels[0] = M.alloc<int>(site);
-    P.labels[1] = M.alloc<int>(site);
+    P.rp = M.alloc<int>(tile * TRUNS);
+    P.rl[0] = M.alloc<int>(tile * TRUNS);
+    P.rl[1] = M.alloc<int>(tile * TRUNS);
+    P.lab_out = M.alloc<int>(max_sites);
     P.owners = M.alloc<int>(site);
-    P.fgbits = M.alloc<unsigned>(word);
+    P.fgbits[0] = M.alloc<unsigned>(word);
+    P.fgbits[1] = M.alloc<unsigned>(word);
     P.rootbits = M.alloc<unsigned>(word);
     P.rankpre = M.alloc<int>(word);
     P.tile_pbase = M.alloc<int>(tile);
@@ -361,11 +365,12 @@ vd_status create_batch(const vd_config* cfgs, int n, vd_batch** out, bool sequen
     chk(cudaMemcpyAsync(P.desc, b->desc.data(), sizeof(InstDesc) * n, cudaMemcpyHostToDevice, b->s));
     chk(cudaMemsetAsync(P.st, 0, sizeof(InstState) * n, b->s));
     chk(cudaMemsetAsync(P.g, 0, sizeof(Globals), b->s));
-    chk(cudaMemsetAsync(P.labels[0], 0xff, sizeof(int) * site, b->s));
-    chk(cudaMemsetAsync(P.labels[1], 0xff, sizeof(int) * site, b->s));
+    chk(cudaMemsetAsync(P.rl[0], 0xff, sizeof(int) * tile * TRUNS, b->s));
+    chk(cudaMemsetAsync(P.rl[1], 0xff, sizeof(int) * tile * TRUNS, b->s));
     chk(cudaMemsetAsync(P.rootbits, 0, sizeof(unsigned) * word, b->s));
     chk(cudaMemsetAsync(P.bcnt, 0, sizeof(int) * bucket, b->s));
     chk(cudaMemsetAsync(P.deg, 0, sizeof(int) * comp, b->s));
+    chk(cudaMemsetAsync(P.best_n, 0, sizeof(unsigned long long) * comp, b->s));
     chk(cudaMemsetAsync(P.tdeg, 0, sizeof(int) * comp, b->s));
     chk(cudaMemsetAsync(P.rowoff[0], 0, sizeof(int) * comp, b->s));
     chk(cudaMemsetAsync(P.rowoff[1], 0, sizeof(int) * comp, b->s));
@@ -507,7 +512,12 @@ vd_status get_array(vd_batch* b, int i, int which, void* out, int64_t cap, int64
     const void* src = nullptr;
     size_t esz = 4;
     switch (which) {
-        case 0: cnt = N; src = b->P.labels[slot] + D.site_off; break;
+        case 0: {
+            cnt = N;
+            launch_expand_labels(b->s, b->P, i, slot, b->P.lab_out, N);
+            src = b->P.lab_out;
+            break;
+        }
         case 1: cnt = N; src = b->P.owners + D.site_off; break;
         case 2: cnt = 2ll * st.K; src = b->P.cq + D.comp_off; break;
         case 3: {

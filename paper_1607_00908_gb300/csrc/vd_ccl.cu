@@ -1,7 +1,7 @@
 // Bubble identification (Section 3.1 of the paper): threshold, periodic
 // 4-connected labelling with canonical ids, sizes and centres of mass in
-// 1/1024-site fixed point, the centroid bucket grid, and the per-site label
-// pass that also builds the past/now overlap histogram (Section 3.2.3).
+// 1/1024-site fixed point, the centroid bucket grid, and the run-label pass
+// that also builds the past/now overlap histogram (Section 3.2.3).
 //
 // Labelling works on 64 x 32 tiles. Pass A reads the field once (vector
 // loads), stores the foreground bits (1 bit per site), runs a union-find in
@@ -10,9 +10,10 @@
 // four tile borders. Pieces are then merged across tile borders (periodic) by
 // a global union-find whose root is the piece with the smallest first site, so
 // the root of every bubble is the bubble's smallest linear index; bubble ids
-// are the ranks of those roots (a scan over a root bitmap). The label pass
-// re-runs the tile union-find from the stored bits (instead of re-reading the
-// field) and writes final labels.
+// are the ranks of those roots (a scan over a root bitmap). Labels are kept
+// per run (a 64-site tile row holds at most 32 runs): pass A records each
+// run's piece, the run-label pass turns pieces into bubble ids, and per-site
+// labels are expanded from the foreground bits and run labels on request.
 #include "vd_internal.cuh"
 
 namespace vd {
@@ -55,7 +56,7 @@ __device__ __forceinline__ void uf_union(int* p, int a, int b) {
 // are numbered left to right; run j of row r has id r*32 + j, so ids follow
 // raster order and the smallest id of a component is its first site.
 // ---------------------------------------------------------------------------
-constexpr int RUNS = TH * 32;   // run ids per tile
+constexpr int RUNS = TRUNS;     // run ids per tile
 
 __device__ __forceinline__ unsigned long long run_starts(unsigned long long m) { return m & ~(m << 1); }
 __device__ __forceinline__ unsigned long long upto(int c) { return c == 63 ? ~0ull : ((2ull << c) - 1ull); }
@@ -110,10 +111,8 @@ struct UfSmem {                  // one warp's tile: row masks and union-find ov
     int par[RUNS];               // swizzled: parent of run id k at par[SW(k)]
     unsigned char col[RUNS];     // swizzled: start column of each run
 };
-struct LabelSmem : UfSmem {
-    int aux[RUNS];     // per root run: (n << 16) | sum(y - y_root), then piece id / bubble id
-};
-struct TileSmem : LabelSmem {
+struct TileSmem : UfSmem {
+    int aux[RUNS];     // per root run: (n << 16) | sum(y - y_root), then piece id
     int su[RUNS];      // per root run: sum(x - x_root)
 };
 
@@ -169,12 +168,12 @@ __device__ __forceinline__ unsigned warp_roots(const UfSmem& T, unsigned long lo
     return R;
 }
 
-// row masks of a tile from the stored foreground bits (lane r -> row r)
-__device__ __forceinline__ unsigned long long load_row_mask(const Pools& P, const InstDesc& D, int x0, int y0) {
+// row masks of a tile from stored foreground bits `fg` (lane r -> row r)
+__device__ __forceinline__ unsigned long long load_row_mask(const unsigned* fg, const InstDesc& D, int x0, int y0) {
     const int y = y0 + (threadIdx.x & 31);
     unsigned long long m = 0;
     if (y < D.Ly) {
-        const unsigned* row = P.fgbits + D.word_off + (long long)y * D.wpr;
+        const unsigned* row = fg + D.word_off + (long long)y * D.wpr;
         const int wx = x0 >> 5;
         m = row[wx];
         if (wx + 1 < D.wpr) m |= (unsigned long long)row[wx + 1] << 32;
@@ -221,7 +220,7 @@ __global__ __launch_bounds__(256) void k_threshold(Pools P, StepTable T) {
             for (int i = 0; i < n; ++i)
                 if (is_fg(__ldcs(f + i), thr, pol)) bits |= 1u << i;
         }
-        P.fgbits[D.word_off + w] = bits;
+        P.fgbits[S.slot ^ 1][D.word_off + w] = bits;
     }
 }
 
@@ -244,7 +243,7 @@ __global__ __launch_bounds__(32 * CCL_WARPS) void k_ccl_tiles(Pools P, StepTable
     const int Lx = D.Lx, Ly = D.Ly;
 
     // 1. foreground masks of the tile rows (written by k_threshold; L2-resident)
-    const unsigned long long my_m = load_row_mask(P, D, x0, y0);
+    const unsigned long long my_m = load_row_mask(P.fgbits[S.slot ^ 1], D, x0, y0);
     TS.m[lane] = my_m;
 
     // 2. union-find over runs
@@ -316,6 +315,11 @@ __global__ __launch_bounds__(32 * CCL_WARPS) void k_ccl_tiles(Pools P, StepTable
         }
     }
     __syncwarp();
+    // piece id of every run of this row (resolved to bubble labels later)
+    {
+        int* rp = P.rp + (long long)(D.tile_off + t) * RUNS + lane * 32;
+        for (int j = 0; j < nr; ++j) rp[j] = TS.aux[SW(TS.par[SW(lane * 32 + j)])];
+    }
 
     // 5. borders: [0,TH) left col, [TH,2TH) right col, [2TH,2TH+TW) top row, [.., +TW) bottom row
     const int ncols = min(TW, Lx - x0), nrows = min(TH, Ly - y0);
@@ -454,7 +458,7 @@ __global__ __launch_bounds__(32 * WIDE_WARPS) void k_comp_wide(Pools P) {
         const int r = P.p_parent[pid];
         const int qr = P.p_q[r];
         const int yr = qr / D.Lx, xr = qr - yr * D.Lx;
-        const unsigned long long m = load_row_mask(P, D, x0, y0);
+        const unsigned long long m = load_row_mask(P.fgbits[P.st[inst].slot ^ 1], D, x0, y0);
         TS.m[lane] = m;
         warp_runs_uf(TS, m);
         const unsigned long long Sq = run_starts(TS.m[yq - y0]);
@@ -489,11 +493,17 @@ __global__ __launch_bounds__(32 * WIDE_WARPS) void k_comp_wide(Pools P) {
     }
 }
 
-// Q10 centroids of bubbles; bucket counts; clear the root bitmap for the next step
+// Q10 centroids of bubbles; bucket counts; clear the root bitmap for the next
+// step and the match state of every now-bubble; every non-root piece takes its
+// bubble id (for the run-label pass)
 __global__ void k_comp_final(Pools P) {
     const int n = min(P.g->n_pieces, P.piece_cap);
     for (int pid = blockIdx.x * blockDim.x + threadIdx.x; pid < n; pid += gridDim.x * blockDim.x) {
-        if (P.p_parent[pid] != pid) continue;
+        const int r = P.p_parent[pid];
+        if (r != pid) {
+            P.p_comp[pid] = P.p_comp[r];   // roots were ranked by k_comp_accum
+            continue;
+        }
         const int inst = P.p_inst[pid];
         const InstDesc& D = P.desc[inst];
         const InstState& S = P.st[inst];
@@ -502,6 +512,10 @@ __global__ void k_comp_final(Pools P) {
         P.rootbits[D.word_off + (long long)yq * D.wpr + (xq >> 5)] = 0u;
         const int c = P.p_comp[pid];
         if (c >= D.comp_cap) continue;
+        // match state of now-bubble c, filled by the graph stage of this step
+        P.best_p[D.comp_off + c] = 0ull;
+        P.inv[D.comp_off + c] = -1;
+        P.active[D.comp_off + c] = 0;
         const long long nn = P.p_accn[pid];
         const long long MX = (long long)Q * D.Lx, MY = (long long)Q * D.Ly;
         // round half up: floor((2p + n) / 2n) with p = 1024 * S
@@ -540,31 +554,22 @@ __global__ void k_bucket_scatter(Pools P) {
 constexpr int LBL_WARPS = 4;    // tiles per block in the label pass
 constexpr int WSET = 128;       // per-warp overlap set
 
-// add (key, count) to the warp's shared set (read-first probe, 32-bit hash)
-__device__ __forceinline__ void ovl_add_w(unsigned long long* key, unsigned* cnt, const Pools& P, const InstDesc& D,
-                                          int inst, unsigned long long k, unsigned c) {
-    unsigned h = hash_small(k) & (WSET - 1);
-    for (int probe = 0; probe < WSET; ++probe) {
-        const unsigned long long o = key[h] == k ? k : atomicCAS(&key[h], EMPTY_KEY, k);
-        if (o == EMPTY_KEY || o == k) {
-            atomicAdd(&cnt[h], c);
-            return;
-        }
-        h = (h + 1) & (WSET - 1);
-    }
-    ovl_global_insert(P, D, inst, k, c);   // set full
-}
-
-__global__ __launch_bounds__(32 * LBL_WARPS) void k_labels(Pools P, StepTable T) {
-    __shared__ LabelSmem s_tile[LBL_WARPS];
+// ---------------------------------------------------------------------------
+// Run labels and the overlap histogram (Sections 3.1 and 3.2.3), one warp per
+// 64 x 32 labelling tile, lane r on tile row r. Every run of the frame gets
+// the bubble label of its piece (kept per slot for the next frame and for
+// label queries). The sites shared by bubble i of the past frame and bubble j
+// now form, in each row, runs of (past mask AND now mask); each such run lies
+// inside one past run and one now run, so the overlap histogram is a sum of
+// run lengths over (past label, now label) pairs and no site is visited.
+// ---------------------------------------------------------------------------
+__global__ __launch_bounds__(32 * LBL_WARPS) void k_run_labels(Pools P, StepTable T) {
+    __shared__ int s_lab[LBL_WARPS][RUNS];
     __shared__ unsigned long long s_key[LBL_WARPS][WSET];
     __shared__ unsigned s_cnt[LBL_WARPS][WSET];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int b = blockIdx.x * LBL_WARPS + w;
     if (b >= T.tileA_pre[T.n_act]) return;
-    LabelSmem& TS = s_tile[w];
-    unsigned long long* skey = s_key[w];
-    unsigned* scnt = s_cnt[w];
     const int a = seg_of_int(T.tileA_pre, T.n_act, b);
     const int inst = T.act[a];
     const InstDesc& D = P.desc[inst];
@@ -573,186 +578,107 @@ __global__ __launch_bounds__(32 * LBL_WARPS) void k_labels(Pools P, StepTable T)
     const int tx = t % D.ntx, ty = t / D.ntx;
     const int x0 = tx * TW, y0 = ty * TH;
     const int now = S.slot ^ 1;
-    // past labels are read here only when they come from an earlier step; a
-    // past frame written in this step is compared by k_overlap afterwards
-    const bool with_prev = S.has_prev != 0 && !S.prev_same;
-    const int Lx = D.Lx;
+    int* lab = s_lab[w];
+    unsigned long long* skey = s_key[w];
+    unsigned* scnt = s_cnt[w];
 
+    // 1. bubble label of each run of this row
+    const long long rbase = (long long)(D.tile_off + t) * RUNS + lane * 32;
+    const unsigned long long m = load_row_mask(P.fgbits[now], D, x0, y0);
+    const unsigned long long Sn = run_starts(m);
+    const int nr = __popcll(Sn);
+    for (int j = 0; j < nr; ++j) {
+        const int pid = P.rp[rbase + j];
+        const int l = pid >= 0 ? P.p_comp[pid] : -1;
+        P.rl[now][rbase + j] = l;
+        lab[SW(lane * 32 + j)] = l;
+    }
+    if (!S.has_prev) return;   // warp-uniform
+
+    // 2. overlap runs with the past frame (same lattice, same tile)
     for (int k = lane; k < WSET; k += 32) {
         skey[k] = EMPTY_KEY;
         scnt[k] = 0;
     }
-    const unsigned long long my_m = load_row_mask(P, D, x0, y0);
-    TS.m[lane] = my_m;
-    warp_runs_uf(TS, my_m);
-    {
-        int rbase, m_tot;
-        const unsigned R = warp_roots(TS, my_m, &rbase, &m_tot);
-        const int pbase = P.tile_pbase[D.tile_off + t];
-        unsigned rq = R;
-        int k = rbase;
-        while (rq) {
-            const int j = __ffs(rq) - 1;
-            rq &= rq - 1;
-            TS.aux[SW(lane * 32 + j)] = pbase >= 0 ? P.p_comp[P.p_parent[pbase + k]] : -1;
-            ++k;
+    __syncwarp();
+    const int pb = S.prev_buf;
+    const bool same = S.prev_same != 0;   // past frame labelled in this step: its runs still hold piece ids
+    const InstDesc& DP = P.desc[S.prev_inst];
+    const long long pbase = (long long)(DP.tile_off + t) * RUNS + lane * 32;
+    const unsigned long long mp = load_row_mask(P.fgbits[pb], DP, x0, y0);
+    const unsigned long long Sp = run_starts(mp);
+    const unsigned long long A = m & mp;
+    unsigned long long As = run_starts(A);
+    const int nA = __reduce_max_sync(0xffffffffu, __popcll(As));
+    for (int i = 0; i < nA; ++i) {   // all lanes: the set insertion is warp-wide
+        unsigned long long key = EMPTY_KEY;
+        unsigned len = 0;
+        if (As) {
+            const int c = __ffsll(As) - 1;
+            As &= As - 1;
+            len = run_length(A, c);
+            const int ln = lab[SW(lane * 32 + run_index(Sn, c))];
+            const int jp = run_index(Sp, c);
+            int lp;
+            if (same) {
+                const int pid = P.rp[pbase + jp];
+                lp = pid >= 0 ? P.p_comp[pid] : -1;
+            } else {
+                lp = P.rl[pb][pbase + jp];
+            }
+            if (ln >= 0 && lp >= 0) key = ((unsigned long long)(unsigned)lp << 32) | (unsigned)ln;
         }
+        unsigned csum = 0;
+        if (!warp_set_add(skey, scnt, WSET, key, len, &csum)) ovl_global_insert(P, D, inst, key, csum);
     }
     __syncwarp();
-
-    // labels, row by row: lane l writes columns l and l+32 (coalesced)
-    const bool in0 = x0 + lane < Lx, in1 = x0 + 32 + lane < Lx;
-    const int nrows = min(TH, D.Ly - y0);
-    int* out = P.labels[now] + D.site_off + (long long)y0 * Lx + x0 + lane;
-    const int* prv = P.labels[S.prev_buf] + P.desc[S.prev_inst].site_off + (long long)y0 * Lx + x0 + lane;
-    unsigned long long cur0 = EMPTY_KEY, cur1 = EMPTY_KEY;
-    unsigned c0 = 0, c1 = 0;
-    for (int rb = 0; rb < nrows; rb += 8) {
-        // past labels of 8 rows in flight at once
-        int p0[8], p1[8];
-#pragma unroll
-        for (int k = 0; k < 8; ++k) {
-            const int r = rb + k;
-            const bool ok = with_prev && r < nrows;
-            p0[k] = (ok && in0) ? __ldcs(prv + (long long)r * Lx) : -1;
-            p1[k] = (ok && in1) ? __ldcs(prv + (long long)r * Lx + 32) : -1;
-        }
-#pragma unroll
-        for (int k = 0; k < 8; ++k) {
-            const int r = rb + k;
-            if (r >= nrows) break;
-            const unsigned long long m = TS.m[r];
-            const unsigned long long Sr = run_starts(m);
-            const int l0 = ((m >> lane) & 1ull) ? TS.aux[SW(TS.par[SW(r * 32 + run_index(Sr, lane))])] : -1;
-            const int l1 = ((m >> (lane + 32)) & 1ull) ? TS.aux[SW(TS.par[SW(r * 32 + run_index(Sr, lane + 32))])] : -1;
-            if (in0) out[(long long)r * Lx] = l0;
-            if (in1) out[(long long)r * Lx + 32] = l1;
-            if (with_prev) {
-                // aggregate equal (past, now) pairs down each column
-                const unsigned long long k0 = (l0 >= 0 && p0[k] >= 0) ? (((unsigned long long)(unsigned)p0[k] << 32) | (unsigned)l0) : EMPTY_KEY;
-                const unsigned long long k1 = (l1 >= 0 && p1[k] >= 0) ? (((unsigned long long)(unsigned)p1[k] << 32) | (unsigned)l1) : EMPTY_KEY;
-                if (k0 != cur0) {
-                    if (cur0 != EMPTY_KEY) ovl_add_w(skey, scnt, P, D, inst, cur0, c0);
-                    cur0 = k0;
-                    c0 = 0;
-                }
-                if (k0 != EMPTY_KEY) ++c0;
-                if (k1 != cur1) {
-                    if (cur1 != EMPTY_KEY) ovl_add_w(skey, scnt, P, D, inst, cur1, c1);
-                    cur1 = k1;
-                    c1 = 0;
-                }
-                if (k1 != EMPTY_KEY) ++c1;
-            }
-        }
-    }
-    if (with_prev) {
-        if (cur0 != EMPTY_KEY) ovl_add_w(skey, scnt, P, D, inst, cur0, c0);
-        if (cur1 != EMPTY_KEY) ovl_add_w(skey, scnt, P, D, inst, cur1, c1);
-        __syncwarp();
-        // append the tile's (past, now, count) triples (one reservation per
-        // round); k_merge_lists adds them into the overlap hash
-        for (int kb = 0; kb < WSET; kb += 32) {
-            const unsigned long long key = skey[kb + lane];
-            const bool has = key != EMPTY_KEY;
-            const unsigned m = __ballot_sync(0xffffffffu, has);
-            if (!m) continue;
-            int base = 0;
-            if (lane == 0) base = atomicAdd(&P.st[inst].n_oapp, __popc(m));
-            base = __shfl_sync(0xffffffffu, base, 0);
-            if (has) {
-                const int pos = base + __popc(m & ((1u << lane) - 1u));
-                if (pos < D.ovl_cap) {
-                    P.oapp_key[D.ovl_off + pos] = key;
-                    P.oapp_cnt[D.ovl_off + pos] = scnt[kb + lane];
-                } else {
-                    ovl_global_insert(P, D, inst, key, scnt[kb + lane]);   // list full: insert directly
-                }
+    // append the tile's (past, now, count) triples (one reservation per round);
+    // k_merge_lists adds them into the overlap hash
+    for (int kb = 0; kb < WSET; kb += 32) {
+        const unsigned long long key = skey[kb + lane];
+        const bool has = key != EMPTY_KEY;
+        const unsigned mk = __ballot_sync(0xffffffffu, has);
+        if (!mk) continue;
+        int base = 0;
+        if (lane == 0) base = atomicAdd(&P.st[inst].n_oapp, __popc(mk));
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (has) {
+            const int pos = base + __popc(mk & ((1u << lane) - 1u));
+            if (pos < D.ovl_cap) {
+                P.oapp_key[D.ovl_off + pos] = key;
+                P.oapp_cnt[D.ovl_off + pos] = scnt[kb + lane];
+            } else {
+                ovl_global_insert(P, D, inst, key, scnt[kb + lane]);   // list full: insert directly
             }
         }
     }
 }
 
-// Overlap histogram for frames whose past frame was labelled in the same step
-// (frame sequences): reads both label arrays, one warp per 64 x 32 tile.
-__global__ __launch_bounds__(32 * LBL_WARPS) void k_overlap(Pools P, StepTable T) {
-    __shared__ unsigned long long s_key[LBL_WARPS][WSET];
-    __shared__ unsigned s_cnt[LBL_WARPS][WSET];
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int b = blockIdx.x * LBL_WARPS + w;
-    if (b >= T.tileA_pre[T.n_act]) return;
-    const int a = seg_of_int(T.tileA_pre, T.n_act, b);
-    const int inst = T.act[a];
-    const InstState& S = P.st[inst];
-    if (!(S.has_prev && S.prev_same)) return;
+// per-site labels of one instance's frame in `slot`, from its foreground bits
+// and run labels (-1 for background)
+__global__ void k_expand_labels(Pools P, int inst, int slot, int* out, long long n) {
     const InstDesc& D = P.desc[inst];
-    unsigned long long* skey = s_key[w];
-    unsigned* scnt = s_cnt[w];
-    const int t = b - T.tileA_pre[a];
-    const int tx = t % D.ntx, ty = t / D.ntx;
-    const int x0 = tx * TW, y0 = ty * TH;
-    const int Lx = D.Lx;
-    for (int k = lane; k < WSET; k += 32) {
-        skey[k] = EMPTY_KEY;
-        scnt[k] = 0;
-    }
-    __syncwarp();
-    const bool in0 = x0 + lane < Lx, in1 = x0 + 32 + lane < Lx;
-    const int nrows = min(TH, D.Ly - y0);
-    const int* cur = P.labels[S.slot ^ 1] + D.site_off + (long long)y0 * Lx + x0 + lane;
-    const int* prv = P.labels[S.prev_buf] + P.desc[S.prev_inst].site_off + (long long)y0 * Lx + x0 + lane;
-    unsigned long long cur0 = EMPTY_KEY, cur1 = EMPTY_KEY;
-    unsigned c0 = 0, c1 = 0;
-    for (int rb = 0; rb < nrows; rb += 8) {
-        int l0[8], l1[8], p0[8], p1[8];
-#pragma unroll
-        for (int k = 0; k < 8; ++k) {
-            const bool ok = rb + k < nrows;
-            const long long o = (long long)(rb + k) * Lx;
-            l0[k] = (ok && in0) ? __ldcs(cur + o) : -1;
-            l1[k] = (ok && in1) ? __ldcs(cur + o + 32) : -1;
-            p0[k] = (ok && in0) ? __ldcs(prv + o) : -1;
-            p1[k] = (ok && in1) ? __ldcs(prv + o + 32) : -1;
+    const unsigned* fg = P.fgbits[slot] + D.word_off;
+    const int* rl = P.rl[slot] + (long long)D.tile_off * RUNS;
+    for (long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x; g < n; g += (long long)gridDim.x * blockDim.x) {
+        const int y = (int)(g / D.Lx), x = (int)(g - (long long)y * D.Lx);
+        const int tx = x / TW, x0 = tx * TW, wx = x0 >> 5;
+        const unsigned* row = fg + (long long)y * D.wpr;
+        unsigned long long m = row[wx];
+        if (wx + 1 < D.wpr) m |= (unsigned long long)row[wx + 1] << 32;
+        const int c = x - x0;
+        int l = -1;
+        if ((m >> c) & 1ull) {
+            const int tile = (y / TH) * D.ntx + tx;
+            l = rl[(long long)tile * RUNS + (y % TH) * 32 + run_index(run_starts(m), c)];
         }
-#pragma unroll
-        for (int k = 0; k < 8; ++k) {
-            const unsigned long long k0 = (l0[k] >= 0 && p0[k] >= 0) ? (((unsigned long long)(unsigned)p0[k] << 32) | (unsigned)l0[k]) : EMPTY_KEY;
-            const unsigned long long k1 = (l1[k] >= 0 && p1[k] >= 0) ? (((unsigned long long)(unsigned)p1[k] << 32) | (unsigned)l1[k]) : EMPTY_KEY;
-            if (k0 != cur0) {
-                if (cur0 != EMPTY_KEY) ovl_add_w(skey, scnt, P, D, inst, cur0, c0);
-                cur0 = k0;
-                c0 = 0;
-            }
-            if (k0 != EMPTY_KEY) ++c0;
-            if (k1 != cur1) {
-                if (cur1 != EMPTY_KEY) ovl_add_w(skey, scnt, P, D, inst, cur1, c1);
-                cur1 = k1;
-                c1 = 0;
-            }
-            if (k1 != EMPTY_KEY) ++c1;
-        }
+        out[g] = l;
     }
-    if (cur0 != EMPTY_KEY) ovl_add_w(skey, scnt, P, D, inst, cur0, c0);
-    if (cur1 != EMPTY_KEY) ovl_add_w(skey, scnt, P, D, inst, cur1, c1);
-    __syncwarp();
-    for (int kb = 0; kb < WSET; kb += 32) {
-        const unsigned long long key = skey[kb + lane];
-        const bool has = key != EMPTY_KEY;
-        const unsigned m = __ballot_sync(0xffffffffu, has);
-        if (!m) continue;
-        int base = 0;
-        if (lane == 0) base = atomicAdd(&P.st[inst].n_oapp, __popc(m));
-        base = __shfl_sync(0xffffffffu, base, 0);
-        if (has) {
-            const int pos = base + __popc(m & ((1u << lane) - 1u));
-            if (pos < D.ovl_cap) {
-                P.oapp_key[D.ovl_off + pos] = key;
-                P.oapp_cnt[D.ovl_off + pos] = scnt[kb + lane];
-            } else {
-                ovl_global_insert(P, D, inst, key, scnt[kb + lane]);
-            }
-        }
-    }
+}
+
+void launch_expand_labels(cudaStream_t s, const Pools& P, int inst, int slot, int* out, long long n) {
+    const long long blocks = (n + 255) / 256;
+    k_expand_labels<<<(int)(blocks < 4096 ? (blocks > 0 ? blocks : 1) : 4096), 256, 0, s>>>(P, inst, slot, out, n);
 }
 
 void launch_ccl_tiles(const Launch& L) {
@@ -773,7 +699,7 @@ void launch_ccl_rest(const Launch& L) {
     }
     k_ccl_flatten<<<L.grid_items, 256, 0, L.s>>>(L.P);
     ++*L.nlaunch;
-    launch_plan(L, 1);
+    launch_plan(L, 1, ends_bit(SCAN_BUCKETS));
     launch_scan(L, SCAN_ROOTBITS);
     k_comp_accum<<<L.grid_items, 256, 0, L.s>>>(L.P);
     ++*L.nlaunch;
@@ -787,12 +713,8 @@ void launch_ccl_rest(const Launch& L) {
 }
 
 void launch_labels(const Launch& L) {
-    k_labels<<<(L.total_tilesA + LBL_WARPS - 1) / LBL_WARPS, 32 * LBL_WARPS, 0, L.s>>>(L.P, L.T);
+    k_run_labels<<<(L.total_tilesA + LBL_WARPS - 1) / LBL_WARPS, 32 * LBL_WARPS, 0, L.s>>>(L.P, L.T);
     ++*L.nlaunch;
-    if (L.sequence) {
-        k_overlap<<<(L.total_tilesA + LBL_WARPS - 1) / LBL_WARPS, 32 * LBL_WARPS, 0, L.s>>>(L.P, L.T);
-        ++*L.nlaunch;
-    }
 }
 
 }  // namespace vd

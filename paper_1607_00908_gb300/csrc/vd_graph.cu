@@ -31,6 +31,8 @@ __global__ void k_step_begin(Pools P, StepTable T) {
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         P.g->n_pieces = 0;
         P.g->n_wide = 0;
+        P.g->scan_step = (P.g->scan_step + 1) & 0x07FFFFFFu;   // new tags for this step's scans
+        for (int k = 0; k < 8; ++k) P.g->scan_ticket[k] = 0;
     }
     for (int a = blockIdx.x * blockDim.x + threadIdx.x; a < T.n_act; a += gridDim.x * blockDim.x) {
         const int inst = T.act[a];
@@ -147,18 +149,6 @@ __global__ void k_csr_sort(Pools P, StepTable T) {
 // ---------------------------------------------------------------------------
 // isomorphism Phi by mutual best overlap
 // ---------------------------------------------------------------------------
-__global__ void k_match_init(Pools P, StepTable T) {
-    for_items(T, PRE_KP, [&](int inst, long long p) {
-        P.best_n[P.desc[inst].comp_off + p] = 0ull;
-    });
-    for_items(T, PRE_K, [&](int inst, long long n) {
-        const long long o = P.desc[inst].comp_off + n;
-        P.best_p[o] = 0ull;
-        P.inv[o] = -1;
-        P.active[o] = 0;
-    });
-}
-
 // pack (count, label) so that atomicMax picks the largest count, then the smallest label
 __device__ __forceinline__ unsigned long long pack_best(unsigned cnt, int label) {
     return ((unsigned long long)cnt << 32) | (0xffffffffu - (unsigned)label);
@@ -188,6 +178,7 @@ __global__ void k_match_phi(Pools P, StepTable T) {
     for_items(T, PRE_KP, [&](int inst, long long p) {
         const InstDesc& D = P.desc[inst];
         const unsigned long long v = P.best_n[D.comp_off + p];
+        P.best_n[D.comp_off + p] = 0ull;   // zero again for the next step
         int res = -1;
         if (v != 0ull) {
             const int n = unpack_label(v);
@@ -324,12 +315,11 @@ __global__ void k_flip_write(Pools P, StepTable T) {
 
 void launch_graph(const Launch& L) {
     const int g = L.grid_items;
+    launch_plan(L, 0, ends_bit(SCAN_DEG));
     launch_scan(L, SCAN_DEG);
     k_csr_scatter<<<g, 256, 0, L.s>>>(L.P, L.T);
     ++*L.nlaunch;
     k_csr_sort<<<g, 256, 0, L.s>>>(L.P, L.T);
-    ++*L.nlaunch;
-    k_match_init<<<g, 256, 0, L.s>>>(L.P, L.T);
     ++*L.nlaunch;
     k_match_best<<<g, 256, 0, L.s>>>(L.P, L.T);
     ++*L.nlaunch;
@@ -337,6 +327,7 @@ void launch_graph(const Launch& L) {
     ++*L.nlaunch;
     k_translate_count<<<g, 256, 0, L.s>>>(L.P, L.T);
     ++*L.nlaunch;
+    launch_plan(L, 0, ends_bit(SCAN_TDEG));
     launch_scan(L, SCAN_TDEG);
     k_translate_scatter<<<g, 256, 0, L.s>>>(L.P, L.T);
     ++*L.nlaunch;
@@ -344,6 +335,7 @@ void launch_graph(const Launch& L) {
     ++*L.nlaunch;
     k_flip_count<<<g, 256, 0, L.s>>>(L.P, L.T);
     ++*L.nlaunch;
+    launch_plan(L, 0, ends_bit(SCAN_FLIPS) | ends_bit(SCAN_FLIPS_A));
     launch_scan(L, SCAN_FLIPS);
     launch_scan(L, SCAN_FLIPS_A);
     k_flip_write<<<g, 256, 0, L.s>>>(L.P, L.T);

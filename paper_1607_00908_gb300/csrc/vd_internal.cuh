@@ -19,6 +19,7 @@ namespace vd {
 // ---------------------------------------------------------------------------
 constexpr int TW = 64;          // labelling tile width  (sites)
 constexpr int TH = 32;          // labelling tile height (sites)
+constexpr int TRUNS = TH * 32;  // run slots per labelling tile (at most 32 runs per 64-site row)
 constexpr int TSITES = TW * TH; // 2048
 constexpr int TTHREADS = 256;   // 8 threads per tile row, 8 sites each
 constexpr int BORDER = 2 * (TW + TH);   // left col, right col, top row, bottom row
@@ -106,9 +107,8 @@ struct Globals {
     int n_pieces;
     int n_wide;
     int err;
-    unsigned scan_epoch;     // bumped before every scan; tags look-back flags
-    int scan_ticket;         // dynamic tile index of the running scan
-    int pad[3];
+    unsigned scan_step;      // bumped once per step; with the scan kind it tags look-back flags
+    int scan_ticket[8];      // dynamic tile index of each scan kind (reset once per step)
 };
 
 // ---------------------------------------------------------------------------
@@ -119,10 +119,12 @@ struct Pools {
     InstState* st;
     Globals* g;
     // sites
-    int* labels[2];
     int* owners;
     // bitmask words
-    unsigned* fgbits;
+    unsigned* fgbits[2];     // foreground bits of the frames in slot 0 / 1
+    int* rp;                 // piece id of every run of this step's frames (tile run slots)
+    int* rl[2];              // bubble label of every run of the frames in slot 0 / 1
+    int* lab_out;            // per-site labels of one instance, expanded on request
     unsigned* rootbits;
     int* rankpre;            // global exclusive prefix per word (this step)
     // labelling tiles
@@ -137,7 +139,7 @@ struct Pools {
     int* p_su;               // sum of (x - x_q) over the piece
     int* p_sv;               // sum of (y - y_q)
     int* p_parent;           // union-find over pieces (root = piece with smallest q)
-    int* p_comp;             // bubble id (valid after ranking)
+    int* p_comp;             // bubble id (roots after ranking, every piece after k_comp_final)
     long long* p_accn;
     long long* p_accx;
     long long* p_accy;
@@ -401,7 +403,7 @@ struct Launch {
 
 void launch_ccl_tiles(const Launch& L);    // threshold + tile union-find (pass A)
 void launch_ccl_rest(const Launch& L);     // border merge, ranks, centroids, bucket grid
-void launch_labels(const Launch& L);       // per-site labels + overlap histogram
+void launch_labels(const Launch& L);       // run labels + overlap histogram
 void launch_voronoi(const Launch& L);      // exact owner of every site
 void launch_links(const Launch& L);        // per-tile links from the owners
 void launch_merge_lists(const Launch& L);  // appended links/pairs -> hash tables
@@ -409,6 +411,7 @@ void launch_graph(const Launch& L);        // CSR, match, translation, flips
 void launch_begin(const Launch& L);        // per-step counters and field pointers
 void launch_finish(const Launch& L);       // swap frames
 void launch_edge_keys(cudaStream_t s, const Pools& P, int inst, int slot, unsigned long long* out);
+void launch_expand_labels(cudaStream_t s, const Pools& P, int inst, int slot, int* out, long long n);
 
 // generic decoupled look-back scan over a virtual concatenation (vd_scan.cu)
 constexpr int SCAN_THREADS = 256;
@@ -422,7 +425,12 @@ enum ScanKind : int {
     SCAN_FLIPS = 4,      // breaking counts per row
     SCAN_FLIPS_A = 5,    // arising counts per row
 };
-void launch_scan(const Launch& L, ScanKind kind);   // k_plan + k_scan
-void launch_plan(const Launch& L, int with_comp);   // recompute prefixes (and bucket grids)
+// the end value of the offset array of scan `kind`, written by k_plan
+constexpr int ENDS_NONE = 0;
+__host__ __device__ constexpr int ends_bit(ScanKind kind) { return 1 << kind; }
+void launch_scan(const Launch& L, ScanKind kind);   // k_scan over the current plan
+// recompute prefixes (and bucket grids when with_comp) and the end values of
+// the offset arrays whose bits are set in ends
+void launch_plan(const Launch& L, int with_comp, int ends);
 
 }  // namespace vd

@@ -3,7 +3,8 @@
 // A "virtual concatenation" lists, for every instance active in the step, a
 // segment of items (bitmask words, buckets, bubbles). k_plan recomputes the
 // segment prefixes from the per-instance counters produced by the previous
-// kernel; k_scan then runs one single-pass scan (decoupled look-back, tiles
+// kernels (and the end values of the offset arrays scanned next); k_scan then
+// runs one single-pass scan (decoupled look-back, tiles
 // claimed in order through an atomic ticket) over the whole concatenation and
 // writes each item's exclusive prefix *within its own instance*: the global
 // prefix minus the sum of the totals of the earlier instances, which the
@@ -17,7 +18,7 @@ namespace vd {
 // ---------------------------------------------------------------------------
 constexpr int PLAN_THREADS = 256;
 
-__global__ __launch_bounds__(PLAN_THREADS) void k_plan(Pools P, StepTable T, int with_comp) {
+__global__ __launch_bounds__(PLAN_THREADS) void k_plan(Pools P, StepTable T, int with_comp, int ends) {
     // one block: thread per instance, block scans for the prefixes
     __shared__ long long s_v[NPRE][PLAN_THREADS];
     __shared__ long long s_carry[NPRE];
@@ -70,6 +71,13 @@ __global__ __launch_bounds__(PLAN_THREADS) void k_plan(Pools P, StepTable T, int
             v[PRE_FA] = S.n_arise;
             v[PRE_EA] = S.n_eapp < D.edge_cap ? S.n_eapp : D.edge_cap;
             v[PRE_OA] = S.n_oapp < D.ovl_cap ? S.n_oapp : D.ovl_cap;
+            // end values of the offset arrays (off[size] = total) of the scans that follow
+            const int now = S.slot ^ 1;
+            if (ends & ends_bit(SCAN_BUCKETS)) P.boff[D.bucket_off + (long long)S.nbx * S.nby] = S.K;
+            if (ends & ends_bit(SCAN_DEG)) P.rowoff[now][D.comp_off + S.K] = S.n_edge_list;
+            if (ends & ends_bit(SCAN_TDEG)) P.trowoff[D.comp_off + S.K] = S.n_tedges;
+            if (ends & ends_bit(SCAN_FLIPS)) P.foff[D.comp_off + S.K] = S.n_break;
+            if (ends & ends_bit(SCAN_FLIPS_A)) P.foff_a[D.comp_off + S.K] = S.n_arise;
         }
         for (int k = 0; k < NPRE; ++k) s_v[k][tid] = v[k];
         __syncthreads();
@@ -88,30 +96,6 @@ __global__ __launch_bounds__(PLAN_THREADS) void k_plan(Pools P, StepTable T, int
         __syncthreads();
     }
     if (tid < NPRE) pre_arr(T, tid)[n] = s_carry[tid];
-    if (tid == 0) {
-        // fresh scan epoch and ticket for the scan that follows
-        P.g->scan_epoch = (P.g->scan_epoch + 1) & 0x3FFFFFFFu;
-        if (P.g->scan_epoch == 0) P.g->scan_epoch = 1;
-        P.g->scan_ticket = 0;
-    }
-}
-
-// end values of offset arrays (off[size] = total) for each instance
-__global__ void k_plan_ends(Pools P, StepTable T, int kind) {
-    for (int a = threadIdx.x; a < T.n_act; a += blockDim.x) {
-        const int inst = T.act[a];
-        const InstState& S = P.st[inst];
-        const InstDesc& D = P.desc[inst];
-        const int now = S.slot ^ 1;
-        switch (kind) {
-            case SCAN_BUCKETS: P.boff[D.bucket_off + (long long)S.nbx * S.nby] = S.K; break;
-            case SCAN_DEG: P.rowoff[now][D.comp_off + S.K] = S.n_edge_list; break;
-            case SCAN_TDEG: P.trowoff[D.comp_off + S.K] = S.n_tedges; break;
-            case SCAN_FLIPS: P.foff[D.comp_off + S.K] = S.n_break; break;
-            case SCAN_FLIPS_A: P.foff_a[D.comp_off + S.K] = S.n_arise; break;
-            default: break;
-        }
-    }
 }
 
 // ---------------------------------------------------------------------------
@@ -175,13 +159,14 @@ __global__ __launch_bounds__(SCAN_THREADS) void k_scan(Pools P, StepTable T, int
     const long long* seg = sel.seg < 0 ? T.word_pre : pre_arr(T, sel.seg);
     const long long* base = pre_arr(T, sel.base);
     const long long total = seg[n];
-    const unsigned epoch = *(volatile unsigned*)&P.g->scan_epoch;
+    // every scan of a step has its own tag (step count, kind) and ticket counter
+    const unsigned epoch = ((*(volatile unsigned*)&P.g->scan_step << 3) | (unsigned)kind) & 0x3FFFFFFFu;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     // blocks beyond the number of tiles never take a ticket
     if ((long long)blockIdx.x * SCAN_TILE >= total) return;
 
     for (;;) {
-        if (threadIdx.x == 0) s_tile = atomicAdd(&P.g->scan_ticket, 1);
+        if (threadIdx.x == 0) s_tile = atomicAdd(&P.g->scan_ticket[kind], 1);
         __syncthreads();
         const long long tile = s_tile;
         const long long start = tile * SCAN_TILE;
@@ -290,18 +275,12 @@ __global__ __launch_bounds__(SCAN_THREADS) void k_scan(Pools P, StepTable T, int
     }
 }
 
-void launch_plan(const Launch& L, int with_comp) {
-    k_plan<<<1, PLAN_THREADS, 0, L.s>>>(L.P, L.T, with_comp);
+void launch_plan(const Launch& L, int with_comp, int ends) {
+    k_plan<<<1, PLAN_THREADS, 0, L.s>>>(L.P, L.T, with_comp, ends);
     ++*L.nlaunch;
 }
 
 void launch_scan(const Launch& L, ScanKind kind) {
-    k_plan<<<1, PLAN_THREADS, 0, L.s>>>(L.P, L.T, 0);
-    ++*L.nlaunch;
-    if (kind != SCAN_ROOTBITS) {
-        k_plan_ends<<<1, 256, 0, L.s>>>(L.P, L.T, (int)kind);
-        ++*L.nlaunch;
-    }
     int grid = L.grid_items;
     k_scan<<<grid, SCAN_THREADS, 0, L.s>>>(L.P, L.T, (int)kind);
     ++*L.nlaunch;

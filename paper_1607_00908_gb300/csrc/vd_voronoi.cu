@@ -572,7 +572,7 @@ __global__ void k_merge_lists(Pools P, StepTable T) {
 }
 
 void launch_merge_lists(const Launch& L) {
-    launch_plan(L, 0);
+    launch_plan(L, 0, ENDS_NONE);
     k_merge_lists<<<L.grid_items, 256, 0, L.s>>>(L.P, L.T);
     ++*L.nlaunch;
 }
