@@ -199,14 +199,14 @@ def run_reference(args, world, rank):
 def stage_bytes(sequence: bool):
     """Algorithmic bytes per site of the stages that touch every site.
 
-    stage 0 threshold + tile union-find: field read 4, foreground bit write and
-            read 1/8 + 1/8
+    stage 0 threshold + tile union-find (one kernel): field read 4,
+            foreground bit write 1/8
     stage 2 run labels + overlaps: foreground bits of the frame and of its
             past frame, 1/8 + 1/8 (run tables are per run, not per site)
     stage 3 Voronoi owners: owner write 4
     stage 4 links: owner read 4
     """
-    return {0: 4.25, 2: 0.25, 3: 4.0, 4: 4.0}
+    return {0: 4.125, 2: 0.25, 3: 4.0, 4: 4.0}
 
 
 def roofline_of(stage_ms, names, launches_per_stage, sites_per_launch, sequence, peak, peak_kind):

@@ -4,8 +4,8 @@
 // that also builds the past/now overlap histogram (Section 3.2.3).
 //
 // Labelling works on 64 x 32 tiles. Pass A reads the field once (vector
-// loads), stores the foreground bits (1 bit per site), runs a union-find in
-// shared memory and emits one "piece" per tile-local component with its size
+// loads, one tile row per lane), stores the foreground bits (1 bit per site),
+// runs a union-find in shared memory and emits one "piece" per tile-local component with its size
 // and coordinate sums relative to its first site, plus the piece ids along the
 // four tile borders. Pieces are then merged across tile borders (periodic) by
 // a global union-find whose root is the piece with the smallest first site, so
@@ -86,12 +86,28 @@ __device__ __forceinline__ int rfind(volatile int* p, int x) {
     return x;
 }
 
+// root of run x, splitting the path on the way (each visited run is pointed at
+// its grandparent). Used only while unions run: concurrent splits and unions
+// store ancestors of non-roots, so the sets stay intact. The flatten that
+// follows must not run concurrently with splits, which could replace a
+// flattened root by an intermediate ancestor.
+__device__ __forceinline__ int rfind_split(volatile int* p, int x) {
+    int y = p[SW(x)];
+    while (y != x) {
+        const int z = p[SW(y)];
+        if (z != y) p[SW(x)] = z;
+        x = y;
+        y = z;
+    }
+    return x;
+}
+
 // lock-free union by smaller run id on the swizzled parent array
 __device__ __forceinline__ void runion(int* p, int a, int b) {
     bool done;
     do {
-        a = rfind(p, a);
-        b = rfind(p, b);
+        a = rfind_split(p, a);
+        b = rfind_split(p, b);
         if (a < b) {
             const int old = atomicMin(&p[SW(b)], a);
             done = (old == b);
@@ -111,10 +127,17 @@ struct UfSmem {                  // one warp's tile: row masks and union-find ov
     int par[RUNS];               // swizzled: parent of run id k at par[SW(k)]
     unsigned char col[RUNS];     // swizzled: start column of each run
 };
-struct TileSmem : UfSmem {
-    int aux[RUNS];     // per root run: (n << 16) | sum(y - y_root), then piece id
-    int su[RUNS];      // per root run: sum(x - x_root)
-};
+// piece id of run `id` after pass A has stored -2 - (piece id) in the parent
+// slot of every root; *root = the run id of its root
+__device__ __forceinline__ int run_piece(const UfSmem& T, int id, int* root) {
+    const int v = T.par[SW(id)];
+    if (v < 0) {
+        *root = id;
+        return -2 - v;
+    }
+    *root = v;
+    return -2 - T.par[SW(v)];
+}
 
 // union-find over runs; lane r owns row r; m = this lane's row mask, mu = row r-1
 __device__ void warp_runs_uf(UfSmem& T, unsigned long long m) {
@@ -185,54 +208,44 @@ __device__ __forceinline__ bool is_fg(float v, float thr, int pol) {
     return pol > 0 ? (v > thr) : (v < thr);
 }
 
-constexpr int CCL_WARPS = 2;    // tiles per block in pass A
+constexpr int CCL_WARPS = 4;    // tiles per block in pass A
 
-// ---------------------------------------------------------------------------
-// Threshold (Section 3.1): one 32-bit foreground word per thread, streamed
-// from the field with 16-byte loads; bit i of word w of row y is site
-// (32w + i, y). Items are the words of all active instances.
-// ---------------------------------------------------------------------------
-__global__ __launch_bounds__(256) void k_threshold(Pools P, StepTable T) {
-    const long long total = T.word_pre[T.n_act];
-    for (long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x; g < total;
-         g += (long long)gridDim.x * blockDim.x) {
-        const int a = seg_of(T.word_pre, T.n_act, g);
-        const int inst = T.act[a];
-        const InstDesc& D = P.desc[inst];
-        const InstState& S = P.st[inst];
-        const long long w = g - T.word_pre[a];
-        const int y = (int)(w / D.wpr), wx = (int)(w - (long long)y * D.wpr);
-        const int x = wx * 32;
-        const float* f = S.field + (long long)y * S.pitch + x;
-        const float thr = D.thr;
-        const int pol = D.pol;
-        unsigned bits = 0;
-        if (x + 32 <= D.Lx && ((reinterpret_cast<uintptr_t>(f) & 15u) == 0)) {
-            const float4* f4 = reinterpret_cast<const float4*>(f);
+// Threshold (Section 3.1) of one 64-site tile row, read straight from the
+// field: 16-byte streaming loads when the row is aligned and complete, else
+// scalar loads. Bit i of the mask is site (x0 + i, y); bits past Lx are 0.
+__device__ __forceinline__ unsigned long long threshold_row(const float* f, int n, float thr, int pol) {
+    unsigned long long m = 0;
+    if (n == TW && ((reinterpret_cast<uintptr_t>(f) & 15u) == 0)) {
+        const float4* f4 = reinterpret_cast<const float4*>(f);
 #pragma unroll
-            for (int i = 0; i < 8; ++i) {
-                const float4 v = __ldcs(f4 + i);
-                bits |= ((unsigned)is_fg(v.x, thr, pol) | ((unsigned)is_fg(v.y, thr, pol) << 1) |
-                         ((unsigned)is_fg(v.z, thr, pol) << 2) | ((unsigned)is_fg(v.w, thr, pol) << 3)) << (4 * i);
-            }
-        } else {
-            const int n = min(32, D.Lx - x);
-            for (int i = 0; i < n; ++i)
-                if (is_fg(__ldcs(f + i), thr, pol)) bits |= 1u << i;
+        for (int h = 0; h < 2; ++h) {   // two halves of 8 loads in flight
+            float4 v[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) v[i] = __ldcs(f4 + 8 * h + i);
+            unsigned bits = 0;
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+                bits |= ((unsigned)is_fg(v[i].x, thr, pol) | ((unsigned)is_fg(v[i].y, thr, pol) << 1) |
+                         ((unsigned)is_fg(v[i].z, thr, pol) << 2) | ((unsigned)is_fg(v[i].w, thr, pol) << 3))
+                        << (4 * i);
+            m |= (unsigned long long)bits << (32 * h);
         }
-        P.fgbits[S.slot ^ 1][D.word_off + w] = bits;
+    } else {
+        for (int i = 0; i < n; ++i)
+            if (is_fg(__ldcs(f + i), thr, pol)) m |= 1ull << i;
     }
+    return m;
 }
 
 // ---------------------------------------------------------------------------
 // Pass A: union-find over runs + pieces + borders (one warp per tile)
 // ---------------------------------------------------------------------------
-__global__ __launch_bounds__(32 * CCL_WARPS) void k_ccl_tiles(Pools P, StepTable T) {
-    __shared__ TileSmem s_tile[CCL_WARPS];
+__global__ __launch_bounds__(32 * CCL_WARPS, 8) void k_ccl_tiles(Pools P, StepTable T) {
+    __shared__ UfSmem s_tile[CCL_WARPS];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int b = blockIdx.x * CCL_WARPS + w;
     if (b >= T.tileA_pre[T.n_act]) return;
-    TileSmem& TS = s_tile[w];
+    UfSmem& TS = s_tile[w];
     const int a = seg_of_int(T.tileA_pre, T.n_act, b);
     const int inst = T.act[a];
     const InstDesc& D = P.desc[inst];
@@ -242,39 +255,28 @@ __global__ __launch_bounds__(32 * CCL_WARPS) void k_ccl_tiles(Pools P, StepTable
     const int x0 = tx * TW, y0 = ty * TH;
     const int Lx = D.Lx, Ly = D.Ly;
 
-    // 1. foreground masks of the tile rows (written by k_threshold; L2-resident)
-    const unsigned long long my_m = load_row_mask(P.fgbits[S.slot ^ 1], D, x0, y0);
+    // 1. threshold: lane r reads tile row r of the field and stores its
+    //    foreground words (kept for the run-label pass and the next frame)
+    unsigned long long my_m = 0;
+    {
+        const int y = y0 + lane;
+        if (y < Ly) {
+            const int n = min(TW, Lx - x0);
+            my_m = threshold_row(S.field + (long long)y * S.pitch + x0, n, D.thr, D.pol);
+            unsigned* row = P.fgbits[S.slot ^ 1] + D.word_off + (long long)y * D.wpr + (x0 >> 5);
+            row[0] = (unsigned)my_m;
+            if (n > 32) row[1] = (unsigned)(my_m >> 32);
+        }
+    }
     TS.m[lane] = my_m;
 
     // 2. union-find over runs
     warp_runs_uf(TS, my_m);
 
-    // 3. sums per root run
+    // 3. roots in raster order -> piece ids; a root's parent slot then holds
+    //    -2 - (its piece id), so every run reaches its piece in two steps
     const unsigned long long S0 = run_starts(my_m);
     const int nr = __popcll(S0);
-    for (int j = 0; j < nr; ++j) {
-        TS.aux[SW(lane * 32 + j)] = 0;
-        TS.su[SW(lane * 32 + j)] = 0;
-    }
-    __syncwarp();
-    {
-        unsigned long long q = S0;
-        int j = 0;
-        while (q) {
-            const int c = __ffsll(q) - 1;
-            q &= q - 1;
-            const int len = run_length(my_m, c);
-            const int root = TS.par[SW(lane * 32 + j)];
-            const int rr = root >> 5;
-            const int cr = TS.col[SW(root)];
-            atomicAdd(&TS.aux[SW(root)], (len << 16) + len * (lane - rr));
-            atomicAdd(&TS.su[SW(root)], len * (c - cr) + (len * (len - 1)) / 2);
-            ++j;
-        }
-    }
-    __syncwarp();
-
-    // 4. roots in raster order -> piece ids
     int rbase, m_tot;
     const unsigned R = warp_roots(TS, my_m, &rbase, &m_tot);
     int pbase = 0;
@@ -299,26 +301,52 @@ __global__ __launch_bounds__(32 * CCL_WARPS) void k_ccl_tiles(Pools P, StepTable
             int pid = -1;
             if (pbase >= 0) {
                 pid = pbase + k;
-                const int nsv = TS.aux[id];
                 P.p_q[pid] = (y0 + lane) * Lx + x0 + TS.col[id];
                 P.p_inst[pid] = inst;
-                P.p_n[pid] = nsv >> 16;
-                P.p_sv[pid] = nsv & 0xFFFF;
-                P.p_su[pid] = TS.su[id];
+                P.p_n[pid] = 0;
+                P.p_sv[pid] = 0;
+                P.p_su[pid] = 0;
                 P.p_parent[pid] = pid;
                 P.p_accn[pid] = 0;
                 P.p_accx[pid] = 0;
                 P.p_accy[pid] = 0;
             }
             ++k;
-            TS.aux[id] = pid;   // root slot now holds the piece id
+            TS.par[id] = -2 - pid;
         }
     }
     __syncwarp();
-    // piece id of every run of this row (resolved to bubble labels later)
+
+    // 4. per run: its piece id (kept for the run-label pass) and its share of
+    //    the piece's size and coordinate sums relative to the piece's first
+    //    site; runs of one piece are merged across the warp, then one atomic
+    //    add per group
     {
         int* rp = P.rp + (long long)(D.tile_off + t) * RUNS + lane * 32;
-        for (int j = 0; j < nr; ++j) rp[j] = TS.aux[SW(TS.par[SW(lane * 32 + j)])];
+        const int maxnr = __reduce_max_sync(0xffffffffu, nr);
+        unsigned long long q = S0;
+        for (int j = 0; j < maxnr; ++j) {
+            int pid = -1, len = 0, sv = 0, su = 0;
+            if (j < nr) {
+                const int c = __ffsll(q) - 1;
+                q &= q - 1;
+                len = run_length(my_m, c);
+                int root;
+                pid = run_piece(TS, lane * 32 + j, &root);
+                sv = len * (lane - (root >> 5));
+                su = len * (c - TS.col[SW(root)]) + (len * (len - 1)) / 2;
+                rp[j] = pid;
+            }
+            const unsigned grp = __match_any_sync(0xffffffffu, pid);
+            const int gn = __reduce_add_sync(grp, len);
+            const int gsv = __reduce_add_sync(grp, sv);
+            const int gsu = __reduce_add_sync(grp, su);
+            if (pid >= 0 && lane == __ffs(grp) - 1) {
+                atomicAdd(&P.p_n[pid], gn);
+                atomicAdd(&P.p_sv[pid], gsv);
+                atomicAdd(&P.p_su[pid], gsu);
+            }
+        }
     }
 
     // 5. borders: [0,TH) left col, [TH,2TH) right col, [2TH,2TH+TW) top row, [.., +TW) bottom row
@@ -333,7 +361,10 @@ __global__ __launch_bounds__(32 * CCL_WARPS) void k_ccl_tiles(Pools P, StepTable
         int v = -1;
         if (lx < ncols && ly < nrows) {
             const unsigned long long m = TS.m[ly];
-            if ((m >> lx) & 1ull) v = TS.aux[SW(TS.par[SW(ly * 32 + run_index(run_starts(m), lx))])];
+            if ((m >> lx) & 1ull) {
+                int root;
+                v = run_piece(TS, ly * 32 + run_index(run_starts(m), lx), &root);
+            }
         }
         bd[k] = v;
     }
@@ -682,12 +713,6 @@ void launch_expand_labels(cudaStream_t s, const Pools& P, int inst, int slot, in
 }
 
 void launch_ccl_tiles(const Launch& L) {
-    {
-        const long long need = (L.total_words + 255) / 256;
-        const int grid = (int)(need < 8LL * L.grid_items ? need : 8LL * L.grid_items);
-        k_threshold<<<grid > 0 ? grid : 1, 256, 0, L.s>>>(L.P, L.T);
-        ++*L.nlaunch;
-    }
     k_ccl_tiles<<<(L.total_tilesA + CCL_WARPS - 1) / CCL_WARPS, 32 * CCL_WARPS, 0, L.s>>>(L.P, L.T);
     ++*L.nlaunch;
 }
