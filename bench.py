@@ -37,14 +37,17 @@ from paper_1607_00908_gb300 import inputs  # noqa: E402
 METRIC = "Gsites/s full detect pipeline"
 UNIT = "Gsites/s"
 
-# The pipeline's algorithmic traffic per site: field read 4, past label read
-# 4, label write 4, owner write 4.
-PIPELINE_BYTES_PER_SITE = 16.0
+# The pipeline's per-site traffic floor: the field is read once (4) and the
+# Voronoi owners, the one per-site result kept in HBM, are written once (4);
+# labels are kept per run, not per site.
+PIPELINE_BYTES_PER_SITE = 8.0
 
-# Measured DRAM bytes (read + write) per site of a stage, from one ncu
-# capture of the current kernels (profiles/voronoi_links_c2.txt); scaled to
-# the bench launch for roofline.traffic. Stages not captured report null.
-TRAFFIC_BYTES_PER_SITE = {}
+# Measured DRAM bytes (read + write) per site of a stage's kernels, from one
+# ncu capture of the current kernels on this workload
+# (profiles/launches_c1_sequence.txt); scaled to the bench launch for
+# roofline.traffic. A stage not captured, or whose kernels changed since the
+# capture, reports null.
+TRAFFIC_BYTES_PER_SITE = {0: 5.099, 2: 2.847, 3: 3.136, 4: 4.327}
 
 
 def workload(name: str, n_frames: int | None):
@@ -274,7 +277,7 @@ def run_ours(args, world, rank, local):
     stage_ms, names, _, _ = seq.timing()
     seq.set_timing(False)
     roofline = roofline_of(stage_ms, names, args.steps, sites_per_step, n > 1, peak, peak_kind)
-    roofline["pipeline_frac_16B_per_site"] = value * PIPELINE_BYTES_PER_SITE / peak
+    roofline["pipeline_frac_8B_per_site"] = value * PIPELINE_BYTES_PER_SITE / peak
 
     # ---- end to end through the C ABI with host buffers ----
     host = [torch.from_numpy(F).pin_memory() for F in frames]
