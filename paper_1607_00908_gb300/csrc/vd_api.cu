@@ -172,6 +172,7 @@ Launch make_launch(vd_batch* b, const StepTables& T) {
     L.T.merge_pre = T.d_merge;
     L.T.pre = T.d_pre;
     L.grid_items = b->grid_items;
+    L.grid_wide = 4 * b->grid_items;
     L.total_tilesA = T.total_tilesA;
     L.total_tilesV = T.total_tilesV;
     L.total_merge = T.total_merge;

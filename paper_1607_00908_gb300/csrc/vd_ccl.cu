@@ -394,28 +394,39 @@ __device__ __forceinline__ void punion(const Pools& P, int a, int b) {
     }
 }
 
+// one thread per border position (right edge, then bottom edge of every
+// tile); a position whose piece pair equals the previous position's on the
+// same edge adds nothing and is skipped
 __global__ void k_ccl_merge(Pools P, StepTable T, int total) {
+    __shared__ int s_pre[SEG_CACHE];
+    const int* pre = seg_table(T.merge_pre, T.n_act, s_pre);
     const int g = blockIdx.x * blockDim.x + threadIdx.x;
-    if (g >= total) return;
-    const int a = seg_of_int(T.merge_pre, T.n_act, g);
-    const int inst = T.act[a];
-    const InstDesc& D = P.desc[inst];
-    const int loc = g - T.merge_pre[a];
-    const int t = loc / (TW + TH), j = loc % (TW + TH);
-    const int tx = t % D.ntx, ty = t / D.ntx;
-    const int* bd = P.border + D.border_off;
-    int pa, pb;
-    if (j < TH) {
-        const int tn = ty * D.ntx + (tx + 1) % D.ntx;
-        pa = bd[(long long)t * BORDER + TH + j];
-        pb = bd[(long long)tn * BORDER + j];
-    } else {
-        const int k = j - TH;
-        const int tn = ((ty + 1) % D.nty) * D.ntx + tx;
-        pa = bd[(long long)t * BORDER + 2 * TH + TW + k];
-        pb = bd[(long long)tn * BORDER + 2 * TH + k];
+    int pa = -1, pb = -1, edge = -1;   // edge: (tile, side) of this position
+    if (g < total) {
+        const int a = seg_of_int(pre, T.n_act, g);
+        const int inst = T.act[a];
+        const InstDesc& D = P.desc[inst];
+        const int loc = g - pre[a];
+        const int t = loc / (TW + TH), j = loc % (TW + TH);
+        const int tx = t % D.ntx, ty = t / D.ntx;
+        const int* bd = P.border + D.border_off;
+        if (j < TH) {
+            const int tn = ty * D.ntx + (tx + 1) % D.ntx;
+            pa = bd[(long long)t * BORDER + TH + j];
+            pb = bd[(long long)tn * BORDER + j];
+        } else {
+            const int k = j - TH;
+            const int tn = ((ty + 1) % D.nty) * D.ntx + tx;
+            pa = bd[(long long)t * BORDER + 2 * TH + TW + k];
+            pb = bd[(long long)tn * BORDER + 2 * TH + k];
+        }
+        edge = (g - j) * 2 + (j < TH ? 0 : 1);
     }
-    if (pa >= 0 && pb >= 0) punion(P, pa, pb);
+    const int lane = threadIdx.x & 31;
+    const int ppa = __shfl_up_sync(0xffffffffu, pa, 1), ppb = __shfl_up_sync(0xffffffffu, pb, 1);
+    const int pedge = __shfl_up_sync(0xffffffffu, edge, 1);
+    const bool repeat = lane > 0 && pedge == edge && ppa == pa && ppb == pb;
+    if (pa >= 0 && pb >= 0 && !repeat) punion(P, pa, pb);
 }
 
 // root of each piece; roots are counted per instance and marked in the root bitmap
@@ -618,11 +629,18 @@ __global__ __launch_bounds__(32 * LBL_WARPS) void k_run_labels(Pools P, StepTabl
     const unsigned long long m = load_row_mask(P.fgbits[now], D, x0, y0);
     const unsigned long long Sn = run_starts(m);
     const int nr = __popcll(Sn);
-    for (int j = 0; j < nr; ++j) {
-        const int pid = P.rp[rbase + j];
-        const int l = pid >= 0 ? P.p_comp[pid] : -1;
-        P.rl[now][rbase + j] = l;
-        lab[SW(lane * 32 + j)] = l;
+    for (int j0 = 0; j0 < nr; j0 += 4) {   // four runs' loads in flight at once
+        int pid[4], l[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) pid[k] = j0 + k < nr ? P.rp[rbase + j0 + k] : -1;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) l[k] = pid[k] >= 0 ? P.p_comp[pid[k]] : -1;
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            if (j0 + k < nr) {
+                P.rl[now][rbase + j0 + k] = l[k];
+                lab[SW(lane * 32 + j0 + k)] = l[k];
+            }
     }
     if (!S.has_prev) return;   // warp-uniform
 
@@ -641,26 +659,35 @@ __global__ __launch_bounds__(32 * LBL_WARPS) void k_run_labels(Pools P, StepTabl
     const unsigned long long A = m & mp;
     unsigned long long As = run_starts(A);
     const int nA = __reduce_max_sync(0xffffffffu, __popcll(As));
-    for (int i = 0; i < nA; ++i) {   // all lanes: the set insertion is warp-wide
-        unsigned long long key = EMPTY_KEY;
-        unsigned len = 0;
-        if (As) {
-            const int c = __ffsll(As) - 1;
-            As &= As - 1;
-            len = run_length(A, c);
-            const int ln = lab[SW(lane * 32 + run_index(Sn, c))];
-            const int jp = run_index(Sp, c);
-            int lp;
-            if (same) {
-                const int pid = P.rp[pbase + jp];
-                lp = pid >= 0 ? P.p_comp[pid] : -1;
-            } else {
-                lp = P.rl[pb][pbase + jp];
+    for (int i0 = 0; i0 < nA; i0 += 4) {   // all lanes: the set insertion is warp-wide
+        // four overlap runs at a time: their past-label loads are in flight together
+        unsigned len[4];
+        int ln[4], lp[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            len[k] = 0;
+            ln[k] = -1;
+            lp[k] = -1;
+            if (As) {
+                const int c = __ffsll(As) - 1;
+                As &= As - 1;
+                len[k] = run_length(A, c);
+                ln[k] = lab[SW(lane * 32 + run_index(Sn, c))];
+                const int jp = run_index(Sp, c);
+                lp[k] = same ? P.rp[pbase + jp] : P.rl[pb][pbase + jp];
             }
-            if (ln >= 0 && lp >= 0) key = ((unsigned long long)(unsigned)lp << 32) | (unsigned)ln;
         }
-        unsigned csum = 0;
-        if (!warp_set_add(skey, scnt, WSET, key, len, &csum)) ovl_global_insert(P, D, inst, key, csum);
+        if (same) {   // the past frame's runs hold piece ids: one more step to labels
+#pragma unroll
+            for (int k = 0; k < 4; ++k) lp[k] = lp[k] >= 0 ? P.p_comp[lp[k]] : -1;
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const unsigned long long key =
+                (ln[k] >= 0 && lp[k] >= 0) ? (((unsigned long long)(unsigned)lp[k] << 32) | (unsigned)ln[k]) : EMPTY_KEY;
+            unsigned csum = 0;
+            if (!warp_set_add(skey, scnt, WSET, key, len[k], &csum)) ovl_global_insert(P, D, inst, key, csum);
+        }
     }
     __syncwarp();
     // append the tile's (past, now, count) triples (one reservation per round);
@@ -722,18 +749,18 @@ void launch_ccl_rest(const Launch& L) {
         k_ccl_merge<<<(L.total_merge + 255) / 256, 256, 0, L.s>>>(L.P, L.T, L.total_merge);
         ++*L.nlaunch;
     }
-    k_ccl_flatten<<<L.grid_items, 256, 0, L.s>>>(L.P);
+    k_ccl_flatten<<<L.grid_wide, 256, 0, L.s>>>(L.P);
     ++*L.nlaunch;
     launch_plan(L, 1, ends_bit(SCAN_BUCKETS));
     launch_scan(L, SCAN_ROOTBITS);
-    k_comp_accum<<<L.grid_items, 256, 0, L.s>>>(L.P);
+    k_comp_accum<<<L.grid_wide, 256, 0, L.s>>>(L.P);
     ++*L.nlaunch;
     k_comp_wide<<<L.grid_items, 32 * WIDE_WARPS, 0, L.s>>>(L.P);
     ++*L.nlaunch;
-    k_comp_final<<<L.grid_items, 256, 0, L.s>>>(L.P);
+    k_comp_final<<<L.grid_wide, 256, 0, L.s>>>(L.P);
     ++*L.nlaunch;
     launch_scan(L, SCAN_BUCKETS);
-    k_bucket_scatter<<<L.grid_items, 256, 0, L.s>>>(L.P);
+    k_bucket_scatter<<<L.grid_wide, 256, 0, L.s>>>(L.P);
     ++*L.nlaunch;
 }
 

@@ -13,9 +13,12 @@
 
 namespace vd {
 
+// every item of the virtual concatenation `which` (all threads of the block
+// must call this: the segment table is copied to shared memory first)
 template <class F>
 __device__ __forceinline__ void for_items(const StepTable& T, int which, F f) {
-    const long long* pre = pre_arr(T, which);
+    __shared__ long long s_pre[SEG_CACHE];
+    const long long* pre = seg_table(pre_arr(T, which), T.n_act, s_pre);
     const long long total = pre[T.n_act];
     for (long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x; g < total;
          g += (long long)gridDim.x * blockDim.x) {
@@ -314,7 +317,7 @@ __global__ void k_flip_write(Pools P, StepTable T) {
 }
 
 void launch_graph(const Launch& L) {
-    const int g = L.grid_items;
+    const int g = L.grid_wide;
     launch_plan(L, 0, ends_bit(SCAN_DEG));
     launch_scan(L, SCAN_DEG);
     k_csr_scatter<<<g, 256, 0, L.s>>>(L.P, L.T);

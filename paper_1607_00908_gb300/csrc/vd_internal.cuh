@@ -255,6 +255,23 @@ __device__ __forceinline__ int seg_of(const long long* pre, int n_act, long long
 __device__ __forceinline__ int seg_of_int(const int* pre, int n_act, int g) {
     return upper_bound_int(pre, n_act + 1, g) - 1;
 }
+__device__ __forceinline__ int seg_of_any(const long long* pre, int n_act, long long g) { return seg_of(pre, n_act, g); }
+__device__ __forceinline__ int seg_of_any(const int* pre, int n_act, long long g) {
+    return seg_of_int(pre, n_act, (int)g);
+}
+
+// A block's copy of a segment prefix table (n_act + 1 entries) in shared
+// memory, loaded in one round, so that item -> instance searches do not chain
+// dependent global loads; tables longer than SEG_CACHE entries stay global.
+// All threads of the block must call it (it synchronises).
+constexpr int SEG_CACHE = 512;
+template <class PreT>
+__device__ __forceinline__ const PreT* seg_table(const PreT* pre, int n_act, PreT* cache) {
+    if (n_act + 1 > SEG_CACHE) return pre;
+    for (int i = threadIdx.x; i <= n_act; i += blockDim.x) cache[i] = pre[i];
+    __syncthreads();
+    return cache;
+}
 
 __device__ __forceinline__ unsigned long long hash64(unsigned long long k) {
     k ^= k >> 33;
@@ -399,6 +416,7 @@ struct Launch {
     int grid_items;      // fixed grid for grid-stride item loops
     int total_tilesA, total_tilesV, total_merge;
     long long total_words;
+    int grid_wide;               // blocks for kernels with one thread per item (pieces, bubbles, links)
 };
 
 void launch_ccl_tiles(const Launch& L);    // threshold + tile union-find (pass A)

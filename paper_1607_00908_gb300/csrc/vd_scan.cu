@@ -152,18 +152,20 @@ __device__ __forceinline__ void publish(unsigned long long* f, unsigned epoch, u
 
 __global__ __launch_bounds__(SCAN_THREADS) void k_scan(Pools P, StepTable T, int kind) {
     __shared__ int s_tile;
+    __shared__ long long s_pre[SEG_CACHE];
     __shared__ int s_warp[SCAN_THREADS / 32];
     __shared__ long long s_excl;
     const ScanSel sel = scan_sel(kind);
     const int n = T.n_act;
-    const long long* seg = sel.seg < 0 ? T.word_pre : pre_arr(T, sel.seg);
+    const long long* seg0 = sel.seg < 0 ? T.word_pre : pre_arr(T, sel.seg);
     const long long* base = pre_arr(T, sel.base);
-    const long long total = seg[n];
+    const long long total = seg0[n];
     // every scan of a step has its own tag (step count, kind) and ticket counter
     const unsigned epoch = ((*(volatile unsigned*)&P.g->scan_step << 3) | (unsigned)kind) & 0x3FFFFFFFu;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     // blocks beyond the number of tiles never take a ticket
     if ((long long)blockIdx.x * SCAN_TILE >= total) return;
+    const long long* seg = seg_table(seg0, n, s_pre);
 
     for (;;) {
         if (threadIdx.x == 0) s_tile = atomicAdd(&P.g->scan_ticket[kind], 1);

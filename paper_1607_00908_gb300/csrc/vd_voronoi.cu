@@ -550,8 +550,9 @@ __global__ __launch_bounds__(32 * LINK_WARPS) void k_links(Pools P, StepTable T)
 // appended links -> link hash (+ degrees); appended pairs -> overlap hash
 
 __global__ void k_merge_lists(Pools P, StepTable T) {
-    const long long* pe = pre_arr(T, PRE_EA);
-    const long long* po = pre_arr(T, PRE_OA);
+    __shared__ long long s_pe[SEG_CACHE], s_po[SEG_CACHE];
+    const long long* pe = seg_table(pre_arr(T, PRE_EA), T.n_act, s_pe);
+    const long long* po = seg_table(pre_arr(T, PRE_OA), T.n_act, s_po);
     const long long ne = pe[T.n_act], no = po[T.n_act];
     for (long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x; g < ne + no;
          g += (long long)gridDim.x * blockDim.x) {
@@ -573,7 +574,7 @@ __global__ void k_merge_lists(Pools P, StepTable T) {
 
 void launch_merge_lists(const Launch& L) {
     launch_plan(L, 0, ENDS_NONE);
-    k_merge_lists<<<L.grid_items, 256, 0, L.s>>>(L.P, L.T);
+    k_merge_lists<<<L.grid_wide, 256, 0, L.s>>>(L.P, L.T);
     ++*L.nlaunch;
 }
 
