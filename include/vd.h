@@ -24,7 +24,10 @@
  *  - An edge/link key is uint64 (lo << 32) | hi with lo < hi labels.
  *  - Device work is asynchronous on the stream given at creation. Getters
  *    synchronise that stream and copy into caller buffers, which may be host
- *    or device memory (cudaMemcpyDefault).
+ *    or device memory (cudaMemcpyDefault). After a push, the first state or
+ *    change query copies every instance's counts (and, for changes, every
+ *    instance's change lists, packed on the device) to the host at once;
+ *    further queries about the same push are answered from those copies.
  *  - A context is not thread-safe: one host thread drives it at a time.
  */
 #ifndef VD_H_
@@ -191,6 +194,41 @@ vd_status vd_batch_push_host(vd_batch* b, const float* const* h_fields);
 vd_status vd_batch_push_subset(vd_batch* b, const int32_t* active, int32_t n_active,
                                const float* const* d_fields);
 vd_status vd_batch_get_changes(vd_batch* b, int32_t i, vd_changes* out);
+
+/* Double-buffered host input. vd_batch_stage_host copies h_fields (HOST array
+ * of n HOST pointers, Ly*Lx floats each, pinned for asynchrony) into the next
+ * of two batch-owned input buffers on a copy stream of the batch and returns;
+ * the copy waits only for the step that last read that buffer. It does not
+ * advance the batch. vd_batch_push_staged enqueues one step on the most
+ * recently staged inputs (the step waits for their copy); VD_ERR_STATE if
+ * nothing was staged since the last vd_batch_push_staged. Staging the next
+ * frames before querying the current step's results overlaps the host->device
+ * copy with the step. The caller keeps the host arrays unchanged until the
+ * step that reads them has been queried. */
+vd_status vd_batch_stage_host(vd_batch* b, const float* const* h_fields);
+vd_status vd_batch_push_staged(vd_batch* b);
+
+/* Results of every instance of the last push in one call. Per-instance arrays
+ * (n entries, may be NULL) receive the counts and a status per instance (the
+ * vd_status its vd_batch_get_changes would return; failed instances add no
+ * entries). The change lists of all instances are packed instance-major into
+ * the list arrays (may be NULL); the totals are always set. VD_ERR_CAPACITY
+ * when a non-NULL list array is smaller than its total (nothing is copied into
+ * the lists then). */
+typedef struct vd_batch_changes {
+    int32_t* status;
+    int32_t* n_prev;
+    int32_t* n_now;
+    int32_t* n_breaking;
+    int32_t* n_arising;
+    uint64_t* breaking;        /* all instances' breaking keys */
+    uint64_t* breaking_prev;   /* their past keys, same order */
+    int64_t cap_breaking;
+    uint64_t* arising;         int64_t cap_arising;
+    uint8_t* active;           int64_t cap_active;   /* K entries per instance */
+    int64_t total_breaking, total_arising, total_active;   /* set by the call */
+} vd_batch_changes;
+vd_status vd_batch_get_changes_all(vd_batch* b, vd_batch_changes* out);
 vd_status vd_batch_get_labels(vd_batch* b, int32_t i, int32_t* out, int64_t cap, int64_t* n);
 vd_status vd_batch_get_owners(vd_batch* b, int32_t i, int32_t* out, int64_t cap, int64_t* n);
 vd_status vd_batch_get_edges(vd_batch* b, int32_t i, uint64_t* out, int64_t cap, int64_t* n);

@@ -82,9 +82,17 @@ struct vd_batch {
     long long* d_pitches = nullptr;
     std::vector<const float*> h_fields;
     std::vector<long long> h_pitches;
-    // host input staging for vd_push_frame_host (instance 0) and vd_batch_push_host
+    // host input staging for vd_push_frame_host (instance 0)
     float* d_host_field = nullptr;
-    std::vector<float*> d_inputs;
+    // double-buffered host input (vd_batch_stage_host / vd_batch_push_staged):
+    // two sets of input buffers filled on a copy stream
+    std::vector<float*> d_stage[2];
+    cudaStream_t cs = nullptr;
+    cudaEvent_t ev_staged[2] = {nullptr, nullptr};   // copies into buffer k done
+    cudaEvent_t ev_read[2] = {nullptr, nullptr};     // the step reading buffer k done
+    bool read_pending[2] = {false, false};
+    int stage_next = 0;                              // buffer the next stage call fills
+    int staged = -1;                                 // staged, not yet pushed
     // graph of the all-active step
     cudaGraphExec_t graph = nullptr;
     bool use_graph = false;
@@ -96,6 +104,21 @@ struct vd_batch {
     bool timing = false;
     std::vector<cudaEvent_t> ev_pool;
     int ev_used = 0;
+    // host copies of the last step's results, filled by the first query after
+    // a push: every instance's state in one copy, and every instance's change
+    // lists gathered on the device and copied in one piece
+    std::vector<InstState> h_st;
+    long long st_at = -1;                 // frames_pushed when h_st was filled
+    long long chg_at = -1;                // frames_pushed when the lists were filled
+    long long chg_nb = 0;                 // breaking entries of all instances
+    unsigned long long* d_chg = nullptr;  // [breaking | breaking_prev | arising]
+    unsigned long long* h_chg = nullptr;  // pinned
+    long long chg_cap = 0;
+    unsigned char* d_act = nullptr;       // active flags of all instances
+    unsigned char* h_act = nullptr;       // pinned
+    long long act_cap = 0;
+    long long* d_off = nullptr;           // per instance: breaking, arising, active offsets
+    long long* h_off = nullptr;           // pinned
 };
 
 static const int N_STAGES = 6;
@@ -209,7 +232,11 @@ void enqueue_step(vd_batch* b, const Launch& L, bool timed) {
     launch_links(L);
     launch_merge_lists(L);
     mark(b, timed);
-    launch_graph(L);
+    launch_graph_prep(L);
+    launch_graph_csr(L);
+    launch_graph_match(L);
+    launch_graph_translate(L);
+    launch_graph_flips(L);
     launch_finish(L);
     mark(b, timed);
 }
@@ -351,7 +378,7 @@ vd_status create_batch(const vd_config* cfgs, int n, vd_batch** out, bool sequen
     P.oapp_key = M.alloc<unsigned long long>(ovl);
     P.oapp_cnt = M.alloc<unsigned>(ovl);
     P.scan_flag_cap = scan_items / SCAN_TILE + 2;
-    P.scan_flags = M.alloc<unsigned long long>(P.scan_flag_cap);
+    P.scan_flags = M.alloc<unsigned long long>(SCAN_KINDS * P.scan_flag_cap);
     b->d_fields = M.alloc<const float*>(n);
     b->d_pitches = M.alloc<long long>(n);
     P.fields = b->d_fields;
@@ -378,7 +405,7 @@ vd_status create_batch(const vd_config* cfgs, int n, vd_batch** out, bool sequen
     chk(cudaMemsetAsync(P.ehash, 0xff, sizeof(unsigned long long) * eh, b->s));
     chk(cudaMemsetAsync(P.ohash, 0xff, sizeof(unsigned long long) * oh, b->s));
     chk(cudaMemsetAsync(P.oval, 0, sizeof(unsigned) * oh, b->s));
-    chk(cudaMemsetAsync(P.scan_flags, 0, sizeof(unsigned long long) * P.scan_flag_cap, b->s));
+    chk(cudaMemsetAsync(P.scan_flags, 0, sizeof(unsigned long long) * SCAN_KINDS * P.scan_flag_cap, b->s));
     int dev = 0, sms = 152;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -404,12 +431,98 @@ vd_status create_batch(const vd_config* cfgs, int n, vd_batch** out, bool sequen
     return VD_OK;
 }
 
+// state of instance i after the last push; the first call after a push waits
+// for the stream and copies every instance's state at once
 vd_status read_state(vd_batch* b, int i, InstState* st) {
     if (!b || i < 0 || i >= b->n) return VD_ERR_INVALID;
-    cudaError_t e = cudaStreamSynchronize(b->s);
+    if (b->st_at != b->frames_pushed) {
+        cudaError_t e = cudaStreamSynchronize(b->s);
+        if (e != cudaSuccess) return VD_ERR_CUDA;
+        b->h_st.resize(b->n);
+        e = cudaMemcpy(b->h_st.data(), b->P.st, sizeof(InstState) * b->n, cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return VD_ERR_CUDA;
+        b->st_at = b->frames_pushed;
+    }
+    *st = b->h_st[i];
+    return VD_OK;
+}
+
+// change lists of every instance of the last push in host memory: offsets
+// from the cached states, one gather kernel into a packed device buffer, one
+// copy to pinned host memory
+vd_status ensure_changes(vd_batch* b) {
+    if (b->chg_at == b->frames_pushed) return VD_OK;
+    InstState tmp;
+    vd_status r = read_state(b, 0, &tmp);
+    if (r) return r;
+    const int n = b->n;
+    if (!b->h_off) {
+        if (cudaMallocHost(&b->h_off, sizeof(long long) * 3 * (n + 1)) != cudaSuccess) return VD_ERR_OOM;
+        if (cudaMalloc(&b->d_off, sizeof(long long) * 3 * (n + 1)) != cudaSuccess) return VD_ERR_OOM;
+    }
+    long long nb = 0, na = 0, nk = 0;
+    for (int j = 0; j < n; ++j) {
+        const InstState& s = b->h_st[j];
+        b->h_off[3 * j] = nb;
+        b->h_off[3 * j + 1] = na;
+        b->h_off[3 * j + 2] = nk;
+        if (s.frame > 0 && !s.err) {
+            nb += s.n_break;
+            na += s.n_arise;
+            nk += s.K;
+        }
+    }
+    b->h_off[3 * n] = nb;
+    b->h_off[3 * n + 1] = na;
+    b->h_off[3 * n + 2] = nk;
+    const long long need = 2 * nb + na;
+    if (need > b->chg_cap) {
+        cudaFree(b->d_chg);
+        cudaFreeHost(b->h_chg);
+        b->d_chg = nullptr;
+        b->h_chg = nullptr;
+        b->chg_cap = 0;
+        const long long cap = need + need / 2 + 1024;
+        if (cudaMalloc(&b->d_chg, sizeof(unsigned long long) * cap) != cudaSuccess) return VD_ERR_OOM;
+        if (cudaMallocHost(&b->h_chg, sizeof(unsigned long long) * cap) != cudaSuccess) return VD_ERR_OOM;
+        b->chg_cap = cap;
+    }
+    if (nk > b->act_cap) {
+        cudaFree(b->d_act);
+        cudaFreeHost(b->h_act);
+        b->d_act = nullptr;
+        b->h_act = nullptr;
+        b->act_cap = 0;
+        const long long cap = nk + nk / 2 + 1024;
+        if (cudaMalloc(&b->d_act, cap) != cudaSuccess) return VD_ERR_OOM;
+        if (cudaMallocHost(&b->h_act, cap) != cudaSuccess) return VD_ERR_OOM;
+        b->act_cap = cap;
+    }
+    cudaError_t e = cudaMemcpyAsync(b->d_off, b->h_off, sizeof(long long) * 3 * (n + 1), cudaMemcpyHostToDevice, b->s);
     if (e != cudaSuccess) return VD_ERR_CUDA;
-    e = cudaMemcpy(st, b->P.st + i, sizeof(InstState), cudaMemcpyDeviceToHost);
-    return cuda_status(e);
+    launch_gather_changes(b->s, b->P, b->d_off, n, nb, b->d_chg, b->d_act);
+    b->launches += 1;
+    if (need > 0) e = cudaMemcpyAsync(b->h_chg, b->d_chg, sizeof(unsigned long long) * need, cudaMemcpyDeviceToHost, b->s);
+    if (e == cudaSuccess && nk > 0) e = cudaMemcpyAsync(b->h_act, b->d_act, nk, cudaMemcpyDeviceToHost, b->s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->s);
+    if (e != cudaSuccess) return VD_ERR_CUDA;
+    b->chg_nb = nb;
+    b->chg_at = b->frames_pushed;
+    return VD_OK;
+}
+
+// copy from host staging into a caller buffer in host or device memory
+vd_status copy_from_host(void* dst, const void* src, size_t bytes) {
+    if (bytes == 0) return VD_OK;
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, dst) != cudaSuccess) {
+        cudaGetLastError();
+        at.type = cudaMemoryTypeUnregistered;
+    }
+    if (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged)
+        return cuda_status(cudaMemcpy(dst, src, bytes, cudaMemcpyHostToDevice));
+    std::memcpy(dst, src, bytes);
+    return VD_OK;
 }
 
 vd_status err_status(const InstState& st) {
@@ -488,15 +601,17 @@ vd_status get_changes(vd_batch* b, int i, vd_changes* out) {
     if (st.n_arise > 0 && (!out->arising || out->cap_arising < st.n_arise)) fit = false;
     if (out->active && out->cap_active < st.K) fit = false;
     if (!fit) return VD_ERR_CAPACITY;
+    vd_status r = ensure_changes(b);
+    if (r) return r;
     const size_t u8 = sizeof(unsigned long long);
-    vd_status r = VD_OK;
+    const long long ob = b->h_off[3 * i], oa = b->h_off[3 * i + 1], ok = b->h_off[3 * i + 2];
     if (st.n_break > 0) {
-        r = copy_out(out->breaking, b->P.brk + D.edge_off, u8 * st.n_break, b->s);
-        if (!r && out->breaking_prev)
-            r = copy_out(out->breaking_prev, b->P.brk_prev + D.edge_off, u8 * st.n_break, b->s);
+        r = copy_from_host(out->breaking, b->h_chg + ob, u8 * st.n_break);
+        if (!r && out->breaking_prev) r = copy_from_host(out->breaking_prev, b->h_chg + b->chg_nb + ob, u8 * st.n_break);
     }
-    if (!r && st.n_arise > 0) r = copy_out(out->arising, b->P.ari + D.edge_off, u8 * st.n_arise, b->s);
-    if (!r && out->active && st.K > 0) r = copy_out(out->active, b->P.active + D.comp_off, st.K, b->s);
+    if (!r && st.n_arise > 0) r = copy_from_host(out->arising, b->h_chg + 2 * b->chg_nb + oa, u8 * st.n_arise);
+    if (!r && out->active && st.K > 0) r = copy_from_host(out->active, b->h_act + ok, st.K);
+    (void)D;
     return r;
 }
 
@@ -742,22 +857,87 @@ vd_status vd_batch_push(vd_batch* b, const float* const* d_fields) {
     return run_all(b);
 }
 
-vd_status vd_batch_push_host(vd_batch* b, const float* const* h_fields) {
+vd_status vd_batch_stage_host(vd_batch* b, const float* const* h_fields) {
     if (!b || !h_fields) return VD_ERR_INVALID;
-    if (b->d_inputs.empty()) {
-        b->d_inputs.resize(b->n);
+    for (int i = 0; i < b->n; ++i)
+        if (!h_fields[i]) return VD_ERR_INVALID;
+    if (!b->cs) {
+        if (cudaStreamCreateWithFlags(&b->cs, cudaStreamNonBlocking) != cudaSuccess) return VD_ERR_CUDA;
+        for (int k = 0; k < 2; ++k)
+            if (cudaEventCreateWithFlags(&b->ev_staged[k], cudaEventDisableTiming) != cudaSuccess ||
+                cudaEventCreateWithFlags(&b->ev_read[k], cudaEventDisableTiming) != cudaSuccess)
+                return VD_ERR_CUDA;
+    }
+    const int k = b->stage_next;
+    if (b->d_stage[k].empty()) {
+        b->d_stage[k].resize(b->n);
         for (int i = 0; i < b->n; ++i) {
-            b->d_inputs[i] = b->mem.alloc<float>((long long)b->desc[i].Lx * b->desc[i].Ly);
-            if (!b->mem.ok) return VD_ERR_OOM;
+            b->d_stage[k][i] = b->mem.alloc<float>((long long)b->desc[i].Lx * b->desc[i].Ly);
+            if (!b->mem.ok) {
+                b->d_stage[k].clear();
+                return VD_ERR_OOM;
+            }
         }
     }
+    // the step that last read this buffer must be done with it
+    if (b->read_pending[k] && cudaStreamWaitEvent(b->cs, b->ev_read[k], 0) != cudaSuccess) return VD_ERR_CUDA;
     for (int i = 0; i < b->n; ++i) {
-        if (!h_fields[i]) return VD_ERR_INVALID;
         const size_t bytes = sizeof(float) * (size_t)b->desc[i].Lx * b->desc[i].Ly;
-        if (cudaMemcpyAsync(b->d_inputs[i], h_fields[i], bytes, cudaMemcpyHostToDevice, b->s) != cudaSuccess)
+        if (cudaMemcpyAsync(b->d_stage[k][i], h_fields[i], bytes, cudaMemcpyHostToDevice, b->cs) != cudaSuccess)
             return VD_ERR_CUDA;
     }
-    return vd_batch_push(b, b->d_inputs.data());
+    if (cudaEventRecord(b->ev_staged[k], b->cs) != cudaSuccess) return VD_ERR_CUDA;
+    b->staged = k;
+    b->stage_next = k ^ 1;
+    return VD_OK;
+}
+
+vd_status vd_batch_push_staged(vd_batch* b) {
+    if (!b) return VD_ERR_INVALID;
+    if (b->staged < 0) return VD_ERR_STATE;
+    const int k = b->staged;
+    if (cudaStreamWaitEvent(b->s, b->ev_staged[k], 0) != cudaSuccess) return VD_ERR_CUDA;
+    vd_status r = vd_batch_push(b, b->d_stage[k].data());
+    if (r) return r;
+    if (cudaEventRecord(b->ev_read[k], b->s) != cudaSuccess) return VD_ERR_CUDA;
+    b->read_pending[k] = true;
+    b->staged = -1;
+    return VD_OK;
+}
+
+vd_status vd_batch_push_host(vd_batch* b, const float* const* h_fields) {
+    vd_status r = vd_batch_stage_host(b, h_fields);
+    return r ? r : vd_batch_push_staged(b);
+}
+
+vd_status vd_batch_get_changes_all(vd_batch* b, vd_batch_changes* out) {
+    if (!b || !out) return VD_ERR_INVALID;
+    vd_status r = ensure_changes(b);
+    if (r) return r;
+    const int n = b->n;
+    const long long nb = b->h_off[3 * n], na = b->h_off[3 * n + 1], nk = b->h_off[3 * n + 2];
+    out->total_breaking = nb;
+    out->total_arising = na;
+    out->total_active = nk;
+    for (int j = 0; j < n; ++j) {
+        const InstState& st = b->h_st[j];
+        const vd_status sj = st.frame == 0 ? VD_ERR_STATE : err_status(st);
+        const bool ok = sj == VD_OK;
+        if (out->status) out->status[j] = sj;
+        if (out->n_prev) out->n_prev[j] = ok ? st.rep_K_prev : 0;
+        if (out->n_now) out->n_now[j] = ok ? st.K : 0;
+        if (out->n_breaking) out->n_breaking[j] = ok ? st.n_break : 0;
+        if (out->n_arising) out->n_arising[j] = ok ? st.n_arise : 0;
+    }
+    if ((out->breaking && out->cap_breaking < nb) || (out->breaking_prev && out->cap_breaking < nb) ||
+        (out->arising && out->cap_arising < na) || (out->active && out->cap_active < nk))
+        return VD_ERR_CAPACITY;
+    const size_t u8 = sizeof(unsigned long long);
+    if (out->breaking) r = copy_from_host(out->breaking, b->h_chg, u8 * nb);
+    if (!r && out->breaking_prev) r = copy_from_host(out->breaking_prev, b->h_chg + nb, u8 * nb);
+    if (!r && out->arising) r = copy_from_host(out->arising, b->h_chg + 2 * nb, u8 * na);
+    if (!r && out->active) r = copy_from_host(out->active, b->h_act, nk);
+    return r;
 }
 
 vd_status vd_batch_push_subset(vd_batch* b, const int32_t* active, int32_t n_active, const float* const* d_fields) {
@@ -814,6 +994,20 @@ vd_status vd_batch_destroy(vd_batch* b) {
     cudaStreamSynchronize(b->s);
     if (b->graph) cudaGraphExecDestroy(b->graph);
     for (cudaEvent_t e : b->ev_pool) cudaEventDestroy(e);
+    cudaFree(b->d_chg);
+    cudaFreeHost(b->h_chg);
+    cudaFree(b->d_act);
+    cudaFreeHost(b->h_act);
+    cudaFree(b->d_off);
+    cudaFreeHost(b->h_off);
+    if (b->cs) {
+        cudaStreamSynchronize(b->cs);
+        cudaStreamDestroy(b->cs);
+    }
+    for (int k = 0; k < 2; ++k) {
+        if (b->ev_staged[k]) cudaEventDestroy(b->ev_staged[k]);
+        if (b->ev_read[k]) cudaEventDestroy(b->ev_read[k]);
+    }
     b->mem.release();
     delete b;
     return VD_OK;

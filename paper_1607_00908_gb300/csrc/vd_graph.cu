@@ -316,29 +316,69 @@ __global__ void k_flip_write(Pools P, StepTable T) {
     for_items(T, PRE_K, [&](int inst, long long a) { compare_row<true>(P, inst, (int)a); });
 }
 
-void launch_graph(const Launch& L) {
-    const int g = L.grid_wide;
+// packed copy of every instance's breaking keys (then their past keys), arising
+// keys and active flags: out = [breaking (nb) | breaking_prev (nb) | arising]
+__global__ void k_gather_changes(Pools P, const long long* off, int n, long long nb, unsigned long long* out,
+                                 unsigned char* act) {
+    for (int j = blockIdx.x; j < n; j += gridDim.x) {
+        const InstDesc& D = P.desc[j];
+        const long long b0 = off[3 * j], b1 = off[3 * j + 3];
+        const long long a0 = off[3 * j + 1], a1 = off[3 * j + 4];
+        const long long k0 = off[3 * j + 2], k1 = off[3 * j + 5];
+        for (long long t = threadIdx.x; t < b1 - b0; t += blockDim.x) {
+            out[b0 + t] = P.brk[D.edge_off + t];
+            out[nb + b0 + t] = P.brk_prev[D.edge_off + t];
+        }
+        for (long long t = threadIdx.x; t < a1 - a0; t += blockDim.x) out[2 * nb + a0 + t] = P.ari[D.edge_off + t];
+        for (long long t = threadIdx.x; t < k1 - k0; t += blockDim.x) act[k0 + t] = P.active[D.comp_off + t];
+    }
+}
+
+void launch_gather_changes(cudaStream_t s, const Pools& P, const long long* off, int n, long long nb,
+                           unsigned long long* out, unsigned char* act) {
+    k_gather_changes<<<n < 1024 ? n : 1024, 256, 0, s>>>(P, off, n, nb, out, act);
+}
+
+void launch_graph_prep(const Launch& L) {
     launch_plan(L, 0, ends_bit(SCAN_DEG));
+}
+
+void launch_graph_csr(const Launch& L) {
     launch_scan(L, SCAN_DEG);
-    k_csr_scatter<<<g, 256, 0, L.s>>>(L.P, L.T);
+    k_csr_scatter<<<L.grid_wide, 256, 0, L.s>>>(L.P, L.T);
     ++*L.nlaunch;
-    k_csr_sort<<<g, 256, 0, L.s>>>(L.P, L.T);
+    k_csr_sort<<<L.grid_wide, 256, 0, L.s>>>(L.P, L.T);
     ++*L.nlaunch;
+}
+
+void launch_graph_match(const Launch& L) {
+    const int g = L.grid_wide;
     k_match_best<<<g, 256, 0, L.s>>>(L.P, L.T);
     ++*L.nlaunch;
     k_match_phi<<<g, 256, 0, L.s>>>(L.P, L.T);
     ++*L.nlaunch;
+}
+
+// The translation reads the past frame's CSR, which in a frame sequence is the
+// now-frame CSR of the previous instance built in this step: it follows both
+// the match and the CSR chain.
+void launch_graph_translate(const Launch& L) {
+    const int g = L.grid_wide;
     k_translate_count<<<g, 256, 0, L.s>>>(L.P, L.T);
     ++*L.nlaunch;
-    launch_plan(L, 0, ends_bit(SCAN_TDEG));
+    launch_plan(L, 0, ends_bit(SCAN_TDEG), pre_bit(PRE_ET));
     launch_scan(L, SCAN_TDEG);
     k_translate_scatter<<<g, 256, 0, L.s>>>(L.P, L.T);
     ++*L.nlaunch;
     k_tcsr_sort<<<g, 256, 0, L.s>>>(L.P, L.T);
     ++*L.nlaunch;
+}
+
+void launch_graph_flips(const Launch& L) {
+    const int g = L.grid_wide;
     k_flip_count<<<g, 256, 0, L.s>>>(L.P, L.T);
     ++*L.nlaunch;
-    launch_plan(L, 0, ends_bit(SCAN_FLIPS) | ends_bit(SCAN_FLIPS_A));
+    launch_plan(L, 0, ends_bit(SCAN_FLIPS) | ends_bit(SCAN_FLIPS_A), pre_bit(PRE_FB) | pre_bit(PRE_FA));
     launch_scan(L, SCAN_FLIPS);
     launch_scan(L, SCAN_FLIPS_A);
     k_flip_write<<<g, 256, 0, L.s>>>(L.P, L.T);

@@ -213,6 +213,8 @@ enum PreIdx : int {
     PRE_OA,         // appended overlap pairs
     NPRE
 };
+constexpr int PRE_ALL = (1 << NPRE) - 1;
+__host__ __device__ constexpr int pre_bit(int k) { return 1 << k; }
 
 __device__ __forceinline__ long long* pre_arr(const StepTable& T, int which) {
     return T.pre + (long long)which * (T.n_act + 1);
@@ -425,11 +427,21 @@ void launch_labels(const Launch& L);       // run labels + overlap histogram
 void launch_voronoi(const Launch& L);      // exact owner of every site
 void launch_links(const Launch& L);        // per-tile links from the owners
 void launch_merge_lists(const Launch& L);  // appended links/pairs -> hash tables
-void launch_graph(const Launch& L);        // CSR, match, translation, flips
+// graph stage: prefixes of the merged lists, the now-frame CSR, the match,
+// the translated past CSR, the flips
+void launch_graph_prep(const Launch& L);
+void launch_graph_csr(const Launch& L);
+void launch_graph_match(const Launch& L);
+void launch_graph_translate(const Launch& L);
+void launch_graph_flips(const Launch& L);
 void launch_begin(const Launch& L);        // per-step counters and field pointers
 void launch_finish(const Launch& L);       // swap frames
 void launch_edge_keys(cudaStream_t s, const Pools& P, int inst, int slot, unsigned long long* out);
 void launch_expand_labels(cudaStream_t s, const Pools& P, int inst, int slot, int* out, long long n);
+// every instance's change lists packed at the offsets `off` (3 per instance:
+// breaking, arising, active; entry 3n holds the totals)
+void launch_gather_changes(cudaStream_t s, const Pools& P, const long long* off, int n, long long nb,
+                           unsigned long long* out, unsigned char* act);
 
 // generic decoupled look-back scan over a virtual concatenation (vd_scan.cu)
 constexpr int SCAN_THREADS = 256;
@@ -443,12 +455,14 @@ enum ScanKind : int {
     SCAN_FLIPS = 4,      // breaking counts per row
     SCAN_FLIPS_A = 5,    // arising counts per row
 };
+constexpr int SCAN_KINDS = 6;
 // the end value of the offset array of scan `kind`, written by k_plan
 constexpr int ENDS_NONE = 0;
 __host__ __device__ constexpr int ends_bit(ScanKind kind) { return 1 << kind; }
 void launch_scan(const Launch& L, ScanKind kind);   // k_scan over the current plan
 // recompute prefixes (and bucket grids when with_comp) and the end values of
-// the offset arrays whose bits are set in ends
-void launch_plan(const Launch& L, int with_comp, int ends);
+// the offset arrays whose bits are set in ends; only the prefix arrays whose
+// bits are set in pre_mask are written
+void launch_plan(const Launch& L, int with_comp, int ends, int pre_mask = PRE_ALL);
 
 }  // namespace vd

@@ -18,7 +18,7 @@ namespace vd {
 // ---------------------------------------------------------------------------
 constexpr int PLAN_THREADS = 256;
 
-__global__ __launch_bounds__(PLAN_THREADS) void k_plan(Pools P, StepTable T, int with_comp, int ends) {
+__global__ __launch_bounds__(PLAN_THREADS) void k_plan(Pools P, StepTable T, int with_comp, int ends, int pre_mask) {
     // one block: thread per instance, block scans for the prefixes
     __shared__ long long s_v[NPRE][PLAN_THREADS];
     __shared__ long long s_carry[NPRE];
@@ -90,12 +90,13 @@ __global__ __launch_bounds__(PLAN_THREADS) void k_plan(Pools P, StepTable T, int
             __syncthreads();
         }
         if (a < n)
-            for (int k = 0; k < NPRE; ++k) pre_arr(T, k)[a] = s_carry[k] + s_v[k][tid] - v[k];
+            for (int k = 0; k < NPRE; ++k)
+                if (pre_mask & pre_bit(k)) pre_arr(T, k)[a] = s_carry[k] + s_v[k][tid] - v[k];
         __syncthreads();
         if (tid < NPRE) s_carry[tid] += s_v[tid][PLAN_THREADS - 1];
         __syncthreads();
     }
-    if (tid < NPRE) pre_arr(T, tid)[n] = s_carry[tid];
+    if (tid < NPRE && (pre_mask & pre_bit(tid))) pre_arr(T, tid)[n] = s_carry[tid];
 }
 
 // ---------------------------------------------------------------------------
@@ -216,7 +217,8 @@ __global__ __launch_bounds__(SCAN_THREADS) void k_scan(Pools P, StepTable T, int
 
         if (warp == 0) {
             // warp-parallel decoupled look-back over windows of 32 predecessors
-            unsigned long long* flags = P.scan_flags;
+            // each scan kind has its own flags
+            unsigned long long* flags = P.scan_flags + (long long)kind * P.scan_flag_cap;
             long long excl = 0;
             if (tile == 0) {
                 if (lane == 0) publish(&flags[0], epoch, ST_INC, btot);
@@ -277,8 +279,8 @@ __global__ __launch_bounds__(SCAN_THREADS) void k_scan(Pools P, StepTable T, int
     }
 }
 
-void launch_plan(const Launch& L, int with_comp, int ends) {
-    k_plan<<<1, PLAN_THREADS, 0, L.s>>>(L.P, L.T, with_comp, ends);
+void launch_plan(const Launch& L, int with_comp, int ends, int pre_mask) {
+    k_plan<<<1, PLAN_THREADS, 0, L.s>>>(L.P, L.T, with_comp, ends, pre_mask);
     ++*L.nlaunch;
 }
 

@@ -132,15 +132,17 @@ __global__ __launch_bounds__(32 * VWARPS) void k_voronoi(Pools P, StepTable T) {
     __shared__ int s_cx[VWARPS][WSCAN], s_cy[VWARPS][WSCAN], s_id[VWARPS][WSCAN];
     __shared__ float2 s_fc[VWARPS][WCAND];
     __shared__ int s_kk[VWARPS][WCAND];
+    __shared__ int s_tpre[SEG_CACHE];
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int* tpre = seg_table(T.tileV_pre, T.n_act, s_tpre);
     const int b = blockIdx.x * VWARPS + warp;
-    if (b >= T.tileV_pre[T.n_act]) return;
-    const int a = seg_of_int(T.tileV_pre, T.n_act, b);
+    if (b >= tpre[T.n_act]) return;
+    const int a = seg_of_int(tpre, T.n_act, b);
     const int inst = T.act[a];
     const InstDesc& D = P.desc[inst];
     const InstState& S = P.st[inst];
-    const int t = b - T.tileV_pre[a];
+    const int t = b - tpre[a];
     const int tx = t % D.vtx, ty = t / D.vtx;
     const int Lx = D.Lx, Ly = D.Ly;
     const int x0 = tx * VW, y0 = ty * VH;
@@ -323,7 +325,26 @@ __global__ __launch_bounds__(32 * VWARPS) void k_voronoi(Pools P, StepTable T) {
                 const int sx = pxo + c;
                 const float sxf = (float)(Q * sx);
                 int o[4];
-                if (nk <= WCAND) {
+                if (nk == 1) {
+                    // one candidate owns the whole patch
+                    o[0] = o[1] = o[2] = o[3] = ids[kk[0]];
+                } else if (nk == 2) {
+                    // the bisector decides: d(s,c1)^2 - d(s,c2)^2 = 2 s.(c2 - c1) + |c1|^2 - |c2|^2,
+                    // exact in int64 (tile-relative minimum images), ties to the smaller label
+                    const int e1 = kk[0], e2 = kk[1];
+                    const long long c1x = cxs[e1], c1y = cys[e1], c2x = cxs[e2], c2y = cys[e2];
+                    const int i1 = ids[e1], i2 = ids[e2];
+                    const int itie = i1 < i2 ? i1 : i2;
+                    const long long ax = 2 * (c2x - c1x), ay = 2 * (c2y - c1y);
+                    long long dv = ax * ((long long)Q * sx) + ay * ((long long)Q * (pyo + rb)) +
+                                   (c1x * c1x + c1y * c1y) - (c2x * c2x + c2y * c2y);
+                    const long long step = ay * Q;
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        o[k] = dv < 0 ? i1 : (dv > 0 ? i2 : itie);
+                        dv += step;
+                    }
+                } else if (nk <= WCAND) {
                     float syf[4];
                     unsigned f1[4], f2[4];
 #pragma unroll

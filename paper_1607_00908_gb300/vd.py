@@ -34,6 +34,7 @@ EXPORTS = (
     "vd_get_counts", "vd_get_labels", "vd_get_centroids_q10", "vd_get_owners", "vd_get_edges",
     "vd_get_match", "vd_set_timing", "vd_get_timing", "vd_stage_name", "vd_destroy", "vd_status_string",
     "vd_batch_create", "vd_batch_create_sequence", "vd_batch_push", "vd_batch_push_host", "vd_batch_push_subset", "vd_batch_get_changes",
+    "vd_batch_stage_host", "vd_batch_push_staged", "vd_batch_get_changes_all",
     "vd_batch_get_labels", "vd_batch_get_owners", "vd_batch_get_edges", "vd_batch_get_centroids_q10",
     "vd_batch_get_counts", "vd_batch_set_timing", "vd_batch_get_timing", "vd_batch_destroy",
     "vd_voronoi_owners_static", "vd_server_create", "vd_server_submit", "vd_server_poll",
@@ -68,6 +69,17 @@ class vd_changes(C.Structure):
         ("breaking_prev", C.POINTER(C.c_uint64)),
         ("arising", C.POINTER(C.c_uint64)), ("cap_arising", C.c_int32),
         ("active", C.POINTER(C.c_uint8)), ("cap_active", C.c_int32),
+    ]
+
+
+class vd_batch_changes(C.Structure):
+    _fields_ = [
+        ("status", C.POINTER(C.c_int32)), ("n_prev", C.POINTER(C.c_int32)), ("n_now", C.POINTER(C.c_int32)),
+        ("n_breaking", C.POINTER(C.c_int32)), ("n_arising", C.POINTER(C.c_int32)),
+        ("breaking", C.POINTER(C.c_uint64)), ("breaking_prev", C.POINTER(C.c_uint64)), ("cap_breaking", C.c_int64),
+        ("arising", C.POINTER(C.c_uint64)), ("cap_arising", C.c_int64),
+        ("active", C.POINTER(C.c_uint8)), ("cap_active", C.c_int64),
+        ("total_breaking", C.c_int64), ("total_arising", C.c_int64), ("total_active", C.c_int64),
     ]
 
 
@@ -117,6 +129,9 @@ def lib():
         "vd_batch_push_host": [VP, P(VP)],
         "vd_batch_push_subset": [VP, P(I32), I32, P(VP)],
         "vd_batch_get_changes": [VP, I32, P(vd_changes)],
+        "vd_batch_stage_host": [VP, P(VP)],
+        "vd_batch_push_staged": [VP],
+        "vd_batch_get_changes_all": [VP, P(vd_batch_changes)],
         "vd_batch_get_labels": [VP, I32, VP, I64, P(I64)],
         "vd_batch_get_owners": [VP, I32, VP, I64, P(I64)],
         "vd_batch_get_edges": [VP, I32, VP, I64, P(I64)],
@@ -396,6 +411,38 @@ class Batch(_Base):
     def push_host_ptrs(self, host_ptrs) -> None:
         arr = (C.c_void_p * len(host_ptrs))(*[C.c_void_p(p) for p in host_ptrs])
         _check(lib().vd_batch_push_host(self.h, arr), "vd_batch_push_host")
+
+    def stage_host_ptrs(self, host_ptrs) -> None:
+        """Copy the next frames (host pointers) into the batch's spare input
+        buffers on its copy stream (vd_batch_stage_host)."""
+        arr = (C.c_void_p * len(host_ptrs))(*[C.c_void_p(p) for p in host_ptrs])
+        _check(lib().vd_batch_stage_host(self.h, arr), "vd_batch_stage_host")
+
+    def push_staged(self) -> None:
+        _check(lib().vd_batch_push_staged(self.h), "vd_batch_push_staged")
+
+    def changes_all(self) -> dict:
+        """Every instance's results of the last push (vd_batch_get_changes_all):
+        per-instance status and counts, and the packed change lists."""
+        n = len(self.sizes)
+        per = {k: np.zeros(n, np.int32) for k in ("status", "n_prev", "n_now", "n_breaking", "n_arising")}
+        c = vd_batch_changes()
+        for k, a in per.items():
+            setattr(c, k, a.ctypes.data_as(C.POINTER(C.c_int32)))
+        _check(lib().vd_batch_get_changes_all(self.h, C.byref(c)), "vd_batch_get_changes_all")
+        brk = np.empty(c.total_breaking, np.uint64)
+        brkp = np.empty(c.total_breaking, np.uint64)
+        ari = np.empty(c.total_arising, np.uint64)
+        act = np.empty(c.total_active, np.uint8)
+        c.breaking = brk.ctypes.data_as(C.POINTER(C.c_uint64))
+        c.breaking_prev = brkp.ctypes.data_as(C.POINTER(C.c_uint64))
+        c.cap_breaking = len(brk)
+        c.arising = ari.ctypes.data_as(C.POINTER(C.c_uint64))
+        c.cap_arising = len(ari)
+        c.active = act.ctypes.data_as(C.POINTER(C.c_uint8))
+        c.cap_active = len(act)
+        _check(lib().vd_batch_get_changes_all(self.h, C.byref(c)), "vd_batch_get_changes_all")
+        return dict(per, breaking=brk, breaking_prev=brkp, arising=ari, active=act)
 
     def set_timing(self, on: bool) -> None:
         _check(lib().vd_batch_set_timing(self.h, int(bool(on))), "vd_batch_set_timing")

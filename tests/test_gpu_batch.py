@@ -96,3 +96,55 @@ def test_subsets_and_alone_vs_mix():
     b.close()
     for d in alone:
         d.close()
+
+
+def _pinned(frames):
+    return [torch.from_numpy(np.ascontiguousarray(F)).pin_memory() for F in frames]
+
+
+def test_staged_host_pipeline_and_packed_changes_match_oracle():
+    """Host frames staged on the copy stream while the previous push runs
+    (vd_batch_stage_host / vd_batch_push_staged), results read packed for the
+    whole sequence (vd_batch_get_changes_all): every frame equals the oracle
+    and the per-frame getters."""
+    L, n_seq, pushes = 140, 5, 4
+    frames = frames_for(L, 3.0, 41, n_seq * pushes)
+    host = [_pinned(frames[p * n_seq:(p + 1) * n_seq]) for p in range(pushes)]
+    b = vd.Batch([(L, L)], sequence=n_seq)
+    ref = O.Detector(L, L, voronoi="brute")
+    b.stage_host_ptrs([h.data_ptr() for h in host[0]])
+    b.push_staged()
+    for p in range(pushes):
+        if p + 1 < pushes:   # next frames copied while this push runs
+            b.stage_host_ptrs([h.data_ptr() for h in host[p + 1]])
+        allc = b.changes_all()
+        ob = oa = ok = 0
+        for i in range(n_seq):
+            r = ref.push(frames[p * n_seq + i])
+            assert allc["status"][i] == vd.VD_OK
+            assert allc["n_now"][i] == r["K"] and allc["n_prev"][i] == r["K_prev"]
+            nb, na, nk = allc["n_breaking"][i], allc["n_arising"][i], allc["n_now"][i]
+            assert np.array_equal(allc["breaking"][ob:ob + nb], r["breaking"]), (p, i)
+            assert np.array_equal(allc["breaking_prev"][ob:ob + nb], r["breaking_prev"]), (p, i)
+            assert np.array_equal(allc["arising"][oa:oa + na], r["arising"]), (p, i)
+            assert np.array_equal(allc["active"][ok:ok + nk], r["active"]), (p, i)
+            check(b, i, r, f"push {p} frame {i}")
+            ob, oa, ok = ob + nb, oa + na, ok + nk
+        assert (ob, oa, ok) == (len(allc["breaking"]), len(allc["arising"]), len(allc["active"]))
+        if p + 1 < pushes:
+            b.push_staged()
+    b.close()
+
+
+def test_push_staged_needs_a_stage():
+    b = vd.Batch([(64, 64)])
+    with pytest.raises(vd.VdError) as e:
+        b.push_staged()
+    assert e.value.status == vd.VD_ERR_STATE
+    F = _pinned(frames_for(64, 2.0, 3, 1))
+    b.stage_host_ptrs([F[0].data_ptr()])
+    b.push_staged()
+    with pytest.raises(vd.VdError) as e:
+        b.push_staged()
+    assert e.value.status == vd.VD_ERR_STATE
+    b.close()
