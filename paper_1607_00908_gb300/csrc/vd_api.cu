@@ -870,21 +870,39 @@ vd_status vd_batch_stage_host(vd_batch* b, const float* const* h_fields) {
     }
     const int k = b->stage_next;
     if (b->d_stage[k].empty()) {
+        // one allocation per buffer set: instance i's frame follows instance i-1's
+        long long total = 0;
+        for (int i = 0; i < b->n; ++i) total += (long long)b->desc[i].Lx * b->desc[i].Ly;
+        float* base = b->mem.alloc<float>(total);
+        if (!b->mem.ok) return VD_ERR_OOM;
         b->d_stage[k].resize(b->n);
         for (int i = 0; i < b->n; ++i) {
-            b->d_stage[k][i] = b->mem.alloc<float>((long long)b->desc[i].Lx * b->desc[i].Ly);
-            if (!b->mem.ok) {
-                b->d_stage[k].clear();
-                return VD_ERR_OOM;
-            }
+            b->d_stage[k][i] = base;
+            base += (long long)b->desc[i].Lx * b->desc[i].Ly;
         }
     }
     // the step that last read this buffer must be done with it
     if (b->read_pending[k] && cudaStreamWaitEvent(b->cs, b->ev_read[k], 0) != cudaSuccess) return VD_ERR_CUDA;
-    for (int i = 0; i < b->n; ++i) {
-        const size_t bytes = sizeof(float) * (size_t)b->desc[i].Lx * b->desc[i].Ly;
-        if (cudaMemcpyAsync(b->d_stage[k][i], h_fields[i], bytes, cudaMemcpyHostToDevice, b->cs) != cudaSuccess)
-            return VD_ERR_CUDA;
+    // host frames that follow each other in memory go in one copy; adjacent
+    // frames from different host allocations make the runtime refuse the
+    // merged copy (a non-sticky argument error), and they are copied one by one
+    for (int i = 0; i < b->n;) {
+        size_t bytes = sizeof(float) * (size_t)b->desc[i].Lx * b->desc[i].Ly;
+        int j = i + 1;
+        while (j < b->n && h_fields[j] == h_fields[i] + bytes / sizeof(float)) {
+            bytes += sizeof(float) * (size_t)b->desc[j].Lx * b->desc[j].Ly;
+            ++j;
+        }
+        if (cudaMemcpyAsync(b->d_stage[k][i], h_fields[i], bytes, cudaMemcpyHostToDevice, b->cs) != cudaSuccess) {
+            if (j == i + 1) return VD_ERR_CUDA;
+            cudaGetLastError();
+            for (int m = i; m < j; ++m) {
+                const size_t bm = sizeof(float) * (size_t)b->desc[m].Lx * b->desc[m].Ly;
+                if (cudaMemcpyAsync(b->d_stage[k][m], h_fields[m], bm, cudaMemcpyHostToDevice, b->cs) != cudaSuccess)
+                    return VD_ERR_CUDA;
+            }
+        }
+        i = j;
     }
     if (cudaEventRecord(b->ev_staged[k], b->cs) != cudaSuccess) return VD_ERR_CUDA;
     b->staged = k;
