@@ -41,6 +41,10 @@ UNIT = "Gsites/s"
 # Voronoi owners, the one per-site result kept in HBM, are written once (4);
 # labels are kept per run, not per site.
 PIPELINE_BYTES_PER_SITE = 8.0
+# The metric's own % HBM figure counts 16 B/site (field read, previous-label
+# read, label write, owner write: the per-site traffic of a pipeline that
+# stores per-site labels), whatever this implementation actually moves.
+METRIC_BYTES_PER_SITE = 16.0
 
 # Measured DRAM bytes (read + write) per site of a stage's kernels, from one
 # ncu capture of the current kernels on this workload
@@ -278,6 +282,7 @@ def run_ours(args, world, rank, local):
     seq.set_timing(False)
     roofline = roofline_of(stage_ms, names, args.steps, sites_per_step, n > 1, peak, peak_kind)
     roofline["pipeline_frac_8B_per_site"] = value * PIPELINE_BYTES_PER_SITE / peak
+    roofline["pct_hbm_16B_per_site"] = 100.0 * value * METRIC_BYTES_PER_SITE / peak
 
     # ---- end to end through the C ABI with host buffers: every step's frames
     # are copied from pinned host memory (staged on the batch's copy stream
@@ -346,14 +351,14 @@ def run_ours(args, world, rank, local):
 
 
 def run_served(args, world, rank, local):
-    """Served form: 64 simulations, seeded Poisson arrivals at 2000 frames/s,
+    """Served form: 64 simulations, seeded Poisson arrivals (2000 frames/s by default),
     40 GB budget; the same trace replayed with batching and one frame per step."""
     import torch
     from paper_1607_00908_gb300 import serve, vd
 
     torch.cuda.set_device(local if world > 1 else 0)
     vd.lib()
-    r = serve.serve_workload(n_sims=64, rate=2000.0, duration=args.serve_seconds, pool=4, budget_gb=40.0,
+    r = serve.serve_workload(n_sims=64, rate=args.serve_rate, duration=args.serve_seconds, pool=4, budget_gb=40.0,
                              seed=5 + rank)
     if rank == 0:
         s, p = r["served"], r["plain"]
@@ -380,6 +385,7 @@ def main():
     ap.add_argument("--frames", type=int, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--serve-seconds", type=float, default=5.0)
+    ap.add_argument("--serve-rate", type=float, default=2000.0, help="served workload: arrivals per second")
     args = ap.parse_args()
     world, rank, local = dist_setup()
     if args.impl == "reference":
