@@ -98,6 +98,7 @@ struct vd_batch {
     bool use_graph = false;
     long long frames_pushed = 0;
     long long launches = 0;
+    cudaError_t launch_err = cudaSuccess;   // first failed launch of the step being enqueued
     long long graph_launches = 0;
     bool sequence = false;
     // stage timing
@@ -184,6 +185,7 @@ void build_table(vd_batch* b, const std::vector<int>& act, StepTables& T, bool a
 Launch make_launch(vd_batch* b, const StepTables& T) {
     Launch L;
     L.nlaunch = &b->launches;
+    L.err = &b->launch_err;
     L.sequence = b->sequence;
     L.s = b->s;
     L.P = b->P;
@@ -543,12 +545,21 @@ vd_status push_fields(vd_batch* b, const std::vector<int>& act, const float* con
     return cuda_status(e);
 }
 
+// status of the step just enqueued: a failed launch, else the runtime's
+// last error
+vd_status step_status(vd_batch* b) {
+    const cudaError_t le = b->launch_err;
+    b->launch_err = cudaSuccess;
+    const cudaError_t e = cudaGetLastError();
+    return cuda_status(le != cudaSuccess ? le : e);
+}
+
 vd_status run_all(vd_batch* b) {
     const Launch L = make_launch(b, b->all);
     b->frames_pushed += 1;
     if (b->timing) {
         enqueue_step(b, L, true);
-        return cuda_status(cudaGetLastError());
+        return step_status(b);
     }
     if (b->use_graph) {
         if (!b->graph) {
@@ -561,6 +572,10 @@ vd_status run_all(vd_batch* b) {
             b->launches = before;
             e = cudaStreamEndCapture(b->s, &g);
             if (e != cudaSuccess) return VD_ERR_CUDA;
+            if (step_status(b)) {
+                cudaGraphDestroy(g);
+                return VD_ERR_CUDA;
+            }
             e = cudaGraphInstantiate(&b->graph, g, 0);
             cudaGraphDestroy(g);
             if (e != cudaSuccess) return VD_ERR_CUDA;
@@ -569,7 +584,7 @@ vd_status run_all(vd_batch* b) {
         return cuda_status(cudaGraphLaunch(b->graph, b->s));
     }
     enqueue_step(b, L, false);
-    return cuda_status(cudaGetLastError());
+    return step_status(b);
 }
 
 vd_status copy_out(void* dst, const void* src, size_t bytes, cudaStream_t s) {
@@ -980,7 +995,7 @@ vd_status vd_batch_push_subset(vd_batch* b, const int32_t* active, int32_t n_act
     build_table(b, act, b->sub, false);
     enqueue_step(b, make_launch(b, b->sub), false);
     b->frames_pushed += 1;
-    return cuda_status(cudaGetLastError());
+    return step_status(b);
 }
 
 vd_status vd_batch_get_changes(vd_batch* b, int32_t i, vd_changes* out) { return get_changes(b, i, out); }

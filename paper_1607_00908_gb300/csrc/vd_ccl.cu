@@ -241,6 +241,7 @@ __device__ __forceinline__ unsigned long long threshold_row(const float* f, int 
 // Pass A: union-find over runs + pieces + borders (one warp per tile)
 // ---------------------------------------------------------------------------
 __global__ __launch_bounds__(32 * CCL_WARPS, 8) void k_ccl_tiles(Pools P, StepTable T) {
+    pdl_enter();
     __shared__ UfSmem s_tile[CCL_WARPS];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int b = blockIdx.x * CCL_WARPS + w;
@@ -398,6 +399,7 @@ __device__ __forceinline__ void punion(const Pools& P, int a, int b) {
 // tile); a position whose piece pair equals the previous position's on the
 // same edge adds nothing and is skipped
 __global__ void k_ccl_merge(Pools P, StepTable T, int total) {
+    pdl_enter();
     __shared__ int s_pre[SEG_CACHE];
     const int* pre = seg_table(T.merge_pre, T.n_act, s_pre);
     const int g = blockIdx.x * blockDim.x + threadIdx.x;
@@ -431,6 +433,7 @@ __global__ void k_ccl_merge(Pools P, StepTable T, int total) {
 
 // root of each piece; roots are counted per instance and marked in the root bitmap
 __global__ void k_ccl_flatten(Pools P) {
+    pdl_enter();
     const int n = min(P.g->n_pieces, P.piece_cap);
     for (int pid = blockIdx.x * blockDim.x + threadIdx.x; pid < n; pid += gridDim.x * blockDim.x) {
         const int r = pfind(P.p_parent, pid);
@@ -448,6 +451,7 @@ __global__ void k_ccl_flatten(Pools P) {
 
 // bubble ids of roots; exact coordinate sums relative to the bubble's first site
 __global__ void k_comp_accum(Pools P) {
+    pdl_enter();
     const int n = min(P.g->n_pieces, P.piece_cap);
     for (int pid = blockIdx.x * blockDim.x + threadIdx.x; pid < n; pid += gridDim.x * blockDim.x) {
         const int inst = P.p_inst[pid];
@@ -486,6 +490,7 @@ __global__ void k_comp_accum(Pools P) {
 // (one warp per piece; warps of a block work on different pieces)
 constexpr int WIDE_WARPS = 4;
 __global__ __launch_bounds__(32 * WIDE_WARPS) void k_comp_wide(Pools P) {
+    pdl_enter();
     __shared__ UfSmem s_tile[WIDE_WARPS];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     UfSmem& TS = s_tile[w];
@@ -539,6 +544,7 @@ __global__ __launch_bounds__(32 * WIDE_WARPS) void k_comp_wide(Pools P) {
 // step and the match state of every now-bubble; every non-root piece takes its
 // bubble id (for the run-label pass)
 __global__ void k_comp_final(Pools P) {
+    pdl_enter();
     const int n = min(P.g->n_pieces, P.piece_cap);
     for (int pid = blockIdx.x * blockDim.x + threadIdx.x; pid < n; pid += gridDim.x * blockDim.x) {
         const int r = P.p_parent[pid];
@@ -573,6 +579,7 @@ __global__ void k_comp_final(Pools P) {
 
 // counting-sort scatter of centroids into bucket order (counts return to zero)
 __global__ void k_bucket_scatter(Pools P) {
+    pdl_enter();
     const int n = min(P.g->n_pieces, P.piece_cap);
     for (int pid = blockIdx.x * blockDim.x + threadIdx.x; pid < n; pid += gridDim.x * blockDim.x) {
         if (P.p_parent[pid] != pid) continue;
@@ -606,6 +613,7 @@ constexpr int WSET = 128;       // per-warp overlap set
 // run lengths over (past label, now label) pairs and no site is visited.
 // ---------------------------------------------------------------------------
 __global__ __launch_bounds__(32 * LBL_WARPS) void k_run_labels(Pools P, StepTable T) {
+    pdl_enter();
     __shared__ int s_lab[LBL_WARPS][RUNS];
     __shared__ unsigned long long s_key[LBL_WARPS][WSET];
     __shared__ unsigned s_cnt[LBL_WARPS][WSET];
@@ -740,33 +748,25 @@ void launch_expand_labels(cudaStream_t s, const Pools& P, int inst, int slot, in
 }
 
 void launch_ccl_tiles(const Launch& L) {
-    k_ccl_tiles<<<(L.total_tilesA + CCL_WARPS - 1) / CCL_WARPS, 32 * CCL_WARPS, 0, L.s>>>(L.P, L.T);
-    ++*L.nlaunch;
+    launch_step(L, k_ccl_tiles, dim3((L.total_tilesA + CCL_WARPS - 1) / CCL_WARPS), dim3(32 * CCL_WARPS), L.P, L.T);
 }
 
 void launch_ccl_rest(const Launch& L) {
     if (L.total_merge > 0) {
-        k_ccl_merge<<<(L.total_merge + 255) / 256, 256, 0, L.s>>>(L.P, L.T, L.total_merge);
-        ++*L.nlaunch;
+        launch_step(L, k_ccl_merge, dim3((L.total_merge + 255) / 256), dim3(256), L.P, L.T, L.total_merge);
     }
-    k_ccl_flatten<<<L.grid_wide, 256, 0, L.s>>>(L.P);
-    ++*L.nlaunch;
+    launch_step(L, k_ccl_flatten, dim3(L.grid_wide), dim3(256), L.P);
     launch_plan(L, 1, ends_bit(SCAN_BUCKETS));
     launch_scan(L, SCAN_ROOTBITS);
-    k_comp_accum<<<L.grid_wide, 256, 0, L.s>>>(L.P);
-    ++*L.nlaunch;
-    k_comp_wide<<<L.grid_items, 32 * WIDE_WARPS, 0, L.s>>>(L.P);
-    ++*L.nlaunch;
-    k_comp_final<<<L.grid_wide, 256, 0, L.s>>>(L.P);
-    ++*L.nlaunch;
+    launch_step(L, k_comp_accum, dim3(L.grid_wide), dim3(256), L.P);
+    launch_step(L, k_comp_wide, dim3(L.grid_items), dim3(32 * WIDE_WARPS), L.P);
+    launch_step(L, k_comp_final, dim3(L.grid_wide), dim3(256), L.P);
     launch_scan(L, SCAN_BUCKETS);
-    k_bucket_scatter<<<L.grid_wide, 256, 0, L.s>>>(L.P);
-    ++*L.nlaunch;
+    launch_step(L, k_bucket_scatter, dim3(L.grid_wide), dim3(256), L.P);
 }
 
 void launch_labels(const Launch& L) {
-    k_run_labels<<<(L.total_tilesA + LBL_WARPS - 1) / LBL_WARPS, 32 * LBL_WARPS, 0, L.s>>>(L.P, L.T);
-    ++*L.nlaunch;
+    launch_step(L, k_run_labels, dim3((L.total_tilesA + LBL_WARPS - 1) / LBL_WARPS), dim3(32 * LBL_WARPS), L.P, L.T);
 }
 
 }  // namespace vd

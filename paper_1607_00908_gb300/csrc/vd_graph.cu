@@ -31,6 +31,7 @@ __device__ __forceinline__ void for_items(const StepTable& T, int which, F f) {
 // step begin / finish
 // ---------------------------------------------------------------------------
 __global__ void k_step_begin(Pools P, StepTable T) {
+    pdl_enter();
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         P.g->n_pieces = 0;
         P.g->n_wide = 0;
@@ -73,6 +74,7 @@ __global__ void k_step_begin(Pools P, StepTable T) {
 }
 
 __global__ void k_step_finish(Pools P, StepTable T) {
+    pdl_enter();
     for (int a = blockIdx.x * blockDim.x + threadIdx.x; a < T.n_act; a += gridDim.x * blockDim.x) {
         const int inst = T.act[a];
         InstState& S = P.st[inst];
@@ -113,6 +115,7 @@ void launch_edge_keys(cudaStream_t s, const Pools& P, int inst, int slot, unsign
 // CSR of the now links
 // ---------------------------------------------------------------------------
 __global__ void k_csr_scatter(Pools P, StepTable T) {
+    pdl_enter();
     for_items(T, PRE_E, [&](int inst, long long j) {
         const InstDesc& D = P.desc[inst];
         if (j >= D.edge_cap) return;
@@ -140,6 +143,7 @@ __device__ __forceinline__ void sort_small(int* v, int n) {
 }
 
 __global__ void k_csr_sort(Pools P, StepTable T) {
+    pdl_enter();
     for_items(T, PRE_K, [&](int inst, long long a) {
         const InstDesc& D = P.desc[inst];
         const int now = P.st[inst].slot ^ 1;
@@ -161,6 +165,7 @@ __device__ __forceinline__ int unpack_label(unsigned long long v) {
 }
 
 __global__ void k_match_best(Pools P, StepTable T) {
+    pdl_enter();
     for_items(T, PRE_O, [&](int inst, long long j) {
         const InstDesc& D = P.desc[inst];
         const int slot = P.olist[D.ovl_off + j];
@@ -178,6 +183,7 @@ __global__ void k_match_best(Pools P, StepTable T) {
 }
 
 __global__ void k_match_phi(Pools P, StepTable T) {
+    pdl_enter();
     for_items(T, PRE_KP, [&](int inst, long long p) {
         const InstDesc& D = P.desc[inst];
         const unsigned long long v = P.best_n[D.comp_off + p];
@@ -200,6 +206,7 @@ __global__ void k_match_phi(Pools P, StepTable T) {
 // translation of the past links into now labels, then a sorted CSR of them
 // ---------------------------------------------------------------------------
 __global__ void k_translate_count(Pools P, StepTable T) {
+    pdl_enter();
     for_items(T, PRE_KP, [&](int inst, long long a) {
         const InstDesc& D = P.desc[inst];
         const InstState& S = P.st[inst];
@@ -220,6 +227,7 @@ __global__ void k_translate_count(Pools P, StepTable T) {
 }
 
 __global__ void k_translate_scatter(Pools P, StepTable T) {
+    pdl_enter();
     for_items(T, PRE_KP, [&](int inst, long long a) {
         const InstDesc& D = P.desc[inst];
         const InstState& S = P.st[inst];
@@ -239,6 +247,7 @@ __global__ void k_translate_scatter(Pools P, StepTable T) {
 }
 
 __global__ void k_tcsr_sort(Pools P, StepTable T) {
+    pdl_enter();
     for_items(T, PRE_K, [&](int inst, long long a) {
         const InstDesc& D = P.desc[inst];
         const int* ro = P.trowoff + D.comp_off;
@@ -309,10 +318,12 @@ __device__ __forceinline__ void compare_row(const Pools& P, int inst, int a) {
 }
 
 __global__ void k_flip_count(Pools P, StepTable T) {
+    pdl_enter();
     for_items(T, PRE_K, [&](int inst, long long a) { compare_row<false>(P, inst, (int)a); });
 }
 
 __global__ void k_flip_write(Pools P, StepTable T) {
+    pdl_enter();
     for_items(T, PRE_K, [&](int inst, long long a) { compare_row<true>(P, inst, (int)a); });
 }
 
@@ -345,18 +356,14 @@ void launch_graph_prep(const Launch& L) {
 
 void launch_graph_csr(const Launch& L) {
     launch_scan(L, SCAN_DEG);
-    k_csr_scatter<<<L.grid_wide, 256, 0, L.s>>>(L.P, L.T);
-    ++*L.nlaunch;
-    k_csr_sort<<<L.grid_wide, 256, 0, L.s>>>(L.P, L.T);
-    ++*L.nlaunch;
+    launch_step(L, k_csr_scatter, dim3(L.grid_wide), dim3(256), L.P, L.T);
+    launch_step(L, k_csr_sort, dim3(L.grid_wide), dim3(256), L.P, L.T);
 }
 
 void launch_graph_match(const Launch& L) {
     const int g = L.grid_wide;
-    k_match_best<<<g, 256, 0, L.s>>>(L.P, L.T);
-    ++*L.nlaunch;
-    k_match_phi<<<g, 256, 0, L.s>>>(L.P, L.T);
-    ++*L.nlaunch;
+    launch_step(L, k_match_best, dim3(g), dim3(256), L.P, L.T);
+    launch_step(L, k_match_phi, dim3(g), dim3(256), L.P, L.T);
 }
 
 // The translation reads the past frame's CSR, which in a frame sequence is the
@@ -364,34 +371,27 @@ void launch_graph_match(const Launch& L) {
 // the match and the CSR chain.
 void launch_graph_translate(const Launch& L) {
     const int g = L.grid_wide;
-    k_translate_count<<<g, 256, 0, L.s>>>(L.P, L.T);
-    ++*L.nlaunch;
+    launch_step(L, k_translate_count, dim3(g), dim3(256), L.P, L.T);
     launch_plan(L, 0, ends_bit(SCAN_TDEG), pre_bit(PRE_ET));
     launch_scan(L, SCAN_TDEG);
-    k_translate_scatter<<<g, 256, 0, L.s>>>(L.P, L.T);
-    ++*L.nlaunch;
-    k_tcsr_sort<<<g, 256, 0, L.s>>>(L.P, L.T);
-    ++*L.nlaunch;
+    launch_step(L, k_translate_scatter, dim3(g), dim3(256), L.P, L.T);
+    launch_step(L, k_tcsr_sort, dim3(g), dim3(256), L.P, L.T);
 }
 
 void launch_graph_flips(const Launch& L) {
     const int g = L.grid_wide;
-    k_flip_count<<<g, 256, 0, L.s>>>(L.P, L.T);
-    ++*L.nlaunch;
+    launch_step(L, k_flip_count, dim3(g), dim3(256), L.P, L.T);
     launch_plan(L, 0, ends_bit(SCAN_FLIPS) | ends_bit(SCAN_FLIPS_A), pre_bit(PRE_FB) | pre_bit(PRE_FA));
     launch_scan(L, SCAN_FLIPS);
     launch_scan(L, SCAN_FLIPS_A);
-    k_flip_write<<<g, 256, 0, L.s>>>(L.P, L.T);
-    ++*L.nlaunch;
+    launch_step(L, k_flip_write, dim3(g), dim3(256), L.P, L.T);
 }
 
 void launch_begin(const Launch& L) {
-    k_step_begin<<<1, 256, 0, L.s>>>(L.P, L.T);
-    ++*L.nlaunch;
+    launch_step(L, k_step_begin, dim3(1), dim3(256), L.P, L.T);
 }
 void launch_finish(const Launch& L) {
-    k_step_finish<<<1, 256, 0, L.s>>>(L.P, L.T);
-    ++*L.nlaunch;
+    launch_step(L, k_step_finish, dim3(1), dim3(256), L.P, L.T);
 }
 
 }  // namespace vd

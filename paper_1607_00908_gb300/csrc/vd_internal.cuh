@@ -411,6 +411,7 @@ __device__ __forceinline__ void ovl_global_insert(const Pools& P, const InstDesc
 // ---------------------------------------------------------------------------
 struct Launch {
     long long* nlaunch;  // host counter of kernel launches
+    cudaError_t* err;    // first launch error of the step (host)
     bool sequence;       // some instance's past frame is produced in the same step
     cudaStream_t s;
     Pools P;
@@ -420,6 +421,31 @@ struct Launch {
     long long total_words;
     int grid_wide;               // blocks for kernels with one thread per item (pieces, bubbles, links)
 };
+
+// Kernels of a step are launched with programmatic dependent launch, so the
+// launch of a kernel overlaps the end of the previous one; every step kernel
+// begins with pdl_enter(), which waits until the previous kernel has
+// completed and its memory is visible. No step kernel touches memory before
+// pdl_enter().
+__device__ __forceinline__ void pdl_enter() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+void launch_step(const Launch& L, void (*kernel)(KArgs...), dim3 grid, dim3 block, Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = L.s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    const cudaError_t e = cudaLaunchKernelEx(&cfg, kernel, args...);
+    if (e != cudaSuccess && L.err && *L.err == cudaSuccess) *L.err = e;
+    ++*L.nlaunch;
+}
+
 
 void launch_ccl_tiles(const Launch& L);    // threshold + tile union-find (pass A)
 void launch_ccl_rest(const Launch& L);     // border merge, ranks, centroids, bucket grid

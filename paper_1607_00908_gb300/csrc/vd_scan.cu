@@ -19,6 +19,7 @@ namespace vd {
 constexpr int PLAN_THREADS = 256;
 
 __global__ __launch_bounds__(PLAN_THREADS) void k_plan(Pools P, StepTable T, int with_comp, int ends, int pre_mask) {
+    pdl_enter();
     // one block: thread per instance, block scans for the prefixes
     __shared__ long long s_v[NPRE][PLAN_THREADS];
     __shared__ long long s_carry[NPRE];
@@ -152,6 +153,7 @@ __device__ __forceinline__ void publish(unsigned long long* f, unsigned epoch, u
 }
 
 __global__ __launch_bounds__(SCAN_THREADS) void k_scan(Pools P, StepTable T, int kind) {
+    pdl_enter();
     __shared__ int s_tile;
     __shared__ long long s_pre[SEG_CACHE];
     __shared__ int s_warp[SCAN_THREADS / 32];
@@ -280,14 +282,12 @@ __global__ __launch_bounds__(SCAN_THREADS) void k_scan(Pools P, StepTable T, int
 }
 
 void launch_plan(const Launch& L, int with_comp, int ends, int pre_mask) {
-    k_plan<<<1, PLAN_THREADS, 0, L.s>>>(L.P, L.T, with_comp, ends, pre_mask);
-    ++*L.nlaunch;
+    launch_step(L, k_plan, dim3(1), dim3(PLAN_THREADS), L.P, L.T, with_comp, ends, pre_mask);
 }
 
 void launch_scan(const Launch& L, ScanKind kind) {
     int grid = L.grid_items;
-    k_scan<<<grid, SCAN_THREADS, 0, L.s>>>(L.P, L.T, (int)kind);
-    ++*L.nlaunch;
+    launch_step(L, k_scan, dim3(grid), dim3(SCAN_THREADS), L.P, L.T, (int)kind);
 }
 
 }  // namespace vd

@@ -129,6 +129,7 @@ __device__ __forceinline__ float far2_ru(int d, int lo, int hi, int halfM) {
 //     are within 2^-15 relative of each other the site is decided exactly in
 //     int64 (ties to the smallest label).
 __global__ __launch_bounds__(32 * VWARPS) void k_voronoi(Pools P, StepTable T) {
+    pdl_enter();
     __shared__ int s_cx[VWARPS][WSCAN], s_cy[VWARPS][WSCAN], s_id[VWARPS][WSCAN];
     __shared__ float2 s_fc[VWARPS][WCAND];
     __shared__ int s_kk[VWARPS][WCAND];
@@ -466,6 +467,7 @@ __device__ __forceinline__ void cp_async16(int* smem, const int* gmem) {
 }
 
 __global__ __launch_bounds__(32 * LINK_WARPS) void k_links(Pools P, StepTable T) {
+    pdl_enter();
     __shared__ __align__(16) int s_own[LINK_WARPS][(VH + 1) * LS];
     __shared__ unsigned long long s_list[LINK_WARPS][LSET];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -571,6 +573,7 @@ __global__ __launch_bounds__(32 * LINK_WARPS) void k_links(Pools P, StepTable T)
 // appended links -> link hash (+ degrees); appended pairs -> overlap hash
 
 __global__ void k_merge_lists(Pools P, StepTable T) {
+    pdl_enter();
     __shared__ long long s_pe[SEG_CACHE], s_po[SEG_CACHE];
     const long long* pe = seg_table(pre_arr(T, PRE_EA), T.n_act, s_pe);
     const long long* po = seg_table(pre_arr(T, PRE_OA), T.n_act, s_po);
@@ -595,18 +598,15 @@ __global__ void k_merge_lists(Pools P, StepTable T) {
 
 void launch_merge_lists(const Launch& L) {
     launch_plan(L, 0, ENDS_NONE);
-    k_merge_lists<<<L.grid_wide, 256, 0, L.s>>>(L.P, L.T);
-    ++*L.nlaunch;
+    launch_step(L, k_merge_lists, dim3(L.grid_wide), dim3(256), L.P, L.T);
 }
 
 void launch_voronoi(const Launch& L) {
-    k_voronoi<<<(L.total_tilesV + VWARPS - 1) / VWARPS, 32 * VWARPS, 0, L.s>>>(L.P, L.T);
-    ++*L.nlaunch;
+    launch_step(L, k_voronoi, dim3((L.total_tilesV + VWARPS - 1) / VWARPS), dim3(32 * VWARPS), L.P, L.T);
 }
 
 void launch_links(const Launch& L) {
-    k_links<<<(L.total_tilesV + LINK_WARPS - 1) / LINK_WARPS, 32 * LINK_WARPS, 0, L.s>>>(L.P, L.T);
-    ++*L.nlaunch;
+    launch_step(L, k_links, dim3((L.total_tilesV + LINK_WARPS - 1) / LINK_WARPS), dim3(32 * LINK_WARPS), L.P, L.T);
 }
 
 }  // namespace vd
