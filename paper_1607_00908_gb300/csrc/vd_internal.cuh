@@ -86,7 +86,8 @@ struct InstState {
     int Kb[2];               // bubbles of the frame stored in each buffer
     int Eb[2];               // links of the frame stored in each buffer
     long long frame;         // index of the frame in progress / last finished
-    int K, K_prev;           // bubbles now / previous frame
+    int K, K_prev;           // bubbles now (clamped to the capacity) / previous frame
+    int K_roots;             // roots found by labelling this step, before clamping
     int E, E_prev;           // links now / previous frame
     int B, nbx, nby;         // bucket grid
     int n_matched;
@@ -211,6 +212,7 @@ enum PreIdx : int {
     PRE_FA,         // arising links
     PRE_EA,         // appended links
     PRE_OA,         // appended overlap pairs
+    PRE_KR,         // roots found by labelling (bubbles before clamping to the capacity)
     NPRE
 };
 constexpr int PRE_ALL = (1 << NPRE) - 1;

@@ -37,6 +37,7 @@ __global__ __launch_bounds__(PLAN_THREADS) void k_plan(Pools P, StepTable T, int
             const InstDesc& D = P.desc[inst];
             if (with_comp) {
                 int K = S.K;
+                S.K_roots = K;   // every root is ranked, also past the capacity
                 if (K > D.comp_cap) {
                     S.err |= ERR_COMP_CAP;
                     K = D.comp_cap;
@@ -72,6 +73,7 @@ __global__ __launch_bounds__(PLAN_THREADS) void k_plan(Pools P, StepTable T, int
             v[PRE_FA] = S.n_arise;
             v[PRE_EA] = S.n_eapp < D.edge_cap ? S.n_eapp : D.edge_cap;
             v[PRE_OA] = S.n_oapp < D.ovl_cap ? S.n_oapp : D.ovl_cap;
+            v[PRE_KR] = S.K_roots;
             // end values of the offset arrays (off[size] = total) of the scans that follow
             const int now = S.slot ^ 1;
             if (ends & ends_bit(SCAN_BUCKETS)) P.boff[D.bucket_off + (long long)S.nbx * S.nby] = S.K;
@@ -110,7 +112,7 @@ struct ScanSel {
 
 __device__ __forceinline__ ScanSel scan_sel(int kind) {
     switch (kind) {
-        case SCAN_ROOTBITS: return {-1, PRE_K};
+        case SCAN_ROOTBITS: return {-1, PRE_KR};   // ranks count every root, clamped or not
         case SCAN_BUCKETS: return {PRE_NB, PRE_K};
         case SCAN_DEG: return {PRE_K, PRE_E};
         case SCAN_TDEG: return {PRE_K, PRE_ET};

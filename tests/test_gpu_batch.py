@@ -148,3 +148,42 @@ def test_push_staged_needs_a_stage():
         b.push_staged()
     assert e.value.status == vd.VD_ERR_STATE
     b.close()
+
+
+def test_staged_uneven_batch_with_a_failing_instance():
+    """Uneven batch fed through the staged host path; one instance overflows
+    its bubble capacity: vd_batch_get_changes_all reports VD_ERR_CAPACITY for
+    it, packs only the others' lists, and those equal the oracle."""
+    specs = [(96, 80, 2.5), (64, 64, 0.0), (120, 120, 3.0)]
+    n_frames = 3
+    cap = 100
+    checker = ((np.indices((64, 64)).sum(0) % 2) == 0).astype(np.float32)   # 2048 bubbles > cap
+    seqs = []
+    for k, (lx, ly, s) in enumerate(specs):
+        seqs.append([checker] * n_frames if s == 0.0 else frames_for(ly, s, 60 + k, n_frames, Lx=lx))
+    host = [[torch.from_numpy(np.ascontiguousarray(F)).pin_memory() for F in seq] for seq in seqs]
+    b = vd.Batch([(lx, ly) for lx, ly, _ in specs], max_components=cap)
+    refs = {i: O.Detector(lx, ly, voronoi="brute") for i, (lx, ly, s) in enumerate(specs) if s != 0.0}
+    for f in range(n_frames):
+        b.stage_host_ptrs([host[i][f].data_ptr() for i in range(len(specs))])
+        b.push_staged()
+        allc = b.changes_all()
+        assert allc["status"][1] == vd.VD_ERR_CAPACITY
+        assert allc["n_breaking"][1] == 0 and allc["n_arising"][1] == 0 and allc["n_now"][1] == 0
+        ob = oa = ok = 0
+        for i, ref in refs.items():
+            r = ref.push(seqs[i][f])
+            assert allc["status"][i] == vd.VD_OK
+            nb, na, nk = allc["n_breaking"][i], allc["n_arising"][i], allc["n_now"][i]
+            assert nk == r["K"]
+            assert np.array_equal(allc["breaking"][ob:ob + nb], r["breaking"]), (f, i)
+            assert np.array_equal(allc["breaking_prev"][ob:ob + nb], r["breaking_prev"]), (f, i)
+            assert np.array_equal(allc["arising"][oa:oa + na], r["arising"]), (f, i)
+            assert np.array_equal(allc["active"][ok:ok + nk], r["active"]), (f, i)
+            check(b, i, r, f"inst {i} frame {f}")
+            ob, oa, ok = ob + nb, oa + na, ok + nk
+        assert (ob, oa, ok) == (len(allc["breaking"]), len(allc["arising"]), len(allc["active"]))
+        with pytest.raises(vd.VdError) as e:
+            b.changes(1)
+        assert e.value.status == vd.VD_ERR_CAPACITY
+    b.close()
