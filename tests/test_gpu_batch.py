@@ -187,3 +187,23 @@ def test_staged_uneven_batch_with_a_failing_instance():
             b.changes(1)
         assert e.value.status == vd.VD_ERR_CAPACITY
     b.close()
+
+
+def test_batch_with_degenerate_instances():
+    """Empty field (no bubble), one bubble covering the whole torus, one
+    single-site bubble, and ordinary noise advance in one batch; each equals
+    the oracle run alone."""
+    L = 48
+    empty = np.zeros((L, L), np.float32)
+    full = np.ones((L, L), np.float32)
+    dot = np.zeros((L, L), np.float32)
+    dot[7, 11] = 1.0
+    noise = frames_for(L, 2.0, 77, 2)
+    seqs = [[empty, empty], [full, full], [dot, dot], noise, [empty, full]]
+    b = vd.Batch([(L, L)] * len(seqs))
+    refs = [O.Detector(L, L, voronoi="brute") for _ in seqs]
+    for f in range(2):
+        b.push([torch.from_numpy(np.ascontiguousarray(s[f])).cuda() for s in seqs])
+        for i, ref in enumerate(refs):
+            check(b, i, ref.push(seqs[i][f]), f"inst {i} frame {f}")
+    b.close()
