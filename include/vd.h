@@ -184,10 +184,10 @@ vd_status vd_batch_create_sequence(const vd_config* cfg, int32_t n_frames, vd_ba
 /* `d_fields` is a HOST array of n device pointers (each Ly*pitch floats,
  * pitch = Lx); instance i reads d_fields[i]. Enqueues one step. */
 vd_status vd_batch_push(vd_batch* b, const float* const* d_fields);
-/* Same with HOST fields (h_fields[i]: Ly*Lx floats, row-major): each is
- * copied into a batch-owned device buffer on the batch stream, then the step
- * is enqueued. Pinned host memory makes the copies asynchronous; the caller
- * keeps the host arrays unchanged until the stream has consumed them. */
+/* Same with HOST fields (h_fields[i]: Ly*Lx floats, row-major): equivalent to
+ * vd_batch_stage_host followed by vd_batch_push_staged (below). Pinned host
+ * memory makes the copies asynchronous; the caller keeps the host arrays
+ * unchanged until the step has been queried. */
 vd_status vd_batch_push_host(vd_batch* b, const float* const* h_fields);
 /* Advance only the `n_active` instances listed in `active` (host array of
  * instance ids, each at most once); the others keep their state. */

@@ -735,7 +735,7 @@ vd_status vd_create(const vd_config* cfg, vd_ctx** out) {
     vd_status r = create_batch(cfg, 1, &b);
     if (r) return r;
     // graph replay needs a capturable stream (not the legacy default stream)
-    b->use_graph = (cfg->stream != nullptr) && !getenv("VD_NO_GRAPH");
+    b->use_graph = (cfg->stream != nullptr);
     vd_ctx* c = new (std::nothrow) vd_ctx();
     if (!c) {
         b->mem.release();
@@ -847,7 +847,7 @@ vd_status vd_destroy(vd_ctx* ctx) {
 
 vd_status vd_batch_create(const vd_config* cfgs, int32_t n, vd_batch** out) {
     vd_status r = create_batch(cfgs, n, out);
-    if (!r) (*out)->use_graph = (cfgs[0].stream != nullptr) && !getenv("VD_NO_GRAPH");
+    if (!r) (*out)->use_graph = (cfgs[0].stream != nullptr);
     return r;
 }
 
@@ -855,7 +855,7 @@ vd_status vd_batch_create_sequence(const vd_config* cfg, int32_t n_frames, vd_ba
     if (!cfg || n_frames < 1 || !out) return VD_ERR_INVALID;
     std::vector<vd_config> cfgs(n_frames, *cfg);
     vd_status r = create_batch(cfgs.data(), n_frames, out, true);
-    if (!r) (*out)->use_graph = (cfg->stream != nullptr) && !getenv("VD_NO_GRAPH");
+    if (!r) (*out)->use_graph = (cfg->stream != nullptr);
     return r;
 }
 

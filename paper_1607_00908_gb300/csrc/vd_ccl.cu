@@ -62,12 +62,6 @@ __device__ __forceinline__ unsigned long long run_starts(unsigned long long m) {
 __device__ __forceinline__ unsigned long long upto(int c) { return c == 63 ? ~0ull : ((2ull << c) - 1ull); }
 // index of the run of row mask m (starts S) that contains column c (bit c set)
 __device__ __forceinline__ int run_index(unsigned long long S, int c) { return __popcll(S & upto(c)) - 1; }
-// column of the j-th run start (0-based)
-__device__ __forceinline__ int run_column(unsigned long long S, int j) {
-    const unsigned lo = (unsigned)S, hi = (unsigned)(S >> 32);
-    const int nlo = __popc(lo);
-    return j < nlo ? (int)__fns(lo, 0, j + 1) : 32 + (int)__fns(hi, 0, j - nlo + 1);
-}
 __device__ __forceinline__ int run_length(unsigned long long m, int c) {
     const unsigned long long inv = ~(m >> c);
     return inv ? __ffsll(inv) - 1 : 64;   // all ones only when c == 0

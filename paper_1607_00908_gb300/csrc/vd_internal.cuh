@@ -259,10 +259,6 @@ __device__ __forceinline__ int seg_of(const long long* pre, int n_act, long long
 __device__ __forceinline__ int seg_of_int(const int* pre, int n_act, int g) {
     return upper_bound_int(pre, n_act + 1, g) - 1;
 }
-__device__ __forceinline__ int seg_of_any(const long long* pre, int n_act, long long g) { return seg_of(pre, n_act, g); }
-__device__ __forceinline__ int seg_of_any(const int* pre, int n_act, long long g) {
-    return seg_of_int(pre, n_act, (int)g);
-}
 
 // A block's copy of a segment prefix table (n_act + 1 entries) in shared
 // memory, loaded in one round, so that item -> instance searches do not chain
@@ -289,30 +285,6 @@ __device__ __forceinline__ unsigned long long hash64(unsigned long long k) {
 // cheap 32-bit hash of a (lo, hi) key for small shared-memory sets
 __device__ __forceinline__ unsigned hash_small(unsigned long long k) {
     return ((unsigned)k * 0x9E3779B1u) ^ ((unsigned)(k >> 32) * 0x85EBCA77u);
-}
-
-// Warp-cooperative insert of per-lane keys (EMPTY_KEY = none) into a shared
-// open-addressing set of `cap` slots (power of two). All lanes first probe
-// read-only (almost every key is already present); keys not found are merged
-// across the warp and inserted by one lane each. Returns false for a lane
-// whose key could not be placed (set full).
-__device__ __forceinline__ bool warp_set_insert(unsigned long long* set, int cap, unsigned long long key) {
-    const int lane = threadIdx.x & 31;
-    if (!__any_sync(0xffffffffu, key != EMPTY_KEY)) return true;
-    unsigned h = hash_small(key) & (cap - 1);
-    const bool pending = key != EMPTY_KEY && set[h] != key;
-    if (!__any_sync(0xffffffffu, pending)) return true;
-    const unsigned grp = __match_any_sync(0xffffffffu, pending ? key : EMPTY_KEY);
-    bool ok = true;
-    if (pending && lane == __ffs(grp) - 1) {
-        ok = false;
-        for (int probe = 0; probe < cap; ++probe) {
-            const unsigned long long o = atomicCAS(&set[h], EMPTY_KEY, key);
-            if (o == EMPTY_KEY || o == key) { ok = true; break; }
-            h = (h + 1) & (cap - 1);
-        }
-    }
-    return ok;
 }
 
 // Warp-cooperative add of per-lane (key, count) pairs into a shared counted
