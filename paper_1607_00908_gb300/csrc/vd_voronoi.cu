@@ -2,13 +2,16 @@
 //
 // owner(s) = argmin_i |1024*s - c_i|^2 over all bubble centres (exact int64,
 // minimum image on the torus, ties to the smallest label). The paper computes
-// this by scanning every centre from every site; here each 32 x 32 tile first
-// collects a provably complete candidate set from a bucket grid of centres:
-//   U     = min over scanned centres of an upper bound of their largest
-//           distance to the tile (so every site has a centre within U),
-//   keep  = centres whose smallest distance to the tile is <= U,
+// this by scanning every centre from every site; here each 64 x 32 tile first
+// collects a provably complete candidate set from a bucket grid of centres,
+// and each 16 x 8 patch of it keeps only the centres that can own one of its
+// sites:
+//   U_p   = min over scanned centres of an upper bound of their largest
+//           distance to patch p (so every site of p has a centre within U_p),
+//   keep  = centres whose smallest distance to the patch is <= U_p,
 // scanning rings of buckets around the tile until the unscanned region is
-// farther than sqrt(U). Each site then scans only the kept candidates.
+// farther than sqrt(max_p U_p). Each site then scans only its patch's kept
+// candidates.
 //
 // Links: a link {a, b} joins owners that meet where a site and its +x or +y
 // neighbour differ, and for a 2x2 plaquette with four distinct owners the
@@ -85,9 +88,10 @@ __device__ __forceinline__ void edge_global_insert(const Pools& P, const InstDes
 }
 
 
-constexpr int VWARPS = 4;        // tiles per block, one warp each
-constexpr int PW = 16, PH = 8;   // patch: a 32 x 32 tile holds 2 x 4 patches
-constexpr int WSCAN = 256;       // per-warp list of scanned centres
+constexpr int VWARPS = 2;        // tiles per block, one warp each
+constexpr int PW = 16, PH = 8;   // patch
+constexpr int NPX = TW / PW, NPY = TH / PH, NPATCH = NPX * NPY;   // a 64 x 32 tile holds 4 x 4 patches
+constexpr int WSCAN = 384;       // per-warp list of scanned centres
 constexpr int WCAND = 64;        // per-patch list of kept candidates (index fits 6 bits)
 
 // Exact owner over a candidate list with int64 distances (coordinates
@@ -114,9 +118,11 @@ __device__ __forceinline__ float far2_ru(int d, int lo, int hi, int halfM) {
     return __fmul_ru(f, f);
 }
 
-// One warp per 32 x 32 tile, no block-level synchronisation.
+// One warp per 64 x 32 tile (the labelling tiles), no block-level
+// synchronisation; two tiles per block and 64 registers, so that small frames
+// still spread over the SMs.
 //  1. Ring search over the bucket grid around the tile. For each of the
-//     tile's eight 16 x 8 patches, U_p = min over scanned centres of an upper
+//     tile's sixteen 16 x 8 patches, U_p = min over scanned centres of an upper
 //     bound of their largest squared distance to the patch (float32 rounded
 //     up), so every site of patch p has a centre within sqrt(U_p). The search
 //     stops when the unscanned region is farther than sqrt(max_p U_p) from
@@ -128,15 +134,16 @@ __device__ __forceinline__ float far2_ru(int d, int lo, int hi, int halfM) {
 //     index in the low 6 bits give the nearest and second-nearest; when they
 //     are within 2^-15 relative of each other the site is decided exactly in
 //     int64 (ties to the smallest label).
-__global__ __launch_bounds__(32 * VWARPS) void k_voronoi(Pools P, StepTable T) {
+__global__ __launch_bounds__(32 * VWARPS, 16) void k_voronoi(Pools P, StepTable T) {
     pdl_enter();
     __shared__ int s_cx[VWARPS][WSCAN], s_cy[VWARPS][WSCAN], s_id[VWARPS][WSCAN];
     __shared__ float2 s_fc[VWARPS][WCAND];
     __shared__ int s_kk[VWARPS][WCAND];
+    __shared__ float s_U[VWARPS][NPATCH];
     __shared__ int s_tpre[SEG_CACHE];
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int* tpre = seg_table(T.tileV_pre, T.n_act, s_tpre);
+    const int* tpre = seg_table(T.tileA_pre, T.n_act, s_tpre);
     const int b = blockIdx.x * VWARPS + warp;
     if (b >= tpre[T.n_act]) return;
     const int a = seg_of_int(tpre, T.n_act, b);
@@ -144,10 +151,10 @@ __global__ __launch_bounds__(32 * VWARPS) void k_voronoi(Pools P, StepTable T) {
     const InstDesc& D = P.desc[inst];
     const InstState& S = P.st[inst];
     const int t = b - tpre[a];
-    const int tx = t % D.vtx, ty = t / D.vtx;
+    const int tx = t % D.ntx, ty = t / D.ntx;
     const int Lx = D.Lx, Ly = D.Ly;
-    const int x0 = tx * VW, y0 = ty * VH;
-    const int ncols = min(VW, Lx - x0), nrows = min(VH, Ly - y0);
+    const int x0 = tx * TW, y0 = ty * TH;
+    const int ncols = min(TW, Lx - x0), nrows = min(TH, Ly - y0);
     const int K = min(S.K, D.comp_cap);
     int* own = P.owners + D.site_off;
     if (K <= 0) {
@@ -163,9 +170,8 @@ __global__ __launch_bounds__(32 * VWARPS) void k_voronoi(Pools P, StepTable T) {
     const long long MX = (long long)Q * Lx, MY = (long long)Q * Ly;
     const long long X0 = (long long)Q * x0, Y0 = (long long)Q * y0;
     const int hMX = (int)(MX >> 1), hMY = (int)(MY >> 1);
-    // patch extents relative to the tile origin (Q units); patch p = 2 * pyi + pxi
-    const int xlo0 = 0, xhi0 = Q * (min(PW, ncols) - 1);
-    const int xlo1 = Q * PW, xhi1 = Q * (ncols - 1);
+    // patch p = NPX * pyi + pxi covers columns [PW * pxi, PW * (pxi + 1)) and
+    // rows [PH * pyi, PH * (pyi + 1)) of the tile, clipped to it
     const int Bk = S.B, nbx = S.nbx, nby = S.nby;
     const int bx0 = x0 / Bk, bx1 = (x0 + ncols - 1) / Bk;
     const int by0 = y0 / Bk, by1 = (y0 + nrows - 1) / Bk;
@@ -175,9 +181,9 @@ __global__ __launch_bounds__(32 * VWARPS) void k_voronoi(Pools P, StepTable T) {
     int* cxs = s_cx[warp];
     int* cys = s_cy[warp];
     int* ids = s_id[warp];
-    float Up[8];
+    float Up[NPATCH];
 #pragma unroll
-    for (int p = 0; p < 8; ++p) Up[p] = INFINITY;
+    for (int p = 0; p < NPATCH; ++p) Up[p] = INFINITY;
     int qx0 = 0, qx1 = -1, qy0 = 0, qy1 = -1;   // previous round's region
     bool qfx = false, qfy = false, have_prev = false;
     int rx0, rx1, ry0, ry1;
@@ -222,13 +228,17 @@ __global__ __launch_bounds__(32 * VWARPS) void k_voronoi(Pools P, StepTable T) {
                 const int2 cc = bcq[j];
                 const int ddx = (int)wrapM((long long)cc.x - X0, MX);
                 const int ddy = (int)wrapM((long long)cc.y - Y0, MY);
-                const float fx0 = far2_ru(ddx, xlo0, xhi0, hMX), fx1 = far2_ru(ddx, xlo1, xhi1, hMX);
+                float fxs[NPX];
 #pragma unroll
-                for (int pyi = 0; pyi < 4; ++pyi) {
+                for (int pxi = 0; pxi < NPX; ++pxi)
+                    fxs[pxi] = far2_ru(ddx, Q * PW * pxi, Q * (min(PW * (pxi + 1), ncols) - 1), hMX);
+#pragma unroll
+                for (int pyi = 0; pyi < NPY; ++pyi) {
                     const int ylo = Q * PH * pyi, yhi = Q * (min(PH * (pyi + 1), nrows) - 1);
                     const float fy = far2_ru(ddy, ylo, yhi, hMY);
-                    Up[2 * pyi] = fminf(Up[2 * pyi], __fadd_ru(fx0, fy));
-                    Up[2 * pyi + 1] = fminf(Up[2 * pyi + 1], __fadd_ru(fx1, fy));
+#pragma unroll
+                    for (int pxi = 0; pxi < NPX; ++pxi)
+                        Up[NPX * pyi + pxi] = fminf(Up[NPX * pyi + pxi], __fadd_ru(fxs[pxi], fy));
                 }
                 if (pos < WSCAN) {
                     cxs[pos] = ddx;
@@ -239,10 +249,10 @@ __global__ __launch_bounds__(32 * VWARPS) void k_voronoi(Pools P, StepTable T) {
         }
         float Umax = 0.f;
 #pragma unroll
-        for (int p = 0; p < 8; ++p) {
+        for (int p = 0; p < NPATCH; ++p) {
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) Up[p] = fminf(Up[p], __shfl_xor_sync(0xffffffffu, Up[p], o));
-            const bool valid = PW * (p & 1) < ncols && PH * (p >> 1) < nrows;
+            const bool valid = PW * (p % NPX) < ncols && PH * (p / NPX) < nrows;
             if (valid) Umax = fmaxf(Umax, Up[p]);
         }
         if (fx && fy) break;
@@ -263,6 +273,10 @@ __global__ __launch_bounds__(32 * VWARPS) void k_voronoi(Pools P, StepTable T) {
         // double product is within 2^-53 of g^2, so the margin makes it exact
         if (g > 0 && (double)g * (double)g > (double)Umax * (1.0 + 1.0 / (1ll << 50))) break;
         qx0 = rx0; qx1 = rx1; qy0 = ry0; qy1 = ry1; qfx = fx; qfy = fy; have_prev = true;
+    }
+    if (lane == 0) {
+#pragma unroll
+        for (int p = 0; p < NPATCH; ++p) s_U[warp][p] = Up[p];
     }
     __syncwarp();
 
@@ -287,15 +301,13 @@ __global__ __launch_bounds__(32 * VWARPS) void k_voronoi(Pools P, StepTable T) {
         int* kk = s_kk[warp];
         const int c = lane & 15, rb = 4 * (lane >> 4);   // this lane: column c, rows rb..rb+3 of the patch
 #pragma unroll 1
-        for (int p = 0; p < 8; ++p) {
-            const int pxo = PW * (p & 1), pyo = PH * (p >> 1);
+        for (int p = 0; p < NPATCH; ++p) {
+            const int pxo = PW * (p % NPX), pyo = PH * (p / NPX);
             if (pxo >= ncols || pyo >= nrows) continue;   // warp-uniform
             const int pw = min(PW, ncols - pxo), ph = min(PH, nrows - pyo);
             const int xlo = Q * pxo, xhi = Q * (pxo + pw - 1);
             const int ylo = Q * pyo, yhi = Q * (pyo + ph - 1);
-            float Uq = Up[0];
-#pragma unroll
-            for (int q = 1; q < 8; ++q) Uq = (q == p) ? Up[q] : Uq;
+            const float Uq = s_U[warp][p];
             // ---- 2a. keep the scanned centres within sqrt(U_p) of the patch ----
             int nk = 0;
             __syncwarp();
@@ -602,7 +614,7 @@ void launch_merge_lists(const Launch& L) {
 }
 
 void launch_voronoi(const Launch& L) {
-    launch_step(L, k_voronoi, dim3((L.total_tilesV + VWARPS - 1) / VWARPS), dim3(32 * VWARPS), L.P, L.T);
+    launch_step(L, k_voronoi, dim3((L.total_tilesA + VWARPS - 1) / VWARPS), dim3(32 * VWARPS), L.P, L.T);
 }
 
 void launch_links(const Launch& L) {
