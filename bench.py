@@ -51,7 +51,7 @@ METRIC_BYTES_PER_SITE = 16.0
 # (profiles/launches_c1_sequence.txt); scaled to the bench launch for
 # roofline.traffic. A stage not captured, or whose kernels changed since the
 # capture, reports null.
-TRAFFIC_BYTES_PER_SITE = {0: 5.099, 2: 2.847, 3: 3.136, 4: 4.327}
+TRAFFIC_BYTES_PER_SITE = {0: 5.100, 2: 2.845, 3: 3.422, 4: 4.326}
 
 
 def workload(name: str, n_frames: int | None):
