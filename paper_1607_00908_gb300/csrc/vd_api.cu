@@ -57,12 +57,12 @@ struct DevBuf {
 struct StepTables {
     int n_act = 0;
     int total_tilesA = 0, total_tilesV = 0, total_merge = 0;
-    long long total_words = 0;
+    long long total_groups = 0;
     int* d_act = nullptr;
     int* d_tileA = nullptr;
     int* d_tileV = nullptr;
     int* d_merge = nullptr;
-    long long* d_words = nullptr;
+    long long* d_groups = nullptr;
     long long* d_pre = nullptr;
 };
 
@@ -159,14 +159,14 @@ void build_table(vd_batch* b, const std::vector<int>& act, StepTables& T, bool a
         tA[a + 1] = tA[a] + D.ntx * D.nty;
         tV[a + 1] = tV[a] + D.vtx * D.vty;
         mg[a + 1] = mg[a] + D.ntx * D.nty * (TW + TH);
-        wd[a + 1] = wd[a] + (long long)D.Ly * D.wpr;
+        wd[a + 1] = wd[a] + (long long)D.Ly * D.gpr;
     }
     if (alloc) {
         T.d_act = b->mem.alloc<int>(b->n);
         T.d_tileA = b->mem.alloc<int>(b->n + 1);
         T.d_tileV = b->mem.alloc<int>(b->n + 1);
         T.d_merge = b->mem.alloc<int>(b->n + 1);
-        T.d_words = b->mem.alloc<long long>(b->n + 1);
+        T.d_groups = b->mem.alloc<long long>(b->n + 1);
         T.d_pre = b->mem.alloc<long long>((long long)NPRE * (b->n + 1));
         if (!b->mem.ok) return;
     }
@@ -174,12 +174,12 @@ void build_table(vd_batch* b, const std::vector<int>& act, StepTables& T, bool a
     T.total_tilesA = tA[n];
     T.total_tilesV = tV[n];
     T.total_merge = mg[n];
-    T.total_words = wd[n];
+    T.total_groups = wd[n];
     cudaMemcpyAsync(T.d_act, act.data(), sizeof(int) * n, cudaMemcpyHostToDevice, b->s);
     cudaMemcpyAsync(T.d_tileA, tA.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice, b->s);
     cudaMemcpyAsync(T.d_tileV, tV.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice, b->s);
     cudaMemcpyAsync(T.d_merge, mg.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice, b->s);
-    cudaMemcpyAsync(T.d_words, wd.data(), sizeof(long long) * (n + 1), cudaMemcpyHostToDevice, b->s);
+    cudaMemcpyAsync(T.d_groups, wd.data(), sizeof(long long) * (n + 1), cudaMemcpyHostToDevice, b->s);
 }
 
 Launch make_launch(vd_batch* b, const StepTables& T) {
@@ -193,7 +193,7 @@ Launch make_launch(vd_batch* b, const StepTables& T) {
     L.T.act = T.d_act;
     L.T.tileA_pre = T.d_tileA;
     L.T.tileV_pre = T.d_tileV;
-    L.T.word_pre = T.d_words;
+    L.T.grp_pre = T.d_groups;
     L.T.merge_pre = T.d_merge;
     L.T.pre = T.d_pre;
     L.grid_items = b->grid_items;
@@ -201,7 +201,7 @@ Launch make_launch(vd_batch* b, const StepTables& T) {
     L.total_tilesA = T.total_tilesA;
     L.total_tilesV = T.total_tilesV;
     L.total_merge = T.total_merge;
-    L.total_words = T.total_words;
+    L.total_groups = T.total_groups;
     return L;
 }
 
@@ -237,7 +237,6 @@ void enqueue_step(vd_batch* b, const Launch& L, bool timed) {
     launch_graph_prep(L);
     launch_graph_csr(L);
     launch_graph_match(L);
-    launch_graph_translate(L);
     launch_graph_flips(L);
     launch_finish(L);
     mark(b, timed);
@@ -253,7 +252,7 @@ vd_status create_batch(const vd_config* cfgs, int n, vd_batch** out, bool sequen
     b->sequence = sequence && n > 1;
     b->s = (cudaStream_t)cfgs[0].stream;
     b->desc.resize(n);
-    long long site = 0, word = 0, tile = 0, border = 0, comp = 0, edge = 0, eh = 0, oh = 0, bucket = 0, ovl = 0;
+    long long site = 0, word = 0, grp = 0, tile = 0, border = 0, comp = 0, edge = 0, eh = 0, oh = 0, bucket = 0, ovl = 0;
     long long piece_cap = 0, scan_items = 0, max_sites = 0;
     for (int i = 0; i < n; ++i) {
         const vd_config& c = cfgs[i];
@@ -269,6 +268,7 @@ vd_status create_batch(const vd_config* cfgs, int n, vd_batch** out, bool sequen
         D.vtx = (c.Lx + VW - 1) / VW;
         D.vty = (c.Ly + VH - 1) / VH;
         D.wpr = (c.Lx + 31) / 32;
+        D.gpr = (D.wpr + RGW - 1) / RGW;
         // frame sequence: instance i's past frame is instance i-1 of the same
         // step, instance 0's is instance n-1 of the previous step
         D.seq_prev = sequence ? (i == 0 ? n - 1 : i - 1) : i;
@@ -286,6 +286,7 @@ vd_status create_batch(const vd_config* cfgs, int n, vd_batch** out, bool sequen
         D.bucket_cap = ((c.Lx + 3) / 4) * ((c.Ly + 3) / 4);
         D.site_off = site;
         D.word_off = word;
+        D.grp_off = grp;
         D.tile_off = tile;
         D.border_off = border;
         D.comp_off = comp;
@@ -298,6 +299,7 @@ vd_status create_batch(const vd_config* cfgs, int n, vd_batch** out, bool sequen
         site += N;
         max_sites = std::max(max_sites, N);
         word += (long long)c.Ly * D.wpr;
+        grp += (long long)c.Ly * D.gpr;
         tile += ntiles;
         border += ntiles * BORDER;
         comp += kcap + 1;
@@ -309,8 +311,8 @@ vd_status create_batch(const vd_config* cfgs, int n, vd_batch** out, bool sequen
         piece_cap += (N <= 65536) ? ntiles * (TSITES / 2) : N / 8 + ntiles * 16;
         scan_items = std::max(scan_items, (long long)0);
     }
-    scan_items = std::max(std::max(word, comp), bucket);
-    if (piece_cap >= (1ll << 31) || comp >= (1ll << 31) || edge >= (1ll << 31)) {
+    scan_items = std::max(std::max(grp, comp), bucket);
+    if (piece_cap >= (1ll << 31) || comp >= (1ll << 31) || edge >= (1ll << 30)) {
         delete b;
         return VD_ERR_INVALID;
     }
@@ -327,7 +329,8 @@ vd_status create_batch(const vd_config* cfgs, int n, vd_batch** out, bool sequen
     P.fgbits[0] = M.alloc<unsigned>(word);
     P.fgbits[1] = M.alloc<unsigned>(word);
     P.rootbits = M.alloc<unsigned>(word);
-    P.rankpre = M.alloc<int>(word);
+    P.rgcnt = M.alloc<int>(grp);
+    P.rankpre = M.alloc<int>(grp);
     P.tile_pbase = M.alloc<int>(tile);
     P.tile_pcnt = M.alloc<int>(tile);
     P.border = M.alloc<int>(border);
@@ -357,17 +360,14 @@ vd_status create_batch(const vd_config* cfgs, int n, vd_batch** out, bool sequen
     P.deg = M.alloc<int>(comp);
     P.rowoff[0] = M.alloc<int>(comp);
     P.rowoff[1] = M.alloc<int>(comp);
-    P.rowlen[0] = nullptr;
-    P.rowlen[1] = nullptr;
-    P.tdeg = M.alloc<int>(comp);
-    P.trowoff = M.alloc<int>(comp);
+    P.tlen = M.alloc<int>(comp);
     P.fcnt = M.alloc<int>(comp);
     P.fcnt_a = M.alloc<int>(comp);
     P.foff = M.alloc<int>(comp);
     P.foff_a = M.alloc<int>(comp);
-    P.cols[0] = M.alloc<int>(edge);
-    P.cols[1] = M.alloc<int>(edge);
-    P.tcols = M.alloc<int>(edge);
+    P.cols[0] = M.alloc<int>(2 * edge);
+    P.cols[1] = M.alloc<int>(2 * edge);
+    P.tcols = M.alloc<int>(2 * edge);
     P.ehash = M.alloc<unsigned long long>(eh);
     P.elist = M.alloc<int>(edge);
     P.ohash = M.alloc<unsigned long long>(oh);
@@ -398,10 +398,10 @@ vd_status create_batch(const vd_config* cfgs, int n, vd_batch** out, bool sequen
     chk(cudaMemsetAsync(P.rl[0], 0xff, sizeof(int) * tile * TRUNS, b->s));
     chk(cudaMemsetAsync(P.rl[1], 0xff, sizeof(int) * tile * TRUNS, b->s));
     chk(cudaMemsetAsync(P.rootbits, 0, sizeof(unsigned) * word, b->s));
+    chk(cudaMemsetAsync(P.rgcnt, 0, sizeof(int) * grp, b->s));
     chk(cudaMemsetAsync(P.bcnt, 0, sizeof(int) * bucket, b->s));
     chk(cudaMemsetAsync(P.deg, 0, sizeof(int) * comp, b->s));
     chk(cudaMemsetAsync(P.best_n, 0, sizeof(unsigned long long) * comp, b->s));
-    chk(cudaMemsetAsync(P.tdeg, 0, sizeof(int) * comp, b->s));
     chk(cudaMemsetAsync(P.rowoff[0], 0, sizeof(int) * comp, b->s));
     chk(cudaMemsetAsync(P.rowoff[1], 0, sizeof(int) * comp, b->s));
     chk(cudaMemsetAsync(P.ehash, 0xff, sizeof(unsigned long long) * eh, b->s));

@@ -438,6 +438,7 @@ __global__ void k_ccl_flatten(Pools P) {
             const int q = P.p_q[pid];
             const int y = q / D.Lx, x = q - y * D.Lx;
             atomicOr(&P.rootbits[D.word_off + (long long)y * D.wpr + (x >> 5)], 1u << (x & 31));
+            atomicAdd(&P.rgcnt[D.grp_off + (long long)y * D.gpr + (x >> 5) / RGW], 1);
             warp_add(&P.st[inst].K, 1);
         }
     }
@@ -454,8 +455,13 @@ __global__ void k_comp_accum(Pools P) {
         const int q = P.p_q[pid];
         const int yq = q / D.Lx, xq = q - yq * D.Lx;
         if (r == pid) {
-            const long long w = D.word_off + (long long)yq * D.wpr + (xq >> 5);
-            const int c = P.rankpre[w] + __popc(P.rootbits[w] & ((1u << (xq & 31)) - 1u));
+            // rank = roots of earlier groups + earlier roots of this group
+            const unsigned* row = P.rootbits + D.word_off + (long long)yq * D.wpr;
+            const int wq = xq >> 5, w0 = wq - wq % RGW;
+            int c = P.rankpre[D.grp_off + (long long)yq * D.gpr + wq / RGW] + __popc(row[wq] & ((1u << (xq & 31)) - 1u));
+#pragma unroll
+            for (int k = 0; k < RGW - 1; ++k)   // independent loads, issued together
+                if (w0 + k < wq) c += __popc(row[w0 + k]);
             P.p_comp[pid] = c;
             if (c < D.comp_cap) P.comp_root[D.comp_off + c] = pid;
         }

@@ -1,14 +1,18 @@
 // Adjacency lists, isomorphism and topology changes (Sections 3.2.2-3.2.4).
 //
-// Links of a frame are kept as a CSR adjacency list: row a holds the labels
-// b > a linked to a, sorted (the paper's compressed adjacency matrix). The
-// isomorphism Phi between past and now labels is the mutual best overlap. The
-// past list is translated into now labels and re-sorted (the paper's
-// "translation"), then one thread per now-label row compares the translated
-// past row with the now row: entries only in the past row are breaking links,
-// entries only in the now row are arising links. Labels outside Phi's domain
-// or image are excluded, as the paper does for appearing and vanishing
-// bubbles. Row-by-row output keeps both lists sorted by now-key.
+// Links of a frame are kept as a CSR adjacency list of both directions: row a
+// holds every label linked to a, sorted (the paper's compressed adjacency
+// matrix, stored for both ends of each link). The isomorphism Phi between past
+// and now labels is the mutual best overlap. For each now-bubble a with a past
+// counterpart ia = Phi^-1(a), the translated past row is Phi of the past
+// neighbours of ia that lie above a, sorted (the paper's "translation"; with
+// both directions stored, row a needs only past row ia, so no translated CSR
+// has to be counted and scattered). One thread per now row then merges the
+// translated row with the now row's entries above a: entries only in the past
+// row are breaking links, entries only in the now row are arising links.
+// Labels outside Phi's domain or image are excluded, as the paper does for
+// appearing and vanishing bubbles. Row-by-row output keeps both lists sorted
+// by now-key.
 #include "vd_internal.cuh"
 
 namespace vd {
@@ -18,12 +22,14 @@ namespace vd {
 template <class F>
 __device__ __forceinline__ void for_items(const StepTable& T, int which, F f) {
     __shared__ long long s_pre[SEG_CACHE];
-    const long long* pre = seg_table(pre_arr(T, which), T.n_act, s_pre);
+    __shared__ int s_act[SEG_CACHE];
+    const int* act;
+    const long long* pre = seg_table(pre_arr(T, which), T.act, T.n_act, s_pre, s_act, &act);
     const long long total = pre[T.n_act];
     for (long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x; g < total;
          g += (long long)gridDim.x * blockDim.x) {
         const int a = seg_of(pre, T.n_act, g);
-        f(T.act[a], g - pre[a]);
+        f(act[a], g - pre[a]);
     }
 }
 
@@ -66,7 +72,6 @@ __global__ void k_step_begin(Pools P, StepTable T) {
         S.n_wide = 0;
         S.n_ovl = 0;
         S.n_edge_list = 0;
-        S.n_tedges = 0;
         S.n_eapp = 0;
         S.n_oapp = 0;
         S.err = 0;
@@ -94,21 +99,53 @@ __global__ void k_step_finish(Pools P, StepTable T) {
     }
 }
 
-// sorted link keys of one instance's frame in `slot`
-__global__ void k_edge_keys(Pools P, int inst, int slot, unsigned long long* out) {
+// sorted link keys of one instance's frame in `slot`: the entries above the
+// diagonal of each row, placed by a block-wide scan of their counts
+constexpr int EK_THREADS = 1024;
+__global__ __launch_bounds__(EK_THREADS) void k_edge_keys(Pools P, int inst, int slot, unsigned long long* out) {
+    __shared__ int s_warp[EK_THREADS / 32];
+    __shared__ int s_base;
     const InstDesc& D = P.desc[inst];
     const InstState& S = P.st[inst];
     const int K = min(S.Kb[slot], D.comp_cap);
+    const int cap = 2 * D.edge_cap;
     const int* ro = P.rowoff[slot] + D.comp_off;
-    const int* cl = P.cols[slot] + D.edge_off;
-    for (int a = blockIdx.x * blockDim.x + threadIdx.x; a < K; a += gridDim.x * blockDim.x) {
-        const int s = min(ro[a], D.edge_cap), e = min(ro[a + 1], D.edge_cap);
-        for (int k = s; k < e; ++k) out[k] = edge_key(a, cl[k]);
+    const int* cl = P.cols[slot] + 2 * D.edge_off;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (threadIdx.x == 0) s_base = 0;
+    __syncthreads();
+    for (int a0 = 0; a0 < K; a0 += EK_THREADS) {
+        const int a = a0 + threadIdx.x;
+        int s = 0, e = 0;
+        if (a < K) {
+            s = min(ro[a], cap);
+            e = min(ro[a + 1], cap);
+            while (s < e && cl[s] < a) ++s;   // rows are sorted: the entries above a are a suffix
+        }
+        const int cnt = e - s;
+        int inc = cnt;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += y;
+        }
+        if (lane == 31) s_warp[warp] = inc;
+        __syncthreads();
+        int pre = s_base, tot = 0;
+        for (int w = 0; w < EK_THREADS / 32; ++w) {
+            if (w < warp) pre += s_warp[w];
+            tot += s_warp[w];
+        }
+        int pos = pre + inc - cnt;
+        for (int k = s; k < e; ++k, ++pos)
+            if (pos < D.edge_cap) out[pos] = edge_key(a, cl[k]);
+        __syncthreads();
+        if (threadIdx.x == 0) s_base += tot;
+        __syncthreads();
     }
 }
 
 void launch_edge_keys(cudaStream_t s, const Pools& P, int inst, int slot, unsigned long long* out) {
-    k_edge_keys<<<64, 256, 0, s>>>(P, inst, slot, out);
+    k_edge_keys<<<1, EK_THREADS, 0, s>>>(P, inst, slot, out);
 }
 
 // ---------------------------------------------------------------------------
@@ -125,22 +162,54 @@ __global__ void k_csr_scatter(Pools P, StepTable T) {
         const unsigned long long key = H[slot];
         H[slot] = EMPTY_KEY;
         const int lo = (int)(key >> 32), hi = (int)(key & 0xffffffffu);
-        const int pos = P.rowoff[now][D.comp_off + lo] + atomicSub(&P.deg[D.comp_off + lo], 1) - 1;
-        if (pos < D.edge_cap) P.cols[now][D.edge_off + pos] = hi;
+        const int* ro = P.rowoff[now] + D.comp_off;
+        int* cl = P.cols[now] + 2 * D.edge_off;
+        const int cap = 2 * D.edge_cap;
+        const int plo = ro[lo] + atomicSub(&P.deg[D.comp_off + lo], 1) - 1;
+        const int phi_ = ro[hi] + atomicSub(&P.deg[D.comp_off + hi], 1) - 1;
+        if (plo < cap) cl[plo] = hi;
+        if (phi_ < cap) cl[phi_] = lo;
     });
 }
 
-__device__ __forceinline__ void sort_small(int* v, int n) {
-    for (int i = 1; i < n; ++i) {
-        const int x = v[i];
-        int j = i - 1;
-        while (j >= 0 && v[j] > x) {
-            v[j + 1] = v[j];
-            --j;
+// ascending sort of a short row in place: insertion sort up to 32 entries,
+// heap sort beyond (rows of very high degree stay O(d log d))
+__device__ __forceinline__ void sift_down(int* v, int i, int n) {
+    const int x = v[i];
+    for (;;) {
+        int c = 2 * i + 1;
+        if (c >= n) break;
+        if (c + 1 < n && v[c + 1] > v[c]) ++c;
+        if (v[c] <= x) break;
+        v[i] = v[c];
+        i = c;
+    }
+    v[i] = x;
+}
+
+__device__ void sort_row(int* v, int n) {
+    if (n <= 32) {
+        for (int i = 1; i < n; ++i) {
+            const int x = v[i];
+            int j = i - 1;
+            while (j >= 0 && v[j] > x) {
+                v[j + 1] = v[j];
+                --j;
+            }
+            v[j + 1] = x;
         }
-        v[j + 1] = x;
+        return;
+    }
+    for (int i = n / 2 - 1; i >= 0; --i) sift_down(v, i, n);
+    for (int e = n - 1; e > 0; --e) {
+        const int t = v[0];
+        v[0] = v[e];
+        v[e] = t;
+        sift_down(v, 0, e);
     }
 }
+
+constexpr int RLOC = 32;   // rows up to this length are handled in a local array (loads issued together)
 
 __global__ void k_csr_sort(Pools P, StepTable T) {
     pdl_enter();
@@ -148,8 +217,20 @@ __global__ void k_csr_sort(Pools P, StepTable T) {
         const InstDesc& D = P.desc[inst];
         const int now = P.st[inst].slot ^ 1;
         const int* ro = P.rowoff[now] + D.comp_off;
-        const int s = min(ro[a], D.edge_cap), e = min(ro[a + 1], D.edge_cap);
-        sort_small(P.cols[now] + D.edge_off + s, e - s);
+        const int cap = 2 * D.edge_cap;
+        const int s = min(ro[a], cap), e = min(ro[a + 1], cap);
+        int* row = P.cols[now] + 2 * D.edge_off + s;
+        const int n = e - s;
+        if (n > RLOC) {
+            sort_row(row, n);
+            return;
+        }
+        int v[RLOC];
+#pragma unroll 8
+        for (int k = 0; k < n; ++k) v[k] = row[k];
+        sort_row(v, n);
+#pragma unroll 8
+        for (int k = 0; k < n; ++k) row[k] = v[k];
     });
 }
 
@@ -203,66 +284,92 @@ __global__ void k_match_phi(Pools P, StepTable T) {
 }
 
 // ---------------------------------------------------------------------------
-// translation of the past links into now labels, then a sorted CSR of them
+// translation and row comparison: breaking = translated past only, arising =
+// now only
 // ---------------------------------------------------------------------------
-__global__ void k_translate_count(Pools P, StepTable T) {
-    pdl_enter();
-    for_items(T, PRE_KP, [&](int inst, long long a) {
-        const InstDesc& D = P.desc[inst];
-        const InstState& S = P.st[inst];
-        const InstDesc& DP = P.desc[S.prev_inst];
-        const int pa = P.phi[D.comp_off + a];
-        if (pa < 0) return;
-        const int* ro = P.rowoff[S.prev_buf] + DP.comp_off;
-        const int* cl = P.cols[S.prev_buf] + DP.edge_off;
-        int cnt = 0;
-        for (int k = ro[a]; k < ro[a + 1]; ++k) {
-            const int pb = P.phi[D.comp_off + cl[k]];
-            if (pb < 0) continue;
-            atomicAdd(&P.tdeg[D.comp_off + min(pa, pb)], 1);
-            ++cnt;
+// Translated past row of now-bubble a (ia = Phi^-1(a) >= 0): Phi(b) for the
+// past neighbours b of ia with Phi(b) > a, sorted, written at the past row's
+// position in tcols; returns its length
+__device__ int translate_row(const Pools& P, const InstDesc& D, const InstState& S, int a, int ia) {
+    const InstDesc& DP = P.desc[S.prev_inst];
+    const int pcap = 2 * DP.edge_cap, cap = 2 * D.edge_cap;
+    const int* pro = P.rowoff[S.prev_buf] + DP.comp_off;
+    const int* pcl = P.cols[S.prev_buf] + 2 * DP.edge_off;
+    const int s = min(pro[ia], pcap), e = min(min(pro[ia + 1], pcap), cap);
+    if (s >= e) return 0;
+    int* tr = P.tcols + 2 * D.edge_off + s;
+    const int* phi = P.phi + D.comp_off;
+    const int n = e - s;
+    int t = 0;
+    if (n <= RLOC) {
+        int v[RLOC];
+#pragma unroll 8
+        for (int k = 0; k < n; ++k) v[k] = pcl[s + k];
+#pragma unroll 8
+        for (int k = 0; k < n; ++k) {
+            const int b = v[k];
+            v[k] = (b >= 0 && b < D.comp_cap) ? phi[b] : -1;   // out of range only after an overflow
         }
-        warp_add(&P.st[inst].n_tedges, cnt);
-    });
-}
-
-__global__ void k_translate_scatter(Pools P, StepTable T) {
-    pdl_enter();
-    for_items(T, PRE_KP, [&](int inst, long long a) {
-        const InstDesc& D = P.desc[inst];
-        const InstState& S = P.st[inst];
-        const InstDesc& DP = P.desc[S.prev_inst];
-        const int pa = P.phi[D.comp_off + a];
-        if (pa < 0) return;
-        const int* ro = P.rowoff[S.prev_buf] + DP.comp_off;
-        const int* cl = P.cols[S.prev_buf] + DP.edge_off;
-        for (int k = ro[a]; k < ro[a + 1]; ++k) {
-            const int pb = P.phi[D.comp_off + cl[k]];
-            if (pb < 0) continue;
-            const int lo = min(pa, pb), hi = max(pa, pb);
-            const int pos = P.trowoff[D.comp_off + lo] + atomicSub(&P.tdeg[D.comp_off + lo], 1) - 1;
-            if (pos < D.edge_cap) P.tcols[D.edge_off + pos] = hi;
+        for (int k = 0; k < n; ++k)
+            if (v[k] > a) v[t++] = v[k];
+        sort_row(v, t);
+#pragma unroll 8
+        for (int k = 0; k < t; ++k) tr[k] = v[k];
+    } else {
+        for (int k = s; k < e; ++k) {
+            const int b = pcl[k];
+            if (b < 0 || b >= D.comp_cap) continue;
+            const int pb = phi[b];
+            if (pb > a) tr[t++] = pb;
         }
-    });
+        sort_row(tr, t);
+    }
+    return t;
 }
 
-__global__ void k_tcsr_sort(Pools P, StepTable T) {
-    pdl_enter();
-    for_items(T, PRE_K, [&](int inst, long long a) {
-        const InstDesc& D = P.desc[inst];
-        const int* ro = P.trowoff + D.comp_off;
-        const int s = ro[a], e = ro[a + 1];
-        sort_small(P.tcols + D.edge_off + s, e - s);
-    });
+// Merge of the translated row tr[0..nt) with the now row's candidates: the
+// entries nowv(i), i < nn, for which skip(i) is false (above a, other end
+// matched), ascending
+template <bool WRITE, class NowV, class Skip>
+__device__ __forceinline__ void merge_row(const Pools& P, const InstDesc& D, int a, int ia, const int* tr, int nt,
+                                          int nn, NowV nowv, Skip skip, int ob, int oa, int& nb, int& na) {
+    const long long co = D.comp_off;
+    int i = 0, j = 0;
+    for (;;) {
+        while (i < nn && skip(i)) ++i;
+        const bool hn = i < nn, ht = j < nt;
+        if (!hn && !ht) break;
+        const int vn = hn ? nowv(i) : INT_MAX, vt = ht ? tr[j] : INT_MAX;
+        if (vn == vt) {
+            ++i;
+            ++j;
+        } else if (vt < vn) {   // only in the past: breaking
+            if (WRITE) {
+                const long long o = D.edge_off + ob + nb;
+                P.brk[o] = edge_key(a, vt);
+                P.brk_prev[o] = edge_key(ia, P.inv[co + vt]);
+                P.active[co + a] = 1;
+                P.active[co + vt] = 1;
+            }
+            ++nb;
+            ++j;
+        } else {                // only now: arising
+            if (WRITE) {
+                P.ari[D.edge_off + oa + na] = edge_key(a, vn);
+                P.active[co + a] = 1;
+                P.active[co + vn] = 1;
+            }
+            ++na;
+            ++i;
+        }
+    }
 }
 
-// ---------------------------------------------------------------------------
-// row comparison: breaking = translated past only, arising = now only
-// ---------------------------------------------------------------------------
 template <bool WRITE>
 __device__ __forceinline__ void compare_row(const Pools& P, int inst, int a) {
     const InstDesc& D = P.desc[inst];
-    const int now = P.st[inst].slot ^ 1;
+    const InstState& S = P.st[inst];
+    const int now = S.slot ^ 1;
     const long long co = D.comp_off;
     int nb = 0, na = 0;
     int ob = 0, oa = 0;
@@ -270,43 +377,46 @@ __device__ __forceinline__ void compare_row(const Pools& P, int inst, int a) {
         ob = P.foff[co + a];
         oa = P.foff_a[co + a];
     }
-    const int ia = P.inv[co + a];
+    const int ia = S.has_prev ? P.inv[co + a] : -1;
     if (ia >= 0) {
-        const int* nr = P.cols[now] + D.edge_off;
-        int i = min(P.rowoff[now][co + a], D.edge_cap);
-        const int ie = min(P.rowoff[now][co + a + 1], D.edge_cap);
-        const int* tr = P.tcols + D.edge_off;
-        int j = min(P.trowoff[co + a], D.edge_cap);
-        const int je = min(P.trowoff[co + a + 1], D.edge_cap);
-        for (;;) {
-            // next now-entry whose other end is matched
-            while (i < ie && (nr[i] >= D.comp_cap || P.inv[co + nr[i]] < 0)) ++i;
-            const bool hn = i < ie, ht = j < je;
-            if (!hn && !ht) break;
-            const int vn = hn ? nr[i] : INT_MAX, vt = ht ? tr[j] : INT_MAX;
-            if ((hn && vn >= D.comp_cap) || (ht && vt >= D.comp_cap)) break;   // only after an overflow
-            if (vn == vt) {
-                ++i;
-                ++j;
-            } else if (vt < vn) {   // only in the past: breaking
-                if (WRITE) {
-                    const long long o = D.edge_off + ob + nb;
-                    P.brk[o] = edge_key(a, vt);
-                    P.brk_prev[o] = edge_key(ia, P.inv[co + vt]);
-                    P.active[co + a] = 1;
-                    P.active[co + vt] = 1;
-                }
-                ++nb;
-                ++j;
-            } else {                // only now: arising
-                if (WRITE) {
-                    P.ari[D.edge_off + oa + na] = edge_key(a, vn);
-                    P.active[co + a] = 1;
-                    P.active[co + vn] = 1;
-                }
-                ++na;
-                ++i;
+        int nt;
+        const int* tr;
+        {
+            const InstDesc& DP = P.desc[S.prev_inst];
+            const int s = min(P.rowoff[S.prev_buf][DP.comp_off + ia], 2 * DP.edge_cap);
+            tr = P.tcols + 2 * D.edge_off + s;
+        }
+        if (WRITE) {
+            nt = P.tlen[co + a];
+        } else {
+            nt = translate_row(P, D, S, a, ia);
+            P.tlen[co + a] = nt;
+        }
+        const int cap = 2 * D.edge_cap;
+        const int* nr = P.cols[now] + 2 * D.edge_off;
+        const int s = min(P.rowoff[now][co + a], cap);
+        const int n = min(P.rowoff[now][co + a + 1], cap) - s;
+        if (n <= RLOC && nt <= RLOC) {
+            // both rows in local arrays: loads issued together, then the merge
+            int v[RLOC], w[RLOC], t[RLOC];
+#pragma unroll 8
+            for (int k = 0; k < n; ++k) v[k] = nr[s + k];
+#pragma unroll 8
+            for (int k = 0; k < n; ++k) {
+                const int c = v[k];
+                w[k] = (c > a && c < D.comp_cap) ? P.inv[co + c] : -1;
             }
+#pragma unroll 8
+            for (int k = 0; k < nt; ++k) t[k] = tr[k];
+            merge_row<WRITE>(P, D, a, ia, t, nt, n, [&](int i) { return v[i]; }, [&](int i) { return w[i] < 0; },
+                             ob, oa, nb, na);
+        } else {
+            merge_row<WRITE>(P, D, a, ia, tr, nt, n, [&](int i) { return nr[s + i]; },
+                             [&](int i) {
+                                 const int c = nr[s + i];
+                                 return c <= a || c >= D.comp_cap || P.inv[co + c] < 0;
+                             },
+                             ob, oa, nb, na);
         }
     }
     if (!WRITE) {
@@ -367,23 +477,13 @@ void launch_graph_match(const Launch& L) {
 }
 
 // The translation reads the past frame's CSR, which in a frame sequence is the
-// now-frame CSR of the previous instance built in this step: it follows both
-// the match and the CSR chain.
-void launch_graph_translate(const Launch& L) {
-    const int g = L.grid_wide;
-    launch_step(L, k_translate_count, dim3(g), dim3(256), L.P, L.T);
-    launch_plan(L, 0, ends_bit(SCAN_TDEG), pre_bit(PRE_ET));
-    launch_scan(L, SCAN_TDEG);
-    launch_step(L, k_translate_scatter, dim3(g), dim3(256), L.P, L.T);
-    launch_step(L, k_tcsr_sort, dim3(g), dim3(256), L.P, L.T);
-}
-
+// now-frame CSR of the previous instance built in this step: the row
+// comparison follows both the match and the CSR chain.
 void launch_graph_flips(const Launch& L) {
     const int g = L.grid_wide;
     launch_step(L, k_flip_count, dim3(g), dim3(256), L.P, L.T);
     launch_plan(L, 0, ends_bit(SCAN_FLIPS) | ends_bit(SCAN_FLIPS_A), pre_bit(PRE_FB) | pre_bit(PRE_FA));
-    launch_scan(L, SCAN_FLIPS);
-    launch_scan(L, SCAN_FLIPS_A);
+    launch_scan2(L, SCAN_FLIPS, SCAN_FLIPS_A);
     launch_step(L, k_flip_write, dim3(g), dim3(256), L.P, L.T);
 }
 

@@ -30,6 +30,12 @@ constexpr int VTHREADS = 256;
 
 constexpr int Q = 1024;         // centroid fixed point: 1/1024 site
 
+// Bubble ids are the ranks of the roots in raster order of their first sites.
+// Roots are counted per root group (RGW consecutive bitmask words of one row,
+// 32 * RGW sites); the groups are scanned and a root adds the bits before it
+// in its own group.
+constexpr int RGW = 8;
+
 constexpr unsigned long long EMPTY_KEY = ~0ull;
 
 // error bits in InstState::err and Globals::err
@@ -55,9 +61,10 @@ struct InstDesc {
     int wpr;                 // 32-bit bitmask words per lattice row
     int seq_prev;            // instance holding this instance's past frame (itself when independent)
     int seq_same;            // 1: that past frame is produced in the same step (frame sequence)
-    int pad0;
+    int gpr;                 // root groups per lattice row (RGW words each)
     long long site_off;      // labels / owners pools
-    long long word_off;      // fg-bit / root-bit / rank pools (Ly * wpr words)
+    long long word_off;      // fg-bit / root-bit pools (Ly * wpr words)
+    long long grp_off;       // root-group count / rank pools (Ly * gpr groups)
     long long tile_off;      // per-labelling-tile pools (tile piece base/count)
     long long border_off;    // border pool (ntx*nty*BORDER)
     long long comp_off;      // per-bubble pools (comp_cap entries, +1 for offsets)
@@ -95,7 +102,6 @@ struct InstState {
     int n_wide;
     int n_ovl;               // overlap pairs this frame
     int n_edge_list;         // unique links inserted in the hash (= E)
-    int n_tedges;            // translated past links
     int n_eapp;              // links appended by Voronoi tiles (before dedup)
     int n_oapp;              // overlap pairs appended by label tiles (before merge)
     int err;
@@ -127,7 +133,8 @@ struct Pools {
     int* rl[2];              // bubble label of every run of the frames in slot 0 / 1
     int* lab_out;            // per-site labels of one instance, expanded on request
     unsigned* rootbits;
-    int* rankpre;            // global exclusive prefix per word (this step)
+    int* rgcnt;              // roots per root group (zero between steps)
+    int* rankpre;            // exclusive rank prefix per root group (this step)
     // labelling tiles
     int* tile_pbase;         // first piece index of the tile in the piece pool
     int* tile_pcnt;          // number of pieces of the tile
@@ -158,17 +165,17 @@ struct Pools {
     int* inv;                // now -> past
     unsigned char* active;
     int* deg;                // link degree counts (zero between steps)
-    int* rowoff[2];          // CSR row offsets (global scan values) of past/now frames
-    int* rowlen[2];          // CSR row lengths
-    int* tdeg;               // translated-link degrees (zero between steps)
-    int* trowoff;
-    int* fcnt;               // per-row flip counts (breaking << 16 | arising is not used; two arrays)
+    int* rowoff[2];          // CSR row offsets (per-instance scan values) of past/now frames
+    int* tlen;               // length of the translated past row of each now-bubble
+    int* fcnt;               // per-row flip counts: breaking, arising
     int* fcnt_a;
     int* foff;
     int* foff_a;
     // links
-    int* cols[2];            // CSR columns (hi label) of past/now frames, local offsets
-    int* tcols;              // translated past links
+    // CSR of both directions (row a lists every neighbour of a, sorted):
+    // 2 * edge_cap entries per instance from 2 * edge_off
+    int* cols[2];            // past/now frames
+    int* tcols;              // translated past rows, each at its past row's position
     unsigned long long* ehash;
     int* elist;              // occupied hash slots
     unsigned long long* ohash;
@@ -194,7 +201,7 @@ struct StepTable {
     const int* act;              // instance ids
     const int* tileA_pre;        // prefix of labelling tiles over act (n_act+1)
     const int* tileV_pre;        // prefix of Voronoi tiles
-    const long long* word_pre;   // prefix of bitmask words
+    const long long* grp_pre;    // prefix of root groups
     const int* merge_pre;        // prefix of merge threads (tiles * (TW+TH))
     // device-computed prefixes over act (n_act+1 each), filled by k_plan
     long long* pre;              // NPRE arrays back to back
@@ -207,7 +214,6 @@ enum PreIdx : int {
     PRE_E,          // links now
     PRE_EP,         // links previous frame
     PRE_O,          // overlap pairs
-    PRE_ET,         // translated links
     PRE_FB,         // breaking links
     PRE_FA,         // arising links
     PRE_EA,         // appended links
@@ -270,6 +276,22 @@ __device__ __forceinline__ const PreT* seg_table(const PreT* pre, int n_act, Pre
     if (n_act + 1 > SEG_CACHE) return pre;
     for (int i = threadIdx.x; i <= n_act; i += blockDim.x) cache[i] = pre[i];
     __syncthreads();
+    return cache;
+}
+// the same with the instance ids of the active list (act) in the same round
+template <class PreT>
+__device__ __forceinline__ const PreT* seg_table(const PreT* pre, const int* act, int n_act, PreT* cache,
+                                                 int* act_cache, const int** act_out) {
+    if (n_act + 1 > SEG_CACHE) {
+        *act_out = act;
+        return pre;
+    }
+    for (int i = threadIdx.x; i <= n_act; i += blockDim.x) {
+        cache[i] = pre[i];
+        if (i < n_act) act_cache[i] = act[i];
+    }
+    __syncthreads();
+    *act_out = act_cache;
     return cache;
 }
 
@@ -392,7 +414,7 @@ struct Launch {
     StepTable T;
     int grid_items;      // fixed grid for grid-stride item loops
     int total_tilesA, total_tilesV, total_merge;
-    long long total_words;
+    long long total_groups;
     int grid_wide;               // blocks for kernels with one thread per item (pieces, bubbles, links)
 };
 
@@ -432,7 +454,6 @@ void launch_merge_lists(const Launch& L);  // appended links/pairs -> hash table
 void launch_graph_prep(const Launch& L);
 void launch_graph_csr(const Launch& L);
 void launch_graph_match(const Launch& L);
-void launch_graph_translate(const Launch& L);
 void launch_graph_flips(const Launch& L);
 void launch_begin(const Launch& L);        // per-step counters and field pointers
 void launch_finish(const Launch& L);       // swap frames
@@ -451,15 +472,15 @@ enum ScanKind : int {
     SCAN_ROOTBITS = 0,   // popcount of root-bit words
     SCAN_BUCKETS = 1,    // bucket counts
     SCAN_DEG = 2,        // link degrees (now frame)
-    SCAN_TDEG = 3,       // translated link degrees
-    SCAN_FLIPS = 4,      // breaking counts per row
-    SCAN_FLIPS_A = 5,    // arising counts per row
+    SCAN_FLIPS = 3,      // breaking counts per row
+    SCAN_FLIPS_A = 4,    // arising counts per row
 };
-constexpr int SCAN_KINDS = 6;
+constexpr int SCAN_KINDS = 5;
 // the end value of the offset array of scan `kind`, written by k_plan
 constexpr int ENDS_NONE = 0;
 __host__ __device__ constexpr int ends_bit(ScanKind kind) { return 1 << kind; }
-void launch_scan(const Launch& L, ScanKind kind);   // k_scan over the current plan
+void launch_scan(const Launch& L, ScanKind kind);
+void launch_scan2(const Launch& L, ScanKind kind1, ScanKind kind2);   // two scans over the same segments
 // recompute prefixes (and bucket grids when with_comp) and the end values of
 // the offset arrays whose bits are set in ends; only the prefix arrays whose
 // bits are set in pre_mask are written

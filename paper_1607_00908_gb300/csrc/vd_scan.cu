@@ -68,7 +68,6 @@ __global__ __launch_bounds__(PLAN_THREADS) void k_plan(Pools P, StepTable T, int
             v[PRE_E] = S.n_edge_list;
             v[PRE_EP] = S.has_prev ? S.E_prev : 0;
             v[PRE_O] = S.n_ovl < D.ovl_cap ? S.n_ovl : D.ovl_cap;
-            v[PRE_ET] = S.n_tedges;
             v[PRE_FB] = S.n_break;
             v[PRE_FA] = S.n_arise;
             v[PRE_EA] = S.n_eapp < D.edge_cap ? S.n_eapp : D.edge_cap;
@@ -77,8 +76,7 @@ __global__ __launch_bounds__(PLAN_THREADS) void k_plan(Pools P, StepTable T, int
             // end values of the offset arrays (off[size] = total) of the scans that follow
             const int now = S.slot ^ 1;
             if (ends & ends_bit(SCAN_BUCKETS)) P.boff[D.bucket_off + (long long)S.nbx * S.nby] = S.K;
-            if (ends & ends_bit(SCAN_DEG)) P.rowoff[now][D.comp_off + S.K] = S.n_edge_list;
-            if (ends & ends_bit(SCAN_TDEG)) P.trowoff[D.comp_off + S.K] = S.n_tedges;
+            if (ends & ends_bit(SCAN_DEG)) P.rowoff[now][D.comp_off + S.K] = 2 * S.n_edge_list;
             if (ends & ends_bit(SCAN_FLIPS)) P.foff[D.comp_off + S.K] = S.n_break;
             if (ends & ends_bit(SCAN_FLIPS_A)) P.foff_a[D.comp_off + S.K] = S.n_arise;
         }
@@ -106,28 +104,27 @@ __global__ __launch_bounds__(PLAN_THREADS) void k_plan(Pools P, StepTable T, int
 // k_scan
 // ---------------------------------------------------------------------------
 struct ScanSel {
-    int seg;      // PreIdx of segment sizes, or -1 for words (static table)
+    int seg;      // PreIdx of segment sizes, or -1 for root groups (static table)
     int base;     // PreIdx of output totals
+    int mul;      // an instance's total is mul x its entry in base
 };
 
 __device__ __forceinline__ ScanSel scan_sel(int kind) {
     switch (kind) {
-        case SCAN_ROOTBITS: return {-1, PRE_KR};   // ranks count every root, clamped or not
-        case SCAN_BUCKETS: return {PRE_NB, PRE_K};
-        case SCAN_DEG: return {PRE_K, PRE_E};
-        case SCAN_TDEG: return {PRE_K, PRE_ET};
-        case SCAN_FLIPS: return {PRE_K, PRE_FB};
-        default: return {PRE_K, PRE_FA};
+        case SCAN_ROOTBITS: return {-1, PRE_KR, 1};   // ranks count every root, clamped or not
+        case SCAN_BUCKETS: return {PRE_NB, PRE_K, 1};
+        case SCAN_DEG: return {PRE_K, PRE_E, 2};      // every link is in the rows of both ends
+        case SCAN_FLIPS: return {PRE_K, PRE_FB, 1};
+        default: return {PRE_K, PRE_FA, 1};
     }
 }
 
 __device__ __forceinline__ int scan_value(const Pools& P, int kind, int inst, long long j) {
     const InstDesc& D = P.desc[inst];
     switch (kind) {
-        case SCAN_ROOTBITS: return __popc(P.rootbits[D.word_off + j]);
+        case SCAN_ROOTBITS: return P.rgcnt[D.grp_off + j];
         case SCAN_BUCKETS: return P.bcnt[D.bucket_off + j];
         case SCAN_DEG: return P.deg[D.comp_off + j];
-        case SCAN_TDEG: return P.tdeg[D.comp_off + j];
         case SCAN_FLIPS: return P.fcnt[D.comp_off + j];
         default: return P.fcnt_a[D.comp_off + j];
     }
@@ -136,10 +133,12 @@ __device__ __forceinline__ int scan_value(const Pools& P, int kind, int inst, lo
 __device__ __forceinline__ void scan_write(const Pools& P, int kind, int inst, long long j, int v) {
     const InstDesc& D = P.desc[inst];
     switch (kind) {
-        case SCAN_ROOTBITS: P.rankpre[D.word_off + j] = v; break;
+        case SCAN_ROOTBITS:
+            P.rankpre[D.grp_off + j] = v;
+            P.rgcnt[D.grp_off + j] = 0;   // zero again for the next step (stores after all loads)
+            break;
         case SCAN_BUCKETS: P.boff[D.bucket_off + j] = v; break;
         case SCAN_DEG: P.rowoff[P.st[inst].slot ^ 1][D.comp_off + j] = v; break;
-        case SCAN_TDEG: P.trowoff[D.comp_off + j] = v; break;
         case SCAN_FLIPS: P.foff[D.comp_off + j] = v; break;
         default: P.foff_a[D.comp_off + j] = v; break;
     }
@@ -154,30 +153,41 @@ __device__ __forceinline__ void publish(unsigned long long* f, unsigned epoch, u
     *(volatile unsigned long long*)f = w;
 }
 
-__global__ __launch_bounds__(SCAN_THREADS) void k_scan(Pools P, StepTable T, int kind) {
+// kind2 >= 0: a second scan over the same segments in the same launch (tiles
+// numbered after the first scan's); each scan keeps its own flags and tag
+__global__ __launch_bounds__(SCAN_THREADS) void k_scan(Pools P, StepTable T, int kind1, int kind2) {
     pdl_enter();
     __shared__ int s_tile;
     __shared__ long long s_pre[SEG_CACHE];
+    __shared__ int s_act[SEG_CACHE];
     __shared__ int s_warp[SCAN_THREADS / 32];
     __shared__ long long s_excl;
-    const ScanSel sel = scan_sel(kind);
+    const ScanSel sel1 = scan_sel(kind1);
     const int n = T.n_act;
-    const long long* seg0 = sel.seg < 0 ? T.word_pre : pre_arr(T, sel.seg);
-    const long long* base = pre_arr(T, sel.base);
+    const long long* seg0 = sel1.seg < 0 ? T.grp_pre : pre_arr(T, sel1.seg);
     const long long total = seg0[n];
-    // every scan of a step has its own tag (step count, kind) and ticket counter
-    const unsigned epoch = ((*(volatile unsigned*)&P.g->scan_step << 3) | (unsigned)kind) & 0x3FFFFFFFu;
+    const long long ntiles1 = (total + SCAN_TILE - 1) / SCAN_TILE;
+    const long long ntiles = kind2 >= 0 ? 2 * ntiles1 : ntiles1;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     // blocks beyond the number of tiles never take a ticket
-    if ((long long)blockIdx.x * SCAN_TILE >= total) return;
-    const long long* seg = seg_table(seg0, n, s_pre);
+    if ((long long)blockIdx.x >= ntiles) return;
+    const int* act;
+    const long long* seg = seg_table(seg0, T.act, n, s_pre, s_act, &act);
 
     for (;;) {
-        if (threadIdx.x == 0) s_tile = atomicAdd(&P.g->scan_ticket[kind], 1);
+        if (threadIdx.x == 0) s_tile = atomicAdd(&P.g->scan_ticket[kind1], 1);
         __syncthreads();
-        const long long tile = s_tile;
+        const long long ticket = s_tile;
+        if (ticket >= ntiles) break;
+        const bool second = ticket >= ntiles1;
+        const int kind = second ? kind2 : kind1;
+        const long long tile = second ? ticket - ntiles1 : ticket;
+        if (tile >= P.scan_flag_cap) break;
         const long long start = tile * SCAN_TILE;
-        if (start >= total || tile >= P.scan_flag_cap) break;
+        const ScanSel sel = scan_sel(kind);
+        const long long* base = pre_arr(T, sel.base);
+        // every scan of a step has its own tag (step count, kind)
+        const unsigned epoch = ((*(volatile unsigned*)&P.g->scan_step << 3) | (unsigned)kind) & 0x3FFFFFFFu;
 
         // load SCAN_ITEMS consecutive items per thread
         int v[SCAN_ITEMS];
@@ -194,7 +204,7 @@ __global__ __launch_bounds__(SCAN_THREADS) void k_scan(Pools P, StepTable T, int
                     a = seg_of(seg, n, g);
                     lo = seg[a];
                     hi = seg[a + 1];
-                    inst = T.act[a];
+                    inst = act[a];
                 }
                 x = scan_value(P, kind, inst, g - lo);
             }
@@ -273,9 +283,9 @@ __global__ __launch_bounds__(SCAN_THREADS) void k_scan(Pools P, StepTable T, int
                     a = seg_of(seg, n, g);
                     lo = seg[a];
                     hi = seg[a + 1];
-                    inst = T.act[a];
+                    inst = act[a];
                 }
-                scan_write(P, kind, inst, g - lo, (int)(run - base[a]));
+                scan_write(P, kind, inst, g - lo, (int)(run - sel.mul * base[a]));
                 run += v[i];
             }
         }
@@ -288,8 +298,11 @@ void launch_plan(const Launch& L, int with_comp, int ends, int pre_mask) {
 }
 
 void launch_scan(const Launch& L, ScanKind kind) {
-    int grid = L.grid_items;
-    launch_step(L, k_scan, dim3(grid), dim3(SCAN_THREADS), L.P, L.T, (int)kind);
+    launch_step(L, k_scan, dim3(L.grid_items), dim3(SCAN_THREADS), L.P, L.T, (int)kind, -1);
+}
+
+void launch_scan2(const Launch& L, ScanKind kind1, ScanKind kind2) {
+    launch_step(L, k_scan, dim3(L.grid_items), dim3(SCAN_THREADS), L.P, L.T, (int)kind1, (int)kind2);
 }
 
 }  // namespace vd

@@ -79,6 +79,7 @@ __device__ __forceinline__ void edge_global_insert(const Pools& P, const InstDes
             if (idx < D.edge_cap) P.elist[D.edge_off + idx] = (int)h;
             else atomicOr(&P.st[inst].err, ERR_EDGE_CAP);
             atomicAdd(&P.deg[D.comp_off + (int)(key >> 32)], 1);
+            atomicAdd(&P.deg[D.comp_off + (int)(key & 0xffffffffu)], 1);
             return;
         }
         if (k == key) return;
@@ -587,20 +588,22 @@ __global__ __launch_bounds__(32 * LINK_WARPS) void k_links(Pools P, StepTable T)
 __global__ void k_merge_lists(Pools P, StepTable T) {
     pdl_enter();
     __shared__ long long s_pe[SEG_CACHE], s_po[SEG_CACHE];
-    const long long* pe = seg_table(pre_arr(T, PRE_EA), T.n_act, s_pe);
+    __shared__ int s_act[SEG_CACHE];
+    const int* act;
+    const long long* pe = seg_table(pre_arr(T, PRE_EA), T.act, T.n_act, s_pe, s_act, &act);
     const long long* po = seg_table(pre_arr(T, PRE_OA), T.n_act, s_po);
     const long long ne = pe[T.n_act], no = po[T.n_act];
     for (long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x; g < ne + no;
          g += (long long)gridDim.x * blockDim.x) {
         if (g < ne) {
             const int a = seg_of(pe, T.n_act, g);
-            const int inst = T.act[a];
+            const int inst = act[a];
             const InstDesc& D = P.desc[inst];
             edge_global_insert(P, D, inst, P.ekeys[D.edge_off + (g - pe[a])]);
         } else {
             const long long h = g - ne;
             const int a = seg_of(po, T.n_act, h);
-            const int inst = T.act[a];
+            const int inst = act[a];
             const InstDesc& D = P.desc[inst];
             const long long j = D.ovl_off + (h - po[a]);
             ovl_global_insert(P, D, inst, P.oapp_key[j], P.oapp_cnt[j]);
