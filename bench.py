@@ -310,6 +310,27 @@ def run_ours(args, world, rank, local):
                    "vd_batch_get_changes_all for every step"}
     seq.close()
 
+    # ---- options beyond steps a1-a8 on the same workload: the event classes
+    # of Section 3.2.4, and the centre match of Section 3.2.3 (with events) ----
+    variants = {}
+    for name, opts in (("events", dict(events=True)),
+                       ("centroid_match_r8_events", dict(events=True, match_rule=vd.VD_MATCH_CENTROID,
+                                                         match_radius=8))):
+        vb = vd.Batch([(Lx, Ly)], sequence=n, stream=s.cuda_stream, **opts)
+        for _ in range(max(1, args.warmup)):
+            vb.push(dev)
+        torch.cuda.synchronize()
+        vsteps = max(1, min(args.steps, 5))
+        e0.record(s)
+        for _ in range(vsteps):
+            vb.push(dev)
+        e1.record(s)
+        torch.cuda.synchronize()
+        vms = max_over_ranks(e0.elapsed_time(e1), world)
+        variants[name] = {"value": world * sites_per_step * vsteps / (vms / 1e3) / 1e9, "unit": UNIT,
+                          "ms_per_step": vms / vsteps, "steps": vsteps}
+        vb.close()
+
     # ---- the plain per-frame path (vd_push_frame, one frame per call) ----
     det = vd.Detector(Lx, Ly, stream=s.cuda_stream)
     for F in dev[: min(n, 4)]:
@@ -342,7 +363,7 @@ def run_ours(args, world, rank, local):
                        "l2_policy": "inputs larger than L2 (each step reads all frames once)",
                        "parallelism": f"replicas x{world}"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
-            "gpu_launches": launches, "plain_per_frame": plain,
+            "gpu_launches": launches, "plain_per_frame": plain, "options": variants,
         }
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -65,10 +65,22 @@ typedef struct vd_config {
     int32_t max_components;    /* capacity for bubbles per frame; 0 = ceil(Lx*Ly/2) (cannot overflow) */
     int32_t max_edges;         /* capacity for links per frame; 0 = 3*max_components + 64 */
     void* stream;              /* cudaStream_t for all device work; NULL = legacy default stream */
+    int32_t events;            /* 1: classify the active labels into bulk / boundary events (Section 3.2.4) */
+    int32_t match_rule;        /* VD_MATCH_OVERLAP (default) or VD_MATCH_CENTROID (Section 3.2.3) */
+    int32_t match_radius;      /* VD_MATCH_CENTROID: largest centre displacement matched, in sites (>= 1) */
 } vd_config;
 
+/* Isomorphism Phi between past and now labels (Section 3.2.3). OVERLAP: the
+ * mutual best overlap of the two frames' bubbles (largest shared site count,
+ * ties to the smallest label). CENTROID: the paper's kinematic comparison of
+ * the two sets of centres -- mutual nearest centres (minimum-image squared
+ * distance in 1/1024 sites, ties to the smallest label) no farther apart than
+ * match_radius sites. */
+enum { VD_MATCH_OVERLAP = 0, VD_MATCH_CENTROID = 1 };
+
 /* Fill `cfg` with defaults for an Lx x Ly lattice (threshold 0.5, VD_ABOVE,
- * 4-connectivity, automatic capacities, default stream). */
+ * 4-connectivity, automatic capacities, default stream, no event classes,
+ * overlap match). */
 vd_status vd_config_init(vd_config* cfg, int32_t Lx, int32_t Ly);
 
 typedef struct vd_ctx vd_ctx;
@@ -94,7 +106,17 @@ vd_status vd_push_frame_host(vd_ctx* ctx, const float* h_field, size_t pitch);
  * writes an array only when it fits (else returns VD_ERR_CAPACITY after
  * writing all counts). `breaking` / `breaking_prev` / `arising` are sorted by
  * now-key; `breaking_prev[i]` is breaking[i] in past labels. `active` (length
- * n_now) is the local trigger: 1 for labels at an end of a flip. */
+ * n_now) holds per-label flags: bit 0 (VD_EV_ACTIVE) is the local trigger, set
+ * for labels at an end of a flip; the event classes of Section 3.2.4
+ * ("Extracting Topology Change Events") sit above it: VD_EV_BULK (active and
+ * linked to at least three active labels in the past or in the now
+ * triangulation), VD_EV_BOUNDARY (active, a boundary point of one
+ * triangulation -- an end of a link whose ends share exactly one neighbour --
+ * linked there to an active boundary point), VD_EV_BPOINT_NOW /
+ * VD_EV_BPOINT_PAST (the active label is a boundary point of that
+ * triangulation); the classes are computed when the config sets `events`.
+ * Inactive labels are 0. */
+enum { VD_EV_ACTIVE = 1, VD_EV_BULK = 2, VD_EV_BOUNDARY = 4, VD_EV_BPOINT_NOW = 8, VD_EV_BPOINT_PAST = 16 };
 typedef struct vd_changes {
     int64_t frame_index;       /* 0-based index of the frame these results belong to */
     int32_t n_prev, n_now;     /* bubbles in the past and current frame */

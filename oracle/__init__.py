@@ -8,7 +8,15 @@ fields of ``paper_1607_00908_gb300.inputs``.
 from .detect import (  # noqa: F401
     Q,
     Detector,
+    EV_ACTIVE,
+    EV_BOUNDARY,
+    EV_BPOINT_NOW,
+    EV_BPOINT_PAST,
+    EV_BULK,
+    adjacency,
+    boundary_point,
     centroids_q10,
+    classify_events,
     component_sums,
     delaunay_edges,
     flips,
@@ -16,6 +24,7 @@ from .detect import (  # noqa: F401
     incircle,
     label_components,
     make_keys,
+    match_centroid,
     match_overlap,
     orient2d,
     owners,

@@ -397,6 +397,54 @@ def match_overlap(lab_prev: np.ndarray, lab_now: np.ndarray, K_prev: int, K_now:
     return phi, inv
 
 
+def _nearest(q: np.ndarray, c: np.ndarray, Lx: int, Ly: int, R2: int) -> np.ndarray:
+    """For every row of q (Q10 centres) the index of the nearest row of c by
+    minimum-image squared distance (int64), ties to the smallest index, or -1
+    when the nearest is farther than sqrt(R2). Brute force in chunks."""
+    out = np.full(q.shape[0], -1, dtype=np.int64)
+    if q.shape[0] == 0 or c.shape[0] == 0:
+        return out
+    cx = c[:, 0].astype(np.int64)
+    cy = c[:, 1].astype(np.int64)
+    for i0 in range(0, q.shape[0], 512):
+        qx = q[i0:i0 + 512, 0].astype(np.int64)[:, None]
+        qy = q[i0:i0 + 512, 1].astype(np.int64)[:, None]
+        dx = wrap(cx[None, :] - qx, Q * Lx)
+        dy = wrap(cy[None, :] - qy, Q * Ly)
+        d = dx * dx + dy * dy
+        j = np.argmin(d, axis=1)          # first index of the minimum: ties to the smallest
+        dmin = d[np.arange(d.shape[0]), j]
+        out[i0:i0 + 512] = np.where(dmin <= R2, j, -1)
+    return out
+
+
+def match_centroid(cq_prev: np.ndarray, cq_now: np.ndarray, Lx: int, Ly: int, radius: int):
+    """Label isomorphism Phi_{P->N} from the two sets of centres (Section 3.2.3,
+    the paper's kinematic comparison of frames a short time apart).
+
+    Reading: best_n(p) = the now centre nearest to past centre p, best_p(n)
+    the past centre nearest to now centre n (minimum-image squared distance in
+    1/1024 sites, ties to the smallest label), each only within `radius`
+    sites. Phi(p) = n exactly when the choice is mutual, which keeps the map
+    injective; every other label is unmatched (-1), as the paper excludes
+    vanishing and appearing bubbles. Returns (phi [K_prev], inv [K_now]).
+    """
+    cq_prev = np.asarray(cq_prev, dtype=np.int64).reshape(-1, 2)
+    cq_now = np.asarray(cq_now, dtype=np.int64).reshape(-1, 2)
+    K_prev, K_now = cq_prev.shape[0], cq_now.shape[0]
+    phi = np.full(K_prev, -1, dtype=np.int32)
+    inv = np.full(K_now, -1, dtype=np.int32)
+    R2 = (Q * int(radius)) ** 2
+    best_n = _nearest(cq_prev, cq_now, Lx, Ly, R2)
+    best_p = _nearest(cq_now, cq_prev, Lx, Ly, R2)
+    for p in range(K_prev):
+        n = int(best_n[p])
+        if n >= 0 and int(best_p[n]) == p:
+            phi[p] = n
+            inv[n] = p
+    return phi, inv
+
+
 # ----------------------------------------------------------------------------
 # Sections 3.2.3-3.2.4: translation, comparison, breaking and arising links
 # ----------------------------------------------------------------------------
@@ -448,6 +496,90 @@ def flips(E_prev: np.ndarray, E_now: np.ndarray, phi: np.ndarray, inv: np.ndarra
 
 
 # ----------------------------------------------------------------------------
+# Section 3.2.4 "Extracting Topology Change Events": bulk and boundary events
+# ----------------------------------------------------------------------------
+
+#: bits of the per-label event flags (bit 0 is the local trigger itself)
+EV_ACTIVE, EV_BULK, EV_BOUNDARY, EV_BPOINT_NOW, EV_BPOINT_PAST = 1, 2, 4, 8, 16
+
+
+def adjacency(E: np.ndarray, K: int) -> list:
+    """Neighbour sets of labels 0..K-1 from sorted link keys (both directions)."""
+    nb = [set() for _ in range(K)]
+    a, b = split_keys(E)
+    for x, y in zip(a.tolist(), b.tolist()):
+        nb[x].add(y)
+        nb[y].add(x)
+    return nb
+
+
+def boundary_point(nb: list, u: int) -> bool:
+    """Section 3.2.4: an edge whose two ends share exactly one neighbour is a
+    boundary edge (two shared neighbours: bulk edge); both ends of a boundary
+    edge are boundary points."""
+    return any(len(nb[u] & nb[v]) == 1 for v in nb[u])
+
+
+def classify_events(E_prev: np.ndarray, E_now: np.ndarray, phi: np.ndarray, inv: np.ndarray,
+                    active: np.ndarray) -> np.ndarray:
+    """Event flags of the now-labels (Section 3.2.4, "Extracting Topology Change Events").
+
+    The active points are the now-labels with the local trigger set; every one
+    is matched (flips only join matched labels), so its past label is
+    Phi^-1(a). Readings:
+
+    * eventsCount, counted in each triangulation: c_N(a) = active now
+      neighbours of a; c_P(a) = past neighbours q of Phi^-1(a) with Phi(q)
+      active (the past configuration seen through the isomorphism).
+    * bulk event point: active and, in a single configuration, linked to at
+      least three other active points: max(c_N, c_P) >= 3.
+    * boundary point of a triangulation: an end of a boundary edge (its two
+      ends share exactly one neighbour).
+    * boundary event point: active and, in the past or in the now
+      triangulation, a boundary point linked to at least one other active
+      point that is a boundary point of the same triangulation.
+
+    Returns uint8 flags per now-label: EV_ACTIVE (the local trigger), EV_BULK,
+    EV_BOUNDARY, EV_BPOINT_NOW / EV_BPOINT_PAST (the active point is a
+    boundary point of that triangulation); inactive labels get 0.
+    """
+    K_now = inv.shape[0]
+    K_prev = phi.shape[0]
+    flags = np.zeros(K_now, dtype=np.uint8)
+    act = np.asarray(active, dtype=np.uint8) != 0
+    if not act.any():
+        return flags
+    nbN = adjacency(E_now, K_now)
+    nbP = adjacency(E_prev, K_prev)
+
+    def active_now(n: int) -> bool:
+        return 0 <= n < K_now and bool(act[n])
+
+    def active_past(q: int) -> bool:   # past label q seen through Phi
+        return active_now(int(phi[q])) if phi[q] >= 0 else False
+
+    for a in np.flatnonzero(act).tolist():
+        ia = int(inv[a])
+        f = EV_ACTIVE
+        c_now = sum(1 for b in nbN[a] if active_now(b))
+        c_past = sum(1 for q in nbP[ia] if active_past(q)) if ia >= 0 else 0
+        if max(c_now, c_past) >= 3:
+            f |= EV_BULK
+        bnow = boundary_point(nbN, a)
+        bpast = ia >= 0 and boundary_point(nbP, ia)
+        if bnow:
+            f |= EV_BPOINT_NOW
+        if bpast:
+            f |= EV_BPOINT_PAST
+        ev_now = bnow and any(active_now(b) and boundary_point(nbN, b) for b in nbN[a])
+        ev_past = bpast and any(active_past(q) and boundary_point(nbP, q) for q in nbP[ia])
+        if ev_now or ev_past:
+            f |= EV_BOUNDARY
+        flags[a] = f
+    return flags
+
+
+# ----------------------------------------------------------------------------
 # Whole pipeline, one frame after another
 # ----------------------------------------------------------------------------
 
@@ -456,12 +588,19 @@ class Detector:
 
     ``push(F)`` runs threshold -> labels -> Q10 centroids -> Voronoi owners ->
     edge keys on F, then (from the second frame on) the match against the
-    previous frame and the flip lists. The first frame reports no changes.
+    previous frame (by overlap, or by centres with ``match="centroid"``), the
+    flip lists and, with ``events=True``, the event flags (``active`` carries
+    the local trigger in bit 0 and the classes of ``classify_events`` above
+    it). The first frame reports no changes.
     """
 
     def __init__(self, Lx: int, Ly: int, theta: float = 0.5, polarity: int = 1,
-                 connectivity: int = 4, workers: int = 1, voronoi: str = "kdtree"):
+                 connectivity: int = 4, workers: int = 1, voronoi: str = "kdtree",
+                 events: bool = False, match: str = "overlap", match_radius: int = 0):
         self.Lx, self.Ly = Lx, Ly
+        self.events = events
+        self.match = match
+        self.match_radius = match_radius
         self.theta, self.polarity = theta, polarity
         self.connectivity = connectivity
         self.workers = workers
@@ -488,9 +627,14 @@ class Detector:
                        global_trigger=0, K_prev=0, n_matched=0)
         else:
             p = self.prev
-            phi, inv = match_overlap(p["labels"], labels, p["K"], K)
+            if self.match == "centroid":
+                phi, inv = match_centroid(p["centroids"], cq, self.Lx, self.Ly, self.match_radius)
+            else:
+                phi, inv = match_overlap(p["labels"], labels, p["K"], K)
             fl = flips(p["edges"], E, phi, inv)
+            if self.events:
+                fl["active"] = classify_events(p["edges"], E, phi, inv, fl["active"])
             out.update(phi=phi, inv=inv, K_prev=p["K"], n_matched=int((phi >= 0).sum()), **fl)
-        self.prev = dict(labels=labels, K=K, edges=E)
+        self.prev = dict(labels=labels, K=K, edges=E, centroids=cq)
         self.frame += 1
         return out

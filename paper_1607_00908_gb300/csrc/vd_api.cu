@@ -77,6 +77,8 @@ struct vd_batch {
     StepTables all;               // every instance active
     StepTables sub;               // scratch table for subsets
     int grid_items = 0;
+    bool any_events = false;           // some instance classifies its events
+    bool any_centroid_match = false;   // some instance matches by centres
     // field pointer tables (device) and their host mirrors
     const float** d_fields = nullptr;
     long long* d_pitches = nullptr;
@@ -147,6 +149,9 @@ bool valid_cfg(const vd_config& c) {
     if (c.connectivity != 4) return false;
     if (c.polarity != VD_ABOVE && c.polarity != VD_BELOW) return false;
     if (c.max_components < 0 || c.max_edges < 0) return false;
+    if (c.events != 0 && c.events != 1) return false;
+    if (c.match_rule != VD_MATCH_OVERLAP && c.match_rule != VD_MATCH_CENTROID) return false;
+    if (c.match_rule == VD_MATCH_CENTROID && (c.match_radius < 1 || c.match_radius > (1 << 20))) return false;
     return true;
 }
 
@@ -197,6 +202,8 @@ Launch make_launch(vd_batch* b, const StepTables& T) {
     L.T.merge_pre = T.d_merge;
     L.T.pre = T.d_pre;
     L.grid_items = b->grid_items;
+    L.events = b->any_events;
+    L.centroid_match = b->any_centroid_match;
     L.grid_wide = 4 * b->grid_items;
     L.total_tilesA = T.total_tilesA;
     L.total_tilesV = T.total_tilesV;
@@ -263,6 +270,11 @@ vd_status create_batch(const vd_config* cfgs, int n, vd_batch** out, bool sequen
         D.Ly = c.Ly;
         D.thr = c.threshold;
         D.pol = c.polarity;
+        D.events = c.events;
+        D.match_rule = c.match_rule;
+        D.match_radius = c.match_rule == VD_MATCH_CENTROID ? c.match_radius : 0;
+        b->any_events = b->any_events || c.events;
+        b->any_centroid_match = b->any_centroid_match || c.match_rule == VD_MATCH_CENTROID;
         D.ntx = (c.Lx + TW - 1) / TW;
         D.nty = (c.Ly + TH - 1) / TH;
         D.vtx = (c.Lx + VW - 1) / VW;
@@ -346,12 +358,15 @@ vd_status create_batch(const vd_config* cfgs, int n, vd_batch** out, bool sequen
     P.p_accx = M.alloc<long long>(piece_cap);
     P.p_accy = M.alloc<long long>(piece_cap);
     P.wide = M.alloc<int>(piece_cap);
-    P.cq = M.alloc<int2>(comp);
+    P.cq[0] = M.alloc<int2>(comp);
+    P.cq[1] = M.alloc<int2>(comp);
     P.comp_root = M.alloc<int>(comp);
     P.bcnt = M.alloc<int>(bucket);
-    P.boff = M.alloc<int>(bucket);
-    P.bcq = M.alloc<int2>(comp);
-    P.bid = M.alloc<int>(comp);
+    for (int k = 0; k < 2; ++k) {
+        P.boff[k] = M.alloc<int>(bucket);
+        P.bcq[k] = M.alloc<int2>(comp);
+        P.bid[k] = M.alloc<int>(comp);
+    }
     P.best_n = M.alloc<unsigned long long>(comp);
     P.best_p = M.alloc<unsigned long long>(comp);
     P.phi = M.alloc<int>(comp);
@@ -650,7 +665,7 @@ vd_status get_array(vd_batch* b, int i, int which, void* out, int64_t cap, int64
             break;
         }
         case 1: cnt = N; src = b->P.owners + D.site_off; break;
-        case 2: cnt = 2ll * st.K; src = b->P.cq + D.comp_off; break;
+        case 2: cnt = 2ll * st.K; src = b->P.cq[slot] + D.comp_off; break;
         case 3: {
             cnt = st.E;
             esz = 8;

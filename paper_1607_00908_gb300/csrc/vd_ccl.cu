@@ -571,7 +571,7 @@ __global__ void k_comp_final(Pools P) {
         long long cy = (long long)Q * yq + floordiv_ll(2 * (long long)Q * P.p_accy[pid] + nn, 2 * nn);
         cx %= MX; if (cx < 0) cx += MX;
         cy %= MY; if (cy < 0) cy += MY;
-        P.cq[D.comp_off + c] = make_int2((int)cx, (int)cy);
+        P.cq[S.slot ^ 1][D.comp_off + c] = make_int2((int)cx, (int)cy);
         const int bx = (int)(cx / Q) / S.B, by = (int)(cy / Q) / S.B;
         atomicAdd(&P.bcnt[D.bucket_off + (long long)by * S.nbx + bx], 1);
     }
@@ -588,11 +588,12 @@ __global__ void k_bucket_scatter(Pools P) {
         const InstState& S = P.st[inst];
         const int c = P.p_comp[pid];
         if (c >= D.comp_cap) continue;
-        const int2 v = P.cq[D.comp_off + c];
-        const long long bk = D.bucket_off + (long long)((v.y / Q) / S.B) * S.nbx + (v.x / Q) / S.B;
-        const int pos = P.boff[bk] + atomicSub(&P.bcnt[bk], 1) - 1;
-        P.bcq[D.comp_off + pos] = v;
-        P.bid[D.comp_off + pos] = c;
+        const int now = S.slot ^ 1;
+        const int2 v = P.cq[now][D.comp_off + c];
+        const long long bk = (long long)((v.y / Q) / S.B) * S.nbx + (v.x / Q) / S.B;
+        const int pos = P.boff[now][D.bucket_off + bk] + atomicSub(&P.bcnt[D.bucket_off + bk], 1) - 1;
+        P.bcq[now][D.comp_off + pos] = v;
+        P.bid[now][D.comp_off + pos] = c;
     }
 }
 
@@ -650,7 +651,7 @@ __global__ __launch_bounds__(32 * LBL_WARPS) void k_run_labels(Pools P, StepTabl
                 lab[SW(lane * 32 + j0 + k)] = l[k];
             }
     }
-    if (!S.has_prev) return;   // warp-uniform
+    if (!S.has_prev || D.match_rule) return;   // warp-uniform; the centroid match needs no overlaps
 
     // 2. overlap runs with the past frame (same lattice, same tile)
     for (int k = lane; k < WSET; k += 32) {

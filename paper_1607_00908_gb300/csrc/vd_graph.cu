@@ -263,6 +263,80 @@ __global__ void k_match_best(Pools P, StepTable T) {
     });
 }
 
+// Centroid rule (Section 3.2.3, the kinematic comparison of the two sets of
+// centres): best_n(p) = the now centre nearest to past centre p, best_p(n)
+// the past centre nearest to now centre n, within the match radius; Phi is
+// then the mutual choice (k_match_phi). The search runs over the other
+// frame's bucket grid: every centre within R sites lies in a bucket at most
+// ceil(R / B) + 1 buckets away (the ragged last bucket adds one boundary).
+struct CentreGrid {
+    const int2* bcq;   // centres in bucket order
+    const int* bid;    // their labels
+    const int* boff;   // bucket offsets (nbx * nby + 1)
+    int B, nbx, nby;
+};
+
+__device__ int nearest_centre(const CentreGrid& G, int2 q, int Lx, int Ly, int radius) {
+    if (G.nbx <= 0 || G.nby <= 0) return -1;
+    const long long MX = (long long)Q * Lx, MY = (long long)Q * Ly;
+    const long long R2 = ((long long)Q * radius) * ((long long)Q * radius);
+    const int rr = (radius + G.B - 1) / G.B + 1;
+    int x0 = (q.x / Q) / G.B - rr, nx = 2 * rr + 1;
+    int y0 = (q.y / Q) / G.B - rr, ny = 2 * rr + 1;
+    if (nx >= G.nbx) { x0 = 0; nx = G.nbx; }   // the ring covers the grid: every column once
+    if (ny >= G.nby) { y0 = 0; ny = G.nby; }
+    int best = -1;
+    long long bd = R2;
+    for (int iy = 0; iy < ny; ++iy) {
+        const int by = ((y0 + iy) % G.nby + G.nby) % G.nby;
+        for (int ix = 0; ix < nx; ++ix) {
+            const int bx = ((x0 + ix) % G.nbx + G.nbx) % G.nbx;
+            const int b = by * G.nbx + bx;
+            for (int k = G.boff[b]; k < G.boff[b + 1]; ++k) {
+                const int2 c = G.bcq[k];
+                const long long dx = wrap_ll((long long)c.x - q.x, MX), dy = wrap_ll((long long)c.y - q.y, MY);
+                const long long d = dx * dx + dy * dy;
+                const int id = G.bid[k];
+                if (d < bd || (d == bd && (best < 0 || id < best))) {
+                    bd = d;
+                    best = id;
+                }
+            }
+        }
+    }
+    return best;
+}
+
+__global__ void k_match_kin(Pools P, StepTable T) {
+    pdl_enter();
+    // past centres: the nearest now centre
+    for_items(T, PRE_KP, [&](int inst, long long p) {
+        const InstDesc& D = P.desc[inst];
+        if (!D.match_rule) return;
+        const InstState& S = P.st[inst];
+        const int now = S.slot ^ 1;
+        const InstDesc& DP = P.desc[S.prev_inst];
+        const CentreGrid G{P.bcq[now] + D.comp_off, P.bid[now] + D.comp_off, P.boff[now] + D.bucket_off, S.B,
+                           S.nbx, S.nby};
+        const int2 q = P.cq[S.prev_buf][DP.comp_off + p];
+        const int n = nearest_centre(G, q, D.Lx, D.Ly, D.match_radius);
+        P.best_n[D.comp_off + p] = n >= 0 ? pack_best(1u, n) : 0ull;
+    });
+    // now centres: the nearest past centre
+    for_items(T, PRE_K, [&](int inst, long long n) {
+        const InstDesc& D = P.desc[inst];
+        const InstState& S = P.st[inst];
+        if (!D.match_rule || !S.has_prev) return;
+        const int now = S.slot ^ 1, pb = S.prev_buf;
+        const InstDesc& DP = P.desc[S.prev_inst];
+        const InstState& SP = P.st[S.prev_inst];
+        const CentreGrid G{P.bcq[pb] + DP.comp_off, P.bid[pb] + DP.comp_off, P.boff[pb] + DP.bucket_off,
+                           SP.Bs[pb], SP.nbxs[pb], SP.nbys[pb]};
+        const int p = nearest_centre(G, P.cq[now][D.comp_off + n], D.Lx, D.Ly, D.match_radius);
+        P.best_p[D.comp_off + n] = p >= 0 ? pack_best(1u, p) : 0ull;
+    });
+}
+
 __global__ void k_match_phi(Pools P, StepTable T) {
     pdl_enter();
     for_items(T, PRE_KP, [&](int inst, long long p) {
@@ -437,6 +511,161 @@ __global__ void k_flip_write(Pools P, StepTable T) {
     for_items(T, PRE_K, [&](int inst, long long a) { compare_row<true>(P, inst, (int)a); });
 }
 
+// ---------------------------------------------------------------------------
+// Event classes of the active labels (Section 3.2.4, "Extracting Topology
+// Change Events"). For each active now-bubble a (its past label ia = Phi^-1(a)
+// exists: flips join matched labels only):
+//   c_N = active now neighbours of a, c_P = past neighbours q of ia whose
+//   Phi(q) is active; bulk event point: max(c_N, c_P) >= 3;
+//   boundary point of a triangulation: an end of a link whose ends share
+//   exactly one neighbour; boundary event point: a boundary point of the past
+//   or the now triangulation linked there to an active boundary point.
+// The classes are OR-ed into the active flags above bit 0. One thread per
+// active row; rows are staged in local arrays so that their loads are issued
+// together, and shared neighbours are counted by merging sorted rows.
+// ---------------------------------------------------------------------------
+struct Graph {
+    const int* ro;     // row offsets (per-instance values)
+    const int* cl;     // columns
+    int cap;           // columns available
+    int K;             // rows
+};
+
+__device__ __forceinline__ void row_of(const Graph& G, int u, int& s, int& e) {
+    s = min(G.ro[u], G.cap);
+    e = min(G.ro[u + 1], G.cap);
+    if (e < s) e = s;
+}
+
+// labels in both sorted lists x[0..nx) and y[0..ny), counting stops at 2
+__device__ __forceinline__ int shared2(const int* x, int nx, const int* y, int ny) {
+    int i = 0, j = 0, n = 0;
+    while (i < nx && j < ny && n < 2) {
+        const int p = x[i], q = y[j];
+        n += (p == q) ? 1 : 0;
+        i += (p <= q) ? 1 : 0;
+        j += (q <= p) ? 1 : 0;
+    }
+    return n;
+}
+
+// true when one of row u's links shares exactly one neighbour
+__device__ bool boundary_pt_global(const Graph& G, int u) {
+    int s, e;
+    row_of(G, u, s, e);
+    for (int k = s; k < e; ++k) {
+        const int v = G.cl[k];
+        if (v < 0 || v >= G.K) continue;
+        int vs, ve;
+        row_of(G, v, vs, ve);
+        if (shared2(G.cl + s, e - s, G.cl + vs, ve - vs) == 1) return true;
+    }
+    return false;
+}
+
+// The same with row u and its neighbours' rows in registers when every one
+// of them has at most DREG entries (the usual Voronoi degrees): row u, the
+// neighbours' row ranges and all their entries are three rounds of
+// independent loads, and the shared neighbours are counted by comparisons.
+constexpr int DREG = 10;
+
+__device__ bool boundary_pt(const Graph& G, int u) {
+    int s, e;
+    row_of(G, u, s, e);
+    const int nu = e - s;
+    if (nu > DREG) return boundary_pt_global(G, u);
+    int ru[DREG], vs[DREG], vn[DREG];
+    bool small = true;
+#pragma unroll
+    for (int k = 0; k < DREG; ++k) ru[k] = k < nu ? G.cl[s + k] : -1;
+#pragma unroll
+    for (int k = 0; k < DREG; ++k) {
+        vs[k] = 0;
+        vn[k] = 0;
+        const int v = ru[k];
+        if (v >= 0 && v < G.K) {
+            int a, b;
+            row_of(G, v, a, b);
+            vs[k] = a;
+            vn[k] = b - a;
+            small = small && (b - a) <= DREG;
+        }
+    }
+    if (!small) return boundary_pt_global(G, u);
+    bool hit = false;
+#pragma unroll
+    for (int k = 0; k < DREG; ++k) {
+        int n = 0;
+#pragma unroll
+        for (int t = 0; t < DREG; ++t) {
+            const int w = t < vn[k] ? G.cl[vs[k] + t] : -2;
+#pragma unroll
+            for (int j = 0; j < DREG; ++j) n += (ru[j] == w) ? 1 : 0;
+        }
+        hit = hit || (vn[k] > 0 && n == 1);
+    }
+    return hit;
+}
+
+__global__ void k_events(Pools P, StepTable T) {
+    pdl_enter();
+    for_items(T, PRE_K, [&](int inst, long long a_) {
+        const int a = (int)a_;
+        const InstDesc& D = P.desc[inst];
+        const long long co = D.comp_off;
+        if (!D.events || !(P.active[co + a] & EV_ACTIVE)) return;
+        const InstState& S = P.st[inst];
+        const int ia = S.has_prev ? P.inv[co + a] : -1;
+        const int now = S.slot ^ 1;
+        const int K = min(S.K, D.comp_cap);
+        const Graph GN{P.rowoff[now] + co, P.cols[now] + 2 * D.edge_off, 2 * D.edge_cap, K};
+        const int* phi = P.phi + co;
+        const unsigned char* act = P.active + co;
+        auto active_now = [&](int n) { return n >= 0 && n < K && (act[n] & EV_ACTIVE); };
+        unsigned f = 0;
+        // the now triangulation
+        int c_now = 0;
+        bool bnow = false, evnow = false;
+        {
+            int s, e;
+            row_of(GN, a, s, e);
+#pragma unroll 8
+            for (int k = s; k < e; ++k) c_now += active_now(GN.cl[k]) ? 1 : 0;
+            bnow = boundary_pt(GN, a);
+            if (bnow)
+                for (int k = s; k < e && !evnow; ++k) {
+                    const int b = GN.cl[k];
+                    evnow = active_now(b) && boundary_pt(GN, b);
+                }
+        }
+        // the past triangulation, seen through Phi
+        int c_past = 0;
+        bool bpast = false, evpast = false;
+        if (ia >= 0) {
+            const InstDesc& DP = P.desc[S.prev_inst];
+            const int Kp = S.K_prev;
+            const Graph GP{P.rowoff[S.prev_buf] + DP.comp_off, P.cols[S.prev_buf] + 2 * DP.edge_off,
+                           2 * DP.edge_cap, Kp};
+            auto active_past = [&](int q) { return q >= 0 && q < Kp && q < D.comp_cap && active_now(phi[q]); };
+            int s, e;
+            row_of(GP, ia, s, e);
+#pragma unroll 8
+            for (int k = s; k < e; ++k) c_past += active_past(GP.cl[k]) ? 1 : 0;
+            bpast = boundary_pt(GP, ia);
+            if (bpast)
+                for (int k = s; k < e && !evpast; ++k) {
+                    const int q = GP.cl[k];
+                    evpast = active_past(q) && boundary_pt(GP, q);
+                }
+        }
+        if (max(c_now, c_past) >= 3) f |= EV_BULK;
+        if (evnow || evpast) f |= EV_BOUNDARY;
+        if (bnow) f |= EV_BPOINT_NOW;
+        if (bpast) f |= EV_BPOINT_PAST;
+        if (f) P.active[co + a] = (unsigned char)(EV_ACTIVE | f);
+    });
+}
+
 // packed copy of every instance's breaking keys (then their past keys), arising
 // keys and active flags: out = [breaking (nb) | breaking_prev (nb) | arising]
 __global__ void k_gather_changes(Pools P, const long long* off, int n, long long nb, unsigned long long* out,
@@ -472,6 +701,7 @@ void launch_graph_csr(const Launch& L) {
 
 void launch_graph_match(const Launch& L) {
     const int g = L.grid_wide;
+    if (L.centroid_match) launch_step(L, k_match_kin, dim3(g), dim3(256), L.P, L.T);
     launch_step(L, k_match_best, dim3(g), dim3(256), L.P, L.T);
     launch_step(L, k_match_phi, dim3(g), dim3(256), L.P, L.T);
 }
@@ -485,6 +715,7 @@ void launch_graph_flips(const Launch& L) {
     launch_plan(L, 0, ends_bit(SCAN_FLIPS) | ends_bit(SCAN_FLIPS_A), pre_bit(PRE_FB) | pre_bit(PRE_FA));
     launch_scan2(L, SCAN_FLIPS, SCAN_FLIPS_A);
     launch_step(L, k_flip_write, dim3(g), dim3(256), L.P, L.T);
+    if (L.events) launch_step(L, k_events, dim3(g), dim3(256), L.P, L.T);
 }
 
 void launch_begin(const Launch& L) {

@@ -49,6 +49,18 @@ enum : int {
     ERR_PREV = 64,          // the past frame (same step) had an error
 };
 
+// bits of the per-bubble active flags: bit 0 is the local trigger (an end of a
+// breaking or arising link); the others are the event classes of Section
+// 3.2.4 (bulk / boundary event point; boundary point of the now / past
+// triangulation)
+enum EventBits : unsigned {
+    EV_ACTIVE = 1u,
+    EV_BULK = 2u,
+    EV_BOUNDARY = 4u,
+    EV_BPOINT_NOW = 8u,
+    EV_BPOINT_PAST = 16u,
+};
+
 // ---------------------------------------------------------------------------
 // Static per-instance description (written once at creation)
 // ---------------------------------------------------------------------------
@@ -76,6 +88,10 @@ struct InstDesc {
     int comp_cap, edge_cap;
     int ehash_mask, ohash_mask;
     int bucket_cap, ovl_cap;
+    int events;              // classify the active labels (Section 3.2.4)
+    int match_rule;          // VD_MATCH_OVERLAP / VD_MATCH_CENTROID
+    int match_radius;        // centroid match: largest displacement, sites
+    int pad1;
 };
 
 // ---------------------------------------------------------------------------
@@ -96,7 +112,8 @@ struct InstState {
     int K, K_prev;           // bubbles now (clamped to the capacity) / previous frame
     int K_roots;             // roots found by labelling this step, before clamping
     int E, E_prev;           // links now / previous frame
-    int B, nbx, nby;         // bucket grid
+    int B, nbx, nby;         // bucket grid of the frame in progress
+    int Bs[2], nbxs[2], nbys[2];   // bucket grid of the frame stored in each buffer
     int n_matched;
     int n_break, n_arise;
     int n_wide;
@@ -153,12 +170,14 @@ struct Pools {
     long long* p_accy;
     int* wide;               // pieces whose sums need the exact per-site path
     // bubbles
-    int2* cq;                // centroids (now)
+    int2* cq[2];             // centroids of the frame in each buffer (the step writes slot ^ 1)
     int* comp_root;          // root piece of each bubble
     int* bcnt;               // bucket counts (zero between steps)
-    int* boff;               // bucket offsets (global scan values)
-    int2* bcq;               // centroids in bucket order
-    int* bid;                // bubble id in bucket order
+    // bucket grid of the frame in each buffer: offsets (per-instance scan
+    // values), centroids in bucket order, bubble ids in bucket order
+    int* boff[2];
+    int2* bcq[2];
+    int* bid[2];
     unsigned long long* best_n;   // indexed by past label
     unsigned long long* best_p;   // indexed by now label
     int* phi;                // past -> now, -1 unmatched
@@ -409,6 +428,8 @@ struct Launch {
     long long* nlaunch;  // host counter of kernel launches
     cudaError_t* err;    // first launch error of the step (host)
     bool sequence;       // some instance's past frame is produced in the same step
+    bool events;         // some instance classifies its events
+    bool centroid_match; // some instance matches by centres
     cudaStream_t s;
     Pools P;
     StepTable T;

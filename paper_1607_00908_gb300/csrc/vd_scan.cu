@@ -54,6 +54,10 @@ __global__ __launch_bounds__(PLAN_THREADS) void k_plan(Pools P, StepTable T, int
                 } else {
                     S.B = 4; S.nbx = 0; S.nby = 0;
                 }
+                const int nw = S.slot ^ 1;   // the grid is kept with the frame's buffer
+                S.Bs[nw] = S.B;
+                S.nbxs[nw] = S.nbx;
+                S.nbys[nw] = S.nby;
                 if (S.prev_same) {
                     // the past frame was labelled in this step by instance prev_inst
                     const int kp = P.st[S.prev_inst].K;
@@ -75,7 +79,7 @@ __global__ __launch_bounds__(PLAN_THREADS) void k_plan(Pools P, StepTable T, int
             v[PRE_KR] = S.K_roots;
             // end values of the offset arrays (off[size] = total) of the scans that follow
             const int now = S.slot ^ 1;
-            if (ends & ends_bit(SCAN_BUCKETS)) P.boff[D.bucket_off + (long long)S.nbx * S.nby] = S.K;
+            if (ends & ends_bit(SCAN_BUCKETS)) P.boff[now][D.bucket_off + (long long)S.nbx * S.nby] = S.K;
             if (ends & ends_bit(SCAN_DEG)) P.rowoff[now][D.comp_off + S.K] = 2 * S.n_edge_list;
             if (ends & ends_bit(SCAN_FLIPS)) P.foff[D.comp_off + S.K] = S.n_break;
             if (ends & ends_bit(SCAN_FLIPS_A)) P.foff_a[D.comp_off + S.K] = S.n_arise;
@@ -137,7 +141,7 @@ __device__ __forceinline__ void scan_write(const Pools& P, int kind, int inst, l
             P.rankpre[D.grp_off + j] = v;
             P.rgcnt[D.grp_off + j] = 0;   // zero again for the next step (stores after all loads)
             break;
-        case SCAN_BUCKETS: P.boff[D.bucket_off + j] = v; break;
+        case SCAN_BUCKETS: P.boff[P.st[inst].slot ^ 1][D.bucket_off + j] = v; break;
         case SCAN_DEG: P.rowoff[P.st[inst].slot ^ 1][D.comp_off + j] = v; break;
         case SCAN_FLIPS: P.foff[D.comp_off + j] = v; break;
         default: P.foff_a[D.comp_off + j] = v; break;

@@ -176,9 +176,9 @@ __global__ __launch_bounds__(32 * VWARPS, 16) void k_voronoi(Pools P, StepTable 
     const int Bk = S.B, nbx = S.nbx, nby = S.nby;
     const int bx0 = x0 / Bk, bx1 = (x0 + ncols - 1) / Bk;
     const int by0 = y0 / Bk, by1 = (y0 + nrows - 1) / Bk;
-    const int* boff = P.boff + D.bucket_off;
-    const int2* bcq = P.bcq + D.comp_off;
-    const int* bid = P.bid + D.comp_off;
+    const int* boff = P.boff[S.slot ^ 1] + D.bucket_off;
+    const int2* bcq = P.bcq[S.slot ^ 1] + D.comp_off;
+    const int* bid = P.bid[S.slot ^ 1] + D.comp_off;
     int* cxs = s_cx[warp];
     int* cys = s_cy[warp];
     int* ids = s_id[warp];
@@ -496,7 +496,7 @@ __global__ __launch_bounds__(32 * LINK_WARPS) void k_links(Pools P, StepTable T)
     const int x0 = tx * VW, y0 = ty * VH;
     const int ncols = min(VW, D.Lx - x0), nrows = min(VH, D.Ly - y0);
     const long long MX = (long long)Q * D.Lx, MY = (long long)Q * D.Ly;
-    const int2* cq = P.cq + D.comp_off;
+    const int2* cq = P.cq[P.st[inst].slot ^ 1] + D.comp_off;
     const int* own = P.owners + D.site_off;
     int* S = s_own[warp];
     unsigned long long* list = s_list[warp];

@@ -27,6 +27,10 @@ VD_ERR_STATE = -6
 VD_ERR_UNSUPPORTED = -7
 VD_ABOVE = 1
 VD_BELOW = -1
+# per-label flags of the `active` arrays (bit 0: local trigger; event classes above it)
+VD_EV_ACTIVE, VD_EV_BULK, VD_EV_BOUNDARY, VD_EV_BPOINT_NOW, VD_EV_BPOINT_PAST = 1, 2, 4, 8, 16
+# isomorphism rules (Section 3.2.3)
+VD_MATCH_OVERLAP, VD_MATCH_CENTROID = 0, 1
 
 #: every symbol include/vd.h declares
 EXPORTS = (
@@ -56,7 +60,7 @@ class vd_config(C.Structure):
     _fields_ = [
         ("Lx", C.c_int32), ("Ly", C.c_int32), ("threshold", C.c_float), ("polarity", C.c_int32),
         ("connectivity", C.c_int32), ("max_components", C.c_int32), ("max_edges", C.c_int32),
-        ("stream", C.c_void_p),
+        ("stream", C.c_void_p), ("events", C.c_int32), ("match_rule", C.c_int32), ("match_radius", C.c_int32),
     ]
 
 
@@ -171,7 +175,8 @@ def _check(s: int, where: str):
 # ----------------------------------------------------------------------------
 
 def vd_config_init(Lx: int, Ly: int, threshold: float = 0.5, polarity: int = VD_ABOVE,
-                   stream: int | None = None, max_components: int = 0, max_edges: int = 0) -> vd_config:
+                   stream: int | None = None, max_components: int = 0, max_edges: int = 0,
+                   events: bool = False, match_rule: int = VD_MATCH_OVERLAP, match_radius: int = 0) -> vd_config:
     cfg = vd_config()
     _check(lib().vd_config_init(C.byref(cfg), int(Lx), int(Ly)), "vd_config_init")
     cfg.threshold = float(threshold)
@@ -179,6 +184,9 @@ def vd_config_init(Lx: int, Ly: int, threshold: float = 0.5, polarity: int = VD_
     cfg.max_components = int(max_components)
     cfg.max_edges = int(max_edges)
     cfg.stream = C.c_void_p(stream or 0)
+    cfg.events = int(bool(events))
+    cfg.match_rule = int(match_rule)
+    cfg.match_radius = int(match_radius)
     return cfg
 
 
@@ -311,12 +319,14 @@ class Detector(_Base):
     """One periodic lattice (vd_create / vd_push_frame / vd_get_* / vd_destroy)."""
 
     def __init__(self, Lx: int, Ly: int, threshold: float = 0.5, polarity: int = VD_ABOVE,
-                 stream: int | None = None, max_components: int = 0, max_edges: int = 0):
+                 stream: int | None = None, max_components: int = 0, max_edges: int = 0,
+                 events: bool = False, match_rule: int = VD_MATCH_OVERLAP, match_radius: int = 0):
         if stream is None:
             import torch
             stream = torch.cuda.current_stream().cuda_stream
         self.Lx, self.Ly = Lx, Ly
-        self.cfg = vd_config_init(Lx, Ly, threshold, polarity, stream, max_components, max_edges)
+        self.cfg = vd_config_init(Lx, Ly, threshold, polarity, stream, max_components, max_edges,
+                                  events, match_rule, match_radius)
         self.h = vd_create(self.cfg)
 
     def push(self, field) -> None:
@@ -389,20 +399,23 @@ class Batch(_Base):
     lattice whose push takes n consecutive frames (vd_batch_create_sequence)."""
 
     def __init__(self, sizes, threshold: float = 0.5, polarity: int = VD_ABOVE, stream: int | None = None,
-                 max_components: int = 0, sequence: int = 0):
+                 max_components: int = 0, sequence: int = 0, events: bool = False,
+                 match_rule: int = VD_MATCH_OVERLAP, match_radius: int = 0):
         if stream is None:
             import torch
             stream = torch.cuda.current_stream().cuda_stream
         self.sizes = [(int(lx), int(ly)) for lx, ly in sizes]
+        opts = dict(events=events, match_rule=match_rule, match_radius=match_radius)
         if sequence:
             lx, ly = self.sizes[0]
             self.sizes = [(lx, ly)] * int(sequence)
-            cfg = vd_config_init(lx, ly, threshold, polarity, stream, max_components)
+            cfg = vd_config_init(lx, ly, threshold, polarity, stream, max_components, **opts)
             h = C.c_void_p()
             _check(lib().vd_batch_create_sequence(C.byref(cfg), int(sequence), C.byref(h)), "vd_batch_create_sequence")
             self.h = h
         else:
-            cfgs = [vd_config_init(lx, ly, threshold, polarity, stream, max_components) for lx, ly in self.sizes]
+            cfgs = [vd_config_init(lx, ly, threshold, polarity, stream, max_components, **opts)
+                    for lx, ly in self.sizes]
             self.h = vd_batch_create(cfgs)
 
     def push(self, fields) -> None:

@@ -67,10 +67,14 @@ def check_frame(det, r, what=("labels", "centroids", "owners", "edges", "changes
             assert np.array_equal(det.match(), r["phi"]), f"{tag} phi differs"
 
 
-def run_pair(frames, threshold=0.5, polarity=1, voronoi="kdtree", what=None, tag=""):
+def run_pair(frames, threshold=0.5, polarity=1, voronoi="kdtree", what=None, tag="", events=False,
+             match="overlap", match_radius=0):
     Ly, Lx = frames[0].shape
-    det = vd.Detector(Lx, Ly, threshold=threshold, polarity=polarity)
-    ref = O.Detector(Lx, Ly, theta=threshold, polarity=polarity, voronoi=voronoi, workers=-1)
+    det = vd.Detector(Lx, Ly, threshold=threshold, polarity=polarity, events=events,
+                      match_rule=vd.VD_MATCH_CENTROID if match == "centroid" else vd.VD_MATCH_OVERLAP,
+                      match_radius=match_radius)
+    ref = O.Detector(Lx, Ly, theta=threshold, polarity=polarity, voronoi=voronoi, workers=-1, events=events,
+                     match=match, match_radius=match_radius)
     for f, F in enumerate(frames):
         det.push(torch.from_numpy(np.ascontiguousarray(F)).cuda())
         r = ref.push(F)
@@ -207,3 +211,57 @@ def test_capacity_overflow_is_reported():
     G[10:20, 10:20] = 1.0
     det.push(torch.from_numpy(G).cuda())
     assert det.counts()[0] == 1
+
+
+def test_event_classes_with_boundary_points():
+    """Few large bubbles (64 x 64, sigma 6): the digital link graph of frame 1
+    is not a full triangulation of the torus, so some active labels are
+    boundary points (a link whose ends share one neighbour) and boundary event
+    points (Section 3.2.4). The flags must equal the oracle's; the oracle is
+    checked to show the boundary class, so the case keeps its point."""
+    frames = list(I.noise_frames(64, 6.0, 5, 0.05, 18))
+    ref = O.Detector(64, 64, events=True)
+    rs = [ref.push(F) for F in frames]
+    assert any(int((r["active"] & O.EV_BOUNDARY).sum()) for r in rs)
+    run_pair(frames, tag="events 64", events=True)
+
+
+@pytest.mark.parametrize("radius", [1, 3, 12])
+def test_centroid_match_sequences(radius):
+    """Isomorphism by centres (VD_MATCH_CENTROID): sheared smoothed noise on a
+    lattice ragged against the tiles, with the event classes on. Phi, the flips
+    and the flags must equal the oracle's; radius 1 leaves many labels
+    unmatched, 12 reaches across several buckets."""
+    F = I.smoothed_noise(136, 200, 3.0, seed=radius)
+    frames = [F]
+    for k in range(3):
+        frames.append(I.shear_resample(frames[-1], 0.02, 0.01, np.random.default_rng(k + 10 * radius)))
+    r = run_pair(frames, tag=f"centroid r{radius}", events=True, match="centroid", match_radius=radius)
+    assert r["K"] > 10
+
+
+def test_centroid_match_c1_frames():
+    """1024x1024 smoothed noise, centre match within 8 sites, event classes on."""
+    frames = list(I.workload_c1(seed=2, n_frames=3))
+    r = run_pair(frames, tag="c1 centroid", events=True, match="centroid", match_radius=8)
+    assert r["n_matched"] > 0.8 * r["K"]
+
+
+def test_centroid_match_in_batches():
+    """Sequence and independent batches with the centre match: every frame's
+    changes equal the oracle run frame by frame (the past grid of a sequence
+    instance is the previous instance's grid of the same push)."""
+    frames = list(I.noise_frames(256, 3.0, 6, 0.01, 5))
+    dev = [torch.from_numpy(np.ascontiguousarray(F)).cuda() for F in frames]
+    ref = O.Detector(256, 256, events=True, match="centroid", match_radius=6)
+    rs = [ref.push(F) for F in frames]
+    seq = vd.Batch([(256, 256)], sequence=3, events=True, match_rule=vd.VD_MATCH_CENTROID, match_radius=6)
+    for p in range(2):
+        seq.push(dev[3 * p:3 * p + 3])
+        for i in range(3):
+            r = rs[3 * p + i]
+            ch = seq.changes(i)
+            assert np.array_equal(ch["breaking"], r["breaking"]), (p, i)
+            assert np.array_equal(ch["arising"], r["arising"]), (p, i)
+            assert np.array_equal(ch["active"], r["active"]), (p, i)
+    seq.close()

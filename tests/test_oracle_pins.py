@@ -518,7 +518,7 @@ def test_single_t1_flip_matches_bruteforce_delaunay_difference():
                    (int(np.floor(pts0[l][1] - s * vy / dist)) % Ly) + 0.5)
         st0 = I.DiscState(Lx, np.array([p[0] for p in pts0]), np.array([p[1] for p in pts0]), np.full(K, r))
         st1 = I.DiscState(Lx, np.array([p[0] for p in pts1]), np.array([p[1] for p in pts1]), np.full(K, r))
-        d = O.Detector(Lx, Ly, voronoi="brute")
+        d = O.Detector(Lx, Ly, voronoi="brute", events=True)
         ra = d.push(_raster_rect(st0, Lx, Ly))
         rb = d.push(_raster_rect(st1, Lx, Ly))
         if ra["K"] != K or rb["K"] != K or rb["n_matched"] != K:
@@ -542,7 +542,13 @@ def test_single_t1_flip_matches_bruteforce_delaunay_difference():
         brk = {tuple(sorted((m1[x], m1[y]))) for x, y in zip(*[v.tolist() for v in O.split_keys(rb["breaking"])])}
         ari = {tuple(sorted((m1[x], m1[y]))) for x, y in zip(*[v.tolist() for v in O.split_keys(rb["arising"])])}
         assert brk == s0 - s1 and ari == s1 - s0
-        assert int(rb["active"].sum()) == 4
+        assert int((rb["active"] & O.EV_ACTIVE).sum()) == 4
+        # a bulk T1 on the torus: the four active labels are bulk event points
+        # (each linked to three active labels in one triangulation), and no
+        # edge of a periodic triangulation is a boundary edge
+        act = np.flatnonzero(rb["active"])
+        assert act.size == 4
+        assert all(int(rb["active"][x]) == O.EV_ACTIVE | O.EV_BULK for x in act.tolist())
         prev = {tuple(sorted((m0[x], m0[y]))) for x, y in zip(*[v.tolist() for v in O.split_keys(rb["breaking_prev"])])}
         assert prev == s0 - s1
         found += 1
@@ -617,3 +623,155 @@ def test_overlap_tie_goes_to_smallest_label():
     phi, inv = O.match_overlap(np.array([[0, 0, 0, 0, 0]], np.int32),
                                np.array([[0, 1, 1, 1, -1]], np.int32), 1, 2)
     assert phi.tolist() == [1] and inv.tolist() == [-1, 0]
+
+
+# ----------------------------------------------------------------------------
+# Section 3.2.4 "Extracting Topology Change Events": hand-built triangulations
+# whose event classes follow from the definitions by counting
+# ----------------------------------------------------------------------------
+
+def _keys(pairs):
+    return np.sort(O.make_keys([p[0] for p in pairs], [p[1] for p in pairs])) if pairs else np.zeros(0, np.uint64)
+
+
+def _events(past, now, K):
+    phi = np.arange(K, dtype=np.int32)
+    inv = np.arange(K, dtype=np.int32)
+    fl = O.flips(_keys(past), _keys(now), phi, inv)
+    return fl, O.classify_events(_keys(past), _keys(now), phi, inv, fl["active"])
+
+
+def test_events_boundary_link_breaking():
+    """Two triangles (0,1,2), (1,2,3) sharing the bulk edge {1,2}; the boundary
+    edge {0,1} (its ends share only label 2) breaks. Labels 0 and 1 are active,
+    each linked to one other active label: boundary event points, not bulk.
+    In the past both are boundary points; now 1 is still a boundary point
+    (edge {1,2} shares only 3), 0 is not (its one edge {0,2} shares nothing)."""
+    past = [(0, 1), (0, 2), (1, 2), (1, 3), (2, 3)]
+    now = [(0, 2), (1, 2), (1, 3), (2, 3)]
+    fl, ev = _events(past, now, 4)
+    assert fl["breaking"].tolist() == O.make_keys([0], [1]).tolist() and fl["arising"].size == 0
+    E = O
+    assert ev.tolist() == [E.EV_ACTIVE | E.EV_BOUNDARY | E.EV_BPOINT_PAST,
+                           E.EV_ACTIVE | E.EV_BOUNDARY | E.EV_BPOINT_PAST | E.EV_BPOINT_NOW, 0, 0]
+
+
+def test_events_isolated_rhombus_is_bulk_and_boundary():
+    """A lone rhombus A=0, B=1, C=2, D=3 whose diagonal turns from {0,2} to
+    {1,3}: every label is linked to the three others in one triangulation
+    (bulk), and the rim edges share one label (boundary points linked to
+    active boundary points) -- a point in a bulk and a boundary event at once."""
+    past = [(0, 1), (1, 2), (2, 3), (0, 3), (0, 2)]
+    now = [(0, 1), (1, 2), (2, 3), (0, 3), (1, 3)]
+    _, ev = _events(past, now, 4)
+    allf = O.EV_ACTIVE | O.EV_BULK | O.EV_BOUNDARY | O.EV_BPOINT_PAST | O.EV_BPOINT_NOW
+    assert ev.tolist() == [allf] * 4
+
+
+def test_events_t1_inside_a_closed_patch_is_bulk_only():
+    """The rhombus 0-1-2-3 with its diagonal turning from {0,2} to {1,3},
+    closed by two apexes 4 and 5 linked to all four: every link shares at least
+    two labels in both frames, so there is no boundary edge and the four
+    active labels are bulk event points only."""
+    rim = [(0, 1), (1, 2), (2, 3), (0, 3)]
+    caps = [(4, 0), (4, 1), (4, 2), (4, 3), (5, 0), (5, 1), (5, 2), (5, 3)]
+    past = rim + caps + [(0, 2)]
+    now = rim + caps + [(1, 3)]
+    # sanity of the construction: label pairs that are linked share >= 2 labels
+    for E in (past, now):
+        nb = O.adjacency(_keys(E), 6)
+        assert all(len(nb[u] & nb[v]) >= 2 for u, v in E)
+    _, ev = _events(past, now, 6)
+    assert ev.tolist() == [O.EV_ACTIVE | O.EV_BULK] * 4 + [0, 0]
+
+
+def test_events_identity_and_unmatched():
+    """No flip: no flags. An unmatched past label never counts as an active
+    neighbour (it has no now label)."""
+    past = [(0, 1), (1, 2), (0, 2)]
+    _, ev = _events(past, past, 3)
+    assert not ev.any()
+    # past label 2 unmatched: the now frame has labels 0, 1 only
+    phi = np.array([0, 1, -1], np.int32)
+    inv = np.array([0, 1], np.int32)
+    fl = O.flips(_keys(past), _keys([]), phi, inv)
+    ev = O.classify_events(_keys(past), _keys([]), phi, inv, fl["active"])
+    assert fl["breaking"].tolist() == O.make_keys([0], [1]).tolist()
+    # 0 and 1: one active neighbour each (2 is unmatched), past edge {0,1}
+    # shares label 2 only -> boundary points linked to each other
+    assert ev.tolist() == [O.EV_ACTIVE | O.EV_BOUNDARY | O.EV_BPOINT_PAST] * 2
+
+
+# ----------------------------------------------------------------------------
+# Section 3.2.3, centre comparison (match_centroid): cases whose Phi follows
+# from the definition by hand
+# ----------------------------------------------------------------------------
+
+def _q(pts):
+    return np.array([[int(Q * x), int(Q * y)] for x, y in pts], dtype=np.int64).reshape(-1, 2)
+
+
+def test_centroid_match_permuted_translation():
+    """Centres moved by a small common shift and relabelled: Phi inverts the
+    relabelling (every centre's nearest is its own image, mutually); a shift
+    beyond the radius leaves every label unmatched."""
+    rng = np.random.default_rng(3)
+    L = 200
+    g = np.array([(20 * i + 5, 20 * j + 7) for i in range(10) for j in range(10)], dtype=float)
+    prev = _q(g)
+    perm = rng.permutation(len(g))
+    moved = (g + np.array([2.25, -1.5])) % L
+    now = _q(moved[perm])
+    phi, inv = O.match_centroid(prev, now, L, L, radius=4)
+    want = np.empty(len(g), dtype=np.int64)
+    want[perm] = np.arange(len(g))
+    assert phi.tolist() == want.tolist()
+    assert inv.tolist() == perm.tolist()
+    phi, inv = O.match_centroid(prev, now, L, L, radius=2)
+    assert (phi == -1).all() and (inv == -1).all()
+
+
+def test_centroid_match_ties_mutuality_and_seam():
+    """(a) a past centre midway between two now centres takes the smaller
+    label; (b) two past centres near one now centre: only the nearer is
+    matched (mutual choice), the other stays unmatched; (c) centres on both
+    sides of the periodic seam are 1 site apart, not L - 1."""
+    L = 64
+    prev = _q([(10, 10)])
+    now = _q([(12, 10), (8, 10)])
+    phi, inv = O.match_centroid(prev, now, L, L, radius=3)
+    assert phi.tolist() == [0] and inv.tolist() == [0, -1]
+    prev = _q([(20, 20), (23, 20)])
+    now = _q([(21, 20)])
+    phi, inv = O.match_centroid(prev, now, L, L, radius=5)
+    assert phi.tolist() == [0, -1] and inv.tolist() == [0]
+    prev = _q([(0.25, 30), (40, 40)])
+    now = _q([(63.5, 30.5), (40, 40)])
+    phi, inv = O.match_centroid(prev, now, L, L, radius=1)
+    assert phi.tolist() == [0, 1] and inv.tolist() == [0, 1]
+
+
+def test_centroid_match_equals_bruteforce_loops():
+    """The chunked numpy search equals a plain double loop on random centres."""
+    rng = np.random.default_rng(11)
+    Lx, Ly = 50, 37
+    prev = rng.integers(0, [Q * Lx, Q * Ly], size=(40, 2))
+    now = (prev[rng.permutation(40)[:33]] + rng.integers(-3 * Q, 3 * Q, size=(33, 2))) % [Q * Lx, Q * Ly]
+    R = 4
+    phi, inv = O.match_centroid(prev, now, Lx, Ly, radius=R)
+
+    def nearest(q, c):
+        best, bd = -1, (Q * R) ** 2
+        for j, (x, y) in enumerate(c.tolist()):
+            dx = O.wrap(x - int(q[0]), Q * Lx)
+            dy = O.wrap(y - int(q[1]), Q * Ly)
+            d = dx * dx + dy * dy
+            if d < bd or (d == bd and (best < 0 or j < best)):
+                best, bd = j, d
+        return best
+
+    bn = [nearest(p, now) for p in prev]
+    bp = [nearest(n, prev) for n in now]
+    want = [bn[p] if bn[p] >= 0 and bp[bn[p]] == p else -1 for p in range(40)]
+    assert phi.tolist() == want
+    assert sorted(i for i in inv.tolist() if i >= 0) == sorted(p for p in range(40) if want[p] >= 0)
