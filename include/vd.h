@@ -61,7 +61,7 @@ typedef struct vd_config {
     int32_t Lx, Ly;            /* lattice size, 1 <= Lx, Ly, Lx*Ly < 2^31 */
     float threshold;           /* bubble threshold */
     int32_t polarity;          /* VD_ABOVE or VD_BELOW */
-    int32_t connectivity;      /* 4 (only value supported) */
+    int32_t connectivity;      /* 4 (default) or 8 neighbours (Section 3.1) */
     int32_t max_components;    /* capacity for bubbles per frame; 0 = ceil(Lx*Ly/2) (cannot overflow) */
     int32_t max_edges;         /* capacity for links per frame; 0 = 3*max_components + 64 */
     void* stream;              /* cudaStream_t for all device work; NULL = legacy default stream */

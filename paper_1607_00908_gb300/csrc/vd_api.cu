@@ -146,11 +146,12 @@ bool valid_cfg(const vd_config& c) {
     if (c.Lx < 1 || c.Ly < 1) return false;
     if (c.Lx >= (1 << 21) || c.Ly >= (1 << 21)) return false;   // 1024*L must fit int32
     if ((long long)c.Lx * c.Ly >= (1ll << 31)) return false;
-    if (c.connectivity != 4) return false;
+    if (c.connectivity != 4 && c.connectivity != 8) return false;
     if (c.polarity != VD_ABOVE && c.polarity != VD_BELOW) return false;
     if (c.max_components < 0 || c.max_edges < 0) return false;
     if (c.events != 0 && c.events != 1) return false;
     if (c.match_rule != VD_MATCH_OVERLAP && c.match_rule != VD_MATCH_CENTROID) return false;
+    if (c.match_radius < 0) return false;
     if (c.match_rule == VD_MATCH_CENTROID && (c.match_radius < 1 || c.match_radius > (1 << 20))) return false;
     return true;
 }
@@ -271,6 +272,7 @@ vd_status create_batch(const vd_config* cfgs, int n, vd_batch** out, bool sequen
         D.thr = c.threshold;
         D.pol = c.polarity;
         D.events = c.events;
+        D.conn8 = c.connectivity == 8 ? 1 : 0;
         D.match_rule = c.match_rule;
         D.match_radius = c.match_rule == VD_MATCH_CENTROID ? c.match_radius : 0;
         b->any_events = b->any_events || c.events;

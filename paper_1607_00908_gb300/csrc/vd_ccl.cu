@@ -133,8 +133,11 @@ __device__ __forceinline__ int run_piece(const UfSmem& T, int id, int* root) {
     return -2 - T.par[SW(v)];
 }
 
-// union-find over runs; lane r owns row r; m = this lane's row mask, mu = row r-1
-__device__ void warp_runs_uf(UfSmem& T, unsigned long long m) {
+// union-find over runs; lane r owns row r; m = this lane's row mask, mu = row r-1.
+// 4-connectivity joins runs of rows r-1 and r that share a column; with
+// 8-connectivity a run of row r-1 widened by one column on each side joins
+// every run of row r it meets.
+__device__ void warp_runs_uf(UfSmem& T, unsigned long long m, bool conn8) {
     const int r = threadIdx.x & 31;
     const unsigned long long S = run_starts(m);
     {
@@ -152,11 +155,29 @@ __device__ void warp_runs_uf(UfSmem& T, unsigned long long m) {
     __syncwarp();
     if (r > 0) {
         const unsigned long long Su = run_starts(mu);
-        unsigned long long os = run_starts(m & mu);
-        while (os) {
-            const int c = __ffsll(os) - 1;
-            os &= os - 1;
-            runion(T.par, r * 32 + run_index(S, c), (r - 1) * 32 + run_index(Su, c));
+        if (!conn8) {
+            unsigned long long os = run_starts(m & mu);
+            while (os) {
+                const int c = __ffsll(os) - 1;
+                os &= os - 1;
+                runion(T.par, r * 32 + run_index(S, c), (r - 1) * 32 + run_index(Su, c));
+            }
+        } else {
+            unsigned long long tu = Su;
+            int ju = 0;
+            while (tu) {
+                const int cu = __ffsll(tu) - 1;
+                tu &= tu - 1;
+                const int len = run_length(mu, cu);
+                const unsigned long long ru = (len >= 64 ? ~0ull : ((1ull << len) - 1ull)) << cu;
+                unsigned long long hs = run_starts(m & (ru | (ru << 1) | (ru >> 1)));
+                while (hs) {
+                    const int c = __ffsll(hs) - 1;
+                    hs &= hs - 1;
+                    runion(T.par, r * 32 + run_index(S, c), (r - 1) * 32 + ju);
+                }
+                ++ju;
+            }
         }
     }
     __syncwarp();
@@ -266,7 +287,7 @@ __global__ __launch_bounds__(32 * CCL_WARPS, 8) void k_ccl_tiles(Pools P, StepTa
     TS.m[lane] = my_m;
 
     // 2. union-find over runs
-    warp_runs_uf(TS, my_m);
+    warp_runs_uf(TS, my_m, D.conn8 != 0);
 
     // 3. roots in raster order -> piece ids; a root's parent slot then holds
     //    -2 - (its piece id), so every run reaches its piece in two steps
@@ -391,13 +412,16 @@ __device__ __forceinline__ void punion(const Pools& P, int a, int b) {
 
 // one thread per border position (right edge, then bottom edge of every
 // tile); a position whose piece pair equals the previous position's on the
-// same edge adds nothing and is skipped
+// same edge adds nothing and is skipped. With 8-connectivity a position also
+// joins the diagonal neighbours across its edge (the next row / column), and
+// the right edge's first and last rows join across the tile corners.
 __global__ void k_ccl_merge(Pools P, StepTable T, int total) {
     pdl_enter();
     __shared__ int s_pre[SEG_CACHE];
     const int* pre = seg_table(T.merge_pre, T.n_act, s_pre);
     const int g = blockIdx.x * blockDim.x + threadIdx.x;
     int pa = -1, pb = -1, edge = -1;   // edge: (tile, side) of this position
+    int da[4] = {-1, -1, -1, -1}, db[4] = {-1, -1, -1, -1};   // diagonal pairs (8-connectivity)
     if (g < total) {
         const int a = seg_of_int(pre, T.n_act, g);
         const int inst = T.act[a];
@@ -406,15 +430,42 @@ __global__ void k_ccl_merge(Pools P, StepTable T, int total) {
         const int t = loc / (TW + TH), j = loc % (TW + TH);
         const int tx = t % D.ntx, ty = t / D.ntx;
         const int* bd = P.border + D.border_off;
+        const int nrows = min(TH, D.Ly - ty * TH), ncols = min(TW, D.Lx - tx * TW);
         if (j < TH) {
             const int tn = ty * D.ntx + (tx + 1) % D.ntx;
             pa = bd[(long long)t * BORDER + TH + j];
             pb = bd[(long long)tn * BORDER + j];
+            if (D.conn8) {
+                if (j + 1 < nrows) {
+                    da[0] = pa;
+                    db[0] = bd[(long long)tn * BORDER + j + 1];
+                    da[1] = bd[(long long)t * BORDER + TH + j + 1];
+                    db[1] = pb;
+                }
+                if (j == nrows - 1) {   // bottom-right corner: top-left site of the tile below-right
+                    const int tc = ((ty + 1) % D.nty) * D.ntx + (tx + 1) % D.ntx;
+                    da[2] = pa;
+                    db[2] = bd[(long long)tc * BORDER + 0];
+                }
+                if (j == 0) {           // top-right corner: bottom-left site of the tile above-right
+                    const int tyu = (ty + D.nty - 1) % D.nty;
+                    const int tc = tyu * D.ntx + (tx + 1) % D.ntx;
+                    const int nru = min(TH, D.Ly - tyu * TH);
+                    da[3] = pa;
+                    db[3] = bd[(long long)tc * BORDER + nru - 1];
+                }
+            }
         } else {
             const int k = j - TH;
             const int tn = ((ty + 1) % D.nty) * D.ntx + tx;
             pa = bd[(long long)t * BORDER + 2 * TH + TW + k];
             pb = bd[(long long)tn * BORDER + 2 * TH + k];
+            if (D.conn8 && k + 1 < ncols) {
+                da[0] = pa;
+                db[0] = bd[(long long)tn * BORDER + 2 * TH + k + 1];
+                da[1] = bd[(long long)t * BORDER + 2 * TH + TW + k + 1];
+                db[1] = pb;
+            }
         }
         edge = (g - j) * 2 + (j < TH ? 0 : 1);
     }
@@ -423,6 +474,9 @@ __global__ void k_ccl_merge(Pools P, StepTable T, int total) {
     const int pedge = __shfl_up_sync(0xffffffffu, edge, 1);
     const bool repeat = lane > 0 && pedge == edge && ppa == pa && ppb == pb;
     if (pa >= 0 && pb >= 0 && !repeat) punion(P, pa, pb);
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+        if (da[q] >= 0 && db[q] >= 0 && da[q] != db[q]) punion(P, da[q], db[q]);
 }
 
 // root of each piece; roots are counted per instance and marked in the root bitmap
@@ -507,7 +561,7 @@ __global__ __launch_bounds__(32 * WIDE_WARPS) void k_comp_wide(Pools P) {
         const int yr = qr / D.Lx, xr = qr - yr * D.Lx;
         const unsigned long long m = load_row_mask(P.fgbits[P.st[inst].slot ^ 1], D, x0, y0);
         TS.m[lane] = m;
-        warp_runs_uf(TS, m);
+        warp_runs_uf(TS, m, D.conn8 != 0);
         const unsigned long long Sq = run_starts(TS.m[yq - y0]);
         const int lq = (yq - y0) * 32 + run_index(Sq, xq - x0);
         const unsigned long long S = run_starts(m);

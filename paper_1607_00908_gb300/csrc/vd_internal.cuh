@@ -91,7 +91,7 @@ struct InstDesc {
     int events;              // classify the active labels (Section 3.2.4)
     int match_rule;          // VD_MATCH_OVERLAP / VD_MATCH_CENTROID
     int match_radius;        // centroid match: largest displacement, sites
-    int pad1;
+    int conn8;               // 8-connectivity (else 4)
 };
 
 // ---------------------------------------------------------------------------

@@ -176,7 +176,8 @@ def _check(s: int, where: str):
 
 def vd_config_init(Lx: int, Ly: int, threshold: float = 0.5, polarity: int = VD_ABOVE,
                    stream: int | None = None, max_components: int = 0, max_edges: int = 0,
-                   events: bool = False, match_rule: int = VD_MATCH_OVERLAP, match_radius: int = 0) -> vd_config:
+                   events: bool = False, match_rule: int = VD_MATCH_OVERLAP, match_radius: int = 0,
+                   connectivity: int = 4) -> vd_config:
     cfg = vd_config()
     _check(lib().vd_config_init(C.byref(cfg), int(Lx), int(Ly)), "vd_config_init")
     cfg.threshold = float(threshold)
@@ -187,6 +188,7 @@ def vd_config_init(Lx: int, Ly: int, threshold: float = 0.5, polarity: int = VD_
     cfg.events = int(bool(events))
     cfg.match_rule = int(match_rule)
     cfg.match_radius = int(match_radius)
+    cfg.connectivity = int(connectivity)
     return cfg
 
 
@@ -320,13 +322,14 @@ class Detector(_Base):
 
     def __init__(self, Lx: int, Ly: int, threshold: float = 0.5, polarity: int = VD_ABOVE,
                  stream: int | None = None, max_components: int = 0, max_edges: int = 0,
-                 events: bool = False, match_rule: int = VD_MATCH_OVERLAP, match_radius: int = 0):
+                 events: bool = False, match_rule: int = VD_MATCH_OVERLAP, match_radius: int = 0,
+                 connectivity: int = 4):
         if stream is None:
             import torch
             stream = torch.cuda.current_stream().cuda_stream
         self.Lx, self.Ly = Lx, Ly
         self.cfg = vd_config_init(Lx, Ly, threshold, polarity, stream, max_components, max_edges,
-                                  events, match_rule, match_radius)
+                                  events, match_rule, match_radius, connectivity)
         self.h = vd_create(self.cfg)
 
     def push(self, field) -> None:
@@ -400,12 +403,12 @@ class Batch(_Base):
 
     def __init__(self, sizes, threshold: float = 0.5, polarity: int = VD_ABOVE, stream: int | None = None,
                  max_components: int = 0, sequence: int = 0, events: bool = False,
-                 match_rule: int = VD_MATCH_OVERLAP, match_radius: int = 0):
+                 match_rule: int = VD_MATCH_OVERLAP, match_radius: int = 0, connectivity: int = 4):
         if stream is None:
             import torch
             stream = torch.cuda.current_stream().cuda_stream
         self.sizes = [(int(lx), int(ly)) for lx, ly in sizes]
-        opts = dict(events=events, match_rule=match_rule, match_radius=match_radius)
+        opts = dict(events=events, match_rule=match_rule, match_radius=match_radius, connectivity=connectivity)
         if sequence:
             lx, ly = self.sizes[0]
             self.sizes = [(lx, ly)] * int(sequence)

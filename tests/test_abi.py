@@ -41,8 +41,9 @@ def test_status_strings(lib):
     assert vd.status_string(12345) == "unknown status"
 
 
-@pytest.mark.parametrize("field,value", [("Lx", 0), ("Ly", -3), ("connectivity", 8), ("polarity", 0),
-                                         ("Lx", 1 << 21), ("max_components", -1)])
+@pytest.mark.parametrize("field,value", [("Lx", 0), ("Ly", -3), ("connectivity", 6), ("polarity", 0),
+                                         ("Lx", 1 << 21), ("max_components", -1), ("events", 2),
+                                         ("match_rule", 7), ("match_radius", -1)])
 def test_invalid_config_is_rejected_without_touching_the_gpu(lib, field, value):
     cfg = vd.vd_config_init(16, 16)
     setattr(cfg, field, value)

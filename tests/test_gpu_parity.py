@@ -68,13 +68,13 @@ def check_frame(det, r, what=("labels", "centroids", "owners", "edges", "changes
 
 
 def run_pair(frames, threshold=0.5, polarity=1, voronoi="kdtree", what=None, tag="", events=False,
-             match="overlap", match_radius=0):
+             match="overlap", match_radius=0, connectivity=4):
     Ly, Lx = frames[0].shape
     det = vd.Detector(Lx, Ly, threshold=threshold, polarity=polarity, events=events,
                       match_rule=vd.VD_MATCH_CENTROID if match == "centroid" else vd.VD_MATCH_OVERLAP,
-                      match_radius=match_radius)
+                      match_radius=match_radius, connectivity=connectivity)
     ref = O.Detector(Lx, Ly, theta=threshold, polarity=polarity, voronoi=voronoi, workers=-1, events=events,
-                     match=match, match_radius=match_radius)
+                     match=match, match_radius=match_radius, connectivity=connectivity)
     for f, F in enumerate(frames):
         det.push(torch.from_numpy(np.ascontiguousarray(F)).cuda())
         r = ref.push(F)
@@ -265,3 +265,29 @@ def test_centroid_match_in_batches():
             assert np.array_equal(ch["arising"], r["arising"]), (p, i)
             assert np.array_equal(ch["active"], r["active"]), (p, i)
     seq.close()
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_eight_connectivity(seed):
+    """8-connected bubbles (Section 3.1 with the diagonal lattice directions):
+    random fields on lattices ragged against the 64 x 32 tiles, including
+    one-tile-wide and one-row tori, and smoothed noise across tile corners."""
+    rng = np.random.default_rng(300 + seed)
+    for trial in range(5):
+        Lx = int(rng.integers(1, 200))
+        Ly = int(rng.integers(1, 120))
+        if trial % 2 == 0:
+            p = float(rng.uniform(0.2, 0.6))
+            F0 = (rng.random((Ly, Lx)) < p).astype(np.float32)
+            F1 = np.where(rng.random((Ly, Lx)) < 0.05, 1.0 - F0, F0).astype(np.float32)
+        else:
+            F0 = I.smoothed_noise(Ly, Lx, float(rng.uniform(1.0, 3.0)), seed=seed * 10 + trial)
+            F1 = I.shear_resample(F0, 0.03, 0.02, np.random.default_rng(trial))
+        run_pair([F0, F1], voronoi="brute", tag=f"c8 {Lx}x{Ly}", connectivity=8)
+
+
+def test_eight_connectivity_c1_frames():
+    """1024x1024 smoothed noise with 8-connected bubbles: full oracle."""
+    frames = list(I.workload_c1(seed=3, n_frames=3))
+    r = run_pair(frames, tag="c1 c8", connectivity=8)
+    assert r["K"] > 300
