@@ -310,12 +310,15 @@ def run_ours(args, world, rank, local):
                    "vd_batch_get_changes_all for every step"}
     seq.close()
 
-    # ---- options beyond steps a1-a8 on the same workload: the event classes
-    # of Section 3.2.4, and the centre match of Section 3.2.3 (with events) ----
+    # ---- options beyond the default steps a1-a8, on the same workload: the
+    # event classes of Section 3.2.4, the centre match of Section 3.2.3 (with
+    # events), the paper's vertex link rule of Section 3.2.2, 8-connectivity ----
     variants = {}
     for name, opts in (("events", dict(events=True)),
                        ("centroid_match_r8_events", dict(events=True, match_rule=vd.VD_MATCH_CENTROID,
-                                                         match_radius=8))):
+                                                         match_radius=8)),
+                       ("vertex_links", dict(edge_rule=vd.VD_EDGE_VERTEX)),
+                       ("connectivity_8", dict(connectivity=8))):
         vb = vd.Batch([(Lx, Ly)], sequence=n, stream=s.cuda_stream, **opts)
         for _ in range(max(1, args.warmup)):
             vb.push(dev)

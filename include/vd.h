@@ -68,7 +68,18 @@ typedef struct vd_config {
     int32_t events;            /* 1: classify the active labels into bulk / boundary events (Section 3.2.4) */
     int32_t match_rule;        /* VD_MATCH_OVERLAP (default) or VD_MATCH_CENTROID (Section 3.2.3) */
     int32_t match_radius;      /* VD_MATCH_CENTROID: largest centre displacement matched, in sites (>= 1) */
+    int32_t edge_rule;         /* VD_EDGE_ADJ4 (default) or VD_EDGE_VERTEX (Section 3.2.2) */
 } vd_config;
+
+/* Links of the digital Voronoi diagram (Section 3.2.2). ADJ4: owners that
+ * differ between +x / +y neighbouring sites, plus the exact incircle diagonal
+ * of every plaquette with four distinct owners. VERTEX: the paper's own rule,
+ * read at vertex sites only (three or more colour changes around the 8-site
+ * frame) with its first- and second-neighbour conditions; the inner-frame
+ * point of a diagonal is read as the plaquette centre, owned by the exact
+ * nearest-centre rule. The figure defining the inner frame is lost, so the
+ * VERTEX rule follows that reading. */
+enum { VD_EDGE_ADJ4 = 0, VD_EDGE_VERTEX = 1 };
 
 /* Isomorphism Phi between past and now labels (Section 3.2.3). OVERLAP: the
  * mutual best overlap of the two frames' bubbles (largest shared site count,

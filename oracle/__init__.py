@@ -7,6 +7,7 @@ fields of ``paper_1607_00908_gb300.inputs``.
 """
 from .detect import (  # noqa: F401
     Q,
+    FRAME,
     Detector,
     EV_ACTIVE,
     EV_BOUNDARY,
@@ -21,6 +22,7 @@ from .detect import (  # noqa: F401
     delaunay_edges,
     flips,
     foreground,
+    frame_gaps,
     incircle,
     label_components,
     make_keys,
@@ -28,9 +30,11 @@ from .detect import (  # noqa: F401
     match_overlap,
     orient2d,
     owners,
+    owners_at_q10,
     owners_bruteforce,
     plaquette_diagonal,
     rdiv,
     split_keys,
+    vertex_edges,
     wrap,
 )

@@ -17,6 +17,10 @@ components on the open rectangle), ``numpy.unique`` / sorting, and
 arithmetic is exact for the integer fixed-point coordinates used here, and
 ties are resolved in integers afterwards). ``owners_bruteforce`` is the
 literal definition and pins ``owners``.
+
+Parity unpinned: ``vertex_edges`` (the paper's frame / inner-frame link rule,
+an option) follows a reading of figures that are lost; it is checked only on
+hand-counted frames, not against the authors' code.
 """
 from __future__ import annotations
 
@@ -355,6 +359,93 @@ def delaunay_edges(owner: np.ndarray, cq: np.ndarray) -> np.ndarray:
 
 
 # ----------------------------------------------------------------------------
+# Section 3.2.2, the paper's own link rule: vertex sites of the digital
+# Voronoi diagram and the frame / inner-frame conditions (option)
+# ----------------------------------------------------------------------------
+
+#: the frame of a site: its eight neighbours in counter-clockwise order,
+#: starting at +x (spx, spxpy, spy, spymx, smx, smxmy, smy, smypx)
+FRAME = ((1, 0), (1, 1), (0, 1), (-1, 1), (-1, 0), (-1, -1), (0, -1), (1, -1))
+
+
+def owners_at_q10(cq: np.ndarray, Lx: int, Ly: int, px: np.ndarray, py: np.ndarray) -> np.ndarray:
+    """Owner of arbitrary Q10 points: nearest centre by exact minimum-image
+    squared distance, ties to the smallest label (the Section 3.2.1 rule away
+    from the lattice sites)."""
+    px = np.asarray(px, dtype=np.int64)
+    py = np.asarray(py, dtype=np.int64)
+    out = np.full(px.shape[0], -1, dtype=np.int64)
+    K = cq.shape[0]
+    if K == 0 or px.size == 0:
+        return out
+    cx = cq[:, 0].astype(np.int64)
+    cy = cq[:, 1].astype(np.int64)
+    chunk = max(1, 2_000_000 // K)
+    for s in range(0, px.shape[0], chunk):
+        d2 = sq_dist_q10(px[s:s + chunk, None], py[s:s + chunk, None], cx[None, :], cy[None, :], Lx, Ly)
+        out[s:s + chunk] = np.argmin(d2, axis=1)
+    return out
+
+
+def frame_gaps(owner: np.ndarray) -> np.ndarray:
+    """Number of colour changes between consecutive sites of each frame."""
+    fr = [np.roll(np.roll(owner, -dy, axis=0), -dx, axis=1) for dx, dy in FRAME]
+    return sum((fr[i] != fr[(i + 1) % 8]).astype(np.int64) for i in range(8))
+
+
+def vertex_edges(owner: np.ndarray, cq: np.ndarray) -> np.ndarray:
+    """Links read at the vertex sites of the digital Voronoi diagram (Section
+    3.2.2, the paper's frame rule), as sorted uint64 keys. PARITY UNPINNED: the
+    figures that define the inner frame and the pathological colourings are
+    lost, so only the readings below are checked, not agreement with the
+    authors' code.
+
+    Readings: a vertex site has three or more colour changes around its frame
+    (two: a cell edge, none: a cell interior). On a periodic lattice without
+    obstacles no colour is MAXLINK. With e1 one of +x, +y, -x, -y and e2 = e1
+    turned a quarter counter-clockwise, the conditions written for spx and
+    spxpy are applied to the four quarter turns:
+
+    * first neighbour k+e1 is linked to k when its colour differs from k's and
+      C(k+e2) != C(k+e1-e2) (the long-diagonal pathology);
+    * second neighbour k+e1+e2 is linked to k when its colour differs from
+      k's, C(k+e2) != C(k+e1-e2), C(k+e2) != C(k+e1) (the short diagonal),
+      and the inner-frame point -- read as the centre of the plaquette,
+      k + (e1+e2)/2 -- is owned by k's colour or by the neighbour's.
+    """
+    Ly, Lx = owner.shape
+    own = owner.astype(np.int64)
+
+    def at(dx, dy):
+        return np.roll(np.roll(own, -dy, axis=0), -dx, axis=1)
+
+    vert = frame_gaps(own) >= 3
+    keys = []
+    turns = ((1, 0), (0, 1), (-1, 0), (0, -1))
+    for e1x, e1y in turns:
+        e2x, e2y = -e1y, e1x
+        X = at(e1x, e1y)
+        ok = vert & (X != own) & (at(e2x, e2y) != at(e1x - e2x, e1y - e2y))
+        keys.append(make_keys(own[ok], X[ok]).astype(np.int64))
+    for e1x, e1y in turns:
+        e2x, e2y = -e1y, e1x
+        X = at(e1x + e2x, e1y + e2y)
+        A1, A2, A3 = at(e1x, e1y), at(e2x, e2y), at(e1x - e2x, e1y - e2y)
+        ok = vert & (X != own) & (A2 != A3) & (A2 != A1)
+        ys, xs = np.nonzero(ok)
+        if xs.size == 0:
+            continue
+        px = (Q * xs + (Q // 2) * (e1x + e2x)) % (Q * Lx)
+        py = (Q * ys + (Q // 2) * (e1y + e2y)) % (Q * Ly)
+        ca = owners_at_q10(cq, Lx, Ly, px, py)
+        kk, xx = own[ys, xs], X[ys, xs]
+        sel = (ca == kk) | (ca == xx)
+        keys.append(make_keys(kk[sel], xx[sel]).astype(np.int64))
+    allk = np.concatenate(keys) if keys else np.zeros(0, dtype=np.int64)
+    return np.unique(allk).astype(np.uint64)
+
+
+# ----------------------------------------------------------------------------
 # Section 3.2.3: isomorphism between past and now labels
 # ----------------------------------------------------------------------------
 
@@ -596,8 +687,10 @@ class Detector:
 
     def __init__(self, Lx: int, Ly: int, theta: float = 0.5, polarity: int = 1,
                  connectivity: int = 4, workers: int = 1, voronoi: str = "kdtree",
-                 events: bool = False, match: str = "overlap", match_radius: int = 0):
+                 events: bool = False, match: str = "overlap", match_radius: int = 0,
+                 edge_rule: str = "adj4"):
         self.Lx, self.Ly = Lx, Ly
+        self.edge_rule = edge_rule
         self.events = events
         self.match = match
         self.match_radius = match_radius
@@ -618,7 +711,7 @@ class Detector:
             own = owners_bruteforce(cq, self.Lx, self.Ly)
         else:
             own = owners(cq, self.Lx, self.Ly, workers=self.workers)
-        E = delaunay_edges(own, cq)
+        E = vertex_edges(own, cq) if self.edge_rule == "vertex" else delaunay_edges(own, cq)
         out = dict(frame=self.frame, labels=labels, K=K, centroids=cq, owners=own, edges=E)
         if self.prev is None:
             out.update(phi=np.zeros(0, np.int32), inv=np.full(K, -1, np.int32),

@@ -79,6 +79,7 @@ struct vd_batch {
     int grid_items = 0;
     bool any_events = false;           // some instance classifies its events
     bool any_centroid_match = false;   // some instance matches by centres
+    bool any_vertex_rule = false;      // some instance reads links at Voronoi vertices
     // field pointer tables (device) and their host mirrors
     const float** d_fields = nullptr;
     long long* d_pitches = nullptr;
@@ -152,6 +153,7 @@ bool valid_cfg(const vd_config& c) {
     if (c.events != 0 && c.events != 1) return false;
     if (c.match_rule != VD_MATCH_OVERLAP && c.match_rule != VD_MATCH_CENTROID) return false;
     if (c.match_radius < 0) return false;
+    if (c.edge_rule != VD_EDGE_ADJ4 && c.edge_rule != VD_EDGE_VERTEX) return false;
     if (c.match_rule == VD_MATCH_CENTROID && (c.match_radius < 1 || c.match_radius > (1 << 20))) return false;
     return true;
 }
@@ -205,6 +207,7 @@ Launch make_launch(vd_batch* b, const StepTables& T) {
     L.grid_items = b->grid_items;
     L.events = b->any_events;
     L.centroid_match = b->any_centroid_match;
+    L.vertex_rule = b->any_vertex_rule;
     L.grid_wide = 4 * b->grid_items;
     L.total_tilesA = T.total_tilesA;
     L.total_tilesV = T.total_tilesV;
@@ -273,6 +276,8 @@ vd_status create_batch(const vd_config* cfgs, int n, vd_batch** out, bool sequen
         D.pol = c.polarity;
         D.events = c.events;
         D.conn8 = c.connectivity == 8 ? 1 : 0;
+        D.edge_rule = c.edge_rule;
+        b->any_vertex_rule = b->any_vertex_rule || c.edge_rule == VD_EDGE_VERTEX;
         D.match_rule = c.match_rule;
         D.match_radius = c.match_rule == VD_MATCH_CENTROID ? c.match_radius : 0;
         b->any_events = b->any_events || c.events;

@@ -92,6 +92,8 @@ struct InstDesc {
     int match_rule;          // VD_MATCH_OVERLAP / VD_MATCH_CENTROID
     int match_radius;        // centroid match: largest displacement, sites
     int conn8;               // 8-connectivity (else 4)
+    int edge_rule;           // VD_EDGE_ADJ4 / VD_EDGE_VERTEX
+    int pad2;
 };
 
 // ---------------------------------------------------------------------------
@@ -430,6 +432,7 @@ struct Launch {
     bool sequence;       // some instance's past frame is produced in the same step
     bool events;         // some instance classifies its events
     bool centroid_match; // some instance matches by centres
+    bool vertex_rule;    // some instance reads its links at Voronoi vertices
     cudaStream_t s;
     Pools P;
     StepTable T;

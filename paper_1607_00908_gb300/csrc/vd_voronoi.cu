@@ -490,7 +490,7 @@ __global__ __launch_bounds__(32 * LINK_WARPS) void k_links(Pools P, StepTable T)
     const int inst = T.act[a];
     const InstDesc& D = P.desc[inst];
     const int K = min(P.st[inst].K, D.comp_cap);
-    if (K < 2) return;
+    if (K < 2 || D.edge_rule) return;   // the vertex rule has its own kernel
     const int t = b - T.tileV_pre[a];
     const int tx = t % D.vtx, ty = t / D.vtx;
     const int x0 = tx * VW, y0 = ty * VH;
@@ -620,8 +620,128 @@ void launch_voronoi(const Launch& L) {
     launch_step(L, k_voronoi, dim3((L.total_tilesA + VWARPS - 1) / VWARPS), dim3(32 * VWARPS), L.P, L.T);
 }
 
+// ---------------------------------------------------------------------------
+// The paper's link rule (Section 3.2.2), an option: links are read only at
+// vertex sites, i.e. sites with three or more colour changes around their
+// 8-site frame. With e1 one of +x, +y, -x, -y and e2 = e1 turned a quarter
+// counter-clockwise, the conditions written for spx and spxpy apply to the
+// four quarter turns:
+//   first neighbour k+e1: C(k+e1) != C(k) and C(k+e2) != C(k+e1-e2);
+//   second neighbour k+e1+e2: C(k+e1+e2) != C(k), C(k+e2) != C(k+e1-e2),
+//   C(k+e2) != C(k+e1), and the inner-frame point (read as the plaquette
+//   centre k + (e1+e2)/2) is owned by C(k) or by C(k+e1+e2).
+// One thread per site of a 32 x 32 tile (one warp per tile, lane = column);
+// vertex sites are rare, and the owner of a plaquette centre comes from an
+// exact ring search over the frame's bucket grid.
+// ---------------------------------------------------------------------------
+
+// owner of the Q10 point (qx, qy): nearest centre, ties to the smallest label.
+// Rings of buckets are scanned outwards; a bucket r rings away is at least
+// (r - 2) * B sites from the point (r - 1 buckets lie between, one of them
+// possibly the ragged last one), so the scan stops before ring r once the
+// best distance is below that.
+__device__ int owner_of_point(const int2* bcq, const int* bid, const int* boff, int B, int nbx, int nby,
+                              long long qx, long long qy, long long MX, long long MY) {
+    if (nbx <= 0 || nby <= 0) return -1;
+    const int bx = (int)(qx / Q) / B, by = (int)(qy / Q) / B;
+    int best = -1;
+    long long bd = 0;
+    const int rmax = max(nbx, nby);
+    for (int r = 0; r <= rmax; ++r) {
+        if (best >= 0 && r >= 3) {
+            const long long lim = (long long)(r - 2) * B * Q;
+            if (bd < lim * lim) break;
+        }
+        for (int dy = -r; dy <= r; ++dy) {
+            const bool edge_row = dy == -r || dy == r;
+            for (int dx = -r; dx <= r; dx += (edge_row ? 1 : 2 * r)) {
+                const int cbx = ((bx + dx) % nbx + nbx) % nbx, cby = ((by + dy) % nby + nby) % nby;
+                const int bk = cby * nbx + cbx;
+                for (int k = boff[bk]; k < boff[bk + 1]; ++k) {
+                    const int2 c = bcq[k];
+                    const long long ddx = wrap_ll((long long)c.x - qx, MX), ddy = wrap_ll((long long)c.y - qy, MY);
+                    const long long d = ddx * ddx + ddy * ddy;
+                    const int id = bid[k];
+                    if (best < 0 || d < bd || (d == bd && id < best)) {
+                        bd = d;
+                        best = id;
+                    }
+                }
+                if (r == 0) break;
+            }
+        }
+    }
+    return best;
+}
+
+__device__ __forceinline__ void vertex_link(const Pools& P, const InstDesc& D, int inst, int a, int b) {
+    const unsigned long long key = edge_key(a, b);
+    const int pos = atomicAdd(&P.st[inst].n_eapp, 1);
+    if (pos < D.edge_cap) P.ekeys[D.edge_off + pos] = key;
+    else edge_global_insert(P, D, inst, key);
+}
+
+__global__ __launch_bounds__(32 * LINK_WARPS) void k_links_vertex(Pools P, StepTable T) {
+    pdl_enter();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int b = blockIdx.x * LINK_WARPS + warp;
+    if (b >= T.tileV_pre[T.n_act]) return;
+    const int a = seg_of_int(T.tileV_pre, T.n_act, b);
+    const int inst = T.act[a];
+    const InstDesc& D = P.desc[inst];
+    const InstState& S = P.st[inst];
+    const int K = min(S.K, D.comp_cap);
+    if (K < 2 || !D.edge_rule) return;
+    const int t = b - T.tileV_pre[a];
+    const int tx = t % D.vtx, ty = t / D.vtx;
+    const int Lx = D.Lx, Ly = D.Ly;
+    const int x = tx * VW + lane;
+    if (x >= Lx) return;
+    const int now = S.slot ^ 1;
+    const int* own = P.owners + D.site_off;
+    const long long MX = (long long)Q * Lx, MY = (long long)Q * Ly;
+    const int xm = x == 0 ? Lx - 1 : x - 1, xp = x + 1 == Lx ? 0 : x + 1;
+    const int y0 = ty * VH, y1 = min(y0 + VH, Ly);
+    for (int y = y0; y < y1; ++y) {
+        const int ym = y == 0 ? Ly - 1 : y - 1, yp = y + 1 == Ly ? 0 : y + 1;
+        const int* rm = own + (long long)ym * Lx;
+        const int* r0 = own + (long long)y * Lx;
+        const int* rp = own + (long long)yp * Lx;
+        // the frame in counter-clockwise order from +x; f[8] = the site itself
+        int f[9];
+        f[0] = r0[xp]; f[1] = rp[xp]; f[2] = rp[x]; f[3] = rp[xm];
+        f[4] = r0[xm]; f[5] = rm[xm]; f[6] = rm[x]; f[7] = rm[xp];
+        f[8] = r0[x];
+        int gaps = 0;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) gaps += f[i] != f[(i + 1) & 7] ? 1 : 0;
+        if (gaps < 3) continue;
+        const int k = f[8];
+        // quarter turn q: e1 = frame entry 2q, e1 + e2 = entry 2q + 1, e2 = entry 2q + 2,
+        // e1 - e2 = entry 2q - 1 (all mod 8)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int c1 = f[2 * q], cd = f[2 * q + 1], c2 = f[(2 * q + 2) & 7], c3 = f[(2 * q + 7) & 7];
+            if (c1 != k && c2 != c3) vertex_link(P, D, inst, k, c1);
+            if (cd != k && c2 != c3 && c2 != c1) {
+                // plaquette centre k + (e1 + e2) / 2
+                const int ex = (q == 0 || q == 3) ? 1 : -1, ey = (q == 0 || q == 1) ? 1 : -1;
+                long long qx = (long long)Q * x + (Q / 2) * ex, qy = (long long)Q * y + (Q / 2) * ey;
+                qx = (qx % MX + MX) % MX;
+                qy = (qy % MY + MY) % MY;
+                const int ca = owner_of_point(P.bcq[now] + D.comp_off, P.bid[now] + D.comp_off,
+                                              P.boff[now] + D.bucket_off, S.B, S.nbx, S.nby, qx, qy, MX, MY);
+                if (ca == k || ca == cd) vertex_link(P, D, inst, k, cd);
+            }
+        }
+    }
+}
+
 void launch_links(const Launch& L) {
     launch_step(L, k_links, dim3((L.total_tilesV + LINK_WARPS - 1) / LINK_WARPS), dim3(32 * LINK_WARPS), L.P, L.T);
+    if (L.vertex_rule)
+        launch_step(L, k_links_vertex, dim3((L.total_tilesV + LINK_WARPS - 1) / LINK_WARPS), dim3(32 * LINK_WARPS),
+                    L.P, L.T);
 }
 
 }  // namespace vd

@@ -31,6 +31,8 @@ VD_BELOW = -1
 VD_EV_ACTIVE, VD_EV_BULK, VD_EV_BOUNDARY, VD_EV_BPOINT_NOW, VD_EV_BPOINT_PAST = 1, 2, 4, 8, 16
 # isomorphism rules (Section 3.2.3)
 VD_MATCH_OVERLAP, VD_MATCH_CENTROID = 0, 1
+# link rules (Section 3.2.2)
+VD_EDGE_ADJ4, VD_EDGE_VERTEX = 0, 1
 
 #: every symbol include/vd.h declares
 EXPORTS = (
@@ -61,6 +63,7 @@ class vd_config(C.Structure):
         ("Lx", C.c_int32), ("Ly", C.c_int32), ("threshold", C.c_float), ("polarity", C.c_int32),
         ("connectivity", C.c_int32), ("max_components", C.c_int32), ("max_edges", C.c_int32),
         ("stream", C.c_void_p), ("events", C.c_int32), ("match_rule", C.c_int32), ("match_radius", C.c_int32),
+        ("edge_rule", C.c_int32),
     ]
 
 
@@ -177,7 +180,7 @@ def _check(s: int, where: str):
 def vd_config_init(Lx: int, Ly: int, threshold: float = 0.5, polarity: int = VD_ABOVE,
                    stream: int | None = None, max_components: int = 0, max_edges: int = 0,
                    events: bool = False, match_rule: int = VD_MATCH_OVERLAP, match_radius: int = 0,
-                   connectivity: int = 4) -> vd_config:
+                   connectivity: int = 4, edge_rule: int = VD_EDGE_ADJ4) -> vd_config:
     cfg = vd_config()
     _check(lib().vd_config_init(C.byref(cfg), int(Lx), int(Ly)), "vd_config_init")
     cfg.threshold = float(threshold)
@@ -189,6 +192,7 @@ def vd_config_init(Lx: int, Ly: int, threshold: float = 0.5, polarity: int = VD_
     cfg.match_rule = int(match_rule)
     cfg.match_radius = int(match_radius)
     cfg.connectivity = int(connectivity)
+    cfg.edge_rule = int(edge_rule)
     return cfg
 
 
@@ -323,13 +327,13 @@ class Detector(_Base):
     def __init__(self, Lx: int, Ly: int, threshold: float = 0.5, polarity: int = VD_ABOVE,
                  stream: int | None = None, max_components: int = 0, max_edges: int = 0,
                  events: bool = False, match_rule: int = VD_MATCH_OVERLAP, match_radius: int = 0,
-                 connectivity: int = 4):
+                 connectivity: int = 4, edge_rule: int = VD_EDGE_ADJ4):
         if stream is None:
             import torch
             stream = torch.cuda.current_stream().cuda_stream
         self.Lx, self.Ly = Lx, Ly
         self.cfg = vd_config_init(Lx, Ly, threshold, polarity, stream, max_components, max_edges,
-                                  events, match_rule, match_radius, connectivity)
+                                  events, match_rule, match_radius, connectivity, edge_rule)
         self.h = vd_create(self.cfg)
 
     def push(self, field) -> None:
@@ -403,12 +407,14 @@ class Batch(_Base):
 
     def __init__(self, sizes, threshold: float = 0.5, polarity: int = VD_ABOVE, stream: int | None = None,
                  max_components: int = 0, sequence: int = 0, events: bool = False,
-                 match_rule: int = VD_MATCH_OVERLAP, match_radius: int = 0, connectivity: int = 4):
+                 match_rule: int = VD_MATCH_OVERLAP, match_radius: int = 0, connectivity: int = 4,
+                 edge_rule: int = VD_EDGE_ADJ4):
         if stream is None:
             import torch
             stream = torch.cuda.current_stream().cuda_stream
         self.sizes = [(int(lx), int(ly)) for lx, ly in sizes]
-        opts = dict(events=events, match_rule=match_rule, match_radius=match_radius, connectivity=connectivity)
+        opts = dict(events=events, match_rule=match_rule, match_radius=match_radius, connectivity=connectivity,
+                    edge_rule=edge_rule)
         if sequence:
             lx, ly = self.sizes[0]
             self.sizes = [(lx, ly)] * int(sequence)

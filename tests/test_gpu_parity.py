@@ -68,13 +68,14 @@ def check_frame(det, r, what=("labels", "centroids", "owners", "edges", "changes
 
 
 def run_pair(frames, threshold=0.5, polarity=1, voronoi="kdtree", what=None, tag="", events=False,
-             match="overlap", match_radius=0, connectivity=4):
+             match="overlap", match_radius=0, connectivity=4, edge_rule="adj4"):
     Ly, Lx = frames[0].shape
     det = vd.Detector(Lx, Ly, threshold=threshold, polarity=polarity, events=events,
                       match_rule=vd.VD_MATCH_CENTROID if match == "centroid" else vd.VD_MATCH_OVERLAP,
-                      match_radius=match_radius, connectivity=connectivity)
+                      match_radius=match_radius, connectivity=connectivity,
+                      edge_rule=vd.VD_EDGE_VERTEX if edge_rule == "vertex" else vd.VD_EDGE_ADJ4)
     ref = O.Detector(Lx, Ly, theta=threshold, polarity=polarity, voronoi=voronoi, workers=-1, events=events,
-                     match=match, match_radius=match_radius, connectivity=connectivity)
+                     match=match, match_radius=match_radius, connectivity=connectivity, edge_rule=edge_rule)
     for f, F in enumerate(frames):
         det.push(torch.from_numpy(np.ascontiguousarray(F)).cuda())
         r = ref.push(F)
@@ -290,4 +291,26 @@ def test_eight_connectivity_c1_frames():
     """1024x1024 smoothed noise with 8-connected bubbles: full oracle."""
     frames = list(I.workload_c1(seed=3, n_frames=3))
     r = run_pair(frames, tag="c1 c8", connectivity=8)
+    assert r["K"] > 300
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_vertex_link_rule(seed):
+    """The paper's vertex / frame link rule (VD_EDGE_VERTEX): links, Phi, flips
+    and event flags equal the oracle's reading of it, on lattices ragged against
+    the 32 x 32 link tiles, with bubbles from a handful to a few hundred."""
+    rng = np.random.default_rng(500 + seed)
+    for trial in range(3):
+        Lx = int(rng.integers(16, 260))
+        Ly = int(rng.integers(16, 200))
+        sig = float(rng.uniform(1.5, 4.0))
+        F0 = I.smoothed_noise(Ly, Lx, sig, seed=seed * 10 + trial)
+        F1 = I.shear_resample(F0, 0.03, 0.02, np.random.default_rng(trial))
+        run_pair([F0, F1], voronoi="brute", tag=f"vertex {Lx}x{Ly}", edge_rule="vertex", events=True)
+
+
+def test_vertex_link_rule_c1_frames():
+    """1024x1024 smoothed noise with the vertex rule: full oracle."""
+    frames = list(I.workload_c1(seed=4, n_frames=3))
+    r = run_pair(frames, tag="c1 vertex", edge_rule="vertex")
     assert r["K"] > 300

@@ -775,3 +775,34 @@ def test_centroid_match_equals_bruteforce_loops():
     want = [bn[p] if bn[p] >= 0 and bp[bn[p]] == p else -1 for p in range(40)]
     assert phi.tolist() == want
     assert sorted(i for i in inv.tolist() if i >= 0) == sorted(p for p in range(40) if want[p] >= 0)
+
+
+# ----------------------------------------------------------------------------
+# Section 3.2.2, the frame rule (vertex_edges, an option; parity with the
+# authors' code is unpinned because its figures are lost): hand-counted cases
+# ----------------------------------------------------------------------------
+
+def test_frame_gaps_and_vertex_links_at_a_three_cell_junction():
+    """4 x 4 torus: cell 0 = {x<2, y<2}, cell 1 = {x>=2, y<2}, cell 2 = {y>=2}.
+    Frame of (1,1), counter-clockwise from +x: 1,2,2,2,0,0,0,1 -> 3 colour
+    changes (a vertex site); frame of (0,0): 0,0,0,1,1,2,2,2 -> 3. At (1,1)
+    the +x neighbour (colour 1) passes C(spy)=2 != C(smypx)=1 and the +y
+    neighbour (colour 2) passes C(smx)=0 != C(spxpy)=2; at (2,1) the +y
+    neighbour (colour 2) passes C(smx)=0 != C(spxpy)=2: the three cells are
+    linked pairwise."""
+    own = np.array([[0, 0, 1, 1], [0, 0, 1, 1], [2, 2, 2, 2], [2, 2, 2, 2]], dtype=np.int32)
+    gaps = O.frame_gaps(own)
+    assert int(gaps[1, 1]) == 3 and int(gaps[0, 0]) == 3
+    cq = np.array([[512, 512], [Q * 2 + 512, 512], [Q + 512, Q * 2 + 512]], dtype=np.int64)
+    E = O.vertex_edges(own, cq)
+    assert E.tolist() == O.make_keys([0, 0, 1], [1, 2, 2]).tolist()
+
+
+def test_vertex_rule_sees_no_vertex_between_two_stripes():
+    """Two stripes on a torus: every frame changes colour twice at most, so no
+    site is a vertex and the frame rule reads no link."""
+    own = np.zeros((6, 5), dtype=np.int32)
+    own[3:] = 1
+    assert int(O.frame_gaps(own).max()) == 2
+    cq = np.array([[Q * 2, Q], [Q * 2, Q * 4]], dtype=np.int64)
+    assert O.vertex_edges(own, cq).size == 0
