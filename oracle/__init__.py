@@ -6,6 +6,8 @@ path in ``paper_1607_00908_gb300/``; the two meet only on the seeded input
 fields of ``paper_1607_00908_gb300.inputs``.
 """
 from .detect import (  # noqa: F401
+    OBSTACLE,
+    OUTSIDE,
     Q,
     FRAME,
     Detector,
@@ -37,4 +39,5 @@ from .detect import (  # noqa: F401
     split_keys,
     vertex_edges,
     wrap,
+    wrap_ax,
 )

@@ -46,6 +46,17 @@ def wrap(d, L):
     return ((d + h) % L) - h
 
 
+def wrap_ax(d, L, periodic: bool):
+    """Displacement along one axis: minimum image when the axis is periodic,
+    plain difference when it is bounded by walls."""
+    return wrap(d, L) if periodic else d
+
+
+#: owner of an obstacle site (the paper's MAXLINK colour) and, in frame
+#: tests, of a neighbour that lies beyond a wall
+OBSTACLE, OUTSIDE = -2, -3
+
+
 def rdiv(p, q):
     """Round-half-up integer division p/q for q > 0: floor((2p + q) / (2q))."""
     return (2 * p + q) // (2 * q)
@@ -76,7 +87,7 @@ def _neighbour_offsets(connectivity: int):
     raise ValueError("connectivity must be 4 or 8")
 
 
-def label_components(fg: np.ndarray, connectivity: int = 4):
+def label_components(fg: np.ndarray, connectivity: int = 4, periodic=(True, True)):
     """Periodic connected-component labels with canonical ids (Section 3.1).
 
     Bubbles are maximal sets of foreground sites connected through lattice
@@ -84,7 +95,8 @@ def label_components(fg: np.ndarray, connectivity: int = 4):
     connectivity by default (the Ising cluster-labelling analogy of Section 3.1),
     8 as an option. The paper fixes no label values; here a component's id is
     the rank of its smallest linear index y*Lx + x among all components, so ids
-    run 0..K-1 in raster order of first sites. Background is -1.
+    run 0..K-1 in raster order of first sites. Background is -1. An axis that
+    is not periodic (walls, the paper's channel) joins nothing across its seam.
 
     Returns (labels int32 [Ly, Lx], K).
     """
@@ -106,9 +118,15 @@ def label_components(fg: np.ndarray, connectivity: int = 4):
         return a
 
     pairs = set()
+    xs = np.arange(Lx)[None, :]
+    ys = np.arange(Ly)[:, None]
     for dx, dy in _neighbour_offsets(connectivity):
         nb = np.roll(np.roll(raw, -dy, axis=0), -dx, axis=1)   # raw at (x+dx, y+dy)
         m = (raw > 0) & (nb > 0) & (raw != nb)
+        if not periodic[0]:
+            m &= (xs + dx >= 0) & (xs + dx < Lx)
+        if not periodic[1]:
+            m &= (ys + dy >= 0) & (ys + dy < Ly)
         if m.any():
             a = raw[m].astype(np.int64)
             b = nb[m].astype(np.int64)
@@ -139,7 +157,7 @@ def label_components(fg: np.ndarray, connectivity: int = 4):
 # Section 3.1: size and centre of mass
 # ----------------------------------------------------------------------------
 
-def component_sums(labels: np.ndarray, K: int):
+def component_sums(labels: np.ndarray, K: int, periodic=(True, True)):
     """Per component: root site r, size n, and Sx, Sy = sums of wrap(x - x_r), wrap(y - y_r).
 
     Section 3.1 counts the sites of each bubble and sums their x and y
@@ -158,8 +176,8 @@ def component_sums(labels: np.ndarray, K: int):
     yr = first // Lx
     x = idx % Lx
     y = idx // Lx
-    dx = wrap(x - xr[lab], Lx)
-    dy = wrap(y - yr[lab], Ly)
+    dx = wrap_ax(x - xr[lab], Lx, periodic[0])
+    dy = wrap_ax(y - yr[lab], Ly, periodic[1])
     n = np.bincount(lab, minlength=K).astype(np.int64)
     Sx = np.zeros(K, dtype=np.int64)
     Sy = np.zeros(K, dtype=np.int64)
@@ -168,7 +186,7 @@ def component_sums(labels: np.ndarray, K: int):
     return xr, yr, n, Sx, Sy
 
 
-def centroids_q10(labels: np.ndarray, K: int) -> np.ndarray:
+def centroids_q10(labels: np.ndarray, K: int, periodic=(True, True)) -> np.ndarray:
     """Centre of mass of each bubble in 1/1024-site fixed point (Section 3.1).
 
     c = x_r + Sx / n per axis, with the division rounded half up in units of
@@ -179,7 +197,7 @@ def centroids_q10(labels: np.ndarray, K: int) -> np.ndarray:
     Ly, Lx = labels.shape
     if K == 0:
         return np.zeros((0, 2), dtype=np.int64)
-    xr, yr, n, Sx, Sy = component_sums(labels, K)
+    xr, yr, n, Sx, Sy = component_sums(labels, K, periodic)
     cx = np.mod(Q * xr + rdiv(Q * Sx, n), Q * Lx)
     cy = np.mod(Q * yr + rdiv(Q * Sy, n), Q * Ly)
     return np.stack([cx, cy], axis=1).astype(np.int64)
@@ -194,14 +212,15 @@ def _site_grid(Lx: int, Ly: int):
     return x, y
 
 
-def sq_dist_q10(sx, sy, cx, cy, Lx: int, Ly: int):
-    """Exact squared minimum-image distance between Q10 points (int64)."""
-    dx = wrap(sx - cx, Q * Lx)
-    dy = wrap(sy - cy, Q * Ly)
+def sq_dist_q10(sx, sy, cx, cy, Lx: int, Ly: int, periodic=(True, True)):
+    """Exact squared distance between Q10 points (int64), minimum image on
+    periodic axes."""
+    dx = wrap_ax(sx - cx, Q * Lx, periodic[0])
+    dy = wrap_ax(sy - cy, Q * Ly, periodic[1])
     return dx * dx + dy * dy
 
 
-def owners_bruteforce(cq: np.ndarray, Lx: int, Ly: int, sites=None) -> np.ndarray:
+def owners_bruteforce(cq: np.ndarray, Lx: int, Ly: int, sites=None, periodic=(True, True)) -> np.ndarray:
     """Digital Voronoi colouring, literally as in Section 3.2.1.
 
     Every site (foreground or not) takes the label of the nearest centre of
@@ -228,7 +247,7 @@ def owners_bruteforce(cq: np.ndarray, Lx: int, Ly: int, sites=None) -> np.ndarra
     chunk = max(1, 4_000_000 // K)
     for s in range(0, x.shape[0], chunk):
         d2 = sq_dist_q10(sx[s:s + chunk, None], sy[s:s + chunk, None],
-                         cx[None, :], cy[None, :], Lx, Ly)
+                         cx[None, :], cy[None, :], Lx, Ly, periodic)
         out[s:s + chunk] = np.argmin(d2, axis=1)
     return out if sites is not None else out.reshape(Ly, Lx)
 
@@ -294,7 +313,7 @@ def _sign(v: int) -> int:
 
 
 def plaquette_diagonal(A: int, B: int, C: int, D: int, cq: np.ndarray,
-                       Lx: int, Ly: int):
+                       Lx: int, Ly: int, periodic=(True, True)):
     """Diagonal link of a 2x2 plaquette whose four owners are pairwise distinct.
 
     The plaquette's sites (x,y), (x+1,y), (x+1,y+1), (x,y+1) carry owners A, B,
@@ -311,8 +330,8 @@ def plaquette_diagonal(A: int, B: int, C: int, D: int, cq: np.ndarray,
     ax, ay = int(cq[A, 0]), int(cq[A, 1])
 
     def unwrapped(i):
-        return (ax + int(wrap(int(cq[i, 0]) - ax, Q * Lx)),
-                ay + int(wrap(int(cq[i, 1]) - ay, Q * Ly)))
+        return (ax + int(wrap_ax(int(cq[i, 0]) - ax, Q * Lx, periodic[0])),
+                ay + int(wrap_ax(int(cq[i, 1]) - ay, Q * Ly, periodic[1])))
 
     a = (ax, ay)
     b, c, d = unwrapped(B), unwrapped(C), unwrapped(D)
@@ -322,7 +341,7 @@ def plaquette_diagonal(A: int, B: int, C: int, D: int, cq: np.ndarray,
     return (min(A, C), max(A, C))
 
 
-def delaunay_edges(owner: np.ndarray, cq: np.ndarray) -> np.ndarray:
+def delaunay_edges(owner: np.ndarray, cq: np.ndarray, periodic=(True, True)) -> np.ndarray:
     """Delaunay edge set of the digital Voronoi diagram, as sorted uint64 keys.
 
     Section 3.2.2 reads the adjacency of Voronoi cells off the colours of
@@ -334,24 +353,33 @@ def delaunay_edges(owner: np.ndarray, cq: np.ndarray) -> np.ndarray:
          diagonal chosen by ``plaquette_diagonal`` is linked.
 
     A link {a, b} is stored once as the key (min << 32) | max; the result is
-    sorted and unique (the "compressed adjacency" of Section 3.2.2).
+    sorted and unique (the "compressed adjacency" of Section 3.2.2). Pairs and
+    plaquettes that would cross a wall (a bounded axis), and sites of
+    obstacles (negative owners), give no link.
     """
     Ly, Lx = owner.shape
     A = owner.astype(np.int64)
     B = np.roll(A, -1, axis=1)                    # owner at (x+1, y)
     D = np.roll(A, -1, axis=0)                    # owner at (x, y+1)
     C = np.roll(B, -1, axis=0)                    # owner at (x+1, y+1)
+    inx = np.ones((Ly, Lx), dtype=bool)
+    iny = np.ones((Ly, Lx), dtype=bool)
+    if not periodic[0]:
+        inx[:, Lx - 1] = False                    # (x+1) lies beyond the wall
+    if not periodic[1]:
+        iny[Ly - 1, :] = False
     keys = []
-    for P, R in ((A, B), (A, D)):
-        m = P != R
+    for P, R, inside in ((A, B, inx), (A, D, iny)):
+        m = (P != R) & inside & (P >= 0) & (R >= 0)
         lo = np.minimum(P[m], R[m])
         hi = np.maximum(P[m], R[m])
         keys.append((lo << 32) | hi)
     four = (A != B) & (A != C) & (A != D) & (B != C) & (B != D) & (C != D)
+    four &= inx & iny & (A >= 0) & (B >= 0) & (C >= 0) & (D >= 0)
     diag = []
     for ia, ib, ic, id_ in zip(A[four].tolist(), B[four].tolist(),
                                C[four].tolist(), D[four].tolist()):
-        lo, hi = plaquette_diagonal(ia, ib, ic, id_, cq, Lx, Ly)
+        lo, hi = plaquette_diagonal(ia, ib, ic, id_, cq, Lx, Ly, periodic)
         diag.append((lo << 32) | hi)
     keys.append(np.array(diag, dtype=np.int64))
     allk = np.concatenate(keys) if keys else np.zeros(0, dtype=np.int64)
@@ -368,7 +396,8 @@ def delaunay_edges(owner: np.ndarray, cq: np.ndarray) -> np.ndarray:
 FRAME = ((1, 0), (1, 1), (0, 1), (-1, 1), (-1, 0), (-1, -1), (0, -1), (1, -1))
 
 
-def owners_at_q10(cq: np.ndarray, Lx: int, Ly: int, px: np.ndarray, py: np.ndarray) -> np.ndarray:
+def owners_at_q10(cq: np.ndarray, Lx: int, Ly: int, px: np.ndarray, py: np.ndarray,
+                  periodic=(True, True)) -> np.ndarray:
     """Owner of arbitrary Q10 points: nearest centre by exact minimum-image
     squared distance, ties to the smallest label (the Section 3.2.1 rule away
     from the lattice sites)."""
@@ -382,18 +411,44 @@ def owners_at_q10(cq: np.ndarray, Lx: int, Ly: int, px: np.ndarray, py: np.ndarr
     cy = cq[:, 1].astype(np.int64)
     chunk = max(1, 2_000_000 // K)
     for s in range(0, px.shape[0], chunk):
-        d2 = sq_dist_q10(px[s:s + chunk, None], py[s:s + chunk, None], cx[None, :], cy[None, :], Lx, Ly)
+        d2 = sq_dist_q10(px[s:s + chunk, None], py[s:s + chunk, None], cx[None, :], cy[None, :], Lx, Ly,
+                         periodic)
         out[s:s + chunk] = np.argmin(d2, axis=1)
     return out
 
 
-def frame_gaps(owner: np.ndarray) -> np.ndarray:
-    """Number of colour changes between consecutive sites of each frame."""
-    fr = [np.roll(np.roll(owner, -dy, axis=0), -dx, axis=1) for dx, dy in FRAME]
-    return sum((fr[i] != fr[(i + 1) % 8]).astype(np.int64) for i in range(8))
+def _shifted(owner: np.ndarray, dx: int, dy: int, periodic=(True, True)) -> np.ndarray:
+    """owner at (x+dx, y+dy); OUTSIDE where that crosses a wall."""
+    Ly, Lx = owner.shape
+    out = np.roll(np.roll(owner.astype(np.int64), -dy, axis=0), -dx, axis=1)
+    if not periodic[0]:
+        xs = np.arange(Lx)[None, :] + dx
+        out = np.where((xs < 0) | (xs >= Lx), OUTSIDE, out)
+    if not periodic[1]:
+        ys = np.arange(Ly)[:, None] + dy
+        out = np.where((ys < 0) | (ys >= Ly), OUTSIDE, out)
+    return out
 
 
-def vertex_edges(owner: np.ndarray, cq: np.ndarray) -> np.ndarray:
+def frame_gaps(owner: np.ndarray, periodic=(True, True)) -> np.ndarray:
+    """Number of colour changes between consecutive sites of each frame. At a
+    wall the frame keeps only the neighbours inside the domain (taken in the
+    same cyclic order); an obstacle neighbour counts with its MAXLINK colour."""
+    fr = [_shifted(owner, dx, dy, periodic) for dx, dy in FRAME]
+    Ly, Lx = owner.shape
+    gaps = np.zeros((Ly, Lx), dtype=np.int64)
+    # previous in-domain member of each frame, starting from the last one
+    prev = np.full((Ly, Lx), OUTSIDE, dtype=np.int64)
+    for i in range(8):
+        prev = np.where(fr[i] != OUTSIDE, fr[i], prev)
+    for i in range(8):
+        inside = fr[i] != OUTSIDE
+        gaps += (inside & (fr[i] != prev)).astype(np.int64)
+        prev = np.where(inside, fr[i], prev)
+    return gaps
+
+
+def vertex_edges(owner: np.ndarray, cq: np.ndarray, periodic=(True, True)) -> np.ndarray:
     """Links read at the vertex sites of the digital Voronoi diagram (Section
     3.2.2, the paper's frame rule), as sorted uint64 keys. PARITY UNPINNED: the
     figures that define the inner frame and the pathological colourings are
@@ -412,32 +467,36 @@ def vertex_edges(owner: np.ndarray, cq: np.ndarray) -> np.ndarray:
       k's, C(k+e2) != C(k+e1-e2), C(k+e2) != C(k+e1) (the short diagonal),
       and the inner-frame point -- read as the centre of the plaquette,
       k + (e1+e2)/2 -- is owned by k's colour or by the neighbour's.
+
+    Walls truncate the frame (neighbours beyond them leave it) and obstacle
+    sites carry the MAXLINK colour: neither is ever linked, nor is a site that
+    is itself an obstacle.
     """
     Ly, Lx = owner.shape
     own = owner.astype(np.int64)
 
     def at(dx, dy):
-        return np.roll(np.roll(own, -dy, axis=0), -dx, axis=1)
+        return _shifted(own, dx, dy, periodic)
 
-    vert = frame_gaps(own) >= 3
+    vert = (frame_gaps(own, periodic) >= 3) & (own >= 0)
     keys = []
     turns = ((1, 0), (0, 1), (-1, 0), (0, -1))
     for e1x, e1y in turns:
         e2x, e2y = -e1y, e1x
         X = at(e1x, e1y)
-        ok = vert & (X != own) & (at(e2x, e2y) != at(e1x - e2x, e1y - e2y))
+        ok = vert & (X >= 0) & (X != own) & (at(e2x, e2y) != at(e1x - e2x, e1y - e2y))
         keys.append(make_keys(own[ok], X[ok]).astype(np.int64))
     for e1x, e1y in turns:
         e2x, e2y = -e1y, e1x
         X = at(e1x + e2x, e1y + e2y)
         A1, A2, A3 = at(e1x, e1y), at(e2x, e2y), at(e1x - e2x, e1y - e2y)
-        ok = vert & (X != own) & (A2 != A3) & (A2 != A1)
+        ok = vert & (X >= 0) & (X != own) & (A2 != A3) & (A2 != A1)
         ys, xs = np.nonzero(ok)
         if xs.size == 0:
             continue
         px = (Q * xs + (Q // 2) * (e1x + e2x)) % (Q * Lx)
         py = (Q * ys + (Q // 2) * (e1y + e2y)) % (Q * Ly)
-        ca = owners_at_q10(cq, Lx, Ly, px, py)
+        ca = owners_at_q10(cq, Lx, Ly, px, py, periodic)
         kk, xx = own[ys, xs], X[ys, xs]
         sel = (ca == kk) | (ca == xx)
         keys.append(make_keys(kk[sel], xx[sel]).astype(np.int64))
@@ -488,7 +547,7 @@ def match_overlap(lab_prev: np.ndarray, lab_now: np.ndarray, K_prev: int, K_now:
     return phi, inv
 
 
-def _nearest(q: np.ndarray, c: np.ndarray, Lx: int, Ly: int, R2: int) -> np.ndarray:
+def _nearest(q: np.ndarray, c: np.ndarray, Lx: int, Ly: int, R2: int, periodic=(True, True)) -> np.ndarray:
     """For every row of q (Q10 centres) the index of the nearest row of c by
     minimum-image squared distance (int64), ties to the smallest index, or -1
     when the nearest is farther than sqrt(R2). Brute force in chunks."""
@@ -500,8 +559,8 @@ def _nearest(q: np.ndarray, c: np.ndarray, Lx: int, Ly: int, R2: int) -> np.ndar
     for i0 in range(0, q.shape[0], 512):
         qx = q[i0:i0 + 512, 0].astype(np.int64)[:, None]
         qy = q[i0:i0 + 512, 1].astype(np.int64)[:, None]
-        dx = wrap(cx[None, :] - qx, Q * Lx)
-        dy = wrap(cy[None, :] - qy, Q * Ly)
+        dx = wrap_ax(cx[None, :] - qx, Q * Lx, periodic[0])
+        dy = wrap_ax(cy[None, :] - qy, Q * Ly, periodic[1])
         d = dx * dx + dy * dy
         j = np.argmin(d, axis=1)          # first index of the minimum: ties to the smallest
         dmin = d[np.arange(d.shape[0]), j]
@@ -509,7 +568,8 @@ def _nearest(q: np.ndarray, c: np.ndarray, Lx: int, Ly: int, R2: int) -> np.ndar
     return out
 
 
-def match_centroid(cq_prev: np.ndarray, cq_now: np.ndarray, Lx: int, Ly: int, radius: int):
+def match_centroid(cq_prev: np.ndarray, cq_now: np.ndarray, Lx: int, Ly: int, radius: int,
+                   periodic=(True, True)):
     """Label isomorphism Phi_{P->N} from the two sets of centres (Section 3.2.3,
     the paper's kinematic comparison of frames a short time apart).
 
@@ -526,8 +586,8 @@ def match_centroid(cq_prev: np.ndarray, cq_now: np.ndarray, Lx: int, Ly: int, ra
     phi = np.full(K_prev, -1, dtype=np.int32)
     inv = np.full(K_now, -1, dtype=np.int32)
     R2 = (Q * int(radius)) ** 2
-    best_n = _nearest(cq_prev, cq_now, Lx, Ly, R2)
-    best_p = _nearest(cq_now, cq_prev, Lx, Ly, R2)
+    best_n = _nearest(cq_prev, cq_now, Lx, Ly, R2, periodic)
+    best_p = _nearest(cq_now, cq_prev, Lx, Ly, R2, periodic)
     for p in range(K_prev):
         n = int(best_n[p])
         if n >= 0 and int(best_p[n]) == p:
@@ -688,9 +748,11 @@ class Detector:
     def __init__(self, Lx: int, Ly: int, theta: float = 0.5, polarity: int = 1,
                  connectivity: int = 4, workers: int = 1, voronoi: str = "kdtree",
                  events: bool = False, match: str = "overlap", match_radius: int = 0,
-                 edge_rule: str = "adj4"):
+                 edge_rule: str = "adj4", walls=(False, False), obstacles=None):
         self.Lx, self.Ly = Lx, Ly
         self.edge_rule = edge_rule
+        self.periodic = (not walls[0], not walls[1])
+        self.obstacles = None if obstacles is None else np.asarray(obstacles, dtype=bool)
         self.events = events
         self.match = match
         self.match_radius = match_radius
@@ -705,13 +767,18 @@ class Detector:
         F = np.asarray(F, dtype=np.float32)
         assert F.shape == (self.Ly, self.Lx)
         fg = foreground(F, self.theta, self.polarity)
-        labels, K = label_components(fg, self.connectivity)
-        cq = centroids_q10(labels, K)
-        if self.voronoi == "brute":
-            own = owners_bruteforce(cq, self.Lx, self.Ly)
+        if self.obstacles is not None:
+            fg &= ~self.obstacles            # an obstacle site is never in a bubble
+        per = self.periodic
+        labels, K = label_components(fg, self.connectivity, per)
+        cq = centroids_q10(labels, K, per)
+        if self.voronoi == "brute" or per != (True, True):
+            own = owners_bruteforce(cq, self.Lx, self.Ly, periodic=per)
         else:
             own = owners(cq, self.Lx, self.Ly, workers=self.workers)
-        E = vertex_edges(own, cq) if self.edge_rule == "vertex" else delaunay_edges(own, cq)
+        if self.obstacles is not None:
+            own = np.where(self.obstacles, OBSTACLE, own).astype(np.int32)
+        E = vertex_edges(own, cq, per) if self.edge_rule == "vertex" else delaunay_edges(own, cq, per)
         out = dict(frame=self.frame, labels=labels, K=K, centroids=cq, owners=own, edges=E)
         if self.prev is None:
             out.update(phi=np.zeros(0, np.int32), inv=np.full(K, -1, np.int32),
@@ -721,7 +788,7 @@ class Detector:
         else:
             p = self.prev
             if self.match == "centroid":
-                phi, inv = match_centroid(p["centroids"], cq, self.Lx, self.Ly, self.match_radius)
+                phi, inv = match_centroid(p["centroids"], cq, self.Lx, self.Ly, self.match_radius, per)
             else:
                 phi, inv = match_overlap(p["labels"], labels, p["K"], K)
             fl = flips(p["edges"], E, phi, inv)

@@ -806,3 +806,112 @@ def test_vertex_rule_sees_no_vertex_between_two_stripes():
     assert int(O.frame_gaps(own).max()) == 2
     cq = np.array([[Q * 2, Q], [Q * 2, Q * 4]], dtype=np.int64)
     assert O.vertex_edges(own, cq).size == 0
+
+
+
+# ----------------------------------------------------------------------------
+# Walls (bounded axes, the paper's channel) and obstacles (MAXLINK sites)
+# ----------------------------------------------------------------------------
+
+def bfs_labels_walls(fg: np.ndarray, connectivity: int, periodic) -> np.ndarray:
+    """Flood fill in raster order; a step that crosses a bounded axis is not taken."""
+    Ly, Lx = fg.shape
+    lab = -np.ones((Ly, Lx), dtype=np.int64)
+    if connectivity == 4:
+        steps = [(1, 0), (-1, 0), (0, 1), (0, -1)]
+    else:
+        steps = [(a, b) for a in (-1, 0, 1) for b in (-1, 0, 1) if (a, b) != (0, 0)]
+    nxt = 0
+    for y in range(Ly):
+        for x in range(Lx):
+            if fg[y, x] and lab[y, x] < 0:
+                lab[y, x] = nxt
+                dq = deque([(x, y)])
+                while dq:
+                    cx, cy = dq.popleft()
+                    for dx, dy in steps:
+                        nx, ny = cx + dx, cy + dy
+                        if not periodic[0] and not 0 <= nx < Lx:
+                            continue
+                        if not periodic[1] and not 0 <= ny < Ly:
+                            continue
+                        nx, ny = nx % Lx, ny % Ly
+                        if fg[ny, nx] and lab[ny, nx] < 0:
+                            lab[ny, nx] = nxt
+                            dq.append((nx, ny))
+                nxt += 1
+    return lab
+
+
+@pytest.mark.parametrize("periodic", [(False, True), (True, False), (False, False)])
+@pytest.mark.parametrize("conn", [4, 8])
+def test_ccl_with_walls_matches_bfs(periodic, conn):
+    rng = np.random.default_rng(31 + conn + 2 * periodic[0] + 4 * periodic[1])
+    for trial in range(150):
+        Lx = int(rng.integers(1, 12))
+        Ly = int(rng.integers(1, 12))
+        fg = rng.random((Ly, Lx)) < float(rng.uniform(0.1, 0.9))
+        lab, K = O.label_components(fg, conn, periodic)
+        ref = bfs_labels_walls(fg, conn, periodic)
+        assert np.array_equal(lab, ref), (trial, Lx, Ly)
+
+
+def test_walls_split_bubbles_and_keep_plain_centres():
+    """A bar touching both x walls is two bubbles when x is bounded (one on the
+    torus); each centre is the plain mean of its sites (closed form)."""
+    fg = np.zeros((4, 10), dtype=bool)
+    fg[1, [0, 1, 8, 9]] = True
+    lab, K = O.label_components(fg, 4, (True, True))
+    assert K == 1
+    lab, K = O.label_components(fg, 4, (False, True))
+    assert K == 2
+    cq = O.centroids_q10(lab, K, (False, True))
+    assert cq.tolist() == [[512, Q], [Q * 8 + 512, Q]]
+
+
+def test_walls_change_owners_links_and_matches():
+    """Centres at x = 1 and x = 8 on a 10-wide lattice own the same halves with
+    or without walls; three cells side by side are linked across the seam only
+    on the torus; the centre match measures plain distances with walls."""
+    cq = np.array([[Q * 1, Q], [Q * 8, Q]], dtype=np.int64)
+    own_t = O.owners_bruteforce(cq, 10, 3)
+    own_w = O.owners_bruteforce(cq, 10, 3, periodic=(False, True))
+    assert own_w[0].tolist() == [0, 0, 0, 0, 0, 1, 1, 1, 1, 1]
+    assert own_t[0].tolist() == [0, 0, 0, 0, 0, 1, 1, 1, 1, 1]
+    E_t = O.delaunay_edges(own_t, cq)
+    E_w = O.delaunay_edges(own_w, cq, (False, True))
+    assert E_t.tolist() == E_w.tolist() == O.make_keys([0], [1]).tolist()
+    # three cells side by side: 2 and 0 meet only across the seam
+    own = np.zeros((3, 10), dtype=np.int32)
+    own[:, 3:7] = 1
+    own[:, 7:] = 2
+    cq3 = np.array([[Q, Q], [Q * 5, Q], [Q * 8, Q]], dtype=np.int64)
+    assert O.delaunay_edges(own, cq3).tolist() == O.make_keys([0, 0, 1], [1, 2, 2]).tolist()
+    assert O.delaunay_edges(own, cq3, (False, True)).tolist() == O.make_keys([0, 1], [1, 2]).tolist()
+    # centre match: 9.5 sites apart plainly, 0.5 through the seam
+    p = np.array([[Q // 4, Q]], dtype=np.int64)
+    n = np.array([[Q * 9 + 3 * Q // 4, Q]], dtype=np.int64)
+    assert O.match_centroid(p, n, 10, 3, radius=1)[0].tolist() == [0]
+    assert O.match_centroid(p, n, 10, 3, radius=1, periodic=(False, True))[0].tolist() == [-1]
+
+
+def test_obstacles_are_never_bubbles_owners_or_links():
+    """An obstacle column splits a bar; its sites get the MAXLINK owner and no
+    link touches it, so the two cells beside it are linked only where they
+    meet without the obstacle in between."""
+    L = 12
+    F = np.zeros((L, L), dtype=np.float32)
+    F[5, :] = 1.0
+    obst = np.zeros((L, L), dtype=bool)
+    obst[:, 6] = True
+    d = O.Detector(L, L, voronoi="brute", obstacles=obst)
+    r = d.push(F)
+    assert r["K"] == 1                       # the bar still joins around the seam
+    assert (r["labels"][:, 6] == -1).all()
+    assert (r["owners"][:, 6] == O.OBSTACLE).all()
+    d2 = O.Detector(L, L, voronoi="brute", obstacles=obst, walls=(True, False))
+    r2 = d2.push(F)
+    assert r2["K"] == 2                      # walls in x and the obstacle: two bars
+    a, b = O.split_keys(r2["edges"])
+    assert (a >= 0).all() and (b >= 0).all()
+    assert (r2["owners"][:, 6] == O.OBSTACLE).all()
