@@ -69,16 +69,27 @@ typedef struct vd_config {
     int32_t match_rule;        /* VD_MATCH_OVERLAP (default) or VD_MATCH_CENTROID (Section 3.2.3) */
     int32_t match_radius;      /* VD_MATCH_CENTROID: largest centre displacement matched, in sites (>= 1) */
     int32_t edge_rule;         /* VD_EDGE_ADJ4 (default) or VD_EDGE_VERTEX (Section 3.2.2) */
+    int32_t walls;             /* VD_WALL_X | VD_WALL_Y: bounded axes (0 = periodic torus) */
 } vd_config;
+
+/* Walls (the paper's channel geometry, Sections 3.2.1-3.2.2): a bounded axis
+ * joins nothing across its ends -- no bubble, no minimum image, no link. The
+ * library runs a bounded axis of length L as a periodic axis of length 2L
+ * whose second half is never a bubble: every distance between two points of
+ * the domain is then the plain one (below half the period). Obstacle sites
+ * (vd_set_obstacles) are never in a bubble; their owner is VD_OWNER_OBSTACLE
+ * (the paper's MAXLINK colour) and no link touches them. */
+enum { VD_WALL_X = 1, VD_WALL_Y = 2 };
+enum { VD_OWNER_OBSTACLE = -2 };
 
 /* Links of the digital Voronoi diagram (Section 3.2.2). ADJ4: owners that
  * differ between +x / +y neighbouring sites, plus the exact incircle diagonal
  * of every plaquette with four distinct owners. VERTEX: the paper's own rule,
  * read at vertex sites only (three or more colour changes around the 8-site
  * frame) with its first- and second-neighbour conditions; the inner-frame
- * point of a diagonal is read as the plaquette centre, owned by the exact
- * nearest-centre rule. The figure defining the inner frame is lost, so the
- * VERTEX rule follows that reading. */
+ * point of a diagonal is read as the plaquette centre, coloured by the
+ * nearest centre among the colours at the plaquette's corners. The figure
+ * defining the inner frame is lost, so the VERTEX rule follows that reading. */
 enum { VD_EDGE_ADJ4 = 0, VD_EDGE_VERTEX = 1 };
 
 /* Isomorphism Phi between past and now labels (Section 3.2.3). OVERLAP: the
@@ -107,6 +118,12 @@ vd_status vd_create(const vd_config* cfg, vd_ctx** out);
  * device; the first frame after creation reports no changes. Asynchronous:
  * device-side capacity overflows are reported by the next getter. */
 vd_status vd_push_frame(vd_ctx* ctx, const float* d_field, size_t pitch);
+
+/* Obstacle sites of the lattice: host array of Ly rows of `pitch` bytes, a
+ * nonzero byte marks an obstacle (Lx <= pitch). Applies from the next pushed
+ * frame on; the mask stays until it is replaced (an all-zero mask clears it).
+ * Errors: VD_ERR_INVALID, VD_ERR_CUDA. */
+vd_status vd_set_obstacles(vd_ctx* ctx, const uint8_t* h_mask, int64_t pitch);
 
 /* Same as vd_push_frame with a host-memory field: copies it to a context-owned
  * device buffer on the context stream first (synchronous w.r.t. `h_field`). */
@@ -227,6 +244,9 @@ vd_status vd_batch_push_host(vd_batch* b, const float* const* h_fields);
 vd_status vd_batch_push_subset(vd_batch* b, const int32_t* active, int32_t n_active,
                                const float* const* d_fields);
 vd_status vd_batch_get_changes(vd_batch* b, int32_t i, vd_changes* out);
+
+/* Obstacle sites of instance i (see vd_set_obstacles). */
+vd_status vd_batch_set_obstacles(vd_batch* b, int32_t i, const uint8_t* h_mask, int64_t pitch);
 
 /* Double-buffered host input. vd_batch_stage_host copies h_fields (HOST array
  * of n HOST pointers, Ly*Lx floats each, pinned for asynchrony) into the next

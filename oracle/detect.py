@@ -466,7 +466,9 @@ def vertex_edges(owner: np.ndarray, cq: np.ndarray, periodic=(True, True)) -> np
     * second neighbour k+e1+e2 is linked to k when its colour differs from
       k's, C(k+e2) != C(k+e1-e2), C(k+e2) != C(k+e1) (the short diagonal),
       and the inner-frame point -- read as the centre of the plaquette,
-      k + (e1+e2)/2 -- is owned by k's colour or by the neighbour's.
+      k + (e1+e2)/2 -- takes k's colour or the neighbour's; its colour is the
+      one, among the colours at the plaquette's four corners, whose centre is
+      nearest (exact squared distance, ties to the smallest label).
 
     Walls truncate the frame (neighbours beyond them leave it) and obstacle
     sites carry the MAXLINK colour: neither is ever linked, nor is a site that
@@ -496,8 +498,18 @@ def vertex_edges(owner: np.ndarray, cq: np.ndarray, periodic=(True, True)) -> np
             continue
         px = (Q * xs + (Q // 2) * (e1x + e2x)) % (Q * Lx)
         py = (Q * ys + (Q // 2) * (e1y + e2y)) % (Q * Ly)
-        ca = owners_at_q10(cq, Lx, Ly, px, py, periodic)
         kk, xx = own[ys, xs], X[ys, xs]
+        # colour of the inner-frame point: the nearest centre among the colours
+        # at the plaquette's four corners (k, k+e1, k+e1+e2, k+e2)
+        cand = np.stack([kk, A1[ys, xs], xx, A2[ys, xs]], axis=1)
+        ok_c = cand >= 0
+        cl = np.where(ok_c, cand, 0)
+        d2 = sq_dist_q10(px[:, None], py[:, None], cq[cl, 0].astype(np.int64), cq[cl, 1].astype(np.int64),
+                         Lx, Ly, periodic)
+        big = np.iinfo(np.int64).max
+        d2 = np.where(ok_c, d2, big)
+        best = d2.min(axis=1)
+        ca = np.where(ok_c & (d2 == best[:, None]), cand, big).min(axis=1)
         sel = (ca == kk) | (ca == xx)
         keys.append(make_keys(kk[sel], xx[sel]).astype(np.int64))
     allk = np.concatenate(keys) if keys else np.zeros(0, dtype=np.int64)

@@ -80,6 +80,7 @@ struct vd_batch {
     bool any_events = false;           // some instance classifies its events
     bool any_centroid_match = false;   // some instance matches by centres
     bool any_vertex_rule = false;      // some instance reads links at Voronoi vertices
+    bool any_masked = false;           // some instance has walls or obstacles
     // field pointer tables (device) and their host mirrors
     const float** d_fields = nullptr;
     long long* d_pitches = nullptr;
@@ -145,8 +146,11 @@ vd_status cuda_status(cudaError_t e) { return e == cudaSuccess ? VD_OK : VD_ERR_
 
 bool valid_cfg(const vd_config& c) {
     if (c.Lx < 1 || c.Ly < 1) return false;
-    if (c.Lx >= (1 << 21) || c.Ly >= (1 << 21)) return false;   // 1024*L must fit int32
-    if ((long long)c.Lx * c.Ly >= (1ll << 31)) return false;
+    if (c.walls < 0 || c.walls > 3) return false;
+    // a bounded axis runs with twice its length
+    const long long iLx = (c.walls & 1) ? 2ll * c.Lx : c.Lx, iLy = (c.walls & 2) ? 2ll * c.Ly : c.Ly;
+    if (iLx >= (1 << 21) || iLy >= (1 << 21)) return false;   // 1024*L must fit int32
+    if (iLx * iLy >= (1ll << 31)) return false;
     if (c.connectivity != 4 && c.connectivity != 8) return false;
     if (c.polarity != VD_ABOVE && c.polarity != VD_BELOW) return false;
     if (c.max_components < 0 || c.max_edges < 0) return false;
@@ -208,6 +212,7 @@ Launch make_launch(vd_batch* b, const StepTables& T) {
     L.events = b->any_events;
     L.centroid_match = b->any_centroid_match;
     L.vertex_rule = b->any_vertex_rule;
+    L.masked = b->any_masked;
     L.grid_wide = 4 * b->grid_items;
     L.total_tilesA = T.total_tilesA;
     L.total_tilesV = T.total_tilesV;
@@ -269,9 +274,16 @@ vd_status create_batch(const vd_config* cfgs, int n, vd_batch** out, bool sequen
         const vd_config& c = cfgs[i];
         InstDesc& D = b->desc[i];
         memset(&D, 0, sizeof(D));
-        const long long N = (long long)c.Lx * c.Ly;
-        D.Lx = c.Lx;
-        D.Ly = c.Ly;
+        // a bounded axis (walls) runs as a periodic axis of twice the length
+        // whose second half is never a bubble
+        const int iLx = (c.walls & 1) ? 2 * c.Lx : c.Lx, iLy = (c.walls & 2) ? 2 * c.Ly : c.Ly;
+        const long long N = (long long)iLx * iLy, Nu = (long long)c.Lx * c.Ly;
+        D.Lx = iLx;
+        D.Ly = iLy;
+        D.uLx = c.Lx;
+        D.uLy = c.Ly;
+        D.masked = c.walls ? 1 : 0;
+        b->any_masked = b->any_masked || c.walls;
         D.thr = c.threshold;
         D.pol = c.polarity;
         D.events = c.events;
@@ -282,19 +294,19 @@ vd_status create_batch(const vd_config* cfgs, int n, vd_batch** out, bool sequen
         D.match_radius = c.match_rule == VD_MATCH_CENTROID ? c.match_radius : 0;
         b->any_events = b->any_events || c.events;
         b->any_centroid_match = b->any_centroid_match || c.match_rule == VD_MATCH_CENTROID;
-        D.ntx = (c.Lx + TW - 1) / TW;
-        D.nty = (c.Ly + TH - 1) / TH;
-        D.vtx = (c.Lx + VW - 1) / VW;
-        D.vty = (c.Ly + VH - 1) / VH;
-        D.wpr = (c.Lx + 31) / 32;
+        D.ntx = (iLx + TW - 1) / TW;
+        D.nty = (iLy + TH - 1) / TH;
+        D.vtx = (iLx + VW - 1) / VW;
+        D.vty = (iLy + VH - 1) / VH;
+        D.wpr = (iLx + 31) / 32;
         D.gpr = (D.wpr + RGW - 1) / RGW;
         // frame sequence: instance i's past frame is instance i-1 of the same
         // step, instance 0's is instance n-1 of the previous step
         D.seq_prev = sequence ? (i == 0 ? n - 1 : i - 1) : i;
         D.seq_same = (sequence && i > 0) ? 1 : 0;
         long long kcap = c.max_components ? c.max_components
-                                          : (N <= 65536 ? (N + 1) / 2 : std::max<long long>(N / 8, 65536));
-        kcap = std::min<long long>(kcap, (N + 1) / 2);
+                                          : (Nu <= 65536 ? (Nu + 1) / 2 : std::max<long long>(Nu / 8, 65536));
+        kcap = std::min<long long>(kcap, (Nu + 1) / 2);
         long long ecap = c.max_edges ? c.max_edges : 3 * kcap + 64;
         long long ocap = 2 * kcap + 64;
         D.comp_cap = (int)kcap;
@@ -302,7 +314,7 @@ vd_status create_batch(const vd_config* cfgs, int n, vd_batch** out, bool sequen
         D.ovl_cap = (int)ocap;
         D.ehash_mask = (int)(next_pow2(2 * ecap) - 1);
         D.ohash_mask = (int)(next_pow2(2 * ocap) - 1);
-        D.bucket_cap = ((c.Lx + 3) / 4) * ((c.Ly + 3) / 4);
+        D.bucket_cap = ((iLx + 3) / 4) * ((iLy + 3) / 4);
         D.site_off = site;
         D.word_off = word;
         D.grp_off = grp;
@@ -317,8 +329,8 @@ vd_status create_batch(const vd_config* cfgs, int n, vd_batch** out, bool sequen
         const long long ntiles = (long long)D.ntx * D.nty;
         site += N;
         max_sites = std::max(max_sites, N);
-        word += (long long)c.Ly * D.wpr;
-        grp += (long long)c.Ly * D.gpr;
+        word += (long long)iLy * D.wpr;
+        grp += (long long)iLy * D.gpr;
         tile += ntiles;
         border += ntiles * BORDER;
         comp += kcap + 1;
@@ -348,6 +360,7 @@ vd_status create_batch(const vd_config* cfgs, int n, vd_batch** out, bool sequen
     P.fgbits[0] = M.alloc<unsigned>(word);
     P.fgbits[1] = M.alloc<unsigned>(word);
     P.rootbits = M.alloc<unsigned>(word);
+    P.obst = M.alloc<unsigned>(word);
     P.rgcnt = M.alloc<int>(grp);
     P.rankpre = M.alloc<int>(grp);
     P.tile_pbase = M.alloc<int>(tile);
@@ -420,6 +433,7 @@ vd_status create_batch(const vd_config* cfgs, int n, vd_batch** out, bool sequen
     chk(cudaMemsetAsync(P.rl[0], 0xff, sizeof(int) * tile * TRUNS, b->s));
     chk(cudaMemsetAsync(P.rl[1], 0xff, sizeof(int) * tile * TRUNS, b->s));
     chk(cudaMemsetAsync(P.rootbits, 0, sizeof(unsigned) * word, b->s));
+    chk(cudaMemsetAsync(P.obst, 0, sizeof(unsigned) * word, b->s));
     chk(cudaMemsetAsync(P.rgcnt, 0, sizeof(int) * grp, b->s));
     chk(cudaMemsetAsync(P.bcnt, 0, sizeof(int) * bucket, b->s));
     chk(cudaMemsetAsync(P.deg, 0, sizeof(int) * comp, b->s));
@@ -666,12 +680,12 @@ vd_status get_array(vd_batch* b, int i, int which, void* out, int64_t cap, int64
     size_t esz = 4;
     switch (which) {
         case 0: {
-            cnt = N;
+            cnt = (long long)D.uLx * D.uLy;
             launch_expand_labels(b->s, b->P, i, slot, b->P.lab_out, N);
             src = b->P.lab_out;
             break;
         }
-        case 1: cnt = N; src = b->P.owners + D.site_off; break;
+        case 1: cnt = (long long)D.uLx * D.uLy; src = b->P.owners + D.site_off; break;
         case 2: cnt = 2ll * st.K; src = b->P.cq[slot] + D.comp_off; break;
         case 3: {
             cnt = st.E;
@@ -688,7 +702,47 @@ vd_status get_array(vd_batch* b, int i, int which, void* out, int64_t cap, int64
     vd_status es = err_status(st);
     if (es) return es;
     if (cap < cnt) return VD_ERR_CAPACITY;
+    if ((which == 0 || which == 1) && (D.uLx != D.Lx || D.uLy != D.Ly)) {
+        // a bounded axis runs with twice its length: return the domain only
+        if (cnt == 0) return VD_OK;
+        cudaError_t e = cudaMemcpy2DAsync(out, sizeof(int) * D.uLx, src, sizeof(int) * D.Lx, sizeof(int) * D.uLx,
+                                          D.uLy, cudaMemcpyDefault, b->s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(b->s);
+        return cuda_status(e);
+    }
     return copy_out(out, src, (size_t)cnt * esz, b->s);
+}
+
+// obstacle bits of instance i from a host byte mask (uLy rows of `pitch` bytes)
+vd_status set_obstacles(vd_batch* b, int i, const uint8_t* h_mask, int64_t pitch) {
+    if (!b || i < 0 || i >= b->n || !h_mask) return VD_ERR_INVALID;
+    InstDesc& D = b->desc[i];
+    if (pitch < D.uLx) return VD_ERR_INVALID;
+    std::vector<unsigned> bits((size_t)D.Ly * D.wpr, 0u);
+    bool any = false;
+    for (int y = 0; y < D.uLy; ++y)
+        for (int x = 0; x < D.uLx; ++x)
+            if (h_mask[(long long)y * pitch + x]) {
+                bits[(size_t)y * D.wpr + (x >> 5)] |= 1u << (x & 31);
+                any = true;
+            }
+    cudaError_t e = cudaMemcpyAsync(b->P.obst + D.word_off, bits.data(), sizeof(unsigned) * bits.size(),
+                                    cudaMemcpyHostToDevice, b->s);
+    const int masked = (D.uLx != D.Lx || D.uLy != D.Ly || any) ? 1 : 0;
+    if (e == cudaSuccess && masked != D.masked) {
+        D.masked = masked;
+        e = cudaMemcpyAsync(b->P.desc + i, &D, sizeof(InstDesc), cudaMemcpyHostToDevice, b->s);
+        if (masked && !b->any_masked) {
+            // the step gains the owner-marking launch: capture the graph again
+            b->any_masked = true;
+            if (b->graph) {
+                cudaGraphExecDestroy(b->graph);
+                b->graph = nullptr;
+            }
+        }
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->s);   // `bits` is released on return
+    return cuda_status(e);
 }
 
 }  // namespace
@@ -772,7 +826,7 @@ vd_status vd_create(const vd_config* cfg, vd_ctx** out) {
 vd_status vd_push_frame(vd_ctx* ctx, const float* d_field, size_t pitch) {
     if (!ctx || !d_field) return VD_ERR_INVALID;
     vd_batch* b = ctx->b;
-    if ((long long)pitch < b->desc[0].Lx) return VD_ERR_INVALID;
+    if ((long long)pitch < b->desc[0].uLx) return VD_ERR_INVALID;
     const long long p = (long long)pitch;
     std::vector<int> act{0};
     vd_status r = push_fields(b, act, &d_field, &p);
@@ -784,18 +838,26 @@ vd_status vd_push_frame_host(vd_ctx* ctx, const float* h_field, size_t pitch) {
     if (!ctx || !h_field) return VD_ERR_INVALID;
     vd_batch* b = ctx->b;
     const InstDesc& D = b->desc[0];
-    if ((long long)pitch < D.Lx) return VD_ERR_INVALID;
+    if ((long long)pitch < D.uLx) return VD_ERR_INVALID;
     if (!b->d_host_field) {
-        b->d_host_field = b->mem.alloc<float>((long long)D.Lx * D.Ly);
+        b->d_host_field = b->mem.alloc<float>((long long)D.uLx * D.uLy);
         if (!b->mem.ok) return VD_ERR_OOM;
     }
-    cudaError_t e = cudaMemcpy2DAsync(b->d_host_field, sizeof(float) * D.Lx, h_field, sizeof(float) * pitch,
-                                      sizeof(float) * D.Lx, D.Ly, cudaMemcpyHostToDevice, b->s);
+    cudaError_t e = cudaMemcpy2DAsync(b->d_host_field, sizeof(float) * D.uLx, h_field, sizeof(float) * pitch,
+                                      sizeof(float) * D.uLx, D.uLy, cudaMemcpyHostToDevice, b->s);
     if (e != cudaSuccess) return VD_ERR_CUDA;
-    return vd_push_frame(ctx, b->d_host_field, D.Lx);
+    return vd_push_frame(ctx, b->d_host_field, D.uLx);
 }
 
 vd_status vd_get_changes(vd_ctx* ctx, vd_changes* out) { return ctx ? get_changes(ctx->b, 0, out) : VD_ERR_INVALID; }
+
+vd_status vd_set_obstacles(vd_ctx* ctx, const uint8_t* h_mask, int64_t pitch) {
+    return ctx ? set_obstacles(ctx->b, 0, h_mask, pitch) : VD_ERR_INVALID;
+}
+
+vd_status vd_batch_set_obstacles(vd_batch* b, int32_t i, const uint8_t* h_mask, int64_t pitch) {
+    return set_obstacles(b, i, h_mask, pitch);
+}
 
 vd_status vd_get_counts(vd_ctx* ctx, int32_t* K, int32_t* n_edges, int64_t* frame_index) {
     if (!ctx) return VD_ERR_INVALID;
@@ -887,7 +949,7 @@ vd_status vd_batch_push(vd_batch* b, const float* const* d_fields) {
     std::vector<long long> pitch(b->n);
     for (int i = 0; i < b->n; ++i) {
         act[i] = i;
-        pitch[i] = b->desc[i].Lx;
+        pitch[i] = b->desc[i].uLx;
     }
     vd_status r = push_fields(b, act, d_fields, pitch.data());
     if (r) return r;
@@ -909,13 +971,13 @@ vd_status vd_batch_stage_host(vd_batch* b, const float* const* h_fields) {
     if (b->d_stage[k].empty()) {
         // one allocation per buffer set: instance i's frame follows instance i-1's
         long long total = 0;
-        for (int i = 0; i < b->n; ++i) total += (long long)b->desc[i].Lx * b->desc[i].Ly;
+        for (int i = 0; i < b->n; ++i) total += (long long)b->desc[i].uLx * b->desc[i].uLy;
         float* base = b->mem.alloc<float>(total);
         if (!b->mem.ok) return VD_ERR_OOM;
         b->d_stage[k].resize(b->n);
         for (int i = 0; i < b->n; ++i) {
             b->d_stage[k][i] = base;
-            base += (long long)b->desc[i].Lx * b->desc[i].Ly;
+            base += (long long)b->desc[i].uLx * b->desc[i].uLy;
         }
     }
     // the step that last read this buffer must be done with it
@@ -924,17 +986,17 @@ vd_status vd_batch_stage_host(vd_batch* b, const float* const* h_fields) {
     // frames from different host allocations make the runtime refuse the
     // merged copy (a non-sticky argument error), and they are copied one by one
     for (int i = 0; i < b->n;) {
-        size_t bytes = sizeof(float) * (size_t)b->desc[i].Lx * b->desc[i].Ly;
+        size_t bytes = sizeof(float) * (size_t)b->desc[i].uLx * b->desc[i].uLy;
         int j = i + 1;
         while (j < b->n && h_fields[j] == h_fields[i] + bytes / sizeof(float)) {
-            bytes += sizeof(float) * (size_t)b->desc[j].Lx * b->desc[j].Ly;
+            bytes += sizeof(float) * (size_t)b->desc[j].uLx * b->desc[j].uLy;
             ++j;
         }
         if (cudaMemcpyAsync(b->d_stage[k][i], h_fields[i], bytes, cudaMemcpyHostToDevice, b->cs) != cudaSuccess) {
             if (j == i + 1) return VD_ERR_CUDA;
             cudaGetLastError();
             for (int m = i; m < j; ++m) {
-                const size_t bm = sizeof(float) * (size_t)b->desc[m].Lx * b->desc[m].Ly;
+                const size_t bm = sizeof(float) * (size_t)b->desc[m].uLx * b->desc[m].uLy;
                 if (cudaMemcpyAsync(b->d_stage[k][m], h_fields[m], bm, cudaMemcpyHostToDevice, b->cs) != cudaSuccess)
                     return VD_ERR_CUDA;
             }
@@ -1005,7 +1067,7 @@ vd_status vd_batch_push_subset(vd_batch* b, const int32_t* active, int32_t n_act
     for (int a = 0; a < n_active; ++a) {
         if (act[a] < 0 || act[a] >= b->n || seen[act[a]]) return VD_ERR_INVALID;
         seen[act[a]] = 1;
-        pitch[a] = b->desc[act[a]].Lx;
+        pitch[a] = b->desc[act[a]].uLx;
     }
     if (n_active == b->n) {
         bool ordered = true;

@@ -278,8 +278,17 @@ __global__ __launch_bounds__(32 * CCL_WARPS, 8) void k_ccl_tiles(Pools P, StepTa
         const int y = y0 + lane;
         if (y < Ly) {
             const int n = min(TW, Lx - x0);
-            my_m = threshold_row(S.field + (long long)y * S.pitch + x0, n, D.thr, D.pol);
+            // the field covers the domain only (a bounded axis runs with twice
+            // its length; the second half is never a bubble)
+            const int nu = min(n, D.uLx - x0);
+            if (y < D.uLy && nu > 0) my_m = threshold_row(S.field + (long long)y * S.pitch + x0, nu, D.thr, D.pol);
             unsigned* row = P.fgbits[S.slot ^ 1] + D.word_off + (long long)y * D.wpr + (x0 >> 5);
+            if (D.masked) {   // obstacle sites are never in a bubble
+                const unsigned* ob = P.obst + D.word_off + (long long)y * D.wpr + (x0 >> 5);
+                unsigned long long om = ob[0];
+                if (n > 32) om |= (unsigned long long)ob[1] << 32;
+                my_m &= ~om;
+            }
             row[0] = (unsigned)my_m;
             if (n > 32) row[1] = (unsigned)(my_m >> 32);
         }

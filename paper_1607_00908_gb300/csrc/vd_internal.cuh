@@ -38,6 +38,11 @@ constexpr int RGW = 8;
 
 constexpr unsigned long long EMPTY_KEY = ~0ull;
 
+// owners that are not bubbles: the site of an obstacle (the paper's MAXLINK
+// colour) and a site beyond a wall (a bounded axis runs with twice its length)
+constexpr int OWN_OBSTACLE = -2;
+constexpr int OWN_OUTSIDE = -3;
+
 // error bits in InstState::err and Globals::err
 enum : int {
     ERR_EDGE_CAP = 1,       // link hash or list overflow
@@ -93,7 +98,9 @@ struct InstDesc {
     int match_radius;        // centroid match: largest displacement, sites
     int conn8;               // 8-connectivity (else 4)
     int edge_rule;           // VD_EDGE_ADJ4 / VD_EDGE_VERTEX
-    int pad2;
+    int masked;              // walls or obstacles: owners outside the domain / on obstacles are marked
+    int uLx, uLy;            // the domain as the caller sees it; a bounded axis runs as 2 x its length
+    int pad3;
 };
 
 // ---------------------------------------------------------------------------
@@ -152,6 +159,7 @@ struct Pools {
     int* rl[2];              // bubble label of every run of the frames in slot 0 / 1
     int* lab_out;            // per-site labels of one instance, expanded on request
     unsigned* rootbits;
+    unsigned* obst;          // obstacle bits (word layout of the foreground bits)
     int* rgcnt;              // roots per root group (zero between steps)
     int* rankpre;            // exclusive rank prefix per root group (this step)
     // labelling tiles
@@ -433,6 +441,7 @@ struct Launch {
     bool events;         // some instance classifies its events
     bool centroid_match; // some instance matches by centres
     bool vertex_rule;    // some instance reads its links at Voronoi vertices
+    bool masked;         // some instance has walls or obstacles
     cudaStream_t s;
     Pools P;
     StepTable T;

@@ -21,6 +21,8 @@
 // each label's degree.
 #include "vd_internal.cuh"
 
+#include <type_traits>
+
 namespace vd {
 
 // distance from a point (offset d of the point from the interval start, already
@@ -532,35 +534,47 @@ __global__ __launch_bounds__(32 * LINK_WARPS) void k_links(Pools P, StepTable T)
     const bool valid = lane < ncols;
     const int l = min(lane, ncols - 1);
     const unsigned lt = (1u << lane) - 1u;
-    int o = S[l], rt = S[l + 1];
-    int up = 0, upr = 0;
-    int lf = __shfl_up_sync(0xffffffffu, o, 1);
     int n = 0;   // keys in the warp's list (warp-uniform)
-    for (int r = 0; r < nrows; ++r) {
-        const int dn = S[(r + 1) * LS + l];
-        const int dg = S[(r + 1) * LS + l + 1];
-        const int dlf = __shfl_up_sync(0xffffffffu, dn, 1);
-        const bool eh = valid && o != rt && !(r > 0 && (up == rt || upr == o || (up == o && upr == rt)));
-        const bool ev = valid && o != dn && rt != dn && !(lane > 0 && (lf == dn || (lf == o && dlf == dn)));
-        const bool ep = valid && o != rt && o != dn && o != dg && rt != dn && rt != dg && dn != dg;
-        const unsigned mh = __ballot_sync(0xffffffffu, eh);
-        const unsigned mv = __ballot_sync(0xffffffffu, ev);
-        const unsigned mp = __ballot_sync(0xffffffffu, ep);
-        if (mh | mv | mp) {
-            // append this row's keys: horizontal, vertical, then plaquettes
-            const int nh = __popc(mh), nv = __popc(mv);
-            if (eh) link_list_put(list, n + __popc(mh & lt), edge_key(o, rt), P, D, inst);
-            if (ev) link_list_put(list, n + nh + __popc(mv & lt), edge_key(o, dn), P, D, inst);
-            if (ep) link_list_put(list, n + nh + nv + __popc(mp & lt), plaquette_key(o, rt, dg, dn, cq, MX, MY), P, D,
-                                  inst);
-            n += nh + nv + __popc(mp);
+    // the row loop in two copies: with walls or obstacles negative owners
+    // (obstacles, beyond a wall) are never linked; without them every owner
+    // is a label and the tests are left out
+    auto rows = [&](auto masked) {
+        constexpr bool MK = decltype(masked)::value;
+        int o = S[l], rt = S[l + 1];
+        int up = 0, upr = 0;
+        int lf = __shfl_up_sync(0xffffffffu, o, 1);
+        for (int r = 0; r < nrows; ++r) {
+            const int dn = S[(r + 1) * LS + l];
+            const int dg = S[(r + 1) * LS + l + 1];
+            const int dlf = __shfl_up_sync(0xffffffffu, dn, 1);
+            const bool eh = valid && o != rt && (!MK || (o >= 0 && rt >= 0)) &&
+                            !(r > 0 && (up == rt || upr == o || (up == o && upr == rt)));
+            const bool ev = valid && o != dn && rt != dn && (!MK || (o >= 0 && dn >= 0)) &&
+                            !(lane > 0 && (lf == dn || (lf == o && dlf == dn)));
+            const bool ep = valid && o != rt && o != dn && o != dg && rt != dn && rt != dg && dn != dg &&
+                            (!MK || (o >= 0 && rt >= 0 && dn >= 0 && dg >= 0));
+            const unsigned mh = __ballot_sync(0xffffffffu, eh);
+            const unsigned mv = __ballot_sync(0xffffffffu, ev);
+            const unsigned mp = __ballot_sync(0xffffffffu, ep);
+            if (mh | mv | mp) {
+                // append this row's keys: horizontal, vertical, then plaquettes
+                const int nh = __popc(mh), nv = __popc(mv);
+                if (eh) link_list_put(list, n + __popc(mh & lt), edge_key(o, rt), P, D, inst);
+                if (ev) link_list_put(list, n + nh + __popc(mv & lt), edge_key(o, dn), P, D, inst);
+                if (ep)
+                    link_list_put(list, n + nh + nv + __popc(mp & lt), plaquette_key(o, rt, dg, dn, cq, MX, MY), P,
+                                  D, inst);
+                n += nh + nv + __popc(mp);
+            }
+            up = o;
+            upr = rt;
+            o = dn;
+            rt = dg;
+            lf = dlf;
         }
-        up = o;
-        upr = rt;
-        o = dn;
-        rt = dg;
-        lf = dlf;
-    }
+    };
+    if (D.masked) rows(std::true_type{});
+    else rows(std::false_type{});
     __syncwarp();
     // equal keys within a round of 32 are merged; the tile's keys are
     // appended to the instance's link list (the link hash removes the rest)
@@ -631,48 +645,10 @@ void launch_voronoi(const Launch& L) {
 //   C(k+e2) != C(k+e1), and the inner-frame point (read as the plaquette
 //   centre k + (e1+e2)/2) is owned by C(k) or by C(k+e1+e2).
 // One thread per site of a 32 x 32 tile (one warp per tile, lane = column);
-// vertex sites are rare, and the owner of a plaquette centre comes from an
-// exact ring search over the frame's bucket grid.
+// vertex sites are rare. The colour of a plaquette centre is the nearest
+// centre among the colours at the plaquette's corners (exact, ties to the
+// smallest label).
 // ---------------------------------------------------------------------------
-
-// owner of the Q10 point (qx, qy): nearest centre, ties to the smallest label.
-// Rings of buckets are scanned outwards; a bucket r rings away is at least
-// (r - 2) * B sites from the point (r - 1 buckets lie between, one of them
-// possibly the ragged last one), so the scan stops before ring r once the
-// best distance is below that.
-__device__ int owner_of_point(const int2* bcq, const int* bid, const int* boff, int B, int nbx, int nby,
-                              long long qx, long long qy, long long MX, long long MY) {
-    if (nbx <= 0 || nby <= 0) return -1;
-    const int bx = (int)(qx / Q) / B, by = (int)(qy / Q) / B;
-    int best = -1;
-    long long bd = 0;
-    const int rmax = max(nbx, nby);
-    for (int r = 0; r <= rmax; ++r) {
-        if (best >= 0 && r >= 3) {
-            const long long lim = (long long)(r - 2) * B * Q;
-            if (bd < lim * lim) break;
-        }
-        for (int dy = -r; dy <= r; ++dy) {
-            const bool edge_row = dy == -r || dy == r;
-            for (int dx = -r; dx <= r; dx += (edge_row ? 1 : 2 * r)) {
-                const int cbx = ((bx + dx) % nbx + nbx) % nbx, cby = ((by + dy) % nby + nby) % nby;
-                const int bk = cby * nbx + cbx;
-                for (int k = boff[bk]; k < boff[bk + 1]; ++k) {
-                    const int2 c = bcq[k];
-                    const long long ddx = wrap_ll((long long)c.x - qx, MX), ddy = wrap_ll((long long)c.y - qy, MY);
-                    const long long d = ddx * ddx + ddy * ddy;
-                    const int id = bid[k];
-                    if (best < 0 || d < bd || (d == bd && id < best)) {
-                        bd = d;
-                        best = id;
-                    }
-                }
-                if (r == 0) break;
-            }
-        }
-    }
-    return best;
-}
 
 __device__ __forceinline__ void vertex_link(const Pools& P, const InstDesc& D, int inst, int a, int b) {
     const unsigned long long key = edge_key(a, b);
@@ -697,7 +673,7 @@ __global__ __launch_bounds__(32 * LINK_WARPS) void k_links_vertex(Pools P, StepT
     const int Lx = D.Lx, Ly = D.Ly;
     const int x = tx * VW + lane;
     if (x >= Lx) return;
-    const int now = S.slot ^ 1;
+    const int2* cq = P.cq[S.slot ^ 1] + D.comp_off;
     const int* own = P.owners + D.site_off;
     const long long MX = (long long)Q * Lx, MY = (long long)Q * Ly;
     const int xm = x == 0 ? Lx - 1 : x - 1, xp = x + 1 == Lx ? 0 : x + 1;
@@ -712,32 +688,83 @@ __global__ __launch_bounds__(32 * LINK_WARPS) void k_links_vertex(Pools P, StepT
         f[0] = r0[xp]; f[1] = rp[xp]; f[2] = rp[x]; f[3] = rp[xm];
         f[4] = r0[xm]; f[5] = rm[xm]; f[6] = rm[x]; f[7] = rm[xp];
         f[8] = r0[x];
+        // colour changes around the frame; members beyond a wall (owner
+        // OWN_OUTSIDE) leave it, obstacles keep their MAXLINK colour
+        int prev = OWN_OUTSIDE;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) prev = f[i] != OWN_OUTSIDE ? f[i] : prev;
         int gaps = 0;
 #pragma unroll
-        for (int i = 0; i < 8; ++i) gaps += f[i] != f[(i + 1) & 7] ? 1 : 0;
-        if (gaps < 3) continue;
+        for (int i = 0; i < 8; ++i)
+            if (f[i] != OWN_OUTSIDE) {
+                gaps += f[i] != prev ? 1 : 0;
+                prev = f[i];
+            }
         const int k = f[8];
+        if (gaps < 3 || k < 0) continue;
         // quarter turn q: e1 = frame entry 2q, e1 + e2 = entry 2q + 1, e2 = entry 2q + 2,
         // e1 - e2 = entry 2q - 1 (all mod 8)
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             const int c1 = f[2 * q], cd = f[2 * q + 1], c2 = f[(2 * q + 2) & 7], c3 = f[(2 * q + 7) & 7];
-            if (c1 != k && c2 != c3) vertex_link(P, D, inst, k, c1);
-            if (cd != k && c2 != c3 && c2 != c1) {
-                // plaquette centre k + (e1 + e2) / 2
+            if (c1 >= 0 && c1 != k && c2 != c3) vertex_link(P, D, inst, k, c1);
+            if (cd >= 0 && cd != k && c2 != c3 && c2 != c1) {
+                // plaquette centre k + (e1 + e2) / 2: the nearest centre among
+                // the colours at the plaquette's corners k, k+e1, k+e1+e2, k+e2
                 const int ex = (q == 0 || q == 3) ? 1 : -1, ey = (q == 0 || q == 1) ? 1 : -1;
                 long long qx = (long long)Q * x + (Q / 2) * ex, qy = (long long)Q * y + (Q / 2) * ey;
                 qx = (qx % MX + MX) % MX;
                 qy = (qy % MY + MY) % MY;
-                const int ca = owner_of_point(P.bcq[now] + D.comp_off, P.bid[now] + D.comp_off,
-                                              P.boff[now] + D.bucket_off, S.B, S.nbx, S.nby, qx, qy, MX, MY);
+                const int cand[4] = {k, c1, cd, c2};
+                int ca = -1;
+                long long bd = 0;
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const int c = cand[j];
+                    if (c < 0) continue;
+                    const int2 cc = cq[c];
+                    const long long ddx = wrap_ll((long long)cc.x - qx, MX), ddy = wrap_ll((long long)cc.y - qy, MY);
+                    const long long d = ddx * ddx + ddy * ddy;
+                    if (ca < 0 || d < bd || (d == bd && c < ca)) {
+                        bd = d;
+                        ca = c;
+                    }
+                }
                 if (ca == k || ca == cd) vertex_link(P, D, inst, k, cd);
             }
         }
     }
 }
 
+// Owners of sites beyond a wall (the second half of a bounded axis) become
+// OWN_OUTSIDE and owners of obstacle sites OWN_OBSTACLE (the paper's MAXLINK
+// colour), so that no link is read there; one warp per 32 x 32 tile.
+__global__ __launch_bounds__(32 * LINK_WARPS) void k_mask_owners(Pools P, StepTable T) {
+    pdl_enter();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int b = blockIdx.x * LINK_WARPS + warp;
+    if (b >= T.tileV_pre[T.n_act]) return;
+    const int a = seg_of_int(T.tileV_pre, T.n_act, b);
+    const int inst = T.act[a];
+    const InstDesc& D = P.desc[inst];
+    if (!D.masked) return;
+    const int t = b - T.tileV_pre[a];
+    const int tx = t % D.vtx, ty = t / D.vtx;
+    const int x = tx * VW + lane;
+    if (x >= D.Lx) return;
+    int* own = P.owners + D.site_off;
+    const unsigned* ob = P.obst + D.word_off;
+    for (int y = ty * VH; y < min(ty * VH + VH, D.Ly); ++y) {
+        int* o = own + (long long)y * D.Lx + x;
+        if (x >= D.uLx || y >= D.uLy) *o = OWN_OUTSIDE;
+        else if ((ob[(long long)y * D.wpr + (x >> 5)] >> (x & 31)) & 1u) *o = OWN_OBSTACLE;
+    }
+}
+
 void launch_links(const Launch& L) {
+    if (L.masked)
+        launch_step(L, k_mask_owners, dim3((L.total_tilesV + LINK_WARPS - 1) / LINK_WARPS), dim3(32 * LINK_WARPS),
+                    L.P, L.T);
     launch_step(L, k_links, dim3((L.total_tilesV + LINK_WARPS - 1) / LINK_WARPS), dim3(32 * LINK_WARPS), L.P, L.T);
     if (L.vertex_rule)
         launch_step(L, k_links_vertex, dim3((L.total_tilesV + LINK_WARPS - 1) / LINK_WARPS), dim3(32 * LINK_WARPS),

@@ -33,10 +33,14 @@ VD_EV_ACTIVE, VD_EV_BULK, VD_EV_BOUNDARY, VD_EV_BPOINT_NOW, VD_EV_BPOINT_PAST = 
 VD_MATCH_OVERLAP, VD_MATCH_CENTROID = 0, 1
 # link rules (Section 3.2.2)
 VD_EDGE_ADJ4, VD_EDGE_VERTEX = 0, 1
+# bounded axes and the owner of obstacle sites
+VD_WALL_X, VD_WALL_Y = 1, 2
+VD_OWNER_OBSTACLE = -2
 
 #: every symbol include/vd.h declares
 EXPORTS = (
-    "vd_config_init", "vd_create", "vd_push_frame", "vd_push_frame_host", "vd_get_changes",
+    "vd_config_init", "vd_set_obstacles", "vd_batch_set_obstacles", "vd_create", "vd_push_frame",
+    "vd_push_frame_host", "vd_get_changes",
     "vd_get_counts", "vd_get_labels", "vd_get_centroids_q10", "vd_get_owners", "vd_get_edges",
     "vd_get_match", "vd_set_timing", "vd_get_timing", "vd_stage_name", "vd_destroy", "vd_status_string",
     "vd_batch_create", "vd_batch_create_sequence", "vd_batch_push", "vd_batch_push_host", "vd_batch_push_subset", "vd_batch_get_changes",
@@ -63,7 +67,7 @@ class vd_config(C.Structure):
         ("Lx", C.c_int32), ("Ly", C.c_int32), ("threshold", C.c_float), ("polarity", C.c_int32),
         ("connectivity", C.c_int32), ("max_components", C.c_int32), ("max_edges", C.c_int32),
         ("stream", C.c_void_p), ("events", C.c_int32), ("match_rule", C.c_int32), ("match_radius", C.c_int32),
-        ("edge_rule", C.c_int32),
+        ("edge_rule", C.c_int32), ("walls", C.c_int32),
     ]
 
 
@@ -115,6 +119,8 @@ def lib():
     P, I32, I64, VP = C.POINTER, C.c_int32, C.c_int64, C.c_void_p
     sig = {
         "vd_config_init": [P(vd_config), I32, I32],
+        "vd_set_obstacles": [C.c_void_p, C.c_void_p, C.c_int64],
+        "vd_batch_set_obstacles": [C.c_void_p, I32, C.c_void_p, C.c_int64],
         "vd_create": [P(vd_config), P(VP)],
         "vd_push_frame": [VP, VP, C.c_size_t],
         "vd_push_frame_host": [VP, VP, C.c_size_t],
@@ -180,7 +186,7 @@ def _check(s: int, where: str):
 def vd_config_init(Lx: int, Ly: int, threshold: float = 0.5, polarity: int = VD_ABOVE,
                    stream: int | None = None, max_components: int = 0, max_edges: int = 0,
                    events: bool = False, match_rule: int = VD_MATCH_OVERLAP, match_radius: int = 0,
-                   connectivity: int = 4, edge_rule: int = VD_EDGE_ADJ4) -> vd_config:
+                   connectivity: int = 4, edge_rule: int = VD_EDGE_ADJ4, walls: int = 0) -> vd_config:
     cfg = vd_config()
     _check(lib().vd_config_init(C.byref(cfg), int(Lx), int(Ly)), "vd_config_init")
     cfg.threshold = float(threshold)
@@ -193,6 +199,7 @@ def vd_config_init(Lx: int, Ly: int, threshold: float = 0.5, polarity: int = VD_
     cfg.match_radius = int(match_radius)
     cfg.connectivity = int(connectivity)
     cfg.edge_rule = int(edge_rule)
+    cfg.walls = int(walls)
     return cfg
 
 
@@ -327,14 +334,20 @@ class Detector(_Base):
     def __init__(self, Lx: int, Ly: int, threshold: float = 0.5, polarity: int = VD_ABOVE,
                  stream: int | None = None, max_components: int = 0, max_edges: int = 0,
                  events: bool = False, match_rule: int = VD_MATCH_OVERLAP, match_radius: int = 0,
-                 connectivity: int = 4, edge_rule: int = VD_EDGE_ADJ4):
+                 connectivity: int = 4, edge_rule: int = VD_EDGE_ADJ4, walls: int = 0):
         if stream is None:
             import torch
             stream = torch.cuda.current_stream().cuda_stream
         self.Lx, self.Ly = Lx, Ly
         self.cfg = vd_config_init(Lx, Ly, threshold, polarity, stream, max_components, max_edges,
-                                  events, match_rule, match_radius, connectivity, edge_rule)
+                                  events, match_rule, match_radius, connectivity, edge_rule, walls)
         self.h = vd_create(self.cfg)
+
+    def set_obstacles(self, mask) -> None:
+        """mask: host array [Ly, Lx], nonzero = obstacle site (vd_set_obstacles)."""
+        import numpy as np
+        m = np.ascontiguousarray(np.asarray(mask) != 0, dtype=np.uint8)
+        _check(lib().vd_set_obstacles(self.h, m.ctypes.data, m.shape[1]), "vd_set_obstacles")
 
     def push(self, field) -> None:
         """field: torch CUDA float32 tensor [Ly, Lx] (row stride = field.stride(0))."""
@@ -408,13 +421,13 @@ class Batch(_Base):
     def __init__(self, sizes, threshold: float = 0.5, polarity: int = VD_ABOVE, stream: int | None = None,
                  max_components: int = 0, sequence: int = 0, events: bool = False,
                  match_rule: int = VD_MATCH_OVERLAP, match_radius: int = 0, connectivity: int = 4,
-                 edge_rule: int = VD_EDGE_ADJ4):
+                 edge_rule: int = VD_EDGE_ADJ4, walls: int = 0):
         if stream is None:
             import torch
             stream = torch.cuda.current_stream().cuda_stream
         self.sizes = [(int(lx), int(ly)) for lx, ly in sizes]
         opts = dict(events=events, match_rule=match_rule, match_radius=match_radius, connectivity=connectivity,
-                    edge_rule=edge_rule)
+                    edge_rule=edge_rule, walls=walls)
         if sequence:
             lx, ly = self.sizes[0]
             self.sizes = [(lx, ly)] * int(sequence)

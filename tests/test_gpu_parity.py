@@ -68,14 +68,19 @@ def check_frame(det, r, what=("labels", "centroids", "owners", "edges", "changes
 
 
 def run_pair(frames, threshold=0.5, polarity=1, voronoi="kdtree", what=None, tag="", events=False,
-             match="overlap", match_radius=0, connectivity=4, edge_rule="adj4"):
+             match="overlap", match_radius=0, connectivity=4, edge_rule="adj4", walls=(False, False),
+             obstacles=None):
     Ly, Lx = frames[0].shape
     det = vd.Detector(Lx, Ly, threshold=threshold, polarity=polarity, events=events,
                       match_rule=vd.VD_MATCH_CENTROID if match == "centroid" else vd.VD_MATCH_OVERLAP,
                       match_radius=match_radius, connectivity=connectivity,
-                      edge_rule=vd.VD_EDGE_VERTEX if edge_rule == "vertex" else vd.VD_EDGE_ADJ4)
+                      edge_rule=vd.VD_EDGE_VERTEX if edge_rule == "vertex" else vd.VD_EDGE_ADJ4,
+                      walls=(vd.VD_WALL_X if walls[0] else 0) | (vd.VD_WALL_Y if walls[1] else 0))
+    if obstacles is not None:
+        det.set_obstacles(obstacles)
     ref = O.Detector(Lx, Ly, theta=threshold, polarity=polarity, voronoi=voronoi, workers=-1, events=events,
-                     match=match, match_radius=match_radius, connectivity=connectivity, edge_rule=edge_rule)
+                     match=match, match_radius=match_radius, connectivity=connectivity, edge_rule=edge_rule,
+                     walls=walls, obstacles=obstacles)
     for f, F in enumerate(frames):
         det.push(torch.from_numpy(np.ascontiguousarray(F)).cuda())
         r = ref.push(F)
@@ -314,3 +319,26 @@ def test_vertex_link_rule_c1_frames():
     frames = list(I.workload_c1(seed=4, n_frames=3))
     r = run_pair(frames, tag="c1 vertex", edge_rule="vertex")
     assert r["K"] > 300
+
+
+@pytest.mark.parametrize("walls", [(True, False), (False, True), (True, True)])
+def test_walls_and_obstacles(walls):
+    """Bounded axes (the paper's channel) with posts along one wall: labels,
+    centres, owners (obstacles = VD_OWNER_OBSTACLE), links of both rules,
+    the centre match and the event flags equal the oracle's, on lattices
+    ragged against the tiles."""
+    rng = np.random.default_rng(700 + walls[0] + 2 * walls[1])
+    for trial in range(3):
+        Lx = int(rng.integers(20, 200))
+        Ly = int(rng.integers(20, 150))
+        F0 = I.smoothed_noise(Ly, Lx, float(rng.uniform(1.5, 3.5)), seed=trial + 7)
+        F1 = I.shear_resample(F0, 0.03, 0.02, np.random.default_rng(trial))
+        obst = np.zeros((Ly, Lx), dtype=bool)
+        for y0 in range(2, Ly - 4, 12):          # posts on the left wall
+            obst[y0:y0 + 4, 0:3] = True
+        if trial == 1:
+            obst |= rng.random((Ly, Lx)) < 0.01  # and scattered obstacle sites
+        tag = f"walls {walls} {Lx}x{Ly} t{trial}"
+        run_pair([F0, F1], voronoi="brute", tag=tag, walls=walls, obstacles=obst if trial else None, events=True)
+        run_pair([F0, F1], voronoi="brute", tag=tag + " vertex", walls=walls, obstacles=obst, edge_rule="vertex",
+                 match="centroid", match_radius=6, events=True)
