@@ -56,12 +56,11 @@ struct DevBuf {
 
 struct StepTables {
     int n_act = 0;
-    int total_tilesA = 0, total_tilesV = 0, total_merge = 0;
+    int total_tilesA = 0, total_tilesV = 0;
     long long total_groups = 0;
     int* d_act = nullptr;
     int* d_tileA = nullptr;
     int* d_tileV = nullptr;
-    int* d_merge = nullptr;
     long long* d_groups = nullptr;
     long long* d_pre = nullptr;
 };
@@ -164,20 +163,18 @@ bool valid_cfg(const vd_config& c) {
 
 void build_table(vd_batch* b, const std::vector<int>& act, StepTables& T, bool alloc) {
     const int n = (int)act.size();
-    std::vector<int> tA(n + 1, 0), tV(n + 1, 0), mg(n + 1, 0);
+    std::vector<int> tA(n + 1, 0), tV(n + 1, 0);
     std::vector<long long> wd(n + 1, 0);
     for (int a = 0; a < n; ++a) {
         const InstDesc& D = b->desc[act[a]];
         tA[a + 1] = tA[a] + D.ntx * D.nty;
         tV[a + 1] = tV[a] + D.vtx * D.vty;
-        mg[a + 1] = mg[a] + D.ntx * D.nty * (TW + TH);
         wd[a + 1] = wd[a] + (long long)D.Ly * D.gpr;
     }
     if (alloc) {
         T.d_act = b->mem.alloc<int>(b->n);
         T.d_tileA = b->mem.alloc<int>(b->n + 1);
         T.d_tileV = b->mem.alloc<int>(b->n + 1);
-        T.d_merge = b->mem.alloc<int>(b->n + 1);
         T.d_groups = b->mem.alloc<long long>(b->n + 1);
         T.d_pre = b->mem.alloc<long long>((long long)NPRE * (b->n + 1));
         if (!b->mem.ok) return;
@@ -185,12 +182,10 @@ void build_table(vd_batch* b, const std::vector<int>& act, StepTables& T, bool a
     T.n_act = n;
     T.total_tilesA = tA[n];
     T.total_tilesV = tV[n];
-    T.total_merge = mg[n];
     T.total_groups = wd[n];
     cudaMemcpyAsync(T.d_act, act.data(), sizeof(int) * n, cudaMemcpyHostToDevice, b->s);
     cudaMemcpyAsync(T.d_tileA, tA.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice, b->s);
     cudaMemcpyAsync(T.d_tileV, tV.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice, b->s);
-    cudaMemcpyAsync(T.d_merge, mg.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice, b->s);
     cudaMemcpyAsync(T.d_groups, wd.data(), sizeof(long long) * (n + 1), cudaMemcpyHostToDevice, b->s);
 }
 
@@ -206,7 +201,6 @@ Launch make_launch(vd_batch* b, const StepTables& T) {
     L.T.tileA_pre = T.d_tileA;
     L.T.tileV_pre = T.d_tileV;
     L.T.grp_pre = T.d_groups;
-    L.T.merge_pre = T.d_merge;
     L.T.pre = T.d_pre;
     L.grid_items = b->grid_items;
     L.events = b->any_events;
@@ -216,7 +210,6 @@ Launch make_launch(vd_batch* b, const StepTables& T) {
     L.grid_wide = 4 * b->grid_items;
     L.total_tilesA = T.total_tilesA;
     L.total_tilesV = T.total_tilesV;
-    L.total_merge = T.total_merge;
     L.total_groups = T.total_groups;
     return L;
 }

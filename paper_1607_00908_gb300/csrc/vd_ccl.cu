@@ -419,73 +419,77 @@ __device__ __forceinline__ void punion(const Pools& P, int a, int b) {
     }
 }
 
-// one thread per border position (right edge, then bottom edge of every
-// tile); a position whose piece pair equals the previous position's on the
-// same edge adds nothing and is skipped. With 8-connectivity a position also
-// joins the diagonal neighbours across its edge (the next row / column), and
-// the right edge's first and last rows join across the tile corners.
-__global__ void k_ccl_merge(Pools P, StepTable T, int total) {
+// One warp per labelling tile: lane j joins row j of the tile's right edge
+// with the left edge of the tile to its right, and columns j and 32 + j of
+// its bottom edge with the top edge of the tile below (both periodic). A
+// position whose piece pair equals the previous position's on the same edge
+// adds nothing and is skipped. With 8-connectivity a position also joins the
+// diagonal neighbours across its edge (the next row / column), and the right
+// edge's first and last rows join across the tile corners.
+constexpr int MERGE_WARPS = 8;
+
+__global__ __launch_bounds__(32 * MERGE_WARPS) void k_ccl_merge(Pools P, StepTable T) {
     pdl_enter();
     __shared__ int s_pre[SEG_CACHE];
-    const int* pre = seg_table(T.merge_pre, T.n_act, s_pre);
-    const int g = blockIdx.x * blockDim.x + threadIdx.x;
-    int pa = -1, pb = -1, edge = -1;   // edge: (tile, side) of this position
-    int da[4] = {-1, -1, -1, -1}, db[4] = {-1, -1, -1, -1};   // diagonal pairs (8-connectivity)
-    if (g < total) {
-        const int a = seg_of_int(pre, T.n_act, g);
-        const int inst = T.act[a];
-        const InstDesc& D = P.desc[inst];
-        const int loc = g - pre[a];
-        const int t = loc / (TW + TH), j = loc % (TW + TH);
-        const int tx = t % D.ntx, ty = t / D.ntx;
-        const int* bd = P.border + D.border_off;
-        const int nrows = min(TH, D.Ly - ty * TH), ncols = min(TW, D.Lx - tx * TW);
-        if (j < TH) {
-            const int tn = ty * D.ntx + (tx + 1) % D.ntx;
-            pa = bd[(long long)t * BORDER + TH + j];
-            pb = bd[(long long)tn * BORDER + j];
-            if (D.conn8) {
-                if (j + 1 < nrows) {
-                    da[0] = pa;
-                    db[0] = bd[(long long)tn * BORDER + j + 1];
-                    da[1] = bd[(long long)t * BORDER + TH + j + 1];
-                    db[1] = pb;
-                }
-                if (j == nrows - 1) {   // bottom-right corner: top-left site of the tile below-right
-                    const int tc = ((ty + 1) % D.nty) * D.ntx + (tx + 1) % D.ntx;
-                    da[2] = pa;
-                    db[2] = bd[(long long)tc * BORDER + 0];
-                }
-                if (j == 0) {           // top-right corner: bottom-left site of the tile above-right
-                    const int tyu = (ty + D.nty - 1) % D.nty;
-                    const int tc = tyu * D.ntx + (tx + 1) % D.ntx;
-                    const int nru = min(TH, D.Ly - tyu * TH);
-                    da[3] = pa;
-                    db[3] = bd[(long long)tc * BORDER + nru - 1];
-                }
+    const int* tpre = seg_table(T.tileA_pre, T.n_act, s_pre);
+    const int lane = threadIdx.x & 31;
+    const int b = blockIdx.x * MERGE_WARPS + (threadIdx.x >> 5);
+    if (b >= tpre[T.n_act]) return;
+    const int a = seg_of_int(tpre, T.n_act, b);
+    const InstDesc& D = P.desc[T.act[a]];
+    const int t = b - tpre[a];
+    const int tx = t % D.ntx, ty = t / D.ntx;
+    const int* bd = P.border + D.border_off;
+    const int* bt = bd + (long long)t * BORDER;
+    const int* br = bd + (long long)(ty * D.ntx + (tx + 1) % D.ntx) * BORDER;      // tile to the right
+    const int* bb = bd + (long long)(((ty + 1) % D.nty) * D.ntx + tx) * BORDER;    // tile below
+    const int nrows = min(TH, D.Ly - ty * TH), ncols = min(TW, D.Lx - tx * TW);
+    const bool c8 = D.conn8 != 0;
+
+    // right edge: row `lane`
+    {
+        const int pa = bt[TH + lane], pb = br[lane];
+        const int ppa = __shfl_up_sync(0xffffffffu, pa, 1), ppb = __shfl_up_sync(0xffffffffu, pb, 1);
+        if (pa >= 0 && pb >= 0 && !(lane > 0 && ppa == pa && ppb == pb)) punion(P, pa, pb);
+        if (c8) {
+            if (lane + 1 < nrows) {
+                const int qa = bt[TH + lane + 1], qb = br[lane + 1];
+                if (pa >= 0 && qb >= 0 && pa != qb) punion(P, pa, qb);
+                if (qa >= 0 && pb >= 0 && qa != pb) punion(P, qa, pb);
             }
-        } else {
-            const int k = j - TH;
-            const int tn = ((ty + 1) % D.nty) * D.ntx + tx;
-            pa = bd[(long long)t * BORDER + 2 * TH + TW + k];
-            pb = bd[(long long)tn * BORDER + 2 * TH + k];
-            if (D.conn8 && k + 1 < ncols) {
-                da[0] = pa;
-                db[0] = bd[(long long)tn * BORDER + 2 * TH + k + 1];
-                da[1] = bd[(long long)t * BORDER + 2 * TH + TW + k + 1];
-                db[1] = pb;
+            if (lane == nrows - 1 && pa >= 0) {   // bottom-right corner: top-left site of the tile below-right
+                const int v = bd[(long long)(((ty + 1) % D.nty) * D.ntx + (tx + 1) % D.ntx) * BORDER + 0];
+                if (v >= 0 && v != pa) punion(P, pa, v);
+            }
+            if (lane == 0 && pa >= 0) {           // top-right corner: bottom-left site of the tile above-right
+                const int tyu = (ty + D.nty - 1) % D.nty;
+                const int nru = min(TH, D.Ly - tyu * TH);
+                const int v = bd[(long long)(tyu * D.ntx + (tx + 1) % D.ntx) * BORDER + nru - 1];
+                if (v >= 0 && v != pa) punion(P, pa, v);
             }
         }
-        edge = (g - j) * 2 + (j < TH ? 0 : 1);
     }
-    const int lane = threadIdx.x & 31;
-    const int ppa = __shfl_up_sync(0xffffffffu, pa, 1), ppb = __shfl_up_sync(0xffffffffu, pb, 1);
-    const int pedge = __shfl_up_sync(0xffffffffu, edge, 1);
-    const bool repeat = lane > 0 && pedge == edge && ppa == pa && ppb == pb;
-    if (pa >= 0 && pb >= 0 && !repeat) punion(P, pa, pb);
+    // bottom edge: columns `lane` and 32 + `lane`
+    int lpa = -1, lpb = -1;   // pair of column 31, carried to column 32
 #pragma unroll
-    for (int q = 0; q < 4; ++q)
-        if (da[q] >= 0 && db[q] >= 0 && da[q] != db[q]) punion(P, da[q], db[q]);
+    for (int h = 0; h < 2; ++h) {
+        const int k = 32 * h + lane;
+        const int pa = bt[2 * TH + TW + k], pb = bb[2 * TH + k];
+        int ppa = __shfl_up_sync(0xffffffffu, pa, 1), ppb = __shfl_up_sync(0xffffffffu, pb, 1);
+        if (lane == 0) {
+            ppa = lpa;
+            ppb = lpb;
+        }
+        const bool repeat = (k > 0) && ppa == pa && ppb == pb;
+        if (pa >= 0 && pb >= 0 && !repeat) punion(P, pa, pb);
+        if (c8 && k + 1 < ncols) {
+            const int qa = bt[2 * TH + TW + k + 1], qb = bb[2 * TH + k + 1];
+            if (pa >= 0 && qb >= 0 && pa != qb) punion(P, pa, qb);
+            if (qa >= 0 && pb >= 0 && qa != pb) punion(P, qa, pb);
+        }
+        lpa = __shfl_sync(0xffffffffu, pa, 31);
+        lpb = __shfl_sync(0xffffffffu, pb, 31);
+    }
 }
 
 // root of each piece; roots are counted per instance and marked in the root bitmap
@@ -665,7 +669,7 @@ __global__ void k_bucket_scatter(Pools P) {
 // previous frame's labels (Section 3.2.3)
 // ---------------------------------------------------------------------------
 constexpr int LBL_WARPS = 4;    // tiles per block in the label pass
-constexpr int WSET = 128;       // per-warp overlap set
+constexpr int WSET = 64;        // per-warp overlap set (power of two)
 
 // ---------------------------------------------------------------------------
 // Run labels and the overlap histogram (Sections 3.1 and 3.2.3), one warp per
@@ -676,7 +680,7 @@ constexpr int WSET = 128;       // per-warp overlap set
 // inside one past run and one now run, so the overlap histogram is a sum of
 // run lengths over (past label, now label) pairs and no site is visited.
 // ---------------------------------------------------------------------------
-__global__ __launch_bounds__(32 * LBL_WARPS) void k_run_labels(Pools P, StepTable T) {
+__global__ __launch_bounds__(32 * LBL_WARPS, 10) void k_run_labels(Pools P, StepTable T) {
     pdl_enter();
     __shared__ int s_lab[LBL_WARPS][RUNS];
     __shared__ unsigned long long s_key[LBL_WARPS][WSET];
@@ -816,9 +820,9 @@ void launch_ccl_tiles(const Launch& L) {
 }
 
 void launch_ccl_rest(const Launch& L) {
-    if (L.total_merge > 0) {
-        launch_step(L, k_ccl_merge, dim3((L.total_merge + 255) / 256), dim3(256), L.P, L.T, L.total_merge);
-    }
+    if (L.total_tilesA > 0)
+        launch_step(L, k_ccl_merge, dim3((L.total_tilesA + MERGE_WARPS - 1) / MERGE_WARPS), dim3(32 * MERGE_WARPS), L.P,
+                    L.T);
     launch_step(L, k_ccl_flatten, dim3(L.grid_wide), dim3(256), L.P);
     launch_plan(L, 1, ends_bit(SCAN_BUCKETS));
     launch_scan(L, SCAN_ROOTBITS);

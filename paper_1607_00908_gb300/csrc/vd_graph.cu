@@ -287,10 +287,22 @@ __device__ int nearest_centre(const CentreGrid& G, int2 q, int Lx, int Ly, int r
     if (ny >= G.nby) { y0 = 0; ny = G.nby; }
     int best = -1;
     long long bd = R2;
+    // smallest distance along one axis from q to the centres of a bucket
+    // (an arc of the ring): 0 inside it, else the nearer end
+    auto gap = [&](int bi, int qv, long long M) -> long long {
+        const long long lo = (long long)bi * G.B * Q, hi = min((long long)(bi + 1) * G.B * Q, M) - 1;
+        if (qv >= lo && qv <= hi) return 0;
+        const long long a = wrap_ll(lo - qv, M), c = wrap_ll(hi - qv, M);
+        return min(a < 0 ? -a : a, c < 0 ? -c : c);
+    };
     for (int iy = 0; iy < ny; ++iy) {
         const int by = ((y0 + iy) % G.nby + G.nby) % G.nby;
+        const long long gy = gap(by, q.y, MY);
+        if (gy * gy > R2) continue;
         for (int ix = 0; ix < nx; ++ix) {
             const int bx = ((x0 + ix) % G.nbx + G.nbx) % G.nbx;
+            const long long gx = gap(bx, q.x, MX);
+            if (gx * gx + gy * gy > R2) continue;   // no centre of the bucket is within the radius
             const int b = by * G.nbx + bx;
             for (int k = G.boff[b]; k < G.boff[b + 1]; ++k) {
                 const int2 c = G.bcq[k];

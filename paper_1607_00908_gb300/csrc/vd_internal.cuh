@@ -231,7 +231,6 @@ struct StepTable {
     const int* tileA_pre;        // prefix of labelling tiles over act (n_act+1)
     const int* tileV_pre;        // prefix of Voronoi tiles
     const long long* grp_pre;    // prefix of root groups
-    const int* merge_pre;        // prefix of merge threads (tiles * (TW+TH))
     // device-computed prefixes over act (n_act+1 each), filled by k_plan
     long long* pre;              // NPRE arrays back to back
 };
@@ -446,7 +445,7 @@ struct Launch {
     Pools P;
     StepTable T;
     int grid_items;      // fixed grid for grid-stride item loops
-    int total_tilesA, total_tilesV, total_merge;
+    int total_tilesA, total_tilesV;
     long long total_groups;
     int grid_wide;               // blocks for kernels with one thread per item (pieces, bubbles, links)
 };

@@ -21,8 +21,6 @@
 // each label's degree.
 #include "vd_internal.cuh"
 
-#include <type_traits>
-
 namespace vd {
 
 // distance from a point (offset d of the point from the interval start, already
@@ -465,10 +463,14 @@ constexpr int LSET = 256;       // per-warp key list
 constexpr int LS = VW + 4;      // staged row stride (rows start on 16 bytes)
 
 // slot `pos` of a warp's key list; past its end the key goes to the hash
-__device__ __forceinline__ void link_list_put(unsigned long long* list, int pos, unsigned long long key,
-                                              const Pools& P, const InstDesc& D, int inst) {
-    if (pos < LSET) list[pos] = key;
-    else edge_global_insert(P, D, inst, key);
+// list entry `pos` of a warp's keys: the link {a, b}, or EMPTY_KEY when an
+// end is not a label (obstacle, beyond a wall); past the list, straight into
+// the link hash
+__device__ __forceinline__ void link_list_put(unsigned long long* list, int pos, int a, int b, const Pools& P,
+                                              const InstDesc& D, int inst) {
+    const bool ok = (a | b) >= 0;
+    if (pos < LSET) list[pos] = ok ? edge_key(a, b) : EMPTY_KEY;
+    else if (ok) edge_global_insert(P, D, inst, edge_key(a, b));
 }
 
 __device__ __forceinline__ void cp_async4(int* smem, const int* gmem) {
@@ -534,47 +536,44 @@ __global__ __launch_bounds__(32 * LINK_WARPS) void k_links(Pools P, StepTable T)
     const bool valid = lane < ncols;
     const int l = min(lane, ncols - 1);
     const unsigned lt = (1u << lane) - 1u;
+    int o = S[l], rt = S[l + 1];
+    int up = 0, upr = 0;
+    int lf = __shfl_up_sync(0xffffffffu, o, 1);
     int n = 0;   // keys in the warp's list (warp-uniform)
-    // the row loop in two copies: with walls or obstacles negative owners
-    // (obstacles, beyond a wall) are never linked; without them every owner
-    // is a label and the tests are left out
-    auto rows = [&](auto masked) {
-        constexpr bool MK = decltype(masked)::value;
-        int o = S[l], rt = S[l + 1];
-        int up = 0, upr = 0;
-        int lf = __shfl_up_sync(0xffffffffu, o, 1);
-        for (int r = 0; r < nrows; ++r) {
-            const int dn = S[(r + 1) * LS + l];
-            const int dg = S[(r + 1) * LS + l + 1];
-            const int dlf = __shfl_up_sync(0xffffffffu, dn, 1);
-            const bool eh = valid && o != rt && (!MK || (o >= 0 && rt >= 0)) &&
-                            !(r > 0 && (up == rt || upr == o || (up == o && upr == rt)));
-            const bool ev = valid && o != dn && rt != dn && (!MK || (o >= 0 && dn >= 0)) &&
-                            !(lane > 0 && (lf == dn || (lf == o && dlf == dn)));
-            const bool ep = valid && o != rt && o != dn && o != dg && rt != dn && rt != dg && dn != dg &&
-                            (!MK || (o >= 0 && rt >= 0 && dn >= 0 && dg >= 0));
-            const unsigned mh = __ballot_sync(0xffffffffu, eh);
-            const unsigned mv = __ballot_sync(0xffffffffu, ev);
-            const unsigned mp = __ballot_sync(0xffffffffu, ep);
-            if (mh | mv | mp) {
-                // append this row's keys: horizontal, vertical, then plaquettes
-                const int nh = __popc(mh), nv = __popc(mv);
-                if (eh) link_list_put(list, n + __popc(mh & lt), edge_key(o, rt), P, D, inst);
-                if (ev) link_list_put(list, n + nh + __popc(mv & lt), edge_key(o, dn), P, D, inst);
-                if (ep)
-                    link_list_put(list, n + nh + nv + __popc(mp & lt), plaquette_key(o, rt, dg, dn, cq, MX, MY), P,
-                                  D, inst);
-                n += nh + nv + __popc(mp);
+    for (int r = 0; r < nrows; ++r) {
+        const int dn = S[(r + 1) * LS + l];
+        const int dg = S[(r + 1) * LS + l + 1];
+        const int dlf = __shfl_up_sync(0xffffffffu, dn, 1);
+        // a pair with a negative owner (obstacle, beyond a wall) is dropped when
+        // its key is listed, a plaquette with one before its centres are read
+        const bool eh = valid && o != rt && !(r > 0 && (up == rt || upr == o || (up == o && upr == rt)));
+        const bool ev = valid && o != dn && rt != dn && !(lane > 0 && (lf == dn || (lf == o && dlf == dn)));
+        const bool ep = valid && o != rt && o != dn && o != dg && rt != dn && rt != dg && dn != dg;
+        const unsigned mh = __ballot_sync(0xffffffffu, eh);
+        const unsigned mv = __ballot_sync(0xffffffffu, ev);
+        const unsigned mp = __ballot_sync(0xffffffffu, ep);
+        if (mh | mv | mp) {
+            // append this row's keys: horizontal, vertical, then plaquettes
+            const int nh = __popc(mh), nv = __popc(mv);
+            if (eh) link_list_put(list, n + __popc(mh & lt), o, rt, P, D, inst);
+            if (ev) link_list_put(list, n + nh + __popc(mv & lt), o, dn, P, D, inst);
+            if (ep) {
+                int pa = -1, pb = -1;
+                if ((o | rt | dn | dg) >= 0) {
+                    const unsigned long long pk = plaquette_key(o, rt, dg, dn, cq, MX, MY);
+                    pa = (int)(pk >> 32);
+                    pb = (int)(pk & 0xffffffffu);
+                }
+                link_list_put(list, n + nh + nv + __popc(mp & lt), pa, pb, P, D, inst);
             }
-            up = o;
-            upr = rt;
-            o = dn;
-            rt = dg;
-            lf = dlf;
+            n += nh + nv + __popc(mp);
         }
-    };
-    if (D.masked) rows(std::true_type{});
-    else rows(std::false_type{});
+        up = o;
+        upr = rt;
+        o = dn;
+        rt = dg;
+        lf = dlf;
+    }
     __syncwarp();
     // equal keys within a round of 32 are merged; the tile's keys are
     // appended to the instance's link list (the link hash removes the rest)
@@ -583,7 +582,7 @@ __global__ __launch_bounds__(32 * LINK_WARPS) void k_links(Pools P, StepTable T)
         const bool in = kb + lane < n;
         const unsigned long long key = in ? list[kb + lane] : EMPTY_KEY;
         const unsigned grp = __match_any_sync(0xffffffffu, key);
-        const bool has = in && lane == __ffs(grp) - 1;
+        const bool has = in && key != EMPTY_KEY && lane == __ffs(grp) - 1;
         const unsigned m = __ballot_sync(0xffffffffu, has);
         if (!m) continue;
         int base = 0;
