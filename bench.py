@@ -51,7 +51,7 @@ METRIC_BYTES_PER_SITE = 16.0
 # (profiles/launches_c1_sequence.txt); scaled to the bench launch for
 # roofline.traffic. A stage not captured, or whose kernels changed since the
 # capture, reports null.
-TRAFFIC_BYTES_PER_SITE = {0: 5.100, 2: 2.845, 3: 3.422, 4: 4.326}
+TRAFFIC_BYTES_PER_SITE = {0: 5.071, 2: 2.856, 3: 3.418, 4: 4.325}
 
 
 def workload(name: str, n_frames: int | None):

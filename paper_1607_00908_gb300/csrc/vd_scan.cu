@@ -20,8 +20,9 @@ constexpr int PLAN_THREADS = 256;
 
 __global__ __launch_bounds__(PLAN_THREADS) void k_plan(Pools P, StepTable T, int with_comp, int ends, int pre_mask) {
     pdl_enter();
-    // one block: thread per instance, block scans for the prefixes
-    __shared__ long long s_v[NPRE][PLAN_THREADS];
+    // one block: thread per instance, block scans for the prefixes (warp
+    // scans by shuffles, then the warp totals)
+    __shared__ long long s_w[NPRE][PLAN_THREADS / 32];
     __shared__ long long s_carry[NPRE];
     const int n = T.n_act;
     const int tid = threadIdx.x;
@@ -84,21 +85,29 @@ __global__ __launch_bounds__(PLAN_THREADS) void k_plan(Pools P, StepTable T, int
             if (ends & ends_bit(SCAN_FLIPS)) P.foff[D.comp_off + S.K] = S.n_break;
             if (ends & ends_bit(SCAN_FLIPS_A)) P.foff_a[D.comp_off + S.K] = S.n_arise;
         }
-        for (int k = 0; k < NPRE; ++k) s_v[k][tid] = v[k];
-        __syncthreads();
-        // inclusive scans (Hillis-Steele) of every array
-        for (int o = 1; o < PLAN_THREADS; o <<= 1) {
-            long long add[NPRE];
-            for (int k = 0; k < NPRE; ++k) add[k] = tid >= o ? s_v[k][tid - o] : 0;
-            __syncthreads();
-            for (int k = 0; k < NPRE; ++k) s_v[k][tid] += add[k];
-            __syncthreads();
+        const int lane = tid & 31, wid = tid >> 5;
+        long long inc[NPRE];
+#pragma unroll
+        for (int k = 0; k < NPRE; ++k) {
+            long long x = v[k];
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const long long y = __shfl_up_sync(0xffffffffu, x, o);
+                if (lane >= o) x += y;
+            }
+            inc[k] = x;
+            if (lane == 31) s_w[k][wid] = x;
         }
-        if (a < n)
-            for (int k = 0; k < NPRE; ++k)
-                if (pre_mask & pre_bit(k)) pre_arr(T, k)[a] = s_carry[k] + s_v[k][tid] - v[k];
         __syncthreads();
-        if (tid < NPRE) s_carry[tid] += s_v[tid][PLAN_THREADS - 1];
+        if (a < n)
+            for (int k = 0; k < NPRE; ++k) {
+                long long before = s_carry[k];
+                for (int w = 0; w < wid; ++w) before += s_w[k][w];
+                if (pre_mask & pre_bit(k)) pre_arr(T, k)[a] = before + inc[k] - v[k];
+            }
+        __syncthreads();
+        if (tid < NPRE)
+            for (int w = 0; w < PLAN_THREADS / 32; ++w) s_carry[tid] += s_w[tid][w];
         __syncthreads();
     }
     if (tid < NPRE && (pre_mask & pre_bit(tid))) pre_arr(T, tid)[n] = s_carry[tid];
