@@ -421,7 +421,11 @@ class Batch(_Base):
     def __init__(self, sizes, threshold: float = 0.5, polarity: int = VD_ABOVE, stream: int | None = None,
                  max_components: int = 0, sequence: int = 0, events: bool = False,
                  match_rule: int = VD_MATCH_OVERLAP, match_radius: int = 0, connectivity: int = 4,
-                 edge_rule: int = VD_EDGE_ADJ4, walls: int = 0):
+                 edge_rule: int = VD_EDGE_ADJ4, walls: int = 0, options=None):
+        """``options``: optional list of per-instance dicts of config options
+        (events, match_rule, match_radius, connectivity, edge_rule, walls) for
+        an independent batch; they replace the keyword defaults instance by
+        instance."""
         if stream is None:
             import torch
             stream = torch.cuda.current_stream().cuda_stream
@@ -436,12 +440,19 @@ class Batch(_Base):
             _check(lib().vd_batch_create_sequence(C.byref(cfg), int(sequence), C.byref(h)), "vd_batch_create_sequence")
             self.h = h
         else:
-            cfgs = [vd_config_init(lx, ly, threshold, polarity, stream, max_components, **opts)
-                    for lx, ly in self.sizes]
+            per = options or [{}] * len(self.sizes)
+            cfgs = [vd_config_init(lx, ly, threshold, polarity, stream, max_components, **{**opts, **o})
+                    for (lx, ly), o in zip(self.sizes, per)]
             self.h = vd_batch_create(cfgs)
 
     def push(self, fields) -> None:
         _check(vd_batch_push(self.h, [f.data_ptr() for f in fields]), "vd_batch_push")
+
+    def set_obstacles(self, i: int, mask) -> None:
+        """mask: host array [Ly, Lx] of instance i, nonzero = obstacle site."""
+        import numpy as np
+        m = np.ascontiguousarray(np.asarray(mask) != 0, dtype=np.uint8)
+        _check(lib().vd_batch_set_obstacles(self.h, int(i), m.ctypes.data, m.shape[1]), "vd_batch_set_obstacles")
 
     def push_host_ptrs(self, host_ptrs) -> None:
         arr = (C.c_void_p * len(host_ptrs))(*[C.c_void_p(p) for p in host_ptrs])

@@ -207,3 +207,42 @@ def test_batch_with_degenerate_instances():
         for i, ref in enumerate(refs):
             check(b, i, ref.push(seqs[i][f]), f"inst {i} frame {f}")
     b.close()
+
+
+
+def test_batch_with_mixed_options():
+    """One independent batch whose instances differ in every option (event
+    classes, centre match, 8-connectivity, the vertex link rule, walls and
+    obstacles): each instance's changes equal the oracle run with its own
+    options, so the per-instance switches of the shared launches hold."""
+    L = 96
+    opts = [
+        dict(),
+        dict(events=True),
+        dict(events=True, match_rule=vd.VD_MATCH_CENTROID, match_radius=5),
+        dict(connectivity=8),
+        dict(edge_rule=vd.VD_EDGE_VERTEX, events=True),
+        dict(walls=vd.VD_WALL_X | vd.VD_WALL_Y, events=True),
+    ]
+    ref_opts = [
+        dict(),
+        dict(events=True),
+        dict(events=True, match="centroid", match_radius=5),
+        dict(connectivity=8),
+        dict(edge_rule="vertex", events=True),
+        dict(walls=(True, True), events=True),
+    ]
+    n = len(opts)
+    seqs = [list(I.noise_frames(L, 2.5 + 0.3 * i, 3, 0.02, 40 + i)) for i in range(n)]
+    obst = np.zeros((L, L), dtype=bool)
+    obst[10:20, 0:3] = True
+    b = vd.Batch([(L, L)] * n, options=opts)
+    b.set_obstacles(5, obst)
+    refs = [O.Detector(L, L, voronoi="brute", obstacles=obst if i == 5 else None, **ref_opts[i]) for i in range(n)]
+    for f in range(3):
+        dev = [torch.from_numpy(np.ascontiguousarray(seqs[i][f])).cuda() for i in range(n)]
+        b.push(dev)
+        for i in range(n):
+            r = refs[i].push(seqs[i][f])
+            check(b, i, r, f"mixed inst {i} frame {f}")
+    b.close()
