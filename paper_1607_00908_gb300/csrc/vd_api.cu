@@ -4,8 +4,12 @@
 // pooled device buffers laid out by instance (InstDesc offsets), a step table
 // per active set, and enqueue the same kernel sequence on their stream:
 //   begin -> labelling tiles -> border merge -> roots/ranks -> centroids ->
-//   bucket grid -> labels + overlap -> Voronoi + links -> CSR -> match ->
-//   translation -> row comparison -> finish.
+//   bucket grid -> labels + overlap -> Voronoi -> (owner marks) -> links ->
+//   CSR of both link directions -> match -> translation + row comparison ->
+//   flip lists -> (event classes) -> finish.
+// Launches in parentheses run only when some instance of the batch uses the
+// option (walls or obstacles, event classes; likewise the centre match and the
+// vertex link rule).
 // The batch form captures that sequence once into a CUDA graph per active set
 // size and replays it.
 #include <cuda_runtime.h>

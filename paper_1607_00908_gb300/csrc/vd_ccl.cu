@@ -10,7 +10,8 @@
 // four tile borders. Pieces are then merged across tile borders (periodic) by
 // a global union-find whose root is the piece with the smallest first site, so
 // the root of every bubble is the bubble's smallest linear index; bubble ids
-// are the ranks of those roots (a scan over a root bitmap). Labels are kept
+// are the ranks of those roots (a scan of root counts per 256-site group of a
+// row, then the root bits before each root in its group). Labels are kept
 // per run (a 64-site tile row holds at most 32 runs): pass A records each
 // run's piece, the run-label pass turns pieces into bubble ids, and per-site
 // labels are expanded from the foreground bits and run labels on request.
