@@ -462,7 +462,6 @@ constexpr int LINK_WARPS = 4;
 constexpr int LSET = 256;       // per-warp key list
 constexpr int LS = VW + 4;      // staged row stride (rows start on 16 bytes)
 
-// slot `pos` of a warp's key list; past its end the key goes to the hash
 // list entry `pos` of a warp's keys: the link {a, b}, or EMPTY_KEY when an
 // end is not a label (obstacle, beyond a wall); past the list, straight into
 // the link hash
