@@ -141,14 +141,41 @@ def dist_setup():
     return world, rank, local
 
 
-def max_over_ranks(x: float, world: int) -> float:
+def init_ranks(world: int, local: int, backend: str | None = None) -> None:
+    """One process per GPU under torchrun: replicas that exchange only timings
+    and unit counts (NCCL on GPUs, gloo on the host)."""
+    if world <= 1:
+        return
+    import torch
+    import torch.distributed as dist
+    if backend is None:
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+    if backend == "nccl":
+        torch.cuda.set_device(local)
+    if not dist.is_initialized():
+        dist.init_process_group(backend)
+
+
+def _reduce_over_ranks(x: float, world: int, op_name: str) -> float:
+    """All-reduce of one host number over the ranks (replicas only exchange
+    their timings and unit counts, never data of the path). The tensor lives
+    where the process group's backend wants it: CUDA for NCCL, host for gloo."""
     if world == 1:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
-    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=getattr(dist.ReduceOp, op_name))
     return float(t.item())
+
+
+def max_over_ranks(x: float, world: int) -> float:
+    return _reduce_over_ranks(x, world, "MAX")
+
+
+def sum_over_ranks(x: float, world: int) -> float:
+    return _reduce_over_ranks(x, world, "SUM")
 
 
 def barrier(world: int):
@@ -234,12 +261,7 @@ def run_ours(args, world, rank, local):
     import torch
     from paper_1607_00908_gb300 import vd
 
-    if world > 1:
-        import torch.distributed as dist
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl")
-    else:
-        torch.cuda.set_device(0)
+    torch.cuda.set_device(local if world > 1 else 0)
     vd.lib()
     desc, frames = workload(args.workload, args.frames)
     n = len(frames)
@@ -369,9 +391,6 @@ def run_ours(args, world, rank, local):
             "gpu_launches": launches, "plain_per_frame": plain, "options": variants,
         }
         print(json.dumps(line), flush=True)
-    if world > 1:
-        import torch.distributed as dist
-        dist.destroy_process_group()
 
 
 def run_served(args, world, rank, local):
@@ -384,10 +403,12 @@ def run_served(args, world, rank, local):
     vd.lib()
     r = serve.serve_workload(n_sims=64, rate=args.serve_rate, duration=args.serve_seconds, pool=4, budget_gb=40.0,
                              seed=5 + rank)
+    # every rank serves its own 64 simulations: the job's rate is the sum
+    total = sum_over_ranks(r["served"]["gsites_per_s"], world)
     if rank == 0:
         s, p = r["served"], r["plain"]
         line = {
-            "metric": METRIC + " (served)", "value": world * s["gsites_per_s"], "unit": UNIT, "n_gpus": world,
+            "metric": METRIC + " (served)", "value": total, "unit": UNIT, "n_gpus": world,
             "steps": s["steps"], "warmup": 0, "ms_per_step": 1e3 * s["wall_s"] / max(1, s["steps"]),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
             "data": "synthetic",
@@ -456,9 +477,11 @@ def run_batched_c3(args, world, rank, local):
     ms_plain = max_over_ranks(e0.elapsed_time(e1), world)
     for d in dets:
         d.close()
+    # every rank advances its own 256 lattices: the job's sites are the sum
+    total_sites = sum_over_ranks(float(sites_per_step), world)
     if rank == 0:
-        value = world * sites_per_step * nf / (ms / 1e3) / 1e9
-        plain = world * sites_per_step * nf / (ms_plain / 1e3) / 1e9
+        value = total_sites * nf / (ms / 1e3) / 1e9
+        plain = total_sites * nf / (ms_plain / 1e3) / 1e9
         line = {
             "metric": METRIC + " (batched)", "value": value, "unit": UNIT, "n_gpus": world, "steps": nf,
             "warmup": nf, "ms_per_step": ms / nf, "higher_is_better": True, "scaling": "weak",
@@ -486,13 +509,19 @@ def main():
     args = ap.parse_args()
     world, rank, local = dist_setup()
     if args.impl == "reference":
-        run_reference(args, world, rank)
-    elif args.workload == "c4":
+        run_reference(args, world, rank)   # rank 0 alone; the others exit without work
+        return
+    init_ranks(world, local)
+    if args.workload == "c4":
         run_served(args, world, rank, local)
     elif args.workload == "c3":
         run_batched_c3(args, world, rank, local)
     else:
         run_ours(args, world, rank, local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+        dist.destroy_process_group()
 
 
 if __name__ == "__main__":
