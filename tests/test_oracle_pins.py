@@ -915,3 +915,45 @@ def test_obstacles_are_never_bubbles_owners_or_links():
     a, b = O.split_keys(r2["edges"])
     assert (a >= 0).all() and (b >= 0).all()
     assert (r2["owners"][:, 6] == O.OBSTACLE).all()
+
+
+@pytest.mark.parametrize("periodic", [(False, True), (True, False), (False, False)])
+def test_owners_with_walls_equal_plain_loops(periodic):
+    """Owners on bounded axes: nearest centre by plain (not wrapped) squared
+    distance along a bounded axis, ties to the smallest label, checked by a
+    pure-Python double loop."""
+    rng = np.random.default_rng(91 + 2 * periodic[0] + periodic[1])
+    Lx, Ly = 13, 9
+    cq = rng.integers(0, [Q * Lx, Q * Ly], size=(6, 2))
+    cq[5] = cq[2]                     # an exact tie: label 2 must win
+    own = O.owners_bruteforce(cq, Lx, Ly, periodic=periodic)
+    for y in range(Ly):
+        for x in range(Lx):
+            best, bi = None, -1
+            for i, (cx, cy) in enumerate(cq.tolist()):
+                dx = Q * x - cx
+                dy = Q * y - cy
+                if periodic[0]:
+                    dx = (dx + Q * Lx // 2) % (Q * Lx) - Q * Lx // 2
+                if periodic[1]:
+                    dy = (dy + Q * Ly // 2) % (Q * Ly) - Q * Ly // 2
+                d = dx * dx + dy * dy
+                if best is None or d < best:
+                    best, bi = d, i
+            assert own[y, x] == bi, (x, y)
+
+
+def test_frame_is_truncated_at_a_wall():
+    """A site on the x = 0 wall keeps five frame neighbours (+x, +x+y, +y, -y,
+    +x-y in cyclic order); their colours 1,1,1,0,0 change twice around the
+    frame, so it is not a vertex with walls, while on the torus the three
+    neighbours beyond the seam (colour 2) make a third change."""
+    own = np.zeros((5, 6), dtype=np.int32)
+    own[:, 5] = 2                     # the column beyond the seam on the torus
+    own[2, 1] = 1                     # +x of the site (0, 2)
+    own[3, 1] = 1                     # +x+y
+    own[3, 0] = 1                     # +y
+    g_wall = O.frame_gaps(own, (False, True))
+    g_torus = O.frame_gaps(own)
+    assert int(g_wall[2, 0]) == 2
+    assert int(g_torus[2, 0]) >= 3
