@@ -533,8 +533,9 @@ __global__ void k_flip_write(Pools P, StepTable T) {
 //   exactly one neighbour; boundary event point: a boundary point of the past
 //   or the now triangulation linked there to an active boundary point.
 // The classes are OR-ed into the active flags above bit 0. One thread per
-// active row; rows are staged in local arrays so that their loads are issued
-// together, and shared neighbours are counted by merging sorted rows.
+// active row; a row and its neighbours' rows are held in registers (up to
+// DREG entries each) so that their loads are issued together, and longer
+// rows are merged from global memory.
 // ---------------------------------------------------------------------------
 struct Graph {
     const int* ro;     // row offsets (per-instance values)
