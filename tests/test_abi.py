@@ -43,7 +43,8 @@ def test_status_strings(lib):
 
 @pytest.mark.parametrize("field,value", [("Lx", 0), ("Ly", -3), ("connectivity", 6), ("polarity", 0),
                                          ("Lx", 1 << 21), ("max_components", -1), ("events", 2),
-                                         ("match_rule", 7), ("match_radius", -1)])
+                                         ("match_rule", 7), ("match_radius", -1), ("edge_rule", 3),
+                                         ("walls", 4)])
 def test_invalid_config_is_rejected_without_touching_the_gpu(lib, field, value):
     cfg = vd.vd_config_init(16, 16)
     setattr(cfg, field, value)
@@ -61,3 +62,19 @@ def test_null_handles_are_rejected(lib):
     assert lib.vd_destroy(None) == vd.VD_ERR_INVALID
     assert lib.vd_batch_destroy(None) == vd.VD_ERR_INVALID
     assert lib.vd_config_init(None, 4, 4) == vd.VD_ERR_INVALID
+
+
+def test_centre_match_needs_a_radius_and_walls_double_the_limit(lib):
+    """VD_MATCH_CENTROID without a radius is refused; a bounded axis runs with
+    twice its length, so its length limit is half that of a periodic axis."""
+    import ctypes as C
+    h = C.c_void_p()
+    cfg = vd.vd_config_init(16, 16, match_rule=vd.VD_MATCH_CENTROID, match_radius=0)
+    assert lib.vd_create(C.byref(cfg), C.byref(h)) == vd.VD_ERR_INVALID
+    cfg = vd.vd_config_init((1 << 20) + 1, 1, walls=vd.VD_WALL_X)
+    assert lib.vd_create(C.byref(cfg), C.byref(h)) == vd.VD_ERR_INVALID
+    cfg = vd.vd_config_init((1 << 20) + 1, 1)
+    st = lib.vd_create(C.byref(cfg), C.byref(h))
+    assert st != vd.VD_ERR_INVALID   # a valid config (without a GPU it fails later, at allocation)
+    if st == vd.VD_OK:
+        lib.vd_destroy(h)
