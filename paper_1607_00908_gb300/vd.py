@@ -551,13 +551,16 @@ class Server:
     """Served form (vd_server_*): frames of many simulations, continuous batching."""
 
     def __init__(self, sizes, budget_bytes: int, max_batch: int = 64, threshold: float = 0.5,
-                 polarity: int = VD_ABOVE, stream: int | None = None, max_components: int = 0):
+                 polarity: int = VD_ABOVE, stream: int | None = None, max_components: int = 0, options=None):
+        """``options``: optional list of per-simulation dicts of config options
+        (events, match_rule, match_radius, connectivity, edge_rule, walls)."""
         if stream is None:
             import torch
             stream = torch.cuda.current_stream().cuda_stream
         self.sizes = [(int(lx), int(ly)) for lx, ly in sizes]
-        cfgs = (vd_config * len(sizes))(*[vd_config_init(lx, ly, threshold, polarity, stream, max_components)
-                                          for lx, ly in self.sizes])
+        per = options or [{}] * len(self.sizes)
+        cfgs = (vd_config * len(sizes))(*[vd_config_init(lx, ly, threshold, polarity, stream, max_components, **o)
+                                          for (lx, ly), o in zip(self.sizes, per)])
         h = C.c_void_p()
         _check(lib().vd_server_create(cfgs, len(sizes), int(budget_bytes), int(max_batch), C.byref(h)),
                "vd_server_create")
@@ -594,7 +597,7 @@ class Server:
                                               1 << 22, cap)
         _check(s, "vd_server_get_changes")
         return dict(frame=ch.frame_index, K=ch.n_now, breaking=brk[: ch.n_breaking].copy(),
-                    arising=ari[: ch.n_arising].copy())
+                    arising=ari[: ch.n_arising].copy(), active=act[: ch.n_now].copy())
 
     def close(self):
         if getattr(self, "h", None):

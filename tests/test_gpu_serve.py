@@ -104,3 +104,34 @@ def test_small_served_workload_runs():
     b = serve.run(sims, dev, trace, max_batch=1, budget_bytes=8 << 30)
     assert a["frames"] == b["frames"] == len(trace)
     assert a["steps"] <= b["steps"]
+
+
+def test_served_options_equal_alone():
+    """Simulations with different options (event classes, centre match,
+    8-connectivity, the vertex link rule, walls) served together: every
+    simulation's final labels, flip lists and event flags equal those of its
+    own vd_push_frame context with the same options."""
+    sizes, frames, order = _setup(seed=7)
+    opts = [dict(events=True), dict(events=True, match_rule=vd.VD_MATCH_CENTROID, match_radius=4),
+            dict(connectivity=8), dict(edge_rule=vd.VD_EDGE_VERTEX), dict(walls=vd.VD_WALL_X, events=True)]
+    finals = {}
+    for s, (lx, ly) in enumerate(sizes):
+        det = vd.Detector(lx, ly, **opts[s])
+        for F in frames[s]:
+            det.push(F)
+        finals[s] = (det.labels(), det.changes())
+        det.close()
+    sv = vd.Server(sizes, budget_bytes=1 << 40, max_batch=4, options=opts)
+    for s, f in order:
+        sv.submit(s, frames[s][f])
+    done = 0
+    while done < len(order):
+        done += len(sv.poll(wait=True))
+    for s in range(len(sizes)):
+        lab, ch = finals[s]
+        assert np.array_equal(sv.labels(s), lab), s
+        got = sv.changes(s)
+        assert np.array_equal(got["breaking"], ch["breaking"]), s
+        assert np.array_equal(got["arising"], ch["arising"]), s
+        assert np.array_equal(got["active"], ch["active"]), s
+    sv.close()
