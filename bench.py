@@ -53,6 +53,12 @@ METRIC_BYTES_PER_SITE = 16.0
 # capture, reports null.
 TRAFFIC_BYTES_PER_SITE = {0: 5.071, 2: 2.856, 3: 3.418, 4: 4.325}
 
+# Issue-slot use (smsp__issue_active, % of peak) of the same stages' kernels
+# from one ncu --set full capture on 2 frames of 4096^2 droplets
+# (profiles/site_kernels_c2.txt): the kernels are bound by instruction issue or
+# latency, not by DRAM, and this says how close to the issue limit they run.
+ISSUE_ACTIVE_PCT = {0: 47.8, 2: 23.3, 3: 70.9, 4: 67.5}
+
 
 def workload(name: str, n_frames: int | None):
     if name == "c1":
@@ -253,6 +259,7 @@ def roofline_of(stage_ms, names, launches_per_stage, sites_per_launch, sequence,
     return {"bound": "hbm", "kernel": names[dom], "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": achieved / peak, "peak_kind": peak_kind,
             "traffic": traffic * sites_per_launch if traffic is not None else None,
+            "issue_active_pct_ncu": ISSUE_ACTIVE_PCT.get(dom),
             "bytes_per_site": sb[dom], "bytes_per_launch": bytes_per_launch, "avg_launch_ms": avg_ms,
             "stage_ms_per_launch": {names[k]: stage_ms[k] / launches_per_stage for k in range(len(names))}}
 
