@@ -957,3 +957,53 @@ def test_frame_is_truncated_at_a_wall():
     g_torus = O.frame_gaps(own)
     assert int(g_wall[2, 0]) == 2
     assert int(g_torus[2, 0]) >= 3
+
+
+# ----------------------------------------------------------------------------
+# Symmetries that any correct reading of the match and the flips must have
+# ----------------------------------------------------------------------------
+
+def test_matches_are_symmetric_in_time():
+    """Mutual best overlap and mutual nearest centres do not depend on which
+    frame is called past: swapping the frames swaps Phi and its inverse."""
+    rng = np.random.default_rng(5)
+    for trial in range(8):
+        L = int(rng.integers(24, 64))
+        F0 = I.smoothed_noise(L, L, 2.5, seed=trial)
+        F1 = I.shear_resample(F0, 0.05, 0.05, np.random.default_rng(trial))
+        l0, k0 = O.label_components(O.foreground(F0))
+        l1, k1 = O.label_components(O.foreground(F1))
+        phi, inv = O.match_overlap(l0, l1, k0, k1)
+        phi_r, inv_r = O.match_overlap(l1, l0, k1, k0)
+        assert phi.tolist() == inv_r.tolist() and inv.tolist() == phi_r.tolist()
+        c0, c1 = O.centroids_q10(l0, k0), O.centroids_q10(l1, k1)
+        phi, inv = O.match_centroid(c0, c1, L, L, radius=5)
+        phi_r, inv_r = O.match_centroid(c1, c0, L, L, radius=5)
+        assert phi.tolist() == inv_r.tolist() and inv.tolist() == phi_r.tolist()
+
+
+def test_flips_reverse_in_time():
+    """Run backwards, a breaking link becomes an arising one: the arising links
+    from past to now, written in past labels, are the breaking links from now
+    to past, and the other way round."""
+    rng = np.random.default_rng(6)
+    checked = 0
+    for trial in range(10):
+        L = int(rng.integers(40, 80))
+        F0 = I.smoothed_noise(L, L, 3.0, seed=20 + trial)
+        F1 = I.shear_resample(F0, 0.08, 0.05, np.random.default_rng(trial))
+        d = O.Detector(L, L, voronoi="brute")
+        a = d.push(F0)
+        b = d.push(F1)
+        phi, inv = b["phi"], b["inv"]
+        fwd = O.flips(a["edges"], b["edges"], phi, inv)
+        bwd = O.flips(b["edges"], a["edges"], inv, phi)
+        # arising (now labels) -> past labels, against breaking of the reversed run
+        x, y = O.split_keys(fwd["arising"])
+        arising_in_past = np.sort(O.make_keys(inv[x], inv[y])) if x.size else np.zeros(0, np.uint64)
+        assert arising_in_past.tolist() == bwd["breaking"].tolist()
+        x, y = O.split_keys(bwd["arising"])
+        back = np.sort(O.make_keys(phi[x], phi[y])) if x.size else np.zeros(0, np.uint64)
+        assert back.tolist() == fwd["breaking"].tolist()
+        checked += int(fwd["breaking"].size + fwd["arising"].size > 0)
+    assert checked >= 3
