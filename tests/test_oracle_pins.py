@@ -1007,3 +1007,32 @@ def test_flips_reverse_in_time():
         assert back.tolist() == fwd["breaking"].tolist()
         checked += int(fwd["breaking"].size + fwd["arising"].size > 0)
     assert checked >= 3
+
+
+def test_event_classes_reverse_in_time():
+    """The event classes use both triangulations alike: run backwards, every
+    active label keeps its bulk and boundary event classes, and its boundary
+    point flags of the past and the now triangulation trade places."""
+    rng = np.random.default_rng(8)
+    seen = 0
+    for trial in range(16):
+        L = int(rng.integers(48, 96))
+        F0 = I.smoothed_noise(L, L, float(rng.uniform(2.0, 4.0)), seed=40 + trial)
+        F1 = I.shear_resample(F0, 0.2, 0.05, np.random.default_rng(trial))
+        d = O.Detector(L, L, voronoi="brute")
+        a = d.push(F0)
+        b = d.push(F1)
+        phi, inv = b["phi"], b["inv"]
+        fwd = O.flips(a["edges"], b["edges"], phi, inv)
+        bwd = O.flips(b["edges"], a["edges"], inv, phi)
+        ef = O.classify_events(a["edges"], b["edges"], phi, inv, fwd["active"])
+        eb = O.classify_events(b["edges"], a["edges"], inv, phi, bwd["active"])
+        for n in np.flatnonzero(ef).tolist():
+            p = int(inv[n])
+            f, g = int(ef[n]), int(eb[p])
+            assert (f & (O.EV_ACTIVE | O.EV_BULK | O.EV_BOUNDARY)) == (g & (O.EV_ACTIVE | O.EV_BULK | O.EV_BOUNDARY))
+            assert bool(f & O.EV_BPOINT_NOW) == bool(g & O.EV_BPOINT_PAST)
+            assert bool(f & O.EV_BPOINT_PAST) == bool(g & O.EV_BPOINT_NOW)
+            seen += 1
+        assert int((eb != 0).sum()) == int((ef != 0).sum())
+    assert seen > 20
