@@ -18,9 +18,12 @@ arithmetic is exact for the integer fixed-point coordinates used here, and
 ties are resolved in integers afterwards). ``owners_bruteforce`` is the
 literal definition and pins ``owners``.
 
-Parity unpinned: ``vertex_edges`` (the paper's frame / inner-frame link rule,
-an option) follows a reading of figures that are lost; it is checked only on
-hand-counted frames, not against the authors' code.
+``vertex_edges`` (the paper's frame / inner-frame link rule, an option)
+follows a reading of figures that are lost. It is pinned to geometry -- the
+periodic Delaunay triangulation on generic point sets, a triangulation on dense
+random sets, hand-counted pathological colourings and ties -- but not to the
+authors' code, and the pins do not decide the orientation of its quarter turns
+(the mirror-image reading passes them too).
 """
 from __future__ import annotations
 
@@ -450,10 +453,11 @@ def frame_gaps(owner: np.ndarray, periodic=(True, True)) -> np.ndarray:
 
 def vertex_edges(owner: np.ndarray, cq: np.ndarray, periodic=(True, True)) -> np.ndarray:
     """Links read at the vertex sites of the digital Voronoi diagram (Section
-    3.2.2, the paper's frame rule), as sorted uint64 keys. PARITY UNPINNED: the
-    figures that define the inner frame and the pathological colourings are
-    lost, so only the readings below are checked, not agreement with the
-    authors' code.
+    3.2.2, the paper's frame rule), as sorted uint64 keys. The figures that
+    define the inner frame and the pathological colourings are lost, so the
+    readings below are checked against geometry (Delaunay triangulations,
+    hand-counted colourings), not against the authors' code; the mirror-image
+    reading (quarter turns clockwise) passes the same checks.
 
     Readings: a vertex site has three or more colour changes around its frame
     (two: a cell edge, none: a cell interior). On a periodic lattice without

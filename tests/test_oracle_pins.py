@@ -778,8 +778,9 @@ def test_centroid_match_equals_bruteforce_loops():
 
 
 # ----------------------------------------------------------------------------
-# Section 3.2.2, the frame rule (vertex_edges, an option; parity with the
-# authors' code is unpinned because its figures are lost): hand-counted cases
+# Section 3.2.2, the frame rule (vertex_edges, an option; its figures are
+# lost, so it is pinned to geometry): hand-counted cases, the periodic
+# Delaunay triangulation, pathological colourings and ties
 # ----------------------------------------------------------------------------
 
 def test_frame_gaps_and_vertex_links_at_a_three_cell_junction():
@@ -806,6 +807,146 @@ def test_vertex_rule_sees_no_vertex_between_two_stripes():
     assert int(O.frame_gaps(own).max()) == 2
     cq = np.array([[Q * 2, Q], [Q * 2, Q * 4]], dtype=np.int64)
     assert O.vertex_edges(own, cq).size == 0
+
+
+def test_vertex_rule_equals_bruteforce_delaunay_on_generic_configurations():
+    """Every Voronoi vertex of a generic point set is a site whose frame
+    changes colour three times, so the frame rule reads each Delaunay
+    triangle there. On jittered triangular lattices (no cocircular
+    quadruple, every dual edge longer than 3 sites) its links are exactly the
+    periodic Delaunay triangulation found by empty-circle brute force."""
+    rng = np.random.default_rng(21)
+    a, m, n = 12, 6, 4
+    Lx, Ly = a * m, 42
+    K = m * n
+    checked = 0
+    for trial in range(12):
+        pts = _jittered_triangular(rng, a, m, n, Lx, Ly, jitter=1.5)
+        edges, tris, margin, dual, _ = periodic_delaunay(pts, Q * Lx, Q * Ly, radius=int(2.5 * a * Q))
+        if margin == 0 or dual < 3 * Q or len(edges) != 3 * K:
+            continue
+        cq = np.array(pts, dtype=np.int64)
+        E = O.vertex_edges(O.owners_bruteforce(cq, Lx, Ly), cq)
+        got = set(zip(*[a_.tolist() for a_ in O.split_keys(E)]))
+        assert got == edges, trial
+        checked += 1
+    assert checked >= 5
+
+
+def test_vertex_rule_differs_from_delaunay_only_at_near_degenerate_quads():
+    """On random point sets the frame rule finds every Delaunay edge whose
+    dual Voronoi edge is at least one site long; a missed edge is replaced by
+    the other diagonal of its quad, so the links stay a triangulation."""
+    rng = np.random.default_rng(22)
+    L, K = 48, 14
+    for trial in range(8):
+        pts = _generic_points(rng, L, K, min_sep=7)
+        edges, tris, margin, dual, dual_of = periodic_delaunay(pts, Q * L, Q * L, radius=int(0.8 * L * Q))
+        cq = np.array(pts, dtype=np.int64)
+        E = O.vertex_edges(O.owners_bruteforce(cq, L, L), cq)
+        got = set(zip(*[a_.tolist() for a_ in O.split_keys(E)]))
+        assert len(got) == len(edges), trial
+        nb = {}
+        for x, y in edges:
+            nb.setdefault(x, set()).add(y)
+            nb.setdefault(y, set()).add(x)
+        missed = edges - got
+        for e in missed:
+            assert dual_of[e] < Q, (trial, e, dual_of[e] / Q)
+            # on a small torus two labels can share more than one pair of
+            # neighbours (through different images); the quad is then not
+            # named by labels alone
+            opp = sorted(nb[e[0]] & nb[e[1]])
+            if len(opp) == 2:
+                assert (opp[0], opp[1]) in got, (trial, e, opp)
+        assert len(got - edges) == len(missed), trial
+
+
+def _links_cross(cq, E, M):
+    """Whether two links, drawn as the shortest segments between their centres
+    on the M x M torus, cross at a point inside both (shared ends excluded)."""
+    i, j = O.split_keys(E)
+    seg = []
+    for p, q in zip(i.tolist(), j.tolist()):
+        d = np.array([O.wrap(int(cq[q, t] - cq[p, t]), M) for t in (0, 1)], dtype=np.int64)
+        seg.append((p, q, cq[p].astype(np.int64), d))
+
+    def orient(a, b, c):
+        return np.sign((b[0] - a[0]) * (c[1] - a[1]) - (b[1] - a[1]) * (c[0] - a[0]))
+
+    for u in range(len(seg)):
+        p, q, a, da = seg[u]
+        for w in range(u + 1, len(seg)):
+            r, s_, b, db = seg[w]
+            if len({p, q, r, s_}) < 4:
+                continue
+            b0 = a + np.array([O.wrap(int(b[0] - a[0]), M), O.wrap(int(b[1] - a[1]), M)], dtype=np.int64)
+            for sx in (-1, 0, 1):
+                for sy in (-1, 0, 1):
+                    c0 = b0 + np.array([sx * M, sy * M], dtype=np.int64)
+                    if (orient(a, a + da, c0) * orient(a, a + da, c0 + db) < 0
+                            and orient(c0, c0 + db, a) * orient(c0, c0 + db, a + da) < 0):
+                        return True
+    return False
+
+
+def test_vertex_rule_is_a_triangulation_on_dense_random_sets():
+    """Cells as close as 3 sites, many of them slivers: the frame rule's links
+    still form a triangulation of the torus -- no two links cross, and there
+    are E = 3K of them (Euler). Dropping the inner-frame test adds crossing
+    links; dropping the second neighbours loses links."""
+    rng = np.random.default_rng(7)
+    L, K = 40, 40
+    for trial in range(4):
+        pts = _generic_points(rng, L, K, min_sep=3)
+        cq = np.array(pts, dtype=np.int64)
+        E = O.vertex_edges(O.owners_bruteforce(cq, L, L), cq)
+        assert len(E) == 3 * len(pts), trial
+        assert not _links_cross(cq, E, Q * L), trial
+
+
+@pytest.mark.parametrize("a,b,M,L", [(1, -1, 4, 8), (1, 1, 4, 8), (1, -1, 8, 16), (1, 1, 8, 16),
+                                     (2, 1, 4, 8), (1, 2, 4, 8)])
+def test_vertex_rule_keeps_one_site_bands_apart(a, b, M, L):
+    """Colour (a x + b y) mod M: M bands one site thin, every site a vertex
+    site (eight colour changes around each frame). Band c touches only bands
+    c - 1 and c + 1, and the frame rule reads exactly that ring whatever the
+    centres: across a diagonal band the short-diagonal condition stops the
+    second neighbour (x +- y), and across a steep band the long-diagonal
+    condition stops the first neighbour (2x + y, x + 2y)."""
+    y, x = np.mgrid[0:L, 0:L]
+    own = ((a * x + b * y) % M).astype(np.int32)
+    assert int(O.frame_gaps(own).min()) == 8
+    ring = sorted(tuple(sorted((c, (c + 1) % M))) for c in range(M))
+    rng = np.random.default_rng(M + 3 * a + b)
+    for _ in range(3):
+        cq = rng.integers(0, Q * L, size=(M, 2)).astype(np.int64)
+        got = sorted(zip(*[v.tolist() for v in O.split_keys(O.vertex_edges(own, cq))]))
+        assert got == ring
+
+
+@pytest.mark.parametrize("centres,diagonal", [
+    # the cells of 1 and 3 are equidistant from the junction and nearest: the
+    # plaquette centre takes colour 1, so 1-2 is linked and 0-3 is not
+    (((1, 1), (5.5, 1.5), (1, 6), (5.5, 5.5)), (1, 2)),
+    # all four equidistant (a square of centres): colour 0, so 0-3
+    (((1.5, 1.5), (5.5, 1.5), (1.5, 5.5), (5.5, 5.5)), (0, 3)),
+])
+def test_vertex_rule_tie_at_a_four_cell_junction(centres, diagonal):
+    """8 x 8 box, walls on both axes, four 4 x 4 cells (0 lower left, 1 lower
+    right, 2 upper left, 3 upper right) meeting at the plaquette centred on
+    (3.5, 3.5), whose four sites are the only vertex sites. Both diagonals
+    pass the pathology conditions there; the one whose end owns the plaquette
+    centre -- nearest centre, ties to the smallest label -- is linked."""
+    own = np.zeros((8, 8), dtype=np.int32)
+    own[:4, 4:] = 1
+    own[4:, :4] = 2
+    own[4:, 4:] = 3
+    gaps = O.frame_gaps(own, (False, False))
+    assert sorted(zip(*np.nonzero(gaps >= 3))) == [(3, 3), (3, 4), (4, 3), (4, 4)]
+    cq = np.array([[int(x * Q), int(y * Q)] for x, y in centres], dtype=np.int64)
+    got = sorted(zip(*[v.tolist() for v in O.split_keys(O.vertex_edges(own, cq, periodic=(False, False)))]))
+    assert got == sorted([(0, 1), (0, 2), (1, 3), (2, 3), diagonal])
 
 
 
