@@ -472,6 +472,31 @@ __device__ __forceinline__ void link_list_put(unsigned long long* list, int pos,
     else if (ok) edge_global_insert(P, D, inst, edge_key(a, b));
 }
 
+// the first min(n, LSET) keys of a warp's list (whole warp): equal keys within
+// a round of 32 are merged, the rest appended to the instance's link list (the
+// link hash removes the remaining repeats); EMPTY_KEY entries are dropped
+__device__ __forceinline__ void flush_link_list(const unsigned long long* list, int n, int lane, const Pools& P,
+                                                const InstDesc& D, int inst) {
+    const unsigned lt = (1u << lane) - 1u;
+    n = min(n, LSET);
+    for (int kb = 0; kb < n; kb += 32) {
+        const bool in = kb + lane < n;
+        const unsigned long long key = in ? list[kb + lane] : EMPTY_KEY;
+        const unsigned grp = __match_any_sync(0xffffffffu, key);
+        const bool has = in && key != EMPTY_KEY && lane == __ffs(grp) - 1;
+        const unsigned m = __ballot_sync(0xffffffffu, has);
+        if (!m) continue;
+        int base = 0;
+        if (lane == 0) base = atomicAdd(&P.st[inst].n_eapp, __popc(m));
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (has) {
+            const int pos = base + __popc(m & lt);
+            if (pos < D.edge_cap) P.ekeys[D.edge_off + pos] = key;
+            else edge_global_insert(P, D, inst, key);   // list full: insert directly
+        }
+    }
+}
+
 __device__ __forceinline__ void cp_async4(int* smem, const int* gmem) {
     const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem) : "memory");
@@ -574,25 +599,7 @@ __global__ __launch_bounds__(32 * LINK_WARPS) void k_links(Pools P, StepTable T)
         lf = dlf;
     }
     __syncwarp();
-    // equal keys within a round of 32 are merged; the tile's keys are
-    // appended to the instance's link list (the link hash removes the rest)
-    n = min(n, LSET);
-    for (int kb = 0; kb < n; kb += 32) {
-        const bool in = kb + lane < n;
-        const unsigned long long key = in ? list[kb + lane] : EMPTY_KEY;
-        const unsigned grp = __match_any_sync(0xffffffffu, key);
-        const bool has = in && key != EMPTY_KEY && lane == __ffs(grp) - 1;
-        const unsigned m = __ballot_sync(0xffffffffu, has);
-        if (!m) continue;
-        int base = 0;
-        if (lane == 0) base = atomicAdd(&P.st[inst].n_eapp, __popc(m));
-        base = __shfl_sync(0xffffffffu, base, 0);
-        if (has) {
-            const int pos = base + __popc(m & lt);
-            if (pos < D.edge_cap) P.ekeys[D.edge_off + pos] = key;
-            else edge_global_insert(P, D, inst, key);   // list full: insert directly
-        }
-    }
+    flush_link_list(list, n, lane, P, D, inst);
 }
 
 // appended links -> link hash (+ degrees); appended pairs -> overlap hash
@@ -642,21 +649,40 @@ void launch_voronoi(const Launch& L) {
 //   second neighbour k+e1+e2: C(k+e1+e2) != C(k), C(k+e2) != C(k+e1-e2),
 //   C(k+e2) != C(k+e1), and the inner-frame point (read as the plaquette
 //   centre k + (e1+e2)/2) is owned by C(k) or by C(k+e1+e2).
-// One thread per site of a 32 x 32 tile (one warp per tile, lane = column);
-// vertex sites are rare. The colour of a plaquette centre is the nearest
-// centre among the colours at the plaquette's corners (exact, ties to the
-// smallest label).
+// One warp per 32 x 32 tile, lane = column, walking down the rows with the
+// rows above and below in registers (one load per site, the side columns by
+// shuffle). Vertex sites are rare: a row without one skips the rules. The
+// colour of a plaquette centre is the nearest centre among the colours at the
+// plaquette's corners (exact, ties to the smallest label). Keys go to the
+// per-warp list, merged and appended as in the adjacency rule.
 // ---------------------------------------------------------------------------
 
-__device__ __forceinline__ void vertex_link(const Pools& P, const InstDesc& D, int inst, int a, int b) {
-    const unsigned long long key = edge_key(a, b);
-    const int pos = atomicAdd(&P.st[inst].n_eapp, 1);
-    if (pos < D.edge_cap) P.ekeys[D.edge_off + pos] = key;
-    else edge_global_insert(P, D, inst, key);
+// one owner row seen by a lane: columns x-1, x, x+1 (periodic). The middle
+// value is this lane's load; the sides come from the neighbouring lanes, or
+// from their own loads at the tile's edges and at the lattice's last column
+struct VRow {
+    int c, l, r;
+};
+
+__device__ __forceinline__ VRow vrow_load(const int* row, int xc, int xm, int xp, bool el, bool er) {
+    VRow v;
+    v.c = row[xc];
+    v.l = el ? row[xm] : 0;
+    v.r = er ? row[xp] : 0;
+    return v;
+}
+
+__device__ __forceinline__ VRow vrow_share(VRow v, bool el, bool er) {
+    const int l = __shfl_up_sync(0xffffffffu, v.c, 1);
+    const int r = __shfl_down_sync(0xffffffffu, v.c, 1);
+    if (!el) v.l = l;
+    if (!er) v.r = r;
+    return v;
 }
 
 __global__ __launch_bounds__(32 * LINK_WARPS) void k_links_vertex(Pools P, StepTable T) {
     pdl_enter();
+    __shared__ unsigned long long s_list[LINK_WARPS][LSET];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int b = blockIdx.x * LINK_WARPS + warp;
     if (b >= T.tileV_pre[T.n_act]) return;
@@ -669,23 +695,32 @@ __global__ __launch_bounds__(32 * LINK_WARPS) void k_links_vertex(Pools P, StepT
     const int t = b - T.tileV_pre[a];
     const int tx = t % D.vtx, ty = t / D.vtx;
     const int Lx = D.Lx, Ly = D.Ly;
+    // every lane takes part in the shuffles; lanes past the last column read
+    // the last column and emit nothing
     const int x = tx * VW + lane;
-    if (x >= Lx) return;
+    const bool valid = x < Lx;
+    const int xc = valid ? x : Lx - 1;
+    const int xm = xc == 0 ? Lx - 1 : xc - 1, xp = xc + 1 == Lx ? 0 : xc + 1;
+    const bool el = lane == 0, er = lane == 31 || xc + 1 == Lx;
     const int2* cq = P.cq[S.slot ^ 1] + D.comp_off;
     const int* own = P.owners + D.site_off;
     const long long MX = (long long)Q * Lx, MY = (long long)Q * Ly;
-    const int xm = x == 0 ? Lx - 1 : x - 1, xp = x + 1 == Lx ? 0 : x + 1;
+    unsigned long long* list = s_list[warp];
     const int y0 = ty * VH, y1 = min(y0 + VH, Ly);
+    auto row = [&](int y) { return own + (long long)(y >= Ly ? y - Ly : y) * Lx; };
+    // rows y-1 and y in registers, row y+1 loaded one iteration ahead
+    VRow rm = vrow_share(vrow_load(row(y0 == 0 ? Ly - 1 : y0 - 1), xc, xm, xp, el, er), el, er);
+    VRow r0 = vrow_share(vrow_load(row(y0), xc, xm, xp, el, er), el, er);
+    VRow nx = vrow_load(row(y0 + 1), xc, xm, xp, el, er);
+    int n = 0;   // keys in the warp's list (warp-uniform)
     for (int y = y0; y < y1; ++y) {
-        const int ym = y == 0 ? Ly - 1 : y - 1, yp = y + 1 == Ly ? 0 : y + 1;
-        const int* rm = own + (long long)ym * Lx;
-        const int* r0 = own + (long long)y * Lx;
-        const int* rp = own + (long long)yp * Lx;
+        const VRow rp = vrow_share(nx, el, er);
+        if (y + 1 < y1) nx = vrow_load(row(y + 2), xc, xm, xp, el, er);
         // the frame in counter-clockwise order from +x; f[8] = the site itself
         int f[9];
-        f[0] = r0[xp]; f[1] = rp[xp]; f[2] = rp[x]; f[3] = rp[xm];
-        f[4] = r0[xm]; f[5] = rm[xm]; f[6] = rm[x]; f[7] = rm[xp];
-        f[8] = r0[x];
+        f[0] = r0.r; f[1] = rp.r; f[2] = rp.c; f[3] = rp.l;
+        f[4] = r0.l; f[5] = rm.l; f[6] = rm.c; f[7] = rm.r;
+        f[8] = r0.c;
         // colour changes around the frame; members beyond a wall (owner
         // OWN_OUTSIDE) leave it, obstacles keep their MAXLINK colour
         int prev = OWN_OUTSIDE;
@@ -699,39 +734,65 @@ __global__ __launch_bounds__(32 * LINK_WARPS) void k_links_vertex(Pools P, StepT
                 prev = f[i];
             }
         const int k = f[8];
-        if (gaps < 3 || k < 0) continue;
-        // quarter turn q: e1 = frame entry 2q, e1 + e2 = entry 2q + 1, e2 = entry 2q + 2,
-        // e1 - e2 = entry 2q - 1 (all mod 8)
+        const bool vert = valid && gaps >= 3 && k >= 0;
+        if (__any_sync(0xffffffffu, vert)) {
+            // bit q: first neighbour of quarter turn q; bit 4 + q: second neighbour
+            unsigned em = 0;
+            if (vert) {
+                // quarter turn q: e1 = frame entry 2q, e1 + e2 = entry 2q + 1,
+                // e2 = entry 2q + 2, e1 - e2 = entry 2q - 1 (all mod 8)
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const int c1 = f[2 * q], cd = f[2 * q + 1], c2 = f[(2 * q + 2) & 7], c3 = f[(2 * q + 7) & 7];
-            if (c1 >= 0 && c1 != k && c2 != c3) vertex_link(P, D, inst, k, c1);
-            if (cd >= 0 && cd != k && c2 != c3 && c2 != c1) {
-                // plaquette centre k + (e1 + e2) / 2: the nearest centre among
-                // the colours at the plaquette's corners k, k+e1, k+e1+e2, k+e2
-                const int ex = (q == 0 || q == 3) ? 1 : -1, ey = (q == 0 || q == 1) ? 1 : -1;
-                long long qx = (long long)Q * x + (Q / 2) * ex, qy = (long long)Q * y + (Q / 2) * ey;
-                qx = (qx % MX + MX) % MX;
-                qy = (qy % MY + MY) % MY;
-                const int cand[4] = {k, c1, cd, c2};
-                int ca = -1;
-                long long bd = 0;
+                for (int q = 0; q < 4; ++q) {
+                    const int c1 = f[2 * q], cd = f[2 * q + 1], c2 = f[(2 * q + 2) & 7], c3 = f[(2 * q + 7) & 7];
+                    if (c1 >= 0 && c1 != k && c2 != c3) em |= 1u << q;
+                    if (cd >= 0 && cd != k && c2 != c3 && c2 != c1) {
+                        // plaquette centre k + (e1 + e2) / 2: the nearest centre among
+                        // the colours at the plaquette's corners k, k+e1, k+e1+e2, k+e2
+                        const int ex = (q == 0 || q == 3) ? 1 : -1, ey = (q == 0 || q == 1) ? 1 : -1;
+                        long long qx = (long long)Q * x + (Q / 2) * ex, qy = (long long)Q * y + (Q / 2) * ey;
+                        qx = (qx % MX + MX) % MX;
+                        qy = (qy % MY + MY) % MY;
+                        const int cand[4] = {k, c1, cd, c2};
+                        int ca = -1;
+                        long long bd = 0;
 #pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    const int c = cand[j];
-                    if (c < 0) continue;
-                    const int2 cc = cq[c];
-                    const long long ddx = wrap_ll((long long)cc.x - qx, MX), ddy = wrap_ll((long long)cc.y - qy, MY);
-                    const long long d = ddx * ddx + ddy * ddy;
-                    if (ca < 0 || d < bd || (d == bd && c < ca)) {
-                        bd = d;
-                        ca = c;
+                        for (int j = 0; j < 4; ++j) {
+                            const int c = cand[j];
+                            if (c < 0) continue;
+                            const int2 cc = cq[c];
+                            const long long ddx = wrap_ll((long long)cc.x - qx, MX);
+                            const long long ddy = wrap_ll((long long)cc.y - qy, MY);
+                            const long long d = ddx * ddx + ddy * ddy;
+                            if (ca < 0 || d < bd || (d == bd && c < ca)) {
+                                bd = d;
+                                ca = c;
+                            }
+                        }
+                        if (ca == k || ca == cd) em |= 16u << q;
                     }
                 }
-                if (ca == k || ca == cd) vertex_link(P, D, inst, k, cd);
             }
+            // this lane's keys go after those of the lanes before it
+            const int ne = __popc(em);
+            int inc = ne;
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const int v = __shfl_up_sync(0xffffffffu, inc, d);
+                if (lane >= d) inc += v;
+            }
+            int pos = n + inc - ne;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                if (em & (1u << q)) link_list_put(list, pos++, k, f[2 * q], P, D, inst);
+                if (em & (16u << q)) link_list_put(list, pos++, k, f[2 * q + 1], P, D, inst);
+            }
+            n += __shfl_sync(0xffffffffu, inc, 31);
         }
+        rm = r0;
+        r0 = rp;
     }
+    __syncwarp();
+    flush_link_list(list, n, lane, P, D, inst);
 }
 
 // Owners of sites beyond a wall (the second half of a bounded axis) become
