@@ -359,8 +359,16 @@ def run_ours(args, world, rank, local):
         e1.record(s)
         torch.cuda.synchronize()
         vms = max_over_ranks(e0.elapsed_time(e1), world)
+        # per-stage CUDA events on the library stream, separate untimed pushes
+        vb.set_timing(True)
+        vb.timing()
+        for _ in range(vsteps):
+            vb.push(dev)
+        vst, vnames, _, _ = vb.timing()
+        vb.set_timing(False)
         variants[name] = {"value": world * sites_per_step * vsteps / (vms / 1e3) / 1e9, "unit": UNIT,
-                          "ms_per_step": vms / vsteps, "steps": vsteps}
+                          "ms_per_step": vms / vsteps, "steps": vsteps,
+                          "stage_ms_per_step": {vnames[k]: vst[k] / vsteps for k in range(len(vnames))}}
         vb.close()
 
     # ---- the plain per-frame path (vd_push_frame, one frame per call) ----

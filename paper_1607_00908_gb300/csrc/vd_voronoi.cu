@@ -660,6 +660,14 @@ void launch_voronoi(const Launch& L) {
 // one owner row seen by a lane: columns x-1, x, x+1 (periodic). The middle
 // value is this lane's load; the sides come from the neighbouring lanes, or
 // from their own loads at the tile's edges and at the lattice's last column
+// v mod L for -L <= v < 2L, without a division (a 64-bit remainder is a long
+// dependent chain, and vertex sites take it one lane at a time): plaquette
+// centres lie within half a site of the lattice and centres are stored in
+// [0, Q L), so their differences stay in range
+__device__ __forceinline__ long long wrap_once(long long v, long long L) {
+    return v < 0 ? v + L : (v >= L ? v - L : v);
+}
+
 struct VRow {
     int c, l, r;
 };
@@ -704,7 +712,7 @@ __global__ __launch_bounds__(32 * LINK_WARPS) void k_links_vertex(Pools P, StepT
     const bool el = lane == 0, er = lane == 31 || xc + 1 == Lx;
     const int2* cq = P.cq[S.slot ^ 1] + D.comp_off;
     const int* own = P.owners + D.site_off;
-    const long long MX = (long long)Q * Lx, MY = (long long)Q * Ly;
+    const long long MX = (long long)Q * Lx, MY = (long long)Q * Ly, HX = MX / 2, HY = MY / 2;
     unsigned long long* list = s_list[warp];
     const int y0 = ty * VH, y1 = min(y0 + VH, Ly);
     auto row = [&](int y) { return own + (long long)(y >= Ly ? y - Ly : y) * Lx; };
@@ -750,8 +758,8 @@ __global__ __launch_bounds__(32 * LINK_WARPS) void k_links_vertex(Pools P, StepT
                         // the colours at the plaquette's corners k, k+e1, k+e1+e2, k+e2
                         const int ex = (q == 0 || q == 3) ? 1 : -1, ey = (q == 0 || q == 1) ? 1 : -1;
                         long long qx = (long long)Q * x + (Q / 2) * ex, qy = (long long)Q * y + (Q / 2) * ey;
-                        qx = (qx % MX + MX) % MX;
-                        qy = (qy % MY + MY) % MY;
+                        qx = wrap_once(qx, MX);
+                        qy = wrap_once(qy, MY);
                         const int cand[4] = {k, c1, cd, c2};
                         int ca = -1;
                         long long bd = 0;
@@ -760,8 +768,8 @@ __global__ __launch_bounds__(32 * LINK_WARPS) void k_links_vertex(Pools P, StepT
                             const int c = cand[j];
                             if (c < 0) continue;
                             const int2 cc = cq[c];
-                            const long long ddx = wrap_ll((long long)cc.x - qx, MX);
-                            const long long ddy = wrap_ll((long long)cc.y - qy, MY);
+                            const long long ddx = wrap_once((long long)cc.x - qx + HX, MX) - HX;
+                            const long long ddy = wrap_once((long long)cc.y - qy + HY, MY) - HY;
                             const long long d = ddx * ddx + ddy * ddy;
                             if (ca < 0 || d < bd || (d == bd && c < ca)) {
                                 bd = d;
