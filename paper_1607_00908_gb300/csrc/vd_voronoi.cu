@@ -649,17 +649,15 @@ void launch_voronoi(const Launch& L) {
 //   second neighbour k+e1+e2: C(k+e1+e2) != C(k), C(k+e2) != C(k+e1-e2),
 //   C(k+e2) != C(k+e1), and the inner-frame point (read as the plaquette
 //   centre k + (e1+e2)/2) is owned by C(k) or by C(k+e1+e2).
-// One warp per 32 x 32 tile, lane = column, walking down the rows with the
-// rows above and below in registers (one load per site, the side columns by
-// shuffle). Vertex sites are rare: a row without one skips the rules. The
+// One warp per 32 x 32 tile, lane = column: the tile's owners with a one-site
+// halo are staged in shared memory with cp.async (all rows in flight at once),
+// then the warp walks down the rows with the rows above and below in
+// registers. Vertex sites are rare: a row without one skips the rules. The
 // colour of a plaquette centre is the nearest centre among the colours at the
 // plaquette's corners (exact, ties to the smallest label). Keys go to the
 // per-warp list, merged and appended as in the adjacency rule.
 // ---------------------------------------------------------------------------
 
-// one owner row seen by a lane: columns x-1, x, x+1 (periodic). The middle
-// value is this lane's load; the sides come from the neighbouring lanes, or
-// from their own loads at the tile's edges and at the lattice's last column
 // v mod L for -L <= v < 2L, without a division (a 64-bit remainder is a long
 // dependent chain, and vertex sites take it one lane at a time): plaquette
 // centres lie within half a site of the lattice and centres are stored in
@@ -668,28 +666,11 @@ __device__ __forceinline__ long long wrap_once(long long v, long long L) {
     return v < 0 ? v + L : (v >= L ? v - L : v);
 }
 
-struct VRow {
-    int c, l, r;
-};
-
-__device__ __forceinline__ VRow vrow_load(const int* row, int xc, int xm, int xp, bool el, bool er) {
-    VRow v;
-    v.c = row[xc];
-    v.l = el ? row[xm] : 0;
-    v.r = er ? row[xp] : 0;
-    return v;
-}
-
-__device__ __forceinline__ VRow vrow_share(VRow v, bool el, bool er) {
-    const int l = __shfl_up_sync(0xffffffffu, v.c, 1);
-    const int r = __shfl_down_sync(0xffffffffu, v.c, 1);
-    if (!el) v.l = l;
-    if (!er) v.r = r;
-    return v;
-}
+constexpr int VS = VW + 8;      // staged row stride of the vertex rule: column c at 4 + c
 
 __global__ __launch_bounds__(32 * LINK_WARPS) void k_links_vertex(Pools P, StepTable T) {
     pdl_enter();
+    __shared__ __align__(16) int s_own[LINK_WARPS][(VH + 2) * VS];
     __shared__ unsigned long long s_list[LINK_WARPS][LSET];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int b = blockIdx.x * LINK_WARPS + warp;
@@ -697,38 +678,65 @@ __global__ __launch_bounds__(32 * LINK_WARPS) void k_links_vertex(Pools P, StepT
     const int a = seg_of_int(T.tileV_pre, T.n_act, b);
     const int inst = T.act[a];
     const InstDesc& D = P.desc[inst];
-    const InstState& S = P.st[inst];
-    const int K = min(S.K, D.comp_cap);
+    const InstState& St = P.st[inst];
+    const int K = min(St.K, D.comp_cap);
     if (K < 2 || !D.edge_rule) return;
     const int t = b - T.tileV_pre[a];
     const int tx = t % D.vtx, ty = t / D.vtx;
     const int Lx = D.Lx, Ly = D.Ly;
-    // every lane takes part in the shuffles; lanes past the last column read
-    // the last column and emit nothing
-    const int x = tx * VW + lane;
-    const bool valid = x < Lx;
-    const int xc = valid ? x : Lx - 1;
-    const int xm = xc == 0 ? Lx - 1 : xc - 1, xp = xc + 1 == Lx ? 0 : xc + 1;
-    const bool el = lane == 0, er = lane == 31 || xc + 1 == Lx;
-    const int2* cq = P.cq[S.slot ^ 1] + D.comp_off;
+    const int x0 = tx * VW, y0 = ty * VH;
+    const int ncols = min(VW, Lx - x0), nrows = min(VH, Ly - y0);
+    const int2* cq = P.cq[St.slot ^ 1] + D.comp_off;
     const int* own = P.owners + D.site_off;
     const long long MX = (long long)Q * Lx, MY = (long long)Q * Ly, HX = MX / 2, HY = MY / 2;
+    int* S = s_own[warp];
     unsigned long long* list = s_list[warp];
-    const int y0 = ty * VH, y1 = min(y0 + VH, Ly);
-    auto row = [&](int y) { return own + (long long)(y >= Ly ? y - Ly : y) * Lx; };
-    // rows y-1 and y in registers, row y+1 loaded one iteration ahead
-    VRow rm = vrow_share(vrow_load(row(y0 == 0 ? Ly - 1 : y0 - 1), xc, xm, xp, el, er), el, er);
-    VRow r0 = vrow_share(vrow_load(row(y0), xc, xm, xp, el, er), el, er);
-    VRow nx = vrow_load(row(y0 + 1), xc, xm, xp, el, er);
+
+    // stage rows y0-1 .. y0+nrows and columns x0-1 .. x0+ncols (both periodic):
+    // staged row r holds lattice row y0-1+r, column c lattice column x0+c at
+    // S[r * VS + 4 + c]; a full-width tile whose rows start on 16-byte
+    // boundaries copies its 32 columns 16 bytes per lane, the halo 4 bytes
+    auto wrap_row = [&](int y) { return y < 0 ? y + Ly : (y >= Ly ? y - Ly : y); };
+    const bool vec = ncols == VW && ((D.site_off | Lx) & 3) == 0;
+    if (vec) {
+        const int c4 = (lane & 7) * 4;
+        for (int r = lane >> 3; r < nrows + 2; r += 4)
+            cp_async16(S + r * VS + 4 + c4, own + (long long)wrap_row(y0 - 1 + r) * Lx + x0 + c4);
+        const int xl = x0 == 0 ? Lx - 1 : x0 - 1, xr = x0 + VW == Lx ? 0 : x0 + VW;
+        for (int r = lane; r < nrows + 2; r += 32) {
+            const int* row = own + (long long)wrap_row(y0 - 1 + r) * Lx;
+            cp_async4(S + r * VS + 3, row + xl);
+            cp_async4(S + r * VS + 4 + VW, row + xr);
+        }
+    } else {
+        for (int r = 0; r < nrows + 2; ++r) {
+            const int* row = own + (long long)wrap_row(y0 - 1 + r) * Lx;
+            for (int c = lane - 1; c <= ncols; c += 32) {
+                const int xx = x0 + c < 0 ? x0 + c + Lx : (x0 + c >= Lx ? x0 + c - Lx : x0 + c);
+                cp_async4(S + r * VS + 4 + c, row + xx);
+            }
+        }
+    }
+    asm volatile("cp.async.wait_all;\n" ::: "memory");
+    __syncwarp();
+
+    // lanes past the last column read the last column and emit nothing
+    const bool valid = lane < ncols;
+    const int x = x0 + lane;
+    const int* sc = S + 4 + min(lane, ncols - 1);
+    // rows y-1 and y in registers (columns x-1, x, x+1), row y+1 read per step
+    int um = sc[-1], u0 = sc[0], up = sc[1];
+    int om = sc[VS - 1], o0 = sc[VS], op = sc[VS + 1];
     int n = 0;   // keys in the warp's list (warp-uniform)
-    for (int y = y0; y < y1; ++y) {
-        const VRow rp = vrow_share(nx, el, er);
-        if (y + 1 < y1) nx = vrow_load(row(y + 2), xc, xm, xp, el, er);
+    for (int ri = 0; ri < nrows; ++ri) {
+        const int y = y0 + ri;
+        const int* sd = sc + (ri + 2) * VS;
+        const int dm = sd[-1], d0 = sd[0], dp = sd[1];
         // the frame in counter-clockwise order from +x; f[8] = the site itself
         int f[9];
-        f[0] = r0.r; f[1] = rp.r; f[2] = rp.c; f[3] = rp.l;
-        f[4] = r0.l; f[5] = rm.l; f[6] = rm.c; f[7] = rm.r;
-        f[8] = r0.c;
+        f[0] = op; f[1] = dp; f[2] = d0; f[3] = dm;
+        f[4] = om; f[5] = um; f[6] = u0; f[7] = up;
+        f[8] = o0;
         // colour changes around the frame; members beyond a wall (owner
         // OWN_OUTSIDE) leave it, obstacles keep their MAXLINK colour
         int prev = OWN_OUTSIDE;
@@ -796,8 +804,8 @@ __global__ __launch_bounds__(32 * LINK_WARPS) void k_links_vertex(Pools P, StepT
             }
             n += __shfl_sync(0xffffffffu, inc, 31);
         }
-        rm = r0;
-        r0 = rp;
+        um = om; u0 = o0; up = op;
+        om = dm; o0 = d0; op = dp;
     }
     __syncwarp();
     flush_link_list(list, n, lane, P, D, inst);
