@@ -196,6 +196,37 @@ def test_centroid_closed_form_discs_on_grid_points():
             assert tuple(cq[0]) == (int(round(Q * cx)) % (Q * L), int(round(Q * cy)) % (Q * L))
 
 
+def test_centroid_exact_half_rounds_up():
+    """A 64 x 32 block with its corner (63, 31) moved to (64, 0): n = 2048,
+    Sx = 32 * 2016 - 63 + 64 = 64513 and Sy = 64 * 496 - 31 = 31713 about the
+    first site (0, 0), so 1024 Sx / n = 32256.5 and 1024 Sy / n = 15856.5:
+    both exact halves, rounded up."""
+    fg = np.zeros((80, 160), dtype=bool)
+    fg[:32, :64] = True
+    fg[31, 63] = False
+    fg[0, 64] = True
+    lab, K = O.label_components(fg)
+    assert K == 1
+    assert O.centroids_q10(lab, K).tolist() == [[32257, 15857]]
+
+
+@pytest.mark.parametrize("axis", [0, 1])
+def test_bar_longer_than_half_a_bounded_axis_has_plain_centre(axis):
+    """Walls across the bar's axis, sites 1..8 of a 10-site axis: the
+    displacements from the first site are plain (0..7), not minimum images
+    (which would fold 5, 6, 7 to -5, -4, -3), so the centre is the plain mean
+    4.5."""
+    fg = np.zeros((10, 4), dtype=bool)
+    fg[1:9, 2] = True
+    per = (True, False)
+    if axis == 0:
+        fg, per = fg.T.copy(), (False, True)
+    lab, K = O.label_components(fg, 4, per)
+    assert K == 1
+    c = O.centroids_q10(lab, K, per).tolist()[0]
+    assert c[1 - axis] == 2 * Q and c[axis] == Q * 9 // 2
+
+
 def test_centroid_within_half_unit_of_plain_mean():
     """Away from the seams the centroid is the plain mean of coordinates; near a
     seam, rolling the lattice to move the bubble away gives the same answer."""
@@ -416,6 +447,35 @@ def test_edges_differ_from_delaunay_only_near_degenerate_quads():
                 assert (opp[0], opp[1]) in got, (trial, e, opp)
         if len(edges) == 3 * K:
             assert len(got) == 3 * K, trial
+
+
+def test_links_translation_covariance_across_seams():
+    """Rolling the owner map by whole sites and moving every centre with it
+    leaves the link set unchanged, also where a four-colour plaquette's centres
+    straddle a seam (the plaquette test unwraps them around one corner).
+    Centres near a square lattice make four-cell junctions, so four-colour
+    plaquettes are common."""
+    rng = np.random.default_rng(31)
+    a, m = 8, 5
+    L = a * m
+    seen_four = 0
+    for trial in range(4):
+        pts = [(int((i * a + a / 2 + rng.uniform(-0.3, 0.3)) * Q), int((j * a + a / 2 + rng.uniform(-0.3, 0.3)) * Q))
+               for j in range(m) for i in range(m)]
+        cq = np.array(pts, dtype=np.int64)
+        own = O.owners_bruteforce(cq, L, L)
+        A = own
+        B = np.roll(A, -1, 1)
+        C = np.roll(B, -1, 0)
+        D = np.roll(A, -1, 0)
+        seen_four += int(((A != B) & (A != C) & (A != D) & (B != C) & (B != D) & (C != D)).sum())
+        E = O.delaunay_edges(own, cq)
+        for _ in range(6):
+            sx, sy = (int(v) for v in rng.integers(0, L, size=2))
+            own2 = np.roll(np.roll(own, sy, axis=0), sx, axis=1)
+            cq2 = (cq + Q * np.array([sx, sy], dtype=np.int64)) % (Q * L)
+            assert O.delaunay_edges(own2, cq2).tolist() == E.tolist(), (trial, sx, sy)
+    assert seen_four >= 10
 
 
 def test_every_cell_connected_on_generic_configurations():
@@ -639,6 +699,68 @@ def _events(past, now, K):
     inv = np.arange(K, dtype=np.int32)
     fl = O.flips(_keys(past), _keys(now), phi, inv)
     return fl, O.classify_events(_keys(past), _keys(now), phi, inv, fl["active"])
+
+
+def test_centroid_match_radius_is_inclusive():
+    """Centres exactly 3 sites apart match within radius 3 and not within 2."""
+    p = np.array([[Q * 2, Q * 2]], dtype=np.int64)
+    n = np.array([[Q * 5, Q * 2]], dtype=np.int64)
+    assert O.match_centroid(p, n, 16, 16, radius=3)[0].tolist() == [0]
+    assert O.match_centroid(p, n, 16, 16, radius=2)[0].tolist() == [-1]
+
+
+def test_global_trigger_with_one_kind_of_flip():
+    """A link that only arises (or only breaks) between matched labels still
+    sets the global trigger and the local trigger of its ends."""
+    ident = np.arange(3, dtype=np.int32)
+    fl = O.flips(O.make_keys([0], [1]), O.make_keys([0, 1], [1, 2]), ident, ident)
+    assert fl["breaking"].size == 0 and fl["arising"].tolist() == O.make_keys([1], [2]).tolist()
+    assert fl["global_trigger"] == 1 and fl["active"].tolist() == [0, 1, 1]
+    fl = O.flips(O.make_keys([0, 1], [1, 2]), O.make_keys([0], [1]), ident, ident)
+    assert fl["arising"].size == 0 and fl["breaking"].tolist() == O.make_keys([1], [2]).tolist()
+    assert fl["global_trigger"] == 1 and fl["active"].tolist() == [0, 1, 1]
+
+
+def _wheel(missing=()):
+    """Hub 0 joined to rim 1..6, rim joined in a cycle: each rim link's ends
+    share only the hub (boundary links, so the rim labels are boundary points);
+    each spoke's ends share two rim labels (the hub is not a boundary point)."""
+    pairs = [(0, i) for i in range(1, 7)] + [(i, i % 6 + 1) for i in range(1, 7)]
+    pairs = [p for p in pairs if p not in missing]
+    return O.make_keys([p[0] for p in pairs], [p[1] for p in pairs])
+
+
+def test_event_classes_on_a_wheel_by_counting():
+    """Same wheel before and after, identity match, active labels given:
+    {hub, 1}: 1 is a boundary point whose only active neighbour (the hub) is
+    not one, and the hub is not a boundary point -- no boundary event, and
+    one active neighbour each -- no bulk event. {hub, 1, 2}: 1 and 2 are
+    active boundary points linked to each other -- boundary events; every
+    active label has two active neighbours -- still no bulk event (three are
+    needed)."""
+    E = _wheel()
+    ident = np.arange(7, dtype=np.int32)
+    bp = O.EV_BPOINT_NOW | O.EV_BPOINT_PAST
+    act = np.zeros(7, np.uint8)
+    act[[0, 1]] = 1
+    f = O.classify_events(E, E, ident, ident, act)
+    assert f.tolist() == [O.EV_ACTIVE, O.EV_ACTIVE | bp, 0, 0, 0, 0, 0]
+    act[2] = 1
+    f = O.classify_events(E, E, ident, ident, act)
+    be = O.EV_ACTIVE | bp | O.EV_BOUNDARY
+    assert f.tolist() == [O.EV_ACTIVE, be, be, 0, 0, 0, 0]
+
+
+def test_bulk_event_needs_three_in_one_triangulation():
+    """Past wheel without the spoke 0-2, now the whole wheel, active {hub, 1, 2}:
+    the hub has two active neighbours now and one in the past, label 2 two now
+    and one in the past. Three in the two triangulations together, but never
+    three in one: no bulk event."""
+    ident = np.arange(7, dtype=np.int32)
+    act = np.zeros(7, np.uint8)
+    act[[0, 1, 2]] = 1
+    f = O.classify_events(_wheel(missing=((0, 2),)), _wheel(), ident, ident, act)
+    assert not any(int(v) & O.EV_BULK for v in f)
 
 
 def test_events_boundary_link_breaking():
@@ -1053,9 +1175,27 @@ def test_obstacles_are_never_bubbles_owners_or_links():
     d2 = O.Detector(L, L, voronoi="brute", obstacles=obst, walls=(True, False))
     r2 = d2.push(F)
     assert r2["K"] == 2                      # walls in x and the obstacle: two bars
-    a, b = O.split_keys(r2["edges"])
-    assert (a >= 0).all() and (b >= 0).all()
+    for res in (r, r2):
+        a, b = O.split_keys(res["edges"])
+        assert ((a >= 0) & (a < b) & (b < res["K"])).all()
     assert (r2["owners"][:, 6] == O.OBSTACLE).all()
+
+
+def test_obstacle_corner_breaks_adjacency_and_plaquette():
+    """4 x 4 box with walls on both axes, cells 0 (top left), 1 (top right), 2
+    (bottom left), 3 (bottom right) and an obstacle at (2, 2): the plaquette at
+    (1, 1) carries 0, 1, the obstacle and 2 -- four distinct values, but not
+    four labels, so it gives no diagonal -- and no pair touching the obstacle
+    is linked. What remains are the four side adjacencies."""
+    X = O.OBSTACLE
+    own = np.array([[0, 0, 1, 1],
+                    [0, 0, 1, 1],
+                    [2, 2, X, 3],
+                    [2, 2, 3, 3]], dtype=np.int32)
+    cq = np.array([[Q // 2, Q // 2], [Q * 5 // 2, Q // 2], [Q // 2, Q * 5 // 2], [Q * 5 // 2, Q * 5 // 2]],
+                  dtype=np.int64)
+    E = O.delaunay_edges(own, cq, (False, False))
+    assert E.tolist() == O.make_keys([0, 0, 1, 2], [1, 2, 3, 3]).tolist()
 
 
 @pytest.mark.parametrize("periodic", [(False, True), (True, False), (False, False)])
