@@ -44,7 +44,7 @@ def test_status_strings(lib):
 @pytest.mark.parametrize("field,value", [("Lx", 0), ("Ly", -3), ("connectivity", 6), ("polarity", 0),
                                          ("Lx", 1 << 21), ("max_components", -1), ("events", 2),
                                          ("match_rule", 7), ("match_radius", -1), ("edge_rule", 3),
-                                         ("walls", 4)])
+                                         ("walls", 4), ("walls", -1), ("max_edges", -1), ("polarity", 2)])
 def test_invalid_config_is_rejected_without_touching_the_gpu(lib, field, value):
     cfg = vd.vd_config_init(16, 16)
     setattr(cfg, field, value)
@@ -72,6 +72,11 @@ def test_centre_match_needs_a_radius_and_walls_double_the_limit(lib):
     cfg = vd.vd_config_init(16, 16, match_rule=vd.VD_MATCH_CENTROID, match_radius=0)
     assert lib.vd_create(C.byref(cfg), C.byref(h)) == vd.VD_ERR_INVALID
     cfg = vd.vd_config_init((1 << 20) + 1, 1, walls=vd.VD_WALL_X)
+    assert lib.vd_create(C.byref(cfg), C.byref(h)) == vd.VD_ERR_INVALID
+    cfg = vd.vd_config_init(16, 16, match_rule=vd.VD_MATCH_CENTROID, match_radius=(1 << 20) + 1)
+    assert lib.vd_create(C.byref(cfg), C.byref(h)) == vd.VD_ERR_INVALID
+    # each axis within its limit, but Lx * Ly sites would not fit a 32-bit site index
+    cfg = vd.vd_config_init(50000, 50000)
     assert lib.vd_create(C.byref(cfg), C.byref(h)) == vd.VD_ERR_INVALID
     cfg = vd.vd_config_init((1 << 20) + 1, 1)
     st = lib.vd_create(C.byref(cfg), C.byref(h))
