@@ -37,6 +37,7 @@ from .detect import (  # noqa: F401
     plaquette_diagonal,
     rdiv,
     split_keys,
+    wide_components,
     vertex_edges,
     wrap,
     wrap_ax,

@@ -206,6 +206,37 @@ def centroids_q10(labels: np.ndarray, K: int, periodic=(True, True)) -> np.ndarr
     return np.stack([cx, cy], axis=1).astype(np.int64)
 
 
+def wide_components(labels: np.ndarray, K: int, periodic=(True, True)) -> np.ndarray:
+    """Components too wide for a compact centre on the torus (Section 3.1 with
+    the minimum-image reading of ``component_sums``): along a periodic axis the
+    minimum-image displacements of the sites from the first site span half the
+    period or more (one that winds around the torus spans all of it). The
+    centroid formula still applies to them, but its result is then a
+    convention, not the centre of a blob. Displacements along a bounded axis
+    are plain, so walls never make a component wide. Returns bool [K].
+    """
+    Ly, Lx = labels.shape
+    out = np.zeros(K, dtype=bool)
+    if K == 0:
+        return out
+    flat = labels.ravel().astype(np.int64)
+    idx = np.flatnonzero(flat >= 0)
+    lab = flat[idx]
+    first = np.full(K, Lx * Ly, dtype=np.int64)
+    np.minimum.at(first, lab, idx)
+    axes = ((idx % Lx, first % Lx, Lx, periodic[0]), (idx // Lx, first // Lx, Ly, periodic[1]))
+    for c, c_r, L, per in axes:
+        if not per:
+            continue
+        d = wrap(c - c_r[lab], L)
+        lo = np.full(K, L, dtype=np.int64)
+        hi = np.full(K, -L, dtype=np.int64)
+        np.minimum.at(lo, lab, d)
+        np.maximum.at(hi, lab, d)
+        out |= 2 * (hi - lo + 1) >= L
+    return out
+
+
 # ----------------------------------------------------------------------------
 # Section 3.2.1: digital Voronoi tessellation
 # ----------------------------------------------------------------------------

@@ -227,6 +227,36 @@ def test_bar_longer_than_half_a_bounded_axis_has_plain_centre(axis):
     assert c[1 - axis] == 2 * Q and c[axis] == Q * 9 // 2
 
 
+@pytest.mark.parametrize("L,length,wide", [(10, 4, False), (10, 5, True), (10, 10, True),
+                                            (11, 5, False), (11, 6, True)])
+def test_wide_components_by_extent(L, length, wide):
+    """A bar of `length` sites on a periodic ring of L sites is wide exactly
+    when 2 * length >= L (the full ring winds around the torus); a bar along
+    the other, bounded, axis is never wide, whatever its length."""
+    fg = np.zeros((3, L), dtype=bool)
+    fg[1, :length] = True
+    lab, K = O.label_components(fg)
+    assert K == 1 and O.wide_components(lab, K).tolist() == [wide]
+    lab, K = O.label_components(fg.T.copy(), 4, (True, False))
+    assert K == 1 and O.wide_components(lab, K, (True, False)).tolist() == [False]
+
+
+def test_wide_components_of_discs_and_a_winding_band():
+    """Discs of radius 3 on a 32 x 32 torus are never wide, also across the
+    seams; a diagonal band that winds around the torus is."""
+    fg = np.zeros((32, 32), dtype=bool)
+    y, x = np.mgrid[0:32, 0:32]
+    for cx, cy in ((0, 0), (16, 31), (8, 12)):
+        dx = (x - cx + 16) % 32 - 16
+        dy = (y - cy + 16) % 32 - 16
+        fg |= dx * dx + dy * dy <= 9
+    lab, K = O.label_components(fg)
+    assert K == 3 and not O.wide_components(lab, K).any()
+    band = ((x - y) % 32) < 2
+    lab, K = O.label_components(band)
+    assert K == 1 and O.wide_components(lab, K).tolist() == [True]
+
+
 def test_centroid_within_half_unit_of_plain_mean():
     """Away from the seams the centroid is the plain mean of coordinates; near a
     seam, rolling the lattice to move the bubble away gives the same answer."""
