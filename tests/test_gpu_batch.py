@@ -9,6 +9,8 @@
 """
 from __future__ import annotations
 
+import os
+
 import numpy as np
 import pytest
 
@@ -19,6 +21,9 @@ torch = pytest.importorskip("torch")
 import oracle as O  # noqa: E402
 from paper_1607_00908_gb300 import inputs as I  # noqa: E402
 from paper_1607_00908_gb300 import vd  # noqa: E402
+from tests.oracle_digest import batched_frames, oracle_digests, site_digests  # noqa: E402
+
+FULL = os.environ.get("VD_FULL", "0") == "1"
 
 
 def check(b, i, r, tag):
@@ -245,4 +250,36 @@ def test_batch_with_mixed_options():
         for i in range(n):
             r = refs[i].push(seqs[i][f])
             check(b, i, r, f"mixed inst {i} frame {f}")
+    b.close()
+
+
+@pytest.mark.skipif(not FULL, reason="the full batched workload takes minutes of oracle time: VD_FULL=1")
+def test_batched_workload_every_instance_and_frame():
+    """The batched workload at full size -- 256 instances of 256^2 ... 2048^2
+    smoothed noise, 8 frames each, one push per frame -- against the oracle
+    for every instance and frame. The oracle runs in spawned worker processes
+    (one instance per task) and returns per-site arrays as digests."""
+    import multiprocessing as mp
+    specs = I.batch_instances()
+    with mp.get_context("spawn").Pool(min(16, os.cpu_count() or 1)) as pool:
+        want = pool.map(oracle_digests, specs)
+    b = vd.Batch([(L, L) for L, _, _ in specs])
+    gens = [batched_frames(spec) for spec in specs]
+    for f in range(8):
+        dev = [torch.from_numpy(next(g)).cuda() for g in gens]
+        b.push(dev)
+        for i, spec in enumerate(specs):
+            w = want[i][f]
+            tag = f"instance {i} ({spec[0]}^2) frame {f}"
+            K, _, _ = b.counts(i)
+            assert K == w["K"], tag
+            assert site_digests(b.labels(i), b.owners(i)) == (w["labels"], w["owners"]), tag
+            assert np.array_equal(b.centroids(i), w["centroids"]), tag
+            assert np.array_equal(b.edges(i), w["edges"]), tag
+            ch = b.changes(i)
+            for k in ("K_prev", "n_matched"):
+                assert ch[k] == w[k], (tag, k)
+            for k in ("breaking", "breaking_prev", "arising", "active"):
+                assert np.array_equal(ch[k], w[k]), (tag, k)
+        del dev
     b.close()
