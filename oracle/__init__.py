@@ -32,7 +32,6 @@ from .detect import (  # noqa: F401
     match_overlap,
     orient2d,
     owners,
-    owners_at_q10,
     owners_bruteforce,
     plaquette_diagonal,
     rdiv,

@@ -430,27 +430,6 @@ def delaunay_edges(owner: np.ndarray, cq: np.ndarray, periodic=(True, True)) -> 
 FRAME = ((1, 0), (1, 1), (0, 1), (-1, 1), (-1, 0), (-1, -1), (0, -1), (1, -1))
 
 
-def owners_at_q10(cq: np.ndarray, Lx: int, Ly: int, px: np.ndarray, py: np.ndarray,
-                  periodic=(True, True)) -> np.ndarray:
-    """Owner of arbitrary Q10 points: nearest centre by exact minimum-image
-    squared distance, ties to the smallest label (the Section 3.2.1 rule away
-    from the lattice sites)."""
-    px = np.asarray(px, dtype=np.int64)
-    py = np.asarray(py, dtype=np.int64)
-    out = np.full(px.shape[0], -1, dtype=np.int64)
-    K = cq.shape[0]
-    if K == 0 or px.size == 0:
-        return out
-    cx = cq[:, 0].astype(np.int64)
-    cy = cq[:, 1].astype(np.int64)
-    chunk = max(1, 2_000_000 // K)
-    for s in range(0, px.shape[0], chunk):
-        d2 = sq_dist_q10(px[s:s + chunk, None], py[s:s + chunk, None], cx[None, :], cy[None, :], Lx, Ly,
-                         periodic)
-        out[s:s + chunk] = np.argmin(d2, axis=1)
-    return out
-
-
 def _shifted(owner: np.ndarray, dx: int, dy: int, periodic=(True, True)) -> np.ndarray:
     """owner at (x+dx, y+dy); OUTSIDE where that crosses a wall."""
     Ly, Lx = owner.shape

@@ -257,6 +257,16 @@ def test_wide_components_of_discs_and_a_winding_band():
     assert K == 1 and O.wide_components(lab, K).tolist() == [True]
 
 
+def test_wide_bar_centroid_follows_the_first_site():
+    """A bar over sites 0..5 of a 10-site ring is wide: from its first site
+    x = 0 the displacements are 0, 1, 2, 3, 4 and wrap(5) = -5, so Sx = 5 and
+    cx = rdiv(1024 * 5, 6) = 853 (measured from x = 5 it would be 2.5 sites)."""
+    fg = np.zeros((3, 10), dtype=bool)
+    fg[1, :6] = True
+    lab, K = O.label_components(fg)
+    assert K == 1 and O.centroids_q10(lab, K).tolist() == [[853, Q]]
+
+
 def test_centroid_within_half_unit_of_plain_mean():
     """Away from the seams the centroid is the plain mean of coordinates; near a
     seam, rolling the lattice to move the bubble away gives the same answer."""
@@ -731,6 +741,46 @@ def _events(past, now, K):
     return fl, O.classify_events(_keys(past), _keys(now), phi, inv, fl["active"])
 
 
+def test_breaking_prev_stays_aligned_with_breaking():
+    """Phi reverses four labels: past links 0-1 and 2-3 become 3-2 and 1-0 and
+    both break. Sorted by now-key the breaking list is (0,1), (2,3); the past
+    keys follow it pair by pair: (2,3), (0,1)."""
+    phi = np.array([3, 2, 1, 0], dtype=np.int32)
+    inv = np.array([3, 2, 1, 0], dtype=np.int32)
+    fl = O.flips(O.make_keys([0, 2], [1, 3]), np.zeros(0, np.uint64), phi, inv)
+    assert fl["breaking"].tolist() == O.make_keys([0, 2], [1, 3]).tolist()
+    assert fl["breaking_prev"].tolist() == O.make_keys([2, 0], [3, 1]).tolist()
+
+
+def test_centroid_match_with_walls_in_both_directions():
+    """Past centre at x = 0.25 of a 10-site axis, now centres at 9.75 and 1.5,
+    radius 2. On the torus 9.75 is 0.5 away through the seam and matches;
+    with walls only the plain distances count, in both directions of the
+    mutual test, and 1.5 (1.25 away) matches."""
+    p = np.array([[Q // 4, Q]], dtype=np.int64)
+    n = np.array([[Q * 9 + 3 * Q // 4, Q], [3 * Q // 2, Q]], dtype=np.int64)
+    assert O.match_centroid(p, n, 10, 3, radius=2)[0].tolist() == [0]
+    assert O.match_centroid(p, n, 10, 3, radius=2, periodic=(False, True))[0].tolist() == [1]
+
+
+def test_detector_passes_its_options():
+    """The whole-frame detector applies its options: 8-connectivity joins two
+    diagonal sites, polarity -1 takes the sites below the threshold, and the
+    centre match uses the radius it is given."""
+    F = np.zeros((8, 8), dtype=np.float32)
+    F[2, 2] = F[3, 3] = 1.0
+    assert O.Detector(8, 8).push(F)["K"] == 2
+    assert O.Detector(8, 8, connectivity=8).push(F)["K"] == 1
+    assert O.Detector(8, 8, polarity=-1).push(F)["K"] == 1          # the background, one piece
+    G = np.zeros((32, 32), dtype=np.float32)
+    G[10:13, 10:13] = 1.0
+    H = np.roll(G, 3, axis=1)                                        # the block moves 3 sites
+    for radius, want in ((4, [0]), (2, [-1])):
+        d = O.Detector(32, 32, match="centroid", match_radius=radius)
+        d.push(G)
+        assert d.push(H)["phi"].tolist() == want, radius
+
+
 def test_centroid_match_radius_is_inclusive():
     """Centres exactly 3 sites apart match within radius 3 and not within 2."""
     p = np.array([[Q * 2, Q * 2]], dtype=np.int64)
@@ -1075,6 +1125,20 @@ def test_vertex_rule_keeps_one_site_bands_apart(a, b, M, L):
         cq = rng.integers(0, Q * L, size=(M, 2)).astype(np.int64)
         got = sorted(zip(*[v.tolist() for v in O.split_keys(O.vertex_edges(own, cq))]))
         assert got == ring
+
+
+def test_vertex_rule_reads_nothing_at_an_obstacle_site():
+    """The three-cell junction with its vertex site (1, 1) made an obstacle:
+    the obstacle is never an end of a link, and the links read at the other
+    vertex sites are unchanged."""
+    own = np.array([[0, 0, 1, 1], [0, 0, 1, 1], [2, 2, 2, 2], [2, 2, 2, 2]], dtype=np.int32)
+    cq = np.array([[512, 512], [Q * 2 + 512, 512], [Q + 512, Q * 2 + 512]], dtype=np.int64)
+    own[1, 1] = O.OBSTACLE
+    assert int(O.frame_gaps(own)[1, 1]) >= 3
+    E = O.vertex_edges(own, cq)
+    a, b = O.split_keys(E)
+    assert ((a >= 0) & (a < b) & (b < 3)).all()
+    assert E.tolist() == O.make_keys([0, 0, 1], [1, 2, 2]).tolist()
 
 
 @pytest.mark.parametrize("centres,diagonal", [
