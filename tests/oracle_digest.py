@@ -13,9 +13,12 @@ import oracle as O
 from paper_1607_00908_gb300 import inputs as I
 
 
+def array_digest(a) -> str:
+    return hashlib.sha256(np.ascontiguousarray(a, dtype=np.int32).tobytes()).hexdigest()
+
+
 def site_digests(labels, owners):
-    return tuple(hashlib.sha256(np.ascontiguousarray(a, dtype=np.int32).tobytes()).hexdigest()
-                 for a in (labels, owners))
+    return array_digest(labels), array_digest(owners)
 
 
 def batched_frames(spec, n_frames: int = 8):
@@ -35,3 +38,18 @@ def oracle_digests(spec, n_frames: int = 8):
                         K_prev=r["K_prev"], n_matched=r["n_matched"], breaking=r["breaking"],
                         breaking_prev=r["breaking_prev"], arising=r["arising"], active=r["active"]))
     return out
+
+
+def oracle_sequence(task):
+    """Oracle over one simulation's frame sequence: `task` = (L, pool frames,
+    indices into the pool). Returns per-frame (K, links, breaking, arising)
+    and the final frame's label digest and flip lists."""
+    L, pool, seq = task
+    det = O.Detector(L, L)
+    counts = []
+    r = None
+    for j in seq:
+        r = det.push(pool[j])
+        counts.append((r["K"], len(r["edges"]), len(r["breaking"]), len(r["arising"])))
+    lab = array_digest(r["labels"]) if r is not None else None
+    return counts, lab, (r["breaking"] if r else None), (r["arising"] if r else None)

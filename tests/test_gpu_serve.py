@@ -9,6 +9,8 @@ own vd_push_frame context.
 """
 from __future__ import annotations
 
+import os
+
 import numpy as np
 import pytest
 
@@ -19,6 +21,9 @@ torch = pytest.importorskip("torch")
 from paper_1607_00908_gb300 import inputs as I  # noqa: E402
 from paper_1607_00908_gb300 import serve  # noqa: E402
 from paper_1607_00908_gb300 import vd  # noqa: E402
+from tests.oracle_digest import array_digest, oracle_sequence  # noqa: E402
+
+FULL = os.environ.get("VD_FULL", "0") == "1"
 
 
 def _setup(seed=3):
@@ -134,4 +139,65 @@ def test_served_options_equal_alone():
         assert np.array_equal(got["breaking"], ch["breaking"]), s
         assert np.array_equal(got["arising"], ch["arising"]), s
         assert np.array_equal(got["active"], ch["active"]), s
+    sv.close()
+
+
+@pytest.mark.skipif(not FULL, reason="the full served workload takes minutes of oracle time: VD_FULL=1")
+def test_served_workload_full_size():
+    """The served workload's 64 simulations (512^2 ... 4096^2, smoothed noise
+    and droplets) on a seeded Poisson trace of 500 arrivals, frames taken
+    from the shared pools in the served driver's order: every simulation's
+    per-frame counts and final labels and flip lists equal those run alone,
+    and for the first 8 simulations those of the oracle."""
+    import multiprocessing as mp
+    params = I.serve_sims()
+    sims = [(L, rec) for L, rec, _ in params]
+    host_pools = serve.make_pools([L for L, _ in sims], 4)
+    trace = serve.poisson_trace(len(sims), 2000.0, 0.25, 5)
+    seqs = [[] for _ in sims]
+    for _, s in trace:
+        seqs[s].append((len(seqs[s]) + s) % 4)
+    tasks = [(sims[s][0], host_pools[sims[s]], seqs[s]) for s in range(8)]
+    with mp.get_context("spawn").Pool(8) as pool:
+        oracle = pool.map(oracle_sequence, tasks)
+    dev_pools = {k: [torch.from_numpy(F).cuda() for F in v] for k, v in host_pools.items()}
+    del host_pools
+    # alone: one context per simulation
+    alone, finals = {}, {}
+    for s, (L, rec) in enumerate(sims):
+        det = vd.Detector(L, L)
+        for k, j in enumerate(seqs[s]):
+            det.push(dev_pools[(L, rec)][j])
+            ch = det.changes()
+            alone[(s, k)] = (ch["K"], ch["n_edges"], len(ch["breaking"]), len(ch["arising"]))
+        if seqs[s]:
+            finals[s] = (det.labels(), det.changes())
+        det.close()
+    # served, in trace order
+    sv = vd.Server([(L, L) for L, _ in sims], budget_bytes=40_000_000_000, max_batch=len(sims))
+    tickets, seen, count = {}, {}, [0] * len(sims)
+    for _, s in trace:
+        L, rec = sims[s]
+        tickets[sv.submit(s, dev_pools[(L, rec)][seqs[s][count[s]]])] = (s, count[s])
+        count[s] += 1
+        for d in sv.poll(wait=False):
+            seen[tickets[d[0]]] = d
+    while len(seen) < len(trace):
+        for d in sv.poll(wait=True):
+            seen[tickets[d[0]]] = d
+    for key, d in seen.items():
+        ticket, s, status, ts, td, K, E, nb, na = d
+        assert status == 0, key
+        assert (K, E, nb, na) == alone[key], (key, (K, E, nb, na), alone[key])
+    for s, (lab, ch) in finals.items():
+        assert np.array_equal(sv.labels(s), lab), s
+        got = sv.changes(s)
+        assert np.array_equal(got["breaking"], ch["breaking"]) and np.array_equal(got["arising"], ch["arising"]), s
+    for s in range(8):
+        counts, lab_digest, breaking, arising = oracle[s]
+        assert [alone[(s, k)] for k in range(len(seqs[s]))] == counts, s
+        if seqs[s]:
+            assert array_digest(finals[s][0]) == lab_digest, s
+            assert np.array_equal(finals[s][1]["breaking"], breaking), s
+            assert np.array_equal(finals[s][1]["arising"], arising), s
     sv.close()
