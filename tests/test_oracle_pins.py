@@ -367,6 +367,23 @@ def test_owner_tie_goes_to_smallest_label():
     assert O.owners(cq, Lx, Ly)[4, 4] == 3
 
 
+def test_owners_without_centres_are_minus_one():
+    """With no centre (no bubble) no site has an owner, in both the literal
+    definition and the k-d tree path."""
+    cq = np.zeros((0, 2), dtype=np.int64)
+    assert (O.owners_bruteforce(cq, 5, 4) == -1).all() and O.owners_bruteforce(cq, 5, 4).shape == (4, 5)
+    assert (O.owners(cq, 5, 4) == -1).all()
+
+
+def test_first_frame_reports_no_changes():
+    """The first frame has no past: no match, no flips, no trigger."""
+    F = I.smoothed_noise(48, 48, 2.5, seed=3)
+    r = O.Detector(48, 48, voronoi="brute", events=True).push(F)
+    assert r["K"] > 0 and r["global_trigger"] == 0 and r["K_prev"] == 0 and r["n_matched"] == 0
+    assert r["breaking"].size == r["arising"].size == r["breaking_prev"].size == 0
+    assert not r["active"].any() and (r["inv"] == -1).all()
+
+
 def test_owners_translation_covariance():
     rng = np.random.default_rng(8)
     Lx, Ly, K = 37, 29, 15
@@ -829,6 +846,34 @@ def test_event_classes_on_a_wheel_by_counting():
     f = O.classify_events(E, E, ident, ident, act)
     be = O.EV_ACTIVE | bp | O.EV_BOUNDARY
     assert f.tolist() == [O.EV_ACTIVE, be, be, 0, 0, 0, 0]
+
+
+def test_event_classes_follow_a_relabelling_of_the_now_frame():
+    """The wheel before and after, the now labels permuted by pi(i) = 6 - i
+    (Phi = pi): the flags of now label pi(i) are those label i gets under the
+    identity. The past neighbours are seen through Phi, so the hub (now 6)
+    still has two active past neighbours (pi(1) = 5 and pi(2) = 4), not
+    three."""
+    E = _wheel()
+    pi = np.array([6 - i for i in range(7)], dtype=np.int32)
+    a, b = O.split_keys(E)
+    E_now = O.make_keys(pi[a], pi[b])
+    ident = np.arange(7, dtype=np.int32)
+    act = np.zeros(7, np.uint8)
+    act[[0, 1, 2]] = 1
+    want = O.classify_events(E, E, ident, ident, act)
+    act_pi = np.zeros(7, np.uint8)
+    act_pi[pi[[0, 1, 2]]] = 1
+    inv = np.argsort(pi).astype(np.int32)
+    got = O.classify_events(E, E_now, pi, inv, act_pi)
+    assert got[pi].tolist() == want.tolist()
+    # no links now: a boundary event can only come from the past wheel, where
+    # rim labels 1 and 2 are linked boundary points, active as pi(1), pi(2)
+    act_pi[:] = 0
+    act_pi[pi[[1, 2]]] = 1
+    got = O.classify_events(E, np.zeros(0, np.uint64), pi, inv, act_pi)
+    be = O.EV_ACTIVE | O.EV_BPOINT_PAST | O.EV_BOUNDARY
+    assert got.tolist() == [0, 0, 0, 0, be, be, 0]
 
 
 def test_bulk_event_needs_three_in_one_triangulation():
