@@ -32,6 +32,7 @@ from .detect import (  # noqa: F401
     match_overlap,
     orient2d,
     owners,
+    owners_at_points,
     owners_bruteforce,
     plaquette_diagonal,
     rdiv,

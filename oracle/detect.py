@@ -286,6 +286,27 @@ def owners_bruteforce(cq: np.ndarray, Lx: int, Ly: int, sites=None, periodic=(Tr
     return out if sites is not None else out.reshape(Ly, Lx)
 
 
+def owners_at_points(cq: np.ndarray, Lx: int, Ly: int, px, py, periodic=(True, True)) -> np.ndarray:
+    """Voronoi colour of arbitrary points in 1/1024-site units (the colouring
+    rule of Section 3.2.1 applied to points that need not be lattice sites,
+    such as the inner-frame points of Section 3.2.2): the label of the nearest
+    centre by exact int64 squared distance, minimum image on periodic axes,
+    ties to the smallest label; -1 when there are no centres."""
+    px = np.asarray(px, dtype=np.int64).ravel()
+    py = np.asarray(py, dtype=np.int64).ravel()
+    K = cq.shape[0]
+    out = np.full(px.shape[0], -1, dtype=np.int32)
+    if K == 0 or px.size == 0:
+        return out
+    cx = cq[:, 0].astype(np.int64)
+    cy = cq[:, 1].astype(np.int64)
+    chunk = max(1, 4_000_000 // K)
+    for s in range(0, px.shape[0], chunk):
+        d2 = sq_dist_q10(px[s:s + chunk, None], py[s:s + chunk, None], cx[None, :], cy[None, :], Lx, Ly, periodic)
+        out[s:s + chunk] = np.argmin(d2, axis=1)
+    return out
+
+
 def owners(cq: np.ndarray, Lx: int, Ly: int, workers: int = 1) -> np.ndarray:
     """Same result as ``owners_bruteforce``, with a k-d tree as the search step.
 
@@ -480,9 +501,11 @@ def vertex_edges(owner: np.ndarray, cq: np.ndarray, periodic=(True, True)) -> np
     * second neighbour k+e1+e2 is linked to k when its colour differs from
       k's, C(k+e2) != C(k+e1-e2), C(k+e2) != C(k+e1) (the short diagonal),
       and the inner-frame point -- read as the centre of the plaquette,
-      k + (e1+e2)/2 -- takes k's colour or the neighbour's; its colour is the
-      one, among the colours at the plaquette's four corners, whose centre is
-      nearest (exact squared distance, ties to the smallest label).
+      k + (e1+e2)/2 -- takes k's colour or the neighbour's. Its colour C(a_k)
+      is its Voronoi colour, as for every point of the stencil: the nearest
+      centre over all centres, by the exact rule of Section 3.2.1
+      (``owners_at_points``). A centre whose cell holds the plaquette centre
+      but no lattice site therefore blocks the diagonal.
 
     Walls truncate the frame (neighbours beyond them leave it) and obstacle
     sites carry the MAXLINK colour: neither is ever linked, nor is a site that
@@ -513,17 +536,8 @@ def vertex_edges(owner: np.ndarray, cq: np.ndarray, periodic=(True, True)) -> np
         px = (Q * xs + (Q // 2) * (e1x + e2x)) % (Q * Lx)
         py = (Q * ys + (Q // 2) * (e1y + e2y)) % (Q * Ly)
         kk, xx = own[ys, xs], X[ys, xs]
-        # colour of the inner-frame point: the nearest centre among the colours
-        # at the plaquette's four corners (k, k+e1, k+e1+e2, k+e2)
-        cand = np.stack([kk, A1[ys, xs], xx, A2[ys, xs]], axis=1)
-        ok_c = cand >= 0
-        cl = np.where(ok_c, cand, 0)
-        d2 = sq_dist_q10(px[:, None], py[:, None], cq[cl, 0].astype(np.int64), cq[cl, 1].astype(np.int64),
-                         Lx, Ly, periodic)
-        big = np.iinfo(np.int64).max
-        d2 = np.where(ok_c, d2, big)
-        best = d2.min(axis=1)
-        ca = np.where(ok_c & (d2 == best[:, None]), cand, big).min(axis=1)
+        # colour of the inner-frame point: its exact Voronoi owner
+        ca = owners_at_points(cq, Lx, Ly, px, py, periodic)
         sel = (ca == kk) | (ca == xx)
         keys.append(make_keys(kk[sel], xx[sel]).astype(np.int64))
     allk = np.concatenate(keys) if keys else np.zeros(0, dtype=np.int64)

@@ -1046,6 +1046,58 @@ def test_frame_gaps_and_vertex_links_at_a_three_cell_junction():
     assert E.tolist() == O.make_keys([0, 0, 1], [1, 2, 2]).tolist()
 
 
+def test_inner_frame_point_takes_its_exact_voronoi_colour():
+    """The fifth second-neighbour condition of Section 3.2.2 reads C(a_k), the
+    colour of an inner-frame point, which is a point of the stencil like any
+    other: its colour is the Voronoi colour of the point, i.e. the nearest
+    centre over all centres. Hand-built 16 x 16 box with walls on both axes,
+    so that the four cells meet only once (1/1024-site units):
+    centres A, B, C, D sit 0.1 site inside the corners (8,8), (9,8), (9,9),
+    (8,9) of one plaquette and E exactly at its centre p = (8.5, 8.5).
+    Squared distances to the corner site (8,8): A 2*110^2 = 24,200, E
+    2*512^2 = 524,288, so every corner site (and every other site, each at
+    least 512*sqrt(2) from E) is owned by one of A-D: E owns no site. Its own
+    point p is E's (distance 0). Frame of (8,8), counter-clockwise from +x:
+    B C D D A A A B -> 4 colour changes, a vertex site; the diagonal A-C
+    passes conditions 1-4 there (C != A, C(spy) = D != C(smypx) = B,
+    D != B), and condition 5 reads C(p) = E, neither A nor C: no link. The
+    same holds for the diagonal B-D (read at (9,8) and (8,9)) and for A-C read
+    from (9,9). A reading that colours p only among the four corner colours
+    would give it A (2*402^2 = 323,208 against 2*412^2 = 339,488 for B, C, D)
+    and link A-C. The four sides are first-neighbour links, and the four
+    sites of the plaquette are the only vertex sites."""
+    A, B, C, D, E = 0, 1, 2, 3, 4
+    box = (False, False)
+    cq = np.array([[8302, 8302], [9116, 8292], [9116, 9116], [8292, 9116], [8704, 8704]], dtype=np.int64)
+    own = O.owners_bruteforce(cq, 16, 16, periodic=box)
+    assert not (own == E).any()
+    assert [int(own[8, 8]), int(own[8, 9]), int(own[9, 9]), int(own[9, 8])] == [A, B, C, D]
+    gaps = O.frame_gaps(own, box)
+    assert int(gaps[8, 8]) == 4
+    assert np.argwhere(gaps >= 3).tolist() == [[8, 8], [8, 9], [9, 8], [9, 9]]
+    assert O.owners_at_points(cq, 16, 16, [8704], [8704], box).tolist() == [E]
+    keys = O.vertex_edges(own, cq, box)
+    assert keys.tolist() == np.sort(O.make_keys([A, B, C, A], [B, C, D, D])).tolist()
+
+
+def test_points_take_the_owner_of_the_bruteforce_definition():
+    """owners_at_points at lattice sites equals the brute-force owners, and at
+    half-site points it equals a direct argmin written out for three centres
+    with a tie (ties go to the smaller label)."""
+    rng = np.random.default_rng(5)
+    cq = np.stack([rng.integers(0, Q * 40, 30), rng.integers(0, Q * 24, 30)], axis=1)
+    own = O.owners_bruteforce(cq, 40, 24)
+    y, x = np.divmod(np.arange(40 * 24), 40)
+    assert np.array_equal(O.owners_at_points(cq, 40, 24, Q * x, Q * y), own.ravel())
+    # (Q/2, Q/2) is equidistant from (0, Q) and (Q, 0) and farther from (3Q, 3Q)
+    cq3 = np.array([[3 * Q, 3 * Q], [Q, 0], [0, Q]], dtype=np.int64)
+    assert O.owners_at_points(cq3, 8, 8, [Q // 2], [Q // 2]).tolist() == [1]
+    # across the seam: (7.5 Q, 0) is nearer to (0, 0) than to (6 Q, 0) on an 8-site ring
+    cq2 = np.array([[6 * Q, 0], [0, 0]], dtype=np.int64)
+    assert O.owners_at_points(cq2, 8, 8, [7 * Q + Q // 2], [0]).tolist() == [1]
+    assert O.owners_at_points(cq2, 8, 8, [7 * Q + Q // 2], [0], periodic=(False, True)).tolist() == [0]
+
+
 def test_vertex_rule_sees_no_vertex_between_two_stripes():
     """Two stripes on a torus: every frame changes colour twice at most, so no
     site is a vertex and the frame rule reads no link."""
