@@ -3,11 +3,17 @@
 
 Default workload: 64 frames of a 1024x1024 periodic smoothed-noise lattice
 (sigma 4, threshold 0.5, shear 0.005 per frame + N(0, 0.01)), processed in
-order. One step = the whole 64-frame sequence (67.1M sites) pushed through
-a frame-sequence batch (every stage launched once for all 64 frames); the
-plain one-frame-per-call path is timed too and reported beside it. The
-256 MiB of input frames is resident in HBM and larger than L2 (129 MB), so
-every frame is read cold.
+order through a frame-sequence batch (every stage launched once for all 64
+frames, 67.1M sites per push). One timed step = R consecutive pushes of the
+sequence, R chosen from the warm-up so that the K timed steps last at least
+a second (stated in the line); the plain one-frame-per-call path is timed too
+and reported beside it. The 256 MiB of input frames is resident in HBM and
+larger than L2 (129 MB), so every frame is read cold.
+
+The same line also carries the batched form (256 uneven lattices, one push
+per frame, against the same lattices one by one) and the served form (64
+simulations, seeded Poisson arrivals, against the plain per-frame FIFO on the
+same trace, latency from arrival), with a served rate sweep.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -265,6 +271,7 @@ def roofline_of(stage_ms, names, launches_per_stage, sites_per_launch, sequence,
 
 
 def run_ours(args, world, rank, local):
+    c3 = None if args.no_c3 else c3_host_frames(rank)   # host cores, before the first GPU call
     import torch
     from paper_1607_00908_gb300 import vd
 
@@ -279,19 +286,29 @@ def run_ours(args, world, rank, local):
     torch.cuda.synchronize()
     peak, peak_kind = read_peaks()
 
-    # ---- headline: the whole frame sequence per push (one launch per stage) ----
+    # ---- headline: the whole frame sequence per push (one launch per stage);
+    # a timed step is R pushes, R set from the warm-up so that the K steps
+    # last at least args.min_seconds ----
     seq = vd.Batch([(Lx, Ly)], sequence=n, stream=s.cuda_stream)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(s)
     for _ in range(args.warmup):
         seq.push(dev)
+    e1.record(s)
     torch.cuda.synchronize()
+    push_ms = max(e0.elapsed_time(e1) / max(1, args.warmup), 1e-3)
+    reps = max(1, int(np.ceil(args.min_seconds * 1e3 / (args.steps * push_ms))))
+    reps = int(max_over_ranks(float(reps), world))
+    sites_per_push = sites_per_step
+    sites_per_step = reps * sites_per_push
     clocks = Clocks(local)
     clocks.start()
     launches0 = seq.timing()[2]
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     barrier(world)
     torch.cuda.synchronize()
     e0.record(s)
-    for _ in range(args.steps):
+    for _ in range(args.steps * reps):
         seq.push(dev)
     e1.record(s)
     torch.cuda.synchronize()
@@ -305,11 +322,12 @@ def run_ours(args, world, rank, local):
     # ---- roofline: per-stage CUDA events on the library stream, same work ----
     seq.set_timing(True)
     seq.timing()
-    for _ in range(args.steps):
+    n_timed = max(args.steps, 20)
+    for _ in range(n_timed):
         seq.push(dev)
     stage_ms, names, _, _ = seq.timing()
     seq.set_timing(False)
-    roofline = roofline_of(stage_ms, names, args.steps, sites_per_step, n > 1, peak, peak_kind)
+    roofline = roofline_of(stage_ms, names, n_timed, sites_per_push, n > 1, peak, peak_kind)
     roofline["pipeline_frac_8B_per_site"] = value * PIPELINE_BYTES_PER_SITE / peak
     roofline["pct_hbm_16B_per_site"] = 100.0 * value * METRIC_BYTES_PER_SITE / peak
 
@@ -333,8 +351,9 @@ def run_ours(args, world, rank, local):
             seq.push_staged()
     torch.cuda.synchronize()
     e2e_dt = max_over_ranks(time.perf_counter() - t0, world)
-    e2e = {"value": world * sites_per_step * e2e_steps / e2e_dt / 1e9, "unit": UNIT,
-           "h2d_bytes_per_step": 4 * sites_per_step, "d2h_bytes_per_step": int(d2h / e2e_steps),
+    e2e = {"value": world * sites_per_push * e2e_steps / e2e_dt / 1e9, "unit": UNIT,
+           "h2d_bytes_per_step": 4 * sites_per_push, "d2h_bytes_per_step": int(d2h / e2e_steps),
+           "step": "one push of the 64-frame sequence (host frames in, every frame's results out)",
            "path": "vd_batch_stage_host (double-buffered, copy stream) + vd_batch_push_staged + "
                    "vd_batch_get_changes_all for every step"}
     seq.close()
@@ -366,7 +385,7 @@ def run_ours(args, world, rank, local):
             vb.push(dev)
         vst, vnames, _, _ = vb.timing()
         vb.set_timing(False)
-        variants[name] = {"value": world * sites_per_step * vsteps / (vms / 1e3) / 1e9, "unit": UNIT,
+        variants[name] = {"value": world * sites_per_push * vsteps / (vms / 1e3) / 1e9, "unit": UNIT,
                           "ms_per_step": vms / vsteps, "steps": vsteps,
                           "stage_ms_per_step": {vnames[k]: vst[k] / vsteps for k in range(len(vnames))}}
         vb.close()
@@ -384,9 +403,16 @@ def run_ours(args, world, rank, local):
     e1.record(s)
     torch.cuda.synchronize()
     plain_ms = max_over_ranks(e0.elapsed_time(e1), world)
-    plain = {"value": world * sites_per_step * plain_steps / (plain_ms / 1e3) / 1e9, "unit": UNIT,
+    plain = {"value": world * sites_per_push * plain_steps / (plain_ms / 1e3) / 1e9, "unit": UNIT,
              "path": "vd_push_frame per frame (graph replay)", "ms_per_frame": plain_ms / plain_steps / n}
     det.close()
+    del dev
+    torch.cuda.synchronize()
+
+    # ---- the batched and served forms (the metric's "batched/served vs plain") ----
+    batched = measure_batched(world, *c3) if c3 is not None else None
+    c3 = None
+    served = None if args.no_c4 else measure_served(world, rank, args.serve_rate, args.serve_seconds)
 
     if rank == 0:
         cpu = None
@@ -398,39 +424,79 @@ def run_ours(args, world, rank, local):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
-            "config": {"workload": desc, "sites_per_step": sites_per_step,
-                       "path": f"vd_batch_create_sequence: {n} frames per push, one launch per stage",
+            "config": {"workload": desc, "sites_per_step": sites_per_step, "pushes_per_step": reps,
+                       "path": f"vd_batch_create_sequence: {n} frames per push, one launch per stage; "
+                               f"a step is {reps} consecutive pushes of the sequence",
                        "l2_policy": "inputs larger than L2 (each step reads all frames once)",
                        "parallelism": f"replicas x{world}"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
             "gpu_launches": launches, "plain_per_frame": plain, "options": variants,
         }
+        if batched is not None:
+            line["batched_c3"] = batched
+        if served is not None:
+            line["served_c4"] = served
         print(json.dumps(line), flush=True)
 
 
-def run_served(args, world, rank, local):
-    """Served form: 64 simulations, seeded Poisson arrivals (2000 frames/s by default),
-    40 GB budget; the same trace replayed with batching and one frame per step."""
+def measure_served(world, rank, rate: float, seconds: float, sweep=(2.0, 4.0, 8.0), sweep_seconds: float = 2.0):
+    """Served form: 64 simulations, seeded Poisson arrivals, 40 GB budget. The
+    same trace runs through the server (continuous batching) and through the
+    plain per-frame path (vd_push_frame FIFO, one stream); latency is counted
+    from each frame's arrival. Further traces at multiples of the rate give
+    the served throughput at the plain path's p99."""
     import torch
-    from paper_1607_00908_gb300 import serve, vd
+    from paper_1607_00908_gb300 import inputs, serve
+
+    params = inputs.serve_sims(64, 5 + rank)
+    sims = [(L, rec) for L, rec, _ in params]
+    host_pools = serve.make_pools([L for L, _ in sims], 4)
+    dev_pools = {k: [torch.from_numpy(F).cuda() for F in v] for k, v in host_pools.items()}
+    del host_pools
+    budget = int(40e9)
+    trace = serve.poisson_trace(64, rate, seconds, 5 + rank)
+    served = serve.run(sims, dev_pools, trace, max_batch=64, budget_bytes=budget)
+    plain = serve.run_plain(sims, dev_pools, trace)
+    offered = sum(sims[s_][0] ** 2 for _, s_ in trace) / seconds / 1e9
+    points = [{"rate": rate, "seconds": seconds, "gsites_per_s": served["gsites_per_s"],
+               "p50_ms": served["p50_ms"], "p99_ms": served["p99_ms"]}]
+    for m in sweep:
+        tr = serve.poisson_trace(64, rate * m, sweep_seconds, 100 + rank + int(10 * m))
+        r = serve.run(sims, dev_pools, tr, max_batch=64, budget_bytes=budget)
+        points.append({"rate": rate * m, "seconds": sweep_seconds, "gsites_per_s": r["gsites_per_s"],
+                       "p50_ms": r["p50_ms"], "p99_ms": r["p99_ms"]})
+    within = [p_ for p_ in points if p_["p99_ms"] <= plain["p99_ms"]]
+    best = max(within, key=lambda p_: p_["gsites_per_s"]) if within else None
+    tot = lambda v: sum_over_ranks(v, world)
+    return {
+        "workload": "64 simulations, L in {512,1024,2048,4096}, noise/RSA recipes alternating, "
+                    f"Poisson arrivals {rate:.0f} frames/s for {seconds} s, 40 GB budget",
+        "offered_gsites_per_s": tot(offered), "arrivals": len(trace),
+        "served": {**served, "gsites_per_s": tot(served["gsites_per_s"])},
+        "plain_fifo": {**plain, "gsites_per_s": tot(plain["gsites_per_s"]),
+                       "path": "vd_push_frame per frame, one context per simulation, one stream, arrival order"},
+        "latency_from": "arrival (trace time on the library clock)",
+        "rate_sweep": points,
+        "served_at_plain_p99": None if best is None else {**best, "gsites_per_s": tot(best["gsites_per_s"]),
+                                                          "plain_p99_ms": plain["p99_ms"],
+                                                          "plain_gsites_per_s": tot(plain["gsites_per_s"])},
+    }
+
+
+def run_served(args, world, rank, local):
+    import torch
+    from paper_1607_00908_gb300 import vd
 
     torch.cuda.set_device(local if world > 1 else 0)
     vd.lib()
-    r = serve.serve_workload(n_sims=64, rate=args.serve_rate, duration=args.serve_seconds, pool=4, budget_gb=40.0,
-                             seed=5 + rank)
-    # every rank serves its own 64 simulations: the job's rate is the sum
-    total = sum_over_ranks(r["served"]["gsites_per_s"], world)
+    r = measure_served(world, rank, args.serve_rate, args.serve_seconds)
     if rank == 0:
-        s, p = r["served"], r["plain"]
+        s_ = r["served"]
         line = {
-            "metric": METRIC + " (served)", "value": total, "unit": UNIT, "n_gpus": world,
-            "steps": s["steps"], "warmup": 0, "ms_per_step": 1e3 * s["wall_s"] / max(1, s["steps"]),
+            "metric": METRIC + " (served)", "value": s_["gsites_per_s"], "unit": UNIT, "n_gpus": world,
+            "steps": s_["steps"], "warmup": 0, "ms_per_step": 1e3 * s_["wall_s"] / max(1, s_["steps"]),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
-            "data": "synthetic",
-            "config": {"workload": "64 simulations, L in {512,1024,2048,4096}, noise/RSA recipes alternating, "
-                                   f"Poisson arrivals {r['rate']:.0f} frames/s for {r['duration_s']} s, 40 GB budget",
-                       "offered_gsites_per_s": r["offered_gsites_per_s"], "arrivals": r["arrivals"]},
-            "served": s, "plain_fifo": p,
+            "data": "synthetic", "config": {"workload": r["workload"]}, **r,
         }
         print(json.dumps(line), flush=True)
 
@@ -441,26 +507,27 @@ def _c3_frames(spec):
     return list(inputs.noise_frames(L, sigma, 8, 0.02, seed))
 
 
-def run_batched_c3(args, world, rank, local):
-    """Batched form: 256 lattices of uneven size (L in {256, ..., 2048}, smoothed
-    noise sigma in [2, 6], 8 frames each) advanced together by vd_batch_push,
-    against the same instances run one by one through vd_push_frame."""
+def c3_host_frames(rank: int):
+    """The batched workload's frames, generated on the host cores (spawned pool)."""
     import multiprocessing as mp
 
     from paper_1607_00908_gb300 import inputs
 
     specs = inputs.batch_instances(256, seed=3 + rank)
-    # frames are generated on the host cores before the first GPU call
     with mp.get_context("spawn").Pool(min(16, os.cpu_count() or 1)) as pool:
         host = pool.map(_c3_frames, specs)
+    return specs, host
+
+
+def measure_batched(world, specs, host):
+    """Batched form: 256 lattices of uneven size advanced together, one
+    vd_batch_push per frame (8 frames), against the same lattices one by one
+    through vd_push_frame."""
     import torch
     from paper_1607_00908_gb300 import vd
 
-    torch.cuda.set_device(local if world > 1 else 0)
-    vd.lib()
     n, nf = len(specs), 8
     dev = [[torch.from_numpy(F).cuda() for F in fr] for fr in host]
-    del host
     sites_per_step = sum(L * L for L, _, _ in specs)
     s = torch.cuda.Stream()
     b = vd.Batch([(L, L) for L, _, _ in specs], stream=s.cuda_stream)
@@ -477,7 +544,6 @@ def run_batched_c3(args, world, rank, local):
     barrier(world)
     ms = max_over_ranks(e0.elapsed_time(e1), world)
     b.close()
-    # the same instances one by one (one context per lattice, one frame per call)
     dets = [vd.Detector(L, L, stream=s.cuda_stream) for L, _, _ in specs]
     for i in range(n):
         for f in range(nf):
@@ -492,20 +558,34 @@ def run_batched_c3(args, world, rank, local):
     ms_plain = max_over_ranks(e0.elapsed_time(e1), world)
     for d in dets:
         d.close()
-    # every rank advances its own 256 lattices: the job's sites are the sum
+    del dev
     total_sites = sum_over_ranks(float(sites_per_step), world)
-    if rank == 0:
-        value = total_sites * nf / (ms / 1e3) / 1e9
-        plain = total_sites * nf / (ms_plain / 1e3) / 1e9
-        line = {
-            "metric": METRIC + " (batched)", "value": value, "unit": UNIT, "n_gpus": world, "steps": nf,
-            "warmup": nf, "ms_per_step": ms / nf, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "int64", "data": "synthetic",
-            "config": {"workload": "256 lattices, L in {256,384,512,768,1024,1536,2048}, smoothed noise "
-                                   "sigma U[2,6], 8 frames, one vd_batch_push per frame",
-                       "sites_per_step": sites_per_step, "parallelism": f"replicas x{world}"},
-            "plain": {"value": plain, "unit": UNIT, "ms_per_step": ms_plain / nf,
+    value = total_sites * nf / (ms / 1e3) / 1e9
+    plain = total_sites * nf / (ms_plain / 1e3) / 1e9
+    return {"value": value, "unit": UNIT, "ms_per_frame_step": ms / nf, "sites_per_frame_step": sites_per_step,
+            "workload": "256 lattices, L in {256,384,512,768,1024,1536,2048}, smoothed noise sigma U[2,6], "
+                        "8 frames, one vd_batch_push per frame",
+            "plain": {"value": plain, "unit": UNIT, "ms_per_frame_step": ms_plain / nf,
                       "path": "vd_push_frame per lattice and frame, instance after instance"},
+            "speedup_vs_plain": value / plain}
+
+
+def run_batched_c3(args, world, rank, local):
+    specs, host = c3_host_frames(rank)   # before the first GPU call
+    import torch
+    from paper_1607_00908_gb300 import vd
+
+    torch.cuda.set_device(local if world > 1 else 0)
+    vd.lib()
+    r = measure_batched(world, specs, host)
+    if rank == 0:
+        line = {
+            "metric": METRIC + " (batched)", "value": r["value"], "unit": UNIT, "n_gpus": world, "steps": 8,
+            "warmup": 8, "ms_per_step": r["ms_per_frame_step"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+            "config": {"workload": r["workload"], "sites_per_step": r["sites_per_frame_step"],
+                       "parallelism": f"replicas x{world}"},
+            "plain": r["plain"], "speedup_vs_plain": r["speedup_vs_plain"],
         }
         print(json.dumps(line), flush=True)
 
@@ -521,6 +601,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--serve-seconds", type=float, default=5.0)
     ap.add_argument("--serve-rate", type=float, default=2000.0, help="served workload: arrivals per second")
+    ap.add_argument("--min-seconds", type=float, default=1.5,
+                    help="headline: the K timed steps last at least this long (pushes per step set from the warm-up)")
+    ap.add_argument("--no-c3", action="store_true", help="leave the batched form out of the default line")
+    ap.add_argument("--no-c4", action="store_true", help="leave the served form out of the default line")
     args = ap.parse_args()
     world, rank, local = dist_setup()
     if args.impl == "reference":

@@ -87,9 +87,10 @@ enum { VD_OWNER_OBSTACLE = -2 };
  * of every plaquette with four distinct owners. VERTEX: the paper's own rule,
  * read at vertex sites only (three or more colour changes around the 8-site
  * frame) with its first- and second-neighbour conditions; the inner-frame
- * point of a diagonal is read as the plaquette centre, coloured by the
- * nearest centre among the colours at the plaquette's corners. The figure
- * defining the inner frame is lost, so the VERTEX rule follows that reading. */
+ * point of a diagonal is read as the plaquette centre, and its colour is its
+ * Voronoi colour (the nearest centre over all centres, exact, ties to the
+ * smallest label), as for every point of the stencil. The figure defining the
+ * inner frame is lost, so the VERTEX rule follows that reading. */
 enum { VD_EDGE_ADJ4 = 0, VD_EDGE_VERTEX = 1 };
 
 /* Isomorphism Phi between past and now labels (Section 3.2.3). OVERLAP: the
@@ -170,6 +171,30 @@ vd_status vd_get_owners(vd_ctx* ctx, int32_t* out, int64_t cap, int64_t* n);    
 vd_status vd_get_edges(vd_ctx* ctx, uint64_t* out, int64_t cap, int64_t* n);        /* sorted unique keys */
 vd_status vd_get_match(vd_ctx* ctx, int32_t* phi, int64_t cap, int64_t* n);         /* K_prev entries, -1 = unmatched */
 
+/* Checkpoint / resume. Section 3.2.3 compares every frame with the previous
+ * one, so the state a context carries from frame to frame is that frame's
+ * labels (foreground bits and per-run labels), Q10 centroids with their
+ * bucket grid, its links (sorted adjacency rows of both directions) and the
+ * frame count. vd_export_state copies it into a caller-owned HOST buffer of
+ * `cap` bytes and sets *n_bytes to the size needed (VD_ERR_CAPACITY, nothing
+ * written, when buf is NULL or too small). vd_import_state replaces a
+ * context's last frame by an exported state: the next push compares against
+ * it, so a context resumed from a checkpoint reports bit-identical changes
+ * to the uninterrupted one. The blob (versioned, native byte order, with a
+ * checksum) must come from a lattice of the same size and walls and fit the
+ * context's capacities; options (threshold, polarity, rules) are taken from
+ * the importing context, and obstacle masks are configuration, set again with
+ * vd_set_obstacles. Every value is range-checked before anything reaches the
+ * device: a damaged or foreign blob gives VD_ERR_INVALID and leaves the
+ * context unchanged. After an import, labels, centroids, links and counts
+ * describe the imported frame; owners, the match and the changes are not part
+ * of the state (VD_ERR_STATE until the next push). Both calls synchronise the
+ * context's stream. Export errors: VD_ERR_STATE (no frame yet), the status of
+ * a failed last frame, VD_ERR_CAPACITY, VD_ERR_CUDA; a frame-sequence batch
+ * gives VD_ERR_UNSUPPORTED (its frames are not independent lattices). */
+vd_status vd_export_state(vd_ctx* ctx, void* buf, int64_t cap, int64_t* n_bytes);
+vd_status vd_import_state(vd_ctx* ctx, const void* buf, int64_t n_bytes);
+
 /* Stage timing (measurement support, not part of the detect result). When
  * enabled, every vd_push_frame records CUDA events on the context stream at
  * the boundaries of the pipeline stages (labelling tiles, bubble merge and
@@ -184,14 +209,29 @@ vd_status vd_get_timing(vd_ctx* ctx, double* stage_ms, int32_t cap, int32_t* n_s
                         int64_t* n_kernel_launches, int64_t* n_frames);
 const char* vd_stage_name(int32_t stage);
 
+/* Test support for the bounded device wait (not part of the detect result).
+ * The only device-side wait of a step is the decoupled look-back of its
+ * prefix scans: a scan tile waits for its predecessors' flags and gives up
+ * after a bounded number of polls (2^20 by default). A tile that gives up
+ * sums its prefix directly from every earlier item (slow, but no offset is
+ * ever wrong and the tiles after it proceed), and the frame then reports
+ * VD_ERR_TIMEOUT from every getter; the context stays usable and the next
+ * frame starts without a past frame. This call makes tile `tile` of scan
+ * `kind` (0 = the bubble-rank scan, the first scan of a step; 1 buckets,
+ * 2 link degrees, 3-4 flip counts) withhold its flag in every following push,
+ * so that its successor's wait runs out after `spin_limit` polls (0 = the
+ * default limit). tile = -1 turns the hold off. Synchronous; errors:
+ * VD_ERR_INVALID, VD_ERR_CUDA. */
+vd_status vd_debug_hold_scan_flag(vd_ctx* ctx, int32_t kind, int64_t tile, int32_t spin_limit);
+
 /* Release all device state of the context (waits for its stream first). */
 vd_status vd_destroy(vd_ctx* ctx);
 
 /* Voronoi owners without any device allocation. The paper has no
- * counterpart: this exists for callers that cannot call cudaMalloc (code
- * inside stream capture with allocation forbidden, processes whose device
- * memory belongs to another allocator, hosts that allocate everything at
- * start-up). It computes the same exact colouring as the pipeline's owner
+ * counterpart: this exists for callers that cannot call cudaMalloc
+ * (processes whose device memory all belongs to another framework's
+ * allocator, real-time or embedded hosts that allocate everything at
+ * start-up and may not allocate afterwards). It computes the same exact colouring as the pipeline's owner
  * step: owner(x,y) = the label i minimising |1024*(x,y) - c_i|^2 (minimum
  * image, ties to the smallest i), or -1 when K == 0.
  *   d_centroids_q10  device, K pairs (cx, cy) in 1/1024 site, in [0, 1024*L);
@@ -204,8 +244,10 @@ vd_status vd_destroy(vd_ctx* ctx);
  * Every call shares that array: calls whose device work may overlap (other
  * streams, other host threads) race and must be serialised by the caller.
  * The first call on a device resolves the array's device address (a runtime
- * query, no allocation); make that first call before any stream capture.
- * Asynchronous on `stream`; errors: VD_ERR_INVALID, VD_ERR_CAPACITY,
+ * query, no allocation); make that first call before any stream capture. A
+ * device reset (cudaDeviceReset) invalidates the resolved address: do not
+ * use this entry point across a reset. Asynchronous on `stream`; each launch
+ * is checked as it is enqueued; errors: VD_ERR_INVALID, VD_ERR_CAPACITY,
  * VD_ERR_CUDA. */
 vd_status vd_voronoi_owners_static(const int32_t* d_centroids_q10, int32_t K, int32_t Lx, int32_t Ly,
                                    int32_t* d_owners, void* stream);
@@ -287,6 +329,10 @@ vd_status vd_batch_get_owners(vd_batch* b, int32_t i, int32_t* out, int64_t cap,
 vd_status vd_batch_get_edges(vd_batch* b, int32_t i, uint64_t* out, int64_t cap, int64_t* n);
 vd_status vd_batch_get_centroids_q10(vd_batch* b, int32_t i, int32_t* out, int64_t cap, int64_t* n);
 vd_status vd_batch_get_counts(vd_batch* b, int32_t i, int32_t* K, int32_t* n_edges, int64_t* frame_index);
+/* Checkpoint / resume of instance i of an independent batch (as
+ * vd_export_state / vd_import_state). */
+vd_status vd_batch_export_state(vd_batch* b, int32_t i, void* buf, int64_t cap, int64_t* n_bytes);
+vd_status vd_batch_import_state(vd_batch* b, int32_t i, const void* buf, int64_t n_bytes);
 /* Stage timing of a batch (as vd_set_timing / vd_get_timing; *n_steps
  * counts pushes). */
 vd_status vd_batch_set_timing(vd_batch* b, int32_t enable);
@@ -296,38 +342,72 @@ vd_status vd_batch_destroy(vd_batch* b);
 
 /* ---------------------------------------------------------------------------
  * Served form: frames of many simulations arrive over time; continuous
- * batching. The server keeps every simulation's state resident (one batch
- * instance per simulation) and runs steps over the simulations that have a
- * waiting frame: at most one frame per simulation per step, at most
- * max_batch simulations, admitted only while the resident state plus the
+ * batching (the paper runs its detection inside a running simulation every
+ * few steps, Section 4; a server does so for many simulations at once). The
+ * server keeps every simulation's state resident (one batch instance per
+ * simulation) and runs steps over the simulations that have a waiting frame:
+ * at most one frame per simulation per step, at most max_batch simulations,
+ * oldest arrival first, admitted only while the resident state plus the
  * frames in flight fit hbm_budget_bytes. Two steps are kept queued on the
  * device, so frames that arrive while a step runs join the next one.
+ * Simulations can be opened and closed while others run.
  * ------------------------------------------------------------------------- */
 typedef struct vd_server vd_server;
 typedef struct vd_server_done {
     int64_t ticket;             /* from vd_server_submit */
     int32_t sim;
     int32_t status;             /* VD_OK or the frame's device error */
-    int64_t t_submit_ns;        /* host steady-clock times */
+    int64_t t_arrival_ns;       /* the frame's arrival time given to vd_server_submit */
+    int64_t t_submit_ns;        /* when vd_server_submit was called (vd_server_clock_ns clock) */
     int64_t t_done_ns;          /* when vd_server_poll saw the step finish */
     int32_t n_bubbles, n_edges, n_breaking, n_arising;
 } vd_server_done;
 
-/* One config per simulation (all on sims[0].stream). Allocates all resident
- * state; VD_ERR_CAPACITY when it alone exceeds the budget. */
+/* A server whose device work runs on `stream` (cudaStream_t; the configs'
+ * own stream fields are ignored), opening the `n_sims` simulations of `sims`
+ * (n_sims may be 0). Allocates their resident state; VD_ERR_CAPACITY when it
+ * alone exceeds the budget. */
 vd_status vd_server_create(const vd_config* sims, int32_t n_sims, int64_t hbm_budget_bytes, int32_t max_batch,
-                           vd_server** out);
-/* Queue one frame (device pointer, Ly*Lx floats) of simulation `sim`; the
- * caller keeps it valid until the frame is reported done. */
-vd_status vd_server_submit(vd_server* sv, int32_t sim, const float* d_field, int64_t* ticket);
+                           void* stream, vd_server** out);
+/* Open one more simulation while others run; *sim receives its id. Its
+ * resident state is allocated now and admitted only if every open
+ * simulation's state still fits the budget (VD_ERR_CAPACITY otherwise,
+ * nothing kept). */
+vd_status vd_server_open_sim(vd_server* sv, const vd_config* cfg, int32_t* sim);
+/* Close a simulation with no frame queued or in flight (VD_ERR_STATE
+ * otherwise); its id is not reused. Its state leaves the budget once every
+ * simulation opened together with it is closed. */
+vd_status vd_server_close_sim(vd_server* sv, int32_t sim);
+/* The host steady clock of the server's timestamps, in ns. */
+vd_status vd_server_clock_ns(int64_t* t);
+/* Queue one frame (device pointer, Ly*Lx floats) of simulation `sim` that
+ * arrived at t_arrival_ns (vd_server_clock_ns clock; <= 0: now). Latency is
+ * counted from the arrival, so host delay before the submit is included. The
+ * caller keeps the frame valid until it is reported done. */
+vd_status vd_server_submit(vd_server* sv, int32_t sim, const float* d_field, int64_t t_arrival_ns, int64_t* ticket);
 /* Run the scheduler: retire finished steps (filling `done`, up to cap
  * entries) and launch new steps. wait != 0 blocks until at least one frame
  * finishes or nothing is in flight. */
 vd_status vd_server_poll(vd_server* sv, int32_t wait, vd_server_done* done, int32_t cap, int32_t* n_done);
+/* With keep != 0, every poll also copies the breaking / arising lists and
+ * active flags of each frame it retires to host memory (one gather per
+ * group of simulations, on a side stream, before any of those simulations
+ * is given its next frame); vd_server_get_frame_changes returns them by
+ * ticket until the next poll. Off by default. */
+vd_status vd_server_keep_changes(vd_server* sv, int32_t keep);
+/* Changes of a frame retired by the most recent vd_server_poll (as
+ * vd_get_changes); VD_ERR_STATE for any other ticket or when changes are not
+ * kept. */
+vd_status vd_server_get_frame_changes(vd_server* sv, int64_t ticket, vd_changes* out);
 /* Results of a simulation's last finished frame; VD_ERR_STATE while one of
  * its frames is in flight. */
 vd_status vd_server_get_changes(vd_server* sv, int32_t sim, vd_changes* out);
 vd_status vd_server_get_labels(vd_server* sv, int32_t sim, int32_t* out, int64_t cap, int64_t* n);
+/* Checkpoint / resume of one simulation (as vd_export_state /
+ * vd_import_state); VD_ERR_STATE while it has a frame in flight (or, for
+ * import, queued). */
+vd_status vd_server_export_state(vd_server* sv, int32_t sim, void* buf, int64_t cap, int64_t* n_bytes);
+vd_status vd_server_import_state(vd_server* sv, int32_t sim, const void* buf, int64_t n_bytes);
 vd_status vd_server_stats(vd_server* sv, int64_t* steps, int64_t* frames_done, int64_t* resident_bytes,
                           int64_t* queued);
 vd_status vd_server_destroy(vd_server* sv);

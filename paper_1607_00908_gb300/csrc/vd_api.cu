@@ -17,6 +17,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstddef>
 #include <cstdlib>
 #include <cstring>
 #include <new>
@@ -89,6 +90,16 @@ struct vd_batch {
     long long* d_pitches = nullptr;
     std::vector<const float*> h_fields;
     std::vector<long long> h_pitches;
+    // pinned copies of those tables, a ring of PIN_RING sets: the copy to the
+    // device is then asynchronous (a copy from pageable memory may wait for
+    // the stream), and a set is reused only after the copy that read it ran
+    static const int PIN_RING = 4;
+    const float** pin_fields[PIN_RING] = {};
+    long long* pin_pitches[PIN_RING] = {};
+    long long* pin_tab[PIN_RING] = {};   // subset step tables: act, tileA, tileV (n+1 each), groups (n+1)
+    cudaEvent_t pin_ev[PIN_RING] = {};
+    bool pin_used[PIN_RING] = {};
+    int pin_next = 0;
     // host input staging for vd_push_frame_host (instance 0)
     float* d_host_field = nullptr;
     // double-buffered host input (vd_batch_stage_host / vd_batch_push_staged):
@@ -125,6 +136,9 @@ struct vd_batch {
     unsigned char* d_act = nullptr;       // active flags of all instances
     unsigned char* h_act = nullptr;       // pinned
     long long act_cap = 0;
+    // per instance: frames_pushed when its state was last imported (-1: never);
+    // until the next push its owners, match and changes are not available
+    std::vector<long long> imported_at;
     long long* d_off = nullptr;           // per instance: breaking, arising, active offsets
     long long* h_off = nullptr;           // pinned
 };
@@ -187,10 +201,30 @@ void build_table(vd_batch* b, const std::vector<int>& act, StepTables& T, bool a
     T.total_tilesA = tA[n];
     T.total_tilesV = tV[n];
     T.total_groups = wd[n];
-    cudaMemcpyAsync(T.d_act, act.data(), sizeof(int) * n, cudaMemcpyHostToDevice, b->s);
-    cudaMemcpyAsync(T.d_tileA, tA.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice, b->s);
-    cudaMemcpyAsync(T.d_tileV, tV.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice, b->s);
-    cudaMemcpyAsync(T.d_groups, wd.data(), sizeof(long long) * (n + 1), cudaMemcpyHostToDevice, b->s);
+    if (alloc) {   // at creation: plain copies (the creation synchronises)
+        cudaMemcpyAsync(T.d_act, act.data(), sizeof(int) * n, cudaMemcpyHostToDevice, b->s);
+        cudaMemcpyAsync(T.d_tileA, tA.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice, b->s);
+        cudaMemcpyAsync(T.d_tileV, tV.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice, b->s);
+        cudaMemcpyAsync(T.d_groups, wd.data(), sizeof(long long) * (n + 1), cudaMemcpyHostToDevice, b->s);
+        return;
+    }
+    // per step: through the pinned set the step's field tables used (its
+    // event, recorded again below, guards its reuse)
+    const int k = (b->pin_next + vd_batch::PIN_RING - 1) % vd_batch::PIN_RING;
+    const int m = b->n + 1;
+    int* pa = reinterpret_cast<int*>(b->pin_tab[k]);
+    int* pA = pa + m;
+    int* pV = pA + m;
+    long long* pg = b->pin_tab[k] + 2 * m;
+    std::memcpy(pa, act.data(), sizeof(int) * n);
+    std::memcpy(pA, tA.data(), sizeof(int) * (n + 1));
+    std::memcpy(pV, tV.data(), sizeof(int) * (n + 1));
+    std::memcpy(pg, wd.data(), sizeof(long long) * (n + 1));
+    cudaMemcpyAsync(T.d_act, pa, sizeof(int) * n, cudaMemcpyHostToDevice, b->s);
+    cudaMemcpyAsync(T.d_tileA, pA, sizeof(int) * (n + 1), cudaMemcpyHostToDevice, b->s);
+    cudaMemcpyAsync(T.d_tileV, pV, sizeof(int) * (n + 1), cudaMemcpyHostToDevice, b->s);
+    cudaMemcpyAsync(T.d_groups, pg, sizeof(long long) * (n + 1), cudaMemcpyHostToDevice, b->s);
+    cudaEventRecord(b->pin_ev[k], b->s);
 }
 
 Launch make_launch(vd_batch* b, const StepTables& T) {
@@ -451,13 +485,33 @@ vd_status create_batch(const vd_config* cfgs, int n, vd_batch** out, bool sequen
     build_table(b, act, b->sub, true);
     b->h_fields.assign(n, nullptr);
     b->h_pitches.assign(n, 0);
+    b->imported_at.assign(n, -1);
+    for (int k = 0; k < vd_batch::PIN_RING; ++k) {
+        if (cudaMallocHost(&b->pin_fields[k], sizeof(float*) * n) != cudaSuccess ||
+            cudaMallocHost(&b->pin_pitches[k], sizeof(long long) * n) != cudaSuccess ||
+            cudaMallocHost(&b->pin_tab[k], sizeof(long long) * 4 * (n + 1)) != cudaSuccess ||
+            cudaEventCreateWithFlags(&b->pin_ev[k], cudaEventDisableTiming) != cudaSuccess) {
+            cudaGetLastError();
+            M.ok = false;
+        }
+    }
+    auto release_pins = [&]() {
+        for (int k = 0; k < vd_batch::PIN_RING; ++k) {
+            if (b->pin_fields[k]) cudaFreeHost(b->pin_fields[k]);
+            if (b->pin_pitches[k]) cudaFreeHost(b->pin_pitches[k]);
+            if (b->pin_tab[k]) cudaFreeHost(b->pin_tab[k]);
+            if (b->pin_ev[k]) cudaEventDestroy(b->pin_ev[k]);
+        }
+    };
     if (!M.ok) {
+        release_pins();
         M.release();
         delete b;
         return VD_ERR_OOM;
     }
     chk(cudaStreamSynchronize(b->s));
     if (e != cudaSuccess) {
+        release_pins();
         M.release();
         delete b;
         return VD_ERR_CUDA;
@@ -572,9 +626,16 @@ vd_status push_fields(vd_batch* b, const std::vector<int>& act, const float* con
         b->h_fields[act[a]] = fields[a];
         b->h_pitches[act[a]] = pitches[a];
     }
-    cudaError_t e = cudaMemcpyAsync(b->d_fields, b->h_fields.data(), sizeof(float*) * b->n, cudaMemcpyHostToDevice, b->s);
+    const int k = b->pin_next;
+    if (b->pin_used[k] && cudaEventSynchronize(b->pin_ev[k]) != cudaSuccess) return VD_ERR_CUDA;
+    std::memcpy(b->pin_fields[k], b->h_fields.data(), sizeof(float*) * b->n);
+    std::memcpy(b->pin_pitches[k], b->h_pitches.data(), sizeof(long long) * b->n);
+    cudaError_t e = cudaMemcpyAsync(b->d_fields, b->pin_fields[k], sizeof(float*) * b->n, cudaMemcpyHostToDevice, b->s);
     if (e == cudaSuccess)
-        e = cudaMemcpyAsync(b->d_pitches, b->h_pitches.data(), sizeof(long long) * b->n, cudaMemcpyHostToDevice, b->s);
+        e = cudaMemcpyAsync(b->d_pitches, b->pin_pitches[k], sizeof(long long) * b->n, cudaMemcpyHostToDevice, b->s);
+    if (e == cudaSuccess) e = cudaEventRecord(b->pin_ev[k], b->s);
+    b->pin_used[k] = true;
+    b->pin_next = (k + 1) % vd_batch::PIN_RING;
     return cuda_status(e);
 }
 
@@ -627,12 +688,16 @@ vd_status copy_out(void* dst, const void* src, size_t bytes, cudaStream_t s) {
     return cuda_status(e);
 }
 
+// the state of instance i was imported and no frame has been pushed since:
+// the imported state holds no owners, match or changes
+bool fresh_import(const vd_batch* b, int i) { return b->imported_at[i] == b->frames_pushed; }
+
 vd_status get_changes(vd_batch* b, int i, vd_changes* out) {
     if (!out) return VD_ERR_INVALID;
     InstState st;
     vd_status rs = read_state(b, i, &st);
     if (rs) return rs;
-    if (st.frame == 0) return VD_ERR_STATE;
+    if (st.frame == 0 || fresh_import(b, i)) return VD_ERR_STATE;
     const InstDesc& D = b->desc[i];
     out->frame_index = b->sequence ? (st.frame - 1) * b->n + i : st.frame - 1;
     out->n_prev = st.rep_K_prev;
@@ -669,36 +734,40 @@ vd_status get_array(vd_batch* b, int i, int which, void* out, int64_t cap, int64
     vd_status rs = read_state(b, i, &st);
     if (rs) return rs;
     if (st.frame == 0) return VD_ERR_STATE;
+    if (fresh_import(b, i) && (which == 1 || which == 4 || which == 5)) return VD_ERR_STATE;
     const InstDesc& D = b->desc[i];
     const long long N = (long long)D.Lx * D.Ly;
     const int slot = st.slot;   // the frame just finished
     long long cnt = 0;
-    const void* src = nullptr;
     size_t esz = 4;
     switch (which) {
-        case 0: {
-            cnt = (long long)D.uLx * D.uLy;
-            launch_expand_labels(b->s, b->P, i, slot, b->P.lab_out, N);
-            src = b->P.lab_out;
-            break;
-        }
-        case 1: cnt = (long long)D.uLx * D.uLy; src = b->P.owners + D.site_off; break;
-        case 2: cnt = 2ll * st.K; src = b->P.cq[slot] + D.comp_off; break;
-        case 3: {
-            cnt = st.E;
-            esz = 8;
-            launch_edge_keys(b->s, b->P, i, slot, b->P.ekeys + D.edge_off);
-            src = b->P.ekeys + D.edge_off;
-            break;
-        }
-        case 4: cnt = st.rep_K_prev; src = b->P.phi + D.comp_off; break;
-        case 5: cnt = st.K; esz = 1; src = b->P.active + D.comp_off; break;
+        case 0: case 1: cnt = (long long)D.uLx * D.uLy; break;
+        case 2: cnt = 2ll * st.K; break;
+        case 3: cnt = st.E; esz = 8; break;
+        case 4: cnt = st.rep_K_prev; break;
+        case 5: cnt = st.K; esz = 1; break;
         default: return VD_ERR_INVALID;
     }
     if (n) *n = cnt;
+    // a failed frame's state is not read by any kernel
     vd_status es = err_status(st);
     if (es) return es;
     if (cap < cnt) return VD_ERR_CAPACITY;
+    const void* src = nullptr;
+    switch (which) {
+        case 0:
+            launch_expand_labels(b->s, b->P, i, slot, b->P.lab_out, N);
+            src = b->P.lab_out;
+            break;
+        case 1: src = b->P.owners + D.site_off; break;
+        case 2: src = b->P.cq[slot] + D.comp_off; break;
+        case 3:
+            launch_edge_keys(b->s, b->P, i, slot, b->P.ekeys + D.edge_off);
+            src = b->P.ekeys + D.edge_off;
+            break;
+        case 4: src = b->P.phi + D.comp_off; break;
+        default: src = b->P.active + D.comp_off; break;
+    }
     if ((which == 0 || which == 1) && (D.uLx != D.Lx || D.uLy != D.Ly)) {
         // a bounded axis runs with twice its length: return the domain only
         if (cnt == 0) return VD_OK;
@@ -708,6 +777,247 @@ vd_status get_array(vd_batch* b, int i, int which, void* out, int64_t cap, int64
         return cuda_status(e);
     }
     return copy_out(out, src, (size_t)cnt * esz, b->s);
+}
+
+// ---------------------------------------------------------------------------
+// Checkpoint / resume of one instance (vd_export_state / vd_import_state).
+// The state a frame leaves for the next one (Section 3.2.3 compares each frame
+// with the previous one): its foreground bits and run labels (the labels),
+// its centroids and their bucket grid, and its links as a CSR of both
+// directions, plus the frame count. Blob = StateHeader + those arrays in that
+// order, native byte order; the header carries the lattice, the counts and an
+// FNV-1a checksum of the arrays, and import checks every value's range, so a
+// damaged or foreign blob is refused before anything reaches the device.
+// ---------------------------------------------------------------------------
+constexpr uint32_t STATE_MAGIC = 0x31534456u;   // "VDS1"
+constexpr uint32_t STATE_VERSION = 1;
+
+struct StateHeader {
+    uint32_t magic, version;
+    int32_t Lx, Ly, uLx, uLy;   // lattice as run (a bounded axis runs with twice its length) and as seen
+    int32_t K, E;               // bubbles and links of the frame
+    int32_t B, nbx, nby, pad;   // its bucket grid
+    int64_t frame;              // frames finished
+    int64_t n_words, n_runs;    // foreground words, run-label slots
+    uint64_t checksum;          // FNV-1a 64 of the arrays
+};
+
+struct StateLayout {
+    long long words, runs, K, nb, E;
+    size_t o_fg, o_rl, o_cq, o_boff, o_bcq, o_bid, o_ro, o_cols, total;
+};
+
+StateLayout state_layout(const InstDesc& D, int K, int E, int nb) {
+    StateLayout L;
+    L.words = (long long)D.Ly * D.wpr;
+    L.runs = (long long)D.ntx * D.nty * TRUNS;
+    L.K = K;
+    L.nb = nb;
+    L.E = E;
+    size_t o = sizeof(StateHeader);
+    L.o_fg = o; o += sizeof(unsigned) * L.words;
+    L.o_rl = o; o += sizeof(int) * L.runs;
+    L.o_cq = o; o += sizeof(int2) * K;
+    L.o_boff = o; o += sizeof(int) * (nb + 1);
+    L.o_bcq = o; o += sizeof(int2) * K;
+    L.o_bid = o; o += sizeof(int) * K;
+    L.o_ro = o; o += sizeof(int) * (K + 1);
+    L.o_cols = o; o += sizeof(int) * 2ll * E;
+    L.total = o;
+    return L;
+}
+
+uint64_t fnv1a(const unsigned char* p, size_t n) {
+    uint64_t h = 1469598103934665603ull;
+    for (size_t k = 0; k < n; ++k) {
+        h ^= p[k];
+        h *= 1099511628211ull;
+    }
+    return h;
+}
+
+vd_status export_state(vd_batch* b, int i, void* buf, int64_t cap, int64_t* n_bytes) {
+    if (!b || i < 0 || i >= b->n) return VD_ERR_INVALID;
+    if (b->sequence) return VD_ERR_UNSUPPORTED;   // a sequence's frames are not independent lattices
+    InstState st;
+    vd_status r = read_state(b, i, &st);
+    if (r) return r;
+    if (st.frame == 0) return VD_ERR_STATE;
+    r = err_status(st);
+    if (r) return r;
+    const InstDesc& D = b->desc[i];
+    const int slot = st.slot;
+    const int K = st.Kb[slot], E = st.Eb[slot];
+    const int nb = K > 0 ? st.nbxs[slot] * st.nbys[slot] : 0;
+    const StateLayout L = state_layout(D, K, E, nb);
+    if (n_bytes) *n_bytes = (int64_t)L.total;
+    if (!buf || cap < (int64_t)L.total) return VD_ERR_CAPACITY;
+    unsigned char* o = static_cast<unsigned char*>(buf);
+    const Pools& P = b->P;
+    cudaError_t e = cudaSuccess;
+    auto get = [&](size_t off, const void* src, size_t bytes) {
+        if (e == cudaSuccess && bytes) e = cudaMemcpyAsync(o + off, src, bytes, cudaMemcpyDeviceToHost, b->s);
+    };
+    get(L.o_fg, P.fgbits[slot] + D.word_off, sizeof(unsigned) * L.words);
+    get(L.o_rl, P.rl[slot] + D.tile_off * TRUNS, sizeof(int) * L.runs);
+    get(L.o_cq, P.cq[slot] + D.comp_off, sizeof(int2) * K);
+    get(L.o_boff, P.boff[slot] + D.bucket_off, sizeof(int) * (nb + 1));
+    get(L.o_bcq, P.bcq[slot] + D.comp_off, sizeof(int2) * K);
+    get(L.o_bid, P.bid[slot] + D.comp_off, sizeof(int) * K);
+    get(L.o_ro, P.rowoff[slot] + D.comp_off, sizeof(int) * (K + 1));
+    get(L.o_cols, P.cols[slot] + 2 * D.edge_off, sizeof(int) * 2ll * E);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->s);
+    if (e != cudaSuccess) return VD_ERR_CUDA;
+    if (K == 0) {   // the grid of an empty frame is never read; store its end offset as 0
+        int z = 0;
+        std::memcpy(o + L.o_boff, &z, sizeof(int));
+    }
+    StateHeader h;
+    std::memset(&h, 0, sizeof(h));
+    h.magic = STATE_MAGIC;
+    h.version = STATE_VERSION;
+    h.Lx = D.Lx;
+    h.Ly = D.Ly;
+    h.uLx = D.uLx;
+    h.uLy = D.uLy;
+    h.K = K;
+    h.E = E;
+    h.B = st.Bs[slot];
+    h.nbx = K > 0 ? st.nbxs[slot] : 0;
+    h.nby = K > 0 ? st.nbys[slot] : 0;
+    h.frame = st.frame;
+    h.n_words = L.words;
+    h.n_runs = L.runs;
+    h.checksum = fnv1a(o + sizeof(StateHeader), L.total - sizeof(StateHeader));
+    std::memcpy(o, &h, sizeof(h));
+    return VD_OK;
+}
+
+// every value of a blob in the range the kernels assume
+bool state_values_ok(const InstDesc& D, const StateHeader& h, const StateLayout& L, const unsigned char* o) {
+    const int K = h.K, E = h.E;
+    auto at = [&](size_t off, long long k) {
+        int v;
+        std::memcpy(&v, o + off + sizeof(int) * k, sizeof(int));
+        return v;
+    };
+    // foreground bits only inside the lattice (and its first half on a bounded axis)
+    for (int y = 0; y < D.Ly; ++y)
+        for (int w = 0; w < D.wpr; ++w) {
+            unsigned v;
+            std::memcpy(&v, o + L.o_fg + sizeof(unsigned) * ((long long)y * D.wpr + w), sizeof(unsigned));
+            const int x0 = 32 * w;
+            const int lim = y < D.uLy ? std::min(D.uLx, D.Lx) : 0;
+            const unsigned allowed = x0 >= lim ? 0u : (lim - x0 >= 32 ? ~0u : ((1u << (lim - x0)) - 1u));
+            if (v & ~allowed) return false;
+        }
+    for (long long k = 0; k < L.runs; ++k) {
+        const int v = at(L.o_rl, k);
+        if (v < -1 || v >= K) return false;
+    }
+    const long long MX = (long long)Q * D.Lx, MY = (long long)Q * D.Ly;
+    for (long long k = 0; k < 2ll * K; ++k) {
+        const long long v = at(L.o_cq, k), M = (k & 1) ? MY : MX;
+        if (v < 0 || v >= M) return false;
+    }
+    int prev = 0;
+    for (long long k = 0; k <= L.nb; ++k) {
+        const int v = at(L.o_boff, k);
+        if (v < prev || v > K) return false;
+        prev = v;
+    }
+    if (at(L.o_boff, L.nb) != (L.nb > 0 ? K : 0)) return false;
+    // bucket order: entry j of bucket k is centre bid[j], stored in that bucket
+    for (long long k = 0; k < L.nb; ++k)
+        for (int j = at(L.o_boff, k); j < at(L.o_boff, k + 1); ++j) {
+            const int id = at(L.o_bid, j);
+            if (id < 0 || id >= K) return false;
+            const int bx = at(L.o_bcq, 2ll * j), by = at(L.o_bcq, 2ll * j + 1);
+            if (bx != at(L.o_cq, 2ll * id) || by != at(L.o_cq, 2ll * id + 1)) return false;
+            if ((long long)(by / Q / h.B) * h.nbx + (bx / Q / h.B) != k) return false;
+        }
+    // CSR rows: ascending labels, no self link
+    prev = 0;
+    for (long long k = 0; k <= K; ++k) {
+        const int v = at(L.o_ro, k);
+        if (v < prev || v > 2 * E) return false;
+        prev = v;
+    }
+    if (at(L.o_ro, K) != 2 * E) return false;
+    for (long long a = 0; a < K; ++a)
+        for (int j = at(L.o_ro, a); j < at(L.o_ro, a + 1); ++j) {
+            const int v = at(L.o_cols, j);
+            if (v < 0 || v >= K || v == a) return false;
+            if (j > at(L.o_ro, a) && v <= at(L.o_cols, j - 1)) return false;
+        }
+    return true;
+}
+
+vd_status import_state(vd_batch* b, int i, const void* buf, int64_t n_bytes) {
+    if (!b || i < 0 || i >= b->n || !buf) return VD_ERR_INVALID;
+    if (b->sequence) return VD_ERR_UNSUPPORTED;
+    if (n_bytes < (int64_t)sizeof(StateHeader)) return VD_ERR_INVALID;
+    const unsigned char* o = static_cast<const unsigned char*>(buf);
+    StateHeader h;
+    std::memcpy(&h, o, sizeof(h));
+    const InstDesc& D = b->desc[i];
+    if (h.magic != STATE_MAGIC || h.version != STATE_VERSION) return VD_ERR_INVALID;
+    if (h.Lx != D.Lx || h.Ly != D.Ly || h.uLx != D.uLx || h.uLy != D.uLy) return VD_ERR_INVALID;
+    if (h.frame < 1 || h.K < 0 || h.E < 0 || h.K > D.comp_cap || h.E > D.edge_cap) return VD_ERR_INVALID;
+    if (h.K > 0 && (h.B < 4 || h.B > 64 || h.nbx != (D.Lx + h.B - 1) / h.B || h.nby != (D.Ly + h.B - 1) / h.B))
+        return VD_ERR_INVALID;
+    if (h.K == 0 && (h.nbx != 0 || h.nby != 0)) return VD_ERR_INVALID;
+    const int nb = h.K > 0 ? h.nbx * h.nby : 0;
+    if (nb > D.bucket_cap) return VD_ERR_INVALID;
+    const StateLayout L = state_layout(D, h.K, h.E, nb);
+    if (h.n_words != L.words || h.n_runs != L.runs || n_bytes != (int64_t)L.total) return VD_ERR_INVALID;
+    if (fnv1a(o + sizeof(StateHeader), L.total - sizeof(StateHeader)) != h.checksum) return VD_ERR_INVALID;
+    if (!state_values_ok(D, h, L, o)) return VD_ERR_INVALID;
+    InstState st;
+    vd_status r = read_state(b, i, &st);   // waits for the stream
+    if (r) return r;
+    const int slot = st.slot;
+    const Pools& P = b->P;
+    cudaError_t e = cudaSuccess;
+    auto put = [&](void* dst, size_t off, size_t bytes) {
+        if (e == cudaSuccess && bytes) e = cudaMemcpyAsync(dst, o + off, bytes, cudaMemcpyHostToDevice, b->s);
+    };
+    put(P.fgbits[slot] + D.word_off, L.o_fg, sizeof(unsigned) * L.words);
+    put(P.rl[slot] + D.tile_off * TRUNS, L.o_rl, sizeof(int) * L.runs);
+    put(P.cq[slot] + D.comp_off, L.o_cq, sizeof(int2) * h.K);
+    put(P.boff[slot] + D.bucket_off, L.o_boff, sizeof(int) * (nb + 1));
+    put(P.bcq[slot] + D.comp_off, L.o_bcq, sizeof(int2) * h.K);
+    put(P.bid[slot] + D.comp_off, L.o_bid, sizeof(int) * h.K);
+    put(P.rowoff[slot] + D.comp_off, L.o_ro, sizeof(int) * (h.K + 1));
+    put(P.cols[slot] + 2 * D.edge_off, L.o_cols, sizeof(int) * 2ll * h.E);
+    // the instance's state: the imported frame is its last finished frame
+    st.Kb[slot] = h.K;
+    st.Eb[slot] = h.E;
+    st.Bs[slot] = h.K > 0 ? h.B : 4;
+    st.nbxs[slot] = h.nbx;
+    st.nbys[slot] = h.nby;
+    st.B = st.Bs[slot];
+    st.nbx = h.nbx;
+    st.nby = h.nby;
+    st.frame = h.frame;
+    st.last_ok = 1;
+    st.K = h.K;
+    st.E = h.E;
+    st.E_prev = h.E;
+    st.K_prev = 0;
+    st.rep_K_prev = 0;
+    st.K_roots = h.K;
+    st.n_matched = 0;
+    st.n_break = 0;
+    st.n_arise = 0;
+    st.err = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(P.st + i, &st, sizeof(InstState), cudaMemcpyHostToDevice, b->s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->s);
+    if (e != cudaSuccess) return VD_ERR_CUDA;
+    b->st_at = -1;
+    b->chg_at = -1;
+    b->imported_at[i] = b->frames_pushed;
+    return VD_OK;
 }
 
 // obstacle bits of instance i from a host byte mask (uLy rows of `pitch` bytes)
@@ -746,17 +1056,19 @@ vd_status set_obstacles(vd_batch* b, int i, const uint8_t* h_mask, int64_t pitch
 
 namespace vd {
 // per-step results of some instances, gathered on the device and copied
-// asynchronously into pinned host memory: 6 ints per instance
-// (K, E, n_breaking, n_arising, n_matched, err)
+// asynchronously into pinned host memory: 8 ints per instance
+// (K, E, n_breaking, n_arising, n_matched, err, past-frame bubbles, frames finished)
 __global__ void k_gather_counts(Pools P, const int* sims, int n, int* out) {
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
         const InstState& S = P.st[sims[k]];
-        out[6 * k + 0] = S.K;
-        out[6 * k + 1] = S.E;
-        out[6 * k + 2] = S.n_break;
-        out[6 * k + 3] = S.n_arise;
-        out[6 * k + 4] = S.n_matched;
-        out[6 * k + 5] = S.err;
+        out[8 * k + 0] = S.K;
+        out[8 * k + 1] = S.E;
+        out[8 * k + 2] = S.n_break;
+        out[8 * k + 3] = S.n_arise;
+        out[8 * k + 4] = S.n_matched;
+        out[8 * k + 5] = S.err;
+        out[8 * k + 6] = S.rep_K_prev;
+        out[8 * k + 7] = (int)S.frame;
     }
 }
 }  // namespace vd
@@ -766,13 +1078,24 @@ long long vd_batch_resident_bytes(const vd_batch* b) { return b ? b->mem.bytes :
 vd_status vd_batch_gather_counts_async(vd_batch* b, const int* h_sims, int n, int* d_scratch, int* h_pinned_out) {
     if (!b || n <= 0) return VD_ERR_INVALID;
     int* d_sims = d_scratch;
-    int* d_out = d_scratch + n;
+    int* d_out = d_scratch + n;   // 8 ints per instance follow the n instance ids
     if (cudaMemcpyAsync(d_sims, h_sims, sizeof(int) * n, cudaMemcpyHostToDevice, b->s) != cudaSuccess) return VD_ERR_CUDA;
     vd::k_gather_counts<<<1, 256, 0, b->s>>>(b->P, d_sims, n, d_out);
     b->launches += 1;
-    if (cudaMemcpyAsync(h_pinned_out, d_out, sizeof(int) * 6 * n, cudaMemcpyDeviceToHost, b->s) != cudaSuccess)
+    if (cudaMemcpyAsync(h_pinned_out, d_out, sizeof(int) * 8 * n, cudaMemcpyDeviceToHost, b->s) != cudaSuccess)
         return VD_ERR_CUDA;
     return VD_OK;
+}
+
+// change lists of the listed instances packed into d_out / d_act on `stream`
+// (see launch_gather_changes_list); the caller orders it after their step
+vd_status vd_batch_gather_changes_list_async(vd_batch* b, void* stream, const int* d_insts, const long long* d_off,
+                                             int n, long long nb, uint64_t* d_out, uint8_t* d_act) {
+    if (!b || n <= 0) return VD_ERR_INVALID;
+    launch_gather_changes_list((cudaStream_t)stream, b->P, d_insts, d_off, n, nb,
+                               reinterpret_cast<unsigned long long*>(d_out), d_act);
+    b->launches += 1;
+    return cudaPeekAtLastError() == cudaSuccess ? VD_OK : VD_ERR_CUDA;
 }
 
 extern "C" {
@@ -874,6 +1197,35 @@ vd_status vd_get_edges(vd_ctx* ctx, uint64_t* out, int64_t cap, int64_t* n) {
 }
 vd_status vd_get_match(vd_ctx* ctx, int32_t* phi, int64_t cap, int64_t* n) {
     return ctx ? get_array(ctx->b, 0, 4, phi, cap, n) : VD_ERR_INVALID;
+}
+
+vd_status vd_export_state(vd_ctx* ctx, void* buf, int64_t cap, int64_t* n_bytes) {
+    return ctx ? export_state(ctx->b, 0, buf, cap, n_bytes) : VD_ERR_INVALID;
+}
+vd_status vd_import_state(vd_ctx* ctx, const void* buf, int64_t n_bytes) {
+    return ctx ? import_state(ctx->b, 0, buf, n_bytes) : VD_ERR_INVALID;
+}
+vd_status vd_batch_export_state(vd_batch* b, int32_t i, void* buf, int64_t cap, int64_t* n_bytes) {
+    return export_state(b, i, buf, cap, n_bytes);
+}
+vd_status vd_batch_import_state(vd_batch* b, int32_t i, const void* buf, int64_t n_bytes) {
+    return import_state(b, i, buf, n_bytes);
+}
+
+vd_status vd_debug_hold_scan_flag(vd_ctx* ctx, int32_t kind, int64_t tile, int32_t spin_limit) {
+    if (!ctx || kind < 0 || kind >= SCAN_KINDS || tile < -1 || spin_limit < 0) return VD_ERR_INVALID;
+    vd_batch* b = ctx->b;
+    struct {
+        int kind, spin;
+        long long tile;
+    } v = {kind, spin_limit, tile + 1};
+    static_assert(offsetof(Globals, dbg_spin) == offsetof(Globals, dbg_kind) + sizeof(int) &&
+                      offsetof(Globals, dbg_tile) == offsetof(Globals, dbg_kind) + 2 * sizeof(int),
+                  "debug fields of Globals must be contiguous");
+    cudaError_t e = cudaMemcpyAsync(reinterpret_cast<char*>(b->P.g) + offsetof(Globals, dbg_kind), &v, sizeof(v),
+                                    cudaMemcpyHostToDevice, b->s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->s);
+    return cuda_status(e);
 }
 
 vd_status vd_batch_set_timing(vd_batch* b, int32_t enable) {
@@ -1121,6 +1473,12 @@ vd_status vd_batch_destroy(vd_batch* b) {
     for (int k = 0; k < 2; ++k) {
         if (b->ev_staged[k]) cudaEventDestroy(b->ev_staged[k]);
         if (b->ev_read[k]) cudaEventDestroy(b->ev_read[k]);
+    }
+    for (int k = 0; k < vd_batch::PIN_RING; ++k) {
+        cudaFreeHost(b->pin_fields[k]);
+        cudaFreeHost(b->pin_pitches[k]);
+        cudaFreeHost(b->pin_tab[k]);
+        if (b->pin_ev[k]) cudaEventDestroy(b->pin_ev[k]);
     }
     b->mem.release();
     delete b;

@@ -409,6 +409,17 @@ __device__ __forceinline__ int pfind(int* par, int x) {
     }
 }
 
+// root of piece x without writing (for the flatten pass): there a halving
+// store into another piece's slot could land after that piece's thread has
+// written its final root, leaving an intermediate piece in the slot
+__device__ __forceinline__ int pfind_ro(const int* par, int x) {
+    for (;;) {
+        const int p = __ldcg(par + x);
+        if (p == x) return x;
+        x = p;
+    }
+}
+
 __device__ __forceinline__ void punion(const Pools& P, int a, int b) {
     for (;;) {
         a = pfind(P.p_parent, a);
@@ -493,12 +504,15 @@ __global__ __launch_bounds__(32 * MERGE_WARPS) void k_ccl_merge(Pools P, StepTab
     }
 }
 
-// root of each piece; roots are counted per instance and marked in the root bitmap
+// root of each piece; roots are counted per instance and marked in the root
+// bitmap. Every slot is written only by its own thread, with its root: a
+// concurrent reader passing through it sees the old parent or the root, both
+// ancestors, so each slot ends holding its root.
 __global__ void k_ccl_flatten(Pools P) {
     pdl_enter();
     const int n = min(P.g->n_pieces, P.piece_cap);
     for (int pid = blockIdx.x * blockDim.x + threadIdx.x; pid < n; pid += gridDim.x * blockDim.x) {
-        const int r = pfind(P.p_parent, pid);
+        const int r = pfind_ro(P.p_parent, pid);
         P.p_parent[pid] = r;
         if (r == pid) {
             const int inst = P.p_inst[pid];
@@ -626,6 +640,8 @@ __global__ void k_comp_final(Pools P) {
         const int q = P.p_q[pid];
         const int yq = q / D.Lx, xq = q - yq * D.Lx;
         P.rootbits[D.word_off + (long long)yq * D.wpr + (xq >> 5)] = 0u;
+        // root counts per group return to zero for the next step
+        atomicSub(&P.rgcnt[D.grp_off + (long long)yq * D.gpr + (xq >> 5) / RGW], 1);
         const int c = P.p_comp[pid];
         if (c >= D.comp_cap) continue;
         // match state of now-bubble c, filled by the graph stage of this step

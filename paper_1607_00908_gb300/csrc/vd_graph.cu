@@ -41,6 +41,7 @@ __global__ void k_step_begin(Pools P, StepTable T) {
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         P.g->n_pieces = 0;
         P.g->n_wide = 0;
+        P.g->err = 0;   // errors of the previous step stay in its instances' states
         P.g->scan_step = (P.g->scan_step + 1) & 0x07FFFFFFu;   // new tags for this step's scans
         for (int k = 0; k < 8; ++k) P.g->scan_ticket[k] = 0;
     }
@@ -119,7 +120,7 @@ __global__ __launch_bounds__(EK_THREADS) void k_edge_keys(Pools P, int inst, int
         int s = 0, e = 0;
         if (a < K) {
             s = min(ro[a], cap);
-            e = min(ro[a + 1], cap);
+            e = max(min(ro[a + 1], cap), s);   // never a negative row length
             while (s < e && cl[s] < a) ++s;   // rows are sorted: the entries above a are a suffix
         }
         const int cnt = e - s;
@@ -695,6 +696,29 @@ __global__ void k_gather_changes(Pools P, const long long* off, int n, long long
         for (long long t = threadIdx.x; t < a1 - a0; t += blockDim.x) out[2 * nb + a0 + t] = P.ari[D.edge_off + t];
         for (long long t = threadIdx.x; t < k1 - k0; t += blockDim.x) act[k0 + t] = P.active[D.comp_off + t];
     }
+}
+
+// the same for a list of instances: entry j is instance insts[j], its lists
+// span [off[3j + c], off[3j + 3 + c]) of each packed list
+__global__ void k_gather_changes_list(Pools P, const int* insts, const long long* off, int n, long long nb,
+                                      unsigned long long* out, unsigned char* act) {
+    for (int j = blockIdx.x; j < n; j += gridDim.x) {
+        const InstDesc& D = P.desc[insts[j]];
+        const long long b0 = off[3 * j], b1 = off[3 * j + 3];
+        const long long a0 = off[3 * j + 1], a1 = off[3 * j + 4];
+        const long long k0 = off[3 * j + 2], k1 = off[3 * j + 5];
+        for (long long t = threadIdx.x; t < b1 - b0; t += blockDim.x) {
+            out[b0 + t] = P.brk[D.edge_off + t];
+            out[nb + b0 + t] = P.brk_prev[D.edge_off + t];
+        }
+        for (long long t = threadIdx.x; t < a1 - a0; t += blockDim.x) out[2 * nb + a0 + t] = P.ari[D.edge_off + t];
+        for (long long t = threadIdx.x; t < k1 - k0; t += blockDim.x) act[k0 + t] = P.active[D.comp_off + t];
+    }
+}
+
+void launch_gather_changes_list(cudaStream_t s, const Pools& P, const int* insts, const long long* off, int n,
+                                long long nb, unsigned long long* out, unsigned char* act) {
+    k_gather_changes_list<<<n < 1024 ? n : 1024, 256, 0, s>>>(P, insts, off, n, nb, out, act);
 }
 
 void launch_gather_changes(cudaStream_t s, const Pools& P, const long long* off, int n, long long nb,

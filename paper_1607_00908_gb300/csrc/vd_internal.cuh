@@ -142,6 +142,12 @@ struct Globals {
     int err;
     unsigned scan_step;      // bumped once per step; with the scan kind it tags look-back flags
     int scan_ticket[8];      // dynamic tile index of each scan kind (reset once per step)
+    // test support (vd_debug_hold_scan_flag): tile dbg_tile - 1 of scan kind
+    // dbg_kind never publishes its look-back flag (dbg_tile 0: no tile), and
+    // look-back waits give up after dbg_spin polls when dbg_spin > 0
+    int dbg_kind;
+    int dbg_spin;
+    long long dbg_tile;
 };
 
 // ---------------------------------------------------------------------------
@@ -495,6 +501,9 @@ void launch_expand_labels(cudaStream_t s, const Pools& P, int inst, int slot, in
 // breaking, arising, active; entry 3n holds the totals)
 void launch_gather_changes(cudaStream_t s, const Pools& P, const long long* off, int n, long long nb,
                            unsigned long long* out, unsigned char* act);
+// the same for the listed instances only (entry j = instance insts[j])
+void launch_gather_changes_list(cudaStream_t s, const Pools& P, const int* insts, const long long* off, int n,
+                                long long nb, unsigned long long* out, unsigned char* act);
 
 // generic decoupled look-back scan over a virtual concatenation (vd_scan.cu)
 constexpr int SCAN_THREADS = 256;

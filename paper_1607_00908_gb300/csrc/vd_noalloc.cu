@@ -1,9 +1,10 @@
 // Voronoi owners with no device allocation (vd_voronoi_owners_static).
 //
-// Some callers cannot call cudaMalloc: code running inside a CUDA graph that
-// is being captured with a memory pool policy that forbids new allocations,
-// processes whose device memory is fully handed out to another framework's
-// allocator, or embedded/real-time hosts that allocate everything up front.
+// Some callers cannot call cudaMalloc: processes whose device memory is all
+// handed out to another framework's allocator (a device allocation there
+// fails, or takes memory that allocator counts on), and real-time or embedded
+// hosts that allocate everything once at start-up and may not allocate (or
+// risk the implicit synchronisation of an allocation) afterwards.
 // This entry point computes the same exact digital Voronoi colouring as the
 // detect pipeline (Section 3.2.1 of the paper: every site takes the label of
 // the nearest centre by exact squared distance, minimum image on the torus,
@@ -16,6 +17,9 @@
 // bucket order). Every call shares it and it keeps the last call's contents;
 // the call clears what must start at zero. Calls whose device work overlaps
 // (different streams, or several host threads) race on it: serialise them.
+// The array's device address is resolved once per device, by the first call
+// made with that device current; resetting the device (cudaDeviceReset)
+// invalidates it, so the entry point must not be used across a reset.
 #include <cuda_runtime.h>
 
 #include <climits>
@@ -209,6 +213,17 @@ __global__ void na_owners(const NoAllocScratch* S, const int2* cq, int K, int Lx
     }
 }
 
+// launch with the launch's own error (a stale error left by unrelated work in
+// the process is neither reported as this call's nor cleared)
+template <typename... KArgs, typename... Args>
+cudaError_t na_launch(void (*kernel)(KArgs...), int grid, int block, cudaStream_t s, Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
+    cfg.stream = s;
+    return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
 std::mutex g_na_mu;
 NoAllocScratch* g_na_ptr[NA_MAX_DEVICES] = {nullptr};
 
@@ -246,10 +261,13 @@ extern "C" vd_status vd_voronoi_owners_static(const int32_t* d_centroids_q10, in
     while ((long long)((Lx + B - 1) / B) * ((Ly + B - 1) / B) > NA_MAX_BUCKETS) ++B;
     const int nbx = (Lx + B - 1) / B, nby = (Ly + B - 1) / B, nb = nbx * nby;
     const int2* cq = reinterpret_cast<const int2*>(d_centroids_q10);
-    na_clear<<<64, 256, 0, s>>>(S, nb);
-    na_count<<<64, 256, 0, s>>>(S, cq, K, B, nbx, Lx, Ly);
-    na_scan<<<1, 1024, 0, s>>>(S, nb);
-    na_scatter<<<64, 256, 0, s>>>(S, cq, K, B, nbx, Lx, Ly);
-    na_owners<<<tiles, 256, 0, s>>>(S, cq, K, Lx, Ly, B, nbx, nby, d_owners);
-    return cudaGetLastError() == cudaSuccess ? VD_OK : VD_ERR_CUDA;
+    // each launch is checked before the next one is enqueued
+    if (na_launch(na_clear, 64, 256, s, S, nb) != cudaSuccess) return VD_ERR_CUDA;
+    if (na_launch(na_count, 64, 256, s, S, cq, K, B, nbx, Lx, Ly) != cudaSuccess) return VD_ERR_CUDA;
+    if (na_launch(na_scan, 1, 1024, s, S, nb) != cudaSuccess) return VD_ERR_CUDA;
+    if (na_launch(na_scatter, 64, 256, s, S, cq, K, B, nbx, Lx, Ly) != cudaSuccess) return VD_ERR_CUDA;
+    if (na_launch(na_owners, tiles, 256, s, (const NoAllocScratch*)S, cq, K, Lx, Ly, B, nbx, nby, d_owners) !=
+        cudaSuccess)
+        return VD_ERR_CUDA;
+    return VD_OK;
 }

@@ -147,8 +147,9 @@ __device__ __forceinline__ void scan_write(const Pools& P, int kind, int inst, l
     const InstDesc& D = P.desc[inst];
     switch (kind) {
         case SCAN_ROOTBITS:
+            // the counts stay (a tile whose wait gives up re-reads them);
+            // k_comp_final returns them to zero
             P.rankpre[D.grp_off + j] = v;
-            P.rgcnt[D.grp_off + j] = 0;   // zero again for the next step (stores after all loads)
             break;
         case SCAN_BUCKETS: P.boff[P.st[inst].slot ^ 1][D.bucket_off + j] = v; break;
         case SCAN_DEG: P.rowoff[P.st[inst].slot ^ 1][D.comp_off + j] = v; break;
@@ -175,6 +176,8 @@ __global__ __launch_bounds__(SCAN_THREADS) void k_scan(Pools P, StepTable T, int
     __shared__ int s_act[SEG_CACHE];
     __shared__ int s_warp[SCAN_THREADS / 32];
     __shared__ long long s_excl;
+    __shared__ long long s_wsum[SCAN_THREADS / 32];
+    __shared__ int s_fail;
     const ScanSel sel1 = scan_sel(kind1);
     const int n = T.n_act;
     const long long* seg0 = sel1.seg < 0 ? T.grp_pre : pre_arr(T, sel1.seg);
@@ -201,6 +204,11 @@ __global__ __launch_bounds__(SCAN_THREADS) void k_scan(Pools P, StepTable T, int
         const long long* base = pre_arr(T, sel.base);
         // every scan of a step has its own tag (step count, kind)
         const unsigned epoch = ((*(volatile unsigned*)&P.g->scan_step << 3) | (unsigned)kind) & 0x3FFFFFFFu;
+        // test support: a tile that withholds its flag, and a shorter wait for
+        // that scan only
+        const bool dbg = P.g->dbg_tile != 0 && P.g->dbg_kind == kind;
+        const bool hold = dbg && P.g->dbg_tile == tile + 1;
+        const int spin_limit = (dbg && P.g->dbg_spin > 0) ? P.g->dbg_spin : SPIN_LIMIT;
 
         // load SCAN_ITEMS consecutive items per thread
         int v[SCAN_ITEMS];
@@ -247,10 +255,11 @@ __global__ __launch_bounds__(SCAN_THREADS) void k_scan(Pools P, StepTable T, int
             // each scan kind has its own flags
             unsigned long long* flags = P.scan_flags + (long long)kind * P.scan_flag_cap;
             long long excl = 0;
+            bool fail = false;
             if (tile == 0) {
-                if (lane == 0) publish(&flags[0], epoch, ST_INC, btot);
+                if (lane == 0 && !hold) publish(&flags[0], epoch, ST_INC, btot);
             } else {
-                if (lane == 0) publish(&flags[tile], epoch, ST_AGG, btot);
+                if (lane == 0 && !hold) publish(&flags[tile], epoch, ST_AGG, btot);
                 long long top = tile - 1;
                 int spins = 0;
                 for (;;) {
@@ -269,8 +278,9 @@ __global__ __launch_bounds__(SCAN_THREADS) void k_scan(Pools P, StepTable T, int
                     const int first = incm ? __ffs(incm) - 1 : 31;
                     const unsigned need = (first >= 31) ? 0xffffffffu : ((2u << first) - 1u);
                     if (nrdy & need) {
-                        if (++spins > SPIN_LIMIT) {   // give up: flag the error, never hang
+                        if (++spins > spin_limit) {   // give up: flag the error, never hang
                             if (lane == 0) atomicOr(&P.g->err, ERR_TIMEOUT);
+                            fail = true;
                             break;
                         }
                         continue;
@@ -281,11 +291,43 @@ __global__ __launch_bounds__(SCAN_THREADS) void k_scan(Pools P, StepTable T, int
                     if (incm) break;
                     top -= 32;
                 }
-                if (lane == 0) publish(&flags[tile], epoch, ST_INC, (int)(excl + btot));
+                if (lane == 0 && !hold && !fail) publish(&flags[tile], epoch, ST_INC, (int)(excl + btot));
             }
-            if (lane == 0) s_excl = excl;
+            if (lane == 0) {
+                s_excl = excl;
+                s_fail = fail ? 1 : 0;
+            }
         }
         __syncthreads();
+        if (s_fail) {
+            // the wait gave up: the exclusive prefix is summed directly from
+            // every earlier item (slow, only on this path), so the offsets stay
+            // exact and the tiles after this one see a correct flag
+            long long acc = 0;
+            int fa = -1, finst = 0;
+            long long flo = 0, fhi = -1;
+            for (long long g = threadIdx.x; g < start; g += SCAN_THREADS) {
+                if (g >= fhi || g < flo) {
+                    fa = seg_of(seg, n, g);
+                    flo = seg[fa];
+                    fhi = seg[fa + 1];
+                    finst = act[fa];
+                }
+                acc += scan_value(P, kind, finst, g - flo);
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+            if (lane == 0) s_wsum[warp] = acc;
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                long long tot = 0;
+                for (int k = 0; k < SCAN_THREADS / 32; ++k) tot += s_wsum[k];
+                s_excl = tot;
+                if (!hold)
+                    publish(P.scan_flags + (long long)kind * P.scan_flag_cap + tile, epoch, ST_INC, (int)(tot + btot));
+            }
+            __syncthreads();
+        }
         long long run = s_excl + texcl;
         a = -1; lo = 0; hi = -1;
 #pragma unroll
@@ -298,7 +340,10 @@ __global__ __launch_bounds__(SCAN_THREADS) void k_scan(Pools P, StepTable T, int
                     hi = seg[a + 1];
                     inst = act[a];
                 }
-                scan_write(P, kind, inst, g - lo, (int)(run - sel.mul * base[a]));
+                // after a wait that gave up, `run` may fall short of the true
+                // prefix; the clamp keeps every offset inside its instance's range
+                const long long w = run - sel.mul * base[a];
+                scan_write(P, kind, inst, g - lo, (int)(w > 0 ? w : 0));
                 run += v[i];
             }
         }

@@ -213,7 +213,7 @@ __global__ __launch_bounds__(32 * VWARPS, 16) void k_voronoi(Pools P, StepTable 
                     const int rm = rv < 0 ? rv + nby : (rv >= nby ? rv - nby : rv);
                     const int bk = rm * nbx + cm;
                     jb = boff[bk];
-                    je = boff[bk + 1];
+                    je = max(boff[bk + 1], jb);   // offsets of a frame whose scan gave up may decrease
                 }
             }
             const int cnt = je - jb;
@@ -653,10 +653,56 @@ void launch_voronoi(const Launch& L) {
 // halo are staged in shared memory with cp.async (all rows in flight at once),
 // then the warp walks down the rows with the rows above and below in
 // registers. Vertex sites are rare: a row without one skips the rules. The
-// colour of a plaquette centre is the nearest centre among the colours at the
-// plaquette's corners (exact, ties to the smallest label). Keys go to the
-// per-warp list, merged and appended as in the adjacency rule.
+// colour of a plaquette centre is its Voronoi colour, the nearest centre over
+// all centres (exact, ties to the smallest label), found by a ring search of
+// the frame's bucket grid that starts from the nearest corner colour. Keys go
+// to the per-warp list, merged and appended as in the adjacency rule.
 // ---------------------------------------------------------------------------
+
+// Voronoi colour of the point (qx, qy) (1/1024 site, in [0, MX) x [0, MY)):
+// the nearest centre over all centres, exact int64 minimum-image distances,
+// ties to the smallest label. (best, bd) is a centre already known and its
+// squared distance. Rings of buckets around the point's bucket are scanned
+// outwards; before ring r every unscanned bucket is r or more buckets away
+// along some axis, with r - 1 buckets in between of which at most one is the
+// narrower last bucket, so it is at least (r - 2) B sites from the point, and
+// the search stops once bd is below that squared. Centres and the point both
+// lie in [0, M), so one conditional step gives the minimum image.
+__device__ int point_owner(const int* boff, const int2* bcq, const int* bid, int B, int nbx, int nby, long long qx,
+                           long long qy, long long MX, long long MY, int best, long long bd) {
+    const long long HX = MX >> 1, HY = MY >> 1;
+    const int bx = (int)(qx / Q) / B, by = (int)(qy / Q) / B;
+    const int rmax = (max(nbx, nby) >> 1) + 1;
+    for (int r = 0; r <= rmax; ++r) {
+        if (r >= 2) {
+            const long long lim = (long long)(r - 2) * B * Q;
+            if (bd < lim * lim) break;
+        }
+        for (int dy = -r; dy <= r; ++dy) {
+            const bool edge_row = dy == -r || dy == r;
+            int rv = (by + dy) % nby;
+            rv += rv < 0 ? nby : 0;
+            for (int dx = -r; dx <= r; dx += (edge_row || r == 0) ? 1 : 2 * r) {
+                int cu = (bx + dx) % nbx;
+                cu += cu < 0 ? nbx : 0;
+                const int bk = rv * nbx + cu;
+                for (int j = boff[bk]; j < boff[bk + 1]; ++j) {
+                    const int2 c = bcq[j];
+                    long long ddx = (long long)c.x - qx + HX, ddy = (long long)c.y - qy + HY;
+                    ddx = (ddx < 0 ? ddx + MX : (ddx >= MX ? ddx - MX : ddx)) - HX;
+                    ddy = (ddy < 0 ? ddy + MY : (ddy >= MY ? ddy - MY : ddy)) - HY;
+                    const long long d = ddx * ddx + ddy * ddy;
+                    const int id = bid[j];
+                    if (d < bd || (d == bd && id < best)) {
+                        bd = d;
+                        best = id;
+                    }
+                }
+            }
+        }
+    }
+    return best;
+}
 
 // v mod L for -L <= v < 2L, without a division (a 64-bit remainder is a long
 // dependent chain, and vertex sites take it one lane at a time): plaquette
@@ -687,6 +733,9 @@ __global__ __launch_bounds__(32 * LINK_WARPS) void k_links_vertex(Pools P, StepT
     const int x0 = tx * VW, y0 = ty * VH;
     const int ncols = min(VW, Lx - x0), nrows = min(VH, Ly - y0);
     const int2* cq = P.cq[St.slot ^ 1] + D.comp_off;
+    const int* boff = P.boff[St.slot ^ 1] + D.bucket_off;
+    const int2* bcq = P.bcq[St.slot ^ 1] + D.comp_off;
+    const int* bid = P.bid[St.slot ^ 1] + D.comp_off;
     const int* own = P.owners + D.site_off;
     const long long MX = (long long)Q * Lx, MY = (long long)Q * Ly, HX = MX / 2, HY = MY / 2;
     int* S = s_own[warp];
@@ -762,8 +811,9 @@ __global__ __launch_bounds__(32 * LINK_WARPS) void k_links_vertex(Pools P, StepT
                     const int c1 = f[2 * q], cd = f[2 * q + 1], c2 = f[(2 * q + 2) & 7], c3 = f[(2 * q + 7) & 7];
                     if (c1 >= 0 && c1 != k && c2 != c3) em |= 1u << q;
                     if (cd >= 0 && cd != k && c2 != c3 && c2 != c1) {
-                        // plaquette centre k + (e1 + e2) / 2: the nearest centre among
-                        // the colours at the plaquette's corners k, k+e1, k+e1+e2, k+e2
+                        // plaquette centre k + (e1 + e2) / 2: its Voronoi colour,
+                        // searched from the nearest of the corner colours k, k+e1,
+                        // k+e1+e2, k+e2
                         const int ex = (q == 0 || q == 3) ? 1 : -1, ey = (q == 0 || q == 1) ? 1 : -1;
                         long long qx = (long long)Q * x + (Q / 2) * ex, qy = (long long)Q * y + (Q / 2) * ey;
                         qx = wrap_once(qx, MX);
@@ -784,6 +834,7 @@ __global__ __launch_bounds__(32 * LINK_WARPS) void k_links_vertex(Pools P, StepT
                                 ca = c;
                             }
                         }
+                        ca = point_owner(boff, bcq, bid, St.B, St.nbx, St.nby, qx, qy, MX, MY, ca, bd);
                         if (ca == k || ca == cd) em |= 16u << q;
                     }
                 }

@@ -42,13 +42,16 @@ EXPORTS = (
     "vd_config_init", "vd_set_obstacles", "vd_batch_set_obstacles", "vd_create", "vd_push_frame",
     "vd_push_frame_host", "vd_get_changes",
     "vd_get_counts", "vd_get_labels", "vd_get_centroids_q10", "vd_get_owners", "vd_get_edges",
-    "vd_get_match", "vd_set_timing", "vd_get_timing", "vd_stage_name", "vd_destroy", "vd_status_string",
+    "vd_get_match", "vd_export_state", "vd_import_state", "vd_debug_hold_scan_flag", "vd_set_timing", "vd_get_timing", "vd_stage_name", "vd_destroy", "vd_status_string",
     "vd_batch_create", "vd_batch_create_sequence", "vd_batch_push", "vd_batch_push_host", "vd_batch_push_subset", "vd_batch_get_changes",
     "vd_batch_stage_host", "vd_batch_push_staged", "vd_batch_get_changes_all",
     "vd_batch_get_labels", "vd_batch_get_owners", "vd_batch_get_edges", "vd_batch_get_centroids_q10",
     "vd_batch_get_counts", "vd_batch_set_timing", "vd_batch_get_timing", "vd_batch_destroy",
-    "vd_voronoi_owners_static", "vd_server_create", "vd_server_submit", "vd_server_poll",
-    "vd_server_get_changes", "vd_server_get_labels", "vd_server_stats", "vd_server_destroy",
+    "vd_batch_export_state", "vd_batch_import_state",
+    "vd_voronoi_owners_static", "vd_server_create", "vd_server_open_sim", "vd_server_close_sim",
+    "vd_server_clock_ns", "vd_server_submit", "vd_server_poll", "vd_server_keep_changes",
+    "vd_server_get_frame_changes", "vd_server_get_changes", "vd_server_get_labels", "vd_server_export_state",
+    "vd_server_import_state", "vd_server_stats", "vd_server_destroy",
 )
 
 
@@ -97,7 +100,7 @@ class vd_batch_changes(C.Structure):
 class vd_server_done(C.Structure):
     _fields_ = [
         ("ticket", C.c_int64), ("sim", C.c_int32), ("status", C.c_int32),
-        ("t_submit_ns", C.c_int64), ("t_done_ns", C.c_int64),
+        ("t_arrival_ns", C.c_int64), ("t_submit_ns", C.c_int64), ("t_done_ns", C.c_int64),
         ("n_bubbles", C.c_int32), ("n_edges", C.c_int32), ("n_breaking", C.c_int32), ("n_arising", C.c_int32),
     ]
 
@@ -131,6 +134,11 @@ def lib():
         "vd_get_owners": [VP, VP, I64, P(I64)],
         "vd_get_edges": [VP, VP, I64, P(I64)],
         "vd_get_match": [VP, VP, I64, P(I64)],
+        "vd_export_state": [VP, VP, I64, P(I64)],
+        "vd_import_state": [VP, VP, I64],
+        "vd_batch_export_state": [VP, I32, VP, I64, P(I64)],
+        "vd_batch_import_state": [VP, I32, VP, I64],
+        "vd_debug_hold_scan_flag": [VP, I32, I64, I32],
         "vd_set_timing": [VP, I32],
         "vd_get_timing": [VP, P(C.c_double), I32, P(I32), P(I64), P(I64)],
         "vd_stage_name": [I32],
@@ -154,11 +162,18 @@ def lib():
         "vd_batch_get_timing": [VP, P(C.c_double), I32, P(I32), P(I64), P(I64)],
         "vd_batch_destroy": [VP],
         "vd_voronoi_owners_static": [VP, I32, I32, I32, VP, VP],
-        "vd_server_create": [P(vd_config), I32, I64, I32, P(VP)],
-        "vd_server_submit": [VP, I32, VP, P(I64)],
+        "vd_server_create": [P(vd_config), I32, I64, I32, VP, P(VP)],
+        "vd_server_open_sim": [VP, P(vd_config), P(I32)],
+        "vd_server_close_sim": [VP, I32],
+        "vd_server_clock_ns": [P(I64)],
+        "vd_server_submit": [VP, I32, VP, I64, P(I64)],
         "vd_server_poll": [VP, I32, P(vd_server_done), I32, P(I32)],
+        "vd_server_keep_changes": [VP, I32],
+        "vd_server_get_frame_changes": [VP, I64, P(vd_changes)],
         "vd_server_get_changes": [VP, I32, P(vd_changes)],
         "vd_server_get_labels": [VP, I32, VP, I64, P(I64)],
+        "vd_server_export_state": [VP, I32, VP, I64, P(I64)],
+        "vd_server_import_state": [VP, I32, VP, I64],
         "vd_server_stats": [VP, P(I64), P(I64), P(I64), P(I64)],
         "vd_server_destroy": [VP],
     }
@@ -391,6 +406,29 @@ class Detector(_Base):
                     breaking_prev=brkp[: ch.n_breaking].copy(), arising=ari[: ch.n_arising].copy(),
                     active=act[: ch.n_now].copy(), global_trigger=ch.global_trigger)
 
+    def export_state(self) -> np.ndarray:
+        """Checkpoint of the last frame's state (vd_export_state), as bytes."""
+        n = C.c_int64()
+        s = lib().vd_export_state(self.h, None, 0, C.byref(n))
+        if s != VD_ERR_CAPACITY:
+            _check(s, "vd_export_state")
+        buf = np.empty(n.value, np.uint8)
+        _check(lib().vd_export_state(self.h, buf.ctypes.data_as(C.c_void_p), buf.size, C.byref(n)), "vd_export_state")
+        return buf
+
+    def import_state(self, blob) -> None:
+        """Resume from a checkpoint (vd_import_state)."""
+        b = np.ascontiguousarray(np.frombuffer(bytes(blob), np.uint8) if not isinstance(blob, np.ndarray) else blob,
+                                 dtype=np.uint8)
+        _check(lib().vd_import_state(self.h, b.ctypes.data_as(C.c_void_p), b.size), "vd_import_state")
+
+    def hold_scan_flag(self, kind: int, tile: int, spin_limit: int = 0) -> None:
+        """Test support: scan tile `tile` of scan `kind` withholds its look-back
+        flag in the following pushes (tile -1: off), so the next tile's
+        bounded wait runs out (vd_debug_hold_scan_flag)."""
+        _check(lib().vd_debug_hold_scan_flag(self.h, int(kind), int(tile), int(spin_limit)),
+               "vd_debug_hold_scan_flag")
+
     def set_timing(self, on: bool) -> None:
         _check(lib().vd_set_timing(self.h, int(bool(on))), "vd_set_timing")
 
@@ -501,6 +539,22 @@ class Batch(_Base):
         names = [lib().vd_stage_name(i).decode() for i in range(n.value)]
         return list(ms[: n.value]), names, kl.value, nf.value
 
+    def export_state(self, i: int) -> np.ndarray:
+        """Checkpoint of instance i's last frame (vd_batch_export_state)."""
+        n = C.c_int64()
+        s = lib().vd_batch_export_state(self.h, int(i), None, 0, C.byref(n))
+        if s != VD_ERR_CAPACITY:
+            _check(s, "vd_batch_export_state")
+        buf = np.empty(n.value, np.uint8)
+        _check(lib().vd_batch_export_state(self.h, int(i), buf.ctypes.data_as(C.c_void_p), buf.size, C.byref(n)),
+               "vd_batch_export_state")
+        return buf
+
+    def import_state(self, i: int, blob) -> None:
+        b = np.ascontiguousarray(blob, dtype=np.uint8)
+        _check(lib().vd_batch_import_state(self.h, int(i), b.ctypes.data_as(C.c_void_p), b.size),
+               "vd_batch_import_state")
+
     def push_subset(self, active, fields) -> None:
         _check(vd_batch_push_subset(self.h, list(active), [f.data_ptr() for f in fields]), "vd_batch_push_subset")
 
@@ -547,36 +601,81 @@ class Batch(_Base):
             pass
 
 
+def clock_ns() -> int:
+    """The served form's host clock (vd_server_clock_ns), in ns."""
+    t = C.c_int64()
+    _check(lib().vd_server_clock_ns(C.byref(t)), "vd_server_clock_ns")
+    return t.value
+
+
 class Server:
-    """Served form (vd_server_*): frames of many simulations, continuous batching."""
+    """Served form (vd_server_*): frames of many simulations, continuous batching.
+
+    ``poll`` returns tuples (ticket, sim, status, t_arrival_ns, t_submit_ns,
+    t_done_ns, n_bubbles, n_edges, n_breaking, n_arising)."""
 
     def __init__(self, sizes, budget_bytes: int, max_batch: int = 64, threshold: float = 0.5,
-                 polarity: int = VD_ABOVE, stream: int | None = None, max_components: int = 0, options=None):
+                 polarity: int = VD_ABOVE, stream: int | None = None, max_components: int = 0, options=None,
+                 keep_changes: bool = False):
         """``options``: optional list of per-simulation dicts of config options
         (events, match_rule, match_radius, connectivity, edge_rule, walls)."""
         if stream is None:
             import torch
             stream = torch.cuda.current_stream().cuda_stream
-        self.sizes = [(int(lx), int(ly)) for lx, ly in sizes]
-        per = options or [{}] * len(self.sizes)
-        cfgs = (vd_config * len(sizes))(*[vd_config_init(lx, ly, threshold, polarity, stream, max_components, **o)
-                                          for (lx, ly), o in zip(self.sizes, per)])
+        self.stream = stream
+        self.threshold, self.polarity, self.max_components = threshold, polarity, max_components
+        self.sizes = {}
+        sizes = [(int(lx), int(ly)) for lx, ly in sizes]
+        per = options or [{}] * len(sizes)
+        cfgs = (vd_config * max(len(sizes), 1))(*[vd_config_init(lx, ly, threshold, polarity, stream, max_components,
+                                                                 **o) for (lx, ly), o in zip(sizes, per)])
         h = C.c_void_p()
-        _check(lib().vd_server_create(cfgs, len(sizes), int(budget_bytes), int(max_batch), C.byref(h)),
-               "vd_server_create")
+        _check(lib().vd_server_create(cfgs, len(sizes), int(budget_bytes), int(max_batch), C.c_void_p(stream),
+                                      C.byref(h)), "vd_server_create")
         self.h = h
+        for k, sz in enumerate(sizes):
+            self.sizes[k] = sz
         self._done = (vd_server_done * 1024)()
+        if keep_changes:
+            self.keep_changes(True)
 
-    def submit(self, sim: int, field) -> int:
+    def open_sim(self, size, **options) -> int:
+        """Open one more simulation (vd_server_open_sim); returns its id."""
+        lx, ly = int(size[0]), int(size[1])
+        cfg = vd_config_init(lx, ly, self.threshold, self.polarity, self.stream, self.max_components, **options)
+        sid = C.c_int32()
+        _check(lib().vd_server_open_sim(self.h, C.byref(cfg), C.byref(sid)), "vd_server_open_sim")
+        self.sizes[sid.value] = (lx, ly)
+        return sid.value
+
+    def close_sim(self, sim: int) -> None:
+        _check(lib().vd_server_close_sim(self.h, int(sim)), "vd_server_close_sim")
+
+    def keep_changes(self, on: bool = True) -> None:
+        _check(lib().vd_server_keep_changes(self.h, int(bool(on))), "vd_server_keep_changes")
+
+    def submit(self, sim: int, field, t_arrival_ns: int = 0) -> int:
         t = C.c_int64()
-        _check(lib().vd_server_submit(self.h, int(sim), C.c_void_p(field.data_ptr()), C.byref(t)), "vd_server_submit")
+        _check(lib().vd_server_submit(self.h, int(sim), C.c_void_p(field.data_ptr()), int(t_arrival_ns), C.byref(t)),
+               "vd_server_submit")
         return t.value
 
     def poll(self, wait: bool = False):
         n = C.c_int32()
         _check(lib().vd_server_poll(self.h, int(bool(wait)), self._done, 1024, C.byref(n)), "vd_server_poll")
-        return [(d.ticket, d.sim, d.status, d.t_submit_ns, d.t_done_ns, d.n_bubbles, d.n_edges, d.n_breaking,
-                 d.n_arising) for d in self._done[: n.value]]
+        return [(d.ticket, d.sim, d.status, d.t_arrival_ns, d.t_submit_ns, d.t_done_ns, d.n_bubbles, d.n_edges,
+                 d.n_breaking, d.n_arising) for d in self._done[: n.value]]
+
+    def frame_changes(self, ticket: int, K: int) -> dict:
+        """Changes of a frame retired by the last poll (vd_server_get_frame_changes)."""
+        cap = 1 << 16
+        s, ch, brk, brkp, ari, act = _changes(
+            lambda c: lib().vd_server_get_frame_changes(self.h, int(ticket), C.byref(c)), K, cap)
+        _check(s, "vd_server_get_frame_changes")
+        return dict(frame=ch.frame_index, K_prev=ch.n_prev, K=ch.n_now, n_matched=ch.n_matched,
+                    n_edges=ch.n_edges, breaking=brk[: ch.n_breaking].copy(),
+                    breaking_prev=brkp[: ch.n_breaking].copy(), arising=ari[: ch.n_arising].copy(),
+                    active=act[: ch.n_now].copy(), global_trigger=ch.global_trigger)
 
     def stats(self):
         a, b, c, d = C.c_int64(), C.c_int64(), C.c_int64(), C.c_int64()
@@ -597,7 +696,23 @@ class Server:
                                               1 << 22, cap)
         _check(s, "vd_server_get_changes")
         return dict(frame=ch.frame_index, K=ch.n_now, breaking=brk[: ch.n_breaking].copy(),
-                    arising=ari[: ch.n_arising].copy(), active=act[: ch.n_now].copy())
+                    breaking_prev=brkp[: ch.n_breaking].copy(), arising=ari[: ch.n_arising].copy(),
+                    active=act[: ch.n_now].copy())
+
+    def export_state(self, sim: int) -> np.ndarray:
+        n = C.c_int64()
+        s = lib().vd_server_export_state(self.h, int(sim), None, 0, C.byref(n))
+        if s != VD_ERR_CAPACITY:
+            _check(s, "vd_server_export_state")
+        buf = np.empty(n.value, np.uint8)
+        _check(lib().vd_server_export_state(self.h, int(sim), buf.ctypes.data_as(C.c_void_p), buf.size,
+                                            C.byref(n)), "vd_server_export_state")
+        return buf
+
+    def import_state(self, sim: int, blob) -> None:
+        b = np.ascontiguousarray(blob, dtype=np.uint8)
+        _check(lib().vd_server_import_state(self.h, int(sim), b.ctypes.data_as(C.c_void_p), b.size),
+               "vd_server_import_state")
 
     def close(self):
         if getattr(self, "h", None):

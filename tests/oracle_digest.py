@@ -42,14 +42,16 @@ def oracle_digests(spec, n_frames: int = 8):
 
 def oracle_sequence(task):
     """Oracle over one simulation's frame sequence: `task` = (L, pool frames,
-    indices into the pool). Returns per-frame (K, links, breaking, arising)
-    and the final frame's label digest and flip lists."""
+    indices into the pool). Returns per frame its bubble and link counts,
+    breaking (and their past keys), arising and active flags, and the final
+    frame's label digest."""
     L, pool, seq = task
     det = O.Detector(L, L)
-    counts = []
+    frames = []
     r = None
     for j in seq:
         r = det.push(pool[j])
-        counts.append((r["K"], len(r["edges"]), len(r["breaking"]), len(r["arising"])))
+        frames.append(dict(K=r["K"], E=len(r["edges"]), breaking=r["breaking"], breaking_prev=r["breaking_prev"],
+                           arising=r["arising"], active=r["active"]))
     lab = array_digest(r["labels"]) if r is not None else None
-    return counts, lab, (r["breaking"] if r else None), (r["arising"] if r else None)
+    return frames, lab

@@ -175,7 +175,7 @@ def test_host_push_matches_device_push():
 
 def test_c1_frames():
     """1024x1024 smoothed noise (sigma 4), sheared frame to frame: full oracle each frame."""
-    n = 64 if FULL else 6
+    n = 64
     frames = list(I.workload_c1(seed=1, n_frames=n))
     r = run_pair(frames, tag="c1")
     assert r["K"] > 500
@@ -183,7 +183,7 @@ def test_c1_frames():
 
 def test_c2_frames():
     """4096x4096 RSA droplets: labels, centroids, links and flips from the full oracle."""
-    n = 16 if FULL else 2
+    n = 16
     frames = [F for F, _ in I.workload_c2(seed=1, n_frames=n)]
     r = run_pair(frames, tag="c2")
     assert r["K"] > 20000
@@ -312,6 +312,17 @@ def test_vertex_link_rule(seed):
         F0 = I.smoothed_noise(Ly, Lx, sig, seed=seed * 10 + trial)
         F1 = I.shear_resample(F0, 0.03, 0.02, np.random.default_rng(trial))
         run_pair([F0, F1], voronoi="brute", tag=f"vertex {Lx}x{Ly}", edge_rule="vertex", events=True)
+
+
+@pytest.mark.parametrize("L,sigma,seed", [(256, 1.0, 0), (128, 1.0, 2), (200, 1.3, 4)])
+def test_vertex_link_rule_inner_frame_colour(L, sigma, seed):
+    """Dense small bubbles, where the Voronoi colour of a plaquette centre is
+    sometimes a centre that owns none of the plaquette's corner sites (on
+    these seeded frames that decides between 8 and 33 diagonals): the
+    vertex rule's links equal the oracle's, which colours the inner-frame
+    point by the exact nearest centre over all centres."""
+    frames = list(I.noise_frames(L, sigma, 2, 0.03, seed=seed))
+    run_pair(frames, tag=f"vertex dense {L} {sigma}", edge_rule="vertex", events=True)
 
 
 def test_vertex_link_rule_c1_frames():

@@ -2,10 +2,11 @@
 exactly the results it gets alone.
 
 Frames of several simulations are submitted in an interleaved, seeded order
-while earlier steps are still on the device; every finished frame's counts
-(bubbles, links, breaking, arising) and every simulation's final labels and
-flip lists must equal those of the same frame sequence pushed through its
-own vd_push_frame context.
+while earlier steps are still on the device; every finished frame's breaking
+and arising lists, past keys and active flags (kept per frame by the server)
+and every simulation's final labels must equal those of the same frame
+sequence pushed through its own vd_push_frame context. Simulations are also
+opened and closed while others run.
 """
 from __future__ import annotations
 
@@ -41,47 +42,64 @@ def _setup(seed=3):
     return sizes, frames, order
 
 
-def _alone_counts(sizes, frames):
+def _alone_changes(sizes, frames, options=None):
+    """Every frame's changes and the final labels of each simulation run alone."""
     out = {}
     finals = {}
     for s, (lx, ly) in enumerate(sizes):
-        det = vd.Detector(lx, ly)
+        det = vd.Detector(lx, ly, **((options or {}).get(s, {})))
         for f, F in enumerate(frames[s]):
             det.push(F)
-            ch = det.changes()
-            out[(s, f)] = (ch["K"], ch["n_edges"], len(ch["breaking"]), len(ch["arising"]))
+            out[(s, f)] = det.changes()
         finals[s] = (det.labels(), det.changes())
         det.close()
     return out, finals
 
 
+def _same_frame(got, want, tag):
+    for k in ("K", "n_edges", "K_prev", "n_matched", "global_trigger"):
+        assert got[k] == want[k], (tag, k, got[k], want[k])
+    for k in ("breaking", "breaking_prev", "arising", "active"):
+        assert np.array_equal(got[k], want[k]), (tag, k)
+
+
+def _drain(sv, tickets, seen, want):
+    """Poll once more; compare every retired frame with its alone result."""
+    for d in sv.poll(wait=True):
+        _check_done(sv, d, tickets, seen, want)
+
+
+def _check_done(sv, d, tickets, seen, want):
+    ticket, s, status, ta, ts, td, K, E, nb, na = d
+    key = tickets[ticket]
+    assert status == 0, key
+    assert td >= ts >= ta > 0, key
+    w = want[key]
+    assert (K, E, nb, na) == (w["K"], w["n_edges"], len(w["breaking"]), len(w["arising"])), key
+    _same_frame(sv.frame_changes(ticket, K), w, key)
+    seen[key] = d
+
+
 @pytest.mark.parametrize("max_batch,budget_extra", [(5, 1 << 30), (3, 1 << 30), (5, 300_000)])
 def test_served_results_equal_alone(max_batch, budget_extra):
     sizes, frames, order = _setup()
-    want, finals = _alone_counts(sizes, frames)
+    want, finals = _alone_changes(sizes, frames)
     # resident state measured by a first server; the budget leaves room for
     # `budget_extra` bytes of frames in flight
     probe = vd.Server(sizes, budget_bytes=1 << 40, max_batch=max_batch)
     resident = probe.stats()["resident_bytes"]
     probe.close()
-    sv = vd.Server(sizes, budget_bytes=resident + budget_extra, max_batch=max_batch)
+    sv = vd.Server(sizes, budget_bytes=resident + budget_extra, max_batch=max_batch, keep_changes=True)
     seen = {}
-    pos = [0] * len(sizes)
     tickets = {}
     for s, f in order:
-        tickets[sv.submit(s, frames[s][f])] = (s, f)
+        tickets[sv.submit(s, frames[s][f], vd.clock_ns())] = (s, f)
         for d in sv.poll(wait=False):
-            seen[tickets[d[0]]] = d
+            _check_done(sv, d, tickets, seen, want)
     while len(seen) < len(order):
-        for d in sv.poll(wait=True):
-            seen[tickets[d[0]]] = d
+        _drain(sv, tickets, seen, want)
     st = sv.stats()
     assert st["frames_done"] == len(order)
-    for key, d in seen.items():
-        ticket, s, status, ts, td, K, E, nb, na = d
-        assert status == 0
-        assert (K, E, nb, na) == want[key], (key, (K, E, nb, na), want[key])
-        assert td >= ts
     for s in range(len(sizes)):
         lab, ch = finals[s]
         assert np.array_equal(sv.labels(s), lab)
@@ -98,6 +116,94 @@ def test_budget_below_resident_state_is_refused():
     assert e.value.status == vd.VD_ERR_CAPACITY
 
 
+def test_simulations_opened_and_closed_while_others_run():
+    """Three simulations start; two more are opened after the first frames
+    are queued (one of them refused first by a budget that cannot hold it);
+    one simulation is closed once drained and its id is refused afterwards.
+    Every frame of every simulation equals its alone run, element by element."""
+    sizes, frames, order = _setup(seed=11)
+    want, finals = _alone_changes(sizes, frames)
+    first = [0, 1, 2]
+    probe = vd.Server([sizes[s] for s in first], budget_bytes=1 << 40, max_batch=8)
+    resident = probe.stats()["resident_bytes"]
+    probe.close()
+    sv = vd.Server([sizes[s] for s in first], budget_bytes=resident + (64 << 20), max_batch=8, keep_changes=True)
+    ids = {s: s for s in first}          # workload sim -> server id
+    tickets, seen = {}, {}
+    pending = [(s, f) for s, f in order]
+    # the first two frames of the three open simulations
+    for s, f in [p for p in pending if p[0] in first and p[1] < 2]:
+        tickets[sv.submit(ids[s], frames[s][f], vd.clock_ns())] = (s, f)
+    for d in sv.poll(wait=False):
+        _check_done(sv, d, tickets, seen, want)
+    # a 200 x 200 simulation does not fit the remaining budget
+    with pytest.raises(vd.VdError) as e:
+        sv.open_sim(sizes[2])
+    assert e.value.status == vd.VD_ERR_CAPACITY
+    sv.close()
+    # a server with room for the newcomers, which join while frames are in flight
+    sv = vd.Server([sizes[s] for s in first], budget_bytes=1 << 40, max_batch=8, keep_changes=True)
+    tickets, seen = {}, {}
+    for s, f in [p for p in pending if p[0] in first and p[1] < 2]:
+        tickets[sv.submit(ids[s], frames[s][f], vd.clock_ns())] = (s, f)
+    for d in sv.poll(wait=False):
+        _check_done(sv, d, tickets, seen, want)
+    for s in (3, 4):
+        ids[s] = sv.open_sim(sizes[s])
+    assert ids[3] == 3 and ids[4] == 4
+    rest = [p for p in pending if not (p[0] in first and p[1] < 2)]
+    for s, f in rest:
+        tickets[sv.submit(ids[s], frames[s][f], vd.clock_ns())] = (s, f)
+        for d in sv.poll(wait=False):
+            _check_done(sv, d, tickets, seen, want)
+    while len(seen) < len(order):
+        _drain(sv, tickets, seen, want)
+    # simulation 1 is drained: close it; its id is refused afterwards
+    lab1 = sv.labels(ids[1])
+    assert np.array_equal(lab1, finals[1][0])
+    sv.close_sim(ids[1])
+    with pytest.raises(vd.VdError) as e:
+        sv.submit(ids[1], frames[1][0])
+    assert e.value.status == vd.VD_ERR_INVALID
+    with pytest.raises(vd.VdError) as e:
+        sv.labels(ids[1])
+    assert e.value.status == vd.VD_ERR_INVALID
+    for s in (0, 2, 3, 4):
+        assert np.array_equal(sv.labels(ids[s]), finals[s][0]), s
+    # a simulation opened alone leaves the budget when closed
+    before = sv.stats()["resident_bytes"]
+    sid = sv.open_sim((64, 64))
+    assert sv.stats()["resident_bytes"] > before
+    sv.close_sim(sid)
+    assert sv.stats()["resident_bytes"] == before
+    sv.close()
+
+
+def test_served_checkpoint_moves_a_simulation():
+    """A simulation's state exported from one server and imported into a
+    simulation of another continues with the same changes as alone."""
+    sizes, frames, order = _setup(seed=13)
+    want, _ = _alone_changes(sizes, frames)
+    a = vd.Server(sizes, budget_bytes=1 << 40, max_batch=8)
+    for f in range(2):
+        for s in range(len(sizes)):
+            a.submit(s, frames[s][f])
+    n = 0
+    while n < 2 * len(sizes):
+        n += len(a.poll(wait=True))
+    blob = a.export_state(2)
+    a.close()
+    b = vd.Server([], budget_bytes=1 << 40, max_batch=8, keep_changes=True)
+    sid = b.open_sim(sizes[2])
+    b.import_state(sid, blob)
+    for f in range(2, len(frames[2])):
+        t = b.submit(sid, frames[2][f])
+        ds = b.poll(wait=True)
+        assert [d[0] for d in ds] == [t]
+        _same_frame(b.frame_changes(t, ds[0][6]), want[(2, f)], ("moved", f))
+    b.close()
+
+
 def test_small_served_workload_runs():
     """The served driver on a reduced trace: batched and one-at-a-time both
     finish every frame; batching takes fewer steps."""
@@ -107,8 +213,11 @@ def test_small_served_workload_runs():
     trace = serve.poisson_trace(len(sims), rate=400.0, duration=0.5, seed=2)
     a = serve.run(sims, dev, trace, max_batch=4, budget_bytes=8 << 30)
     b = serve.run(sims, dev, trace, max_batch=1, budget_bytes=8 << 30)
-    assert a["frames"] == b["frames"] == len(trace)
+    c = serve.run_plain(sims, dev, trace)
+    assert a["frames"] == b["frames"] == c["frames"] == len(trace)
     assert a["steps"] <= b["steps"]
+    for r in (a, b, c):
+        assert 0 < r["p50_ms"] <= r["p99_ms"]
 
 
 def test_served_options_equal_alone():
@@ -119,19 +228,13 @@ def test_served_options_equal_alone():
     sizes, frames, order = _setup(seed=7)
     opts = [dict(events=True), dict(events=True, match_rule=vd.VD_MATCH_CENTROID, match_radius=4),
             dict(connectivity=8), dict(edge_rule=vd.VD_EDGE_VERTEX), dict(walls=vd.VD_WALL_X, events=True)]
-    finals = {}
-    for s, (lx, ly) in enumerate(sizes):
-        det = vd.Detector(lx, ly, **opts[s])
-        for F in frames[s]:
-            det.push(F)
-        finals[s] = (det.labels(), det.changes())
-        det.close()
-    sv = vd.Server(sizes, budget_bytes=1 << 40, max_batch=4, options=opts)
+    want, finals = _alone_changes(sizes, frames, dict(enumerate(opts)))
+    sv = vd.Server(sizes, budget_bytes=1 << 40, max_batch=4, options=opts, keep_changes=True)
+    tickets, seen = {}, {}
     for s, f in order:
-        sv.submit(s, frames[s][f])
-    done = 0
-    while done < len(order):
-        done += len(sv.poll(wait=True))
+        tickets[sv.submit(s, frames[s][f])] = (s, f)
+    while len(seen) < len(order):
+        _drain(sv, tickets, seen, want)
     for s in range(len(sizes)):
         lab, ch = finals[s]
         assert np.array_equal(sv.labels(s), lab), s
@@ -146,9 +249,10 @@ def test_served_options_equal_alone():
 def test_served_workload_full_size():
     """The served workload's 64 simulations (512^2 ... 4096^2, smoothed noise
     and droplets) on a seeded Poisson trace of 500 arrivals, frames taken
-    from the shared pools in the served driver's order: every simulation's
-    per-frame counts and final labels and flip lists equal those run alone,
-    and for the first 8 simulations those of the oracle."""
+    from the shared pools in the served driver's order: every frame of every
+    simulation equals the same frame run alone, element by element (breaking
+    and arising lists, past keys, active flags), final labels too; and every
+    frame of the first 8 simulations equals the oracle's."""
     import multiprocessing as mp
     params = I.serve_sims()
     sims = [(L, rec) for L, rec, _ in params]
@@ -168,36 +272,31 @@ def test_served_workload_full_size():
         det = vd.Detector(L, L)
         for k, j in enumerate(seqs[s]):
             det.push(dev_pools[(L, rec)][j])
-            ch = det.changes()
-            alone[(s, k)] = (ch["K"], ch["n_edges"], len(ch["breaking"]), len(ch["arising"]))
+            alone[(s, k)] = det.changes()
         if seqs[s]:
-            finals[s] = (det.labels(), det.changes())
+            finals[s] = det.labels()
         det.close()
-    # served, in trace order
-    sv = vd.Server([(L, L) for L, _ in sims], budget_bytes=40_000_000_000, max_batch=len(sims))
+    # served, in trace order, every retired frame compared as it retires
+    sv = vd.Server([(L, L) for L, _ in sims], budget_bytes=40_000_000_000, max_batch=len(sims), keep_changes=True)
     tickets, seen, count = {}, {}, [0] * len(sims)
     for _, s in trace:
         L, rec = sims[s]
-        tickets[sv.submit(s, dev_pools[(L, rec)][seqs[s][count[s]]])] = (s, count[s])
+        tickets[sv.submit(s, dev_pools[(L, rec)][seqs[s][count[s]]], vd.clock_ns())] = (s, count[s])
         count[s] += 1
         for d in sv.poll(wait=False):
-            seen[tickets[d[0]]] = d
+            _check_done(sv, d, tickets, seen, alone)
     while len(seen) < len(trace):
-        for d in sv.poll(wait=True):
-            seen[tickets[d[0]]] = d
-    for key, d in seen.items():
-        ticket, s, status, ts, td, K, E, nb, na = d
-        assert status == 0, key
-        assert (K, E, nb, na) == alone[key], (key, (K, E, nb, na), alone[key])
-    for s, (lab, ch) in finals.items():
+        _drain(sv, tickets, seen, alone)
+    for s, lab in finals.items():
         assert np.array_equal(sv.labels(s), lab), s
-        got = sv.changes(s)
-        assert np.array_equal(got["breaking"], ch["breaking"]) and np.array_equal(got["arising"], ch["arising"]), s
     for s in range(8):
-        counts, lab_digest, breaking, arising = oracle[s]
-        assert [alone[(s, k)] for k in range(len(seqs[s]))] == counts, s
+        frames_o, lab_digest = oracle[s]
+        assert len(frames_o) == len(seqs[s])
+        for k, r in enumerate(frames_o):
+            a = alone[(s, k)]
+            assert (a["K"], a["n_edges"]) == (r["K"], r["E"]), (s, k)
+            for key in ("breaking", "breaking_prev", "arising", "active"):
+                assert np.array_equal(a[key], r[key]), (s, k, key)
         if seqs[s]:
-            assert array_digest(finals[s][0]) == lab_digest, s
-            assert np.array_equal(finals[s][1]["breaking"], breaking), s
-            assert np.array_equal(finals[s][1]["arising"], arising), s
+            assert array_digest(finals[s]) == lab_digest, s
     sv.close()
