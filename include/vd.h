@@ -171,6 +171,24 @@ vd_status vd_get_owners(vd_ctx* ctx, int32_t* out, int64_t cap, int64_t* n);    
 vd_status vd_get_edges(vd_ctx* ctx, uint64_t* out, int64_t cap, int64_t* n);        /* sorted unique keys */
 vd_status vd_get_match(vd_ctx* ctx, int32_t* phi, int64_t cap, int64_t* n);         /* K_prev entries, -1 = unmatched */
 
+/* Tuning of the launch shapes (not part of the result: every setting gives
+ * bit-identical output). voronoi_patch: the patch layout of the owner kernel,
+ * which splits each 64 x 32 tile into patches that keep their own candidate
+ * centres (VD_PATCH_8x8, the default, 16x8, 32x8 or 16x16 sites); bucket_pct:
+ * side of the centre bucket grid in percent of the mean centre spacing
+ * (25..400, default 100); ring0: sites beyond the tile reached by the first
+ * round of the owner search (0..256, default 9). Applies from the next push;
+ * synchronises the stream. The autotuner (paper_1607_00908_gb300/autotune.py)
+ * times candidates and keeps the fastest per lattice-size and density class. */
+enum { VD_PATCH_8x8 = 0, VD_PATCH_16x8 = 1, VD_PATCH_32x8 = 2, VD_PATCH_16x16 = 3 };
+typedef struct vd_tuning {
+    int32_t voronoi_patch;
+    int32_t bucket_pct;
+    int32_t ring0;
+} vd_tuning;
+vd_status vd_set_tuning(vd_ctx* ctx, const vd_tuning* t);
+vd_status vd_get_tuning(vd_ctx* ctx, vd_tuning* t);
+
 /* Checkpoint / resume. Section 3.2.3 compares every frame with the previous
  * one, so the state a context carries from frame to frame is that frame's
  * labels (foreground bits and per-run labels), Q10 centroids with their
@@ -329,6 +347,9 @@ vd_status vd_batch_get_owners(vd_batch* b, int32_t i, int32_t* out, int64_t cap,
 vd_status vd_batch_get_edges(vd_batch* b, int32_t i, uint64_t* out, int64_t cap, int64_t* n);
 vd_status vd_batch_get_centroids_q10(vd_batch* b, int32_t i, int32_t* out, int64_t cap, int64_t* n);
 vd_status vd_batch_get_counts(vd_batch* b, int32_t i, int32_t* K, int32_t* n_edges, int64_t* frame_index);
+/* Tuning of a batch (as vd_set_tuning; one setting for all instances). */
+vd_status vd_batch_set_tuning(vd_batch* b, const vd_tuning* t);
+vd_status vd_batch_get_tuning(vd_batch* b, vd_tuning* t);
 /* Checkpoint / resume of instance i of an independent batch (as
  * vd_export_state / vd_import_state). */
 vd_status vd_batch_export_state(vd_batch* b, int32_t i, void* buf, int64_t cap, int64_t* n_bytes);

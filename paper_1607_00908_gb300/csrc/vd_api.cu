@@ -85,6 +85,7 @@ struct vd_batch {
     bool any_centroid_match = false;   // some instance matches by centres
     bool any_vertex_rule = false;      // some instance reads links at Voronoi vertices
     bool any_masked = false;           // some instance has walls or obstacles
+    int vpatch = VPATCH_8x8;           // patch layout of the owner kernel (tuning)
     // field pointer tables (device) and their host mirrors
     const float** d_fields = nullptr;
     long long* d_pitches = nullptr;
@@ -142,6 +143,11 @@ struct vd_batch {
     long long* d_off = nullptr;           // per instance: breaking, arising, active offsets
     long long* h_off = nullptr;           // pinned
 };
+
+// default tuning: owner-kernel patches of 8 x 8 sites, buckets of the mean
+// centre spacing, a first owner-search round reaching 9 sites beyond the tile
+static const int DEFAULT_BUCKET_PCT = 100;
+static const int DEFAULT_RING0 = 9;
 
 static const int N_STAGES = 6;
 static const char* STAGE_NAMES[N_STAGES] = {
@@ -246,6 +252,7 @@ Launch make_launch(vd_batch* b, const StepTables& T) {
     L.vertex_rule = b->any_vertex_rule;
     L.masked = b->any_masked;
     L.grid_wide = 4 * b->grid_items;
+    L.vpatch = b->vpatch;
     L.total_tilesA = T.total_tilesA;
     L.total_tilesV = T.total_tilesV;
     L.total_groups = T.total_groups;
@@ -313,6 +320,8 @@ vd_status create_batch(const vd_config* cfgs, int n, vd_batch** out, bool sequen
         D.Ly = iLy;
         D.uLx = c.Lx;
         D.uLy = c.Ly;
+        D.bucket_pct = DEFAULT_BUCKET_PCT;
+        D.ring0 = DEFAULT_RING0;
         D.masked = c.walls ? 1 : 0;
         b->any_masked = b->any_masked || c.walls;
         D.thr = c.threshold;
@@ -1227,6 +1236,39 @@ vd_status vd_debug_hold_scan_flag(vd_ctx* ctx, int32_t kind, int64_t tile, int32
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->s);
     return cuda_status(e);
 }
+
+vd_status vd_batch_set_tuning(vd_batch* b, const vd_tuning* t) {
+    if (!b || !t) return VD_ERR_INVALID;
+    if (t->voronoi_patch < 0 || t->voronoi_patch >= VPATCH_COUNT || t->bucket_pct < 25 || t->bucket_pct > 400 ||
+        t->ring0 < 0 || t->ring0 > 256)
+        return VD_ERR_INVALID;
+    for (InstDesc& D : b->desc) {
+        D.bucket_pct = t->bucket_pct;
+        D.ring0 = t->ring0;
+    }
+    cudaError_t e = cudaMemcpyAsync(b->P.desc, b->desc.data(), sizeof(InstDesc) * b->n, cudaMemcpyHostToDevice, b->s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->s);
+    if (e != cudaSuccess) return VD_ERR_CUDA;
+    if (t->voronoi_patch != b->vpatch) {
+        b->vpatch = t->voronoi_patch;
+        if (b->graph) {   // the step launches another kernel: capture it again
+            cudaGraphExecDestroy(b->graph);
+            b->graph = nullptr;
+        }
+    }
+    return VD_OK;
+}
+
+vd_status vd_batch_get_tuning(vd_batch* b, vd_tuning* t) {
+    if (!b || !t) return VD_ERR_INVALID;
+    t->voronoi_patch = b->vpatch;
+    t->bucket_pct = b->desc[0].bucket_pct;
+    t->ring0 = b->desc[0].ring0;
+    return VD_OK;
+}
+
+vd_status vd_set_tuning(vd_ctx* ctx, const vd_tuning* t) { return ctx ? vd_batch_set_tuning(ctx->b, t) : VD_ERR_INVALID; }
+vd_status vd_get_tuning(vd_ctx* ctx, vd_tuning* t) { return ctx ? vd_batch_get_tuning(ctx->b, t) : VD_ERR_INVALID; }
 
 vd_status vd_batch_set_timing(vd_batch* b, int32_t enable) {
     if (!b) return VD_ERR_INVALID;

@@ -100,6 +100,10 @@ struct InstDesc {
     int edge_rule;           // VD_EDGE_ADJ4 / VD_EDGE_VERTEX
     int masked;              // walls or obstacles: owners outside the domain / on obstacles are marked
     int uLx, uLy;            // the domain as the caller sees it; a bounded axis runs as 2 x its length
+    // tuning (vd_batch_set_tuning): bucket side in percent of the mean centre
+    // spacing; radius in sites of the first ring round of the owner search
+    int bucket_pct;
+    int ring0;
     int pad3;
 };
 
@@ -454,7 +458,11 @@ struct Launch {
     int total_tilesA, total_tilesV;
     long long total_groups;
     int grid_wide;               // blocks for kernels with one thread per item (pieces, bubbles, links)
+    int vpatch;                  // patch layout of the owner kernel (VPATCH_*)
 };
+
+// patch layouts of the owner kernel (PW x PH sites per patch of a 64 x 32 tile)
+enum VPatch : int { VPATCH_8x8 = 0, VPATCH_16x8 = 1, VPATCH_32x8 = 2, VPATCH_16x16 = 3, VPATCH_COUNT = 4 };
 
 // Kernels of a step are launched with programmatic dependent launch, so the
 // launch of a kernel overlaps the end of the previous one; every step kernel

@@ -45,8 +45,9 @@ __global__ __launch_bounds__(PLAN_THREADS) void k_plan(Pools P, StepTable T, int
                     S.K = K;
                 }
                 if (K > 0) {
-                    // bucket side ~ mean spacing of centres, clamped to [4, 64] sites
-                    const double sp = sqrt((double)D.Lx * (double)D.Ly / (double)K);
+                    // bucket side ~ a tuned fraction of the mean spacing of centres,
+                    // clamped to [4, 64] sites
+                    const double sp = sqrt((double)D.Lx * (double)D.Ly / (double)K) * (0.01 * D.bucket_pct);
                     int B = (int)(sp + 0.5);
                     B = B < 4 ? 4 : (B > 64 ? 64 : B);
                     S.B = B;

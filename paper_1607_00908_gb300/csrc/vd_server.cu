@@ -266,7 +266,7 @@ vd_status keep_retired(vd_server* sv, const std::vector<long long>& tickets) {
             R.ob = nb;
             R.oa = na;
             R.ok = nk;
-            if (R.status == VD_OK && R.frame > 1) {
+            if (R.status == VD_OK && R.frame > 0) {
                 nb += R.nb;
                 na += R.na;
                 nk += R.K;
@@ -297,7 +297,7 @@ vd_status keep_retired(vd_server* sv, const std::vector<long long>& tickets) {
         // entry k spans [off[3k], off[3k + 3]) in each list; entry n holds the ends
         for (int k = 0; k < n; ++k) {
             const Retired& R = sv->retired[ts[k]];
-            const bool ok = R.status == VD_OK && R.frame > 1;
+            const bool ok = R.status == VD_OK && R.frame > 0;
             sv->h_ins[k] = sv->sims[R.sim].inst;
             sv->h_off[3 * k] = R.ob;
             sv->h_off[3 * k + 1] = R.oa;
@@ -493,10 +493,7 @@ vd_status vd_server_get_frame_changes(vd_server* sv, int64_t ticket, vd_changes*
     out->n_arising = R.na;
     out->global_trigger = (R.nb + R.na) > 0;
     if (R.status) return R.status;
-    if (R.frame <= 1) {   // a simulation's first frame has no changes
-        out->n_breaking = out->n_arising = 0;
-        return VD_OK;
-    }
+    if (R.frame <= 0) return VD_ERR_STATE;
     if ((R.nb > 0 && (!out->breaking || out->cap_breaking < R.nb)) ||
         (R.na > 0 && (!out->arising || out->cap_arising < R.na)) || (out->active && out->cap_active < R.K))
         return VD_ERR_CAPACITY;

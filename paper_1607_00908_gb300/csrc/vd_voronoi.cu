@@ -90,10 +90,22 @@ __device__ __forceinline__ void edge_global_insert(const Pools& P, const InstDes
 
 
 constexpr int VWARPS = 2;        // tiles per block, one warp each
-constexpr int PW = 16, PH = 8;   // patch
-constexpr int NPX = TW / PW, NPY = TH / PH, NPATCH = NPX * NPY;   // a 64 x 32 tile holds 4 x 4 patches
 constexpr int WSCAN = 384;       // per-warp list of scanned centres
-constexpr int WCAND = 64;        // per-patch list of kept candidates (index fits 6 bits)
+constexpr int KMAX = 16;         // kept centres listed per patch (more: exact over every scanned centre)
+
+// Patch layouts of the owner kernel: a 64 x 32 tile is cut into NP patches of
+// PW x PH sites. Lane p computes the bound and the kept list of patch p
+// (NP <= 32); in the site phase every lane takes SPL sites of one column of a
+// patch (column lane % PW, rows from (lane / PW) * SPL).
+template <int PW_, int PH_>
+struct VLayout {
+    static constexpr int PW = PW_, PH = PH_;
+    static constexpr int NPX = TW / PW, NPY = TH / PH, NP = NPX * NPY;
+    static constexpr int SPL = PW * PH / 32;
+    static_assert(TW % PW == 0 && TH % PH == 0 && NP <= 32 && 32 % PW == 0 && SPL >= 1 &&
+                      (32 / PW) * SPL == PH,
+                  "patch layout");
+};
 
 // Exact owner over a candidate list with int64 distances (coordinates
 // relative to the tile origin, no wrap needed), ties to the smallest label.
@@ -120,27 +132,37 @@ __device__ __forceinline__ float far2_ru(int d, int lo, int hi, int halfM) {
 }
 
 // One warp per 64 x 32 tile (the labelling tiles), no block-level
-// synchronisation; two tiles per block and 64 registers, so that small frames
-// still spread over the SMs.
-//  1. Ring search over the bucket grid around the tile. For each of the
-//     tile's sixteen 16 x 8 patches, U_p = min over scanned centres of an upper
-//     bound of their largest squared distance to the patch (float32 rounded
-//     up), so every site of patch p has a centre within sqrt(U_p). The search
-//     stops when the unscanned region is farther than sqrt(max_p U_p) from
-//     the tile; the first round already takes the rings that usually satisfy
-//     this (about the patch half-diagonal plus one bucket).
-//  2. Per patch: the owners of its sites are among the scanned centres whose
-//     smallest squared distance to the patch (rounded down) is <= U_p; every
-//     site scans only those kept centres. float32 distances with the kept
-//     index in the low 6 bits give the nearest and second-nearest; when they
-//     are within 2^-15 relative of each other the site is decided exactly in
-//     int64 (ties to the smallest label).
+// synchronisation; two tiles per block.
+//  1. Ring search over the bucket grid around the tile: the centres of the
+//     rings of buckets are collected in shared memory (one bucket per lane,
+//     placed by a prefix sum), starting with the rings within `ring0` sites
+//     plus one bucket. Lane p then updates, over the new centres, U_p = the
+//     smallest upper bound (float32 rounded up) of a centre's largest squared
+//     distance to patch p, so every site of patch p has a centre within
+//     sqrt(U_p). The search stops when the unscanned region is farther than
+//     sqrt(max_p U_p) from the tile.
+//  2. Lane p lists the scanned centres whose smallest squared distance to
+//     patch p (rounded down) is <= U_p: the owner of every site of the patch
+//     is among them (it is within sqrt(U_p) of the site, hence of the patch,
+//     and every such centre was scanned).
+//  3. Patch by patch, every lane takes SPL sites: one kept centre owns the
+//     whole patch; two are decided by their exact int64 bisector stepped down
+//     the column; more are screened in float32 (squared distance with the
+//     kept index in the low 6 bits: the two smallest give the nearest and the
+//     runner-up) and decided exactly in int64 over the kept list when the two
+//     are within 2^-15 relative (truncation 2^-17 + rounding 2^-23 cannot
+//     reorder them otherwise), ties to the smallest label.
+//  A tile whose scanned centres are not minimum images for every site or not
+//  exact in float32, or whose scan exceeds WSCAN centres, takes the general
+//  path (exact int64 per site over the scanned list or buckets).
+template <int PW, int PH>
 __global__ __launch_bounds__(32 * VWARPS, 16) void k_voronoi(Pools P, StepTable T) {
+    using LY = VLayout<PW, PH>;
+    constexpr int NPX = LY::NPX, NP = LY::NP, SPL = LY::SPL;
     pdl_enter();
     __shared__ int s_cx[VWARPS][WSCAN], s_cy[VWARPS][WSCAN], s_id[VWARPS][WSCAN];
-    __shared__ float2 s_fc[VWARPS][WCAND];
-    __shared__ int s_kk[VWARPS][WCAND];
-    __shared__ float s_U[VWARPS][NPATCH];
+    __shared__ int s_kept[VWARPS][NP][KMAX];
+    __shared__ int s_nk[VWARPS][NP];
     __shared__ int s_tpre[SEG_CACHE];
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -171,8 +193,6 @@ __global__ __launch_bounds__(32 * VWARPS, 16) void k_voronoi(Pools P, StepTable 
     const long long MX = (long long)Q * Lx, MY = (long long)Q * Ly;
     const long long X0 = (long long)Q * x0, Y0 = (long long)Q * y0;
     const int hMX = (int)(MX >> 1), hMY = (int)(MY >> 1);
-    // patch p = NPX * pyi + pxi covers columns [PW * pxi, PW * (pxi + 1)) and
-    // rows [PH * pyi, PH * (pyi + 1)) of the tile, clipped to it
     const int Bk = S.B, nbx = S.nbx, nby = S.nby;
     const int bx0 = x0 / Bk, bx1 = (x0 + ncols - 1) / Bk;
     const int by0 = y0 / Bk, by1 = (y0 + nrows - 1) / Bk;
@@ -182,14 +202,18 @@ __global__ __launch_bounds__(32 * VWARPS, 16) void k_voronoi(Pools P, StepTable 
     int* cxs = s_cx[warp];
     int* cys = s_cy[warp];
     int* ids = s_id[warp];
-    float Up[NPATCH];
-#pragma unroll
-    for (int p = 0; p < NPATCH; ++p) Up[p] = INFINITY;
+    // this lane's patch (lanes past the last patch repeat it and are not counted)
+    const int pp = lane < NP ? lane : NP - 1;
+    const int ppx = PW * (pp % NPX), ppy = PH * (pp / NPX);
+    const bool pvalid = lane < NP && ppx < ncols && ppy < nrows;
+    const int pxlo = Q * ppx, pxhi = Q * (min(ppx + PW, ncols) - 1);
+    const int pylo = Q * ppy, pyhi = Q * (min(ppy + PH, nrows) - 1);
+    float Up = INFINITY;
     int qx0 = 0, qx1 = -1, qy0 = 0, qy1 = -1;   // previous round's region
     bool qfx = false, qfy = false, have_prev = false;
     int rx0, rx1, ry0, ry1;
-    int n = 0;   // centres scanned so far (warp-uniform)
-    for (int r = (9 + Bk - 1) / Bk + 1;; ++r) {
+    int n = 0, nb = 0;   // centres scanned so far, and those whose bounds are taken (warp-uniform)
+    for (int r = (D.ring0 + Bk - 1) / Bk + 1;; ++r) {
         rx0 = bx0 - r; rx1 = bx1 + r; ry0 = by0 - r; ry1 = by1 + r;
         const bool fx = (rx1 - rx0 + 1) >= nbx, fy = (ry1 - ry0 + 1) >= nby;
         if (fx) { rx0 = 0; rx1 = nbx - 1; }
@@ -225,37 +249,22 @@ __global__ __launch_bounds__(32 * VWARPS, 16) void k_voronoi(Pools P, StepTable 
             }
             int pos = n + inc - cnt;
             n += __shfl_sync(0xffffffffu, inc, 31);
-            for (int j = jb; j < je; ++j, ++pos) {
+            for (int j = jb; j < je && pos < WSCAN; ++j, ++pos) {
                 const int2 cc = bcq[j];
-                const int ddx = (int)wrapM((long long)cc.x - X0, MX);
-                const int ddy = (int)wrapM((long long)cc.y - Y0, MY);
-                float fxs[NPX];
-#pragma unroll
-                for (int pxi = 0; pxi < NPX; ++pxi)
-                    fxs[pxi] = far2_ru(ddx, Q * PW * pxi, Q * (min(PW * (pxi + 1), ncols) - 1), hMX);
-#pragma unroll
-                for (int pyi = 0; pyi < NPY; ++pyi) {
-                    const int ylo = Q * PH * pyi, yhi = Q * (min(PH * (pyi + 1), nrows) - 1);
-                    const float fy = far2_ru(ddy, ylo, yhi, hMY);
-#pragma unroll
-                    for (int pxi = 0; pxi < NPX; ++pxi)
-                        Up[NPX * pyi + pxi] = fminf(Up[NPX * pyi + pxi], __fadd_ru(fxs[pxi], fy));
-                }
-                if (pos < WSCAN) {
-                    cxs[pos] = ddx;
-                    cys[pos] = ddy;
-                    ids[pos] = bid[j];
-                }
+                cxs[pos] = (int)wrapM((long long)cc.x - X0, MX);
+                cys[pos] = (int)wrapM((long long)cc.y - Y0, MY);
+                ids[pos] = bid[j];
             }
         }
-        float Umax = 0.f;
+        __syncwarp();
+        // this lane's patch bound over the centres of this round
+        const int ne = min(n, WSCAN);
+        for (int j = nb; j < ne; ++j)
+            Up = fminf(Up, __fadd_ru(far2_ru(cxs[j], pxlo, pxhi, hMX), far2_ru(cys[j], pylo, pyhi, hMY)));
+        nb = ne;
+        float Umax = pvalid ? Up : 0.f;
 #pragma unroll
-        for (int p = 0; p < NPATCH; ++p) {
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) Up[p] = fminf(Up[p], __shfl_xor_sync(0xffffffffu, Up[p], o));
-            const bool valid = PW * (p % NPX) < ncols && PH * (p / NPX) < nrows;
-            if (valid) Umax = fmaxf(Umax, Up[p]);
-        }
+        for (int o = 16; o > 0; o >>= 1) Umax = fmaxf(Umax, __shfl_xor_sync(0xffffffffu, Umax, o));
         if (fx && fy) break;
         // gap between the region and the unscanned buckets (periods handled by
         // one conditional shift: the ranges are narrower than a period here)
@@ -275,11 +284,6 @@ __global__ __launch_bounds__(32 * VWARPS, 16) void k_voronoi(Pools P, StepTable 
         if (g > 0 && (double)g * (double)g > (double)Umax * (1.0 + 1.0 / (1ll << 50))) break;
         qx0 = rx0; qx1 = rx1; qy0 = ry0; qy1 = ry1; qfx = fx; qfy = fy; have_prev = true;
     }
-    if (lane == 0) {
-#pragma unroll
-        for (int p = 0; p < NPATCH; ++p) s_U[warp][p] = Up[p];
-    }
-    __syncwarp();
 
     // The fast path needs every scanned centre's tile-relative position to be
     // its minimum image for every site of the tile (otherwise the distances
@@ -298,50 +302,39 @@ __global__ __launch_bounds__(32 * VWARPS, 16) void k_voronoi(Pools P, StepTable 
     }
 
     if (!bad) {
-        float2* fc = s_fc[warp];
-        int* kk = s_kk[warp];
-        const int c = lane & 15, rb = 4 * (lane >> 4);   // this lane: column c, rows rb..rb+3 of the patch
+        // ---- 2. kept list of this lane's patch ----
+        if (lane < NP) {
+            int* kl = s_kept[warp][lane];
+            int nk = 0;
+            for (int j = 0; j < n; ++j) {
+                const int cx = cxs[j], cy = cys[j];
+                const int ex = max(0, max(pxlo - cx, cx - pxhi)), ey = max(0, max(pylo - cy, cy - pyhi));
+                const float exf = __int2float_rd(ex), eyf = __int2float_rd(ey);
+                if (__fmaf_rd(exf, exf, __fmul_rd(eyf, eyf)) <= Up) {
+                    if (nk < KMAX) kl[nk] = j;
+                    ++nk;
+                }
+            }
+            s_nk[warp][lane] = nk;
+        }
+        __syncwarp();
+        // ---- 3. nearest kept centre for every site, patch by patch ----
+        const int c = lane % PW, rb = (lane / PW) * SPL;
 #pragma unroll 1
-        for (int p = 0; p < NPATCH; ++p) {
+        for (int p = 0; p < NP; ++p) {
             const int pxo = PW * (p % NPX), pyo = PH * (p / NPX);
             if (pxo >= ncols || pyo >= nrows) continue;   // warp-uniform
             const int pw = min(PW, ncols - pxo), ph = min(PH, nrows - pyo);
-            const int xlo = Q * pxo, xhi = Q * (pxo + pw - 1);
-            const int ylo = Q * pyo, yhi = Q * (pyo + ph - 1);
-            const float Uq = s_U[warp][p];
-            // ---- 2a. keep the scanned centres within sqrt(U_p) of the patch ----
-            int nk = 0;
-            __syncwarp();
-            for (int base = 0; base < n; base += 32) {
-                const int k = base + lane;
-                bool keep = false;
-                int cx = 0, cy = 0;
-                if (k < n) {
-                    cx = cxs[k];
-                    cy = cys[k];
-                    const int ex = max(0, max(xlo - cx, cx - xhi)), ey = max(0, max(ylo - cy, cy - yhi));
-                    const float exf = __int2float_rd(ex), eyf = __int2float_rd(ey);
-                    keep = __fmaf_rd(exf, exf, __fmul_rd(eyf, eyf)) <= Uq;
-                }
-                const unsigned m = __ballot_sync(0xffffffffu, keep);
-                if (keep) {
-                    const int q = nk + __popc(m & ((1u << lane) - 1u));
-                    if (q < WCAND) {
-                        fc[q] = make_float2((float)cx, (float)cy);
-                        kk[q] = k;
-                    }
-                }
-                nk += __popc(m);
-            }
-            __syncwarp();
-            // ---- 2b. nearest kept centre for every site of the patch ----
+            const int nk = s_nk[warp][p];
+            const int* kk = s_kept[warp][p];
             if (c < pw && rb < ph) {
                 const int sx = pxo + c;
-                const float sxf = (float)(Q * sx);
-                int o[4];
+                int o[SPL];
                 if (nk == 1) {
                     // one candidate owns the whole patch
-                    o[0] = o[1] = o[2] = o[3] = ids[kk[0]];
+                    const int o1 = ids[kk[0]];
+#pragma unroll
+                    for (int k = 0; k < SPL; ++k) o[k] = o1;
                 } else if (nk == 2) {
                     // the bisector decides: d(s,c1)^2 - d(s,c2)^2 = 2 s.(c2 - c1) + |c1|^2 - |c2|^2,
                     // exact in int64 (tile-relative minimum images), ties to the smaller label
@@ -354,26 +347,28 @@ __global__ __launch_bounds__(32 * VWARPS, 16) void k_voronoi(Pools P, StepTable 
                                    (c1x * c1x + c1y * c1y) - (c2x * c2x + c2y * c2y);
                     const long long step = ay * Q;
 #pragma unroll
-                    for (int k = 0; k < 4; ++k) {
+                    for (int k = 0; k < SPL; ++k) {
                         o[k] = dv < 0 ? i1 : (dv > 0 ? i2 : itie);
                         dv += step;
                     }
-                } else if (nk <= WCAND) {
-                    float syf[4];
-                    unsigned f1[4], f2[4];
+                } else if (nk <= KMAX) {
+                    const float sxf = (float)(Q * sx);
+                    float syf[SPL];
+                    unsigned f1[SPL], f2[SPL];
 #pragma unroll
-                    for (int k = 0; k < 4; ++k) {
+                    for (int k = 0; k < SPL; ++k) {
                         f1[k] = 0x7f800000u;
                         f2[k] = 0x7f800000u;
                         syf[k] = (float)(Q * (pyo + rb + k));
                     }
                     for (int j = 0; j < nk; ++j) {
-                        const float2 cf = fc[j];
-                        const float dx = sxf - cf.x;
+                        const int e = kk[j];
+                        const float dx = sxf - (float)cxs[e];
+                        const float cyf = (float)cys[e];
                         const float dx2 = dx * dx;
 #pragma unroll
-                        for (int k = 0; k < 4; ++k) {
-                            const float dy = syf[k] - cf.y;
+                        for (int k = 0; k < SPL; ++k) {
+                            const float dy = syf[k] - cyf;
                             const unsigned pk = (__float_as_uint(fmaf(dy, dy, dx2)) & ~63u) | (unsigned)j;
                             const unsigned hi = max(f1[k], pk);
                             f1[k] = min(f1[k], pk);
@@ -381,7 +376,7 @@ __global__ __launch_bounds__(32 * VWARPS, 16) void k_voronoi(Pools P, StepTable 
                         }
                     }
 #pragma unroll
-                    for (int k = 0; k < 4; ++k) {
+                    for (int k = 0; k < SPL; ++k) {
                         const float a1 = __uint_as_float(f1[k] & ~63u), a2 = __uint_as_float(f2[k] & ~63u);
                         // distances carry 2^-23 rounding and 2^-17 truncation: a gap
                         // above 2^-15 relative means the order is the exact order
@@ -393,11 +388,11 @@ __global__ __launch_bounds__(32 * VWARPS, 16) void k_voronoi(Pools P, StepTable 
                 } else {
                     // more kept centres than the list holds: exact over all scanned
 #pragma unroll
-                    for (int k = 0; k < 4; ++k)
+                    for (int k = 0; k < SPL; ++k)
                         o[k] = owner_exact((long long)Q * sx, (long long)Q * (pyo + rb + k), cxs, cys, ids, nullptr, n);
                 }
 #pragma unroll
-                for (int k = 0; k < 4; ++k)
+                for (int k = 0; k < SPL; ++k)
                     if (rb + k < ph) own[(long long)(y0 + pyo + rb + k) * Lx + x0 + sx] = o[k];
             }
         }
@@ -507,10 +502,21 @@ __device__ __forceinline__ void cp_async16(int* smem, const int* gmem) {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
 }
 
+// Two phases per tile. 1: lane l walks its column down the rows with the
+// owners of the site, its right neighbour and the two below in registers and
+// marks the rows where the site differs from its right or lower neighbour
+// (about one site in five on Voronoi cells tens of sites wide); 2: the marked
+// (row, column) items are compacted into a shared queue and processed with
+// every lane on a different item, so the emission rules run with all lanes
+// busy instead of with the one or two lanes of a row that cross a boundary.
+constexpr int LQ = VW * VH;     // queue of marked sites (row * 32 + column)
+
 __global__ __launch_bounds__(32 * LINK_WARPS) void k_links(Pools P, StepTable T) {
     pdl_enter();
     __shared__ __align__(16) int s_own[LINK_WARPS][(VH + 1) * LS];
     __shared__ unsigned long long s_list[LINK_WARPS][LSET];
+    __shared__ unsigned short s_q[LINK_WARPS][LQ];
+    __shared__ int s_n[LINK_WARPS];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int b = blockIdx.x * LINK_WARPS + warp;
     if (b >= T.tileV_pre[T.n_act]) return;
@@ -528,6 +534,7 @@ __global__ __launch_bounds__(32 * LINK_WARPS) void k_links(Pools P, StepTable T)
     const int* own = P.owners + D.site_off;
     int* S = s_own[warp];
     unsigned long long* list = s_list[warp];
+    unsigned short* q = s_q[warp];
 
     // stage rows y0..y0+nrows and columns x0..x0+ncols (both periodic); a
     // full-width tile whose rows start on 16-byte boundaries copies 16 bytes
@@ -554,52 +561,92 @@ __global__ __launch_bounds__(32 * LINK_WARPS) void k_links(Pools P, StepTable T)
             }
         }
     }
+    if (lane == 0) s_n[warp] = 0;
     asm volatile("cp.async.wait_all;\n" ::: "memory");
     __syncwarp();
 
-    const bool valid = lane < ncols;
-    const int l = min(lane, ncols - 1);
-    const unsigned lt = (1u << lane) - 1u;
-    int o = S[l], rt = S[l + 1];
-    int up = 0, upr = 0;
-    int lf = __shfl_up_sync(0xffffffffu, o, 1);
-    int n = 0;   // keys in the warp's list (warp-uniform)
-    for (int r = 0; r < nrows; ++r) {
-        const int dn = S[(r + 1) * LS + l];
-        const int dg = S[(r + 1) * LS + l + 1];
-        const int dlf = __shfl_up_sync(0xffffffffu, dn, 1);
-        // a pair with a negative owner (obstacle, beyond a wall) is dropped when
-        // its key is listed, a plaquette with one before its centres are read
-        const bool eh = valid && o != rt && !(r > 0 && (up == rt || upr == o || (up == o && upr == rt)));
-        const bool ev = valid && o != dn && rt != dn && !(lane > 0 && (lf == dn || (lf == o && dlf == dn)));
-        const bool ep = valid && o != rt && o != dn && o != dg && rt != dn && rt != dg && dn != dg;
-        const unsigned mh = __ballot_sync(0xffffffffu, eh);
-        const unsigned mv = __ballot_sync(0xffffffffu, ev);
-        const unsigned mp = __ballot_sync(0xffffffffu, ep);
-        if (mh | mv | mp) {
-            // append this row's keys: horizontal, vertical, then plaquettes
-            const int nh = __popc(mh), nv = __popc(mv);
-            if (eh) link_list_put(list, n + __popc(mh & lt), o, rt, P, D, inst);
-            if (ev) link_list_put(list, n + nh + __popc(mv & lt), o, dn, P, D, inst);
-            if (ep) {
-                int pa = -1, pb = -1;
-                if ((o | rt | dn | dg) >= 0) {
-                    const unsigned long long pk = plaquette_key(o, rt, dg, dn, cq, MX, MY);
-                    pa = (int)(pk >> 32);
-                    pb = (int)(pk & 0xffffffffu);
-                }
-                link_list_put(list, n + nh + nv + __popc(mp & lt), pa, pb, P, D, inst);
-            }
-            n += nh + nv + __popc(mp);
+    // ---- 1. mark the rows where this column's site differs from its right
+    // or lower neighbour (only those can anchor an emitted link) ----
+    unsigned mark = 0;
+    if (lane < ncols) {
+        int o = S[lane], rt = S[lane + 1];
+        for (int r = 0; r < nrows; ++r) {
+            const int dn = S[(r + 1) * LS + lane];
+            const int dg = S[(r + 1) * LS + lane + 1];
+            mark |= (unsigned)((o != rt) | (o != dn)) << r;
+            o = dn;
+            rt = dg;
         }
-        up = o;
-        upr = rt;
-        o = dn;
-        rt = dg;
-        lf = dlf;
+    }
+    // compact the marked sites into the queue (row-major order is not needed)
+    const int cnt = __popc(mark);
+    int inc = cnt;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const int v = __shfl_up_sync(0xffffffffu, inc, d);
+        if (lane >= d) inc += v;
+    }
+    const int nq = __shfl_sync(0xffffffffu, inc, 31);
+    {
+        int pos = inc - cnt;
+        unsigned m = mark;
+        while (m) {
+            const int r = __ffs(m) - 1;
+            m &= m - 1;
+            q[pos++] = (unsigned short)(r * 32 + lane);
+        }
     }
     __syncwarp();
-    flush_link_list(list, n, lane, P, D, inst);
+
+    // ---- 2. the emission rules at every marked site, one site per lane.
+    // The tile answers for the adjacencies anchored in it, H(l,r) between
+    // sites (l,r),(l+1,r) and V(l,r) between (l,r),(l,r+1). Ordering anchors
+    // by (row, column) with H before V at the same anchor, an adjacency is
+    // emitted only if none of the earlier adjacencies that share a dual
+    // corner with it joins the same two owners:
+    //   H(l,r): H(l,r-1), V(l,r-1), V(l+1,r-1)   (r > 0)
+    //   V(l,r): H(l-1,r), V(l-1,r) (l > 0), H(l,r)
+    // Every suppressed adjacency points to a strictly earlier one with the
+    // same owner pair, which is emitted or suppressed in turn, so by induction
+    // over the order every pair that meets somewhere is emitted at least once
+    // (the tiles of the referenced anchors process them). A straight boundary
+    // crossing the tile is emitted once instead of once per row. Four-owner
+    // plaquettes add their incircle link. A pair with a negative owner
+    // (obstacle, beyond a wall) is dropped when its key is listed, a plaquette
+    // with one before its centres are read.
+    for (int i = lane; i < nq; i += 32) {
+        const int it = q[i];
+        const int r = it >> 5, l = it & 31;
+        const int* row = S + r * LS + l;
+        const int o = row[0], rt = row[1], dn = row[LS], dg = row[LS + 1];
+        if (o != rt) {
+            bool sup = false;
+            if (r > 0) {
+                const int up = row[-LS], upr = row[-LS + 1];
+                sup = up == rt || upr == o || (up == o && upr == rt);
+            }
+            if (!sup) link_list_put(list, atomicAdd(&s_n[warp], 1), o, rt, P, D, inst);
+        }
+        if (o != dn && rt != dn) {
+            bool sup = false;
+            if (l > 0) {
+                const int lf = row[-1], dlf = row[LS - 1];
+                sup = lf == dn || (lf == o && dlf == dn);
+            }
+            if (!sup) link_list_put(list, atomicAdd(&s_n[warp], 1), o, dn, P, D, inst);
+        }
+        if (o != rt && o != dn && o != dg && rt != dn && rt != dg && dn != dg) {
+            int pa = -1, pb = -1;
+            if ((o | rt | dn | dg) >= 0) {
+                const unsigned long long pk = plaquette_key(o, rt, dg, dn, cq, MX, MY);
+                pa = (int)(pk >> 32);
+                pb = (int)(pk & 0xffffffffu);
+            }
+            link_list_put(list, atomicAdd(&s_n[warp], 1), pa, pb, P, D, inst);
+        }
+    }
+    __syncwarp();
+    flush_link_list(list, s_n[warp], lane, P, D, inst);
 }
 
 // appended links -> link hash (+ degrees); appended pairs -> overlap hash
@@ -636,7 +683,13 @@ void launch_merge_lists(const Launch& L) {
 }
 
 void launch_voronoi(const Launch& L) {
-    launch_step(L, k_voronoi, dim3((L.total_tilesA + VWARPS - 1) / VWARPS), dim3(32 * VWARPS), L.P, L.T);
+    const dim3 grid((L.total_tilesA + VWARPS - 1) / VWARPS), block(32 * VWARPS);
+    switch (L.vpatch) {
+        case VPATCH_16x8: launch_step(L, k_voronoi<16, 8>, grid, block, L.P, L.T); break;
+        case VPATCH_32x8: launch_step(L, k_voronoi<32, 8>, grid, block, L.P, L.T); break;
+        case VPATCH_16x16: launch_step(L, k_voronoi<16, 16>, grid, block, L.P, L.T); break;
+        default: launch_step(L, k_voronoi<8, 8>, grid, block, L.P, L.T); break;
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -662,45 +715,67 @@ void launch_voronoi(const Launch& L) {
 // Voronoi colour of the point (qx, qy) (1/1024 site, in [0, MX) x [0, MY)):
 // the nearest centre over all centres, exact int64 minimum-image distances,
 // ties to the smallest label. (best, bd) is a centre already known and its
-// squared distance. Rings of buckets around the point's bucket are scanned
-// outwards; before ring r every unscanned bucket is r or more buckets away
-// along some axis, with r - 1 buckets in between of which at most one is the
-// narrower last bucket, so it is at least (r - 2) B sites from the point, and
-// the search stops once bd is below that squared. Centres and the point both
-// lie in [0, M), so one conditional step gives the minimum image.
+// squared distance, so every centre that can win or tie lies within
+// rho = ceil(sqrt(bd)) of the point on each axis; the buckets overlapping that
+// square (at most two runs of bucket columns and rows, split where the square
+// wraps around the lattice) hold all of them. Centres and the point both lie
+// in [0, M), so one conditional step gives the minimum image.
+__device__ __forceinline__ long long isqrt_ceil(long long v) {
+    long long r = (long long)ceil(sqrt((double)v));
+    while (r > 0 && (r - 1) * (r - 1) >= v) --r;
+    while (r * r < v) ++r;
+    return r;
+}
+
+// site interval [lo, hi] (unwrapped, hi - lo < L) as at most two runs of
+// bucket indices on a ring of L sites cut into buckets of B (the last one
+// possibly narrower)
+__device__ __forceinline__ int bucket_runs(long long lo, long long hi, int L, int B, int nb, int* b0, int* b1) {
+    if (hi - lo + 1 >= L) {
+        b0[0] = 0;
+        b1[0] = nb - 1;
+        return 1;
+    }
+    long long a = lo % L;
+    if (a < 0) a += L;
+    const long long e = a + (hi - lo);
+    if (e < L) {
+        b0[0] = (int)(a / B);
+        b1[0] = (int)(e / B);
+        return 1;
+    }
+    b0[0] = (int)(a / B);
+    b1[0] = nb - 1;
+    b0[1] = 0;
+    b1[1] = (int)((e - L) / B);
+    return 2;
+}
+
 __device__ int point_owner(const int* boff, const int2* bcq, const int* bid, int B, int nbx, int nby, long long qx,
-                           long long qy, long long MX, long long MY, int best, long long bd) {
-    const long long HX = MX >> 1, HY = MY >> 1;
-    const int bx = (int)(qx / Q) / B, by = (int)(qy / Q) / B;
-    const int rmax = (max(nbx, nby) >> 1) + 1;
-    for (int r = 0; r <= rmax; ++r) {
-        if (r >= 2) {
-            const long long lim = (long long)(r - 2) * B * Q;
-            if (bd < lim * lim) break;
-        }
-        for (int dy = -r; dy <= r; ++dy) {
-            const bool edge_row = dy == -r || dy == r;
-            int rv = (by + dy) % nby;
-            rv += rv < 0 ? nby : 0;
-            for (int dx = -r; dx <= r; dx += (edge_row || r == 0) ? 1 : 2 * r) {
-                int cu = (bx + dx) % nbx;
-                cu += cu < 0 ? nbx : 0;
-                const int bk = rv * nbx + cu;
-                for (int j = boff[bk]; j < boff[bk + 1]; ++j) {
-                    const int2 c = bcq[j];
-                    long long ddx = (long long)c.x - qx + HX, ddy = (long long)c.y - qy + HY;
-                    ddx = (ddx < 0 ? ddx + MX : (ddx >= MX ? ddx - MX : ddx)) - HX;
-                    ddy = (ddy < 0 ? ddy + MY : (ddy >= MY ? ddy - MY : ddy)) - HY;
-                    const long long d = ddx * ddx + ddy * ddy;
-                    const int id = bid[j];
-                    if (d < bd || (d == bd && id < best)) {
-                        bd = d;
-                        best = id;
+                           long long qy, int Lx, int Ly, int best, long long bd) {
+    const long long MX = (long long)Q * Lx, MY = (long long)Q * Ly, HX = MX >> 1, HY = MY >> 1;
+    const long long rho = isqrt_ceil(bd);
+    int cx0[2], cx1[2], cy0[2], cy1[2];
+    const int nxr = bucket_runs((qx - rho) >> 10, (qx + rho) >> 10, Lx, B, nbx, cx0, cx1);
+    const int nyr = bucket_runs((qy - rho) >> 10, (qy + rho) >> 10, Ly, B, nby, cy0, cy1);
+    for (int ry = 0; ry < nyr; ++ry)
+        for (int rv = cy0[ry]; rv <= cy1[ry]; ++rv)
+            for (int rx = 0; rx < nxr; ++rx)
+                for (int cu = cx0[rx]; cu <= cx1[rx]; ++cu) {
+                    const int bk = rv * nbx + cu;
+                    for (int j = boff[bk]; j < boff[bk + 1]; ++j) {
+                        const int2 c = bcq[j];
+                        long long ddx = (long long)c.x - qx + HX, ddy = (long long)c.y - qy + HY;
+                        ddx = (ddx < 0 ? ddx + MX : (ddx >= MX ? ddx - MX : ddx)) - HX;
+                        ddy = (ddy < 0 ? ddy + MY : (ddy >= MY ? ddy - MY : ddy)) - HY;
+                        const long long d = ddx * ddx + ddy * ddy;
+                        const int id = bid[j];
+                        if (d < bd || (d == bd && id < best)) {
+                            bd = d;
+                            best = id;
+                        }
                     }
                 }
-            }
-        }
-    }
     return best;
 }
 
@@ -713,11 +788,16 @@ __device__ __forceinline__ long long wrap_once(long long v, long long L) {
 }
 
 constexpr int VS = VW + 8;      // staged row stride of the vertex rule: column c at 4 + c
+constexpr int VQ = 256;         // queued plaquette-centre searches per warp
 
 __global__ __launch_bounds__(32 * LINK_WARPS) void k_links_vertex(Pools P, StepTable T) {
     pdl_enter();
     __shared__ __align__(16) int s_own[LINK_WARPS][(VH + 2) * VS];
     __shared__ unsigned long long s_list[LINK_WARPS][LSET];
+    // plaquette centres whose colour needs the search: (k, diagonal colour,
+    // best corner colour, site, quarter turn), resolved with every lane busy
+    __shared__ int s_q[LINK_WARPS][VQ][4];
+    __shared__ int s_qn[LINK_WARPS], s_ln[LINK_WARPS];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int b = blockIdx.x * LINK_WARPS + warp;
     if (b >= T.tileV_pre[T.n_act]) return;
@@ -740,6 +820,7 @@ __global__ __launch_bounds__(32 * LINK_WARPS) void k_links_vertex(Pools P, StepT
     const long long MX = (long long)Q * Lx, MY = (long long)Q * Ly, HX = MX / 2, HY = MY / 2;
     int* S = s_own[warp];
     unsigned long long* list = s_list[warp];
+    if (lane == 0) s_qn[warp] = 0;
 
     // stage rows y0-1 .. y0+nrows and columns x0-1 .. x0+ncols (both periodic):
     // staged row r holds lattice row y0-1+r, column c lattice column x0+c at
@@ -777,7 +858,35 @@ __global__ __launch_bounds__(32 * LINK_WARPS) void k_links_vertex(Pools P, StepT
     int um = sc[-1], u0 = sc[0], up = sc[1];
     int om = sc[VS - 1], o0 = sc[VS], op = sc[VS + 1];
     int n = 0;   // keys in the warp's list (warp-uniform)
+    // the queued plaquette centres: colour by search, link when it is k's or
+    // the diagonal neighbour's (whole warp; n is updated)
+    auto resolve = [&]() {
+        __syncwarp();
+        const int nq = s_qn[warp];
+        if (lane == 0) s_ln[warp] = n;
+        __syncwarp();
+        for (int i2 = lane; i2 < nq; i2 += 32) {
+            const int* it = s_q[warp][i2];
+            const int k = it[0], cd = it[1], ca0 = it[2], site = it[3] >> 2, q = it[3] & 3;
+            const int yy = site / Lx, xx = site - yy * Lx;
+            const int ex = (q == 0 || q == 3) ? 1 : -1, ey = (q == 0 || q == 1) ? 1 : -1;
+            const long long qx = wrap_once((long long)Q * xx + (Q / 2) * ex, MX);
+            const long long qy = wrap_once((long long)Q * yy + (Q / 2) * ey, MY);
+            const int2 cc = cq[ca0];
+            const long long ddx = wrap_once((long long)cc.x - qx + HX, MX) - HX;
+            const long long ddy = wrap_once((long long)cc.y - qy + HY, MY) - HY;
+            const int ca = point_owner(boff, bcq, bid, St.B, St.nbx, St.nby, qx, qy, Lx, Ly, ca0,
+                                       ddx * ddx + ddy * ddy);
+            if (ca == k || ca == cd) link_list_put(list, atomicAdd(&s_ln[warp], 1), k, cd, P, D, inst);
+        }
+        __syncwarp();
+        n = s_ln[warp];
+        if (lane == 0) s_qn[warp] = 0;
+        __syncwarp();
+    };
     for (int ri = 0; ri < nrows; ++ri) {
+        __syncwarp();   // the queue count is read by every lane alike
+        if (s_qn[warp] > VQ - 4 * 32) resolve();   // a row adds at most 4 items per lane
         const int y = y0 + ri;
         const int* sd = sc + (ri + 2) * VS;
         const int dm = sd[-1], d0 = sd[0], dp = sd[1];
@@ -834,8 +943,17 @@ __global__ __launch_bounds__(32 * LINK_WARPS) void k_links_vertex(Pools P, StepT
                                 ca = c;
                             }
                         }
-                        ca = point_owner(boff, bcq, bid, St.B, St.nbx, St.nby, qx, qy, MX, MY, ca, bd);
-                        if (ca == k || ca == cd) em |= 16u << q;
+                        // a centre that owns no corner can only take the point
+                        // from a corner colour; when that colour is neither end
+                        // of the diagonal the answer is no link either way, else
+                        // the point is queued for the search
+                        if (ca == k || ca == cd) {
+                            int* it = s_q[warp][atomicAdd(&s_qn[warp], 1)];
+                            it[0] = k;
+                            it[1] = cd;
+                            it[2] = ca;
+                            it[3] = ((y * Lx + x) << 2) | q;
+                        }
                     }
                 }
             }
@@ -858,7 +976,7 @@ __global__ __launch_bounds__(32 * LINK_WARPS) void k_links_vertex(Pools P, StepT
         um = om; u0 = o0; up = op;
         om = dm; o0 = d0; op = dp;
     }
-    __syncwarp();
+    resolve();
     flush_link_list(list, n, lane, P, D, inst);
 }
 

@@ -42,12 +42,13 @@ EXPORTS = (
     "vd_config_init", "vd_set_obstacles", "vd_batch_set_obstacles", "vd_create", "vd_push_frame",
     "vd_push_frame_host", "vd_get_changes",
     "vd_get_counts", "vd_get_labels", "vd_get_centroids_q10", "vd_get_owners", "vd_get_edges",
-    "vd_get_match", "vd_export_state", "vd_import_state", "vd_debug_hold_scan_flag", "vd_set_timing", "vd_get_timing", "vd_stage_name", "vd_destroy", "vd_status_string",
+    "vd_get_match", "vd_export_state", "vd_import_state", "vd_set_tuning", "vd_get_tuning",
+    "vd_debug_hold_scan_flag", "vd_set_timing", "vd_get_timing", "vd_stage_name", "vd_destroy", "vd_status_string",
     "vd_batch_create", "vd_batch_create_sequence", "vd_batch_push", "vd_batch_push_host", "vd_batch_push_subset", "vd_batch_get_changes",
     "vd_batch_stage_host", "vd_batch_push_staged", "vd_batch_get_changes_all",
     "vd_batch_get_labels", "vd_batch_get_owners", "vd_batch_get_edges", "vd_batch_get_centroids_q10",
     "vd_batch_get_counts", "vd_batch_set_timing", "vd_batch_get_timing", "vd_batch_destroy",
-    "vd_batch_export_state", "vd_batch_import_state",
+    "vd_batch_export_state", "vd_batch_import_state", "vd_batch_set_tuning", "vd_batch_get_tuning",
     "vd_voronoi_owners_static", "vd_server_create", "vd_server_open_sim", "vd_server_close_sim",
     "vd_server_clock_ns", "vd_server_submit", "vd_server_poll", "vd_server_keep_changes",
     "vd_server_get_frame_changes", "vd_server_get_changes", "vd_server_get_labels", "vd_server_export_state",
@@ -84,6 +85,13 @@ class vd_changes(C.Structure):
         ("arising", C.POINTER(C.c_uint64)), ("cap_arising", C.c_int32),
         ("active", C.POINTER(C.c_uint8)), ("cap_active", C.c_int32),
     ]
+
+
+class vd_tuning(C.Structure):
+    _fields_ = [("voronoi_patch", C.c_int32), ("bucket_pct", C.c_int32), ("ring0", C.c_int32)]
+
+
+VD_PATCH_8x8, VD_PATCH_16x8, VD_PATCH_32x8, VD_PATCH_16x16 = 0, 1, 2, 3
 
 
 class vd_batch_changes(C.Structure):
@@ -139,6 +147,10 @@ def lib():
         "vd_batch_export_state": [VP, I32, VP, I64, P(I64)],
         "vd_batch_import_state": [VP, I32, VP, I64],
         "vd_debug_hold_scan_flag": [VP, I32, I64, I32],
+        "vd_set_tuning": [VP, P(vd_tuning)],
+        "vd_get_tuning": [VP, P(vd_tuning)],
+        "vd_batch_set_tuning": [VP, P(vd_tuning)],
+        "vd_batch_get_tuning": [VP, P(vd_tuning)],
         "vd_set_timing": [VP, I32],
         "vd_get_timing": [VP, P(C.c_double), I32, P(I32), P(I64), P(I64)],
         "vd_stage_name": [I32],
@@ -406,6 +418,16 @@ class Detector(_Base):
                     breaking_prev=brkp[: ch.n_breaking].copy(), arising=ari[: ch.n_arising].copy(),
                     active=act[: ch.n_now].copy(), global_trigger=ch.global_trigger)
 
+    def set_tuning(self, voronoi_patch: int = 0, bucket_pct: int = 100, ring0: int = 9) -> None:
+        """Launch shapes (vd_set_tuning); results are identical for every setting."""
+        t = vd_tuning(int(voronoi_patch), int(bucket_pct), int(ring0))
+        _check(lib().vd_set_tuning(self.h, C.byref(t)), "vd_set_tuning")
+
+    def tuning(self) -> dict:
+        t = vd_tuning()
+        _check(lib().vd_get_tuning(self.h, C.byref(t)), "vd_get_tuning")
+        return dict(voronoi_patch=t.voronoi_patch, bucket_pct=t.bucket_pct, ring0=t.ring0)
+
     def export_state(self) -> np.ndarray:
         """Checkpoint of the last frame's state (vd_export_state), as bytes."""
         n = C.c_int64()
@@ -538,6 +560,16 @@ class Batch(_Base):
         _check(lib().vd_batch_get_timing(self.h, ms, 16, C.byref(n), C.byref(kl), C.byref(nf)), "vd_batch_get_timing")
         names = [lib().vd_stage_name(i).decode() for i in range(n.value)]
         return list(ms[: n.value]), names, kl.value, nf.value
+
+    def set_tuning(self, voronoi_patch: int = 0, bucket_pct: int = 100, ring0: int = 9) -> None:
+        """Launch shapes of the batch (vd_batch_set_tuning); results are identical for every setting."""
+        t = vd_tuning(int(voronoi_patch), int(bucket_pct), int(ring0))
+        _check(lib().vd_batch_set_tuning(self.h, C.byref(t)), "vd_batch_set_tuning")
+
+    def tuning(self) -> dict:
+        t = vd_tuning()
+        _check(lib().vd_batch_get_tuning(self.h, C.byref(t)), "vd_batch_get_tuning")
+        return dict(voronoi_patch=t.voronoi_patch, bucket_pct=t.bucket_pct, ring0=t.ring0)
 
     def export_state(self, i: int) -> np.ndarray:
         """Checkpoint of instance i's last frame (vd_batch_export_state)."""

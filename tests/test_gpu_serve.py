@@ -127,7 +127,9 @@ def test_simulations_opened_and_closed_while_others_run():
     probe = vd.Server([sizes[s] for s in first], budget_bytes=1 << 40, max_batch=8)
     resident = probe.stats()["resident_bytes"]
     probe.close()
-    sv = vd.Server([sizes[s] for s in first], budget_bytes=resident + (64 << 20), max_batch=8, keep_changes=True)
+    # room for the frames in flight (at most 5 x 160 KB) but not for another
+    # lattice's resident state (several MB even at 64 x 64)
+    sv = vd.Server([sizes[s] for s in first], budget_bytes=resident + (2 << 20), max_batch=8, keep_changes=True)
     ids = {s: s for s in first}          # workload sim -> server id
     tickets, seen = {}, {}
     pending = [(s, f) for s, f in order]
