@@ -57,13 +57,13 @@ METRIC_BYTES_PER_SITE = 16.0
 # (profiles/launches_c1_sequence.txt); scaled to the bench launch for
 # roofline.traffic. A stage not captured, or whose kernels changed since the
 # capture, reports null.
-TRAFFIC_BYTES_PER_SITE = {0: 5.071, 2: 2.856, 3: 3.418, 4: 4.325}
+TRAFFIC_BYTES_PER_SITE = {0: 5.071, 2: 2.856}
 
 # Issue-slot use (smsp__issue_active, % of peak) of the same stages' kernels
 # from one ncu --set full capture on 2 frames of 4096^2 droplets
 # (profiles/site_kernels_c2.txt): the kernels are bound by instruction issue or
 # latency, not by DRAM, and this says how close to the issue limit they run.
-ISSUE_ACTIVE_PCT = {0: 47.8, 2: 23.3, 3: 70.9, 4: 67.5}
+ISSUE_ACTIVE_PCT = {0: 47.8, 2: 23.3}
 
 
 def workload(name: str, n_frames: int | None):
@@ -255,6 +255,22 @@ def stage_bytes(sequence: bool):
     return {0: 4.125, 2: 0.25, 3: 4.0, 4: 4.0}
 
 
+def nvtx_push(name):
+    try:
+        import torch
+        torch.cuda.nvtx.range_push(name)
+    except Exception:
+        pass
+
+
+def nvtx_pop():
+    try:
+        import torch
+        torch.cuda.nvtx.range_pop()
+    except Exception:
+        pass
+
+
 def roofline_of(stage_ms, names, launches_per_stage, sites_per_launch, sequence, peak, peak_kind):
     sb = stage_bytes(sequence)
     dom = max(sb, key=lambda k: stage_ms[k])
@@ -270,10 +286,48 @@ def roofline_of(stage_ms, names, launches_per_stage, sites_per_launch, sequence,
             "stage_ms_per_launch": {names[k]: stage_ms[k] / launches_per_stage for k in range(len(names))}}
 
 
+def plain_frames_c2(world, s, e0, e1, n_frames=4, reps=3):
+    """The plain per-frame path on 4096^2 droplet frames: vd_push_frame, one
+    frame per call (graph replay), ms per frame over reps passes."""
+    import torch
+    from paper_1607_00908_gb300 import vd
+    frames = [F for F, _ in inputs.workload_c2(1, n_frames)]
+    Ly, Lx = frames[0].shape
+    dev = [torch.from_numpy(F).cuda() for F in frames]
+    det = vd.Detector(Lx, Ly, stream=s.cuda_stream)
+    for F in dev:
+        det.push(F)
+    torch.cuda.synchronize()
+    e0.record(s)
+    for _ in range(reps):
+        for F in dev:
+            det.push(F)
+    e1.record(s)
+    torch.cuda.synchronize()
+    ms = max_over_ranks(e0.elapsed_time(e1), world)
+    det.close()
+    return {"value": world * Lx * Ly * n_frames * reps / (ms / 1e3) / 1e9, "unit": UNIT,
+            "ms_per_frame": ms / reps / n_frames, "frames": n_frames * reps,
+            "workload": f"{Lx}x{Ly} RSA droplets r~U[8,12], {n_frames} frames, each pushed {reps} times",
+            "path": "vd_push_frame per frame (graph replay)"}
+
+
+def pick_tuning(args, b, dev, s):
+    """The autotuner's choice for batch b, or the setting given as
+    --tuning PATCH,BUCKET_PCT,RING0 (e.g. 8x8,100,9)."""
+    from paper_1607_00908_gb300 import autotune, vd
+    if args.tuning == "auto":
+        return autotune.tune(b, dev, s, use_cache=False)
+    patch, bucket, ring = args.tuning.split(",")
+    t = dict(voronoi_patch=getattr(vd, "VD_PATCH_" + patch), bucket_pct=int(bucket), ring0=int(ring))
+    b.set_tuning(**t)
+    return dict(t, fixed=True)
+
+
 def run_ours(args, world, rank, local):
     c3 = None if args.no_c3 else c3_host_frames(rank)   # host cores, before the first GPU call
     import torch
-    from paper_1607_00908_gb300 import autotune, vd
+    from paper_1607_00908_gb300 import vd
 
     torch.cuda.set_device(local if world > 1 else 0)
     vd.lib()
@@ -290,7 +344,7 @@ def run_ours(args, world, rank, local):
     # a timed step is R pushes, R set from the warm-up so that the K steps
     # last at least args.min_seconds ----
     seq = vd.Batch([(Lx, Ly)], sequence=n, stream=s.cuda_stream)
-    tuned = autotune.tune(seq, dev, s, use_cache=False)   # launch shapes for this workload (untimed)
+    tuned = pick_tuning(args, seq, dev, s)   # launch shapes for this workload (untimed)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
     e0.record(s)
@@ -308,11 +362,13 @@ def run_ours(args, world, rank, local):
     launches0 = seq.timing()[2]
     barrier(world)
     torch.cuda.synchronize()
+    nvtx_push("vd_timed")   # lets a profiler select the timed pushes
     e0.record(s)
     for _ in range(args.steps * reps):
         seq.push(dev)
     e1.record(s)
     torch.cuda.synchronize()
+    nvtx_pop()
     barrier(world)
     ms = e0.elapsed_time(e1)
     clk = clocks.stop()
@@ -409,6 +465,7 @@ def run_ours(args, world, rank, local):
     det.close()
     del dev
     torch.cuda.synchronize()
+    plain_c2 = None if args.no_c2_plain else plain_frames_c2(world, s, e0, e1)
 
     # ---- the batched and served forms (the metric's "batched/served vs plain") ----
     batched = measure_batched(world, *c3) if c3 is not None else None
@@ -432,7 +489,7 @@ def run_ours(args, world, rank, local):
                        "l2_policy": "inputs larger than L2 (each step reads all frames once)",
                        "parallelism": f"replicas x{world}"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
-            "gpu_launches": launches, "plain_per_frame": plain, "options": variants,
+            "gpu_launches": launches, "plain_per_frame": plain, "plain_per_frame_c2": plain_c2, "options": variants,
         }
         if batched is not None:
             line["batched_c3"] = batched
@@ -631,6 +688,9 @@ def main():
     ap.add_argument("--serve-rate", type=float, default=2000.0, help="served workload: arrivals per second")
     ap.add_argument("--min-seconds", type=float, default=1.5,
                     help="headline: the K timed steps last at least this long (pushes per step set from the warm-up)")
+    ap.add_argument("--tuning", default="auto",
+                    help="headline launch shapes: auto (the autotuner) or PATCH,BUCKET_PCT,RING0, e.g. 8x8,100,9")
+    ap.add_argument("--no-c2-plain", action="store_true", help="leave the per-frame 4096^2 figure out of the line")
     ap.add_argument("--no-c3", action="store_true", help="leave the batched form out of the default line")
     ap.add_argument("--no-c4", action="store_true", help="leave the served form out of the default line")
     args = ap.parse_args()

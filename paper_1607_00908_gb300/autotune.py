@@ -10,7 +10,9 @@ VD_AUTOTUNE_CACHE, default ~/.cache/vd_autotune.json).
 
 Candidates are searched one parameter at a time (patch layout, then bucket
 side, then first reach), each timed as whole pushes with CUDA events on the
-batch's stream after a warm-up push. Timing pushes advance the batch: tune it
+batch's stream after a warm-up push (the best of three rounds); a candidate
+replaces the current setting only when it is faster by more than 1%, so that
+timing noise does not pick among equal settings. Timing pushes advance the batch: tune it
 on the first frames of a run, before the frames whose results are used.
 """
 from __future__ import annotations
@@ -58,19 +60,24 @@ def _store(path, data):
     os.replace(tmp, path)
 
 
-def _time_push(b, fields, stream, reps: int) -> float:
+def _time_push(b, fields, stream, reps: int, rounds: int = 3) -> float:
+    """ms per push: the best of `rounds` rounds of `reps` pushes (the best
+    round is the least disturbed by other work on the device)."""
     import torch
     b.push(fields)   # warm-up (and graph capture after a change of layout)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(reps):
-        b.push(fields)
-    e1.record(stream)
-    e1.synchronize()
-    return e0.elapsed_time(e1) / reps
+    best = float("inf")
+    for _ in range(rounds):
+        e0.record(stream)
+        for _ in range(reps):
+            b.push(fields)
+        e1.record(stream)
+        e1.synchronize()
+        best = min(best, e0.elapsed_time(e1) / reps)
+    return best
 
 
-def tune(b, fields, stream, reps: int = 3, use_cache: bool = True) -> dict:
+def tune(b, fields, stream, reps: int = 8, use_cache: bool = True) -> dict:
     """Pick and set the fastest tuning of batch `b` (a vd.Batch) for pushes of
     `fields` (its device frames); returns the chosen setting with its key,
     the ms per push of the default and of the chosen setting, and whether it
@@ -96,7 +103,7 @@ def tune(b, fields, stream, reps: int = 3, use_cache: bool = True) -> dict:
                 continue
             b.set_tuning(**cand)
             tried[k] = ms = _time_push(b, fields, stream, reps)
-            if ms < best_ms:
+            if ms < 0.99 * best_ms:
                 best_ms, cur = ms, cand
         b.set_tuning(**cur)
     result = dict(cur, default_ms=base, tuned_ms=best_ms, candidates=len(tried))

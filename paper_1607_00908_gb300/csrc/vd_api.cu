@@ -91,16 +91,6 @@ struct vd_batch {
     long long* d_pitches = nullptr;
     std::vector<const float*> h_fields;
     std::vector<long long> h_pitches;
-    // pinned copies of those tables, a ring of PIN_RING sets: the copy to the
-    // device is then asynchronous (a copy from pageable memory may wait for
-    // the stream), and a set is reused only after the copy that read it ran
-    static const int PIN_RING = 4;
-    const float** pin_fields[PIN_RING] = {};
-    long long* pin_pitches[PIN_RING] = {};
-    long long* pin_tab[PIN_RING] = {};   // subset step tables: act, tileA, tileV (n+1 each), groups (n+1)
-    cudaEvent_t pin_ev[PIN_RING] = {};
-    bool pin_used[PIN_RING] = {};
-    int pin_next = 0;
     // host input staging for vd_push_frame_host (instance 0)
     float* d_host_field = nullptr;
     // double-buffered host input (vd_batch_stage_host / vd_batch_push_staged):
@@ -207,30 +197,10 @@ void build_table(vd_batch* b, const std::vector<int>& act, StepTables& T, bool a
     T.total_tilesA = tA[n];
     T.total_tilesV = tV[n];
     T.total_groups = wd[n];
-    if (alloc) {   // at creation: plain copies (the creation synchronises)
-        cudaMemcpyAsync(T.d_act, act.data(), sizeof(int) * n, cudaMemcpyHostToDevice, b->s);
-        cudaMemcpyAsync(T.d_tileA, tA.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice, b->s);
-        cudaMemcpyAsync(T.d_tileV, tV.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice, b->s);
-        cudaMemcpyAsync(T.d_groups, wd.data(), sizeof(long long) * (n + 1), cudaMemcpyHostToDevice, b->s);
-        return;
-    }
-    // per step: through the pinned set the step's field tables used (its
-    // event, recorded again below, guards its reuse)
-    const int k = (b->pin_next + vd_batch::PIN_RING - 1) % vd_batch::PIN_RING;
-    const int m = b->n + 1;
-    int* pa = reinterpret_cast<int*>(b->pin_tab[k]);
-    int* pA = pa + m;
-    int* pV = pA + m;
-    long long* pg = b->pin_tab[k] + 2 * m;
-    std::memcpy(pa, act.data(), sizeof(int) * n);
-    std::memcpy(pA, tA.data(), sizeof(int) * (n + 1));
-    std::memcpy(pV, tV.data(), sizeof(int) * (n + 1));
-    std::memcpy(pg, wd.data(), sizeof(long long) * (n + 1));
-    cudaMemcpyAsync(T.d_act, pa, sizeof(int) * n, cudaMemcpyHostToDevice, b->s);
-    cudaMemcpyAsync(T.d_tileA, pA, sizeof(int) * (n + 1), cudaMemcpyHostToDevice, b->s);
-    cudaMemcpyAsync(T.d_tileV, pV, sizeof(int) * (n + 1), cudaMemcpyHostToDevice, b->s);
-    cudaMemcpyAsync(T.d_groups, pg, sizeof(long long) * (n + 1), cudaMemcpyHostToDevice, b->s);
-    cudaEventRecord(b->pin_ev[k], b->s);
+    cudaMemcpyAsync(T.d_act, act.data(), sizeof(int) * n, cudaMemcpyHostToDevice, b->s);
+    cudaMemcpyAsync(T.d_tileA, tA.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice, b->s);
+    cudaMemcpyAsync(T.d_tileV, tV.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice, b->s);
+    cudaMemcpyAsync(T.d_groups, wd.data(), sizeof(long long) * (n + 1), cudaMemcpyHostToDevice, b->s);
 }
 
 Launch make_launch(vd_batch* b, const StepTables& T) {
@@ -495,32 +465,14 @@ vd_status create_batch(const vd_config* cfgs, int n, vd_batch** out, bool sequen
     b->h_fields.assign(n, nullptr);
     b->h_pitches.assign(n, 0);
     b->imported_at.assign(n, -1);
-    for (int k = 0; k < vd_batch::PIN_RING; ++k) {
-        if (cudaMallocHost(&b->pin_fields[k], sizeof(float*) * n) != cudaSuccess ||
-            cudaMallocHost(&b->pin_pitches[k], sizeof(long long) * n) != cudaSuccess ||
-            cudaMallocHost(&b->pin_tab[k], sizeof(long long) * 4 * (n + 1)) != cudaSuccess ||
-            cudaEventCreateWithFlags(&b->pin_ev[k], cudaEventDisableTiming) != cudaSuccess) {
-            cudaGetLastError();
-            M.ok = false;
-        }
-    }
-    auto release_pins = [&]() {
-        for (int k = 0; k < vd_batch::PIN_RING; ++k) {
-            if (b->pin_fields[k]) cudaFreeHost(b->pin_fields[k]);
-            if (b->pin_pitches[k]) cudaFreeHost(b->pin_pitches[k]);
-            if (b->pin_tab[k]) cudaFreeHost(b->pin_tab[k]);
-            if (b->pin_ev[k]) cudaEventDestroy(b->pin_ev[k]);
-        }
-    };
+
     if (!M.ok) {
-        release_pins();
         M.release();
         delete b;
         return VD_ERR_OOM;
     }
     chk(cudaStreamSynchronize(b->s));
     if (e != cudaSuccess) {
-        release_pins();
         M.release();
         delete b;
         return VD_ERR_CUDA;
@@ -635,16 +587,12 @@ vd_status push_fields(vd_batch* b, const std::vector<int>& act, const float* con
         b->h_fields[act[a]] = fields[a];
         b->h_pitches[act[a]] = pitches[a];
     }
-    const int k = b->pin_next;
-    if (b->pin_used[k] && cudaEventSynchronize(b->pin_ev[k]) != cudaSuccess) return VD_ERR_CUDA;
-    std::memcpy(b->pin_fields[k], b->h_fields.data(), sizeof(float*) * b->n);
-    std::memcpy(b->pin_pitches[k], b->h_pitches.data(), sizeof(long long) * b->n);
-    cudaError_t e = cudaMemcpyAsync(b->d_fields, b->pin_fields[k], sizeof(float*) * b->n, cudaMemcpyHostToDevice, b->s);
+    // small copies from pageable memory: the runtime stages them before it
+    // returns (the vectors may change right after) and they do not queue on a
+    // copy engine behind a large staged frame copy, as pinned copies would
+    cudaError_t e = cudaMemcpyAsync(b->d_fields, b->h_fields.data(), sizeof(float*) * b->n, cudaMemcpyHostToDevice, b->s);
     if (e == cudaSuccess)
-        e = cudaMemcpyAsync(b->d_pitches, b->pin_pitches[k], sizeof(long long) * b->n, cudaMemcpyHostToDevice, b->s);
-    if (e == cudaSuccess) e = cudaEventRecord(b->pin_ev[k], b->s);
-    b->pin_used[k] = true;
-    b->pin_next = (k + 1) % vd_batch::PIN_RING;
+        e = cudaMemcpyAsync(b->d_pitches, b->h_pitches.data(), sizeof(long long) * b->n, cudaMemcpyHostToDevice, b->s);
     return cuda_status(e);
 }
 
@@ -1515,12 +1463,6 @@ vd_status vd_batch_destroy(vd_batch* b) {
     for (int k = 0; k < 2; ++k) {
         if (b->ev_staged[k]) cudaEventDestroy(b->ev_staged[k]);
         if (b->ev_read[k]) cudaEventDestroy(b->ev_read[k]);
-    }
-    for (int k = 0; k < vd_batch::PIN_RING; ++k) {
-        cudaFreeHost(b->pin_fields[k]);
-        cudaFreeHost(b->pin_pitches[k]);
-        cudaFreeHost(b->pin_tab[k]);
-        if (b->pin_ev[k]) cudaEventDestroy(b->pin_ev[k]);
     }
     b->mem.release();
     delete b;

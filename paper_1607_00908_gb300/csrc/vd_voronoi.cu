@@ -4,8 +4,8 @@
 // minimum image on the torus, ties to the smallest label). The paper computes
 // this by scanning every centre from every site; here each 64 x 32 tile first
 // collects a provably complete candidate set from a bucket grid of centres,
-// and each 16 x 8 patch of it keeps only the centres that can own one of its
-// sites:
+// and each patch of it (8 x 8 sites by default; the layout is a launch shape)
+// keeps only the centres that can own one of its sites:
 //   U_p   = min over scanned centres of an upper bound of their largest
 //           distance to patch p (so every site of p has a centre within U_p),
 //   keep  = centres whose smallest distance to the patch is <= U_p,
