@@ -53,17 +53,22 @@ PIPELINE_BYTES_PER_SITE = 8.0
 METRIC_BYTES_PER_SITE = 16.0
 
 # Measured DRAM bytes (read + write) per site of a stage's kernels, from one
-# ncu capture of the current kernels on this workload
-# (profiles/launches_c1_sequence.txt); scaled to the bench launch for
-# roofline.traffic. A stage not captured, or whose kernels changed since the
-# capture, reports null.
-TRAFFIC_BYTES_PER_SITE = {0: 5.071, 2: 2.856}
+# ncu capture of the current kernels on 48 frames of this workload
+# (profiles/site_kernels_c1.txt); scaled to the bench launch for
+# roofline.traffic. The owner stage's entry depends on its patch layout
+# (VD_PATCH_*); a stage or layout not captured, or whose kernels changed since
+# the capture, reports null.
+TRAFFIC_BYTES_PER_SITE = {0: 4.935, 2: 2.842, 3: {0: 2.873}, 4: 4.342}
 
-# Issue-slot use (smsp__issue_active, % of peak) of the same stages' kernels
-# from one ncu --set full capture on 2 frames of 4096^2 droplets
-# (profiles/site_kernels_c2.txt): the kernels are bound by instruction issue or
-# latency, not by DRAM, and this says how close to the issue limit they run.
-ISSUE_ACTIVE_PCT = {0: 47.8, 2: 23.3}
+# Issue-slot use (smsp__issue_active, % of peak) of the same kernels in the
+# same capture: the kernels are bound by instruction issue or latency, not by
+# DRAM, and this says how close to the issue limit they run.
+ISSUE_ACTIVE_PCT = {0: 48.8, 2: 32.0, 3: {0: 69.8}, 4: 41.1}
+
+
+def per_stage(table, stage, patch):
+    v = table.get(stage)
+    return v.get(patch) if isinstance(v, dict) else v
 
 
 def workload(name: str, n_frames: int | None):
@@ -271,17 +276,17 @@ def nvtx_pop():
         pass
 
 
-def roofline_of(stage_ms, names, launches_per_stage, sites_per_launch, sequence, peak, peak_kind):
+def roofline_of(stage_ms, names, launches_per_stage, sites_per_launch, sequence, peak, peak_kind, patch=0):
     sb = stage_bytes(sequence)
     dom = max(sb, key=lambda k: stage_ms[k])
     avg_ms = stage_ms[dom] / launches_per_stage
     bytes_per_launch = sb[dom] * sites_per_launch
     achieved = bytes_per_launch / (avg_ms / 1e3) / 1e9
-    traffic = TRAFFIC_BYTES_PER_SITE.get(dom)
+    traffic = per_stage(TRAFFIC_BYTES_PER_SITE, dom, patch)
     return {"bound": "hbm", "kernel": names[dom], "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": achieved / peak, "peak_kind": peak_kind,
             "traffic": traffic * sites_per_launch if traffic is not None else None,
-            "issue_active_pct_ncu": ISSUE_ACTIVE_PCT.get(dom),
+            "issue_active_pct_ncu": per_stage(ISSUE_ACTIVE_PCT, dom, patch),
             "bytes_per_site": sb[dom], "bytes_per_launch": bytes_per_launch, "avg_launch_ms": avg_ms,
             "stage_ms_per_launch": {names[k]: stage_ms[k] / launches_per_stage for k in range(len(names))}}
 
@@ -384,7 +389,8 @@ def run_ours(args, world, rank, local):
         seq.push(dev)
     stage_ms, names, _, _ = seq.timing()
     seq.set_timing(False)
-    roofline = roofline_of(stage_ms, names, n_timed, sites_per_push, n > 1, peak, peak_kind)
+    roofline = roofline_of(stage_ms, names, n_timed, sites_per_push, n > 1, peak, peak_kind,
+                           seq.tuning()["voronoi_patch"])
     roofline["pipeline_frac_8B_per_site"] = value * PIPELINE_BYTES_PER_SITE / peak
     roofline["pct_hbm_16B_per_site"] = 100.0 * value * METRIC_BYTES_PER_SITE / peak
 

@@ -27,8 +27,12 @@ def test_roofline_of_takes_the_slowest_site_stage():
     assert r["bytes_per_launch"] == 4.0 * sites
     assert r["achieved"] == pytest.approx(4.0 * sites / 0.23e-3 / 1e9)
     assert r["frac"] == pytest.approx(r["achieved"] / 6000.0)
-    assert r["traffic"] == pytest.approx(bench.TRAFFIC_BYTES_PER_SITE[3] * sites)
+    t = bench.per_stage(bench.TRAFFIC_BYTES_PER_SITE, 3, 0)
+    assert r["traffic"] is None if t is None else r["traffic"] == pytest.approx(t * sites)
     assert r["stage_ms_per_launch"]["s5"] == pytest.approx(0.99)
+    # a stage whose entry does not depend on the layout
+    r = bench.roofline_of([9.0, 1.0, 0.9, 2.3, 1.9, 0.1], names, 10, sites, True, 6000.0, "measured", patch=2)
+    assert r["kernel"] == "s0" and r["traffic"] == pytest.approx(bench.TRAFFIC_BYTES_PER_SITE[0] * sites)
 
 
 class _Done:
