@@ -102,33 +102,45 @@ struct VLayout {
     static constexpr int PW = PW_, PH = PH_;
     static constexpr int NPX = TW / PW, NPY = TH / PH, NP = NPX * NPY;
     static constexpr int SPL = PW * PH / 32;
+    // resident blocks per SM the registers are sized for (measured: 8x8
+    // patches run fastest at 72 registers, the others at 64)
+    static constexpr int MINB = (PW == 8 && PH == 8) ? 14 : 16;
     static_assert(TW % PW == 0 && TH % PH == 0 && NP <= 32 && 32 % PW == 0 && SPL >= 1 &&
                       (32 / PW) * SPL == PH,
                   "patch layout");
 };
 
-// Exact owner over a candidate list with int64 distances (coordinates
-// relative to the tile origin, no wrap needed), ties to the smallest label.
-// `kk` (may be null) maps list positions to entries of cx/cy/id.
-__device__ __forceinline__ int owner_exact(long long sx, long long sy, const int* cx, const int* cy, const int* id,
-                                           const int* kk, int n) {
+// The integer held in a list coordinate (an integer in [-2^22, 2^22), exact
+// in float32): adding 1.5 * 2^23 places it in [2^23, 2^24), where the float's
+// low mantissa bits are the integer plus 2^22 -- two full-rate instructions
+// instead of a conversion.
+__device__ __forceinline__ int list_int(float v) { return __float_as_int(v + 12582912.f) - 0x4B400000; }
+// and the converse, for integers in [-2^22, 2^22)
+__device__ __forceinline__ float int_to_f(int i) { return __int_as_float(0x4B400000 + i) - 12582912.f; }
+
+// Exact owner over a kept list with int64 distances (coordinates relative to
+// the tile origin, no wrap needed), ties to the smallest label. kk maps list
+// positions to entries.
+__device__ __forceinline__ int owner_exact(long long sx, long long sy, const float2* cf, const int* id, const int* kk,
+                                           int n) {
     long long best = LLONG_MAX;
     int bi = -1;
     for (int j = 0; j < n; ++j) {
-        const int e = kk ? kk[j] : j;
-        const long long dx = sx - cx[e], dy = sy - cy[e];
+        const int e = kk[j];
+        const long long dx = sx - list_int(cf[e].x), dy = sy - list_int(cf[e].y);
         const long long d2 = dx * dx + dy * dy;
         if (d2 < best || (d2 == best && id[e] < bi)) { best = d2; bi = id[e]; }
     }
     return bi;
 }
 
-// squared largest distance from a coordinate to [lo, hi] on a ring (<= M/2),
-// rounded up in float32
-__device__ __forceinline__ float far2_ru(int d, int lo, int hi, int halfM) {
-    const int a = abs(d - lo), b = abs(d - hi);
-    const float f = __int2float_ru(min(max(a, b), halfM));
-    return __fmul_ru(f, f);
+// A scanned centre's coordinate as held in the list: the tile-relative
+// minimum image when it lies in [-2^22, 2^22) (exact in float32), else
+// +-2^31, which makes the patch bound take the half-period cap for that axis
+// (a larger upper bound, still valid); such a tile takes the general path.
+__device__ __forceinline__ bool list_exact(int w) { return w >= -(1 << 22) && w < (1 << 22); }
+__device__ __forceinline__ float list_coord(int w) {
+    return list_exact(w) ? (float)w : (w > 0 ? 2147483648.f : -2147483648.f);
 }
 
 // One warp per 64 x 32 tile (the labelling tiles), no block-level
@@ -152,15 +164,18 @@ __device__ __forceinline__ float far2_ru(int d, int lo, int hi, int halfM) {
 //     runner-up) and decided exactly in int64 over the kept list when the two
 //     are within 2^-15 relative (truncation 2^-17 + rounding 2^-23 cannot
 //     reorder them otherwise), ties to the smallest label.
-//  A tile whose scanned centres are not minimum images for every site or not
-//  exact in float32, or whose scan exceeds WSCAN centres, takes the general
-//  path (exact int64 per site over the scanned list or buckets).
+//  Centres are held in float32 (integers below 2^22, exact), so the bound and
+//  list passes run on the FP32 pipe without conversions. A tile whose scanned
+//  centres are not minimum images for every site or not exact in float32, or
+//  whose scan exceeds WSCAN centres, takes the general path (exact int64 per
+//  site over the scanned buckets).
 template <int PW, int PH>
-__global__ __launch_bounds__(32 * VWARPS, 16) void k_voronoi(Pools P, StepTable T) {
+__global__ __launch_bounds__(32 * VWARPS, VLayout<PW, PH>::MINB) void k_voronoi(Pools P, StepTable T) {
     using LY = VLayout<PW, PH>;
     constexpr int NPX = LY::NPX, NP = LY::NP, SPL = LY::SPL;
     pdl_enter();
-    __shared__ int s_cx[VWARPS][WSCAN], s_cy[VWARPS][WSCAN], s_id[VWARPS][WSCAN];
+    __shared__ float2 s_cf[VWARPS][WSCAN];
+    __shared__ int s_id[VWARPS][WSCAN];
     __shared__ int s_kept[VWARPS][NP][KMAX];
     __shared__ int s_nk[VWARPS][NP];
     __shared__ int s_tpre[SEG_CACHE];
@@ -199,15 +214,23 @@ __global__ __launch_bounds__(32 * VWARPS, 16) void k_voronoi(Pools P, StepTable 
     const int* boff = P.boff[S.slot ^ 1] + D.bucket_off;
     const int2* bcq = P.bcq[S.slot ^ 1] + D.comp_off;
     const int* bid = P.bid[S.slot ^ 1] + D.comp_off;
-    int* cxs = s_cx[warp];
-    int* cys = s_cy[warp];
+    float2* cfs = s_cf[warp];
     int* ids = s_id[warp];
     // this lane's patch (lanes past the last patch repeat it and are not counted)
     const int pp = lane < NP ? lane : NP - 1;
     const int ppx = PW * (pp % NPX), ppy = PH * (pp / NPX);
     const bool pvalid = lane < NP && ppx < ncols && ppy < nrows;
-    const int pxlo = Q * ppx, pxhi = Q * (min(ppx + PW, ncols) - 1);
-    const int pylo = Q * ppy, pyhi = Q * (min(ppy + PH, nrows) - 1);
+    const int pxlo = Q * ppx, pxhi = Q * max(min(ppx + PW, ncols) - 1, ppx);
+    const int pylo = Q * ppy, pyhi = Q * max(min(ppy + PH, nrows) - 1, ppy);
+    // patch centre and half extent (multiples of Q/2: exact in float32); the
+    // largest distance of a point d to the patch along x is |d - mx| + hwx,
+    // the smallest max(0, |d - mx| - hwx)
+    const float mxf = (float)((pxlo + pxhi) >> 1), hwxf = (float)((pxhi - pxlo) >> 1);
+    const float myf = (float)((pylo + pyhi) >> 1), hwyf = (float)((pyhi - pylo) >> 1);
+    const float hMXf = __int2float_ru(hMX), hMYf = __int2float_ru(hMY);
+    // minimum image for every site of the tile, and exact in float32
+    const int WRt = Q * (ncols - 1), HRt = Q * (nrows - 1);
+    bool fit = true;
     float Up = INFINITY;
     int qx0 = 0, qx1 = -1, qy0 = 0, qy1 = -1;   // previous round's region
     bool qfx = false, qfy = false, have_prev = false;
@@ -251,16 +274,21 @@ __global__ __launch_bounds__(32 * VWARPS, 16) void k_voronoi(Pools P, StepTable 
             n += __shfl_sync(0xffffffffu, inc, 31);
             for (int j = jb; j < je && pos < WSCAN; ++j, ++pos) {
                 const int2 cc = bcq[j];
-                cxs[pos] = (int)wrapM((long long)cc.x - X0, MX);
-                cys[pos] = (int)wrapM((long long)cc.y - Y0, MY);
+                const int wx = (int)wrapM((long long)cc.x - X0, MX), wy = (int)wrapM((long long)cc.y - Y0, MY);
+                fit = fit && wx > WRt - hMX && wy > HRt - hMY && list_exact(wx) && list_exact(wy);
+                cfs[pos] = make_float2(list_coord(wx), list_coord(wy));
                 ids[pos] = bid[j];
             }
         }
         __syncwarp();
         // this lane's patch bound over the centres of this round
         const int ne = min(n, WSCAN);
-        for (int j = nb; j < ne; ++j)
-            Up = fminf(Up, __fadd_ru(far2_ru(cxs[j], pxlo, pxhi, hMX), far2_ru(cys[j], pylo, pyhi, hMY)));
+        for (int j = nb; j < ne; ++j) {
+            const float2 c = cfs[j];
+            const float tx = fminf(__fadd_ru(fabsf(c.x - mxf), hwxf), hMXf);
+            const float ty = fminf(__fadd_ru(fabsf(c.y - myf), hwyf), hMYf);
+            Up = fminf(Up, __fadd_ru(__fmul_ru(tx, tx), __fmul_ru(ty, ty)));
+        }
         nb = ne;
         float Umax = pvalid ? Up : 0.f;
 #pragma unroll
@@ -287,19 +315,9 @@ __global__ __launch_bounds__(32 * VWARPS, 16) void k_voronoi(Pools P, StepTable 
 
     // The fast path needs every scanned centre's tile-relative position to be
     // its minimum image for every site of the tile (otherwise the distances
-    // are not the torus distances) and exact in float32 (|v| < 2^23).
+    // are not the torus distances) and exact in float32 (in [-2^22, 2^22)).
     const bool over = n > WSCAN;
-    bool bad = over;
-    if (!over) {
-        const int WRt = Q * (ncols - 1), HRt = Q * (nrows - 1);
-        for (int k = lane; k < n; k += 32) {
-            const int cx = cxs[k], cy = cys[k];
-            if (!(cx > WRt - hMX && cy > HRt - hMY && cx < (1 << 23) && cx > -(1 << 23) && cy < (1 << 23) &&
-                  cy > -(1 << 23)))
-                bad = true;
-        }
-        bad = __any_sync(0xffffffffu, bad);
-    }
+    const bool bad = __any_sync(0xffffffffu, !fit) || over;
 
     if (!bad) {
         // ---- 2. kept list of this lane's patch ----
@@ -307,9 +325,9 @@ __global__ __launch_bounds__(32 * VWARPS, 16) void k_voronoi(Pools P, StepTable 
             int* kl = s_kept[warp][lane];
             int nk = 0;
             for (int j = 0; j < n; ++j) {
-                const int cx = cxs[j], cy = cys[j];
-                const int ex = max(0, max(pxlo - cx, cx - pxhi)), ey = max(0, max(pylo - cy, cy - pyhi));
-                const float exf = __int2float_rd(ex), eyf = __int2float_rd(ey);
+                const float2 c = cfs[j];
+                // exact: integers below 2^23
+                const float exf = fmaxf(fabsf(c.x - mxf) - hwxf, 0.f), eyf = fmaxf(fabsf(c.y - myf) - hwyf, 0.f);
                 if (__fmaf_rd(exf, exf, __fmul_rd(eyf, eyf)) <= Up) {
                     if (nk < KMAX) kl[nk] = j;
                     ++nk;
@@ -319,6 +337,7 @@ __global__ __launch_bounds__(32 * VWARPS, 16) void k_voronoi(Pools P, StepTable 
         }
         __syncwarp();
         // ---- 3. nearest kept centre for every site, patch by patch ----
+        int* ownT = own + (long long)y0 * Lx + x0;   // rows of the tile: row offsets below 2^26
         const int c = lane % PW, rb = (lane / PW) * SPL;
 #pragma unroll 1
         for (int p = 0; p < NP; ++p) {
@@ -339,7 +358,8 @@ __global__ __launch_bounds__(32 * VWARPS, 16) void k_voronoi(Pools P, StepTable 
                     // the bisector decides: d(s,c1)^2 - d(s,c2)^2 = 2 s.(c2 - c1) + |c1|^2 - |c2|^2,
                     // exact in int64 (tile-relative minimum images), ties to the smaller label
                     const int e1 = kk[0], e2 = kk[1];
-                    const long long c1x = cxs[e1], c1y = cys[e1], c2x = cxs[e2], c2y = cys[e2];
+                    const long long c1x = list_int(cfs[e1].x), c1y = list_int(cfs[e1].y);
+                    const long long c2x = list_int(cfs[e2].x), c2y = list_int(cfs[e2].y);
                     const int i1 = ids[e1], i2 = ids[e2];
                     const int itie = i1 < i2 ? i1 : i2;
                     const long long ax = 2 * (c2x - c1x), ay = 2 * (c2y - c1y);
@@ -352,19 +372,20 @@ __global__ __launch_bounds__(32 * VWARPS, 16) void k_voronoi(Pools P, StepTable 
                         dv += step;
                     }
                 } else if (nk <= KMAX) {
-                    const float sxf = (float)(Q * sx);
+                    const float sxf = int_to_f(Q * sx);
                     float syf[SPL];
                     unsigned f1[SPL], f2[SPL];
 #pragma unroll
                     for (int k = 0; k < SPL; ++k) {
                         f1[k] = 0x7f800000u;
                         f2[k] = 0x7f800000u;
-                        syf[k] = (float)(Q * (pyo + rb + k));
+                        syf[k] = int_to_f(Q * (pyo + rb + k));
                     }
                     for (int j = 0; j < nk; ++j) {
                         const int e = kk[j];
-                        const float dx = sxf - (float)cxs[e];
-                        const float cyf = (float)cys[e];
+                        const float2 ce = cfs[e];
+                        const float dx = sxf - ce.x;
+                        const float cyf = ce.y;
                         const float dx2 = dx * dx;
 #pragma unroll
                         for (int k = 0; k < SPL; ++k) {
@@ -383,34 +404,36 @@ __global__ __launch_bounds__(32 * VWARPS, 16) void k_voronoi(Pools P, StepTable 
                         if (f2[k] == 0x7f800000u || a2 - a1 > a2 * 3.0517578125e-05f)
                             o[k] = ids[kk[f1[k] & 63u]];
                         else
-                            o[k] = owner_exact((long long)Q * sx, (long long)Q * (pyo + rb + k), cxs, cys, ids, kk, nk);
+                            o[k] = owner_exact((long long)Q * sx, (long long)Q * (pyo + rb + k), cfs, ids, kk, nk);
                     }
                 } else {
                     // more kept centres than the list holds: exact over all scanned
 #pragma unroll
-                    for (int k = 0; k < SPL; ++k)
-                        o[k] = owner_exact((long long)Q * sx, (long long)Q * (pyo + rb + k), cxs, cys, ids, nullptr, n);
+                    for (int k = 0; k < SPL; ++k) {
+                        const long long qx = (long long)Q * sx, qy = (long long)Q * (pyo + rb + k);
+                        long long best = LLONG_MAX;
+                        int bi = -1;
+                        for (int j = 0; j < n; ++j) {
+                            const long long dx = qx - list_int(cfs[j].x), dy = qy - list_int(cfs[j].y);
+                            const long long d2 = dx * dx + dy * dy;
+                            if (d2 < best || (d2 == best && ids[j] < bi)) { best = d2; bi = ids[j]; }
+                        }
+                        o[k] = bi;
+                    }
                 }
 #pragma unroll
                 for (int k = 0; k < SPL; ++k)
-                    if (rb + k < ph) own[(long long)(y0 + pyo + rb + k) * Lx + x0 + sx] = o[k];
+                    if (rb + k < ph) ownT[(pyo + rb + k) * Lx + sx] = o[k];
             }
         }
     } else {
         // ---- general path: per-site minimum image, exact int64, over the
-        // scanned list, or over the scanned buckets when the list overflowed ----
+        // scanned buckets (the list holds rounded values for far centres) ----
         for (int k = lane; k < ncols * nrows; k += 32) {
             const int lx = k % ncols, ly = k / ncols;
             long long best = LLONG_MAX;
             int bi = -1;
-            if (!over) {
-                const long long sx = (long long)Q * lx, sy = (long long)Q * ly;   // relative to the tile origin
-                for (int j = 0; j < n; ++j) {
-                    const long long dx = wrapM(sx - cxs[j], MX), dy = wrapM(sy - cys[j], MY);
-                    const long long d2 = dx * dx + dy * dy;
-                    if (d2 < best || (d2 == best && ids[j] < bi)) { best = d2; bi = ids[j]; }
-                }
-            } else {
+            {
                 const long long sx = (long long)Q * (x0 + lx), sy = (long long)Q * (y0 + ly);
                 for (int rv = ry0; rv <= ry1; ++rv) {
                     const int rm = rv < 0 ? rv + nby : (rv >= nby ? rv - nby : rv);
