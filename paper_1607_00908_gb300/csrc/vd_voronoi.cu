@@ -102,10 +102,13 @@ struct VLayout {
     static constexpr int PW = PW_, PH = PH_;
     static constexpr int NPX = TW / PW, NPY = TH / PH, NP = NPX * NPY;
     static constexpr int SPL = PW * PH / 32;
+    // lanes per patch in the bound and kept-list passes: lane l serves patch
+    // l % NP and takes every LPP-th scanned centre
+    static constexpr int LPP = 32 / NP;
     // resident blocks per SM the registers are sized for (measured: 8x8
     // patches run fastest at 72 registers, the others at 64)
     static constexpr int MINB = (PW == 8 && PH == 8) ? 14 : 16;
-    static_assert(TW % PW == 0 && TH % PH == 0 && NP <= 32 && 32 % PW == 0 && SPL >= 1 &&
+    static_assert(TW % PW == 0 && TH % PH == 0 && NP <= 32 && 32 % NP == 0 && 32 % PW == 0 && SPL >= 1 &&
                       (32 / PW) * SPL == PH,
                   "patch layout");
 };
@@ -172,7 +175,7 @@ __device__ __forceinline__ float list_coord(int w) {
 template <int PW, int PH>
 __global__ __launch_bounds__(32 * VWARPS, VLayout<PW, PH>::MINB) void k_voronoi(Pools P, StepTable T) {
     using LY = VLayout<PW, PH>;
-    constexpr int NPX = LY::NPX, NP = LY::NP, SPL = LY::SPL;
+    constexpr int NPX = LY::NPX, NP = LY::NP, SPL = LY::SPL, LPP = LY::LPP;
     pdl_enter();
     __shared__ float2 s_cf[VWARPS][WSCAN];
     __shared__ int s_id[VWARPS][WSCAN];
@@ -216,10 +219,10 @@ __global__ __launch_bounds__(32 * VWARPS, VLayout<PW, PH>::MINB) void k_voronoi(
     const int* bid = P.bid[S.slot ^ 1] + D.comp_off;
     float2* cfs = s_cf[warp];
     int* ids = s_id[warp];
-    // this lane's patch (lanes past the last patch repeat it and are not counted)
-    const int pp = lane < NP ? lane : NP - 1;
+    // this lane's patch; the LPP lanes of a patch split the scanned centres
+    const int pp = lane % NP, sub = lane / NP;
     const int ppx = PW * (pp % NPX), ppy = PH * (pp / NPX);
-    const bool pvalid = lane < NP && ppx < ncols && ppy < nrows;
+    const bool pvalid = ppx < ncols && ppy < nrows;
     const int pxlo = Q * ppx, pxhi = Q * max(min(ppx + PW, ncols) - 1, ppx);
     const int pylo = Q * ppy, pyhi = Q * max(min(ppy + PH, nrows) - 1, ppy);
     // patch centre and half extent (multiples of Q/2: exact in float32); the
@@ -283,12 +286,14 @@ __global__ __launch_bounds__(32 * VWARPS, VLayout<PW, PH>::MINB) void k_voronoi(
         __syncwarp();
         // this lane's patch bound over the centres of this round
         const int ne = min(n, WSCAN);
-        for (int j = nb; j < ne; ++j) {
+        for (int j = nb + sub; j < ne; j += LPP) {
             const float2 c = cfs[j];
             const float tx = fminf(__fadd_ru(fabsf(c.x - mxf), hwxf), hMXf);
             const float ty = fminf(__fadd_ru(fabsf(c.y - myf), hwyf), hMYf);
             Up = fminf(Up, __fadd_ru(__fmul_ru(tx, tx), __fmul_ru(ty, ty)));
         }
+#pragma unroll
+        for (int o = NP; o < 32; o <<= 1) Up = fminf(Up, __shfl_xor_sync(0xffffffffu, Up, o));
         nb = ne;
         float Umax = pvalid ? Up : 0.f;
 #pragma unroll
@@ -321,19 +326,42 @@ __global__ __launch_bounds__(32 * VWARPS, VLayout<PW, PH>::MINB) void k_voronoi(
 
     if (!bad) {
         // ---- 2. kept list of this lane's patch ----
-        if (lane < NP) {
-            int* kl = s_kept[warp][lane];
-            int nk = 0;
-            for (int j = 0; j < n; ++j) {
-                const float2 c = cfs[j];
-                // exact: integers below 2^23
-                const float exf = fmaxf(fabsf(c.x - mxf) - hwxf, 0.f), eyf = fmaxf(fabsf(c.y - myf) - hwyf, 0.f);
-                if (__fmaf_rd(exf, exf, __fmul_rd(eyf, eyf)) <= Up) {
-                    if (nk < KMAX) kl[nk] = j;
-                    ++nk;
+        {
+            int* kl = s_kept[warp][pp];
+            int nk = 0;   // the same in every lane of the patch
+            if constexpr (LPP == 1) {
+                for (int j = 0; j < n; ++j) {
+                    const float2 c = cfs[j];
+                    // exact: integers below 2^23
+                    const float exf = fmaxf(fabsf(c.x - mxf) - hwxf, 0.f), eyf = fmaxf(fabsf(c.y - myf) - hwyf, 0.f);
+                    if (__fmaf_rd(exf, exf, __fmul_rd(eyf, eyf)) <= Up) {
+                        if (nk < KMAX) kl[nk] = j;
+                        ++nk;
+                    }
+                }
+            } else {
+                // lanes p, p + NP, ... take centres in turn; each keeps its
+                // place among the patch's kept centres of the round by ballot
+                unsigned same = 0;
+#pragma unroll
+                for (int k = 0; k < LPP; ++k) same |= 1u << (pp + k * NP);
+                const unsigned below = same & ((1u << lane) - 1u);
+                for (int j0 = 0; j0 < n; j0 += LPP) {
+                    const int j = j0 + sub;
+                    bool keep = false;
+                    if (j < n) {
+                        const float2 c = cfs[j];
+                        const float exf = fmaxf(fabsf(c.x - mxf) - hwxf, 0.f),
+                                    eyf = fmaxf(fabsf(c.y - myf) - hwyf, 0.f);
+                        keep = __fmaf_rd(exf, exf, __fmul_rd(eyf, eyf)) <= Up;
+                    }
+                    const unsigned kb = __ballot_sync(0xffffffffu, keep);
+                    const int at = nk + __popc(kb & below);
+                    if (keep && at < KMAX) kl[at] = j;
+                    nk += __popc(kb & same);
                 }
             }
-            s_nk[warp][lane] = nk;
+            if (sub == 0) s_nk[warp][pp] = nk;
         }
         __syncwarp();
         // ---- 3. nearest kept centre for every site, patch by patch ----
