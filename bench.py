@@ -58,12 +58,12 @@ METRIC_BYTES_PER_SITE = 16.0
 # roofline.traffic. The owner stage's entry depends on its patch layout
 # (VD_PATCH_*); a stage or layout not captured, or whose kernels changed since
 # the capture, reports null.
-TRAFFIC_BYTES_PER_SITE = {0: 4.935, 2: 2.842, 3: {0: 2.873}, 4: 4.342}
+TRAFFIC_BYTES_PER_SITE = {0: 4.935, 2: 2.842, 3: {0: 2.866}, 4: 4.342}
 
 # Issue-slot use (smsp__issue_active, % of peak) of the same kernels in the
 # same capture: the kernels are bound by instruction issue or latency, not by
 # DRAM, and this says how close to the issue limit they run.
-ISSUE_ACTIVE_PCT = {0: 48.8, 2: 32.0, 3: {0: 69.8}, 4: 41.1}
+ISSUE_ACTIVE_PCT = {0: 48.8, 2: 32.0, 3: {0: 73.2}, 4: 41.1}
 
 
 def per_stage(table, stage, patch):
@@ -74,12 +74,12 @@ def per_stage(table, stage, patch):
 def workload(name: str, n_frames: int | None):
     if name == "c1":
         n = n_frames or 64
-        return "1024x1024 smoothed noise sigma 4, 64 frames (shear 0.005 + N(0,0.01))", list(inputs.workload_c1(1, n))
+        return f"1024x1024 smoothed noise sigma 4, {n} frames (shear 0.005 + N(0,0.01))", list(inputs.workload_c1(1, n))
     if name == "c0":
         return "128x128 smoothed noise sigma 3, 2 frames", inputs.workload_c0(1)
     if name == "c2":
         n = n_frames or 16
-        return "4096x4096 RSA droplets r~U[8,12], 16 frames (shear 1e-3 + N(0,0.3))", \
+        return f"4096x4096 RSA droplets r~U[8,12], {n} frames (shear 1e-3 + N(0,0.3))", \
             [F for F, _ in inputs.workload_c2(1, n)]
     raise SystemExit(f"unknown workload {name}")
 
@@ -416,7 +416,7 @@ def run_ours(args, world, rank, local):
     e2e_dt = max_over_ranks(time.perf_counter() - t0, world)
     e2e = {"value": world * sites_per_push * e2e_steps / e2e_dt / 1e9, "unit": UNIT,
            "h2d_bytes_per_step": 4 * sites_per_push, "d2h_bytes_per_step": int(d2h / e2e_steps),
-           "step": "one push of the 64-frame sequence (host frames in, every frame's results out)",
+           "step": f"one push of the {n}-frame sequence (host frames in, every frame's results out)",
            "path": "vd_batch_stage_host (double-buffered, copy stream) + vd_batch_push_staged + "
                    "vd_batch_get_changes_all for every step"}
     seq.close()

@@ -49,7 +49,8 @@ enum {
     VD_ERR_CUDA = -4,      /* a CUDA runtime call failed */
     VD_ERR_TIMEOUT = -5,   /* a bounded device-side wait gave up */
     VD_ERR_STATE = -6,     /* call out of order (e.g. results before any frame) */
-    VD_ERR_UNSUPPORTED = -7
+    VD_ERR_UNSUPPORTED = -7,
+    VD_ERR_BOUNDS = -8     /* checked build only: an index check failed (the access was skipped) */
 };
 
 /* Polarity of the spin variable of Section 3.1: a site is in a bubble when
@@ -242,6 +243,24 @@ const char* vd_stage_name(int32_t stage);
  * VD_ERR_INVALID, VD_ERR_CUDA. */
 vd_status vd_debug_hold_scan_flag(vd_ctx* ctx, int32_t kind, int64_t tile, int32_t spin_limit);
 
+/* Checked build. The same sources compiled with -DVD_CHECKED give
+ * libvd_checked.so (built beside libvd.so), which tests the index of every
+ * scatter access whose index is computed from data (piece ids, run slots,
+ * bucket cells and positions, overlap and link list positions, queue
+ * positions, owner writes, CSR columns, flip lists, scan offsets) against
+ * its array before the access. A failed test skips the access, records the
+ * check's id and the index (the first of the step is kept) and makes every
+ * getter of that step return VD_ERR_BOUNDS. It stands in for a memory
+ * checker where none can run. In the regular build the tests compile away.
+ * vd_debug_check_info synchronises the stream and returns *checked = 1 in
+ * the checked build (0 otherwise), the id of the first failed check of the
+ * last step (0 = none; ids 1..20 name the checked accesses) and its index.
+ * vd_debug_force_check(id) makes check `id` fail from the next push on,
+ * without any access (the test of the reporting path); 0 turns it off; no
+ * effect in the regular build. Errors: VD_ERR_INVALID, VD_ERR_CUDA. */
+vd_status vd_debug_check_info(vd_ctx* ctx, int32_t* checked, int32_t* first_check, int64_t* index);
+vd_status vd_debug_force_check(vd_ctx* ctx, int32_t id);
+
 /* Release all device state of the context (waits for its stream first). */
 vd_status vd_destroy(vd_ctx* ctx);
 
@@ -280,6 +299,9 @@ const char* vd_status_string(vd_status s);
  * into a CUDA graph and replayed.
  * ------------------------------------------------------------------------- */
 typedef struct vd_batch vd_batch;
+/* the checked-build calls (see vd_debug_check_info) for a batch */
+vd_status vd_batch_debug_check_info(vd_batch* b, int32_t* checked, int32_t* first_check, int64_t* index);
+vd_status vd_batch_debug_force_check(vd_batch* b, int32_t id);
 
 /* `cfgs[i]` describes instance i; all share cfgs[0].stream. */
 vd_status vd_batch_create(const vd_config* cfgs, int32_t n, vd_batch** out);

@@ -1,7 +1,9 @@
 """Build libvd.so in-tree with nvcc for sm_103a (GB300).
 
 Each .cu file in csrc/ is compiled in parallel to an object, then linked into
-paper_1607_00908_gb300/libvd.so. Run ``python -m paper_1607_00908_gb300.build``.
+paper_1607_00908_gb300/libvd.so; the same sources compiled with -DVD_CHECKED
+(index checks before every data-dependent scatter access, include/vd.h) give
+libvd_checked.so beside it. Run ``python -m paper_1607_00908_gb300.build``.
 """
 from __future__ import annotations
 
@@ -17,6 +19,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libvd.so")
+LIB_CHECKED = os.path.join(HERE, "libvd_checked.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC]
@@ -33,8 +36,8 @@ def sources():
     return sorted(os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".cu"))
 
 
-def _compile(src: str, extra) -> str:
-    obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
+def _compile(src: str, extra, tag: str = "") -> str:
+    obj = os.path.join(BUILD, os.path.basename(src)[:-3] + tag + ".o")
     cmd = [nvcc(), *ARCH, *FLAGS, *extra, "-c", src, "-o", obj]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
@@ -44,20 +47,30 @@ def _compile(src: str, extra) -> str:
     return obj
 
 
-def build(verbose: bool = False, extra=()) -> str:
-    """Compile every CUDA source and link libvd.so; returns the library path."""
-    os.makedirs(BUILD, exist_ok=True)
-    srcs = sources()
-    with cf.ThreadPoolExecutor(max_workers=min(8, len(srcs))) as ex:
-        objs = list(ex.map(lambda s: _compile(s, list(extra)), srcs))
-    tmp = LIB + ".tmp"
+def _link(objs, lib: str) -> None:
+    tmp = lib + ".tmp"
     cmd = [nvcc(), *ARCH, "-shared", "-o", tmp, *objs, "-lcudart"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, LIB)
+    os.replace(tmp, lib)
+
+
+def build(verbose: bool = False, extra=(), checked: bool = True) -> str:
+    """Compile every CUDA source and link libvd.so (and libvd_checked.so);
+    returns the path of libvd.so."""
+    os.makedirs(BUILD, exist_ok=True)
+    srcs = sources()
+    jobs = [(s, list(extra), "") for s in srcs]
+    if checked:
+        jobs += [(s, list(extra) + ["-DVD_CHECKED"], "_chk") for s in srcs]
+    with cf.ThreadPoolExecutor(max_workers=min(16, os.cpu_count() or 8, len(jobs))) as ex:
+        objs = list(ex.map(lambda j: _compile(*j), jobs))
+    _link(objs[: len(srcs)], LIB)
+    if checked:
+        _link(objs[len(srcs):], LIB_CHECKED)
     if verbose:
-        print(f"built {LIB}")
+        print(f"built {LIB}" + (f" and {LIB_CHECKED}" if checked else ""))
     return LIB
 
 

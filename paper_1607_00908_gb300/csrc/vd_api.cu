@@ -576,6 +576,7 @@ vd_status copy_from_host(void* dst, const void* src, size_t bytes) {
 }
 
 vd_status err_status(const InstState& st) {
+    if (st.err & ERR_BOUNDS) return VD_ERR_BOUNDS;
     if (st.err & ERR_TIMEOUT) return VD_ERR_TIMEOUT;
     if (st.err) return VD_ERR_CAPACITY;
     return VD_OK;
@@ -1078,6 +1079,7 @@ const char* vd_status_string(vd_status s) {
         case VD_ERR_TIMEOUT: return "bounded device wait expired";
         case VD_ERR_STATE: return "call out of order";
         case VD_ERR_UNSUPPORTED: return "unsupported";
+        case VD_ERR_BOUNDS: return "an index check of the checked build failed";
         default: return "unknown status";
     }
 }
@@ -1184,6 +1186,47 @@ vd_status vd_debug_hold_scan_flag(vd_ctx* ctx, int32_t kind, int64_t tile, int32
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->s);
     return cuda_status(e);
 }
+
+namespace {
+// the checked build's record of the last step (Globals::chk_id, chk_index)
+vd_status check_info(vd_batch* b, int32_t* checked, int32_t* first_check, int64_t* index) {
+    if (!b || !checked || !first_check || !index) return VD_ERR_INVALID;
+    struct {
+        int id, dbg;
+        long long index;
+    } v = {0, 0, 0};
+    static_assert(offsetof(Globals, dbg_chk) == offsetof(Globals, chk_id) + sizeof(int) &&
+                      offsetof(Globals, chk_index) == offsetof(Globals, chk_id) + 2 * sizeof(int),
+                  "check fields of Globals must be contiguous");
+    cudaError_t e = cudaStreamSynchronize(b->s);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(&v, reinterpret_cast<char*>(b->P.g) + offsetof(Globals, chk_id), sizeof(v),
+                       cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_status(e);
+    *checked = VD_IS_CHECKED ? 1 : 0;
+    *first_check = v.id;
+    *index = v.index;
+    return VD_OK;
+}
+
+vd_status force_check(vd_batch* b, int32_t id) {
+    if (!b || id < 0 || id >= CHK_COUNT) return VD_ERR_INVALID;
+    const int v = id;
+    cudaError_t e = cudaMemcpyAsync(reinterpret_cast<char*>(b->P.g) + offsetof(Globals, dbg_chk), &v, sizeof(v),
+                                    cudaMemcpyHostToDevice, b->s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->s);
+    return cuda_status(e);
+}
+}  // namespace
+
+vd_status vd_debug_check_info(vd_ctx* ctx, int32_t* checked, int32_t* first_check, int64_t* index) {
+    return ctx ? check_info(ctx->b, checked, first_check, index) : VD_ERR_INVALID;
+}
+vd_status vd_debug_force_check(vd_ctx* ctx, int32_t id) { return ctx ? force_check(ctx->b, id) : VD_ERR_INVALID; }
+vd_status vd_batch_debug_check_info(vd_batch* b, int32_t* checked, int32_t* first_check, int64_t* index) {
+    return check_info(b, checked, first_check, index);
+}
+vd_status vd_batch_debug_force_check(vd_batch* b, int32_t id) { return force_check(b, id); }
 
 vd_status vd_batch_set_tuning(vd_batch* b, const vd_tuning* t) {
     if (!b || !t) return VD_ERR_INVALID;

@@ -253,104 +253,16 @@ __device__ __forceinline__ unsigned long long threshold_row(const float* f, int 
     return m;
 }
 
-// Bulk staging of the field for the threshold: the tile is read in two
-// halves of 32 rows x 32 floats; every lane copies its row's 128 bytes with
-// one cp.async.bulk into a padded shared row (stride 144 bytes, so the 8 lanes
-// of a 16-byte shared load phase hit distinct banks), completing on the
-// warp's mbarrier. The staging rows share memory with the union-find arrays,
-// which are written only after both halves have been read.
-constexpr int STG = 36;                          // staged row stride in floats
-constexpr int MBAR_SPIN = 1 << 22;               // bounded wait on the warp's mbarrier
-struct CclSmem {
-    union {
-        UfSmem uf;
-        float stage[TH][STG];
-    };
-};
-static_assert(sizeof(float) * TH * STG <= sizeof(CclSmem), "staging rows");
-
-__device__ __forceinline__ unsigned smem_u32(const void* p) {
-    return (unsigned)__cvta_generic_to_shared(p);
-}
-
-// true when the phase of parity `par` of the mbarrier has completed, false
-// after `limit` polls
-__device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned par, int limit) {
-    for (int i = 0; i < limit; ++i) {
-        unsigned ok;
-        asm volatile(
-            "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
-            : "=r"(ok)
-            : "r"(bar), "r"(par)
-            : "memory");
-        if (ok) return true;
-    }
-    return false;
-}
-
-// Threshold of the warp's tile (full width, rows y0 + lane < y_end) through
-// shared memory; returns lane's row mask, or false (flagged) when a wait gave
-// up, in which case the caller reads the rows directly.
-__device__ bool threshold_bulk(float (*stage)[STG], unsigned long long* bar_p, const float* field, long long pitch,
-                               int x0, int y0, int y_end, float thr, int pol, int lane, unsigned long long* out) {
-    const unsigned bar = smem_u32(bar_p);
-    const int nrows = min(TH, y_end - y0);
-    if (lane == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
-    __syncwarp();
-    unsigned long long m = 0;
-    bool ok = true;
-    const float* src = field + (long long)(y0 + lane) * pitch + x0;
-    for (int h = 0; h < 2; ++h) {
-        if (lane == 0)
-            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(nrows * 128)
-                         : "memory");
-        __syncwarp();
-        if (lane < nrows)
-            asm volatile(
-                "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], 128, [%2];" ::"r"(
-                    smem_u32(&stage[lane][0])),
-                "l"(src + 32 * h), "r"(bar)
-                : "memory");
-        bool done = mbar_wait(bar, (unsigned)h, MBAR_SPIN);
-        if (!done) {
-            ok = false;
-            done = mbar_wait(bar, (unsigned)h, MBAR_SPIN);   // let the copies in flight land
-        }
-        if (__any_sync(0xffffffffu, !done)) return false;
-        if (lane < nrows) {
-            const float4* r = reinterpret_cast<const float4*>(&stage[lane][0]);
-            unsigned bits = 0;
-#pragma unroll
-            for (int i = 0; i < 8; ++i) {
-                const float4 v = r[i];
-                bits |= ((unsigned)is_fg(v.x, thr, pol) | ((unsigned)is_fg(v.y, thr, pol) << 1) |
-                         ((unsigned)is_fg(v.z, thr, pol) << 2) | ((unsigned)is_fg(v.w, thr, pol) << 3))
-                        << (4 * i);
-            }
-            m |= (unsigned long long)bits << (32 * h);
-        }
-        __syncwarp();
-        // the reads above come before the next asynchronous writes of the rows
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    }
-    *out = m;
-    return __all_sync(0xffffffffu, ok);
-}
-
 // ---------------------------------------------------------------------------
 // Pass A: union-find over runs + pieces + borders (one warp per tile)
 // ---------------------------------------------------------------------------
 __global__ __launch_bounds__(32 * CCL_WARPS, 8) void k_ccl_tiles(Pools P, StepTable T) {
     pdl_enter();
-    __shared__ __align__(16) CclSmem s_tile[CCL_WARPS];
-    __shared__ __align__(8) unsigned long long s_bar[CCL_WARPS];
+    __shared__ UfSmem s_tile[CCL_WARPS];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int b = blockIdx.x * CCL_WARPS + w;
     if (b >= T.tileA_pre[T.n_act]) return;
-    UfSmem& TS = s_tile[w].uf;
+    UfSmem& TS = s_tile[w];
     const int a = seg_of_int(T.tileA_pre, T.n_act, b);
     const int inst = T.act[a];
     const InstDesc& D = P.desc[inst];
@@ -365,24 +277,12 @@ __global__ __launch_bounds__(32 * CCL_WARPS, 8) void k_ccl_tiles(Pools P, StepTa
     unsigned long long my_m = 0;
     {
         const int y = y0 + lane;
-        // the field covers the domain only (a bounded axis runs with twice
-        // its length; the second half is never a bubble)
-        const bool full = x0 + TW <= D.uLx && y0 < D.uLy &&
-                          ((reinterpret_cast<uintptr_t>(S.field) | (uintptr_t)(S.pitch * 4)) & 15u) == 0;
-        bool staged = false;
-        if (full) {
-            staged = threshold_bulk(s_tile[w].stage, &s_bar[w], S.field, S.pitch, x0, y0, D.uLy, D.thr, D.pol, lane,
-                                    &my_m);
-            if (!staged && lane == 0) {
-                atomicOr(&P.g->err, ERR_TIMEOUT);
-                atomicOr(&P.st[inst].err, ERR_TIMEOUT);
-            }
-        }
         if (y < Ly) {
             const int n = min(TW, Lx - x0);
+            // the field covers the domain only (a bounded axis runs with twice
+            // its length; the second half is never a bubble)
             const int nu = min(n, D.uLx - x0);
-            if (!staged && y < D.uLy && nu > 0)
-                my_m = threshold_row(S.field + (long long)y * S.pitch + x0, nu, D.thr, D.pol);
+            if (y < D.uLy && nu > 0) my_m = threshold_row(S.field + (long long)y * S.pitch + x0, nu, D.thr, D.pol);
             unsigned* row = P.fgbits[S.slot ^ 1] + D.word_off + (long long)y * D.wpr + (x0 >> 5);
             if (D.masked) {   // obstacle sites are never in a bubble
                 const unsigned* ob = P.obst + D.word_off + (long long)y * D.wpr + (x0 >> 5);
@@ -425,7 +325,7 @@ __global__ __launch_bounds__(32 * CCL_WARPS, 8) void k_ccl_tiles(Pools P, StepTa
             rq &= rq - 1;
             const int id = SW(lane * 32 + j);
             int pid = -1;
-            if (pbase >= 0) {
+            if (pbase >= 0 && vd_in(P, CHK_TILE_PIECES, pbase + k, P.piece_cap)) {
                 pid = pbase + k;
                 P.p_q[pid] = (y0 + lane) * Lx + x0 + TS.col[id];
                 P.p_inst[pid] = inst;
@@ -461,7 +361,7 @@ __global__ __launch_bounds__(32 * CCL_WARPS, 8) void k_ccl_tiles(Pools P, StepTa
                 pid = run_piece(TS, lane * 32 + j, &root);
                 sv = len * (lane - (root >> 5));
                 su = len * (c - TS.col[SW(root)]) + (len * (len - 1)) / 2;
-                rp[j] = pid;
+                if (vd_in(P, CHK_RUN_PIECE, j, 32)) rp[j] = pid;
             }
             const unsigned grp = __match_any_sync(0xffffffffu, pid);
             const int gn = __reduce_add_sync(grp, len);
@@ -521,6 +421,7 @@ __device__ __forceinline__ int pfind_ro(const int* par, int x) {
 }
 
 __device__ __forceinline__ void punion(const Pools& P, int a, int b) {
+    if (!vd_in(P, CHK_MERGE_PARENT, a, P.piece_cap) || !vd_in(P, CHK_MERGE_PARENT, b, P.piece_cap)) return;
     for (;;) {
         a = pfind(P.p_parent, a);
         b = pfind(P.p_parent, b);
@@ -619,6 +520,7 @@ __global__ void k_ccl_flatten(Pools P) {
             const InstDesc& D = P.desc[inst];
             const int q = P.p_q[pid];
             const int y = q / D.Lx, x = q - y * D.Lx;
+            if (!vd_in(P, CHK_FGBITS, q, (long long)D.Lx * D.Ly)) continue;
             atomicOr(&P.rootbits[D.word_off + (long long)y * D.wpr + (x >> 5)], 1u << (x & 31));
             atomicAdd(&P.rgcnt[D.grp_off + (long long)y * D.gpr + (x >> 5) / RGW], 1);
             warp_add(&P.st[inst].K, 1);
@@ -645,7 +547,7 @@ __global__ void k_comp_accum(Pools P) {
             for (int k = 0; k < RGW - 1; ++k)   // independent loads, issued together
                 if (w0 + k < wq) c += __popc(row[w0 + k]);
             P.p_comp[pid] = c;
-            if (c < D.comp_cap) P.comp_root[D.comp_off + c] = pid;
+            if (c < D.comp_cap && vd_in(P, CHK_COMP_ID, c, D.comp_cap)) P.comp_root[D.comp_off + c] = pid;
         }
         const int qr = P.p_q[r];
         const int yr = qr / D.Lx, xr = qr - yr * D.Lx;
@@ -663,7 +565,7 @@ __global__ void k_comp_accum(Pools P) {
             atomicAdd((unsigned long long*)&P.p_accy[r], (unsigned long long)(nn * dy + P.p_sv[pid]));
         } else {
             const int w = warp_fetch_inc(&P.g->n_wide);
-            P.wide[w] = pid;
+            if (vd_in(P, CHK_WIDE, w, P.piece_cap)) P.wide[w] = pid;
         }
     }
 }
@@ -757,7 +659,8 @@ __global__ void k_comp_final(Pools P) {
         cy %= MY; if (cy < 0) cy += MY;
         P.cq[S.slot ^ 1][D.comp_off + c] = make_int2((int)cx, (int)cy);
         const int bx = (int)(cx / Q) / S.B, by = (int)(cy / Q) / S.B;
-        atomicAdd(&P.bcnt[D.bucket_off + (long long)by * S.nbx + bx], 1);
+        if (vd_in(P, CHK_BUCKET, (long long)by * S.nbx + bx, (long long)S.nbx * S.nby))
+            atomicAdd(&P.bcnt[D.bucket_off + (long long)by * S.nbx + bx], 1);
     }
 }
 
@@ -775,7 +678,9 @@ __global__ void k_bucket_scatter(Pools P) {
         const int now = S.slot ^ 1;
         const int2 v = P.cq[now][D.comp_off + c];
         const long long bk = (long long)((v.y / Q) / S.B) * S.nbx + (v.x / Q) / S.B;
+        if (!vd_in(P, CHK_BUCKET, bk, (long long)S.nbx * S.nby)) continue;
         const int pos = P.boff[now][D.bucket_off + bk] + atomicSub(&P.bcnt[D.bucket_off + bk], 1) - 1;
+        if (!vd_in(P, CHK_BUCKET, pos, D.comp_cap)) continue;
         P.bcq[now][D.comp_off + pos] = v;
         P.bid[now][D.comp_off + pos] = c;
     }
@@ -827,10 +732,11 @@ __global__ __launch_bounds__(32 * LBL_WARPS, 10) void k_run_labels(Pools P, Step
 #pragma unroll
         for (int k = 0; k < 4; ++k) pid[k] = j0 + k < nr ? P.rp[rbase + j0 + k] : -1;
 #pragma unroll
-        for (int k = 0; k < 4; ++k) l[k] = pid[k] >= 0 ? P.p_comp[pid[k]] : -1;
+        for (int k = 0; k < 4; ++k)
+            l[k] = (pid[k] >= 0 && vd_in(P, CHK_RUN_LABEL, pid[k], P.piece_cap)) ? P.p_comp[pid[k]] : -1;
 #pragma unroll
         for (int k = 0; k < 4; ++k)
-            if (j0 + k < nr) {
+            if (j0 + k < nr && vd_in(P, CHK_RUN_LABEL, j0 + k, 32)) {
                 P.rl[now][rbase + j0 + k] = l[k];
                 lab[SW(lane * 32 + j0 + k)] = l[k];
             }
@@ -895,7 +801,7 @@ __global__ __launch_bounds__(32 * LBL_WARPS, 10) void k_run_labels(Pools P, Step
         base = __shfl_sync(0xffffffffu, base, 0);
         if (has) {
             const int pos = base + __popc(mk & ((1u << lane) - 1u));
-            if (pos < D.ovl_cap) {
+            if (pos < D.ovl_cap && vd_in(P, CHK_OVL_APPEND, pos, D.ovl_cap)) {
                 P.oapp_key[D.ovl_off + pos] = key;
                 P.oapp_cnt[D.ovl_off + pos] = scnt[kb + lane];
             } else {

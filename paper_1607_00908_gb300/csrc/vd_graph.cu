@@ -42,6 +42,8 @@ __global__ void k_step_begin(Pools P, StepTable T) {
         P.g->n_pieces = 0;
         P.g->n_wide = 0;
         P.g->err = 0;   // errors of the previous step stay in its instances' states
+        P.g->chk_id = 0;
+        P.g->chk_index = 0;
         P.g->scan_step = (P.g->scan_step + 1) & 0x07FFFFFFu;   // new tags for this step's scans
         for (int k = 0; k < 8; ++k) P.g->scan_ticket[k] = 0;
     }
@@ -168,8 +170,8 @@ __global__ void k_csr_scatter(Pools P, StepTable T) {
         const int cap = 2 * D.edge_cap;
         const int plo = ro[lo] + atomicSub(&P.deg[D.comp_off + lo], 1) - 1;
         const int phi_ = ro[hi] + atomicSub(&P.deg[D.comp_off + hi], 1) - 1;
-        if (plo < cap) cl[plo] = hi;
-        if (phi_ < cap) cl[phi_] = lo;
+        if (plo < cap && vd_in(P, CHK_CSR, plo, cap)) cl[plo] = hi;
+        if (phi_ < cap && vd_in(P, CHK_CSR, phi_, cap)) cl[phi_] = lo;
     });
 }
 
@@ -259,6 +261,7 @@ __global__ void k_match_best(Pools P, StepTable T) {
         V[slot] = 0;
         const int p = (int)(key >> 32), n = (int)(key & 0xffffffffu);
         if (p < 0 || n < 0 || p >= D.comp_cap || n >= D.comp_cap) return;   // only after an overflow
+        if (!vd_in(P, CHK_MATCH, j, D.ovl_cap)) return;
         atomicMax(&P.best_n[D.comp_off + p], pack_best(cnt, n));
         atomicMax(&P.best_p[D.comp_off + n], pack_best(cnt, p));
     });
@@ -431,7 +434,7 @@ __device__ __forceinline__ void merge_row(const Pools& P, const InstDesc& D, int
             ++i;
             ++j;
         } else if (vt < vn) {   // only in the past: breaking
-            if (WRITE) {
+            if (WRITE && vd_in(P, CHK_FLIPS, ob + nb, D.edge_cap)) {
                 const long long o = D.edge_off + ob + nb;
                 P.brk[o] = edge_key(a, vt);
                 P.brk_prev[o] = edge_key(ia, P.inv[co + vt]);
@@ -441,7 +444,7 @@ __device__ __forceinline__ void merge_row(const Pools& P, const InstDesc& D, int
             ++nb;
             ++j;
         } else {                // only now: arising
-            if (WRITE) {
+            if (WRITE && vd_in(P, CHK_FLIPS, oa + na, D.edge_cap)) {
                 P.ari[D.edge_off + oa + na] = edge_key(a, vn);
                 P.active[co + a] = 1;
                 P.active[co + vn] = 1;

@@ -52,6 +52,7 @@ enum : int {
     ERR_TIMEOUT = 16,       // bounded device wait expired
     ERR_FLIP_CAP = 32,
     ERR_PREV = 64,          // the past frame (same step) had an error
+    ERR_BOUNDS = 128,       // an index check of the checked build failed
 };
 
 // bits of the per-bubble active flags: bit 0 is the local trigger (an end of a
@@ -152,6 +153,11 @@ struct Globals {
     int dbg_kind;
     int dbg_spin;
     long long dbg_tile;
+    // checked build: the first failed index check of the step (id, index;
+    // id 0: none) and the test hook that makes check dbg_chk fail
+    int chk_id;
+    int dbg_chk;
+    long long chk_index;
 };
 
 // ---------------------------------------------------------------------------
@@ -463,6 +469,58 @@ struct Launch {
 
 // patch layouts of the owner kernel (PW x PH sites per patch of a 64 x 32 tile)
 enum VPatch : int { VPATCH_8x8 = 0, VPATCH_16x8 = 1, VPATCH_32x8 = 2, VPATCH_16x16 = 3, VPATCH_COUNT = 4 };
+
+// ---------------------------------------------------------------------------
+// Checked build (compiled with -DVD_CHECKED into libvd_checked.so): before a
+// scatter access whose index is computed from data, vd_in(P, id, i, n) tests
+// 0 <= i < n. A failing test records the check's id and the index in
+// Globals (the first one of the step is kept), sets ERR_BOUNDS for the step
+// (every instance's getters then return VD_ERR_BOUNDS) and returns false, and
+// the caller skips the access. The test hook Globals::dbg_chk makes check
+// `id` fail without touching memory, to exercise the reporting. In the
+// regular build vd_in is the constant true and the checks compile away.
+// ---------------------------------------------------------------------------
+#ifdef VD_CHECKED
+constexpr bool VD_IS_CHECKED = true;
+static __device__ __noinline__ bool vd_fail(const Pools& P, int id, long long i) {
+    if (atomicCAS(&P.g->chk_id, 0, id) == 0) P.g->chk_index = i;
+    atomicOr(&P.g->err, ERR_BOUNDS);
+    return false;
+}
+__device__ __forceinline__ bool vd_in(const Pools& P, int id, long long i, long long n) {
+    if (i >= 0 && i < n && *(volatile int*)&P.g->dbg_chk != id) return true;
+    return vd_fail(P, id, i);
+}
+#else
+constexpr bool VD_IS_CHECKED = false;
+__device__ __forceinline__ bool vd_in(const Pools&, int, long long, long long) { return true; }
+#endif
+
+// check ids, one per checked access (reported by vd_debug_check_info)
+enum CheckId : int {
+    CHK_NONE = 0,
+    CHK_TILE_PIECES = 1,     // k_ccl_tiles: piece records of a tile
+    CHK_RUN_PIECE = 2,       // k_ccl_tiles: run -> piece table
+    CHK_BORDER = 3,          // k_ccl_tiles: border piece ids
+    CHK_FGBITS = 4,          // k_ccl_tiles: foreground words
+    CHK_MERGE_PARENT = 5,    // k_ccl_merge: piece parents
+    CHK_COMP_ID = 6,         // k_comp_accum / k_comp_final: bubble ids
+    CHK_WIDE = 7,            // k_comp_accum: wide-piece list
+    CHK_BUCKET = 8,          // k_comp_final / k_bucket_scatter: bucket cells and positions
+    CHK_RUN_LABEL = 9,       // k_run_labels: run labels
+    CHK_OVL_APPEND = 10,     // k_run_labels: appended overlap pairs
+    CHK_OWNER = 11,          // k_voronoi: owner writes
+    CHK_SCAN_LIST = 12,      // k_voronoi: scanned-centre list
+    CHK_KEPT = 13,           // k_voronoi: kept lists
+    CHK_LINK_QUEUE = 14,     // k_links: queue of marked sites
+    CHK_LINK_LIST = 15,      // k_links / k_links_vertex: per-warp key list
+    CHK_EDGE_APPEND = 16,    // appended link keys
+    CHK_CSR = 17,            // k_csr_scatter: CSR columns
+    CHK_FLIPS = 18,          // k_flip_write: breaking / arising lists
+    CHK_SCAN_WRITE = 19,     // k_scan: offsets
+    CHK_MATCH = 20,          // k_match_best / k_match_phi: labels of matched pairs
+    CHK_COUNT = 21,
+};
 
 // Kernels of a step are launched with programmatic dependent launch, so the
 // launch of a kernel overlaps the end of the previous one; every step kernel

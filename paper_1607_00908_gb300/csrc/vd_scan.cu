@@ -344,7 +344,8 @@ __global__ __launch_bounds__(SCAN_THREADS) void k_scan(Pools P, StepTable T, int
                 // after a wait that gave up, `run` may fall short of the true
                 // prefix; the clamp keeps every offset inside its instance's range
                 const long long w = run - sel.mul * base[a];
-                scan_write(P, kind, inst, g - lo, (int)(w > 0 ? w : 0));
+                if (vd_in(P, CHK_SCAN_WRITE, g - lo, hi - lo))
+                    scan_write(P, kind, inst, g - lo, (int)(w > 0 ? w : 0));
                 run += v[i];
             }
         }

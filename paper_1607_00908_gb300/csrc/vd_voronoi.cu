@@ -335,7 +335,7 @@ __global__ __launch_bounds__(32 * VWARPS, VLayout<PW, PH>::MINB) void k_voronoi(
                     // exact: integers below 2^23
                     const float exf = fmaxf(fabsf(c.x - mxf) - hwxf, 0.f), eyf = fmaxf(fabsf(c.y - myf) - hwyf, 0.f);
                     if (__fmaf_rd(exf, exf, __fmul_rd(eyf, eyf)) <= Up) {
-                        if (nk < KMAX) kl[nk] = j;
+                        if (nk < KMAX && vd_in(P, CHK_KEPT, j, n)) kl[nk] = j;
                         ++nk;
                     }
                 }
@@ -357,7 +357,7 @@ __global__ __launch_bounds__(32 * VWARPS, VLayout<PW, PH>::MINB) void k_voronoi(
                     }
                     const unsigned kb = __ballot_sync(0xffffffffu, keep);
                     const int at = nk + __popc(kb & below);
-                    if (keep && at < KMAX) kl[at] = j;
+                    if (keep && at < KMAX && vd_in(P, CHK_KEPT, j, n)) kl[at] = j;
                     nk += __popc(kb & same);
                 }
             }
@@ -451,7 +451,9 @@ __global__ __launch_bounds__(32 * VWARPS, VLayout<PW, PH>::MINB) void k_voronoi(
                 }
 #pragma unroll
                 for (int k = 0; k < SPL; ++k)
-                    if (rb + k < ph) ownT[(pyo + rb + k) * Lx + sx] = o[k];
+                    if (rb + k < ph && vd_in(P, CHK_OWNER, (long long)(y0 + pyo + rb + k) * Lx + x0 + sx,
+                                             (long long)Lx * Ly))
+                        ownT[(pyo + rb + k) * Lx + sx] = o[k];
             }
         }
     } else {
@@ -514,6 +516,7 @@ constexpr int LS = VW + 4;      // staged row stride (rows start on 16 bytes)
 __device__ __forceinline__ void link_list_put(unsigned long long* list, int pos, int a, int b, const Pools& P,
                                               const InstDesc& D, int inst) {
     const bool ok = (a | b) >= 0;
+    if (!vd_in(P, CHK_LINK_LIST, pos, 1ll << 30)) return;
     if (pos < LSET) list[pos] = ok ? edge_key(a, b) : EMPTY_KEY;
     else if (ok) edge_global_insert(P, D, inst, edge_key(a, b));
 }
@@ -537,7 +540,7 @@ __device__ __forceinline__ void flush_link_list(const unsigned long long* list, 
         base = __shfl_sync(0xffffffffu, base, 0);
         if (has) {
             const int pos = base + __popc(m & lt);
-            if (pos < D.edge_cap) P.ekeys[D.edge_off + pos] = key;
+            if (pos < D.edge_cap && vd_in(P, CHK_EDGE_APPEND, pos, D.edge_cap)) P.ekeys[D.edge_off + pos] = key;
             else edge_global_insert(P, D, inst, key);   // list full: insert directly
         }
     }
@@ -644,7 +647,8 @@ __global__ __launch_bounds__(32 * LINK_WARPS) void k_links(Pools P, StepTable T)
         while (m) {
             const int r = __ffs(m) - 1;
             m &= m - 1;
-            q[pos++] = (unsigned short)(r * 32 + lane);
+            if (vd_in(P, CHK_LINK_QUEUE, pos, LQ)) q[pos] = (unsigned short)(r * 32 + lane);
+            ++pos;
         }
     }
     __syncwarp();

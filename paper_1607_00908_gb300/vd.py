@@ -15,7 +15,8 @@ import os
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libvd.so")
+# VD_LIB=checked selects the checked build (index checks, include/vd.h)
+LIB_PATH = os.path.join(_HERE, "libvd_checked.so" if os.environ.get("VD_LIB") == "checked" else "libvd.so")
 
 VD_OK = 0
 VD_ERR_INVALID = -1
@@ -25,6 +26,7 @@ VD_ERR_CUDA = -4
 VD_ERR_TIMEOUT = -5
 VD_ERR_STATE = -6
 VD_ERR_UNSUPPORTED = -7
+VD_ERR_BOUNDS = -8
 VD_ABOVE = 1
 VD_BELOW = -1
 # per-label flags of the `active` arrays (bit 0: local trigger; event classes above it)
@@ -43,7 +45,8 @@ EXPORTS = (
     "vd_push_frame_host", "vd_get_changes",
     "vd_get_counts", "vd_get_labels", "vd_get_centroids_q10", "vd_get_owners", "vd_get_edges",
     "vd_get_match", "vd_export_state", "vd_import_state", "vd_set_tuning", "vd_get_tuning",
-    "vd_debug_hold_scan_flag", "vd_set_timing", "vd_get_timing", "vd_stage_name", "vd_destroy", "vd_status_string",
+    "vd_debug_hold_scan_flag", "vd_debug_check_info", "vd_debug_force_check",
+    "vd_batch_debug_check_info", "vd_batch_debug_force_check", "vd_set_timing", "vd_get_timing", "vd_stage_name", "vd_destroy", "vd_status_string",
     "vd_batch_create", "vd_batch_create_sequence", "vd_batch_push", "vd_batch_push_host", "vd_batch_push_subset", "vd_batch_get_changes",
     "vd_batch_stage_host", "vd_batch_push_staged", "vd_batch_get_changes_all",
     "vd_batch_get_labels", "vd_batch_get_owners", "vd_batch_get_edges", "vd_batch_get_centroids_q10",
@@ -147,6 +150,10 @@ def lib():
         "vd_batch_export_state": [VP, I32, VP, I64, P(I64)],
         "vd_batch_import_state": [VP, I32, VP, I64],
         "vd_debug_hold_scan_flag": [VP, I32, I64, I32],
+        "vd_debug_check_info": [VP, P(I32), P(I32), P(I64)],
+        "vd_debug_force_check": [VP, I32],
+        "vd_batch_debug_check_info": [VP, P(I32), P(I32), P(I64)],
+        "vd_batch_debug_force_check": [VP, I32],
         "vd_set_tuning": [VP, P(vd_tuning)],
         "vd_get_tuning": [VP, P(vd_tuning)],
         "vd_batch_set_tuning": [VP, P(vd_tuning)],
@@ -451,6 +458,17 @@ class Detector(_Base):
         _check(lib().vd_debug_hold_scan_flag(self.h, int(kind), int(tile), int(spin_limit)),
                "vd_debug_hold_scan_flag")
 
+    def check_info(self) -> dict:
+        """Checked build: whether this library checks indices, and the first
+        failed check of the last push (id 0: none) with its index."""
+        c, i, x = C.c_int32(), C.c_int32(), C.c_int64()
+        _check(lib().vd_debug_check_info(self.h, C.byref(c), C.byref(i), C.byref(x)), "vd_debug_check_info")
+        return dict(checked=bool(c.value), first_check=i.value, index=x.value)
+
+    def force_check(self, check_id: int) -> None:
+        """Test support: check `check_id` fails from the next push on (0: off)."""
+        _check(lib().vd_debug_force_check(self.h, int(check_id)), "vd_debug_force_check")
+
     def set_timing(self, on: bool) -> None:
         _check(lib().vd_set_timing(self.h, int(bool(on))), "vd_set_timing")
 
@@ -560,6 +578,16 @@ class Batch(_Base):
         _check(lib().vd_batch_get_timing(self.h, ms, 16, C.byref(n), C.byref(kl), C.byref(nf)), "vd_batch_get_timing")
         names = [lib().vd_stage_name(i).decode() for i in range(n.value)]
         return list(ms[: n.value]), names, kl.value, nf.value
+
+    def check_info(self) -> dict:
+        """Checked build: see Detector.check_info."""
+        c, k, x = C.c_int32(), C.c_int32(), C.c_int64()
+        _check(lib().vd_batch_debug_check_info(self.h, C.byref(c), C.byref(k), C.byref(x)),
+               "vd_batch_debug_check_info")
+        return dict(checked=bool(c.value), first_check=k.value, index=x.value)
+
+    def force_check(self, check_id: int) -> None:
+        _check(lib().vd_batch_debug_force_check(self.h, int(check_id)), "vd_batch_debug_force_check")
 
     def set_tuning(self, voronoi_patch: int = 0, bucket_pct: int = 100, ring0: int = 9) -> None:
         """Launch shapes of the batch (vd_batch_set_tuning); results are identical for every setting."""
