@@ -714,7 +714,7 @@ vd_status get_array(vd_batch* b, int i, int which, void* out, int64_t cap, int64
     const void* src = nullptr;
     switch (which) {
         case 0:
-            launch_expand_labels(b->s, b->P, i, slot, b->P.lab_out, N);
+            launch_expand_labels(b->s, b->P, i, slot, b->P.lab_out, D.ntx * D.nty);
             src = b->P.lab_out;
             break;
         case 1: src = b->P.owners + D.site_off; break;
@@ -748,7 +748,7 @@ vd_status get_array(vd_batch* b, int i, int which, void* out, int64_t cap, int64
 // damaged or foreign blob is refused before anything reaches the device.
 // ---------------------------------------------------------------------------
 constexpr uint32_t STATE_MAGIC = 0x31534456u;   // "VDS1"
-constexpr uint32_t STATE_VERSION = 1;
+constexpr uint32_t STATE_VERSION = 2;   // 2: run tables packed per tile (row-major run order)
 
 struct StateHeader {
     uint32_t magic, version;

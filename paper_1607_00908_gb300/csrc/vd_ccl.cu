@@ -207,6 +207,23 @@ __device__ __forceinline__ unsigned warp_roots(const UfSmem& T, unsigned long lo
     return R;
 }
 
+// Run tables (piece id and bubble label of every run) are kept per labelling
+// tile in RUNS slots, packed in row-major order: the runs of row r start at
+// slot run_row_base(r) = the number of runs in rows 0..r-1 of the tile, so a
+// tile's runs fill a contiguous prefix of its slots (few DRAM sectors per
+// tile). Lane r of a warp holding the tile's row masks gets its row's base by
+// a prefix sum of the rows' run counts.
+__device__ __forceinline__ int run_row_base(int nr) {
+    const int lane = threadIdx.x & 31;
+    int inc = nr;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int v = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += v;
+    }
+    return inc - nr;
+}
+
 // row masks of a tile from stored foreground bits `fg` (lane r -> row r)
 __device__ __forceinline__ unsigned long long load_row_mask(const unsigned* fg, const InstDesc& D, int x0, int y0) {
     const int y = y0 + (threadIdx.x & 31);
@@ -348,7 +365,8 @@ __global__ __launch_bounds__(32 * CCL_WARPS, 8) void k_ccl_tiles(Pools P, StepTa
     //    site; runs of one piece are merged across the warp, then one atomic
     //    add per group
     {
-        int* rp = P.rp + (long long)(D.tile_off + t) * RUNS + lane * 32;
+        const int rrow = run_row_base(nr);
+        int* rp = P.rp + (long long)(D.tile_off + t) * RUNS + rrow;
         const int maxnr = __reduce_max_sync(0xffffffffu, nr);
         unsigned long long q = S0;
         for (int j = 0; j < maxnr; ++j) {
@@ -361,7 +379,7 @@ __global__ __launch_bounds__(32 * CCL_WARPS, 8) void k_ccl_tiles(Pools P, StepTa
                 pid = run_piece(TS, lane * 32 + j, &root);
                 sv = len * (lane - (root >> 5));
                 su = len * (c - TS.col[SW(root)]) + (len * (len - 1)) / 2;
-                if (vd_in(P, CHK_RUN_PIECE, j, 32)) rp[j] = pid;
+                if (vd_in(P, CHK_RUN_PIECE, rrow + j, RUNS)) rp[j] = pid;
             }
             const unsigned grp = __match_any_sync(0xffffffffu, pid);
             const int gn = __reduce_add_sync(grp, len);
@@ -723,10 +741,11 @@ __global__ __launch_bounds__(32 * LBL_WARPS, 10) void k_run_labels(Pools P, Step
     unsigned* scnt = s_cnt[w];
 
     // 1. bubble label of each run of this row
-    const long long rbase = (long long)(D.tile_off + t) * RUNS + lane * 32;
     const unsigned long long m = load_row_mask(P.fgbits[now], D, x0, y0);
     const unsigned long long Sn = run_starts(m);
     const int nr = __popcll(Sn);
+    const int rrow = run_row_base(nr);
+    const long long rbase = (long long)(D.tile_off + t) * RUNS + rrow;
     for (int j0 = 0; j0 < nr; j0 += 4) {   // four runs' loads in flight at once
         int pid[4], l[4];
 #pragma unroll
@@ -736,7 +755,7 @@ __global__ __launch_bounds__(32 * LBL_WARPS, 10) void k_run_labels(Pools P, Step
             l[k] = (pid[k] >= 0 && vd_in(P, CHK_RUN_LABEL, pid[k], P.piece_cap)) ? P.p_comp[pid[k]] : -1;
 #pragma unroll
         for (int k = 0; k < 4; ++k)
-            if (j0 + k < nr && vd_in(P, CHK_RUN_LABEL, j0 + k, 32)) {
+            if (j0 + k < nr && vd_in(P, CHK_RUN_LABEL, rrow + j0 + k, RUNS)) {
                 P.rl[now][rbase + j0 + k] = l[k];
                 lab[SW(lane * 32 + j0 + k)] = l[k];
             }
@@ -752,9 +771,9 @@ __global__ __launch_bounds__(32 * LBL_WARPS, 10) void k_run_labels(Pools P, Step
     const int pb = S.prev_buf;
     const bool same = S.prev_same != 0;   // past frame labelled in this step: its runs still hold piece ids
     const InstDesc& DP = P.desc[S.prev_inst];
-    const long long pbase = (long long)(DP.tile_off + t) * RUNS + lane * 32;
     const unsigned long long mp = load_row_mask(P.fgbits[pb], DP, x0, y0);
     const unsigned long long Sp = run_starts(mp);
+    const long long pbase = (long long)(DP.tile_off + t) * RUNS + run_row_base(__popcll(Sp));
     const unsigned long long A = m & mp;
     unsigned long long As = run_starts(A);
     const int nA = __reduce_max_sync(0xffffffffu, __popcll(As));
@@ -813,29 +832,36 @@ __global__ __launch_bounds__(32 * LBL_WARPS, 10) void k_run_labels(Pools P, Step
 
 // per-site labels of one instance's frame in `slot`, from its foreground bits
 // and run labels (-1 for background)
-__global__ void k_expand_labels(Pools P, int inst, int slot, int* out, long long n) {
+// per-site labels of one instance's frame in `slot` from its run labels: one
+// warp per labelling tile, lane r takes row r's mask and run base, then the
+// warp writes the tile row by row (lanes on columns)
+constexpr int EXP_WARPS = 8;
+__global__ __launch_bounds__(32 * EXP_WARPS) void k_expand_labels(Pools P, int inst, int slot, int* out) {
     const InstDesc& D = P.desc[inst];
-    const unsigned* fg = P.fgbits[slot] + D.word_off;
-    const int* rl = P.rl[slot] + (long long)D.tile_off * RUNS;
-    for (long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x; g < n; g += (long long)gridDim.x * blockDim.x) {
-        const int y = (int)(g / D.Lx), x = (int)(g - (long long)y * D.Lx);
-        const int tx = x / TW, x0 = tx * TW, wx = x0 >> 5;
-        const unsigned* row = fg + (long long)y * D.wpr;
-        unsigned long long m = row[wx];
-        if (wx + 1 < D.wpr) m |= (unsigned long long)row[wx + 1] << 32;
-        const int c = x - x0;
-        int l = -1;
-        if ((m >> c) & 1ull) {
-            const int tile = (y / TH) * D.ntx + tx;
-            l = rl[(long long)tile * RUNS + (y % TH) * 32 + run_index(run_starts(m), c)];
+    const int lane = threadIdx.x & 31;
+    const int t = blockIdx.x * EXP_WARPS + (threadIdx.x >> 5);
+    if (t >= D.ntx * D.nty) return;
+    const int tx = t % D.ntx, ty = t / D.ntx;
+    const int x0 = tx * TW, y0 = ty * TH;
+    const int ncols = min(TW, D.Lx - x0), nrows = min(TH, D.Ly - y0);
+    const unsigned long long m = load_row_mask(P.fgbits[slot], D, x0, y0);
+    const int rrow = run_row_base(__popcll(run_starts(m)));
+    const int* rl = P.rl[slot] + (long long)(D.tile_off + t) * RUNS;
+    for (int r = 0; r < nrows; ++r) {
+        const unsigned long long mr = __shfl_sync(0xffffffffu, m, r);
+        const int br = __shfl_sync(0xffffffffu, rrow, r);
+        const unsigned long long Sr = run_starts(mr);
+        int* row = out + (long long)(y0 + r) * D.Lx + x0;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int c = lane + 32 * h;
+            if (c < ncols) row[c] = ((mr >> c) & 1ull) ? rl[br + run_index(Sr, c)] : -1;
         }
-        out[g] = l;
     }
 }
 
-void launch_expand_labels(cudaStream_t s, const Pools& P, int inst, int slot, int* out, long long n) {
-    const long long blocks = (n + 255) / 256;
-    k_expand_labels<<<(int)(blocks < 4096 ? (blocks > 0 ? blocks : 1) : 4096), 256, 0, s>>>(P, inst, slot, out, n);
+void launch_expand_labels(cudaStream_t s, const Pools& P, int inst, int slot, int* out, int n_tiles) {
+    k_expand_labels<<<(n_tiles + EXP_WARPS - 1) / EXP_WARPS, 32 * EXP_WARPS, 0, s>>>(P, inst, slot, out);
 }
 
 void launch_ccl_tiles(const Launch& L) {

@@ -562,7 +562,7 @@ void launch_graph_flips(const Launch& L);
 void launch_begin(const Launch& L);        // per-step counters and field pointers
 void launch_finish(const Launch& L);       // swap frames
 void launch_edge_keys(cudaStream_t s, const Pools& P, int inst, int slot, unsigned long long* out);
-void launch_expand_labels(cudaStream_t s, const Pools& P, int inst, int slot, int* out, long long n);
+void launch_expand_labels(cudaStream_t s, const Pools& P, int inst, int slot, int* out, int n_tiles);
 // every instance's change lists packed at the offsets `off` (3 per instance:
 // breaking, arising, active; entry 3n holds the totals)
 void launch_gather_changes(cudaStream_t s, const Pools& P, const long long* off, int n, long long nb,
