@@ -178,7 +178,11 @@ vd_status vd_get_match(vd_ctx* ctx, int32_t* phi, int64_t cap, int64_t* n);     
  * centres (VD_PATCH_8x8, the default, 16x8, 32x8 or 16x16 sites); bucket_pct:
  * side of the centre bucket grid in percent of the mean centre spacing
  * (25..400, default 100); ring0: sites beyond the tile reached by the first
- * round of the owner search (0..256, default 9). Applies from the next push;
+ * round of the owner search (0..256, default 9); graph_blocks: the graph stage
+ * (CSR, match, flips) as one block per instance in two launches (1; the
+ * default for a single lattice of at most 2^21 sites) or as a chain of
+ * grid-wide launches over all instances' rows and links (0; the default
+ * otherwise). Applies from the next push;
  * synchronises the stream. The autotuner (paper_1607_00908_gb300/autotune.py)
  * times candidates and keeps the fastest per lattice-size and density class. */
 enum { VD_PATCH_8x8 = 0, VD_PATCH_16x8 = 1, VD_PATCH_32x8 = 2, VD_PATCH_16x16 = 3 };
@@ -186,6 +190,7 @@ typedef struct vd_tuning {
     int32_t voronoi_patch;
     int32_t bucket_pct;
     int32_t ring0;
+    int32_t graph_blocks;
 } vd_tuning;
 vd_status vd_set_tuning(vd_ctx* ctx, const vd_tuning* t);
 vd_status vd_get_tuning(vd_ctx* ctx, vd_tuning* t);

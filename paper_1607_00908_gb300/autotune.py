@@ -1,15 +1,16 @@
 """Autotuner of the launch shapes of a batch (vd_batch_set_tuning).
 
-The owner kernel's patch layout, the bucket side of the centre grid (a
-fraction of the mean centre spacing) and the reach of the owner search's
-first round change only the speed: every setting gives bit-identical results.
+The graph stage's form (one block per instance, or grid-wide kernels), the
+owner kernel's patch layout, the bucket side of the centre grid (a fraction
+of the mean centre spacing) and the reach of the owner search's first round
+change only the speed: every setting gives bit-identical results.
 The best setting depends on the lattice size and the density of bubbles, so
 the tuner times candidates on the batch's own frames and keeps the fastest
 per (lattice-size class, density class) in a JSON cache (path from
 VD_AUTOTUNE_CACHE, default ~/.cache/vd_autotune.json).
 
-Candidates are searched one parameter at a time (patch layout, then bucket
-side, then first reach), each timed as whole pushes with CUDA events on the
+Candidates are searched one parameter at a time (graph-stage form, patch
+layout, bucket side, first reach), each timed as whole pushes with CUDA events on the
 batch's stream after a warm-up push (the best of three rounds); a candidate
 replaces the current setting only when it is faster by more than 1%, so that
 timing noise does not pick among equal settings. Timing pushes advance the batch: tune it
@@ -26,6 +27,7 @@ from . import vd
 PATCHES = (vd.VD_PATCH_8x8, vd.VD_PATCH_16x8, vd.VD_PATCH_16x16, vd.VD_PATCH_32x8)
 BUCKETS = (50, 70, 100, 140)
 RINGS = (0, 9, 24)
+GRAPH = (1, 0)
 DEFAULT = dict(voronoi_patch=vd.VD_PATCH_8x8, bucket_pct=100, ring0=9)
 
 
@@ -89,13 +91,15 @@ def tune(b, fields, stream, reps: int = 8, use_cache: bool = True) -> dict:
     cache = _load(path) if use_cache else {}
     if key in cache:
         t = cache[key]
-        b.set_tuning(t["voronoi_patch"], t["bucket_pct"], t["ring0"])
+        b.set_tuning(t["voronoi_patch"], t["bucket_pct"], t["ring0"], t.get("graph_blocks"))
         return dict(t, key=key, cached=True)
-    cur = dict(DEFAULT)
+    # the batch's own default graph-stage form (by lattice size) is the start
+    cur = dict(DEFAULT, graph_blocks=b.tuning()["graph_blocks"])
     b.set_tuning(**cur)
     base = best_ms = _time_push(b, fields, stream, reps)
     tried = {tuple(cur.values()): base}
-    for name, values in (("voronoi_patch", PATCHES), ("bucket_pct", BUCKETS), ("ring0", RINGS)):
+    for name, values in (("graph_blocks", GRAPH), ("voronoi_patch", PATCHES), ("bucket_pct", BUCKETS),
+                         ("ring0", RINGS)):
         for v in values:
             cand = dict(cur, **{name: v})
             k = tuple(cand.values())

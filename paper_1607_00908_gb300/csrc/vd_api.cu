@@ -86,6 +86,7 @@ struct vd_batch {
     bool any_vertex_rule = false;      // some instance reads links at Voronoi vertices
     bool any_masked = false;           // some instance has walls or obstacles
     int vpatch = VPATCH_8x8;           // patch layout of the owner kernel (tuning)
+    int graph_inst = 0;                // graph stage with one block per instance (tuning)
     // field pointer tables (device) and their host mirrors
     const float** d_fields = nullptr;
     long long* d_pitches = nullptr;
@@ -138,6 +139,9 @@ struct vd_batch {
 // centre spacing, a first owner-search round reaching 9 sites beyond the tile
 static const int DEFAULT_BUCKET_PCT = 100;
 static const int DEFAULT_RING0 = 9;
+// a single lattice up to this many sites runs the graph stage as one block by
+// default (a 1024^2 frame: about a thousand rows and three thousand links)
+static const long long GRAPH_INST_MAX_SITES = 1ll << 21;
 
 static const int N_STAGES = 6;
 static const char* STAGE_NAMES[N_STAGES] = {
@@ -223,6 +227,7 @@ Launch make_launch(vd_batch* b, const StepTables& T) {
     L.masked = b->any_masked;
     L.grid_wide = 4 * b->grid_items;
     L.vpatch = b->vpatch;
+    L.graph_inst = b->graph_inst;
     L.total_tilesA = T.total_tilesA;
     L.total_tilesV = T.total_tilesV;
     L.total_groups = T.total_groups;
@@ -258,11 +263,15 @@ void enqueue_step(vd_batch* b, const Launch& L, bool timed) {
     launch_links(L);
     launch_merge_lists(L);
     mark(b, timed);
-    launch_graph_prep(L);
-    launch_graph_csr(L);
-    launch_graph_match(L);
-    launch_graph_flips(L);
-    launch_finish(L);
+    if (L.graph_inst) {
+        launch_graph_inst(L);
+    } else {
+        launch_graph_prep(L);
+        launch_graph_csr(L);
+        launch_graph_match(L);
+        launch_graph_flips(L);
+        launch_finish(L);
+    }
     mark(b, timed);
 }
 
@@ -353,6 +362,10 @@ vd_status create_batch(const vd_config* cfgs, int n, vd_batch** out, bool sequen
         scan_items = std::max(scan_items, (long long)0);
     }
     scan_items = std::max(std::max(grp, comp), bucket);
+    // the graph stage runs as one block by default for a single small lattice
+    // (its rows and links take a few passes of a block; with many instances
+    // the grid-wide kernels are faster)
+    b->graph_inst = (n == 1 && max_sites <= GRAPH_INST_MAX_SITES) ? 1 : 0;
     if (piece_cap >= (1ll << 31) || comp >= (1ll << 31) || edge >= (1ll << 30)) {
         delete b;
         return VD_ERR_INVALID;
@@ -1231,7 +1244,7 @@ vd_status vd_batch_debug_force_check(vd_batch* b, int32_t id) { return force_che
 vd_status vd_batch_set_tuning(vd_batch* b, const vd_tuning* t) {
     if (!b || !t) return VD_ERR_INVALID;
     if (t->voronoi_patch < 0 || t->voronoi_patch >= VPATCH_COUNT || t->bucket_pct < 25 || t->bucket_pct > 400 ||
-        t->ring0 < 0 || t->ring0 > 256)
+        t->ring0 < 0 || t->ring0 > 256 || t->graph_blocks < 0 || t->graph_blocks > 1)
         return VD_ERR_INVALID;
     for (InstDesc& D : b->desc) {
         D.bucket_pct = t->bucket_pct;
@@ -1240,8 +1253,9 @@ vd_status vd_batch_set_tuning(vd_batch* b, const vd_tuning* t) {
     cudaError_t e = cudaMemcpyAsync(b->P.desc, b->desc.data(), sizeof(InstDesc) * b->n, cudaMemcpyHostToDevice, b->s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->s);
     if (e != cudaSuccess) return VD_ERR_CUDA;
-    if (t->voronoi_patch != b->vpatch) {
+    if (t->voronoi_patch != b->vpatch || t->graph_blocks != b->graph_inst) {
         b->vpatch = t->voronoi_patch;
+        b->graph_inst = t->graph_blocks;
         if (b->graph) {   // the step launches another kernel: capture it again
             cudaGraphExecDestroy(b->graph);
             b->graph = nullptr;
@@ -1255,6 +1269,7 @@ vd_status vd_batch_get_tuning(vd_batch* b, vd_tuning* t) {
     t->voronoi_patch = b->vpatch;
     t->bucket_pct = b->desc[0].bucket_pct;
     t->ring0 = b->desc[0].ring0;
+    t->graph_blocks = b->graph_inst;
     return VD_OK;
 }
 

@@ -81,10 +81,9 @@ __global__ void k_step_begin(Pools P, StepTable T) {
     }
 }
 
-__global__ void k_step_finish(Pools P, StepTable T) {
-    pdl_enter();
-    for (int a = blockIdx.x * blockDim.x + threadIdx.x; a < T.n_act; a += gridDim.x * blockDim.x) {
-        const int inst = T.act[a];
+// end of a step for one instance: errors, counts, the frame becomes the past
+__device__ __forceinline__ void finish_instance(const Pools& P, int inst) {
+    {
         InstState& S = P.st[inst];
         S.err |= P.g->err;
         // a past frame from this step that overflowed makes this frame's changes unreliable
@@ -100,6 +99,12 @@ __global__ void k_step_finish(Pools P, StepTable T) {
         S.last_ok = S.err ? 0 : 1;
         S.frame += 1;
     }
+}
+
+__global__ void k_step_finish(Pools P, StepTable T) {
+    pdl_enter();
+    for (int a = blockIdx.x * blockDim.x + threadIdx.x; a < T.n_act; a += gridDim.x * blockDim.x)
+        finish_instance(P, T.act[a]);
 }
 
 // sorted link keys of one instance's frame in `slot`: the entries above the
@@ -154,9 +159,8 @@ void launch_edge_keys(cudaStream_t s, const Pools& P, int inst, int slot, unsign
 // ---------------------------------------------------------------------------
 // CSR of the now links
 // ---------------------------------------------------------------------------
-__global__ void k_csr_scatter(Pools P, StepTable T) {
-    pdl_enter();
-    for_items(T, PRE_E, [&](int inst, long long j) {
+__device__ __forceinline__ void csr_scatter_item(const Pools& P, int inst, long long j) {
+    {
         const InstDesc& D = P.desc[inst];
         if (j >= D.edge_cap) return;
         const int now = P.st[inst].slot ^ 1;
@@ -172,7 +176,12 @@ __global__ void k_csr_scatter(Pools P, StepTable T) {
         const int phi_ = ro[hi] + atomicSub(&P.deg[D.comp_off + hi], 1) - 1;
         if (plo < cap && vd_in(P, CHK_CSR, plo, cap)) cl[plo] = hi;
         if (phi_ < cap && vd_in(P, CHK_CSR, phi_, cap)) cl[phi_] = lo;
-    });
+    }
+}
+
+__global__ void k_csr_scatter(Pools P, StepTable T) {
+    pdl_enter();
+    for_items(T, PRE_E, [&](int inst, long long j) { csr_scatter_item(P, inst, j); });
 }
 
 // ascending sort of a short row in place: insertion sort up to 32 entries,
@@ -214,27 +223,29 @@ __device__ void sort_row(int* v, int n) {
 
 constexpr int RLOC = 32;   // rows up to this length are handled in a local array (loads issued together)
 
+__device__ __forceinline__ void csr_sort_item(const Pools& P, int inst, long long a) {
+    const InstDesc& D = P.desc[inst];
+    const int now = P.st[inst].slot ^ 1;
+    const int* ro = P.rowoff[now] + D.comp_off;
+    const int cap = 2 * D.edge_cap;
+    const int s = min(ro[a], cap), e = min(ro[a + 1], cap);
+    int* row = P.cols[now] + 2 * D.edge_off + s;
+    const int n = e - s;
+    if (n > RLOC) {
+        sort_row(row, n);
+        return;
+    }
+    int v[RLOC];
+#pragma unroll 8
+    for (int k = 0; k < n; ++k) v[k] = row[k];
+    sort_row(v, n);
+#pragma unroll 8
+    for (int k = 0; k < n; ++k) row[k] = v[k];
+}
+
 __global__ void k_csr_sort(Pools P, StepTable T) {
     pdl_enter();
-    for_items(T, PRE_K, [&](int inst, long long a) {
-        const InstDesc& D = P.desc[inst];
-        const int now = P.st[inst].slot ^ 1;
-        const int* ro = P.rowoff[now] + D.comp_off;
-        const int cap = 2 * D.edge_cap;
-        const int s = min(ro[a], cap), e = min(ro[a + 1], cap);
-        int* row = P.cols[now] + 2 * D.edge_off + s;
-        const int n = e - s;
-        if (n > RLOC) {
-            sort_row(row, n);
-            return;
-        }
-        int v[RLOC];
-#pragma unroll 8
-        for (int k = 0; k < n; ++k) v[k] = row[k];
-        sort_row(v, n);
-#pragma unroll 8
-        for (int k = 0; k < n; ++k) row[k] = v[k];
-    });
+    for_items(T, PRE_K, [&](int inst, long long a) { csr_sort_item(P, inst, a); });
 }
 
 // ---------------------------------------------------------------------------
@@ -248,23 +259,25 @@ __device__ __forceinline__ int unpack_label(unsigned long long v) {
     return (int)(0xffffffffu - (unsigned)(v & 0xffffffffu));
 }
 
+__device__ __forceinline__ void match_best_item(const Pools& P, int inst, long long j) {
+    const InstDesc& D = P.desc[inst];
+    const int slot = P.olist[D.ovl_off + j];
+    unsigned long long* H = P.ohash + D.ohash_off;
+    unsigned* V = P.oval + D.ohash_off;
+    const unsigned long long key = H[slot];
+    const unsigned cnt = V[slot];
+    H[slot] = EMPTY_KEY;
+    V[slot] = 0;
+    const int p = (int)(key >> 32), n = (int)(key & 0xffffffffu);
+    if (p < 0 || n < 0 || p >= D.comp_cap || n >= D.comp_cap) return;   // only after an overflow
+    if (!vd_in(P, CHK_MATCH, j, D.ovl_cap)) return;
+    atomicMax(&P.best_n[D.comp_off + p], pack_best(cnt, n));
+    atomicMax(&P.best_p[D.comp_off + n], pack_best(cnt, p));
+}
+
 __global__ void k_match_best(Pools P, StepTable T) {
     pdl_enter();
-    for_items(T, PRE_O, [&](int inst, long long j) {
-        const InstDesc& D = P.desc[inst];
-        const int slot = P.olist[D.ovl_off + j];
-        unsigned long long* H = P.ohash + D.ohash_off;
-        unsigned* V = P.oval + D.ohash_off;
-        const unsigned long long key = H[slot];
-        const unsigned cnt = V[slot];
-        H[slot] = EMPTY_KEY;
-        V[slot] = 0;
-        const int p = (int)(key >> 32), n = (int)(key & 0xffffffffu);
-        if (p < 0 || n < 0 || p >= D.comp_cap || n >= D.comp_cap) return;   // only after an overflow
-        if (!vd_in(P, CHK_MATCH, j, D.ovl_cap)) return;
-        atomicMax(&P.best_n[D.comp_off + p], pack_best(cnt, n));
-        atomicMax(&P.best_p[D.comp_off + n], pack_best(cnt, p));
-    });
+    for_items(T, PRE_O, [&](int inst, long long j) { match_best_item(P, inst, j); });
 }
 
 // Centroid rule (Section 3.2.3, the kinematic comparison of the two sets of
@@ -323,54 +336,60 @@ __device__ int nearest_centre(const CentreGrid& G, int2 q, int Lx, int Ly, int r
     return best;
 }
 
+__device__ __forceinline__ void match_kin_past_item(const Pools& P, int inst, long long p) {
+    const InstDesc& D = P.desc[inst];
+    if (!D.match_rule) return;
+    const InstState& S = P.st[inst];
+    const int now = S.slot ^ 1;
+    const InstDesc& DP = P.desc[S.prev_inst];
+    const CentreGrid G{P.bcq[now] + D.comp_off, P.bid[now] + D.comp_off, P.boff[now] + D.bucket_off, S.B,
+                       S.nbx, S.nby};
+    const int2 q = P.cq[S.prev_buf][DP.comp_off + p];
+    const int n = nearest_centre(G, q, D.Lx, D.Ly, D.match_radius);
+    P.best_n[D.comp_off + p] = n >= 0 ? pack_best(1u, n) : 0ull;
+}
+
+__device__ __forceinline__ void match_kin_now_item(const Pools& P, int inst, long long n) {
+    const InstDesc& D = P.desc[inst];
+    const InstState& S = P.st[inst];
+    if (!D.match_rule || !S.has_prev) return;
+    const int now = S.slot ^ 1, pb = S.prev_buf;
+    const InstDesc& DP = P.desc[S.prev_inst];
+    const InstState& SP = P.st[S.prev_inst];
+    const CentreGrid G{P.bcq[pb] + DP.comp_off, P.bid[pb] + DP.comp_off, P.boff[pb] + DP.bucket_off,
+                       SP.Bs[pb], SP.nbxs[pb], SP.nbys[pb]};
+    const int p = nearest_centre(G, P.cq[now][D.comp_off + n], D.Lx, D.Ly, D.match_radius);
+    P.best_p[D.comp_off + n] = p >= 0 ? pack_best(1u, p) : 0ull;
+}
+
 __global__ void k_match_kin(Pools P, StepTable T) {
     pdl_enter();
     // past centres: the nearest now centre
-    for_items(T, PRE_KP, [&](int inst, long long p) {
-        const InstDesc& D = P.desc[inst];
-        if (!D.match_rule) return;
-        const InstState& S = P.st[inst];
-        const int now = S.slot ^ 1;
-        const InstDesc& DP = P.desc[S.prev_inst];
-        const CentreGrid G{P.bcq[now] + D.comp_off, P.bid[now] + D.comp_off, P.boff[now] + D.bucket_off, S.B,
-                           S.nbx, S.nby};
-        const int2 q = P.cq[S.prev_buf][DP.comp_off + p];
-        const int n = nearest_centre(G, q, D.Lx, D.Ly, D.match_radius);
-        P.best_n[D.comp_off + p] = n >= 0 ? pack_best(1u, n) : 0ull;
-    });
+    for_items(T, PRE_KP, [&](int inst, long long p) { match_kin_past_item(P, inst, p); });
     // now centres: the nearest past centre
-    for_items(T, PRE_K, [&](int inst, long long n) {
-        const InstDesc& D = P.desc[inst];
-        const InstState& S = P.st[inst];
-        if (!D.match_rule || !S.has_prev) return;
-        const int now = S.slot ^ 1, pb = S.prev_buf;
-        const InstDesc& DP = P.desc[S.prev_inst];
-        const InstState& SP = P.st[S.prev_inst];
-        const CentreGrid G{P.bcq[pb] + DP.comp_off, P.bid[pb] + DP.comp_off, P.boff[pb] + DP.bucket_off,
-                           SP.Bs[pb], SP.nbxs[pb], SP.nbys[pb]};
-        const int p = nearest_centre(G, P.cq[now][D.comp_off + n], D.Lx, D.Ly, D.match_radius);
-        P.best_p[D.comp_off + n] = p >= 0 ? pack_best(1u, p) : 0ull;
-    });
+    for_items(T, PRE_K, [&](int inst, long long n) { match_kin_now_item(P, inst, n); });
+}
+
+__device__ __forceinline__ void match_phi_item(const Pools& P, int inst, long long p) {
+    const InstDesc& D = P.desc[inst];
+    const unsigned long long v = P.best_n[D.comp_off + p];
+    P.best_n[D.comp_off + p] = 0ull;   // zero again for the next step
+    int res = -1;
+    if (v != 0ull) {
+        const int n = unpack_label(v);
+        const unsigned long long w = P.best_p[D.comp_off + n];
+        if (w != 0ull && unpack_label(w) == (int)p) {
+            res = n;
+            P.inv[D.comp_off + n] = (int)p;
+            warp_add(&P.st[inst].n_matched, 1);
+        }
+    }
+    P.phi[D.comp_off + p] = res;
 }
 
 __global__ void k_match_phi(Pools P, StepTable T) {
     pdl_enter();
-    for_items(T, PRE_KP, [&](int inst, long long p) {
-        const InstDesc& D = P.desc[inst];
-        const unsigned long long v = P.best_n[D.comp_off + p];
-        P.best_n[D.comp_off + p] = 0ull;   // zero again for the next step
-        int res = -1;
-        if (v != 0ull) {
-            const int n = unpack_label(v);
-            const unsigned long long w = P.best_p[D.comp_off + n];
-            if (w != 0ull && unpack_label(w) == (int)p) {
-                res = n;
-                P.inv[D.comp_off + n] = (int)p;
-                warp_add(&P.st[inst].n_matched, 1);
-            }
-        }
-        P.phi[D.comp_off + p] = res;
-    });
+    for_items(T, PRE_KP, [&](int inst, long long p) { match_phi_item(P, inst, p); });
 }
 
 // ---------------------------------------------------------------------------
@@ -624,63 +643,178 @@ __device__ bool boundary_pt(const Graph& G, int u) {
     return hit;
 }
 
+__device__ __forceinline__ void events_item(const Pools& P, int inst, long long a_) {
+    const int a = (int)a_;
+    const InstDesc& D = P.desc[inst];
+    const long long co = D.comp_off;
+    if (!D.events || !(P.active[co + a] & EV_ACTIVE)) return;
+    const InstState& S = P.st[inst];
+    const int ia = S.has_prev ? P.inv[co + a] : -1;
+    const int now = S.slot ^ 1;
+    const int K = min(S.K, D.comp_cap);
+    const Graph GN{P.rowoff[now] + co, P.cols[now] + 2 * D.edge_off, 2 * D.edge_cap, K};
+    const int* phi = P.phi + co;
+    const unsigned char* act = P.active + co;
+    auto active_now = [&](int n) { return n >= 0 && n < K && (act[n] & EV_ACTIVE); };
+    unsigned f = 0;
+    // the now triangulation
+    int c_now = 0;
+    bool bnow = false, evnow = false;
+    {
+        int s, e;
+        row_of(GN, a, s, e);
+#pragma unroll 8
+        for (int k = s; k < e; ++k) c_now += active_now(GN.cl[k]) ? 1 : 0;
+        bnow = boundary_pt(GN, a);
+        if (bnow)
+            for (int k = s; k < e && !evnow; ++k) {
+                const int b = GN.cl[k];
+                evnow = active_now(b) && boundary_pt(GN, b);
+            }
+    }
+    // the past triangulation, seen through Phi
+    int c_past = 0;
+    bool bpast = false, evpast = false;
+    if (ia >= 0) {
+        const InstDesc& DP = P.desc[S.prev_inst];
+        const int Kp = S.K_prev;
+        const Graph GP{P.rowoff[S.prev_buf] + DP.comp_off, P.cols[S.prev_buf] + 2 * DP.edge_off,
+                       2 * DP.edge_cap, Kp};
+        auto active_past = [&](int q) { return q >= 0 && q < Kp && q < D.comp_cap && active_now(phi[q]); };
+        int s, e;
+        row_of(GP, ia, s, e);
+#pragma unroll 8
+        for (int k = s; k < e; ++k) c_past += active_past(GP.cl[k]) ? 1 : 0;
+        bpast = boundary_pt(GP, ia);
+        if (bpast)
+            for (int k = s; k < e && !evpast; ++k) {
+                const int q = GP.cl[k];
+                evpast = active_past(q) && boundary_pt(GP, q);
+            }
+    }
+    if (max(c_now, c_past) >= 3) f |= EV_BULK;
+    if (evnow || evpast) f |= EV_BOUNDARY;
+    if (bnow) f |= EV_BPOINT_NOW;
+    if (bpast) f |= EV_BPOINT_PAST;
+    if (f) P.active[co + a] = (unsigned char)(EV_ACTIVE | f);
+}
+
 __global__ void k_events(Pools P, StepTable T) {
     pdl_enter();
-    for_items(T, PRE_K, [&](int inst, long long a_) {
-        const int a = (int)a_;
-        const InstDesc& D = P.desc[inst];
-        const long long co = D.comp_off;
-        if (!D.events || !(P.active[co + a] & EV_ACTIVE)) return;
-        const InstState& S = P.st[inst];
-        const int ia = S.has_prev ? P.inv[co + a] : -1;
-        const int now = S.slot ^ 1;
-        const int K = min(S.K, D.comp_cap);
-        const Graph GN{P.rowoff[now] + co, P.cols[now] + 2 * D.edge_off, 2 * D.edge_cap, K};
-        const int* phi = P.phi + co;
-        const unsigned char* act = P.active + co;
-        auto active_now = [&](int n) { return n >= 0 && n < K && (act[n] & EV_ACTIVE); };
-        unsigned f = 0;
-        // the now triangulation
-        int c_now = 0;
-        bool bnow = false, evnow = false;
-        {
-            int s, e;
-            row_of(GN, a, s, e);
-#pragma unroll 8
-            for (int k = s; k < e; ++k) c_now += active_now(GN.cl[k]) ? 1 : 0;
-            bnow = boundary_pt(GN, a);
-            if (bnow)
-                for (int k = s; k < e && !evnow; ++k) {
-                    const int b = GN.cl[k];
-                    evnow = active_now(b) && boundary_pt(GN, b);
-                }
+    for_items(T, PRE_K, [&](int inst, long long a_) { events_item(P, inst, a_); });
+}
+
+// ---------------------------------------------------------------------------
+// The graph stage with one block per instance. For batches of small lattices
+// the stage above is a chain of about a dozen grid-wide launches whose items
+// (rows, links, pairs) number a few thousand per instance: each launch costs
+// a few dependent L2 round trips plus a kernel boundary. Here one block of
+// GI_THREADS threads takes every phase of one instance, with block barriers
+// between the phases: k_graph_inst_a builds the now-frame CSR and the match,
+// k_graph_inst_b (after it, since a frame sequence translates the CSR the
+// previous instance built in this step) counts, places and writes the flips,
+// classifies the events and ends the instance's step. The per-item work is
+// the same code as the grid-wide kernels; the scans are block scans over the
+// instance's rows. No block waits on another.
+// ---------------------------------------------------------------------------
+constexpr int GI_THREADS = 1024;
+
+template <class F>
+__device__ __forceinline__ void block_items(long long n, F f) {
+    for (long long j = threadIdx.x; j < n; j += blockDim.x) f(j);
+}
+
+// exclusive prefix of v(j), j < n, over the block in chunks of its size (the
+// carry held in shared memory); w(j, prefix) stores each prefix. Ends with a
+// barrier.
+template <class V, class W>
+__device__ void block_scan(int n, V v, W w) {
+    __shared__ int s_warp[32];
+    __shared__ int s_carry;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
+    if (tid == 0) s_carry = 0;
+    __syncthreads();
+    for (int base = 0; base < n; base += blockDim.x) {
+        const int j = base + tid;
+        const int x = j < n ? v(j) : 0;
+        int inc = x;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += y;
         }
-        // the past triangulation, seen through Phi
-        int c_past = 0;
-        bool bpast = false, evpast = false;
-        if (ia >= 0) {
-            const InstDesc& DP = P.desc[S.prev_inst];
-            const int Kp = S.K_prev;
-            const Graph GP{P.rowoff[S.prev_buf] + DP.comp_off, P.cols[S.prev_buf] + 2 * DP.edge_off,
-                           2 * DP.edge_cap, Kp};
-            auto active_past = [&](int q) { return q >= 0 && q < Kp && q < D.comp_cap && active_now(phi[q]); };
-            int s, e;
-            row_of(GP, ia, s, e);
-#pragma unroll 8
-            for (int k = s; k < e; ++k) c_past += active_past(GP.cl[k]) ? 1 : 0;
-            bpast = boundary_pt(GP, ia);
-            if (bpast)
-                for (int k = s; k < e && !evpast; ++k) {
-                    const int q = GP.cl[k];
-                    evpast = active_past(q) && boundary_pt(GP, q);
-                }
+        if (lane == 31) s_warp[wid] = inc;
+        __syncthreads();
+        if (wid == 0) {
+            int t = lane < nw ? s_warp[lane] : 0;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, t, o);
+                if (lane >= o) t += y;
+            }
+            if (lane < nw) s_warp[lane] = t;   // inclusive over warps
         }
-        if (max(c_now, c_past) >= 3) f |= EV_BULK;
-        if (evnow || evpast) f |= EV_BOUNDARY;
-        if (bnow) f |= EV_BPOINT_NOW;
-        if (bpast) f |= EV_BPOINT_PAST;
-        if (f) P.active[co + a] = (unsigned char)(EV_ACTIVE | f);
-    });
+        __syncthreads();
+        if (j < n) w(j, s_carry + (wid > 0 ? s_warp[wid - 1] : 0) + inc - x);
+        __syncthreads();
+        if (tid == 0) s_carry += s_warp[nw - 1];
+        __syncthreads();
+    }
+}
+
+__global__ __launch_bounds__(GI_THREADS) void k_graph_inst_a(Pools P, StepTable T) {
+    pdl_enter();
+    const int inst = T.act[blockIdx.x];
+    const InstDesc& D = P.desc[inst];
+    const InstState& S = P.st[inst];
+    const int K = min(S.K, D.comp_cap);
+    const int now = S.slot ^ 1;
+    const int nE = S.n_edge_list;
+    const int KP = S.has_prev ? S.K_prev : 0;
+    const int nO = min(S.n_ovl, D.ovl_cap);
+    int* ro = P.rowoff[now] + D.comp_off;
+    // CSR of the now links: row offsets = prefix of the degrees (every link
+    // lies in the rows of both ends)
+    if (threadIdx.x == 0) ro[K] = 2 * nE;
+    block_scan(K, [&](int j) { return P.deg[D.comp_off + j]; },
+               [&](int j, int pre) { if (vd_in(P, CHK_SCAN_WRITE, j, K)) ro[j] = pre; });
+    block_items(nE, [&](long long j) { csr_scatter_item(P, inst, j); });
+    __syncthreads();
+    block_items(K, [&](long long a) { csr_sort_item(P, inst, a); });
+    // the match (Section 3.2.3)
+    if (D.match_rule) {
+        block_items(KP, [&](long long p) { match_kin_past_item(P, inst, p); });
+        block_items(K, [&](long long n) { match_kin_now_item(P, inst, n); });
+    }
+    __syncthreads();
+    block_items(nO, [&](long long j) { match_best_item(P, inst, j); });
+    __syncthreads();
+    block_items(KP, [&](long long p) { match_phi_item(P, inst, p); });
+}
+
+__global__ __launch_bounds__(GI_THREADS) void k_graph_inst_b(Pools P, StepTable T) {
+    pdl_enter();
+    const int inst = T.act[blockIdx.x];
+    const InstDesc& D = P.desc[inst];
+    const int K = min(P.st[inst].K, D.comp_cap);
+    block_items(K, [&](long long a) { compare_row<false>(P, inst, (int)a); });
+    __syncthreads();
+    // flip offsets: prefixes of the per-row counts, the totals at the end
+    if (threadIdx.x == 0) {
+        P.foff[D.comp_off + K] = *(volatile int*)&P.st[inst].n_break;
+        P.foff_a[D.comp_off + K] = *(volatile int*)&P.st[inst].n_arise;
+    }
+    block_scan(K, [&](int j) { return P.fcnt[D.comp_off + j]; },
+               [&](int j, int pre) { if (vd_in(P, CHK_SCAN_WRITE, j, K)) P.foff[D.comp_off + j] = pre; });
+    block_scan(K, [&](int j) { return P.fcnt_a[D.comp_off + j]; },
+               [&](int j, int pre) { if (vd_in(P, CHK_SCAN_WRITE, j, K)) P.foff_a[D.comp_off + j] = pre; });
+    block_items(K, [&](long long a) { compare_row<true>(P, inst, (int)a); });
+    __syncthreads();
+    if (D.events) {
+        block_items(K, [&](long long a) { events_item(P, inst, a); });
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) finish_instance(P, inst);
 }
 
 // packed copy of every instance's breaking keys (then their past keys), arising
@@ -756,6 +890,11 @@ void launch_graph_flips(const Launch& L) {
     launch_scan2(L, SCAN_FLIPS, SCAN_FLIPS_A);
     launch_step(L, k_flip_write, dim3(g), dim3(256), L.P, L.T);
     if (L.events) launch_step(L, k_events, dim3(g), dim3(256), L.P, L.T);
+}
+
+void launch_graph_inst(const Launch& L) {
+    launch_step(L, k_graph_inst_a, dim3(L.T.n_act), dim3(GI_THREADS), L.P, L.T);
+    launch_step(L, k_graph_inst_b, dim3(L.T.n_act), dim3(GI_THREADS), L.P, L.T);
 }
 
 void launch_begin(const Launch& L) {

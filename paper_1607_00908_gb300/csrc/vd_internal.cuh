@@ -465,6 +465,7 @@ struct Launch {
     long long total_groups;
     int grid_wide;               // blocks for kernels with one thread per item (pieces, bubbles, links)
     int vpatch;                  // patch layout of the owner kernel (VPATCH_*)
+    int graph_inst;              // graph stage with one block per instance (else grid-wide kernels)
 };
 
 // patch layouts of the owner kernel (PW x PH sites per patch of a 64 x 32 tile)
@@ -559,6 +560,7 @@ void launch_graph_prep(const Launch& L);
 void launch_graph_csr(const Launch& L);
 void launch_graph_match(const Launch& L);
 void launch_graph_flips(const Launch& L);
+void launch_graph_inst(const Launch& L);   // the whole graph stage, one block per instance (2 launches)
 void launch_begin(const Launch& L);        // per-step counters and field pointers
 void launch_finish(const Launch& L);       // swap frames
 void launch_edge_keys(cudaStream_t s, const Pools& P, int inst, int slot, unsigned long long* out);

@@ -91,7 +91,8 @@ class vd_changes(C.Structure):
 
 
 class vd_tuning(C.Structure):
-    _fields_ = [("voronoi_patch", C.c_int32), ("bucket_pct", C.c_int32), ("ring0", C.c_int32)]
+    _fields_ = [("voronoi_patch", C.c_int32), ("bucket_pct", C.c_int32), ("ring0", C.c_int32),
+                ("graph_blocks", C.c_int32)]
 
 
 VD_PATCH_8x8, VD_PATCH_16x8, VD_PATCH_32x8, VD_PATCH_16x16 = 0, 1, 2, 3
@@ -425,15 +426,19 @@ class Detector(_Base):
                     breaking_prev=brkp[: ch.n_breaking].copy(), arising=ari[: ch.n_arising].copy(),
                     active=act[: ch.n_now].copy(), global_trigger=ch.global_trigger)
 
-    def set_tuning(self, voronoi_patch: int = 0, bucket_pct: int = 100, ring0: int = 9) -> None:
-        """Launch shapes (vd_set_tuning); results are identical for every setting."""
-        t = vd_tuning(int(voronoi_patch), int(bucket_pct), int(ring0))
+    def set_tuning(self, voronoi_patch: int = 0, bucket_pct: int = 100, ring0: int = 9,
+                   graph_blocks: int | None = None) -> None:
+        """Launch shapes (vd_set_tuning); results are identical for every setting.
+        graph_blocks None keeps the current graph-stage form."""
+        gb = self.tuning()["graph_blocks"] if graph_blocks is None else int(graph_blocks)
+        t = vd_tuning(int(voronoi_patch), int(bucket_pct), int(ring0), gb)
         _check(lib().vd_set_tuning(self.h, C.byref(t)), "vd_set_tuning")
 
     def tuning(self) -> dict:
         t = vd_tuning()
         _check(lib().vd_get_tuning(self.h, C.byref(t)), "vd_get_tuning")
-        return dict(voronoi_patch=t.voronoi_patch, bucket_pct=t.bucket_pct, ring0=t.ring0)
+        return dict(voronoi_patch=t.voronoi_patch, bucket_pct=t.bucket_pct, ring0=t.ring0,
+                    graph_blocks=t.graph_blocks)
 
     def export_state(self) -> np.ndarray:
         """Checkpoint of the last frame's state (vd_export_state), as bytes."""
@@ -589,15 +594,19 @@ class Batch(_Base):
     def force_check(self, check_id: int) -> None:
         _check(lib().vd_batch_debug_force_check(self.h, int(check_id)), "vd_batch_debug_force_check")
 
-    def set_tuning(self, voronoi_patch: int = 0, bucket_pct: int = 100, ring0: int = 9) -> None:
-        """Launch shapes of the batch (vd_batch_set_tuning); results are identical for every setting."""
-        t = vd_tuning(int(voronoi_patch), int(bucket_pct), int(ring0))
+    def set_tuning(self, voronoi_patch: int = 0, bucket_pct: int = 100, ring0: int = 9,
+                   graph_blocks: int | None = None) -> None:
+        """Launch shapes of the batch (vd_batch_set_tuning); results are identical for every setting.
+        graph_blocks None keeps the current graph-stage form."""
+        gb = self.tuning()["graph_blocks"] if graph_blocks is None else int(graph_blocks)
+        t = vd_tuning(int(voronoi_patch), int(bucket_pct), int(ring0), gb)
         _check(lib().vd_batch_set_tuning(self.h, C.byref(t)), "vd_batch_set_tuning")
 
     def tuning(self) -> dict:
         t = vd_tuning()
         _check(lib().vd_batch_get_tuning(self.h, C.byref(t)), "vd_batch_get_tuning")
-        return dict(voronoi_patch=t.voronoi_patch, bucket_pct=t.bucket_pct, ring0=t.ring0)
+        return dict(voronoi_patch=t.voronoi_patch, bucket_pct=t.bucket_pct, ring0=t.ring0,
+                    graph_blocks=t.graph_blocks)
 
     def export_state(self, i: int) -> np.ndarray:
         """Checkpoint of instance i's last frame (vd_batch_export_state)."""

@@ -12,7 +12,7 @@ class FakeBatch:
         self.sizes = sizes
         self._bubbles = bubbles
         self.cost = cost
-        self.t = dict(autotune.DEFAULT)
+        self.t = dict(autotune.DEFAULT, graph_blocks=1)
         self.sets = 0
 
     def push(self, fields):
@@ -21,9 +21,13 @@ class FakeBatch:
     def counts(self, i):
         return self._bubbles[i], 0, 0
 
-    def set_tuning(self, voronoi_patch, bucket_pct, ring0):
-        self.t = dict(voronoi_patch=voronoi_patch, bucket_pct=bucket_pct, ring0=ring0)
+    def set_tuning(self, voronoi_patch, bucket_pct, ring0, graph_blocks=None):
+        gb = self.t["graph_blocks"] if graph_blocks is None else graph_blocks
+        self.t = dict(voronoi_patch=voronoi_patch, bucket_pct=bucket_pct, ring0=ring0, graph_blocks=gb)
         self.sets += 1
+
+    def tuning(self):
+        return dict(self.t)
 
 
 def _fake_time(b, fields, stream, reps):
@@ -41,18 +45,19 @@ def test_search_finds_the_separable_minimum_and_caches_it(tmp_path, monkeypatch)
     monkeypatch.setenv("VD_AUTOTUNE_CACHE", str(tmp_path / "cache.json"))
     monkeypatch.setattr(autotune, "_time_push", _fake_time)
 
-    def cost(t):   # best: 16x16 patches, buckets at 70 %, first reach 0
-        return (abs(t["voronoi_patch"] - 3) + abs(t["bucket_pct"] - 70) / 10 + t["ring0"] / 9 + 1.0)
+    def cost(t):   # best: grid-wide graph stage, 16x16 patches, buckets at 70 %, first reach 0
+        return (abs(t["voronoi_patch"] - 3) + abs(t["bucket_pct"] - 70) / 10 + t["ring0"] / 9 + 1.0 +
+                t["graph_blocks"])
 
     b = FakeBatch([(512, 512)], [300], cost)
     r = autotune.tune(b, None, None)
-    assert (r["voronoi_patch"], r["bucket_pct"], r["ring0"]) == (3, 70, 0)
+    assert (r["voronoi_patch"], r["bucket_pct"], r["ring0"], r["graph_blocks"]) == (3, 70, 0, 0)
     assert not r["cached"] and r["tuned_ms"] < r["default_ms"]
-    assert b.t == dict(voronoi_patch=3, bucket_pct=70, ring0=0)
+    assert b.t == dict(voronoi_patch=3, bucket_pct=70, ring0=0, graph_blocks=0)
     # the second batch of the same classes takes the cached choice without timing
     b2 = FakeBatch([(512, 512)], [310], lambda t: 1 / 0)
     r2 = autotune.tune(b2, None, None)
-    assert r2["cached"] and b2.t == dict(voronoi_patch=3, bucket_pct=70, ring0=0)
+    assert r2["cached"] and b2.t == dict(voronoi_patch=3, bucket_pct=70, ring0=0, graph_blocks=0)
 
 
 def test_default_kept_when_nothing_is_faster(tmp_path, monkeypatch):
