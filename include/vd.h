@@ -179,10 +179,10 @@ vd_status vd_get_match(vd_ctx* ctx, int32_t* phi, int64_t cap, int64_t* n);     
  * side of the centre bucket grid in percent of the mean centre spacing
  * (25..400, default 100); ring0: sites beyond the tile reached by the first
  * round of the owner search (0..256, default 9); graph_blocks: the graph stage
- * (CSR, match, flips) as one block per instance in two launches (1; the
- * default for a single lattice of at most 2^21 sites) or as a chain of
- * grid-wide launches over all instances' rows and links (0; the default
- * otherwise). Applies from the next push;
+ * (CSR, match, flips) as one block per instance in two launches (1) or as a
+ * chain of grid-wide launches over all instances' rows and links, with the
+ * match on a second stream beside the owner, link and CSR kernels (0, the
+ * default). Applies from the next push;
  * synchronises the stream. The autotuner (paper_1607_00908_gb300/autotune.py)
  * times candidates and keeps the fastest per lattice-size and density class. */
 enum { VD_PATCH_8x8 = 0, VD_PATCH_16x8 = 1, VD_PATCH_32x8 = 2, VD_PATCH_16x16 = 3 };

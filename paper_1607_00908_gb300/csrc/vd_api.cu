@@ -87,6 +87,10 @@ struct vd_batch {
     bool any_masked = false;           // some instance has walls or obstacles
     int vpatch = VPATCH_8x8;           // patch layout of the owner kernel (tuning)
     int graph_inst = 0;                // graph stage with one block per instance (tuning)
+    // second stream of a step: the run-label pass, the overlap merge and the
+    // match run on it while the owner, link and CSR kernels run on s
+    cudaStream_t s2 = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     // field pointer tables (device) and their host mirrors
     const float** d_fields = nullptr;
     long long* d_pitches = nullptr;
@@ -139,9 +143,6 @@ struct vd_batch {
 // centre spacing, a first owner-search round reaching 9 sites beyond the tile
 static const int DEFAULT_BUCKET_PCT = 100;
 static const int DEFAULT_RING0 = 9;
-// a single lattice up to this many sites runs the graph stage as one block by
-// default (a 1024^2 frame: about a thousand rows and three thousand links)
-static const long long GRAPH_INST_MAX_SITES = 1ll << 21;
 
 static const int N_STAGES = 6;
 static const char* STAGE_NAMES[N_STAGES] = {
@@ -249,6 +250,10 @@ void mark(vd_batch* b, bool on) {
     if (e) cudaEventRecord(e, b->s);
 }
 
+void note_err(const Launch& L, cudaError_t e) {
+    if (e != cudaSuccess && L.err && *L.err == cudaSuccess) *L.err = e;
+}
+
 void enqueue_step(vd_batch* b, const Launch& L, bool timed) {
     launch_begin(L);
     mark(b, timed);
@@ -256,6 +261,27 @@ void enqueue_step(vd_batch* b, const Launch& L, bool timed) {
     mark(b, timed);
     launch_ccl_rest(L);
     mark(b, timed);
+    if (!timed && !L.graph_inst && b->s2) {
+        // after the bubble stage two independent chains: run labels ->
+        // overlap merge -> match on s2, owners -> links -> link merge -> CSR
+        // on s; the flips need both
+        Launch L2 = L;
+        L2.s = b->s2;
+        note_err(L, cudaEventRecord(b->ev_fork, L.s));
+        note_err(L, cudaStreamWaitEvent(b->s2, b->ev_fork, 0));
+        launch_labels(L2);
+        launch_merge_overlaps(L2);
+        launch_graph_match_chain(L2);
+        note_err(L, cudaEventRecord(b->ev_join, b->s2));
+        launch_voronoi(L);
+        launch_links(L);
+        launch_merge_edges(L);
+        launch_graph_csr_chain(L);
+        note_err(L, cudaStreamWaitEvent(L.s, b->ev_join, 0));
+        launch_graph_flips(L);
+        launch_finish(L);
+        return;
+    }
     launch_labels(L);
     mark(b, timed);
     launch_voronoi(L);
@@ -362,10 +388,10 @@ vd_status create_batch(const vd_config* cfgs, int n, vd_batch** out, bool sequen
         scan_items = std::max(scan_items, (long long)0);
     }
     scan_items = std::max(std::max(grp, comp), bucket);
-    // the graph stage runs as one block by default for a single small lattice
-    // (its rows and links take a few passes of a block; with many instances
-    // the grid-wide kernels are faster)
-    b->graph_inst = (n == 1 && max_sites <= GRAPH_INST_MAX_SITES) ? 1 : 0;
+    // the graph stage runs as grid-wide kernels by default: with the step
+    // forked into two streams they beat the one-block-per-instance form also
+    // for a single 1024^2 lattice; the autotuner tries both
+    b->graph_inst = 0;
     if (piece_cap >= (1ll << 31) || comp >= (1ll << 31) || edge >= (1ll << 30)) {
         delete b;
         return VD_ERR_INVALID;
@@ -471,6 +497,12 @@ vd_status create_batch(const vd_config* cfgs, int n, vd_batch** out, bool sequen
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     b->grid_items = 2 * sms;
+    if (cudaStreamCreateWithFlags(&b->s2, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&b->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        M.ok = false;
+    }
     std::vector<int> act(n);
     for (int i = 0; i < n; ++i) act[i] = i;
     build_table(b, act, b->all, true);
@@ -480,12 +512,18 @@ vd_status create_batch(const vd_config* cfgs, int n, vd_batch** out, bool sequen
     b->imported_at.assign(n, -1);
 
     if (!M.ok) {
+        if (b->s2) cudaStreamDestroy(b->s2);
+        if (b->ev_fork) cudaEventDestroy(b->ev_fork);
+        if (b->ev_join) cudaEventDestroy(b->ev_join);
         M.release();
         delete b;
         return VD_ERR_OOM;
     }
     chk(cudaStreamSynchronize(b->s));
     if (e != cudaSuccess) {
+        cudaStreamDestroy(b->s2);
+        cudaEventDestroy(b->ev_fork);
+        cudaEventDestroy(b->ev_join);
         M.release();
         delete b;
         return VD_ERR_CUDA;
@@ -1518,6 +1556,12 @@ vd_status vd_batch_destroy(vd_batch* b) {
         cudaStreamSynchronize(b->cs);
         cudaStreamDestroy(b->cs);
     }
+    if (b->s2) {
+        cudaStreamSynchronize(b->s2);
+        cudaStreamDestroy(b->s2);
+    }
+    if (b->ev_fork) cudaEventDestroy(b->ev_fork);
+    if (b->ev_join) cudaEventDestroy(b->ev_join);
     for (int k = 0; k < 2; ++k) {
         if (b->ev_staged[k]) cudaEventDestroy(b->ev_staged[k]);
         if (b->ev_read[k]) cudaEventDestroy(b->ev_read[k]);

@@ -892,6 +892,18 @@ void launch_graph_flips(const Launch& L) {
     if (L.events) launch_step(L, k_events, dim3(g), dim3(256), L.P, L.T);
 }
 
+// the CSR and match chains when they run on two forked streams (the prefix
+// arrays each writes are disjoint; K and K_past prefixes are final since the
+// bubble stage)
+void launch_graph_csr_chain(const Launch& L) {
+    launch_plan(L, 0, ends_bit(SCAN_DEG), pre_bit(PRE_E));
+    launch_graph_csr(L);
+}
+void launch_graph_match_chain(const Launch& L) {
+    launch_plan(L, 0, ENDS_NONE, pre_bit(PRE_O));
+    launch_graph_match(L);
+}
+
 void launch_graph_inst(const Launch& L) {
     launch_step(L, k_graph_inst_a, dim3(L.T.n_act), dim3(GI_THREADS), L.P, L.T);
     launch_step(L, k_graph_inst_b, dim3(L.T.n_act), dim3(GI_THREADS), L.P, L.T);

@@ -554,6 +554,10 @@ void launch_labels(const Launch& L);       // run labels + overlap histogram
 void launch_voronoi(const Launch& L);      // exact owner of every site
 void launch_links(const Launch& L);        // per-tile links from the owners
 void launch_merge_lists(const Launch& L);  // appended links/pairs -> hash tables
+void launch_merge_edges(const Launch& L);     // the links alone (forked step)
+void launch_merge_overlaps(const Launch& L);  // the overlap pairs alone (forked step)
+void launch_graph_csr_chain(const Launch& L);     // plan + CSR (forked step)
+void launch_graph_match_chain(const Launch& L);   // plan + match (forked step)
 // graph stage: prefixes of the merged lists, the now-frame CSR, the match,
 // the translated past CSR, the flips
 void launch_graph_prep(const Launch& L);

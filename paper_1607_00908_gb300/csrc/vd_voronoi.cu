@@ -706,14 +706,15 @@ __global__ __launch_bounds__(32 * LINK_WARPS) void k_links(Pools P, StepTable T)
 
 // appended links -> link hash (+ degrees); appended pairs -> overlap hash
 
-__global__ void k_merge_lists(Pools P, StepTable T) {
+// which: bit 0 the appended links, bit 1 the appended overlap pairs
+__global__ void k_merge_lists(Pools P, StepTable T, int which) {
     pdl_enter();
     __shared__ long long s_pe[SEG_CACHE], s_po[SEG_CACHE];
     __shared__ int s_act[SEG_CACHE];
     const int* act;
     const long long* pe = seg_table(pre_arr(T, PRE_EA), T.act, T.n_act, s_pe, s_act, &act);
     const long long* po = seg_table(pre_arr(T, PRE_OA), T.n_act, s_po);
-    const long long ne = pe[T.n_act], no = po[T.n_act];
+    const long long ne = (which & 1) ? pe[T.n_act] : 0, no = (which & 2) ? po[T.n_act] : 0;
     for (long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x; g < ne + no;
          g += (long long)gridDim.x * blockDim.x) {
         if (g < ne) {
@@ -734,7 +735,17 @@ __global__ void k_merge_lists(Pools P, StepTable T) {
 
 void launch_merge_lists(const Launch& L) {
     launch_plan(L, 0, ENDS_NONE);
-    launch_step(L, k_merge_lists, dim3(L.grid_wide), dim3(256), L.P, L.T);
+    launch_step(L, k_merge_lists, dim3(L.grid_wide), dim3(256), L.P, L.T, 3);
+}
+
+void launch_merge_edges(const Launch& L) {
+    launch_plan(L, 0, ENDS_NONE, pre_bit(PRE_EA));
+    launch_step(L, k_merge_lists, dim3(L.grid_wide), dim3(256), L.P, L.T, 1);
+}
+
+void launch_merge_overlaps(const Launch& L) {
+    launch_plan(L, 0, ENDS_NONE, pre_bit(PRE_OA));
+    launch_step(L, k_merge_lists, dim3(L.grid_wide), dim3(256), L.P, L.T, 2);
 }
 
 void launch_voronoi(const Launch& L) {
