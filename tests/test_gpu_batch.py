@@ -283,3 +283,29 @@ def test_batched_workload_every_instance_and_frame():
                 assert np.array_equal(ch[k], w[k]), (tag, k)
         del dev
     b.close()
+
+
+def test_many_instances_and_a_long_sequence():
+    """24 uneven lattices in one batch, and a 20-frame sequence pushed twice,
+    against the oracle frame by frame."""
+    rng = np.random.default_rng(5)
+    specs = [(int(rng.integers(40, 97)), int(rng.integers(40, 97)), float(rng.uniform(1.5, 3.5))) for _ in range(24)]
+    seqs = [frames_for(ly, s, 200 + k, 2, Lx=lx) for k, (lx, ly, s) in enumerate(specs)]
+    b = vd.Batch([(lx, ly) for lx, ly, _ in specs])
+    refs = [O.Detector(lx, ly, voronoi="brute") for lx, ly, _ in specs]
+    for f in range(2):
+        b.push([torch.from_numpy(seq[f]).cuda() for seq in seqs])
+        for i, ref in enumerate(refs):
+            check(b, i, ref.push(seqs[i][f]), f"inst {i} frame {f}")
+    b.close()
+    L, n_seq = 80, 20
+    frames = frames_for(L, 2.5, 321, 2 * n_seq)
+    ref = O.Detector(L, L, voronoi="brute")
+    want = [ref.push(F) for F in frames]
+    b = vd.Batch([(L, L)], sequence=n_seq)
+    dev = [torch.from_numpy(F).cuda() for F in frames]
+    for p in range(2):
+        b.push(dev[p * n_seq:(p + 1) * n_seq])
+        for i in range(n_seq):
+            check(b, i, want[p * n_seq + i], f"seq push {p} frame {i}")
+    b.close()
