@@ -36,8 +36,47 @@ __device__ __forceinline__ void for_items(const StepTable& T, int which, F f) {
 // ---------------------------------------------------------------------------
 // step begin / finish
 // ---------------------------------------------------------------------------
+// Hash slots are returned to empty by the kernels that read the listed ones;
+// a frame whose link or overlap list overflowed left keys that were never
+// listed. The first kernel of the next step clears those instances' tables
+// (whole block per instance; only after an overflow).
+constexpr int CLEAR_LIST = 64;
+__device__ void clear_overflowed_hashes(const Pools& P, const StepTable& T) {
+    __shared__ int s_list[CLEAR_LIST];
+    __shared__ int s_n;
+    if (!*(volatile int*)&P.g->lists_over) return;   // the usual case: nothing overflowed
+    if (threadIdx.x == 0) s_n = 0;
+    __syncthreads();
+    for (int a = threadIdx.x; a < T.n_act; a += blockDim.x) {
+        const int inst = T.act[a];
+        if (P.st[inst].err & (ERR_EDGE_CAP | ERR_OVL_CAP)) {
+            const int k = atomicAdd(&s_n, 1);
+            if (k < CLEAR_LIST) s_list[k] = inst;
+        }
+    }
+    __syncthreads();
+    const int n = s_n;
+    // more overflowed instances than the list holds: clear every active one
+    const int m = n > CLEAR_LIST ? T.n_act : n;
+    for (int i = 0; i < m; ++i) {
+        const int inst = n > CLEAR_LIST ? T.act[i] : s_list[i];
+        const InstDesc& D = P.desc[inst];
+        const int e = P.st[inst].err;
+        if (e & ERR_EDGE_CAP)
+            for (long long h = threadIdx.x; h <= D.ehash_mask; h += blockDim.x) P.ehash[D.ehash_off + h] = EMPTY_KEY;
+        if (e & ERR_OVL_CAP)
+            for (long long h = threadIdx.x; h <= D.ohash_mask; h += blockDim.x) {
+                P.ohash[D.ohash_off + h] = EMPTY_KEY;
+                P.oval[D.ohash_off + h] = 0;
+            }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) atomicSub(&P.g->lists_over, n);   // the active ones among them are clean now
+}
+
 __global__ void k_step_begin(Pools P, StepTable T) {
     pdl_enter();
+    clear_overflowed_hashes(P, T);   // the launch is one block
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         P.g->n_pieces = 0;
         P.g->n_wide = 0;
@@ -225,6 +264,10 @@ constexpr int RLOC = 32;   // rows up to this length are handled in a local arra
 
 __device__ __forceinline__ void csr_sort_item(const Pools& P, int inst, long long a) {
     const InstDesc& D = P.desc[inst];
+    // the scatter returned the degree counts of the listed links to zero;
+    // links past the list's capacity (an overflowed frame) were counted but
+    // not listed, so the row's count is cleared here for the next step
+    P.deg[D.comp_off + a] = 0;
     const int now = P.st[inst].slot ^ 1;
     const int* ro = P.rowoff[now] + D.comp_off;
     const int cap = 2 * D.edge_cap;

@@ -158,6 +158,9 @@ struct Globals {
     int chk_id;
     int dbg_chk;
     long long chk_index;
+    // instances whose link or overlap list overflowed: their hashes keep
+    // unlisted keys, which the first kernel of their next step clears
+    int lists_over;
 };
 
 // ---------------------------------------------------------------------------
@@ -436,13 +439,14 @@ __device__ __forceinline__ void ovl_global_insert(const Pools& P, const InstDesc
             if (k == EMPTY_KEY) {
                 const int idx = warp_fetch_inc(&P.st[inst].n_ovl);
                 if (idx < D.ovl_cap) P.olist[D.ovl_off + idx] = (int)h;
-                else atomicOr(&P.st[inst].err, ERR_OVL_CAP);
+                else if (!(atomicOr(&P.st[inst].err, ERR_OVL_CAP) & (ERR_EDGE_CAP | ERR_OVL_CAP)))
+                    atomicAdd(&P.g->lists_over, 1);
             }
             return;
         }
         h = (h + 1) & mask;
     }
-    atomicOr(&P.st[inst].err, ERR_OVL_CAP);
+    if (!(atomicOr(&P.st[inst].err, ERR_OVL_CAP) & (ERR_EDGE_CAP | ERR_OVL_CAP))) atomicAdd(&P.g->lists_over, 1);
 }
 
 

@@ -76,8 +76,11 @@ __device__ __forceinline__ void edge_global_insert(const Pools& P, const InstDes
         const unsigned long long k = atomicCAS(&H[h], EMPTY_KEY, key);
         if (k == EMPTY_KEY) {
             const int idx = warp_fetch_inc(&P.st[inst].n_edge_list);
-            if (idx < D.edge_cap) P.elist[D.edge_off + idx] = (int)h;
-            else atomicOr(&P.st[inst].err, ERR_EDGE_CAP);
+            if (idx < D.edge_cap) {
+                P.elist[D.edge_off + idx] = (int)h;
+            } else if (!(atomicOr(&P.st[inst].err, ERR_EDGE_CAP) & (ERR_EDGE_CAP | ERR_OVL_CAP))) {
+                atomicAdd(&P.g->lists_over, 1);
+            }
             atomicAdd(&P.deg[D.comp_off + (int)(key >> 32)], 1);
             atomicAdd(&P.deg[D.comp_off + (int)(key & 0xffffffffu)], 1);
             return;
@@ -85,7 +88,7 @@ __device__ __forceinline__ void edge_global_insert(const Pools& P, const InstDes
         if (k == key) return;
         h = (h + 1) & mask;
     }
-    atomicOr(&P.st[inst].err, ERR_EDGE_CAP);
+    if (!(atomicOr(&P.st[inst].err, ERR_EDGE_CAP) & (ERR_EDGE_CAP | ERR_OVL_CAP))) atomicAdd(&P.g->lists_over, 1);
 }
 
 

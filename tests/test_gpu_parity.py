@@ -219,6 +219,30 @@ def test_capacity_overflow_is_reported():
     assert det.counts()[0] == 1
 
 
+def test_link_capacity_overflow_then_exact_frames():
+    """A frame with more links than max_edges reports VD_ERR_CAPACITY; the
+    frames after it (with fewer links) are exact in every output: no count
+    of the overflowed frame carries over into their adjacency."""
+    L = 128
+    dense = I.smoothed_noise(L, L, 1.5, seed=3)
+    sparse = list(I.noise_frames(L, 5.0, 2, 0.02, seed=4))
+    ref = O.Detector(L, L, voronoi="brute")
+    r_dense = ref.push(dense)
+    few = [ref.push(F) for F in sparse]
+    cap = max(len(r["edges"]) for r in few) + 8
+    assert len(r_dense["edges"]) > cap, "the dense frame must overflow the link capacity"
+    det = vd.Detector(L, L, max_edges=cap)
+    det.push(torch.from_numpy(dense).cuda())
+    with pytest.raises(vd.VdError) as e:
+        det.edges()
+    assert e.value.status == vd.VD_ERR_CAPACITY
+    for f, (F, r) in enumerate(zip(sparse, few)):
+        det.push(torch.from_numpy(F).cuda())
+        what = ("labels", "centroids", "owners", "edges") if f == 0 else ("labels", "centroids", "owners", "edges", "changes")
+        check_frame(det, r, what=what, tag=f"after overflow, frame {f}")
+    det.close()
+
+
 def test_event_classes_with_boundary_points():
     """Few large bubbles (64 x 64, sigma 6): the digital link graph of frame 1
     is not a full triangulation of the torus, so some active labels are
