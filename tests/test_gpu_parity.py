@@ -243,6 +243,33 @@ def test_link_capacity_overflow_then_exact_frames():
     det.close()
 
 
+def test_overlap_capacity_overflow_then_exact_frames():
+    """20 horizontal stripes followed by 20 vertical ones overlap in 400
+    (past, now) pairs, more than the overlap list of a context capped at 100
+    bubbles holds (2 * 100 + 64): that frame reports VD_ERR_CAPACITY, and the
+    frames after it are exact again."""
+    L = 80
+    horiz = np.zeros((L, L), np.float32)
+    horiz[(np.arange(L) % 4) < 2, :] = 1.0
+    vert = np.ascontiguousarray(horiz.T)
+    blobs = list(I.noise_frames(L, 3.0, 2, 0.02, seed=8))
+    frames = [horiz, vert] + blobs
+    ref = O.Detector(L, L, voronoi="brute")
+    want = [ref.push(F) for F in frames]
+    det = vd.Detector(L, L, max_components=100)
+    for f, (F, r) in enumerate(zip(frames, want)):
+        det.push(torch.from_numpy(F).cuda())
+        if f == 1:
+            with pytest.raises(vd.VdError) as e:
+                det.changes()
+            assert e.value.status == vd.VD_ERR_CAPACITY
+            continue
+        what = ("labels", "centroids", "owners", "edges") if f == 2 else ("labels", "centroids", "owners", "edges",
+                                                                          "changes")
+        check_frame(det, r, what=what, tag=f"frame {f}")
+    det.close()
+
+
 def test_event_classes_with_boundary_points():
     """Few large bubbles (64 x 64, sigma 6): the digital link graph of frame 1
     is not a full triangulation of the torus, so some active labels are
