@@ -1019,6 +1019,23 @@ vd_status import_state(vd_batch* b, int i, const void* buf, int64_t n_bytes) {
     st.n_matched = 0;
     st.n_break = 0;
     st.n_arise = 0;
+    if (st.err & (ERR_EDGE_CAP | ERR_OVL_CAP)) {
+        // the instance's last frame overflowed a list: its hash tables keep
+        // unlisted keys that its next step would have cleared; clear them here
+        // and take it off the count of such instances
+        const InstDesc& Di = b->desc[i];
+        if (e == cudaSuccess && (st.err & ERR_EDGE_CAP))
+            e = cudaMemsetAsync(P.ehash + Di.ehash_off, 0xff, sizeof(unsigned long long) * (Di.ehash_mask + 1ll), b->s);
+        if (e == cudaSuccess && (st.err & ERR_OVL_CAP))
+            e = cudaMemsetAsync(P.ohash + Di.ohash_off, 0xff, sizeof(unsigned long long) * (Di.ohash_mask + 1ll), b->s);
+        if (e == cudaSuccess && (st.err & ERR_OVL_CAP))
+            e = cudaMemsetAsync(P.oval + Di.ohash_off, 0, sizeof(unsigned) * (Di.ohash_mask + 1ll), b->s);
+        int over = 0;
+        if (e == cudaSuccess) e = cudaStreamSynchronize(b->s);
+        if (e == cudaSuccess) e = cudaMemcpy(&over, &P.g->lists_over, sizeof(int), cudaMemcpyDeviceToHost);
+        over = over > 0 ? over - 1 : 0;
+        if (e == cudaSuccess) e = cudaMemcpy(&P.g->lists_over, &over, sizeof(int), cudaMemcpyHostToDevice);
+    }
     st.err = 0;
     if (e == cudaSuccess) e = cudaMemcpyAsync(P.st + i, &st, sizeof(InstState), cudaMemcpyHostToDevice, b->s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->s);

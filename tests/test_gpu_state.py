@@ -178,3 +178,31 @@ def test_c1_checkpoint_mid_sequence():
         _oracle_changes_equal(b.changes(), r, f"c1 frame {f}")
         assert np.array_equal(b.edges(), r["edges"])
     b.close()
+
+
+def test_import_into_a_context_whose_last_frame_overflowed():
+    """A context whose last frame overflowed its link list (its link hash
+    still holds unlisted keys) imports a checkpoint: the frames after it
+    equal the oracle, changes included."""
+    L = 128
+    dense = I.smoothed_noise(L, L, 1.5, seed=3)
+    sparse = list(I.noise_frames(L, 5.0, 3, 0.02, seed=4))
+    ref = O.Detector(L, L, voronoi="brute")
+    want = [ref.push(F) for F in sparse]
+    cap = max(len(r["edges"]) for r in want) + 8
+    a = vd.Detector(L, L)
+    a.push(torch.from_numpy(sparse[0]).cuda())
+    blob = a.export_state()
+    a.close()
+    b = vd.Detector(L, L, max_edges=cap)
+    b.push(torch.from_numpy(dense).cuda())
+    with pytest.raises(vd.VdError) as e:
+        b.edges()
+    assert e.value.status == vd.VD_ERR_CAPACITY
+    b.import_state(blob)
+    for f in (1, 2):
+        b.push(torch.from_numpy(sparse[f]).cuda())
+        assert np.array_equal(b.labels(), want[f]["labels"]), f
+        assert np.array_equal(b.edges(), want[f]["edges"]), f
+        _oracle_changes_equal(b.changes(), want[f], f"frame {f}")
+    b.close()
