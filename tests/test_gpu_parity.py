@@ -270,6 +270,29 @@ def test_overlap_capacity_overflow_then_exact_frames():
     det.close()
 
 
+def test_piece_pool_overflow_then_exact_frames():
+    """A 512^2 checkerboard has 131,072 one-site bubbles: more tile pieces
+    than the step's piece pool holds (N / 8 + 16 per tile above 65,536 sites)
+    and more bubbles than the default capacity. The frame reports
+    VD_ERR_CAPACITY; the frames after it are exact in every output."""
+    L = 512
+    checker = ((np.indices((L, L)).sum(0) % 2) == 0).astype(np.float32)
+    frames = list(I.noise_frames(L, 4.0, 2, 0.01, seed=12))
+    ref = O.Detector(L, L)
+    want = [ref.push(F) for F in frames]
+    det = vd.Detector(L, L)
+    det.push(torch.from_numpy(checker).cuda())
+    with pytest.raises(vd.VdError) as e:
+        det.labels()
+    assert e.value.status == vd.VD_ERR_CAPACITY
+    for f, (F, r) in enumerate(zip(frames, want)):
+        det.push(torch.from_numpy(F).cuda())
+        what = ("labels", "centroids", "owners", "edges") if f == 0 else ("labels", "centroids", "owners", "edges",
+                                                                          "changes")
+        check_frame(det, r, what=what, tag=f"after overflow, frame {f}")
+    det.close()
+
+
 def test_event_classes_with_boundary_points():
     """Few large bubbles (64 x 64, sigma 6): the digital link graph of frame 1
     is not a full triangulation of the torus, so some active labels are
