@@ -35,7 +35,10 @@ SUBSET = " or ".join((
     "test_tiny_lattices", "test_pitched_field", "test_c1_frames", "test_capacity_overflow_is_reported",
     "test_event_classes_with_boundary_points", "test_centroid_match_sequences", "test_eight_connectivity",
     "test_vertex_link_rule", "test_walls_and_obstacles", "test_uneven_batch_matches_per_instance_oracle",
-    "test_batch_with_mixed_options", "test_frame_sequence_matches_oracle",
+    "test_batch_with_mixed_options", "test_frame_sequence_matches_oracle", "overflow_then_exact_frames",
+    "test_many_instances_and_a_long_sequence", "test_every_tuning_gives_the_oracle_result",
+    "test_graph_stage_forms_give_the_oracle_result", "test_resumed_context_equals_uninterrupted_run_and_oracle",
+    "test_import_into_a_context_whose_last_frame_overflowed",
 ))
 
 
@@ -47,12 +50,13 @@ def _child(args, timeout):
 
 @pytest.mark.skipif(CHECKED, reason="already running under the checked build")
 def test_parity_suite_under_the_checked_build():
-    r = _child(["-m", "pytest", "tests/test_gpu_parity.py", "tests/test_gpu_batch.py", "tests/test_gpu_checked.py",
-                "-m", "gpu", "-q", "-x", "-p", "no:cacheprovider", "-k", SUBSET + " or test_loaded_library"], 1800)
+    r = _child(["-m", "pytest", "tests/test_gpu_parity.py", "tests/test_gpu_batch.py", "tests/test_gpu_tuning.py",
+                "tests/test_gpu_state.py", "tests/test_gpu_checked.py", "-m", "gpu", "-q", "-x", "-p",
+                "no:cacheprovider", "-k", SUBSET + " or test_loaded_library"], 1800)
     tail = (r.stdout + r.stderr)[-3000:]
     assert r.returncode == 0, tail
     m = re.search(r"(\d+) passed", r.stdout)
-    assert m and int(m.group(1)) >= 35 and " failed" not in r.stdout, tail
+    assert m and int(m.group(1)) >= 60 and " failed" not in r.stdout, tail
 
 
 def test_loaded_library():
