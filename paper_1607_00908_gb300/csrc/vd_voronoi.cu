@@ -182,7 +182,7 @@ __global__ __launch_bounds__(32 * VWARPS, VLayout<PW, PH>::MINB) void k_voronoi(
     pdl_enter();
     __shared__ float2 s_cf[VWARPS][WSCAN];
     __shared__ int s_id[VWARPS][WSCAN];
-    __shared__ int s_kept[VWARPS][NP][KMAX];
+    __shared__ __align__(16) int s_kept[VWARPS][NP][KMAX];
     __shared__ int s_nk[VWARPS][NP];
     __shared__ int s_tpre[SEG_CACHE];
 
@@ -367,6 +367,31 @@ __global__ __launch_bounds__(32 * VWARPS, VLayout<PW, PH>::MINB) void k_voronoi(
             if (sub == 0) s_nk[warp][pp] = nk;
         }
         __syncwarp();
+        // ---- per-patch set-up of the site phase, once per patch (in the
+        // unused part of its kept row) instead of once per lane: the owner of
+        // a one-centre patch; for two centres their exact bisector,
+        // d(s,c1)^2 - d(s,c2)^2 = 2 s.(c2 - c1) + |c1|^2 - |c2|^2, as its value
+        // at the patch origin and its steps per site along x and y (int64,
+        // tile-relative minimum images), and the two labels ----
+        if (sub == 0) {
+            const int nk = s_nk[warp][pp];
+            int* kl = s_kept[warp][pp];
+            if (nk == 1) {
+                kl[2] = ids[kl[0]];
+            } else if (nk == 2) {
+                const int e1 = kl[0], e2 = kl[1];
+                const long long c1x = list_int(cfs[e1].x), c1y = list_int(cfs[e1].y);
+                const long long c2x = list_int(cfs[e2].x), c2y = list_int(cfs[e2].y);
+                const long long axq = 2 * (c2x - c1x) * Q, ayq = 2 * (c2y - c1y) * Q;
+                long long* co = reinterpret_cast<long long*>(kl + 4);
+                co[0] = axq * ppx + ayq * ppy + (c1x * c1x + c1y * c1y) - (c2x * c2x + c2y * c2y);
+                co[1] = axq;
+                co[2] = ayq;
+                kl[2] = ids[e1];
+                kl[3] = ids[e2];
+            }
+        }
+        __syncwarp();
         // ---- 3. nearest kept centre for every site, patch by patch ----
         int* ownT = own + (long long)y0 * Lx + x0;   // rows of the tile: row offsets below 2^26
         const int c = lane % PW, rb = (lane / PW) * SPL;
@@ -382,21 +407,16 @@ __global__ __launch_bounds__(32 * VWARPS, VLayout<PW, PH>::MINB) void k_voronoi(
                 int o[SPL];
                 if (nk == 1) {
                     // one candidate owns the whole patch
-                    const int o1 = ids[kk[0]];
+                    const int o1 = kk[2];
 #pragma unroll
                     for (int k = 0; k < SPL; ++k) o[k] = o1;
                 } else if (nk == 2) {
-                    // the bisector decides: d(s,c1)^2 - d(s,c2)^2 = 2 s.(c2 - c1) + |c1|^2 - |c2|^2,
-                    // exact in int64 (tile-relative minimum images), ties to the smaller label
-                    const int e1 = kk[0], e2 = kk[1];
-                    const long long c1x = list_int(cfs[e1].x), c1y = list_int(cfs[e1].y);
-                    const long long c2x = list_int(cfs[e2].x), c2y = list_int(cfs[e2].y);
-                    const int i1 = ids[e1], i2 = ids[e2];
+                    // the bisector decides (set up above), ties to the smaller label
+                    const long long* co = reinterpret_cast<const long long*>(kk + 4);
+                    const int i1 = kk[2], i2 = kk[3];
                     const int itie = i1 < i2 ? i1 : i2;
-                    const long long ax = 2 * (c2x - c1x), ay = 2 * (c2y - c1y);
-                    long long dv = ax * ((long long)Q * sx) + ay * ((long long)Q * (pyo + rb)) +
-                                   (c1x * c1x + c1y * c1y) - (c2x * c2x + c2y * c2y);
-                    const long long step = ay * Q;
+                    const long long step = co[2];
+                    long long dv = co[0] + co[1] * c + step * rb;
 #pragma unroll
                     for (int k = 0; k < SPL; ++k) {
                         o[k] = dv < 0 ? i1 : (dv > 0 ? i2 : itie);
