@@ -58,12 +58,12 @@ METRIC_BYTES_PER_SITE = 16.0
 # roofline.traffic. The owner stage's entry depends on its patch layout
 # (VD_PATCH_*); a stage or layout not captured, or whose kernels changed since
 # the capture, reports null.
-TRAFFIC_BYTES_PER_SITE = {0: 4.146, 2: 0.278, 3: {0: 2.866}, 4: 4.348}
+TRAFFIC_BYTES_PER_SITE = {0: 4.146, 2: 0.278, 3: {0: 2.869}, 4: 4.338}
 
 # Issue-slot use (smsp__issue_active, % of peak) of the same kernels in the
 # same capture: the kernels are bound by instruction issue or latency, not by
 # DRAM, and this says how close to the issue limit they run.
-ISSUE_ACTIVE_PCT = {0: 50.1, 2: 48.3, 3: {0: 73.0}, 4: 41.0}
+ISSUE_ACTIVE_PCT = {0: 50.0, 2: 48.3, 3: {0: 72.9}, 4: 40.7}
 
 
 def per_stage(table, stage, patch):
