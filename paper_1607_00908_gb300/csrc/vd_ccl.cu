@@ -134,13 +134,58 @@ __device__ __forceinline__ int run_piece(const UfSmem& T, int id, int* root) {
     return -2 - T.par[SW(v)];
 }
 
-// union-find over runs; lane r owns row r; m = this lane's row mask, mu = row r-1.
-// 4-connectivity joins runs of rows r-1 and r that share a column; with
-// 8-connectivity a run of row r-1 widened by one column on each side joins
-// every run of row r it meets.
+// The pairs (j, ju) of touching runs between row r (run j) and row r-1 (run
+// ju) of a tile, for lane r > 0; f(j, ju) is called for each. 4-connectivity
+// joins runs that share a column (one pair per segment of m & mu, in column
+// order); with 8-connectivity a run of row r-1 widened by one column on each
+// side joins every run of row r it meets.
+template <class F>
+__device__ __forceinline__ void touching_pairs(unsigned long long m, unsigned long long mu, bool conn8, F&& f) {
+    const unsigned long long S = run_starts(m), Su = run_starts(mu);
+    if (!conn8) {
+        unsigned long long os = run_starts(m & mu);
+        while (os) {
+            const int c = __ffsll(os) - 1;
+            os &= os - 1;
+            f(run_index(S, c), run_index(Su, c));
+        }
+    } else {
+        unsigned long long tu = Su;
+        int ju = 0;
+        while (tu) {
+            const int cu = __ffsll(tu) - 1;
+            tu &= tu - 1;
+            const int len = run_length(mu, cu);
+            const unsigned long long ru = (len >= 64 ? ~0ull : ((1ull << len) - 1ull)) << cu;
+            unsigned long long hs = run_starts(m & (ru | (ru << 1) | (ru >> 1)));
+            while (hs) {
+                const int c = __ffsll(hs) - 1;
+                hs &= hs - 1;
+                f(run_index(S, c), ju);
+            }
+            ++ju;
+        }
+    }
+}
+
+// Union-find over the runs of a tile; lane r owns row r, m = its row mask.
+// On return the parent slot of every run holds its root, the smallest run id
+// of its component (so roots follow raster order).
+//  1. every run of row r > 0 takes as parent the first run of row r-1 it
+//     touches: a forest in which each parent lies one row up, so each tree's
+//     root is its smallest id;
+//  2. pointer jumping (every run's parent becomes its grandparent, rounds
+//     separated by warp barriers, until no parent changes) makes every
+//     parent a tree root in about log2(rows) rounds, where a find per run
+//     would walk one row per step;
+//  3. the remaining touching pairs join their trees (union by smaller root);
+//  4. a find per run (tree root, then the few joined roots) flattens.
+// Reads in step 2 may see another lane's newer value, which is an ancestor
+// too, so the rounds only end sooner.
 __device__ void warp_runs_uf(UfSmem& T, unsigned long long m, bool conn8) {
     const int r = threadIdx.x & 31;
     const unsigned long long S = run_starts(m);
+    const int nr = __popcll(S);
     {
         unsigned long long t = S;
         int j = 0;
@@ -153,36 +198,43 @@ __device__ void warp_runs_uf(UfSmem& T, unsigned long long m, bool conn8) {
         }
     }
     const unsigned long long mu = __shfl_up_sync(0xffffffffu, m, 1);
-    __syncwarp();
+    unsigned linked = 0;    // runs of this row with a parent in row r-1
+    bool more = false;      // a run of this row touches a second run above
     if (r > 0) {
-        const unsigned long long Su = run_starts(mu);
-        if (!conn8) {
-            unsigned long long os = run_starts(m & mu);
-            while (os) {
-                const int c = __ffsll(os) - 1;
-                os &= os - 1;
-                runion(T.par, r * 32 + run_index(S, c), (r - 1) * 32 + run_index(Su, c));
+        touching_pairs(m, mu, conn8, [&](int j, int ju) {
+            if ((linked >> j) & 1u) {
+                more = true;
+            } else {
+                linked |= 1u << j;
+                T.par[SW(r * 32 + j)] = (r - 1) * 32 + ju;
             }
-        } else {
-            unsigned long long tu = Su;
-            int ju = 0;
-            while (tu) {
-                const int cu = __ffsll(tu) - 1;
-                tu &= tu - 1;
-                const int len = run_length(mu, cu);
-                const unsigned long long ru = (len >= 64 ? ~0ull : ((1ull << len) - 1ull)) << cu;
-                unsigned long long hs = run_starts(m & (ru | (ru << 1) | (ru >> 1)));
-                while (hs) {
-                    const int c = __ffsll(hs) - 1;
-                    hs &= hs - 1;
-                    runion(T.par, r * 32 + run_index(S, c), (r - 1) * 32 + ju);
-                }
-                ++ju;
+        });
+    }
+    for (;;) {
+        __syncwarp();
+        bool changed = false;
+        unsigned t = linked;
+        while (t) {
+            const int x = r * 32 + __ffs(t) - 1;
+            t &= t - 1;
+            const int p = T.par[SW(x)];
+            const int pp = T.par[SW(p)];
+            if (pp != p) {
+                T.par[SW(x)] = pp;
+                changed = true;
             }
         }
+        if (!__any_sync(0xffffffffu, changed)) break;
     }
     __syncwarp();
-    const int nr = __popcll(S);
+    if (more) {
+        unsigned seen = 0;
+        touching_pairs(m, mu, conn8, [&](int j, int ju) {
+            if ((seen >> j) & 1u) runion(T.par, r * 32 + j, (r - 1) * 32 + ju);
+            seen |= 1u << j;
+        });
+    }
+    __syncwarp();
     for (int j = 0; j < nr; ++j) T.par[SW(r * 32 + j)] = rfind(T.par, r * 32 + j);
     __syncwarp();
 }
@@ -242,32 +294,59 @@ __device__ __forceinline__ bool is_fg(float v, float thr, int pol) {
 }
 
 constexpr int CCL_WARPS = 4;    // tiles per block in pass A
+constexpr int PCAP = 64;        // pieces per tile summed in shared memory
 
-// Threshold (Section 3.1) of one 64-site tile row, read straight from the
-// field: 16-byte streaming loads when the row is aligned and complete, else
-// scalar loads. Bit i of the mask is site (x0 + i, y); bits past Lx are 0.
-__device__ __forceinline__ unsigned long long threshold_row(const float* f, int n, float thr, int pol) {
-    unsigned long long m = 0;
-    if (n == TW && ((reinterpret_cast<uintptr_t>(f) & 15u) == 0)) {
-        const float4* f4 = reinterpret_cast<const float4*>(f);
+// Threshold (Section 3.1) of a 64 x 32 tile, read straight from the field
+// with coalesced 16-byte loads: one warp load covers two tile rows (lanes
+// 0-15 row 2s, lanes 16-31 row 2s+1, four columns per lane); each 8-lane group
+// holds one 32-bit word of a row, or-reduced across the warp, and the row's
+// lane keeps the 64-bit mask. Eight row pairs are read at a time. Bit i of
+// row y's mask is site (x0 + i, y0 + y); rows at or past nrow and columns at
+// or past ncol are 0. Rows that are not 16-byte aligned, or a tile cut by the
+// domain edge, take scalar loads.
+__device__ __forceinline__ unsigned long long threshold_tile(const float* f0, long long pitch, int nrow, int ncol,
+                                                             float thr, int pol) {
+    const int lane = threadIdx.x & 31;
+    const int hr = lane >> 4, c = 4 * (lane & 15), g = lane >> 3, sh = 4 * (lane & 7);
+    const bool vec = ncol == TW && ((reinterpret_cast<uintptr_t>(f0) | (uintptr_t)(pitch * 4)) & 15u) == 0;
+    const unsigned cm = ncol >= c + 4 ? 0xFu : (ncol > c ? (1u << (ncol - c)) - 1u : 0u);
+    unsigned long long my_m = 0;
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {   // two halves of 8 loads in flight
-            float4 v[8];
+    for (int sb = 0; sb < TH / 2; sb += 8) {
+        float4 v[8];
 #pragma unroll
-            for (int i = 0; i < 8; ++i) v[i] = __ldcs(f4 + 8 * h + i);
-            unsigned bits = 0;
-#pragma unroll
-            for (int i = 0; i < 8; ++i)
-                bits |= ((unsigned)is_fg(v[i].x, thr, pol) | ((unsigned)is_fg(v[i].y, thr, pol) << 1) |
-                         ((unsigned)is_fg(v[i].z, thr, pol) << 2) | ((unsigned)is_fg(v[i].w, thr, pol) << 3))
-                        << (4 * i);
-            m |= (unsigned long long)bits << (32 * h);
+        for (int i = 0; i < 8; ++i) {
+            v[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+            const int y = 2 * (sb + i) + hr;
+            if (y < nrow) {
+                const float* p = f0 + (long long)y * pitch + c;
+                if (vec) {
+                    v[i] = __ldcs(reinterpret_cast<const float4*>(p));
+                } else {
+                    if (cm & 1u) v[i].x = __ldcs(p);
+                    if (cm & 2u) v[i].y = __ldcs(p + 1);
+                    if (cm & 4u) v[i].z = __ldcs(p + 2);
+                    if (cm & 8u) v[i].w = __ldcs(p + 3);
+                }
+            }
         }
-    } else {
-        for (int i = 0; i < n; ++i)
-            if (is_fg(__ldcs(f + i), thr, pol)) m |= 1ull << i;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const int y = 2 * (sb + i) + hr;
+            const unsigned nib = y < nrow ? ((unsigned)is_fg(v[i].x, thr, pol) | ((unsigned)is_fg(v[i].y, thr, pol) << 1) |
+                                             ((unsigned)is_fg(v[i].z, thr, pol) << 2) |
+                                             ((unsigned)is_fg(v[i].w, thr, pol) << 3)) & cm
+                                          : 0u;
+            const unsigned part = nib << sh;
+            const unsigned r0 = __reduce_or_sync(0xffffffffu, g == 0 ? part : 0u);
+            const unsigned r1 = __reduce_or_sync(0xffffffffu, g == 1 ? part : 0u);
+            const unsigned r2 = __reduce_or_sync(0xffffffffu, g == 2 ? part : 0u);
+            const unsigned r3 = __reduce_or_sync(0xffffffffu, g == 3 ? part : 0u);
+            if (lane == 2 * (sb + i)) my_m = ((unsigned long long)r1 << 32) | r0;
+            if (lane == 2 * (sb + i) + 1) my_m = ((unsigned long long)r3 << 32) | r2;
+        }
     }
-    return m;
+    return my_m;
 }
 
 // ---------------------------------------------------------------------------
@@ -276,11 +355,12 @@ __device__ __forceinline__ unsigned long long threshold_row(const float* f, int 
 __global__ __launch_bounds__(32 * CCL_WARPS, 8) void k_ccl_tiles(Pools P, StepTable T) {
     pdl_enter();
     __shared__ UfSmem s_tile[CCL_WARPS];
+    __shared__ int4 s_pc[CCL_WARPS][PCAP];   // per piece: size, row sum, column sum, first site
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int b = blockIdx.x * CCL_WARPS + w;
     if (b >= T.tileA_pre[T.n_act]) return;
     UfSmem& TS = s_tile[w];
-    const int a = seg_of_int(T.tileA_pre, T.n_act, b);
+    const int a = warp_seg_of_int(T.tileA_pre, T.n_act, b);
     const int inst = T.act[a];
     const InstDesc& D = P.desc[inst];
     const InstState& S = P.st[inst];
@@ -289,17 +369,18 @@ __global__ __launch_bounds__(32 * CCL_WARPS, 8) void k_ccl_tiles(Pools P, StepTa
     const int x0 = tx * TW, y0 = ty * TH;
     const int Lx = D.Lx, Ly = D.Ly;
 
-    // 1. threshold: lane r reads tile row r of the field and stores its
-    //    foreground words (kept for the run-label pass and the next frame)
-    unsigned long long my_m = 0;
+    // 1. threshold (coalesced, one tile row per step; lane r keeps row r),
+    //    then lane r stores row r's foreground words (kept for the run-label
+    //    pass and the next frame). The field covers the domain only (a
+    //    bounded axis runs with twice its length; the second half is never a
+    //    bubble).
+    unsigned long long my_m =
+        threshold_tile(S.field + (long long)y0 * S.pitch + x0, S.pitch, min(TH, min(Ly, D.uLy) - y0),
+                       min(TW, D.uLx - x0), D.thr, D.pol);
     {
         const int y = y0 + lane;
         if (y < Ly) {
             const int n = min(TW, Lx - x0);
-            // the field covers the domain only (a bounded axis runs with twice
-            // its length; the second half is never a bubble)
-            const int nu = min(n, D.uLx - x0);
-            if (y < D.uLy && nu > 0) my_m = threshold_row(S.field + (long long)y * S.pitch + x0, nu, D.thr, D.pol);
             unsigned* row = P.fgbits[S.slot ^ 1] + D.word_off + (long long)y * D.wpr + (x0 >> 5);
             if (D.masked) {   // obstacle sites are never in a bubble
                 const unsigned* ob = P.obst + D.word_off + (long long)y * D.wpr + (x0 >> 5);
@@ -316,15 +397,105 @@ __global__ __launch_bounds__(32 * CCL_WARPS, 8) void k_ccl_tiles(Pools P, StepTa
     // 2. union-find over runs
     warp_runs_uf(TS, my_m, D.conn8 != 0);
 
-    // 3. roots in raster order -> piece ids; a root's parent slot then holds
-    //    -2 - (its piece id), so every run reaches its piece in two steps
+    // 3. pieces: the tile's roots in raster order are its pieces 0 .. m_tot-1,
+    //    numbered in the piece pool from a base taken with one atomic add
     const unsigned long long S0 = run_starts(my_m);
     const int nr = __popcll(S0);
     int rbase, m_tot;
     const unsigned R = warp_roots(TS, my_m, &rbase, &m_tot);
     int pbase = 0;
+    if (lane == 0) pbase = atomicAdd(&P.g->n_pieces, m_tot);
+    const int ncols = min(TW, Lx - x0), nrows = min(TH, Ly - y0);
+    int* bd = P.border + D.border_off + (long long)t * BORDER;
+    const int rrow = run_row_base(nr);
+    int* rp = P.rp + (long long)(D.tile_off + t) * RUNS + rrow;
+
+    if (m_tot <= PCAP) {
+        // A tile of at most PCAP pieces sums them in shared memory while the
+        // atomic add is in flight: a root's parent slot takes -2 - (its local
+        // index k), and per piece the size, the sums of row and of column over
+        // its sites (tile coordinates) and its first site (row << 16 | column)
+        // are kept; every run's start-column byte then takes its piece's k.
+        int4* pc = s_pc[w];
+        {
+            unsigned rq = R;
+            int k = rbase;
+            while (rq) {
+                const int id = SW(lane * 32 + __ffs(rq) - 1);
+                rq &= rq - 1;
+                pc[k] = make_int4(0, 0, 0, (lane << 16) | TS.col[id]);
+                TS.par[id] = -2 - k;
+                ++k;
+            }
+        }
+        __syncwarp();
+        {
+            unsigned long long q = S0;
+            for (int j = 0; j < nr; ++j) {
+                const int c = __ffsll(q) - 1;
+                q &= q - 1;
+                const int id = SW(lane * 32 + j);
+                const int v = TS.par[id];
+                const int k = -2 - (v < 0 ? v : TS.par[SW(v)]);
+                const int len = run_length(my_m, c);
+                atomicAdd(&pc[k].x, len);
+                atomicAdd(&pc[k].y, len * lane);
+                atomicAdd(&pc[k].z, len * c + (len * (len - 1)) / 2);
+                TS.col[id] = (unsigned char)k;
+            }
+        }
+        __syncwarp();
+        if (lane == 0) {
+            if (pbase + m_tot > P.piece_cap) {
+                atomicOr(&P.g->err, ERR_PIECE_CAP);
+                atomicOr(&P.st[inst].err, ERR_PIECE_CAP);
+                pbase = -1;
+            }
+            P.tile_pbase[D.tile_off + t] = pbase;
+            P.tile_pcnt[D.tile_off + t] = m_tot;
+        }
+        pbase = __shfl_sync(0xffffffffu, pbase, 0);
+        // 4. run -> piece table (for the run-label pass) and the piece records
+        //    (coalesced; sums relative to the piece's first site)
+        for (int j = 0; j < nr; ++j)
+            if (vd_in(P, CHK_RUN_PIECE, rrow + j, RUNS)) rp[j] = pbase >= 0 ? pbase + TS.col[SW(lane * 32 + j)] : -1;
+        if (pbase >= 0) {
+            for (int k = lane; k < m_tot; k += 32) {
+                const int pid = pbase + k;
+                if (!vd_in(P, CHK_TILE_PIECES, pid, P.piece_cap)) continue;
+                const int4 e = pc[k];
+                const int fr = e.w >> 16, fc = e.w & 0xffff;
+                P.p_q[pid] = (y0 + fr) * Lx + x0 + fc;
+                P.p_inst[pid] = inst;
+                P.p_n[pid] = e.x;
+                P.p_sv[pid] = e.y - e.x * fr;
+                P.p_su[pid] = e.z - e.x * fc;
+                P.p_parent[pid] = pid;
+                P.p_accn[pid] = 0;
+                P.p_accx[pid] = 0;
+                P.p_accy[pid] = 0;
+            }
+        }
+        // 5. borders: [0,TH) left col, [TH,2TH) right col, [2TH,2TH+TW) top
+        //    row, [.., +TW) bottom row: piece id of each site, or -1
+        auto piece_at = [&](unsigned long long m, int ly, int lx) -> int {
+            if (pbase < 0 || lx >= ncols || ly >= nrows || !((m >> lx) & 1ull)) return -1;
+            return pbase + TS.col[SW(ly * 32 + run_index(run_starts(m), lx))];
+        };
+        const unsigned long long mt = TS.m[0], mb = TS.m[nrows - 1];
+        bd[lane] = piece_at(my_m, lane, 0);
+        bd[TH + lane] = piece_at(my_m, lane, ncols - 1);
+        bd[2 * TH + lane] = piece_at(mt, 0, lane);
+        bd[2 * TH + 32 + lane] = piece_at(mt, 0, lane + 32);
+        bd[2 * TH + TW + lane] = piece_at(mb, nrows - 1, lane);
+        bd[2 * TH + TW + 32 + lane] = piece_at(mb, nrows - 1, lane + 32);
+        return;
+    }
+
+    // A tile of more pieces: the records are initialised by their roots' lanes
+    // and the sums added with global atomics, runs of one piece merged across
+    // the warp first; a root's parent slot takes -2 - (its piece id).
     if (lane == 0) {
-        pbase = atomicAdd(&P.g->n_pieces, m_tot);
         if (pbase + m_tot > P.piece_cap) {
             atomicOr(&P.g->err, ERR_PIECE_CAP);
             atomicOr(&P.st[inst].err, ERR_PIECE_CAP);
@@ -359,14 +530,7 @@ __global__ __launch_bounds__(32 * CCL_WARPS, 8) void k_ccl_tiles(Pools P, StepTa
         }
     }
     __syncwarp();
-
-    // 4. per run: its piece id (kept for the run-label pass) and its share of
-    //    the piece's size and coordinate sums relative to the piece's first
-    //    site; runs of one piece are merged across the warp, then one atomic
-    //    add per group
     {
-        const int rrow = run_row_base(nr);
-        int* rp = P.rp + (long long)(D.tile_off + t) * RUNS + rrow;
         const int maxnr = __reduce_max_sync(0xffffffffu, nr);
         unsigned long long q = S0;
         for (int j = 0; j < maxnr; ++j) {
@@ -392,26 +556,18 @@ __global__ __launch_bounds__(32 * CCL_WARPS, 8) void k_ccl_tiles(Pools P, StepTa
             }
         }
     }
-
-    // 5. borders: [0,TH) left col, [TH,2TH) right col, [2TH,2TH+TW) top row, [.., +TW) bottom row
-    const int ncols = min(TW, Lx - x0), nrows = min(TH, Ly - y0);
-    int* bd = P.border + D.border_off + (long long)t * BORDER;
-    for (int k = lane; k < BORDER; k += 32) {
-        int lx, ly;
-        if (k < TH) { ly = k; lx = 0; }
-        else if (k < 2 * TH) { ly = k - TH; lx = ncols - 1; }
-        else if (k < 2 * TH + TW) { lx = k - 2 * TH; ly = 0; }
-        else { lx = k - 2 * TH - TW; ly = nrows - 1; }
-        int v = -1;
-        if (lx < ncols && ly < nrows) {
-            const unsigned long long m = TS.m[ly];
-            if ((m >> lx) & 1ull) {
-                int root;
-                v = run_piece(TS, ly * 32 + run_index(run_starts(m), lx), &root);
-            }
-        }
-        bd[k] = v;
-    }
+    auto piece_at = [&](unsigned long long m, int ly, int lx) -> int {
+        if (lx >= ncols || ly >= nrows || !((m >> lx) & 1ull)) return -1;
+        int root;
+        return run_piece(TS, ly * 32 + run_index(run_starts(m), lx), &root);
+    };
+    const unsigned long long mt = TS.m[0], mb = TS.m[nrows - 1];
+    bd[lane] = piece_at(my_m, lane, 0);
+    bd[TH + lane] = piece_at(my_m, lane, ncols - 1);
+    bd[2 * TH + lane] = piece_at(mt, 0, lane);
+    bd[2 * TH + 32 + lane] = piece_at(mt, 0, lane + 32);
+    bd[2 * TH + TW + lane] = piece_at(mb, nrows - 1, lane);
+    bd[2 * TH + TW + 32 + lane] = piece_at(mb, nrows - 1, lane + 32);
 }
 
 // ---------------------------------------------------------------------------

@@ -312,6 +312,21 @@ __device__ __forceinline__ int seg_of(const long long* pre, int n_act, long long
 __device__ __forceinline__ int seg_of_int(const int* pre, int n_act, int g) {
     return upper_bound_int(pre, n_act + 1, g) - 1;
 }
+// seg_of_int for an index g held by every lane of a full warp: each round the
+// lanes read 32 evenly spaced entries of the remaining range and vote, so the
+// search takes ceil(log32(n_act + 1)) dependent loads instead of log2.
+__device__ __forceinline__ int warp_seg_of_int(const int* pre, int n_act, int g) {
+    const int lane = threadIdx.x & 31;
+    int lo = 0, n = n_act + 1;           // the answer lies in [lo, lo + n), pre[lo] <= g
+    for (;;) {
+        const int s = (n + 31) >> 5;
+        const unsigned v = __ballot_sync(0xffffffffu, lane * s < n && pre[lo + lane * s] <= g);
+        const int k = __popc(v) - 1;     // pre is nondecreasing: the true lanes are a prefix
+        if (s == 1) return lo + k;
+        lo += k * s;
+        n = min(s, n - k * s);
+    }
+}
 
 // A block's copy of a segment prefix table (n_act + 1 entries) in shared
 // memory, loaded in one round, so that item -> instance searches do not chain
