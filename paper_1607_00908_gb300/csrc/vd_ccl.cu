@@ -884,7 +884,7 @@ __global__ __launch_bounds__(32 * LBL_WARPS, 10) void k_run_labels(Pools P, Step
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int b = blockIdx.x * LBL_WARPS + w;
     if (b >= T.tileA_pre[T.n_act]) return;
-    const int a = seg_of_int(T.tileA_pre, T.n_act, b);
+    const int a = warp_seg_of_int(T.tileA_pre, T.n_act, b);
     const int inst = T.act[a];
     const InstDesc& D = P.desc[inst];
     const InstState& S = P.st[inst];

@@ -572,6 +572,7 @@ void launch_ccl_rest(const Launch& L);     // border merge, ranks, centroids, bu
 void launch_labels(const Launch& L);       // run labels + overlap histogram
 void launch_voronoi(const Launch& L);      // exact owner of every site
 void launch_links(const Launch& L);        // per-tile links from the owners
+void set_kernel_attributes();              // shared-memory carveout of the link kernel
 void launch_merge_lists(const Launch& L);  // appended links/pairs -> hash tables
 void launch_merge_edges(const Launch& L);     // the links alone (forked step)
 void launch_merge_overlaps(const Launch& L);  // the overlap pairs alone (forked step)

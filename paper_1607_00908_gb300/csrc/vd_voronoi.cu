@@ -588,7 +588,7 @@ __device__ __forceinline__ void cp_async16(int* smem, const int* gmem) {
 // busy instead of with the one or two lanes of a row that cross a boundary.
 constexpr int LQ = VW * VH;     // queue of marked sites (row * 32 + column)
 
-__global__ __launch_bounds__(32 * LINK_WARPS) void k_links(Pools P, StepTable T) {
+__global__ __launch_bounds__(32 * LINK_WARPS, 6) void k_links(Pools P, StepTable T) {
     pdl_enter();
     __shared__ __align__(16) int s_own[LINK_WARPS][(VH + 1) * LS];
     __shared__ unsigned long long s_list[LINK_WARPS][LSET];
@@ -597,7 +597,7 @@ __global__ __launch_bounds__(32 * LINK_WARPS) void k_links(Pools P, StepTable T)
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int b = blockIdx.x * LINK_WARPS + warp;
     if (b >= T.tileV_pre[T.n_act]) return;
-    const int a = seg_of_int(T.tileV_pre, T.n_act, b);
+    const int a = warp_seg_of_int(T.tileV_pre, T.n_act, b);
     const int inst = T.act[a];
     const InstDesc& D = P.desc[inst];
     const int K = min(P.st[inst].K, D.comp_cap);
@@ -890,7 +890,7 @@ __global__ __launch_bounds__(32 * LINK_WARPS) void k_links_vertex(Pools P, StepT
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int b = blockIdx.x * LINK_WARPS + warp;
     if (b >= T.tileV_pre[T.n_act]) return;
-    const int a = seg_of_int(T.tileV_pre, T.n_act, b);
+    const int a = warp_seg_of_int(T.tileV_pre, T.n_act, b);
     const int inst = T.act[a];
     const InstDesc& D = P.desc[inst];
     const InstState& St = P.st[inst];
@@ -1077,7 +1077,7 @@ __global__ __launch_bounds__(32 * LINK_WARPS) void k_mask_owners(Pools P, StepTa
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int b = blockIdx.x * LINK_WARPS + warp;
     if (b >= T.tileV_pre[T.n_act]) return;
-    const int a = seg_of_int(T.tileV_pre, T.n_act, b);
+    const int a = warp_seg_of_int(T.tileV_pre, T.n_act, b);
     const int inst = T.act[a];
     const InstDesc& D = P.desc[inst];
     if (!D.masked) return;
@@ -1092,6 +1092,16 @@ __global__ __launch_bounds__(32 * LINK_WARPS) void k_mask_owners(Pools P, StepTa
         if (x >= D.uLx || y >= D.uLy) *o = OWN_OUTSIDE;
         else if ((ob[(long long)y * D.wpr + (x >> 5)] >> (x & 31)) & 1u) *o = OWN_OBSTACLE;
     }
+}
+
+// k_links holds 35 KB of shared memory per block; six blocks per SM (the
+// register bound of its launch bounds) need the largest shared-memory
+// carveout, which the driver need not choose by itself. Host-side, once per
+// context creation, outside any stream capture.
+void set_kernel_attributes() {
+    if (cudaFuncSetAttribute(k_links, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             (int)cudaSharedmemCarveoutMaxShared) != cudaSuccess)
+        cudaGetLastError();   // a preference only: the kernel runs either way
 }
 
 void launch_links(const Launch& L) {
