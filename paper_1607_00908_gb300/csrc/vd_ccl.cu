@@ -294,7 +294,7 @@ __device__ __forceinline__ bool is_fg(float v, float thr, int pol) {
 }
 
 constexpr int CCL_WARPS = 4;    // tiles per block in pass A
-constexpr int PCAP = 64;        // pieces per tile summed in shared memory
+constexpr int PCAP = 32;        // pieces per tile summed in shared memory
 
 // Threshold (Section 3.1) of a 64 x 32 tile, read straight from the field
 // with coalesced 16-byte loads: one warp load covers two tile rows (lanes
@@ -350,9 +350,47 @@ __device__ __forceinline__ unsigned long long threshold_tile(const float* f0, lo
 }
 
 // ---------------------------------------------------------------------------
+// Threshold pass (Section 3.1): one warp per 64 x 32 labelling tile reads the
+// field with coalesced loads and stores the tile's foreground words (kept for
+// the labelling, the run-label pass and the next frame). Alone, it streams the
+// field at the HBM rate; the union-find that follows reads the words from L2.
+// ---------------------------------------------------------------------------
+constexpr int THR_WARPS = 4;
+
+__global__ __launch_bounds__(32 * THR_WARPS, 8) void k_threshold(Pools P, StepTable T) {
+    pdl_enter();
+    const int lane = threadIdx.x & 31;
+    const int b = blockIdx.x * THR_WARPS + (threadIdx.x >> 5);
+    if (b >= T.tileA_pre[T.n_act]) return;
+    const int a = warp_seg_of_int(T.tileA_pre, T.n_act, b);
+    const int inst = T.act[a];
+    const InstDesc& D = P.desc[inst];
+    const InstState& S = P.st[inst];
+    const int t = b - T.tileA_pre[a];
+    const int x0 = (t % D.ntx) * TW, y0 = (t / D.ntx) * TH;
+    // the field covers the domain only (a bounded axis runs with twice its
+    // length; the second half is never a bubble)
+    unsigned long long m = threshold_tile(S.field + (long long)y0 * S.pitch + x0, S.pitch,
+                                          min(TH, min(D.Ly, D.uLy) - y0), min(TW, D.uLx - x0), D.thr, D.pol);
+    const int y = y0 + lane;
+    if (y < D.Ly) {
+        const int n = min(TW, D.Lx - x0);
+        unsigned* row = P.fgbits[S.slot ^ 1] + D.word_off + (long long)y * D.wpr + (x0 >> 5);
+        if (D.masked) {   // obstacle sites are never in a bubble
+            const unsigned* ob = P.obst + D.word_off + (long long)y * D.wpr + (x0 >> 5);
+            unsigned long long om = ob[0];
+            if (n > 32) om |= (unsigned long long)ob[1] << 32;
+            m &= ~om;
+        }
+        row[0] = (unsigned)m;
+        if (n > 32) row[1] = (unsigned)(m >> 32);
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Pass A: union-find over runs + pieces + borders (one warp per tile)
 // ---------------------------------------------------------------------------
-__global__ __launch_bounds__(32 * CCL_WARPS, 8) void k_ccl_tiles(Pools P, StepTable T) {
+__global__ __launch_bounds__(32 * CCL_WARPS, 9) void k_ccl_tiles(Pools P, StepTable T) {
     pdl_enter();
     __shared__ UfSmem s_tile[CCL_WARPS];
     __shared__ int4 s_pc[CCL_WARPS][PCAP];   // per piece: size, row sum, column sum, first site
@@ -369,29 +407,8 @@ __global__ __launch_bounds__(32 * CCL_WARPS, 8) void k_ccl_tiles(Pools P, StepTa
     const int x0 = tx * TW, y0 = ty * TH;
     const int Lx = D.Lx, Ly = D.Ly;
 
-    // 1. threshold (coalesced, one tile row per step; lane r keeps row r),
-    //    then lane r stores row r's foreground words (kept for the run-label
-    //    pass and the next frame). The field covers the domain only (a
-    //    bounded axis runs with twice its length; the second half is never a
-    //    bubble).
-    unsigned long long my_m =
-        threshold_tile(S.field + (long long)y0 * S.pitch + x0, S.pitch, min(TH, min(Ly, D.uLy) - y0),
-                       min(TW, D.uLx - x0), D.thr, D.pol);
-    {
-        const int y = y0 + lane;
-        if (y < Ly) {
-            const int n = min(TW, Lx - x0);
-            unsigned* row = P.fgbits[S.slot ^ 1] + D.word_off + (long long)y * D.wpr + (x0 >> 5);
-            if (D.masked) {   // obstacle sites are never in a bubble
-                const unsigned* ob = P.obst + D.word_off + (long long)y * D.wpr + (x0 >> 5);
-                unsigned long long om = ob[0];
-                if (n > 32) om |= (unsigned long long)ob[1] << 32;
-                my_m &= ~om;
-            }
-            row[0] = (unsigned)my_m;
-            if (n > 32) row[1] = (unsigned)(my_m >> 32);
-        }
-    }
+    // 1. this tile's row masks, stored by the threshold pass (lane r: row r)
+    const unsigned long long my_m = load_row_mask(P.fgbits[S.slot ^ 1], D, x0, y0);
     TS.m[lane] = my_m;
 
     // 2. union-find over runs
@@ -1021,6 +1038,7 @@ void launch_expand_labels(cudaStream_t s, const Pools& P, int inst, int slot, in
 }
 
 void launch_ccl_tiles(const Launch& L) {
+    launch_step(L, k_threshold, dim3((L.total_tilesA + THR_WARPS - 1) / THR_WARPS), dim3(32 * THR_WARPS), L.P, L.T);
     launch_step(L, k_ccl_tiles, dim3((L.total_tilesA + CCL_WARPS - 1) / CCL_WARPS), dim3(32 * CCL_WARPS), L.P, L.T);
 }
 

@@ -38,7 +38,7 @@ SUBSET = " or ".join((
     "test_batch_with_mixed_options", "test_frame_sequence_matches_oracle", "overflow_then_exact_frames",
     "test_many_instances_and_a_long_sequence", "test_every_tuning_gives_the_oracle_result",
     "test_graph_stage_forms_give_the_oracle_result", "test_resumed_context_equals_uninterrupted_run_and_oracle",
-    "test_import_into_a_context_whose_last_frame_overflowed",
+    "test_import_into_a_context_whose_last_frame_overflowed", "test_pieces_per_tile_at_the_shared_sum_limit",
 ))
 
 

@@ -128,6 +128,26 @@ def test_degenerate_fields():
         run_pair([F, np.roll(F, 1, axis=1)], voronoi="brute", tag=name)
 
 
+@pytest.mark.parametrize("connectivity", [4, 8])
+def test_pieces_per_tile_at_the_shared_sum_limit(connectivity):
+    """Labelling tiles (64 x 32 sites) holding 31, 32, 33, 1, 0, 200, 64 and 65
+    pieces: a tile of up to 32 pieces sums them in shared memory, a larger one
+    with global atomics, and both must give the oracle's labels, sizes and
+    centres. Pieces are two-site runs three columns and two rows apart; the
+    second frame shifts them by three columns, so the last column of pieces
+    crosses the tile seams (and the lattice's periodic edge)."""
+    L = 128
+    F = np.zeros((L, L), np.float32)
+    counts = [31, 32, 33, 1, 0, 200, 64, 65]
+    slots = [(3 * a, 2 * b) for b in range(16) for a in range(21)]
+    for t, n in enumerate(counts):
+        x0, y0 = 64 * (t % 2), 32 * (t // 2)
+        for (x, y) in slots[:n]:
+            F[y0 + y, x0 + x:x0 + x + 2] = 1.0
+    r = run_pair([F, np.roll(F, 3, axis=1)], voronoi="brute", connectivity=connectivity, tag=f"pcap c{connectivity}")
+    assert r["K"] == sum(counts)
+
+
 def test_wide_bubbles_across_seams():
     """Bubbles wider than half the lattice and winding ones take the exact path."""
     for L in (40, 64, 96, 130):
