@@ -530,27 +530,30 @@ __global__ __launch_bounds__(32 * VWARPS, VLayout<PW, PH>::MINB) void k_voronoi(
 // appended to the instance's link list after merging equal keys.
 // ---------------------------------------------------------------------------
 constexpr int LINK_WARPS = 4;
-constexpr int LSET = 256;       // per-warp key list
+constexpr int LSET = 256;       // per-warp key list of the vertex-rule kernel
+constexpr int LSET_ADJ = 128;   // per-warp key list of k_links (further keys go straight to the link hash)
 constexpr int LS = VW + 4;      // staged row stride (rows start on 16 bytes)
 
 // list entry `pos` of a warp's keys: the link {a, b}, or EMPTY_KEY when an
 // end is not a label (obstacle, beyond a wall); past the list, straight into
 // the link hash
+template <int CAP = LSET>
 __device__ __forceinline__ void link_list_put(unsigned long long* list, int pos, int a, int b, const Pools& P,
                                               const InstDesc& D, int inst) {
     const bool ok = (a | b) >= 0;
     if (!vd_in(P, CHK_LINK_LIST, pos, 1ll << 30)) return;
-    if (pos < LSET) list[pos] = ok ? edge_key(a, b) : EMPTY_KEY;
+    if (pos < CAP) list[pos] = ok ? edge_key(a, b) : EMPTY_KEY;
     else if (ok) edge_global_insert(P, D, inst, edge_key(a, b));
 }
 
-// the first min(n, LSET) keys of a warp's list (whole warp): equal keys within
+// the first min(n, CAP) keys of a warp's list (whole warp): equal keys within
 // a round of 32 are merged, the rest appended to the instance's link list (the
 // link hash removes the remaining repeats); EMPTY_KEY entries are dropped
+template <int CAP = LSET>
 __device__ __forceinline__ void flush_link_list(const unsigned long long* list, int n, int lane, const Pools& P,
                                                 const InstDesc& D, int inst) {
     const unsigned lt = (1u << lane) - 1u;
-    n = min(n, LSET);
+    n = min(n, CAP);
     for (int kb = 0; kb < n; kb += 32) {
         const bool in = kb + lane < n;
         const unsigned long long key = in ? list[kb + lane] : EMPTY_KEY;
@@ -586,12 +589,12 @@ __device__ __forceinline__ void cp_async16(int* smem, const int* gmem) {
 // (row, column) items are compacted into a shared queue and processed with
 // every lane on a different item, so the emission rules run with all lanes
 // busy instead of with the one or two lanes of a row that cross a boundary.
-constexpr int LQ = VW * VH;     // queue of marked sites (row * 32 + column)
+constexpr int LQ = VW * VH / 2; // queue of marked sites (row * 32 + column) of half a tile
 
-__global__ __launch_bounds__(32 * LINK_WARPS, 6) void k_links(Pools P, StepTable T) {
+__global__ __launch_bounds__(32 * LINK_WARPS, 8) void k_links(Pools P, StepTable T) {
     pdl_enter();
     __shared__ __align__(16) int s_own[LINK_WARPS][(VH + 1) * LS];
-    __shared__ unsigned long long s_list[LINK_WARPS][LSET];
+    __shared__ unsigned long long s_list[LINK_WARPS][LSET_ADJ];
     __shared__ unsigned short s_q[LINK_WARPS][LQ];
     __shared__ int s_n[LINK_WARPS];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -655,76 +658,81 @@ __global__ __launch_bounds__(32 * LINK_WARPS, 6) void k_links(Pools P, StepTable
             rt = dg;
         }
     }
-    // compact the marked sites into the queue (row-major order is not needed)
-    const int cnt = __popc(mark);
-    int inc = cnt;
+    // the marked sites of rows 0-15, then of rows 16-31, are compacted into
+    // the queue (row-major order is not needed) and processed
+    for (int h = 0; h < 2; ++h) {
+        const unsigned hmark = mark & (h ? 0xffff0000u : 0x0000ffffu);
+        const int cnt = __popc(hmark);
+        int inc = cnt;
 #pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-        const int v = __shfl_up_sync(0xffffffffu, inc, d);
-        if (lane >= d) inc += v;
-    }
-    const int nq = __shfl_sync(0xffffffffu, inc, 31);
-    {
-        int pos = inc - cnt;
-        unsigned m = mark;
-        while (m) {
-            const int r = __ffs(m) - 1;
-            m &= m - 1;
-            if (vd_in(P, CHK_LINK_QUEUE, pos, LQ)) q[pos] = (unsigned short)(r * 32 + lane);
-            ++pos;
+        for (int d = 1; d < 32; d <<= 1) {
+            const int v = __shfl_up_sync(0xffffffffu, inc, d);
+            if (lane >= d) inc += v;
         }
-    }
-    __syncwarp();
+        const int nq = __shfl_sync(0xffffffffu, inc, 31);
+        {
+            int pos = inc - cnt;
+            unsigned m = hmark;
+            while (m) {
+                const int r = __ffs(m) - 1;
+                m &= m - 1;
+                if (vd_in(P, CHK_LINK_QUEUE, pos, LQ)) q[pos] = (unsigned short)(r * 32 + lane);
+                ++pos;
+            }
+        }
+        __syncwarp();
 
-    // ---- 2. the emission rules at every marked site, one site per lane.
-    // The tile answers for the adjacencies anchored in it, H(l,r) between
-    // sites (l,r),(l+1,r) and V(l,r) between (l,r),(l,r+1). Ordering anchors
-    // by (row, column) with H before V at the same anchor, an adjacency is
-    // emitted only if none of the earlier adjacencies that share a dual
-    // corner with it joins the same two owners:
-    //   H(l,r): H(l,r-1), V(l,r-1), V(l+1,r-1)   (r > 0)
-    //   V(l,r): H(l-1,r), V(l-1,r) (l > 0), H(l,r)
-    // Every suppressed adjacency points to a strictly earlier one with the
-    // same owner pair, which is emitted or suppressed in turn, so by induction
-    // over the order every pair that meets somewhere is emitted at least once
-    // (the tiles of the referenced anchors process them). A straight boundary
-    // crossing the tile is emitted once instead of once per row. Four-owner
-    // plaquettes add their incircle link. A pair with a negative owner
-    // (obstacle, beyond a wall) is dropped when its key is listed, a plaquette
-    // with one before its centres are read.
-    for (int i = lane; i < nq; i += 32) {
-        const int it = q[i];
-        const int r = it >> 5, l = it & 31;
-        const int* row = S + r * LS + l;
-        const int o = row[0], rt = row[1], dn = row[LS], dg = row[LS + 1];
-        if (o != rt) {
-            bool sup = false;
-            if (r > 0) {
-                const int up = row[-LS], upr = row[-LS + 1];
-                sup = up == rt || upr == o || (up == o && upr == rt);
+        // ---- 2. the emission rules at every marked site, one site per lane.
+        // The tile answers for the adjacencies anchored in it, H(l,r) between
+        // sites (l,r),(l+1,r) and V(l,r) between (l,r),(l,r+1). Ordering anchors
+        // by (row, column) with H before V at the same anchor, an adjacency is
+        // emitted only if none of the earlier adjacencies that share a dual
+        // corner with it joins the same two owners:
+        //   H(l,r): H(l,r-1), V(l,r-1), V(l+1,r-1)   (r > 0)
+        //   V(l,r): H(l-1,r), V(l-1,r) (l > 0), H(l,r)
+        // Every suppressed adjacency points to a strictly earlier one with the
+        // same owner pair, which is emitted or suppressed in turn, so by induction
+        // over the order every pair that meets somewhere is emitted at least once
+        // (the tiles of the referenced anchors process them). A straight boundary
+        // crossing the tile is emitted once instead of once per row. Four-owner
+        // plaquettes add their incircle link. A pair with a negative owner
+        // (obstacle, beyond a wall) is dropped when its key is listed, a plaquette
+        // with one before its centres are read.
+        for (int i = lane; i < nq; i += 32) {
+            const int it = q[i];
+            const int r = it >> 5, l = it & 31;
+            const int* row = S + r * LS + l;
+            const int o = row[0], rt = row[1], dn = row[LS], dg = row[LS + 1];
+            if (o != rt) {
+                bool sup = false;
+                if (r > 0) {
+                    const int up = row[-LS], upr = row[-LS + 1];
+                    sup = up == rt || upr == o || (up == o && upr == rt);
+                }
+                if (!sup) link_list_put<LSET_ADJ>(list, atomicAdd(&s_n[warp], 1), o, rt, P, D, inst);
             }
-            if (!sup) link_list_put(list, atomicAdd(&s_n[warp], 1), o, rt, P, D, inst);
-        }
-        if (o != dn && rt != dn) {
-            bool sup = false;
-            if (l > 0) {
-                const int lf = row[-1], dlf = row[LS - 1];
-                sup = lf == dn || (lf == o && dlf == dn);
+            if (o != dn && rt != dn) {
+                bool sup = false;
+                if (l > 0) {
+                    const int lf = row[-1], dlf = row[LS - 1];
+                    sup = lf == dn || (lf == o && dlf == dn);
+                }
+                if (!sup) link_list_put<LSET_ADJ>(list, atomicAdd(&s_n[warp], 1), o, dn, P, D, inst);
             }
-            if (!sup) link_list_put(list, atomicAdd(&s_n[warp], 1), o, dn, P, D, inst);
-        }
-        if (o != rt && o != dn && o != dg && rt != dn && rt != dg && dn != dg) {
-            int pa = -1, pb = -1;
-            if ((o | rt | dn | dg) >= 0) {
-                const unsigned long long pk = plaquette_key(o, rt, dg, dn, cq, MX, MY);
-                pa = (int)(pk >> 32);
-                pb = (int)(pk & 0xffffffffu);
+            if (o != rt && o != dn && o != dg && rt != dn && rt != dg && dn != dg) {
+                int pa = -1, pb = -1;
+                if ((o | rt | dn | dg) >= 0) {
+                    const unsigned long long pk = plaquette_key(o, rt, dg, dn, cq, MX, MY);
+                    pa = (int)(pk >> 32);
+                    pb = (int)(pk & 0xffffffffu);
+                }
+                link_list_put<LSET_ADJ>(list, atomicAdd(&s_n[warp], 1), pa, pb, P, D, inst);
             }
-            link_list_put(list, atomicAdd(&s_n[warp], 1), pa, pb, P, D, inst);
         }
+        __syncwarp();   // the next half overwrites the queue
     }
     __syncwarp();
-    flush_link_list(list, s_n[warp], lane, P, D, inst);
+    flush_link_list<LSET_ADJ>(list, s_n[warp], lane, P, D, inst);
 }
 
 // appended links -> link hash (+ degrees); appended pairs -> overlap hash
