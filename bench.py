@@ -58,12 +58,12 @@ METRIC_BYTES_PER_SITE = 16.0
 # roofline.traffic. The owner stage's entry depends on its patch layout
 # (VD_PATCH_*); a stage or layout not captured, or whose kernels changed since
 # the capture, reports null.
-TRAFFIC_BYTES_PER_SITE = {0: 4.146, 2: 0.278, 3: {0: 2.869}, 4: 4.338}
+TRAFFIC_BYTES_PER_SITE = {0: 4.193, 2: 0.278, 3: {0: 2.869}, 4: 4.342}
 
 # Issue-slot use (smsp__issue_active, % of peak) of the same kernels in the
 # same capture: the kernels are bound by instruction issue or latency, not by
 # DRAM, and this says how close to the issue limit they run.
-ISSUE_ACTIVE_PCT = {0: 50.0, 2: 48.3, 3: {0: 72.9}, 4: 40.7}
+ISSUE_ACTIVE_PCT = {0: 64.7, 2: 49.5, 3: {0: 73.1}, 4: 57.9}
 
 
 def per_stage(table, stage, patch):
@@ -250,8 +250,8 @@ def run_reference(args, world, rank):
 def stage_bytes(sequence: bool):
     """Algorithmic bytes per site of the stages that touch every site.
 
-    stage 0 threshold + tile union-find (one kernel): field read 4,
-            foreground bit write 1/8
+    stage 0 threshold pass + tile union-find: field read 4, foreground
+            bit write 1/8 (the union-find re-reads the bits, from L2)
     stage 2 run labels + overlaps: foreground bits of the frame and of its
             past frame, 1/8 + 1/8 (run tables are per run, not per site)
     stage 3 Voronoi owners: owner write 4

@@ -3,11 +3,12 @@
 // 1/1024-site fixed point, the centroid bucket grid, and the run-label pass
 // that also builds the past/now overlap histogram (Section 3.2.3).
 //
-// Labelling works on 64 x 32 tiles. Pass A reads the field once (vector
-// loads, one tile row per lane), stores the foreground bits (1 bit per site),
-// runs a union-find in shared memory and emits one "piece" per tile-local component with its size
-// and coordinate sums relative to its first site, plus the piece ids along the
-// four tile borders. Pieces are then merged across tile borders (periodic) by
+// Labelling works on 64 x 32 tiles. The threshold pass reads the field once
+// (coalesced 16-byte loads, two tile rows per warp load) and stores the
+// foreground bits (1 bit per site); pass A reads a tile's row words, runs a
+// union-find over its runs in shared memory and emits one "piece" per
+// tile-local component with its size and coordinate sums relative to its
+// first site, plus the piece ids along the four tile borders. Pieces are then merged across tile borders (periodic) by
 // a global union-find whose root is the piece with the smallest first site, so
 // the root of every bubble is the bubble's smallest linear index; bubble ids
 // are the ranks of those roots (a scan of root counts per 256-site group of a
