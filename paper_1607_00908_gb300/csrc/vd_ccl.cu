@@ -121,10 +121,12 @@ __device__ __forceinline__ void runion(int* p, int a, int b) {
 struct UfSmem {                  // one warp's tile: row masks and union-find over runs
     unsigned long long m[TH];
     int par[RUNS];               // swizzled: parent of run id k at par[SW(k)]
-    unsigned char col[RUNS];     // swizzled: start column of each run
+    unsigned char col[RUNS];     // swizzled: start column of each run (pass A: then the run's
+                                 // piece index within the tile, in a tile of at most PCAP pieces)
 };
-// piece id of run `id` after pass A has stored -2 - (piece id) in the parent
-// slot of every root; *root = the run id of its root
+// piece id of run `id` in a tile of more than PCAP pieces, after pass A has
+// stored -2 - (piece id) in the parent slot of every root; *root = the run id
+// of its root
 __device__ __forceinline__ int run_piece(const UfSmem& T, int id, int* root) {
     const int v = T.par[SW(id)];
     if (v < 0) {
